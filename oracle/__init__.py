@@ -1,0 +1,31 @@
+"""CPU FP64 oracle for the commutator-free exponential time-propagator (CFET).
+
+TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, obviously correct
+restatement of Alvermann & Fehske, "High-order commutator-free exponential
+time-propagation of driven quantum systems" (arXiv:1102.5071), written in
+numpy float64 / complex128.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline leg may import it.  The CUDA product path never
+imports, links or calls anything in here, and nothing in here calls the CUDA
+path: the two share no code.
+
+Modules
+-------
+schemes    coefficient tables f_{i,n} (Tables 1-5), the symmetric expansion
+           rule R1 (Eq. FSymm), shifted Legendre polynomials (Sec. 3.1),
+           Gauss-Legendre points/weights (Table 6) and g_{i,m} (Eq. OmGLeg).
+operators  H v for the driven XXZ chain (Pauli-string definitions, Eq. 53-54
+           style spin operators), the transverse field, banded (DIA) and dense
+           operators.
+krylov     Lanczos / Krylov evaluation of exp(-i tau H) psi (Sec. 7.1) with
+           the a-posteriori error estimate and time substepping.
+cfet       the CFET time step (Eq. Ucf with Eq. OmGLeg) and time stepping
+           (Sec. 6.1).
+
+Parity status: every function listed above is pinned by ``tests/test_oracle_*``
+against closed forms or library routines, except the whole-pipeline result at
+the driven-chain and grid-atom workloads, which no closed form covers; those
+are pinned only through properties (factorisation at J=0, time-independent
+exactness, order slopes, unitarity).
+"""
+
+__all__ = ["schemes", "operators", "krylov", "cfet"]

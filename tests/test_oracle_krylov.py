@@ -1,0 +1,92 @@
+"""Pins for oracle/krylov.py against dense library exponentials and closed forms."""
+
+import math
+
+import numpy as np
+import pytest
+from scipy.linalg import expm
+
+from oracle import krylov as K
+import workloads as W
+
+
+def _herm(n, seed):
+    a = W.complex_gaussian(seed, n * n).reshape(n, n)
+    return 0.5 * (a + a.conj().T)
+
+
+def test_tridiag_expm_matches_library():
+    alpha = W.uniform(3, 9, -2, 2)
+    beta = W.uniform(4, 8, 0.1, 1.5)
+    T = K.tridiag_matrix(alpha, beta)
+    for tau in (0.01, 0.3, 2.0):
+        y = K.tridiag_expm_e1(alpha, beta, tau)
+        ref = expm(-1j * tau * T)[:, 0]
+        assert np.max(np.abs(y - ref)) < 1e-13
+
+
+@pytest.mark.parametrize("tau", [0.05, 0.4, 3.0])
+def test_expv_dense_random_hermitian(tau):
+    # exp(-i tau H) psi vs scipy.linalg.expm on a 64-dimensional Hermitian H
+    H = _herm(64, 11)
+    psi = W.random_state(12, 64)
+    out, log, na = K.expv(lambda v: H @ v, psi, tau, tol=1e-12, m_max=30)
+    ref = expm(-1j * tau * H) @ psi
+    assert np.linalg.norm(out - ref) < 1e-10
+    assert abs(np.linalg.norm(out) - 1) < 1e-12
+
+
+def test_expv_harmonic_oscillator_substeps():
+    # Sec. 8.2: H_nn = n omega, exact psi_n(t) = exp(-i t omega n) psi_n; the
+    # large spread forces substepping with a small Krylov space
+    omega = 1.0
+    n = np.arange(50)
+    psi = W.random_state(5, 50)
+    t = 2 * math.pi / omega
+    out, log, na = K.expv(lambda v: n * omega * v, psi, t, tol=1e-11, m_max=20, max_substeps=200)
+    exact = np.exp(-1j * t * omega * n) * psi
+    assert len(log) > 1 and any(h > 0 for k, h in log)
+    assert np.linalg.norm(out - exact) < 1e-9
+
+
+def test_expv_fixed_k_error_order():
+    # Sec. 8.1: for fixed K the Krylov error of exp(-i H dt) is of order dt^K
+    H = _herm(40, 21)
+    psi = W.random_state(22, 40)
+    errs = []
+    for tau in (0.08, 0.04):
+        out, _, _ = K.expv(lambda v: H @ v, psi, tau, tol=0.0, m_max=4)
+        errs.append(np.linalg.norm(out - expm(-1j * tau * H) @ psi))
+    slope = math.log2(errs[0] / errs[1])
+    assert 3.6 < slope < 4.4, slope
+
+
+def test_expv_eigenvector_breakdown():
+    H = _herm(16, 31)
+    lam, Q = np.linalg.eigh(H)
+    psi = Q[:, 3].astype(np.complex128)
+    out, log, na = K.expv(lambda v: H @ v, psi, 0.7, tol=1e-12, m_max=10)
+    assert log == [(1, 0)] and na == 1
+    assert np.linalg.norm(out - np.exp(-0.7j * lam[3]) * psi) < 1e-13
+
+
+def test_expv_zero_operator_is_identity():
+    psi = W.random_state(7, 12)
+    out, log, na = K.expv(lambda v: 0 * v, psi, 0.3, tol=1e-12, m_max=8)
+    assert np.array_equal(out, psi) or np.linalg.norm(out - psi) < 1e-15
+
+
+def test_expv_forced_replay_is_identical():
+    H = _herm(48, 41)
+    psi = W.random_state(42, 48)
+    out, log, _ = K.expv(lambda v: H @ v, psi, 1.5, tol=1e-10, m_max=10, max_substeps=400)
+    out2, log2, _ = K.expv(lambda v: H @ v, psi, 1.5, tol=1e-10, m_max=10, max_substeps=400, forced=log)
+    assert any(h > 0 for _, h in log)
+    assert log2 == log and np.array_equal(out, out2)
+
+
+def test_expv_substep_cap_raises():
+    n = np.arange(200)
+    psi = W.random_state(5, 200)
+    with pytest.raises(K.KrylovError):
+        K.expv(lambda v: 50.0 * n * v, psi, 1.0, tol=1e-12, m_max=4, max_substeps=3)
