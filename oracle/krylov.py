@@ -23,6 +23,10 @@ reading (the CUDA path implements the same rule):
 * acceptance: the smallest k >= m_min with err_k <= tol * tau_s / tau
   (tau the full stage time); a Lanczos breakdown beta_k <= bd_tol * (|alpha_k|
   + beta_{k-1} + 1) ends the iteration with err = 0 (invariant subspace).
+* the estimate is evaluated only when |tau_s| width(T_k) <= 2 k, width the
+  Gershgorin width of T_k (an upper bound of its eigenvalue spread); beyond
+  that the bound Eq. (KryErr), which needs 2 rho <= K with 4 rho = tau times
+  the spread, gives no assurance and the step counts as not converged.
 * if no k <= m_max is accepted, the same basis is reused with tau_s halved
   (tau_s = remaining / 2^h, h = 1, 2, ...) until err <= tol * tau_s / tau;
   psi is advanced by tau_s, the basis is rebuilt from the new psi for the
@@ -64,6 +68,17 @@ def tridiag_expm_e1(alpha, beta, tau):
     T = tridiag_matrix(alpha, beta)
     lam, Q = np.linalg.eigh(T)
     return Q @ (np.exp(-1j * tau * lam) * Q[0, :])
+
+
+def gershgorin_width(alpha, beta):
+    """max_r (alpha_r + |beta_{r-1}| + |beta_r|) - min_r (alpha_r - |beta_{r-1}| - |beta_r|)."""
+    k = len(alpha)
+    lo, hi = np.inf, -np.inf
+    for r in range(k):
+        rad = (abs(beta[r - 1]) if r > 0 else 0.0) + (abs(beta[r]) if r < k - 1 else 0.0)
+        lo = min(lo, alpha[r] - rad)
+        hi = max(hi, alpha[r] + rad)
+    return hi - lo
 
 
 def expv(apply, psi, tau, tol, m_max, m_min=2, max_substeps=64, forced=None):
@@ -123,7 +138,7 @@ def expv(apply, psi, tau, tol, m_max, m_min=2, max_substeps=64, forced=None):
             if breakdown:
                 accepted = (k, 0)
                 break
-            if k >= m_min:
+            if k >= m_min and abs(remaining) * gershgorin_width(alpha, beta[:k - 1]) <= 2 * k:
                 y = tridiag_expm_e1(alpha, beta[:k - 1], remaining)
                 err = beta0 * b * abs(y[k - 1])
                 if err <= tol * remaining / tau:
@@ -135,8 +150,11 @@ def expv(apply, psi, tau, tol, m_max, m_min=2, max_substeps=64, forced=None):
         if accepted is None:
             # not converged at m_max: halve the substep on the same basis
             k = m_max
+            width = gershgorin_width(alpha, beta[:k - 1])
             for h in range(1, MAX_HALVINGS + 1):
                 ts = remaining / (2.0 ** h)
+                if not abs(ts) * width <= 2 * k:
+                    continue
                 y = tridiag_expm_e1(alpha, beta[:k - 1], ts)
                 err = beta0 * beta[k - 1] * abs(y[k - 1])
                 if err <= tol * ts / tau:
