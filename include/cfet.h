@@ -1,0 +1,246 @@
+/*
+ * cfet.h -- C ABI of the GB300 (sm_103a) commutator-free exponential
+ * time-propagator (CFET) library.
+ *
+ * The library propagates a wave function psi under the time-dependent
+ * Schroedinger equation  i d/dt psi = H(t) psi  (Sec. 1 of Alvermann & Fehske,
+ * arXiv:1102.5071) with
+ *
+ *     H(t) = H0 + sum_{k=1..nV} f_k(t) V_k .
+ *
+ * One CFET time step from t to t+dt is the product of s exponentials
+ * (Sec. 4, Eq. (Ucf)); by Gauss-Legendre quadrature each exponential is
+ * exp(-i dt H_j) with the weighted sum  H_j = sum_m g_{j,m} H(t + x_m dt)
+ * (Sec. 7, Eq. (OmGLeg)), i.e.
+ *
+ *     H_j = c_{j,0} H0 + sum_k c_{j,k} V_k,
+ *     c_{j,0} = sum_m g_{j,m},   c_{j,k} = sum_m g_{j,m} f_k(t + x_m dt),
+ *
+ * so H_j is never formed: the apply kernels take the per-stage scalars c_{j,*}
+ * (Sec. 8: weighted sums keep the sparsity pattern of H).  Each exponential
+ * acting on psi is evaluated by a Lanczos/Krylov loop on the device (Sec. 8.1)
+ * with an a-posteriori error estimate, adaptive Krylov dimension and time
+ * substepping.  exp(Omega_s) is applied first and exp(Omega_1) last (Sec. 2.2).
+ *
+ * Conventions common to every entry point:
+ *  - All vectors are complex128 (interleaved re, im doubles), 16-byte aligned,
+ *    length `dim`, in DEVICE memory owned by the caller, unless an argument
+ *    says "host".  psi is updated in place and is not renormalised.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    stream-ordered.  A call that returns device results to the host
+ *    (non-NULL stats, decision logs, cfet_propagate_host) synchronises the
+ *    stream before returning; otherwise the call returns after enqueueing.
+ *  - Every entry point validates its arguments first.  On CFET_EINVAL no device
+ *    work has been issued.  The text of the last error of a context is
+ *    available from cfet_last_error().
+ *  - The library never falls back to a CPU path: without a usable CUDA device
+ *    every call that would compute returns CFET_ENODEV.
+ *  - Device-side waits (grid barriers of the persistent kernel) are bounded by
+ *    cfet_options.barrier_timeout_s; on expiry the kernel records
+ *    CFET_ETIMEOUT, leaves psi in an unspecified state and returns.
+ */
+#ifndef CFET_H
+#define CFET_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum cfet_status {
+  CFET_OK = 0,
+  CFET_EINVAL = 1,    /* invalid argument (no device work issued)            */
+  CFET_ENOMEM = 2,    /* device or pinned-host allocation failed              */
+  CFET_ECUDA = 3,     /* a CUDA runtime call failed                           */
+  CFET_EKRYLOV = 4,   /* a stage exponential needed more than max_substeps    */
+  CFET_ETIMEOUT = 5,  /* a device grid barrier exceeded its wait limit        */
+  CFET_ENAN = 6,      /* psi norm not finite at the start of an exponential   */
+  CFET_ENODEV = 7     /* no CUDA device usable by this library                */
+} cfet_status;
+
+/* ------------------------------------------------------------------------ */
+/* Operators                                                                 */
+/* ------------------------------------------------------------------------ */
+/* Spin-1/2 chains use the basis index x in [0, 2^nsites); bit i of x is site
+ * i; bit value 0 is spin up (sigma_z = +1).  With the Pauli matrices of
+ * Sec. 6.2:  Z_i|x> = (1-2 b_i)|x>,  X_i|x> = |x ^ 2^i>,
+ * Y_i|x> = i (1-2 b_i) |x ^ 2^i>.                                           */
+enum {
+  /* open XXZ chain (the spin chain of Sec. 11.1, Eq. (SpinChain1), with an
+   * Ising anisotropy and site fields):
+   *   H = sum_{i<N-1} [ J (X_i X_{i+1} + Y_i Y_{i+1}) + J*Delta Z_i Z_{i+1} ]
+   *       + sum_i h_i Z_i
+   * uses: nsites, J, Delta, site_coeff = h[nsites] (host, copied).          */
+  CFET_OP_XXZ_CHAIN = 1,
+  /* transverse field  V = sum_i a_i X_i ;  uses nsites, site_coeff = a[nsites]
+   * (host, copied).  Only valid as a drive operator V_k of an XXZ chain.    */
+  CFET_OP_X_FIELD = 2,
+  /* real banded operator in DIA form:
+   *   (D v)[r] = sum_d values[d*dim + r] * v[r + offsets[d]]
+   * terms with r + offsets[d] outside [0, dim) are absent.  uses dim, ndiag,
+   * offsets[ndiag] (host, int64, copied), values[ndiag*dim] (host, copied,
+   * row-aligned).  The caller guarantees the operator is symmetric.        */
+  CFET_OP_DIA = 3
+};
+
+typedef struct cfet_op {
+  int32_t kind;               /* CFET_OP_*                                   */
+  int32_t nsites;             /* spin operators: chain length, dim = 2^nsites */
+  int64_t dim;                /* Hilbert-space dimension                      */
+  double J, Delta;            /* XXZ_CHAIN couplings                          */
+  const double* site_coeff;   /* XXZ_CHAIN: h_i; X_FIELD: a_i  (host)         */
+  int32_t ndiag;              /* DIA: number of stored diagonals              */
+  const int64_t* offsets;     /* DIA: offsets[ndiag] (host)                   */
+  const double* values;       /* DIA: values[ndiag*dim] (host)                */
+} cfet_op;
+
+/* Drive f_k(t), called on the host only at the Gauss-Legendre nodes
+ * t + x_m dt of each step while cfet_propagate builds its stage scalars.   */
+typedef double (*cfet_drive_fn)(double t, void* user);
+
+/* ------------------------------------------------------------------------ */
+/* Schemes (coefficient tables of Secs. 4.2-4.4, 5.2-5.3)                    */
+/* ------------------------------------------------------------------------ */
+enum {
+  CFET_SCHEME_DEFAULT = 0,    /* default for the order: 2->CF2:1, 4->CF4:2,
+                                 6->CF6:5Opt, 8->CF8:11                       */
+  CFET_SCHEME_CF2_1 = 1,      /* Eq. (UCF2)                                   */
+  CFET_SCHEME_CF4_2 = 2,      /* Table 4thCFET, Eq. (UCF4:2)                  */
+  CFET_SCHEME_CF4_3 = 3,      /* Table 4thCFET                                */
+  CFET_SCHEME_CF4_3OPT = 4,   /* Table 4thCFETOpt, Eq. (CF4Optimal)           */
+  CFET_SCHEME_CF6_4 = 5,      /* Table 6thCFET                                */
+  CFET_SCHEME_CF6_5 = 6,      /* Table 6thCFET                                */
+  CFET_SCHEME_CF6_5B = 7,     /* Table 6thCFET (Blanes-Moan)                  */
+  CFET_SCHEME_CF6_6 = 8,      /* Table 6thCFET                                */
+  CFET_SCHEME_CF6_5IMP = 9,   /* Table 6thCFETOpt                             */
+  CFET_SCHEME_CF6_5OPT = 10,  /* Table 6thCFETOpt (recommended, Sec. 12)      */
+  CFET_SCHEME_CF6_6OPT = 11,  /* Table 6thCFETOpt                             */
+  CFET_SCHEME_CF8_11 = 12     /* Table 8thCoeff                               */
+};
+
+/* Coefficients of scheme `scheme` (a CFET_SCHEME_* id, not DEFAULT) as used
+ * by the device path.  Writes order, s (exponentials), M (Gauss-Legendre
+ * points = Legendre terms), and, where the pointers are non-NULL and the
+ * capacities suffice, f[s*M] (full table after rule (R1), Eq. (FSymm)),
+ * x[M], w[M] (Table tab:GaussLeg) and g[s*M] (g_{i,m} of Sec. 7), row-major.
+ * Host only; no device needed.  Returns CFET_EINVAL for an unknown id or too
+ * small a capacity.                                                         */
+cfet_status cfet_scheme_info(int32_t scheme, int32_t* order, int32_t* s, int32_t* M,
+                             double* f, double* x, double* w, double* g, int32_t capacity);
+
+/* ------------------------------------------------------------------------ */
+/* Context                                                                   */
+/* ------------------------------------------------------------------------ */
+typedef struct cfet_options {
+  int32_t m_max;             /* Krylov dimension limit (default 16, <= 64)    */
+  int32_t m_min;             /* first dimension tested (default 2, >= 1)      */
+  int32_t max_substeps;      /* per stage exponential (default 64)            */
+  int32_t block_size;        /* threads per CTA (0 = 256; multiple of 32)     */
+  int32_t grid_size;         /* CTAs of the persistent kernel (0 = auto,
+                                capped at the co-resident maximum)            */
+  int32_t steps_per_launch;  /* CFET steps per persistent launch (0 = 256)    */
+  double barrier_timeout_s;  /* device barrier wait limit (default 2.0 s)     */
+} cfet_options;
+
+typedef struct cfet_stats {
+  int64_t n_exp;             /* stage exponentials evaluated                  */
+  int64_t n_substeps;        /* Krylov substeps (>= n_exp)                    */
+  int64_t n_applies;         /* H_j v applications (Lanczos iterations)       */
+  int32_t max_k;             /* largest Krylov dimension used                 */
+  int32_t status;            /* device status word (a cfet_status)            */
+  double max_err_est;        /* largest accepted error estimate               */
+} cfet_stats;
+
+/* Per-exponential Krylov decisions, host arrays owned by the caller.  One
+ * record per (sub)step, in execution order: k = Krylov dimension, h = number
+ * of halvings (substep length = remaining time / 2^h).  n_sub[e] counts the
+ * records of stage exponential e.  As input (`forced`) the device replays the
+ * records instead of testing its error estimate; as output (`record`) it
+ * receives the decisions taken.                                              */
+typedef struct cfet_decisions {
+  int64_t n_exp;             /* exponentials covered (n_sub has this length)  */
+  int32_t* n_sub;            /* [n_exp]                                       */
+  int32_t* k;                /* [cap]                                         */
+  int32_t* h;                /* [cap]                                         */
+  int64_t cap;               /* capacity of k and h                           */
+  int64_t len;               /* records provided (forced) / written (record)  */
+} cfet_decisions;
+
+typedef struct cfet_ctx cfet_ctx;
+
+/* Fill *opt with the defaults listed above.                                 */
+void cfet_options_default(cfet_options* opt);
+
+/* Create a propagation context for H(t) = H0 + sum_k f_k(t) V_k.
+ *  out     : receives the context (owned by the library; cfet_destroy frees)
+ *  H0      : XXZ_CHAIN or DIA operator
+ *  nV, V   : drive operators (X_FIELD for an XXZ chain, DIA for a DIA H0),
+ *            all with H0's dimension; nV <= 8
+ *  f, f_user: nV drive callbacks and their user pointers (f_user may be NULL)
+ *  opt     : options (NULL = defaults)
+ * Copies all operator data to the device and allocates the Krylov workspace
+ * ((m_max) x dim complex128) on the current CUDA device.  Errors: CFET_EINVAL
+ * (inconsistent operators or options), CFET_ENOMEM, CFET_ENODEV.            */
+cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfet_op* V,
+                        const cfet_drive_fn* f, void* const* f_user, const cfet_options* opt);
+
+void cfet_destroy(cfet_ctx* ctx);
+
+/* Text of the last error recorded on ctx (or of the last failed create when
+ * ctx is NULL).  Valid until the next call on the same context.             */
+const char* cfet_last_error(const cfet_ctx* ctx);
+
+/* ------------------------------------------------------------------------ */
+/* Hot path                                                                  */
+/* ------------------------------------------------------------------------ */
+/* Stage operator apply (Sec. 8):  v_out = (c[0] H0 + sum_k c[1+k] V_k) v_in.
+ * c: host array of 1+nV doubles.  v_in, v_out: device, dim, must not overlap. */
+cfet_status cfet_apply(cfet_ctx* ctx, const double* c, const void* v_in, void* v_out, void* stream);
+
+/* One stage exponential psi <- exp(-i tau (c[0] H0 + sum_k c[1+k] V_k)) psi by
+ * the device Lanczos loop (Sec. 8.1) with Krylov tolerance tol (tol <= 0:
+ * fixed Krylov dimension m_max, no substeps).  stats may be NULL.           */
+cfet_status cfet_expv(cfet_ctx* ctx, const double* c, double tau, void* psi, double tol,
+                      void* stream, cfet_stats* stats);
+
+/* nsteps CFET steps of length dt from time t0 with the default scheme of
+ * `order` (2, 4, 6 or 8): psi(t0 + nsteps dt) <- U psi(t0).  Step n uses
+ * t0 + n dt, so a run can be resumed exactly from (psi, t0 + n dt).
+ * krylov_tol: absolute Krylov tolerance per stage exponential (<= 0: fixed
+ * dimension m_max).  stats may be NULL (then the call does not synchronise). */
+cfet_status cfet_propagate(cfet_ctx* ctx, void* psi, double t0, double dt, int64_t nsteps,
+                           int32_t order, double krylov_tol, void* stream, cfet_stats* stats);
+
+/* As cfet_propagate with an explicit scheme id (CFET_SCHEME_*; DEFAULT uses
+ * `order`), optional forced decisions to replay and optional decision record.
+ * forced->n_exp and record->n_exp must equal nsteps * s when given.         */
+cfet_status cfet_propagate_ex(cfet_ctx* ctx, void* psi, double t0, double dt, int64_t nsteps,
+                              int32_t order, int32_t scheme, double krylov_tol, void* stream,
+                              const cfet_decisions* forced, cfet_decisions* record,
+                              cfet_stats* stats);
+
+/* End-to-end form: psi_host (host memory, dim complex128, pinned or pageable)
+ * is copied to a context-owned device buffer, propagated, and copied back;
+ * synchronises the stream before returning.                                  */
+cfet_status cfet_propagate_host(cfet_ctx* ctx, void* psi_host, double t0, double dt, int64_t nsteps,
+                                int32_t order, double krylov_tol, void* stream, cfet_stats* stats);
+
+/* Device status of the last propagation on ctx: synchronises `stream` and
+ * returns the recorded cfet_status (stats may be NULL).                     */
+cfet_status cfet_sync(cfet_ctx* ctx, void* stream, cfet_stats* stats);
+
+/* Device time in milliseconds of the persistent-kernel launches of the last
+ * cfet_propagate / cfet_propagate_ex call on ctx (CUDA events recorded inside
+ * the launch graph, immediately before the first and after the last kernel
+ * launch).  Synchronises on those events.                                   */
+cfet_status cfet_kernel_time_ms(cfet_ctx* ctx, float* ms);
+
+/* Dimension and drive-operator count of ctx (for bindings).                 */
+int64_t cfet_dim(const cfet_ctx* ctx);
+int32_t cfet_num_drives(const cfet_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CFET_H */

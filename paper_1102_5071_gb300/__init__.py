@@ -1,0 +1,270 @@
+"""GB300-native commutator-free exponential time-propagator (CFET) with a
+device Lanczos/Krylov exponential, after Alvermann & Fehske, arXiv:1102.5071.
+
+This module is the thin Python binding of the C ABI declared in
+``include/cfet.h``: it marshals arguments (torch tensors for device memory and
+streams, Python callables for the drives) and calls the compiled library.
+Every step of the propagation runs in the library's CUDA kernels; there is no
+CPU path, and a missing library or device raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _capi
+from ._capi import SCHEME_IDS, STATUS_NAMES
+
+
+class CfetError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {message}")
+
+
+# ---------------------------------------------------------------- operators
+@dataclass
+class XXZChain:
+    """H0 = sum_i [J (X_i X_{i+1} + Y_i Y_{i+1}) + J Delta Z_i Z_{i+1}] + sum_i h_i Z_i (open chain)."""
+    N: int
+    J: float
+    Delta: float
+    h: np.ndarray
+
+
+@dataclass
+class XField:
+    """V = sum_i a_i X_i."""
+    N: int
+    a: np.ndarray
+
+
+@dataclass
+class DIA:
+    """(D v)[r] = sum_d values[d, r] v[r + offsets[d]] (real, symmetric)."""
+    offsets: np.ndarray
+    values: np.ndarray
+
+
+def _op_struct(op, keep):
+    s = _capi.cfet_op()
+    if isinstance(op, XXZChain):
+        h = np.ascontiguousarray(op.h, dtype=np.float64)
+        keep.append(h)
+        s.kind, s.nsites, s.dim = _capi.CFET_OP_XXZ_CHAIN, op.N, 1 << op.N
+        s.J, s.Delta = op.J, op.Delta
+        s.site_coeff = h.ctypes.data_as(_capi.c_double_p)
+    elif isinstance(op, XField):
+        a = np.ascontiguousarray(op.a, dtype=np.float64)
+        keep.append(a)
+        s.kind, s.nsites, s.dim = _capi.CFET_OP_X_FIELD, op.N, 1 << op.N
+        s.site_coeff = a.ctypes.data_as(_capi.c_double_p)
+    elif isinstance(op, DIA):
+        off = np.ascontiguousarray(op.offsets, dtype=np.int64)
+        val = np.ascontiguousarray(op.values, dtype=np.float64)
+        keep += [off, val]
+        s.kind, s.dim, s.ndiag = _capi.CFET_OP_DIA, val.shape[1], val.shape[0]
+        s.offsets = off.ctypes.data_as(_capi.c_int64_p)
+        s.values = val.ctypes.data_as(_capi.c_double_p)
+    else:
+        raise TypeError(f"unsupported operator {type(op).__name__}")
+    return s
+
+
+def scheme_info(name_or_id):
+    """(order, s, M, f[s,M], x[M], w[M], g[s,M]) as used by the device path."""
+    lib = _capi.load()
+    sid = SCHEME_IDS[name_or_id] if isinstance(name_or_id, str) else int(name_or_id)
+    cap = 11 * 4
+    f, g = np.zeros(cap), np.zeros(cap)
+    x, w = np.zeros(4), np.zeros(4)
+    order, s, M = C.c_int32(), C.c_int32(), C.c_int32()
+    P = _capi.c_double_p
+    st = lib.cfet_scheme_info(sid, C.byref(order), C.byref(s), C.byref(M), f.ctypes.data_as(P),
+                              x.ctypes.data_as(P), w.ctypes.data_as(P), g.ctypes.data_as(P), cap)
+    if st != 0:
+        raise CfetError(st, "unknown scheme")
+    s_, M_ = s.value, M.value
+    return order.value, s_, M_, f[: s_ * M_].reshape(s_, M_), x[:M_].copy(), w[:M_].copy(), g[: s_ * M_].reshape(s_, M_)
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _check_vec(t, dim, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.complex128 or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA complex128 tensor")
+    if not t.is_contiguous() or t.numel() != dim:
+        raise ValueError(f"{name} must be contiguous with {dim} elements")
+
+
+class Propagator:
+    """CFET propagator for H(t) = H0 + sum_k f_k(t) V_k on the current CUDA device."""
+
+    def __init__(self, H0, V=(), drives=(), *, m_max=16, m_min=2, max_substeps=64, block_size=256,
+                 grid_size=0, steps_per_launch=256, barrier_timeout_s=2.0):
+        lib = _capi.load()
+        V = list(V)
+        drives = list(drives)
+        if len(V) != len(drives):
+            raise ValueError("one drive per drive operator")
+        self._keep = []
+        h0 = _op_struct(H0, self._keep)
+        varr = (_capi.cfet_op * max(1, len(V)))(*[_op_struct(v, self._keep) for v in V])
+        self._cbs = [_capi.DRIVE_FN(lambda t, u, fn=fn: float(fn(t))) for fn in drives]
+        fns = (_capi.DRIVE_FN * max(1, len(V)))(*self._cbs)
+        opt = _capi.cfet_options()
+        lib.cfet_options_default(C.byref(opt))
+        opt.m_max, opt.m_min, opt.max_substeps = m_max, m_min, max_substeps
+        opt.block_size, opt.grid_size, opt.steps_per_launch = block_size, grid_size, steps_per_launch
+        opt.barrier_timeout_s = barrier_timeout_s
+        ctx = C.c_void_p()
+        st = lib.cfet_create(C.byref(ctx), C.byref(h0), len(V), varr, fns, None, C.byref(opt))
+        if st != 0:
+            raise CfetError(st, lib.cfet_last_error(None).decode())
+        self._lib = lib
+        self._ctx = ctx
+        self.dim = int(lib.cfet_dim(ctx))
+        self.nV = len(V)
+        self.m_max = m_max
+        self.max_substeps = max_substeps
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.cfet_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _raise(self, st):
+        if st != 0:
+            raise CfetError(st, self._lib.cfet_last_error(self._ctx).decode())
+
+    def _coefs(self, c):
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        if c.shape != (1 + self.nV,):
+            raise ValueError(f"expected {1 + self.nV} stage scalars")
+        return c
+
+    def apply(self, c, v_in, v_out, stream=None):
+        """v_out = (c[0] H0 + sum_k c[1+k] V_k) v_in on the device."""
+        c = self._coefs(c)
+        _check_vec(v_in, self.dim, "v_in")
+        _check_vec(v_out, self.dim, "v_out")
+        self._raise(self._lib.cfet_apply(self._ctx, c.ctypes.data_as(_capi.c_double_p), C.c_void_p(v_in.data_ptr()),
+                                         C.c_void_p(v_out.data_ptr()), _stream_handle(stream)))
+
+    def expv(self, c, tau, psi, tol, stream=None):
+        """psi <- exp(-i tau (c[0] H0 + sum_k c[1+k] V_k)) psi; returns stats."""
+        c = self._coefs(c)
+        _check_vec(psi, self.dim, "psi")
+        stats = _capi.cfet_stats()
+        self._raise(self._lib.cfet_expv(self._ctx, c.ctypes.data_as(_capi.c_double_p), float(tau),
+                                        C.c_void_p(psi.data_ptr()), float(tol), _stream_handle(stream),
+                                        C.byref(stats)))
+        return stats.as_dict()
+
+    def propagate(self, psi, t0, dt, nsteps, order=4, tol=1e-10, scheme=None, stream=None, stats=True,
+                  forced=None, record=False, record_cap=None):
+        """nsteps CFET steps on the device tensor psi (in place).
+
+        forced: decision log to replay, a list over stage exponentials of
+        lists of (k, h).  record: return the device's decision log as well.
+        Returns stats (dict) or (stats, log) when record is true.
+        """
+        _check_vec(psi, self.dim, "psi")
+        sid = 0 if scheme is None else (SCHEME_IDS[scheme] if isinstance(scheme, str) else int(scheme))
+        if scheme is not None:
+            order = scheme_info(sid)[0]
+        default_ids = {2: 1, 4: 2, 6: 10, 8: 12}
+        if sid:
+            s = scheme_info(sid)[1]
+        elif order in default_ids:
+            s = scheme_info(default_ids[order])[1]
+        else:
+            s = 1   # invalid order: the library rejects the call with CFET_EINVAL
+        nexp = int(nsteps) * s
+        keep = []
+        fd = None
+        if forced is not None:
+            if len(forced) != nexp:
+                raise ValueError("forced log must cover nsteps * s exponentials")
+            nsub = np.array([len(x) for x in forced], dtype=np.int32)
+            ks = np.array([k for x in forced for k, _ in x], dtype=np.int32)
+            hs = np.array([h for x in forced for _, h in x], dtype=np.int32)
+            keep += [nsub, ks, hs]
+            fd = _capi.cfet_decisions(nexp, nsub.ctypes.data_as(_capi.c_int32_p), ks.ctypes.data_as(_capi.c_int32_p),
+                                      hs.ctypes.data_as(_capi.c_int32_p), len(ks), len(ks))
+        rd = None
+        if record:
+            cap = record_cap or max(1, nexp * self.max_substeps)
+            rn = np.zeros(nexp, dtype=np.int32)
+            rk = np.zeros(cap, dtype=np.int32)
+            rh = np.zeros(cap, dtype=np.int32)
+            keep += [rn, rk, rh]
+            rd = _capi.cfet_decisions(nexp, rn.ctypes.data_as(_capi.c_int32_p), rk.ctypes.data_as(_capi.c_int32_p),
+                                      rh.ctypes.data_as(_capi.c_int32_p), cap, 0)
+        st_struct = _capi.cfet_stats() if (stats or record) else None
+        st = self._lib.cfet_propagate_ex(self._ctx, C.c_void_p(psi.data_ptr()), float(t0), float(dt), int(nsteps),
+                                         int(order), sid, float(tol), _stream_handle(stream),
+                                         C.byref(fd) if fd is not None else None,
+                                         C.byref(rd) if rd is not None else None,
+                                         C.byref(st_struct) if st_struct is not None else None)
+        self._raise(st)
+        out = st_struct.as_dict() if st_struct is not None else None
+        if record:
+            log, pos = [], 0
+            for e in range(nexp):
+                n = int(rn[e])
+                log.append([(int(rk[pos + i]), int(rh[pos + i])) for i in range(n)])
+                pos += n
+            return out, log
+        return out
+
+    def propagate_host(self, psi_host, t0, dt, nsteps, order=4, tol=1e-10, stream=None):
+        """End-to-end form: psi_host (numpy complex128, or a pinned CPU tensor) is
+        copied to the device, propagated and copied back in place."""
+        if isinstance(psi_host, np.ndarray):
+            if psi_host.dtype != np.complex128 or not psi_host.flags.c_contiguous or psi_host.size != self.dim:
+                raise ValueError("psi_host must be a contiguous complex128 array of length dim")
+            ptr = psi_host.ctypes.data
+        else:
+            if psi_host.is_cuda or psi_host.numel() != self.dim:
+                raise ValueError("psi_host must be a host tensor of length dim")
+            ptr = psi_host.data_ptr()
+        stats = _capi.cfet_stats()
+        self._raise(self._lib.cfet_propagate_host(self._ctx, C.c_void_p(ptr), float(t0), float(dt), int(nsteps),
+                                                  int(order), float(tol), _stream_handle(stream), C.byref(stats)))
+        return stats.as_dict()
+
+    def kernel_time_ms(self):
+        """Device time of the persistent-kernel launches of the last propagate call."""
+        ms = C.c_float()
+        self._raise(self._lib.cfet_kernel_time_ms(self._ctx, C.byref(ms)))
+        return float(ms.value)
+
+    def sync(self, stream=None):
+        stats = _capi.cfet_stats()
+        self._raise(self._lib.cfet_sync(self._ctx, _stream_handle(stream), C.byref(stats)))
+        return stats.as_dict()
+
+
+def build():
+    from .build import build as _b
+    return _b()
+
+
+__all__ = ["Propagator", "XXZChain", "XField", "DIA", "scheme_info", "CfetError", "SCHEME_IDS", "build"]

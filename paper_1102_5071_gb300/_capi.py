@@ -1,0 +1,100 @@
+"""ctypes declarations of the C ABI in include/cfet.h (argument marshalling only)."""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+c_double_p = C.POINTER(C.c_double)
+c_int32_p = C.POINTER(C.c_int32)
+c_int64_p = C.POINTER(C.c_int64)
+
+CFET_OK, CFET_EINVAL, CFET_ENOMEM, CFET_ECUDA, CFET_EKRYLOV, CFET_ETIMEOUT, CFET_ENAN, CFET_ENODEV = range(8)
+STATUS_NAMES = ["CFET_OK", "CFET_EINVAL", "CFET_ENOMEM", "CFET_ECUDA", "CFET_EKRYLOV", "CFET_ETIMEOUT",
+                "CFET_ENAN", "CFET_ENODEV"]
+CFET_OP_XXZ_CHAIN, CFET_OP_X_FIELD, CFET_OP_DIA = 1, 2, 3
+
+SCHEME_IDS = {"CF2:1": 1, "CF4:2": 2, "CF4:3": 3, "CF4:3Opt": 4, "CF6:4": 5, "CF6:5": 6, "CF6:5b": 7,
+              "CF6:6": 8, "CF6:5Imp": 9, "CF6:5Opt": 10, "CF6:6Opt": 11, "CF8:11": 12}
+
+
+class cfet_op(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("nsites", C.c_int32), ("dim", C.c_int64), ("J", C.c_double),
+                ("Delta", C.c_double), ("site_coeff", c_double_p), ("ndiag", C.c_int32),
+                ("offsets", c_int64_p), ("values", c_double_p)]
+
+
+class cfet_options(C.Structure):
+    _fields_ = [("m_max", C.c_int32), ("m_min", C.c_int32), ("max_substeps", C.c_int32),
+                ("block_size", C.c_int32), ("grid_size", C.c_int32), ("steps_per_launch", C.c_int32),
+                ("barrier_timeout_s", C.c_double)]
+
+
+class cfet_stats(C.Structure):
+    _fields_ = [("n_exp", C.c_int64), ("n_substeps", C.c_int64), ("n_applies", C.c_int64),
+                ("max_k", C.c_int32), ("status", C.c_int32), ("max_err_est", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class cfet_decisions(C.Structure):
+    _fields_ = [("n_exp", C.c_int64), ("n_sub", c_int32_p), ("k", c_int32_p), ("h", c_int32_p),
+                ("cap", C.c_int64), ("len", C.c_int64)]
+
+
+DRIVE_FN = C.CFUNCTYPE(C.c_double, C.c_double, C.c_void_p)
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load() -> C.CDLL:
+    """Load the compiled library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: run paper_1102_5071_gb300.build.build() first")
+    lib = C.CDLL(path)
+    vp = C.c_void_p
+    sigs = {
+        "cfet_options_default": (None, [C.POINTER(cfet_options)]),
+        "cfet_scheme_info": (C.c_int, [C.c_int32, c_int32_p, c_int32_p, c_int32_p, c_double_p, c_double_p,
+                                       c_double_p, c_double_p, C.c_int32]),
+        "cfet_create": (C.c_int, [C.POINTER(vp), C.POINTER(cfet_op), C.c_int32, C.POINTER(cfet_op),
+                                  C.POINTER(DRIVE_FN), C.POINTER(vp), C.POINTER(cfet_options)]),
+        "cfet_destroy": (None, [vp]),
+        "cfet_last_error": (C.c_char_p, [vp]),
+        "cfet_apply": (C.c_int, [vp, c_double_p, vp, vp, vp]),
+        "cfet_expv": (C.c_int, [vp, c_double_p, C.c_double, vp, C.c_double, vp, C.POINTER(cfet_stats)]),
+        "cfet_propagate": (C.c_int, [vp, vp, C.c_double, C.c_double, C.c_int64, C.c_int32, C.c_double, vp,
+                                     C.POINTER(cfet_stats)]),
+        "cfet_propagate_ex": (C.c_int, [vp, vp, C.c_double, C.c_double, C.c_int64, C.c_int32, C.c_int32,
+                                        C.c_double, vp, C.POINTER(cfet_decisions), C.POINTER(cfet_decisions),
+                                        C.POINTER(cfet_stats)]),
+        "cfet_propagate_host": (C.c_int, [vp, vp, C.c_double, C.c_double, C.c_int64, C.c_int32, C.c_double, vp,
+                                          C.POINTER(cfet_stats)]),
+        "cfet_sync": (C.c_int, [vp, vp, C.POINTER(cfet_stats)]),
+        "cfet_kernel_time_ms": (C.c_int, [vp, C.POINTER(C.c_float)]),
+        "cfet_dim": (C.c_int64, [vp]),
+        "cfet_num_drives": (C.c_int32, [vp]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+EXPORTED = ["cfet_options_default", "cfet_scheme_info", "cfet_create", "cfet_destroy", "cfet_last_error",
+            "cfet_apply", "cfet_expv", "cfet_propagate", "cfet_propagate_ex", "cfet_propagate_host", "cfet_sync",
+            "cfet_kernel_time_ms",
+            "cfet_dim", "cfet_num_drives"]

@@ -1,0 +1,671 @@
+// C ABI of the CFET/Krylov propagator: contexts, argument validation, the
+// per-step stage-scalar table, and the launch driver.
+//
+// Alvermann & Fehske, arXiv:1102.5071.  A CFET step (Sec. 4, Eq. (Ucf)) is
+// exp(Omega_1) ... exp(Omega_s) with Omega_j = -i dt sum_m g_{j,m} H(t + x_m dt)
+// (Sec. 7, Eq. (OmGLeg)).  For H(t) = H0 + sum_k f_k(t) V_k the host builds,
+// for every step n and stage j, the scalars
+//     c_{j,0} = sum_m g_{j,m},   c_{j,k} = sum_m g_{j,m} f_k(t0 + n dt + x_m dt),
+// evaluating each drive once per node, orders the stage exponentials as they
+// act on psi (exp(Omega_s) first, Sec. 2.2), uploads the table and runs the
+// persistent device kernel over it.  The per-call launch sequence (table
+// upload, state reset, persistent-kernel chunks, status read-back) is
+// captured into a CUDA graph owned by the context and replayed; an unchanged
+// topology only updates the executable graph in place.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cfet_internal.h"
+
+using namespace cfet;
+
+struct cfet_ctx {
+  int device = 0;
+  int family = 0;
+  int dim = 0;
+  int nV = 0;
+  cfet_options opt{};
+  int grid = 1, block = 256;
+  std::string err;
+  // drives
+  std::vector<cfet_drive_fn> f;
+  std::vector<void*> f_user;
+  // operators
+  OpSpin spin{};
+  OpDia dia{};
+  double* d_dz_lo = nullptr;
+  double* d_dz_hi = nullptr;
+  double* d_xf = nullptr;
+  long long* d_off = nullptr;
+  int* d_opidx = nullptr;
+  double* d_val = nullptr;
+  // workspace
+  double2* d_basis = nullptr;
+  double* d_partials = nullptr;
+  unsigned* d_bar = nullptr;
+  DevStatus* d_st = nullptr;
+  DevStatus* h_st = nullptr;  // pinned
+  double* d_scal = nullptr;
+  double* h_scal = nullptr;  // pinned
+  size_t scal_cap = 0;
+  double2* d_psi_e2e = nullptr;
+  // decisions
+  int* d_dec = nullptr;  // [f_nsub | f_k | f_h | r_nsub | r_k | r_h]
+  size_t dec_cap = 0;    // ints
+  // graph driver
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaEvent_t ev_done = nullptr;
+  bool ev_pending = false;
+  cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;  // kernel timing (inside the graph)
+  bool timed = false;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+cfet_status fail(cfet_ctx* ctx, cfet_status s, const std::string& msg) {
+  if (ctx) ctx->err = msg; else g_create_err = msg;
+  return s;
+}
+
+cfet_status cuda_fail(cfet_ctx* ctx, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(ctx, e == cudaErrorMemoryAllocation ? CFET_ENOMEM : CFET_ECUDA, m);
+}
+
+#define CK(call, where)                              \
+  do {                                               \
+    cudaError_t _e = (call);                         \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e, where); \
+  } while (0)
+
+bool is_finite_d(double v) { return std::isfinite(v); }
+
+cfet_status device_available(cfet_ctx* ctx) {
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    return fail(ctx, CFET_ENODEV, "no CUDA device available");
+  }
+  return CFET_OK;
+}
+
+void free_ctx(cfet_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->ev_done) cudaEventDestroy(c->ev_done);
+  if (c->ev_k0) cudaEventDestroy(c->ev_k0);
+  if (c->ev_k1) cudaEventDestroy(c->ev_k1);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  cudaFree(c->d_dz_lo); cudaFree(c->d_dz_hi); cudaFree(c->d_xf);
+  cudaFree(c->d_off); cudaFree(c->d_opidx); cudaFree(c->d_val);
+  cudaFree(c->d_basis); cudaFree(c->d_partials); cudaFree(c->d_bar); cudaFree(c->d_st);
+  cudaFree(c->d_scal); cudaFree(c->d_psi_e2e); cudaFree(c->d_dec);
+  if (c->h_st) cudaFreeHost(c->h_st);
+  if (c->h_scal) cudaFreeHost(c->h_scal);
+  delete c;
+}
+
+cfet_status check_psi(cfet_ctx* ctx, const void* psi) {
+  if (!psi) return fail(ctx, CFET_EINVAL, "psi is NULL");
+  if (reinterpret_cast<uintptr_t>(psi) % 16 != 0) return fail(ctx, CFET_EINVAL, "psi is not 16-byte aligned");
+  return CFET_OK;
+}
+
+cfet_status ensure_scal(cfet_ctx* ctx, size_t n) {
+  if (n <= ctx->scal_cap) return CFET_OK;
+  if (ctx->ev_pending) { cudaEventSynchronize(ctx->ev_done); ctx->ev_pending = false; }
+  cudaFree(ctx->d_scal);
+  if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
+  ctx->d_scal = nullptr; ctx->h_scal = nullptr; ctx->scal_cap = 0;
+  size_t cap = n < 1024 ? 1024 : n;
+  CK(cudaMalloc(&ctx->d_scal, cap * sizeof(double)), "cudaMalloc(scalars)");
+  CK(cudaMallocHost(&ctx->h_scal, cap * sizeof(double)), "cudaMallocHost(scalars)");
+  ctx->scal_cap = cap;
+  return CFET_OK;
+}
+
+cfet_status ensure_dec(cfet_ctx* ctx, size_t n_ints) {
+  if (n_ints <= ctx->dec_cap) return CFET_OK;
+  if (ctx->ev_pending) { cudaEventSynchronize(ctx->ev_done); ctx->ev_pending = false; }
+  cudaFree(ctx->d_dec);
+  ctx->d_dec = nullptr; ctx->dec_cap = 0;
+  CK(cudaMalloc(&ctx->d_dec, n_ints * sizeof(int)), "cudaMalloc(decisions)");
+  ctx->dec_cap = n_ints;
+  return CFET_OK;
+}
+
+void fill_stats(const DevStatus& s, cfet_stats* out) {
+  if (!out) return;
+  out->n_exp = s.n_exp;
+  out->n_substeps = s.n_sub;
+  out->n_applies = s.n_app;
+  out->max_k = s.max_k;
+  out->status = s.status;
+  out->max_err_est = s.max_err;
+}
+
+// One persistent launch over exponentials [e0, e0 + ne).
+cfet_status launch_chunk(cfet_ctx* ctx, const PropParams& base, long long e0, long long ne, cudaStream_t s) {
+  PropParams p = base;
+  p.scal = base.scal + (size_t)e0 * (1 + ctx->nV);
+  p.nexp = ne;
+  p.exp_base = e0;
+  int e = ctx->family == kFamilySpin ? launch_propagate_spin(p, ctx->spin, ctx->grid, ctx->block, s)
+                                     : launch_propagate_dia(p, ctx->dia, ctx->grid, ctx->block, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, (cudaError_t)e, "persistent kernel launch");
+  return CFET_OK;
+}
+
+// Issue the whole device sequence of one propagation on stream s.
+cfet_status issue_sequence(cfet_ctx* ctx, const PropParams& base, long long nexp, long long chunk,
+                           size_t table_bytes, cudaStream_t s, bool timed) {
+  CK(cudaMemcpyAsync(ctx->d_scal, ctx->h_scal, table_bytes, cudaMemcpyHostToDevice, s), "scalar upload");
+  CK(cudaMemsetAsync(ctx->d_st, 0, sizeof(DevStatus), s), "status reset");
+  CK(cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned), s), "barrier reset");
+  if (timed) CK(cudaEventRecordWithFlags(ctx->ev_k0, s, cudaEventRecordExternal), "timing event");
+  for (long long e0 = 0; e0 < nexp; e0 += chunk) {
+    const long long ne = (nexp - e0) < chunk ? (nexp - e0) : chunk;
+    cfet_status st = launch_chunk(ctx, base, e0, ne, s);
+    if (st != CFET_OK) return st;
+  }
+  if (timed) CK(cudaEventRecordWithFlags(ctx->ev_k1, s, cudaEventRecordExternal), "timing event");
+  CK(cudaMemcpyAsync(ctx->h_st, ctx->d_st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s), "status read-back");
+  return CFET_OK;
+}
+
+PropParams base_params(cfet_ctx* ctx, double2* psi, double tau, double tol) {
+  PropParams p{};
+  p.dim = ctx->dim;
+  p.nV = ctx->nV;
+  p.psi = psi;
+  p.basis = ctx->d_basis;
+  p.scal = ctx->d_scal;
+  p.tau = tau;
+  p.tol = tol;
+  p.m_min = ctx->opt.m_min;
+  p.m_max = ctx->opt.m_max;
+  p.max_substeps = ctx->opt.max_substeps;
+  p.partials = ctx->d_partials;
+  p.bar = ctx->d_bar;
+  p.st = ctx->d_st;
+  p.timeout_ns = (long long)(ctx->opt.barrier_timeout_s * 1e9);
+  return p;
+}
+
+cfet_status finish(cfet_ctx* ctx, cudaStream_t s, cfet_stats* stats) {
+  CK(cudaStreamSynchronize(s), "stream synchronize");
+  ctx->ev_pending = false;
+  fill_stats(*ctx->h_st, stats);
+  const int code = ctx->h_st->status;
+  if (code == CFET_EKRYLOV) return fail(ctx, CFET_EKRYLOV, "stage exponential exceeded max_substeps");
+  if (code == CFET_ETIMEOUT) return fail(ctx, CFET_ETIMEOUT, "device grid barrier timed out");
+  if (code == CFET_ENAN) return fail(ctx, CFET_ENAN, "psi norm is not finite");
+  if (code != 0) return fail(ctx, (cfet_status)code, "device error");
+  return CFET_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+void cfet_options_default(cfet_options* opt) {
+  if (!opt) return;
+  opt->m_max = 16;
+  opt->m_min = 2;
+  opt->max_substeps = 64;
+  opt->block_size = 256;
+  opt->grid_size = 0;
+  opt->steps_per_launch = 256;
+  opt->barrier_timeout_s = 2.0;
+}
+
+cfet_status cfet_scheme_info(int32_t scheme, int32_t* order, int32_t* s, int32_t* M, double* f, double* x,
+                             double* w, double* g, int32_t capacity) {
+  SchemeData d;
+  if (!build_scheme(scheme, &d)) return CFET_EINVAL;
+  if (order) *order = d.order;
+  if (s) *s = d.s;
+  if (M) *M = d.M;
+  const int need = d.s * d.M;
+  if ((f || g) && capacity < need) return CFET_EINVAL;
+  if ((x || w) && capacity < d.M) return CFET_EINVAL;
+  for (int i = 0; i < d.s; ++i)
+    for (int m = 0; m < d.M; ++m) {
+      if (f) f[i * d.M + m] = d.f[i][m];
+      if (g) g[i * d.M + m] = d.g[i][m];
+    }
+  for (int m = 0; m < d.M; ++m) {
+    if (x) x[m] = d.x[m];
+    if (w) w[m] = d.w[m];
+  }
+  return CFET_OK;
+}
+
+const char* cfet_last_error(const cfet_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+
+int64_t cfet_dim(const cfet_ctx* ctx) { return ctx ? ctx->dim : 0; }
+int32_t cfet_num_drives(const cfet_ctx* ctx) { return ctx ? ctx->nV : 0; }
+
+cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfet_op* V, const cfet_drive_fn* f,
+                        void* const* f_user, const cfet_options* opt) {
+  cfet_ctx* ctx = nullptr;
+  g_create_err.clear();
+  if (!out) return fail(nullptr, CFET_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!H0) return fail(nullptr, CFET_EINVAL, "H0 is NULL");
+  if (nV < 0 || nV > kMaxDrives) return fail(nullptr, CFET_EINVAL, "nV must be in [0, 8]");
+  if (nV > 0 && (!V || !f)) return fail(nullptr, CFET_EINVAL, "V and f are required when nV > 0");
+  for (int k = 0; k < nV; ++k)
+    if (!f[k]) return fail(nullptr, CFET_EINVAL, "drive callback is NULL");
+  cfet_options o;
+  cfet_options_default(&o);
+  if (opt) o = *opt;
+  if (o.m_max < 1 || o.m_max > kMaxKrylov) return fail(nullptr, CFET_EINVAL, "m_max must be in [1, 64]");
+  if (o.m_min < 1 || o.m_min > o.m_max) return fail(nullptr, CFET_EINVAL, "m_min must be in [1, m_max]");
+  if (o.max_substeps < 1) return fail(nullptr, CFET_EINVAL, "max_substeps must be >= 1");
+  if (o.block_size == 0) o.block_size = 256;
+  if (o.block_size < 32 || o.block_size > 256 || o.block_size % 32)
+    return fail(nullptr, CFET_EINVAL, "block_size must be a multiple of 32 in [32, 256]");
+  if (o.grid_size < 0) return fail(nullptr, CFET_EINVAL, "grid_size must be >= 0");
+  if (o.steps_per_launch <= 0) o.steps_per_launch = 256;
+  if (!(o.barrier_timeout_s > 0.0) || !is_finite_d(o.barrier_timeout_s))
+    return fail(nullptr, CFET_EINVAL, "barrier_timeout_s must be positive");
+
+  int family = 0, dim = 0, nsites = 0;
+  if (H0->kind == CFET_OP_XXZ_CHAIN) {
+    family = kFamilySpin;
+    nsites = H0->nsites;
+    if (nsites < 1 || nsites > kMaxSites) return fail(nullptr, CFET_EINVAL, "nsites must be in [1, 30]");
+    if (H0->dim != (int64_t(1) << nsites)) return fail(nullptr, CFET_EINVAL, "XXZ chain: dim must be 2^nsites");
+    if (!H0->site_coeff) return fail(nullptr, CFET_EINVAL, "XXZ chain: site_coeff (h) is NULL");
+    if (!is_finite_d(H0->J) || !is_finite_d(H0->Delta)) return fail(nullptr, CFET_EINVAL, "XXZ chain: J, Delta not finite");
+    for (int i = 0; i < nsites; ++i)
+      if (!is_finite_d(H0->site_coeff[i])) return fail(nullptr, CFET_EINVAL, "XXZ chain: h not finite");
+    for (int k = 0; k < nV; ++k) {
+      if (V[k].kind != CFET_OP_X_FIELD || V[k].nsites != nsites || V[k].dim != H0->dim || !V[k].site_coeff)
+        return fail(nullptr, CFET_EINVAL, "drive operators of an XXZ chain must be X fields of the same chain");
+      for (int i = 0; i < nsites; ++i)
+        if (!is_finite_d(V[k].site_coeff[i])) return fail(nullptr, CFET_EINVAL, "X field coefficient not finite");
+    }
+    dim = (int)H0->dim;
+  } else if (H0->kind == CFET_OP_DIA) {
+    family = kFamilyDia;
+    if (H0->dim < 1 || H0->dim > 0x7fffffffLL) return fail(nullptr, CFET_EINVAL, "DIA: dim must be in [1, 2^31)");
+    dim = (int)H0->dim;
+    int total = 0;
+    for (int k = -1; k < nV; ++k) {
+      const cfet_op& o2 = k < 0 ? *H0 : V[k];
+      if (o2.kind != CFET_OP_DIA || o2.dim != H0->dim)
+        return fail(nullptr, CFET_EINVAL, "drive operators of a DIA operator must be DIA of the same dimension");
+      if (o2.ndiag < 1 || !o2.offsets || !o2.values) return fail(nullptr, CFET_EINVAL, "DIA: missing diagonals");
+      for (int d = 0; d < o2.ndiag; ++d)
+        if (o2.offsets[d] <= -(int64_t)dim || o2.offsets[d] >= (int64_t)dim)
+          return fail(nullptr, CFET_EINVAL, "DIA: offset out of range");
+      for (int64_t i = 0; i < (int64_t)o2.ndiag * dim; ++i)
+        if (!is_finite_d(o2.values[i])) return fail(nullptr, CFET_EINVAL, "DIA: value not finite");
+      total += o2.ndiag;
+    }
+    if (total > kMaxDiag) return fail(nullptr, CFET_EINVAL, "DIA: more than 32 diagonals in total");
+  } else {
+    return fail(nullptr, CFET_EINVAL, "H0 must be an XXZ chain or a DIA operator");
+  }
+  {
+    cfet_status s = device_available(nullptr);
+    if (s != CFET_OK) return s;
+  }
+
+  ctx = new cfet_ctx();
+  cudaGetDevice(&ctx->device);
+  ctx->family = family;
+  ctx->dim = dim;
+  ctx->nV = nV;
+  ctx->opt = o;
+  ctx->block = o.block_size;
+  for (int k = 0; k < nV; ++k) {
+    ctx->f.push_back(f[k]);
+    ctx->f_user.push_back(f_user ? f_user[k] : nullptr);
+  }
+#define CKC(call, where)                                         \
+  do {                                                           \
+    cudaError_t _e = (call);                                     \
+    if (_e != cudaSuccess) {                                     \
+      cfet_status _s = cuda_fail(nullptr, _e, where);            \
+      free_ctx(ctx);                                             \
+      return _s;                                                 \
+    }                                                            \
+  } while (0)
+
+  if (family == kFamilySpin) {
+    const int N = nsites;
+    const int L = N < 10 ? N : 10;
+    const size_t nlo = size_t(1) << L, nhi = size_t(1) << (N - L + 1);
+    double* d_h = nullptr;
+    CKC(cudaMalloc(&ctx->d_dz_lo, nlo * sizeof(double)), "cudaMalloc(dz_lo)");
+    CKC(cudaMalloc(&ctx->d_dz_hi, nhi * sizeof(double)), "cudaMalloc(dz_hi)");
+    CKC(cudaMalloc(&d_h, N * sizeof(double)), "cudaMalloc(h)");
+    CKC(cudaMemcpy(d_h, H0->site_coeff, N * sizeof(double), cudaMemcpyHostToDevice), "upload h");
+    int e = launch_spin_tables(N, L, H0->J, H0->Delta, d_h, ctx->d_dz_lo, ctx->d_dz_hi, nullptr);
+    cudaError_t es = cudaDeviceSynchronize();
+    cudaFree(d_h);
+    CKC((cudaError_t)e, "spin table kernel");
+    CKC(es, "spin table kernel");
+    std::vector<double> xf((size_t)(nV > 0 ? nV : 1) * N, 0.0);
+    for (int k = 0; k < nV; ++k)
+      for (int i = 0; i < N; ++i) xf[(size_t)k * N + i] = V[k].site_coeff[i];
+    CKC(cudaMalloc(&ctx->d_xf, xf.size() * sizeof(double)), "cudaMalloc(xf)");
+    CKC(cudaMemcpy(ctx->d_xf, xf.data(), xf.size() * sizeof(double), cudaMemcpyHostToDevice), "upload xf");
+    ctx->spin.N = N;
+    ctx->spin.lo_bits = L;
+    ctx->spin.J2 = 2.0 * H0->J;
+    ctx->spin.dz_lo = ctx->d_dz_lo;
+    ctx->spin.dz_hi = ctx->d_dz_hi;
+    ctx->spin.xf = ctx->d_xf;
+  } else {
+    std::vector<long long> off;
+    std::vector<int> opidx;
+    for (int k = -1; k < nV; ++k) {
+      const cfet_op& o2 = k < 0 ? *H0 : V[k];
+      for (int d = 0; d < o2.ndiag; ++d) {
+        off.push_back(o2.offsets[d]);
+        opidx.push_back(k + 1);
+      }
+    }
+    const int nd = (int)off.size();
+    CKC(cudaMalloc(&ctx->d_off, nd * sizeof(long long)), "cudaMalloc(offsets)");
+    CKC(cudaMalloc(&ctx->d_opidx, nd * sizeof(int)), "cudaMalloc(opidx)");
+    CKC(cudaMalloc(&ctx->d_val, (size_t)nd * dim * sizeof(double)), "cudaMalloc(values)");
+    CKC(cudaMemcpy(ctx->d_off, off.data(), nd * sizeof(long long), cudaMemcpyHostToDevice), "upload offsets");
+    CKC(cudaMemcpy(ctx->d_opidx, opidx.data(), nd * sizeof(int), cudaMemcpyHostToDevice), "upload opidx");
+    size_t row = 0;
+    for (int k = -1; k < nV; ++k) {
+      const cfet_op& o2 = k < 0 ? *H0 : V[k];
+      CKC(cudaMemcpy(ctx->d_val + row * dim, o2.values, (size_t)o2.ndiag * dim * sizeof(double),
+                     cudaMemcpyHostToDevice), "upload values");
+      row += o2.ndiag;
+    }
+    ctx->dia.ndiag = nd;
+    ctx->dia.off = ctx->d_off;
+    ctx->dia.opidx = ctx->d_opidx;
+    ctx->dia.val = ctx->d_val;
+  }
+  // persistent grid: co-resident maximum, no more CTAs than needed to give
+  // every thread at least one element
+  const int maxg = max_coresident_blocks(family, ctx->block);
+  if (maxg < 1) {
+    free_ctx(ctx);
+    return fail(nullptr, CFET_ECUDA, "occupancy query failed for the persistent kernel");
+  }
+  int want = (dim + ctx->block - 1) / ctx->block;
+  if (o.grid_size > 0) want = o.grid_size;
+  ctx->grid = want < maxg ? want : maxg;
+  if (ctx->grid < 1) ctx->grid = 1;
+
+  CKC(cudaMalloc(&ctx->d_basis, (size_t)o.m_max * dim * sizeof(double2)), "cudaMalloc(Krylov basis)");
+  CKC(cudaMalloc(&ctx->d_partials, 2 * (size_t)ctx->grid * sizeof(double)), "cudaMalloc(partials)");
+  CKC(cudaMalloc(&ctx->d_bar, 2 * sizeof(unsigned)), "cudaMalloc(barrier)");
+  CKC(cudaMemset(ctx->d_bar, 0, 2 * sizeof(unsigned)), "barrier init");
+  CKC(cudaMalloc(&ctx->d_st, sizeof(DevStatus)), "cudaMalloc(status)");
+  CKC(cudaMemset(ctx->d_st, 0, sizeof(DevStatus)), "status init");
+  CKC(cudaMallocHost(&ctx->h_st, sizeof(DevStatus)), "cudaMallocHost(status)");
+  std::memset(ctx->h_st, 0, sizeof(DevStatus));
+  CKC(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking), "capture stream");
+  CKC(cudaEventCreateWithFlags(&ctx->ev_done, cudaEventDisableTiming), "event");
+  CKC(cudaEventCreate(&ctx->ev_k0), "event");
+  CKC(cudaEventCreate(&ctx->ev_k1), "event");
+#undef CKC
+  *out = ctx;
+  return CFET_OK;
+}
+
+void cfet_destroy(cfet_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->ev_pending) cudaEventSynchronize(ctx->ev_done);
+  free_ctx(ctx);
+}
+
+cfet_status cfet_apply(cfet_ctx* ctx, const double* c, const void* v_in, void* v_out, void* stream) {
+  if (!ctx) return CFET_EINVAL;
+  if (!c) return fail(ctx, CFET_EINVAL, "coefficients are NULL");
+  for (int i = 0; i <= ctx->nV; ++i)
+    if (!is_finite_d(c[i])) return fail(ctx, CFET_EINVAL, "coefficient not finite");
+  cfet_status s = check_psi(ctx, v_in);
+  if (s != CFET_OK) return s;
+  if ((s = check_psi(ctx, v_out)) != CFET_OK) return s;
+  const char* a = (const char*)v_in;
+  const char* b = (const char*)v_out;
+  const size_t bytes = (size_t)ctx->dim * sizeof(double2);
+  if (a < b + bytes && b < a + bytes) return fail(ctx, CFET_EINVAL, "v_in and v_out overlap");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  int e = ctx->family == kFamilySpin
+              ? launch_apply_spin(ctx->spin, ctx->dim, c, ctx->nV, (const double2*)v_in, (double2*)v_out, stream)
+              : launch_apply_dia(ctx->dia, ctx->dim, c, ctx->nV, (const double2*)v_in, (double2*)v_out, stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, (cudaError_t)e, "apply kernel launch");
+  return CFET_OK;
+}
+
+cfet_status cfet_expv(cfet_ctx* ctx, const double* c, double tau, void* psi, double tol, void* stream,
+                      cfet_stats* stats) {
+  if (!ctx) return CFET_EINVAL;
+  if (!c) return fail(ctx, CFET_EINVAL, "coefficients are NULL");
+  for (int i = 0; i <= ctx->nV; ++i)
+    if (!is_finite_d(c[i])) return fail(ctx, CFET_EINVAL, "coefficient not finite");
+  if (!is_finite_d(tau) || tau == 0.0) return fail(ctx, CFET_EINVAL, "tau must be finite and non-zero");
+  if (!is_finite_d(tol)) return fail(ctx, CFET_EINVAL, "tol not finite");
+  cfet_status s = check_psi(ctx, psi);
+  if (s != CFET_OK) return s;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if ((s = ensure_scal(ctx, 1 + ctx->nV)) != CFET_OK) return s;
+  if (ctx->ev_pending) { cudaEventSynchronize(ctx->ev_done); ctx->ev_pending = false; }
+  for (int i = 0; i <= ctx->nV; ++i) ctx->h_scal[i] = c[i];
+  cudaStream_t st = (cudaStream_t)stream;
+  PropParams p = base_params(ctx, (double2*)psi, tau, tol);
+  if ((s = issue_sequence(ctx, p, 1, 1, (1 + ctx->nV) * sizeof(double), st, false)) != CFET_OK) return s;
+  CK(cudaEventRecord(ctx->ev_done, st), "event record");
+  ctx->ev_pending = true;
+  if (stats) return finish(ctx, st, stats);
+  return CFET_OK;
+}
+
+cfet_status cfet_propagate_ex(cfet_ctx* ctx, void* psi, double t0, double dt, int64_t nsteps, int32_t order,
+                              int32_t scheme, double krylov_tol, void* stream, const cfet_decisions* forced,
+                              cfet_decisions* record, cfet_stats* stats) {
+  if (!ctx) return CFET_EINVAL;
+  cfet_status s = check_psi(ctx, psi);
+  if (s != CFET_OK) return s;
+  if (!is_finite_d(t0) || !is_finite_d(dt) || dt == 0.0) return fail(ctx, CFET_EINVAL, "t0, dt must be finite, dt != 0");
+  if (!is_finite_d(krylov_tol)) return fail(ctx, CFET_EINVAL, "krylov_tol not finite");
+  if (nsteps < 0) return fail(ctx, CFET_EINVAL, "nsteps must be >= 0");
+  int id = scheme;
+  if (id == CFET_SCHEME_DEFAULT) {
+    id = default_scheme_for_order(order);
+    if (!id) return fail(ctx, CFET_EINVAL, "order must be 2, 4, 6 or 8");
+  }
+  SchemeData sd;
+  if (!build_scheme(id, &sd)) return fail(ctx, CFET_EINVAL, "unknown scheme id");
+  if (scheme != CFET_SCHEME_DEFAULT && order != 0 && order != sd.order)
+    return fail(ctx, CFET_EINVAL, "order does not match the scheme");
+  if (nsteps == 0) {
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    return CFET_OK;
+  }
+  const long long nexp = nsteps * (long long)sd.s;
+  const int ncoef = 1 + ctx->nV;
+  if (forced) {
+    if (forced->n_exp != nexp || !forced->n_sub || !forced->k || !forced->h || forced->len < nexp)
+      return fail(ctx, CFET_EINVAL, "forced decisions do not cover nsteps * s exponentials");
+    long long tot = 0;
+    for (long long e = 0; e < nexp; ++e) {
+      if (forced->n_sub[e] < 1) return fail(ctx, CFET_EINVAL, "forced decisions: n_sub < 1");
+      tot += forced->n_sub[e];
+    }
+    if (tot != forced->len || tot > forced->cap) return fail(ctx, CFET_EINVAL, "forced decisions: len mismatch");
+    for (long long i = 0; i < tot; ++i)
+      if (forced->k[i] < 1 || forced->k[i] > ctx->opt.m_max || forced->h[i] < 0 || forced->h[i] > 60)
+        return fail(ctx, CFET_EINVAL, "forced decisions: k or h out of range");
+  }
+  if (record && (record->n_exp != nexp || !record->n_sub || !record->k || !record->h || record->cap < 0))
+    return fail(ctx, CFET_EINVAL, "record must cover nsteps * s exponentials");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if ((s = ensure_scal(ctx, (size_t)nexp * ncoef)) != CFET_OK) return s;
+  // decision buffers: [f_nsub nexp | f_k len | f_h len | r_nsub nexp | r_k cap | r_h cap]
+  const size_t flen = forced ? (size_t)forced->len : 0;
+  const size_t rcap = record ? (size_t)record->cap : 0;
+  const size_t nf = forced ? (size_t)nexp + 2 * flen : 0;
+  const size_t nr = record ? (size_t)nexp + 2 * rcap : 0;
+  if (nf + nr > 0 && (s = ensure_dec(ctx, nf + nr)) != CFET_OK) return s;
+  // the previous call's graph may still read the pinned table
+  if (ctx->ev_pending) { cudaEventSynchronize(ctx->ev_done); ctx->ev_pending = false; }
+
+  // ---- stage scalars (host): drives at the Gauss-Legendre nodes of each step
+  std::vector<double> fval((size_t)sd.M * (ctx->nV > 0 ? ctx->nV : 1));
+  for (long long n = 0; n < nsteps; ++n) {
+    const double t = t0 + (double)n * dt;
+    for (int m = 0; m < sd.M; ++m)
+      for (int k = 0; k < ctx->nV; ++k) {
+        const double v = ctx->f[k](t + sd.x[m] * dt, ctx->f_user[k]);
+        if (!is_finite_d(v)) return fail(ctx, CFET_EINVAL, "drive returned a non-finite value");
+        fval[(size_t)m * ctx->nV + k] = v;
+      }
+    for (int jj = 0; jj < sd.s; ++jj) {
+      const int j = sd.s - 1 - jj;  // exp(Omega_s) acts first
+      double* row = ctx->h_scal + ((size_t)n * sd.s + jj) * ncoef;
+      double c0 = 0.0;
+      for (int m = 0; m < sd.M; ++m) c0 += sd.g[j][m];
+      row[0] = c0;
+      for (int k = 0; k < ctx->nV; ++k) {
+        double ck = 0.0;
+        for (int m = 0; m < sd.M; ++m) ck += sd.g[j][m] * fval[(size_t)m * ctx->nV + k];
+        row[1 + k] = ck;
+      }
+    }
+  }
+  // ---- forced decisions blob (host staging)
+  std::vector<int> fblob;
+  if (forced) {
+    fblob.resize(nf);
+    for (long long e = 0; e < nexp; ++e) fblob[e] = forced->n_sub[e];
+    for (size_t i = 0; i < flen; ++i) {
+      fblob[nexp + i] = forced->k[i];
+      fblob[nexp + flen + i] = forced->h[i];
+    }
+  }
+  if (forced) CK(cudaMemcpy(ctx->d_dec, fblob.data(), nf * sizeof(int), cudaMemcpyHostToDevice), "decision upload");
+  PropParams p = base_params(ctx, (double2*)psi, dt, krylov_tol);
+  if (forced) {
+    p.f_nsub = ctx->d_dec;
+    p.f_k = ctx->d_dec + nexp;
+    p.f_h = ctx->d_dec + nexp + flen;
+  }
+  if (record) {
+    int* r = ctx->d_dec + nf;
+    p.r_nsub = r;
+    p.r_k = r + nexp;
+    p.r_h = r + nexp + rcap;
+    p.r_cap = (long long)rcap;
+  }
+  const long long chunk = (long long)ctx->opt.steps_per_launch * sd.s;
+  cudaStream_t user = (cudaStream_t)stream;
+  // ---- capture the launch sequence and replay it on the caller's stream
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+  s = issue_sequence(ctx, p, nexp, chunk, (size_t)nexp * ncoef * sizeof(double), ctx->cap_stream, true);
+  cudaError_t ec = cudaStreamEndCapture(ctx->cap_stream, &graph);
+  if (s != CFET_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (ec != cudaSuccess) return cuda_fail(ctx, ec, "end capture");
+  bool updated = false;
+  if (ctx->gexec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(ctx->gexec, graph, &info) == cudaSuccess) updated = true;
+    else {
+      cudaGetLastError();
+      cudaGraphExecDestroy(ctx->gexec);
+      ctx->gexec = nullptr;
+    }
+  }
+  if (!updated) {
+    cudaError_t ei = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+    if (ei != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      ctx->gexec = nullptr;
+      return cuda_fail(ctx, ei, "graph instantiate");
+    }
+  }
+  cudaGraphDestroy(graph);
+  CK(cudaGraphLaunch(ctx->gexec, user), "graph launch");
+  ctx->timed = true;
+  CK(cudaEventRecord(ctx->ev_done, user), "event record");
+  ctx->ev_pending = true;
+  if (!stats && !record) return CFET_OK;
+  cfet_stats tmp;
+  s = finish(ctx, user, stats ? stats : &tmp);
+  if (record) {
+    // copy decisions back (device -> host), synchronous
+    const DevStatus& hs = *ctx->h_st;
+    const long long len = hs.rec_pos < (long long)rcap ? hs.rec_pos : (long long)rcap;
+    int* r = ctx->d_dec + nf;
+    CK(cudaMemcpy(record->n_sub, r, nexp * sizeof(int), cudaMemcpyDeviceToHost), "record n_sub");
+    if (len > 0) {
+      CK(cudaMemcpy(record->k, r + nexp, len * sizeof(int), cudaMemcpyDeviceToHost), "record k");
+      CK(cudaMemcpy(record->h, r + nexp + rcap, len * sizeof(int), cudaMemcpyDeviceToHost), "record h");
+    }
+    record->len = hs.rec_pos;
+    if (s == CFET_OK && hs.rec_overflow) return fail(ctx, CFET_EINVAL, "decision record capacity too small");
+  }
+  return s;
+}
+
+cfet_status cfet_propagate(cfet_ctx* ctx, void* psi, double t0, double dt, int64_t nsteps, int32_t order,
+                           double krylov_tol, void* stream, cfet_stats* stats) {
+  return cfet_propagate_ex(ctx, psi, t0, dt, nsteps, order, CFET_SCHEME_DEFAULT, krylov_tol, stream, nullptr,
+                           nullptr, stats);
+}
+
+cfet_status cfet_propagate_host(cfet_ctx* ctx, void* psi_host, double t0, double dt, int64_t nsteps, int32_t order,
+                                double krylov_tol, void* stream, cfet_stats* stats) {
+  if (!ctx) return CFET_EINVAL;
+  if (!psi_host) return fail(ctx, CFET_EINVAL, "psi_host is NULL");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const size_t bytes = (size_t)ctx->dim * sizeof(double2);
+  if (!ctx->d_psi_e2e) CK(cudaMalloc(&ctx->d_psi_e2e, bytes), "cudaMalloc(psi staging)");
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(ctx->d_psi_e2e, psi_host, bytes, cudaMemcpyHostToDevice, st), "psi upload");
+  cfet_stats tmp;
+  cfet_status s = cfet_propagate(ctx, ctx->d_psi_e2e, t0, dt, nsteps, order, krylov_tol, stream,
+                                 stats ? stats : &tmp);
+  if (s != CFET_OK) return s;
+  CK(cudaMemcpyAsync(psi_host, ctx->d_psi_e2e, bytes, cudaMemcpyDeviceToHost, st), "psi download");
+  CK(cudaStreamSynchronize(st), "stream synchronize");
+  return CFET_OK;
+}
+
+cfet_status cfet_kernel_time_ms(cfet_ctx* ctx, float* ms) {
+  if (!ctx || !ms) return CFET_EINVAL;
+  if (!ctx->timed) return fail(ctx, CFET_EINVAL, "no timed propagation yet");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  CK(cudaEventSynchronize(ctx->ev_k1), "event synchronize");
+  CK(cudaEventElapsedTime(ms, ctx->ev_k0, ctx->ev_k1), "event elapsed");
+  return CFET_OK;
+}
+
+cfet_status cfet_sync(cfet_ctx* ctx, void* stream, cfet_stats* stats) {
+  if (!ctx) return CFET_EINVAL;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  return finish(ctx, (cudaStream_t)stream, stats);
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// Internal declarations shared by the host C-ABI code and the device kernels.
+#pragma once
+
+#include <cstdint>
+
+#include <vector_types.h>
+
+#include "../../include/cfet.h"
+
+namespace cfet {
+
+constexpr int kMaxKrylov = 64;   // m_max limit (two tridiagonal rows per lane)
+constexpr int kMaxDrives = 8;    // drive operators V_k
+constexpr int kMaxSites = 30;    // spin chains: dim = 2^N < 2^31
+constexpr int kMaxDiag = 32;     // DIA: stored diagonals over H0 and all V_k
+constexpr int kSmallTaylorTerms = 18;
+
+// ---------------------------------------------------------------- schemes
+struct SchemeData {
+  int id, order, s, M;
+  double f[11][4];   // full table after rule (R1)
+  double x[4], w[4];  // Gauss-Legendre points / weights on [0,1]
+  double g[11][4];   // g_{i,m}
+};
+bool build_scheme(int id, SchemeData* out);
+int default_scheme_for_order(int order);
+
+// ---------------------------------------------------------------- device state
+struct DevStatus {
+  int status;          // cfet_status
+  int max_k;
+  int rec_overflow;
+  int pad;
+  long long n_exp, n_sub, n_app;
+  double max_err;
+  long long rec_pos;   // next record slot
+  long long forced_pos;  // next forced slot
+};
+
+// Spin chain operator family: H0 = XXZ chain, V_k = transverse fields.
+struct OpSpin {
+  int N;               // sites
+  int lo_bits;         // L: diagonal table split
+  double J2;           // 2 J  (matrix element of X X + Y Y between |01>, |10>)
+  const double* dz_lo; // [2^L]        sum over bits [0, L)
+  const double* dz_hi; // [2^(N-L+1)]  sum over bits [L-1, N)
+  const double* xf;    // [nV * N] per-field per-site X coefficients
+};
+
+// Banded family: all operators in DIA form, concatenated.
+struct OpDia {
+  int ndiag;
+  const long long* off;  // [ndiag]
+  const int* opidx;      // [ndiag]: 0 = H0, 1 + k = V_k
+  const double* val;     // [ndiag * dim]
+};
+
+struct PropParams {
+  int dim;
+  int nV;
+  double2* psi;
+  double2* basis;        // m_max * dim; q_{i} lives at basis + (i-2)*dim, i >= 2
+  const double* scal;    // [nexp * (1 + nV)]
+  long long nexp;
+  long long exp_base;    // global index of exponential 0 of this launch
+  double tau, tol;
+  int m_min, m_max, max_substeps;
+  int pad0;
+  // decisions (device arrays, nullable)
+  const int* f_nsub; const int* f_k; const int* f_h;
+  int* r_nsub; int* r_k; int* r_h; long long r_cap;
+  // reductions and synchronisation
+  double* partials;      // [2 * gridDim.x]
+  unsigned* bar;         // [2]: arrival count, generation
+  DevStatus* st;
+  long long timeout_ns;
+};
+
+// ---------------------------------------------------------------- launchers
+// (defined in kernels.cu; return a cudaError_t as int)
+int launch_propagate_spin(const PropParams& p, const OpSpin& op, int grid, int block, void* stream);
+int launch_propagate_dia(const PropParams& p, const OpDia& op, int grid, int block, void* stream);
+int launch_apply_spin(const OpSpin& op, int dim, const double* c, int nV, const double2* vin, double2* vout,
+                      void* stream);
+int launch_apply_dia(const OpDia& op, int dim, const double* c, int nV, const double2* vin, double2* vout,
+                     void* stream);
+int launch_spin_tables(int N, int L, double J, double Delta, const double* h, double* dz_lo, double* dz_hi,
+                       void* stream);
+int max_coresident_blocks(int family, int block);  // per device, for the persistent kernel
+size_t propagate_smem_bytes(int block);
+
+enum Family { kFamilySpin = 1, kFamilyDia = 2 };
+
+}  // namespace cfet

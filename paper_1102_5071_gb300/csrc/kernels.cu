@@ -1,0 +1,684 @@
+// Device kernels of the CFET/Krylov propagator (FP64, sm_103a).
+//
+// Alvermann & Fehske, arXiv:1102.5071.  The hot path is the stage
+// exponential exp(-i tau H_j) psi of a CFET step (Sec. 4, Eq. (Ucf); Sec. 7,
+// Eq. (OmGLeg)), evaluated by the Lanczos/Krylov method of Sec. 8.1.  The
+// stage operator H_j = c_0 H0 + sum_k c_k V_k is never formed: the apply
+// functions take the per-stage scalars (Sec. 8, weighted sums keep the
+// sparsity pattern).
+//
+// Structure: one persistent cooperative kernel per launch runs a sequence of
+// stage exponentials.  Every CTA walks a grid-stride slice of the vectors;
+// the two scalar reductions of a Lanczos iteration (alpha, beta) go through a
+// per-CTA warp-shuffle/shared-memory tree, one partial per CTA in global
+// memory, and a bounded grid barrier; every CTA then sums the partials in the
+// same fixed order, so all CTAs hold bit-identical alpha/beta and take the
+// same adaptive decisions without a broadcast.  Warp 0 of each CTA evaluates
+// the small exponential exp(-i tau T_k) e_1 of the tridiagonal Lanczos matrix.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "cfet_internal.h"
+
+namespace cfet {
+
+struct Coefs {
+  double c[1 + kMaxDrives];
+};
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ long long global_timer_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_volatile_u32(const unsigned* p) {
+  return *reinterpret_cast<const volatile unsigned*>(p);
+}
+__device__ __forceinline__ int ld_volatile_i32(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
+
+// Bounded grid-wide barrier (arrival counter + generation).  Returns false in
+// every thread of the CTA when the wait limit expired or another CTA reported
+// an error; the first CTA to time out records CFET_ETIMEOUT.
+__device__ bool grid_barrier(unsigned* bar, unsigned& gen, int* status, long long timeout_ns, int* s_ok) {
+  __syncthreads();
+  if (gridDim.x == 1) {
+    gen += 1;
+    return true;
+  }
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned target = gen + 1;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&bar[0], 1u) + 1u;
+    if (arrived == gridDim.x) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicExch(&bar[1], target);
+    } else {
+      const long long t0 = global_timer_ns();
+      unsigned spins = 0;
+      while (ld_volatile_u32(&bar[1]) != target) {
+        if ((++spins & 63u) == 0u) {
+          if (ld_volatile_i32(status) != 0) { ok = 0; break; }
+          if (global_timer_ns() - t0 > timeout_ns) {
+            atomicCAS(status, 0, (int)CFET_ETIMEOUT);
+            ok = 0;
+            break;
+          }
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    *s_ok = ok;
+  }
+  gen += 1;
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+// Sum over the CTA of one double per thread; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    for (int i = 0; i < nw; ++i) s += red[i];
+  }
+  return s;
+}
+
+// Deterministic sum of the per-CTA partials (same order in every CTA);
+// executed by warp 0, result returned to all lanes of warp 0.
+__device__ __forceinline__ double sum_partials(const double* part) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < (int)gridDim.x; i += 32) s += part[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// ------------------------------------------------------------------ apply
+// Spin family:  (c0 H0 + sum_k c_k V_k) v at index x, everything pre-scaled.
+//   diag   cz * dz(x) v[x],             dz(x) = J Delta sum s_i s_{i+1} + sum h_i s_i
+//   hop    cxx * sum_{antiparallel bonds i} v[x ^ (3 << i)]     (cxx = 2 J c0)
+//   field  sum_i b_i v[x ^ (1 << i)]                             (b_i = sum_k c_k a_{k,i})
+struct SpinScaled {
+  double cz, cxx;
+};
+
+__device__ __forceinline__ double2 apply_spin_at(const double2* q, int x, const OpSpin& op, const SpinScaled& sc,
+                                                 const double* bsite) {
+  const int N = op.N, L = op.lo_bits;
+  const double dz = __ldg(op.dz_lo + (x & ((1 << L) - 1))) + __ldg(op.dz_hi + (x >> (L - 1)));
+  const double2 v = q[x];
+  const double cd = sc.cz * dz;
+  double2 acc = make_double2(cd * v.x, cd * v.y);
+  double hx = 0.0, hy = 0.0;
+  unsigned anti = ((unsigned)x ^ ((unsigned)x >> 1)) & ((1u << (N - 1)) - 1u);
+  while (anti) {
+    const int i = __ffs(anti) - 1;
+    anti &= anti - 1u;
+    const double2 w = q[x ^ (3 << i)];
+    hx += w.x;
+    hy += w.y;
+  }
+  acc.x = fma(sc.cxx, hx, acc.x);
+  acc.y = fma(sc.cxx, hy, acc.y);
+  for (int i = 0; i < N; ++i) {
+    const double2 w = q[x ^ (1 << i)];
+    acc.x = fma(bsite[i], w.x, acc.x);
+    acc.y = fma(bsite[i], w.y, acc.y);
+  }
+  return acc;
+}
+
+// DIA family: sum_d coef[opidx[d]] * val[d][r] * v[r + off[d]], coef pre-scaled.
+__device__ __forceinline__ double2 apply_dia_at(const double2* q, int r, int dim, const OpDia& op,
+                                                const double* copf) {
+  double2 acc = make_double2(0.0, 0.0);
+  for (int d = 0; d < op.ndiag; ++d) {
+    const long long c = (long long)r + __ldg(op.off + d);
+    if (c >= 0 && c < dim) {
+      const double a = copf[__ldg(op.opidx + d)] * __ldg(op.val + (size_t)d * dim + r);
+      const double2 w = q[c];
+      acc.x = fma(a, w.x, acc.x);
+      acc.y = fma(a, w.y, acc.y);
+    }
+  }
+  return acc;
+}
+
+// ------------------------------------------------------------------ small problem
+// y = exp(-i ts T) e_1 for the k x k real symmetric tridiagonal T (diagonal
+// a[0..k-1], off-diagonal b[0..k-2]); executed by one warp, rows r = lane and
+// lane + 32.  Method: spectral shift by the Gershgorin centre sigma, S equal
+// substeps with |ts| rho / S <= 1 (rho the Gershgorin radius), each a Taylor
+// series of kSmallTaylorTerms terms; exp(-i ts T) = e^{-i ts sigma}
+// exp(-i ts (T - sigma)).
+__device__ void small_expm_e1(int k, const double* a, const double* b, double ts, double* yr, double* yi,
+                              double* tr, double* ti) {
+  const int lane = threadIdx.x & 31;
+  double lo = 1e300, hi = -1e300;
+  for (int r = lane; r < k; r += 32) {
+    const double rad = (r > 0 ? fabs(b[r - 1]) : 0.0) + (r < k - 1 ? fabs(b[r]) : 0.0);
+    lo = fmin(lo, a[r] - rad);
+    hi = fmax(hi, a[r] + rad);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  const double sig = 0.5 * (lo + hi), rho = 0.5 * (hi - lo);
+  // number of Taylor substeps, bounded: a non-finite spread gives S = 1 (the
+  // result is then non-finite and rejected by the caller), a huge one 65536
+  const double sr = fabs(ts) * rho;
+  int S = 1;
+  if (sr == sr) S = sr < 65536.0 ? (int)ceil(sr) : 65536;
+  if (S < 1) S = 1;
+  const double hstep = ts / S;
+  // rows owned by this lane
+  const int r0 = lane, r1 = lane + 32;
+  double ar0 = 0, ai0 = 0, ar1 = 0, ai1 = 0;  // accumulators (current y)
+  if (r0 < k) { ar0 = (r0 == 0) ? 1.0 : 0.0; ai0 = 0.0; }
+  if (r1 < k) { ar1 = 0.0; ai1 = 0.0; }
+  for (int sidx = 0; sidx < S; ++sidx) {
+    double t_r0 = ar0, t_i0 = ai0, t_r1 = ar1, t_i1 = ai1;
+    if (r0 < k) { tr[r0] = t_r0; ti[r0] = t_i0; }
+    if (r1 < k) { tr[r1] = t_r1; ti[r1] = t_i1; }
+    __syncwarp();
+    for (int n = 1; n <= kSmallTaylorTerms; ++n) {
+      const double c = hstep / n;
+      double zr0 = 0, zi0 = 0, zr1 = 0, zi1 = 0;
+      if (r0 < k) {
+        zr0 = (a[r0] - sig) * t_r0;
+        zi0 = (a[r0] - sig) * t_i0;
+        if (r0 > 0) { zr0 = fma(b[r0 - 1], tr[r0 - 1], zr0); zi0 = fma(b[r0 - 1], ti[r0 - 1], zi0); }
+        if (r0 < k - 1) { zr0 = fma(b[r0], tr[r0 + 1], zr0); zi0 = fma(b[r0], ti[r0 + 1], zi0); }
+      }
+      if (r1 < k) {
+        zr1 = (a[r1] - sig) * t_r1;
+        zi1 = (a[r1] - sig) * t_i1;
+        zr1 = fma(b[r1 - 1], tr[r1 - 1], zr1);
+        zi1 = fma(b[r1 - 1], ti[r1 - 1], zi1);
+        if (r1 < k - 1) { zr1 = fma(b[r1], tr[r1 + 1], zr1); zi1 = fma(b[r1], ti[r1 + 1], zi1); }
+      }
+      __syncwarp();
+      // t <- (-i c) z
+      t_r0 = c * zi0; t_i0 = -c * zr0;
+      t_r1 = c * zi1; t_i1 = -c * zr1;
+      ar0 += t_r0; ai0 += t_i0; ar1 += t_r1; ai1 += t_i1;
+      if (r0 < k) { tr[r0] = t_r0; ti[r0] = t_i0; }
+      if (r1 < k) { tr[r1] = t_r1; ti[r1] = t_i1; }
+      __syncwarp();
+    }
+  }
+  double sn, cs;
+  sincos(ts * sig, &sn, &cs);
+  // multiply by e^{-i ts sig} = cs - i sn
+  if (r0 < k) { yr[r0] = ar0 * cs + ai0 * sn; yi[r0] = ai0 * cs - ar0 * sn; }
+  if (r1 < k) { yr[r1] = ar1 * cs + ai1 * sn; yi[r1] = ai1 * cs - ar1 * sn; }
+  __syncwarp();
+}
+
+// Gershgorin width of T (max of a_r + radius minus min of a_r - radius), an
+// upper bound of its eigenvalue spread; warp-uniform result.
+__device__ double gersh_width(int k, const double* a, const double* b) {
+  const int lane = threadIdx.x & 31;
+  double lo = 1e300, hi = -1e300;
+  for (int r = lane; r < k; r += 32) {
+    const double rad = (r > 0 ? fabs(b[r - 1]) : 0.0) + (r < k - 1 ? fabs(b[r]) : 0.0);
+    lo = fmin(lo, a[r] - rad);
+    hi = fmax(hi, a[r] + rad);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  return hi - lo;
+}
+
+// ------------------------------------------------------------------ shared layout
+struct SmemLayout {
+  double red[32];
+  double alpha[kMaxKrylov + 1];
+  double beta[kMaxKrylov + 1];   // beta[i] = ||w_i|| (1-based i)
+  double scale[kMaxKrylov + 2];  // scale[i] = 1 / ||q_i||  (q_1 = psi)
+  double yr[kMaxKrylov], yi[kMaxKrylov];
+  double tr[kMaxKrylov], ti[kMaxKrylov];
+  double cre[kMaxKrylov], cim[kMaxKrylov];
+  double bsite[kMaxSites];      // spin: scaled per-site X coefficients
+  double bsite_raw[kMaxSites];  // spin: sum_k c_k a_{k,i} for the current exponential
+  double copf[1 + kMaxDrives];  // dia: scaled per-operator coefficients
+  double scal[1 + kMaxDrives];  // current stage scalars
+  double bcast[4];
+  int dec[4];                   // decision broadcast: accepted, k, h, pad
+  int ok;
+};
+
+// ------------------------------------------------------------------ the persistent kernel
+template <int FAMILY, class Op>
+__global__ void __launch_bounds__(256) k_propagate(PropParams p, Op op) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmemLayout& S = *reinterpret_cast<SmemLayout*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int dim = p.dim;
+  const int stride = gridDim.x * blockDim.x;
+  const int x0 = blockIdx.x * blockDim.x + tid;
+  const int G = gridDim.x;
+  const int ncoef = 1 + p.nV;
+  unsigned gen = 0;
+  double* part0 = p.partials;
+  double* part1 = p.partials + G;
+  DevStatus* st = p.st;
+  const bool lead = (blockIdx.x == 0 && tid == 0);
+  const bool fixed_k = p.tol <= 0.0;
+  const bool forced = p.f_nsub != nullptr;
+
+  long long fpos = st->forced_pos;
+  long long rpos = st->rec_pos;
+  long long n_app = 0, n_sub = 0;
+  int max_k = 0;
+  double max_err = 0.0;
+
+  auto vec = [&](int i) -> double2* { return i == 1 ? p.psi : p.basis + (size_t)(i - 2) * dim; };
+
+  // initial norm of psi
+  {
+    double acc = 0.0;
+    for (int x = x0; x < dim; x += stride) {
+      const double2 v = p.psi[x];
+      acc = fma(v.x, v.x, fma(v.y, v.y, acc));
+    }
+    const double s = block_sum(acc, S.red);
+    if (tid == 0) part0[blockIdx.x] = s;
+    if (!grid_barrier(p.bar, gen, &st->status, p.timeout_ns, &S.ok)) return;
+    if (tid < 32) {
+      const double t = sum_partials(part0);
+      if (tid == 0) S.bcast[0] = sqrt(t);
+    }
+    __syncthreads();
+  }
+  double beta0 = S.bcast[0];
+
+  for (long long e = 0; e < p.nexp; ++e) {
+    // stage scalars of this exponential
+    if (tid < ncoef) S.scal[tid] = p.scal[e * ncoef + tid];
+    __syncthreads();
+    if constexpr (FAMILY == kFamilySpin) {
+      if (tid < op.N) {
+        double bi = 0.0;
+        for (int k = 0; k < p.nV; ++k) bi = fma(S.scal[1 + k], __ldg(op.xf + k * op.N + tid), bi);
+        S.bsite_raw[tid] = bi;
+      }
+      __syncthreads();
+    }
+    const long long eg = p.exp_base + e;
+    const int nforced = forced ? p.f_nsub[eg] : 0;
+    double remaining = p.tau;
+    int nsub_e = 0;
+    while (true) {
+      if (!(beta0 < 1e300) || beta0 != beta0) {
+        if (lead) atomicCAS(&st->status, 0, (int)CFET_ENAN);
+        return;
+      }
+      if (nsub_e >= p.max_substeps || (forced && nsub_e >= nforced)) {
+        if (lead) atomicCAS(&st->status, 0, (int)CFET_EKRYLOV);
+        return;
+      }
+      int kf = -1, hf = 0;
+      if (forced) {
+        kf = p.f_k[fpos];
+        hf = p.f_h[fpos];
+      }
+      int acc_k = 0, acc_h = 0;
+      double acc_err = 0.0;
+      if (beta0 == 0.0) {
+        // zero vector: exp(-i tau H) 0 = 0
+        acc_k = 0;
+      } else {
+        if (tid == 0) S.scale[1] = 1.0 / beta0;
+        __syncthreads();
+        const int klimit = forced ? kf : p.m_max;
+        bool accepted = false;
+        int it = 1;
+        for (;; ++it) {
+          // ---------------- phase A: u = s_it H q_it - beta_{it-1} s_{it-1} q_{it-1}
+          const double s_it = S.scale[it];
+          const double2* q = vec(it);
+          const double2* qm = it > 1 ? vec(it - 1) : nullptr;
+          double2* u = vec(it + 1);
+          const double bm = it > 1 ? S.beta[it - 1] * S.scale[it - 1] : 0.0;
+          if constexpr (FAMILY == kFamilySpin) {
+            if (tid < op.N) S.bsite[tid] = S.bsite_raw[tid] * s_it;
+          } else {
+            if (tid < ncoef) S.copf[tid] = S.scal[tid] * s_it;
+          }
+          __syncthreads();
+          double acc = 0.0;
+          if constexpr (FAMILY == kFamilySpin) {
+            SpinScaled sc;
+            sc.cz = S.scal[0] * s_it;
+            sc.cxx = S.scal[0] * s_it * op.J2;
+            for (int x = x0; x < dim; x += stride) {
+              double2 hv = apply_spin_at(q, x, op, sc, S.bsite);
+              if (qm) {
+                const double2 w = qm[x];
+                hv.x = fma(-bm, w.x, hv.x);
+                hv.y = fma(-bm, w.y, hv.y);
+              }
+              u[x] = hv;
+              const double2 v = q[x];
+              acc = fma(v.x, hv.x, fma(v.y, hv.y, acc));
+            }
+          } else {
+            for (int x = x0; x < dim; x += stride) {
+              double2 hv = apply_dia_at(q, x, dim, op, S.copf);
+              if (qm) {
+                const double2 w = qm[x];
+                hv.x = fma(-bm, w.x, hv.x);
+                hv.y = fma(-bm, w.y, hv.y);
+              }
+              u[x] = hv;
+              const double2 v = q[x];
+              acc = fma(v.x, hv.x, fma(v.y, hv.y, acc));
+            }
+          }
+          {
+            const double s = block_sum(acc, S.red);
+            if (tid == 0) part0[blockIdx.x] = s;
+          }
+          if (!grid_barrier(p.bar, gen, &st->status, p.timeout_ns, &S.ok)) return;
+          if (tid < 32) {
+            const double t = sum_partials(part0);
+            if (tid == 0) S.alpha[it] = t * s_it;
+          }
+          __syncthreads();
+          // ---------------- phase B: w = u - alpha s_it q_it, beta = ||w||
+          const double am = S.alpha[it] * s_it;
+          acc = 0.0;
+          for (int x = x0; x < dim; x += stride) {
+            const double2 v = q[x];
+            double2 w = u[x];
+            w.x = fma(-am, v.x, w.x);
+            w.y = fma(-am, v.y, w.y);
+            u[x] = w;
+            acc = fma(w.x, w.x, fma(w.y, w.y, acc));
+          }
+          {
+            const double s = block_sum(acc, S.red);
+            if (tid == 0) part1[blockIdx.x] = s;
+          }
+          if (!grid_barrier(p.bar, gen, &st->status, p.timeout_ns, &S.ok)) return;
+          // ---------------- decision (warp 0)
+          if (tid < 32) {
+            const double t = sum_partials(part1);
+            const double b = sqrt(t);
+            const double prev_b = it > 1 ? S.beta[it - 1] : 0.0;
+            const bool breakdown = b <= 1e-13 * (fabs(S.alpha[it]) + prev_b + 1.0);
+            int acc_flag = 0;
+            double err = 0.0;
+            if (forced) {
+              acc_flag = (it == kf);
+            } else if (fixed_k) {
+              acc_flag = (it == p.m_max) || breakdown;
+            } else if (breakdown) {
+              acc_flag = 1;
+            } else if (it >= p.m_min &&
+                       fabs(remaining) * gersh_width(it, S.alpha + 1, S.beta + 1) <= 2.0 * it) {
+              // T_it: diagonal alpha[1..it], off-diagonal beta[1..it-1]; the
+              // estimate is evaluated only where Eq. (KryErr) applies
+              small_expm_e1(it, S.alpha + 1, S.beta + 1, remaining, S.yr, S.yi, S.tr, S.ti);
+              const double yk = hypot(S.yr[it - 1], S.yi[it - 1]);
+              err = beta0 * b * yk;
+              acc_flag = err <= p.tol * remaining / p.tau;
+            }
+            if (tid == 0) {
+              S.beta[it] = b;
+              S.scale[it + 1] = 1.0 / b;
+              S.dec[0] = acc_flag;
+              S.bcast[1] = err;
+            }
+          }
+          __syncthreads();
+          if (S.dec[0]) {
+            accepted = true;
+            acc_err = S.bcast[1];
+            break;
+          }
+          if (it >= klimit) break;
+        }
+        acc_k = it;
+        acc_h = 0;
+        if (forced) {
+          acc_h = hf;
+        } else if (!accepted) {
+          // halve the substep on the same basis (T_{m_max}) until the estimate
+          // meets the proportional tolerance
+          if (tid < 32) {
+            int hh = 0;
+            double err = 0.0;
+            const double width = gersh_width(it, S.alpha + 1, S.beta + 1);
+            for (int h = 1; h <= 40; ++h) {
+              const double ts = ldexp(remaining, -h);
+              if (!(fabs(ts) * width <= 2.0 * it)) continue;
+              small_expm_e1(it, S.alpha + 1, S.beta + 1, ts, S.yr, S.yi, S.tr, S.ti);
+              err = beta0 * S.beta[it] * hypot(S.yr[it - 1], S.yi[it - 1]);
+              if (err <= p.tol * ts / p.tau) { hh = h; break; }
+            }
+            if (tid == 0) { S.dec[2] = hh; S.bcast[1] = err; }
+          }
+          __syncthreads();
+          acc_h = S.dec[2];
+          acc_err = S.bcast[1];
+          if (acc_h == 0) {
+            if (lead) atomicCAS(&st->status, 0, (int)CFET_EKRYLOV);
+            return;
+          }
+        }
+        n_app += it;
+      }
+      const double ts = ldexp(remaining, -acc_h);
+      if (acc_k > 0) {
+        // ---------------- reconstruct psi <- beta0 sum_i y_i q_i / ||q_i||
+        if (tid < 32) {
+          small_expm_e1(acc_k, S.alpha + 1, S.beta + 1, ts, S.yr, S.yi, S.tr, S.ti);
+          for (int i = tid; i < acc_k; i += 32) {
+            const double f = beta0 * S.scale[i + 1];
+            S.cre[i] = f * S.yr[i];
+            S.cim[i] = f * S.yi[i];
+          }
+        }
+        __syncthreads();
+        double acc = 0.0;
+        for (int x = x0; x < dim; x += stride) {
+          double re = 0.0, im = 0.0;
+          for (int i = 0; i < acc_k; ++i) {
+            const double2 v = vec(i + 1)[x];
+            const double cr = S.cre[i], ci = S.cim[i];
+            re = fma(cr, v.x, re);
+            re = fma(-ci, v.y, re);
+            im = fma(cr, v.y, im);
+            im = fma(ci, v.x, im);
+          }
+          p.psi[x] = make_double2(re, im);
+          acc = fma(re, re, fma(im, im, acc));
+        }
+        {
+          const double s = block_sum(acc, S.red);
+          if (tid == 0) part0[blockIdx.x] = s;
+        }
+        if (!grid_barrier(p.bar, gen, &st->status, p.timeout_ns, &S.ok)) return;
+        if (tid < 32) {
+          const double t = sum_partials(part0);
+          if (tid == 0) S.bcast[0] = sqrt(t);
+        }
+        __syncthreads();
+        beta0 = S.bcast[0];
+      }
+      // ---------------- bookkeeping (identical in every CTA; CTA 0 writes)
+      if (lead) {
+        if (p.r_k != nullptr) {
+          if (rpos < p.r_cap) {
+            p.r_k[rpos] = acc_k;
+            p.r_h[rpos] = acc_h;
+          } else {
+            st->rec_overflow = 1;
+          }
+        }
+      }
+      rpos += 1;
+      if (forced) fpos += 1;
+      n_sub += 1;
+      nsub_e += 1;
+      if (acc_k > max_k) max_k = acc_k;
+      if (acc_err > max_err) max_err = acc_err;
+      if (acc_h == 0) break;
+      remaining -= ts;
+    }
+    if (lead && p.r_nsub != nullptr) p.r_nsub[eg] = nsub_e;
+  }
+  if (lead) {
+    st->forced_pos = fpos;
+    st->rec_pos = rpos;
+    st->n_exp += p.nexp;
+    st->n_sub += n_sub;
+    st->n_app += n_app;
+    if (max_k > st->max_k) st->max_k = max_k;
+    if (max_err > st->max_err) st->max_err = max_err;
+  }
+}
+
+// ------------------------------------------------------------------ standalone apply
+template <int FAMILY, class Op>
+__global__ void k_apply(Op op, int dim, Coefs c, int nV, const double2* __restrict__ vin, double2* __restrict__ vout) {
+  __shared__ double bsite[kMaxSites];
+  __shared__ double copf[1 + kMaxDrives];
+  if constexpr (FAMILY == kFamilySpin) {
+    if (threadIdx.x < (unsigned)op.N) {
+      double bi = 0.0;
+      for (int k = 0; k < nV; ++k) bi = fma(c.c[1 + k], op.xf[k * op.N + threadIdx.x], bi);
+      bsite[threadIdx.x] = bi;
+    }
+  } else {
+    if (threadIdx.x < (unsigned)(1 + nV)) copf[threadIdx.x] = c.c[threadIdx.x];
+  }
+  __syncthreads();
+  const int stride = gridDim.x * blockDim.x;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < dim; x += stride) {
+    if constexpr (FAMILY == kFamilySpin) {
+      SpinScaled sc;
+      sc.cz = c.c[0];
+      sc.cxx = c.c[0] * op.J2;
+      vout[x] = apply_spin_at(vin, x, op, sc, bsite);
+    } else {
+      vout[x] = apply_dia_at(vin, x, dim, op, copf);
+    }
+  }
+}
+
+// Diagonal tables of the XXZ chain: dz(x) = dz_lo[x & (2^L-1)] + dz_hi[x >> (L-1)]
+//   dz_lo: J Delta sum_{i < L-1} s_i s_{i+1} + sum_{i < L} h_i s_i
+//   dz_hi: J Delta sum_{L-1 <= i < N-1} s_i s_{i+1} + sum_{L <= i < N} h_i s_i
+// (the index of dz_hi holds bits L-1 .. N-1 of x).
+__global__ void k_spin_tables(int N, int L, double J, double Delta, const double* h, double* dz_lo, double* dz_hi) {
+  const int nlo = 1 << L, nhi = 1 << (N - L + 1);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nlo) {
+    const int y = t;
+    double v = 0.0;
+    for (int i = 0; i + 1 < L; ++i) {
+      const double si = 1.0 - 2.0 * ((y >> i) & 1), sj = 1.0 - 2.0 * ((y >> (i + 1)) & 1);
+      v += J * Delta * si * sj;
+    }
+    for (int i = 0; i < L; ++i) v += h[i] * (1.0 - 2.0 * ((y >> i) & 1));
+    dz_lo[t] = v;
+  } else if (t < nlo + nhi) {
+    const int y = t - nlo;  // bit j of y is bit (L-1+j) of x
+    double v = 0.0;
+    for (int i = L - 1; i + 1 < N; ++i) {
+      const int j = i - (L - 1);
+      const double si = 1.0 - 2.0 * ((y >> j) & 1), sj = 1.0 - 2.0 * ((y >> (j + 1)) & 1);
+      v += J * Delta * si * sj;
+    }
+    for (int i = L; i < N; ++i) v += h[i] * (1.0 - 2.0 * ((y >> (i - (L - 1))) & 1));
+    dz_hi[t - nlo] = v;
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+size_t propagate_smem_bytes(int /*block*/) { return sizeof(SmemLayout); }
+
+template <int FAMILY, class Op>
+static int launch_prop(const PropParams& p, const Op& op, int grid, int block, void* stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = sizeof(SmemLayout);
+  cfg.stream = (cudaStream_t)stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return (int)cudaLaunchKernelEx(&cfg, k_propagate<FAMILY, Op>, p, op);
+}
+
+int launch_propagate_spin(const PropParams& p, const OpSpin& op, int grid, int block, void* stream) {
+  return launch_prop<kFamilySpin>(p, op, grid, block, stream);
+}
+int launch_propagate_dia(const PropParams& p, const OpDia& op, int grid, int block, void* stream) {
+  return launch_prop<kFamilyDia>(p, op, grid, block, stream);
+}
+
+int max_coresident_blocks(int family, int block) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e;
+  if (family == kFamilySpin)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate<kFamilySpin, OpSpin>, block, sizeof(SmemLayout));
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate<kFamilyDia, OpDia>, block, sizeof(SmemLayout));
+  if (e != cudaSuccess) return -1;
+  return per * nsm;
+}
+
+static int apply_grid(int dim, int block) {
+  int g = (dim + block - 1) / block;
+  return g < 1 ? 1 : (g > 65535 ? 65535 : g);
+}
+
+int launch_apply_spin(const OpSpin& op, int dim, const double* c, int nV, const double2* vin, double2* vout,
+                      void* stream) {
+  Coefs cc = {};
+  for (int i = 0; i < 1 + nV; ++i) cc.c[i] = c[i];
+  k_apply<kFamilySpin, OpSpin><<<apply_grid(dim, 256), 256, 0, (cudaStream_t)stream>>>(op, dim, cc, nV, vin, vout);
+  return (int)cudaGetLastError();
+}
+int launch_apply_dia(const OpDia& op, int dim, const double* c, int nV, const double2* vin, double2* vout,
+                     void* stream) {
+  Coefs cc = {};
+  for (int i = 0; i < 1 + nV; ++i) cc.c[i] = c[i];
+  k_apply<kFamilyDia, OpDia><<<apply_grid(dim, 256), 256, 0, (cudaStream_t)stream>>>(op, dim, cc, nV, vin, vout);
+  return (int)cudaGetLastError();
+}
+int launch_spin_tables(int N, int L, double J, double Delta, const double* h, double* dz_lo, double* dz_hi,
+                       void* stream) {
+  const int n = (1 << L) + (1 << (N - L + 1));
+  k_spin_tables<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(N, L, J, Delta, h, dz_lo, dz_hi);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace cfet

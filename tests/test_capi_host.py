@@ -1,0 +1,118 @@
+"""Host-side checks of the C-ABI library (no GPU compute calls).
+
+The library must load, export every entry point declared in include/cfet.h,
+reproduce the oracle's scheme tables in its host code, and reject invalid
+arguments before touching a device.
+"""
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import schemes as S
+import paper_1102_5071_gb300 as P
+from paper_1102_5071_gb300 import _capi
+from paper_1102_5071_gb300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return _capi.load()
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "cfet.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cfet_[a-z_]+)\s*\(", text)) - {"cfet_drive_fn"})
+
+
+def test_library_exports_every_declared_symbol(lib):
+    syms = _declared_symbols()
+    assert len(syms) >= 10
+    for name in syms:
+        assert hasattr(lib, name), name
+    assert set(syms) == set(_capi.EXPORTED)
+
+
+@pytest.mark.parametrize("name", list(S.SCHEMES))
+def test_scheme_tables_match_oracle(lib, name):
+    order, s, M, f, x, w, g = P.scheme_info(name)
+    sc = S.SCHEMES[name]
+    g_o, x_o, w_o, f_o = S.g_coefficients(sc)
+    assert (order, s, M) == (sc.order, sc.s, sc.nA)
+    assert np.max(np.abs(f - f_o)) < 1e-15
+    assert np.max(np.abs(x - x_o)) < 1e-15 and np.max(np.abs(w - w_o)) < 1e-15
+    assert np.max(np.abs(g - g_o)) < 1e-15
+
+
+def test_scheme_info_rejects_unknown_id(lib):
+    o = C.c_int32()
+    assert lib.cfet_scheme_info(99, C.byref(o), None, None, None, None, None, None, 0) == _capi.CFET_EINVAL
+    assert lib.cfet_scheme_info(0, C.byref(o), None, None, None, None, None, None, 0) == _capi.CFET_EINVAL
+
+
+def _create(lib, h0, vs, fns, opt=None):
+    ctx = C.c_void_p()
+    varr = (_capi.cfet_op * max(1, len(vs)))(*vs)
+    farr = (_capi.DRIVE_FN * max(1, len(fns)))(*fns)
+    st = lib.cfet_create(C.byref(ctx), C.byref(h0), len(vs), varr, farr, None, C.byref(opt) if opt else None)
+    return st, ctx
+
+
+def test_create_validates_arguments(lib):
+    keep = []
+    h = np.zeros(4)
+    ok_h0 = P._op_struct(P.XXZChain(4, 1.0, 0.5, h), keep)
+    xf = P._op_struct(P.XField(4, np.ones(4)), keep)
+    cb = _capi.DRIVE_FN(lambda t, u: 0.0)
+    # mismatched chain length
+    bad_v = P._op_struct(P.XField(5, np.ones(5)), keep)
+    st, _ = _create(lib, ok_h0, [bad_v], [cb])
+    assert st == _capi.CFET_EINVAL and b"X fields" in lib.cfet_last_error(None)
+    # dim inconsistent with nsites
+    bad = P._op_struct(P.XXZChain(4, 1.0, 0.5, h), keep)
+    bad.dim = 17
+    assert _create(lib, bad, [xf], [cb])[0] == _capi.CFET_EINVAL
+    # non-finite field
+    hn = np.array([0.0, np.nan, 0.0, 0.0])
+    assert _create(lib, P._op_struct(P.XXZChain(4, 1.0, 0.5, hn), keep), [xf], [cb])[0] == _capi.CFET_EINVAL
+    # options out of range
+    opt = _capi.cfet_options()
+    lib.cfet_options_default(C.byref(opt))
+    opt.m_max = 65
+    assert _create(lib, ok_h0, [xf], [cb], opt)[0] == _capi.CFET_EINVAL
+    opt.m_max, opt.block_size = 16, 48
+    assert _create(lib, ok_h0, [xf], [cb], opt)[0] == _capi.CFET_EINVAL
+    # DIA offsets out of range
+    dia = P._op_struct(P.DIA(np.array([0, 7]), np.ones((2, 7))), keep)
+    assert _create(lib, dia, [], [])[0] == _capi.CFET_EINVAL
+
+
+def test_options_default(lib):
+    opt = _capi.cfet_options()
+    lib.cfet_options_default(C.byref(opt))
+    assert (opt.m_max, opt.m_min, opt.max_substeps, opt.block_size) == (16, 2, 64, 256)
+    assert opt.barrier_timeout_s == 2.0
+
+
+def test_no_device_gives_enodev(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    keep = []
+    h0 = P._op_struct(P.XXZChain(3, 1.0, 0.5, np.zeros(3)), keep)
+    st, ctx = _create(lib, h0, [], [])
+    assert st == _capi.CFET_ENODEV and not ctx.value
+
+
+def test_binding_refuses_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(_capi, "_lib", None)
+    monkeypatch.setattr(_capi, "library_path", lambda: str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        _capi.load()
