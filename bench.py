@@ -265,9 +265,10 @@ def run_gpu(args):
     # from pinned host memory, runs one CFET step, downloads psi
     host = torch.empty(dim, dtype=torch.complex128, pin_memory=True)
     host.copy_(psi.cpu())
-    e2e_steps = max(3, min(args.steps, 10))
-    prop.propagate_host(host, t0, DT, 1, order=ORDER, tol=TOL)   # warm the staging buffer
-    t0 += DT
+    e2e_steps = 0 if args.no_e2e else max(3, min(args.steps, 10))
+    if e2e_steps:
+        prop.propagate_host(host, t0, DT, 1, order=ORDER, tol=TOL)   # warm the staging buffer
+        t0 += DT
     barrier()
     te = time.perf_counter()
     e2e_app = 0
@@ -277,8 +278,8 @@ def run_gpu(args):
         t0 += DT
     barrier()
     e2e_s = time.perf_counter() - te
-    e2e_val = e2e_app / e2e_s
-    if ws > 1:
+    e2e_val = e2e_app / e2e_s if e2e_steps else None
+    if ws > 1 and e2e_steps:
         import torch.distributed as dist
         tt = torch.tensor([e2e_s, float(e2e_app)], dtype=torch.float64, device="cuda")
         tm = tt.clone()
@@ -328,6 +329,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
