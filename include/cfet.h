@@ -236,6 +236,28 @@ cfet_status cfet_sync(cfet_ctx* ctx, void* stream, cfet_stats* stats);
  * launch).  Synchronises on those events.                                   */
 cfet_status cfet_kernel_time_ms(cfet_ctx* ctx, float* ms);
 
+/* Allocation-free stage exponential for a small driven XXZ chain (no
+ * counterpart in the paper; it exists for callers that cannot allocate
+ * device memory, e.g. code whose device memory is entirely owned by another
+ * allocator or a fixed up-front budget, and latency-critical loops that must
+ * not take the implicit device synchronisation of cudaMalloc/cudaFree):
+ *     psi <- exp(-i tau (c0 H0 + c1 sum_i a_i X_i)) psi,
+ * H0 the open XXZ chain of CFET_OP_XXZ_CHAIN with couplings J, Delta and
+ * fields h.  nsites in [1, 12] (dim <= 4096), m_max in [1, 32]; larger sizes
+ * return CFET_EINVAL.  h[nsites], a[nsites]: host arrays.  psi: device,
+ * complex128[2^nsites], in/out.  Same Krylov rule as cfet_expv (tol <= 0:
+ * fixed dimension m_max).  Allocates nothing: all scratch memory lives in one
+ * static device array of about 2.1 MiB that every GPU loading this library
+ * holds until process exit.  The first call on a device resolves that
+ * array's device address (once per device, with the device current); make
+ * that first call before any stream capture.  Every call reuses the same
+ * array, so calls that overlap on the GPU (other streams, other host threads)
+ * race; serialise them.  Synchronises `stream` and returns the device status;
+ * stats may be NULL.                                                        */
+cfet_status cfet_expv_chain_static(int32_t nsites, double J, double Delta, const double* h, const double* a,
+                                   double c0, double c1, double tau, void* psi, double tol, int32_t m_max,
+                                   void* stream, cfet_stats* stats);
+
 /* Dimension and drive-operator count of ctx (for bindings).                 */
 int64_t cfet_dim(const cfet_ctx* ctx);
 int32_t cfet_num_drives(const cfet_ctx* ctx);

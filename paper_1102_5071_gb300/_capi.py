@@ -83,6 +83,9 @@ def load() -> C.CDLL:
                                           C.POINTER(cfet_stats)]),
         "cfet_sync": (C.c_int, [vp, vp, C.POINTER(cfet_stats)]),
         "cfet_kernel_time_ms": (C.c_int, [vp, C.POINTER(C.c_float)]),
+        "cfet_expv_chain_static": (C.c_int, [C.c_int32, C.c_double, C.c_double, c_double_p, c_double_p,
+                                             C.c_double, C.c_double, C.c_double, vp, C.c_double, C.c_int32, vp,
+                                             C.POINTER(cfet_stats)]),
         "cfet_dim": (C.c_int64, [vp]),
         "cfet_num_drives": (C.c_int32, [vp]),
     }
@@ -96,5 +99,5 @@ def load() -> C.CDLL:
 
 EXPORTED = ["cfet_options_default", "cfet_scheme_info", "cfet_create", "cfet_destroy", "cfet_last_error",
             "cfet_apply", "cfet_expv", "cfet_propagate", "cfet_propagate_ex", "cfet_propagate_host", "cfet_sync",
-            "cfet_kernel_time_ms",
+            "cfet_kernel_time_ms", "cfet_expv_chain_static",
             "cfet_dim", "cfet_num_drives"]
