@@ -212,7 +212,7 @@ def run_gpu(args):
     pr, psi0 = problem()
     dim = 1 << N_SITES
     prop = P.Propagator(P.XXZChain(N_SITES, pr.J, pr.Delta, pr.h), [P.XField(N_SITES, pr.xfield)], [pr.drive],
-                        m_max=M_MAX, max_substeps=64)
+                        m_max=M_MAX, max_substeps=64, precision=args.precision)
     psi = torch.from_numpy(psi0).cuda()
     t0 = 0.0
     # warm-up steps (untimed)
@@ -291,22 +291,31 @@ def run_gpu(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample()
 
+    if args.precision == "fx":
+        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved_gbs / hbm_peak, "traffic": None,
+                    "kernel": "k_propagate_fx (persistent Lanczos, int64 fixed-point vectors)",
+                    "kernel_ms": kernel_ms, "launches": math.ceil(args.steps / 256),
+                    "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), burst figure",
+                    "fp64_equivalent_tflops": achieved_tflops}
+    else:
+        roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                    "kernel": "k_propagate (persistent Lanczos, FP64)", "kernel_ms": kernel_ms,
+                    "launches": math.ceil(args.steps / 256),
+                    "hbm_algorithmic_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak,
+                    "hbm_frac": achieved_gbs / hbm_peak,
+                    "peak_note": "FP64 peak from unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(),
+            "scaling": "weak", "vs_baseline": None, "dtype": "i64" if args.precision == "fx" else "f64",
+            "data": "synthetic", "config": dict(workload_config(), precision=args.precision),
             "cfet_steps_per_s": args.steps * ws / (ms_max * 1e-3),
             "krylov": {"applies_per_step": n_app / args.steps, "substeps": stats["n_substeps"],
                        "max_k": stats["max_k"], "max_err_est": stats["max_err_est"]},
-            "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                         "kernel": "k_propagate (persistent Lanczos, FP64)", "kernel_ms": kernel_ms,
-                         "launches": math.ceil(args.steps / 256),
-                         "hbm_algorithmic_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak,
-                         "hbm_frac": achieved_gbs / hbm_peak,
-                         "peak_note": "FP64 peak from unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"},
+            "roofline": roofline,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 16 * dim, "d2h_bytes_per_step": 16 * dim,
                     "steps": e2e_steps},
             "gpu_launches": math.ceil(args.steps / 256),
@@ -322,6 +331,65 @@ def run_gpu(args):
     return 0
 
 
+def run_sweep(args):
+    """Accuracy study behind "at fixed final-state error": the N=20 chain over
+    T = 20 with orders 4, 6, 8 (default schemes) and dt in {0.05, 0.02, 0.01},
+    each compared with a reference run (CF8:11, dt = 0.0025, tol 1e-13, m <= 24)
+    by ||psi - psi_ref||_2.  Prints one JSON line per run and a summary line."""
+    import torch
+    import paper_1102_5071_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    pr, psi0 = problem()
+    T = args.sweep_T
+
+    def make(m_max):
+        return P.Propagator(P.XXZChain(N_SITES, pr.J, pr.Delta, pr.h), [P.XField(N_SITES, pr.xfield)],
+                            [pr.drive], m_max=m_max, max_substeps=64, precision=args.precision)
+
+    ref_prop = make(24)
+    ref = torch.from_numpy(psi0).cuda()
+    dt_ref = 0.0025
+    n_ref = int(round(T / dt_ref))
+    t = time.perf_counter()
+    st_ref = ref_prop.propagate(ref, 0.0, dt_ref, n_ref, order=8, tol=1e-13)
+    ref_s = time.perf_counter() - t
+    ref_prop.close()
+    rows = []
+    prop = make(M_MAX)
+    for order in (4, 6, 8):
+        for dt in (0.05, 0.02, 0.01):
+            n = int(round(T / dt))
+            psi = torch.from_numpy(psi0).cuda()
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            st = prop.propagate(psi, 0.0, dt, n, order=order, tol=TOL)
+            ev1.record()
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1)
+            err = torch.linalg.vector_norm(psi - ref).item()
+            row = {"order": order, "dt": dt, "steps": n, "final_state_error": err,
+                   "H_applies": st["n_applies"], "H_applies_per_s": st["n_applies"] / (ms * 1e-3),
+                   "cfet_steps_per_s": n / (ms * 1e-3), "time_s": ms * 1e-3,
+                   "norm_drift": abs(torch.linalg.vector_norm(psi).item() - 1.0)}
+            rows.append(row)
+            print(json.dumps(row))
+    prop.close()
+    summary = {"sweep": "driven XXZ chain N=20, T=%g, tol %g, m_max %d, precision %s" % (T, TOL, M_MAX, args.precision),
+               "reference": {"scheme": "CF8:11", "dt": dt_ref, "tol": 1e-13, "m_max": 24,
+                             "H_applies": st_ref["n_applies"], "time_s": ref_s},
+               "cheapest_for_error": {}}
+    for target in (1e-4, 1e-6, 1e-8):
+        ok = [r for r in rows if r["final_state_error"] <= target]
+        if ok:
+            best = min(ok, key=lambda r: r["time_s"])
+            summary["cheapest_for_error"][f"{target:g}"] = {k: best[k] for k in ("order", "dt", "time_s",
+                                                                                 "final_state_error")}
+    print(json.dumps(summary))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -330,11 +398,18 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
+    ap.add_argument("--precision", default="fx", choices=["fx", "f64"],
+                    help="Krylov vector format: int64 fixed point (default) or FP64")
+    ap.add_argument("--sweep", action="store_true",
+                    help="accuracy study: final-state error and throughput per (order, dt) over T")
+    ap.add_argument("--sweep-T", type=float, default=20.0)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
     return run_gpu(args)
 
 

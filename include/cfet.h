@@ -141,7 +141,19 @@ typedef struct cfet_options {
                                 capped at the co-resident maximum)            */
   int32_t steps_per_launch;  /* CFET steps per persistent launch (0 = 256)    */
   double barrier_timeout_s;  /* device barrier wait limit (default 2.0 s)     */
+  int32_t precision;         /* CFET_PREC_* (default CFET_PREC_FX)            */
 } cfet_options;
+
+/* Number format of the Krylov vectors on the device.  Both keep alpha, beta,
+ * the tridiagonal exponential and all decisions in FP64.
+ *  CFET_PREC_F64: complex128 vectors, FP64 arithmetic throughout.
+ *  CFET_PREC_FX : int64 (re, im) mantissas with one exponent per vector
+ *                 (|mantissa| < 2^57), exact integer neighbour sums, exact
+ *                 64x64->128-bit scalar products, exact 128-bit dot products;
+ *                 resolution finer than FP64 relative to each vector's
+ *                 largest entry.  Uses integer units instead of the FP64
+ *                 units, which run at 1/64 of the FP32 rate on GB300.     */
+enum { CFET_PREC_DEFAULT = 0, CFET_PREC_F64 = 1, CFET_PREC_FX = 2 };
 
 typedef struct cfet_stats {
   int64_t n_exp;             /* stage exponentials evaluated                  */

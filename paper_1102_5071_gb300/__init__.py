@@ -111,7 +111,7 @@ class Propagator:
     """CFET propagator for H(t) = H0 + sum_k f_k(t) V_k on the current CUDA device."""
 
     def __init__(self, H0, V=(), drives=(), *, m_max=16, m_min=2, max_substeps=64, block_size=256,
-                 grid_size=0, steps_per_launch=256, barrier_timeout_s=2.0):
+                 grid_size=0, steps_per_launch=256, barrier_timeout_s=2.0, precision="default"):
         lib = _capi.load()
         V = list(V)
         drives = list(drives)
@@ -127,6 +127,7 @@ class Propagator:
         opt.m_max, opt.m_min, opt.max_substeps = m_max, m_min, max_substeps
         opt.block_size, opt.grid_size, opt.steps_per_launch = block_size, grid_size, steps_per_launch
         opt.barrier_timeout_s = barrier_timeout_s
+        opt.precision = _capi.PRECISIONS[precision]
         ctx = C.c_void_p()
         st = lib.cfet_create(C.byref(ctx), C.byref(h0), len(V), varr, fns, None, C.byref(opt))
         if st != 0:

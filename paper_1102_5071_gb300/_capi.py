@@ -29,7 +29,11 @@ class cfet_op(C.Structure):
 class cfet_options(C.Structure):
     _fields_ = [("m_max", C.c_int32), ("m_min", C.c_int32), ("max_substeps", C.c_int32),
                 ("block_size", C.c_int32), ("grid_size", C.c_int32), ("steps_per_launch", C.c_int32),
-                ("barrier_timeout_s", C.c_double)]
+                ("barrier_timeout_s", C.c_double), ("precision", C.c_int32)]
+
+
+CFET_PREC_DEFAULT, CFET_PREC_F64, CFET_PREC_FX = 0, 1, 2
+PRECISIONS = {"default": CFET_PREC_DEFAULT, "f64": CFET_PREC_F64, "fx": CFET_PREC_FX}
 
 
 class cfet_stats(C.Structure):

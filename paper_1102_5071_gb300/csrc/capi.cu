@@ -31,6 +31,7 @@ struct cfet_ctx {
   int nV = 0;
   cfet_options opt{};
   int grid = 1, block = 256;
+  int precision = CFET_PREC_FX;
   std::string err;
   // drives
   std::vector<cfet_drive_fn> f;
@@ -46,6 +47,12 @@ struct cfet_ctx {
   double* d_val = nullptr;
   // workspace
   double2* d_basis = nullptr;
+  // fixed-point path
+  OpSpinFx spin_fx{};
+  OpDiaFx dia_fx{};
+  long long* d_DZ = nullptr;   // DZ_lo | DZ_hi
+  long long* d_VAL = nullptr;
+  longlong2* d_qbasis = nullptr;
   double* d_partials = nullptr;
   unsigned* d_bar = nullptr;
   DevStatus* d_st = nullptr;
@@ -110,6 +117,7 @@ void free_ctx(cfet_ctx* c) {
   cudaFree(c->d_off); cudaFree(c->d_opidx); cudaFree(c->d_val);
   cudaFree(c->d_basis); cudaFree(c->d_partials); cudaFree(c->d_bar); cudaFree(c->d_st);
   cudaFree(c->d_scal); cudaFree(c->d_psi_e2e); cudaFree(c->d_dec);
+  cudaFree(c->d_DZ); cudaFree(c->d_VAL); cudaFree(c->d_qbasis);
   if (c->h_st) cudaFreeHost(c->h_st);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   delete c;
@@ -160,8 +168,13 @@ cfet_status launch_chunk(cfet_ctx* ctx, const PropParams& base, long long e0, lo
   p.scal = base.scal + (size_t)e0 * (1 + ctx->nV);
   p.nexp = ne;
   p.exp_base = e0;
-  int e = ctx->family == kFamilySpin ? launch_propagate_spin(p, ctx->spin, ctx->grid, ctx->block, s)
-                                     : launch_propagate_dia(p, ctx->dia, ctx->grid, ctx->block, s);
+  int e;
+  if (ctx->precision == CFET_PREC_FX)
+    e = ctx->family == kFamilySpin ? launch_propagate_spin_fx(p, ctx->spin_fx, ctx->grid, ctx->block, s)
+                                   : launch_propagate_dia_fx(p, ctx->dia_fx, ctx->grid, ctx->block, s);
+  else
+    e = ctx->family == kFamilySpin ? launch_propagate_spin(p, ctx->spin, ctx->grid, ctx->block, s)
+                                   : launch_propagate_dia(p, ctx->dia, ctx->grid, ctx->block, s);
   if (e != cudaSuccess) return cuda_fail(ctx, (cudaError_t)e, "persistent kernel launch");
   return CFET_OK;
 }
@@ -199,6 +212,7 @@ PropParams base_params(cfet_ctx* ctx, double2* psi, double tau, double tol) {
   p.bar = ctx->d_bar;
   p.st = ctx->d_st;
   p.timeout_ns = (long long)(ctx->opt.barrier_timeout_s * 1e9);
+  p.qbasis = ctx->d_qbasis;
   return p;
 }
 
@@ -228,6 +242,7 @@ void cfet_options_default(cfet_options* opt) {
   opt->grid_size = 0;
   opt->steps_per_launch = 256;
   opt->barrier_timeout_s = 2.0;
+  opt->precision = CFET_PREC_FX;
 }
 
 cfet_status cfet_scheme_info(int32_t scheme, int32_t* order, int32_t* s, int32_t* M, double* f, double* x,
@@ -281,6 +296,9 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
   if (o.steps_per_launch <= 0) o.steps_per_launch = 256;
   if (!(o.barrier_timeout_s > 0.0) || !is_finite_d(o.barrier_timeout_s))
     return fail(nullptr, CFET_EINVAL, "barrier_timeout_s must be positive");
+  if (o.precision == CFET_PREC_DEFAULT) o.precision = CFET_PREC_FX;
+  if (o.precision != CFET_PREC_F64 && o.precision != CFET_PREC_FX)
+    return fail(nullptr, CFET_EINVAL, "precision must be CFET_PREC_F64 or CFET_PREC_FX");
 
   int family = 0, dim = 0, nsites = 0;
   if (H0->kind == CFET_OP_XXZ_CHAIN) {
@@ -331,7 +349,10 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
   ctx->dim = dim;
   ctx->nV = nV;
   ctx->opt = o;
-  ctx->block = o.block_size;
+  // FP64 kernel: block_size threads; fixed-point kernel: 2 * block_size
+  // worker threads plus one control warp (default 512 + 32, one CTA per SM)
+  ctx->block = o.precision == CFET_PREC_FX ? 2 * o.block_size + 32 : o.block_size;
+  ctx->precision = o.precision;
   for (int k = 0; k < nV; ++k) {
     ctx->f.push_back(f[k]);
     ctx->f_user.push_back(f_user ? f_user[k] : nullptr);
@@ -371,6 +392,38 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
     ctx->spin.dz_lo = ctx->d_dz_lo;
     ctx->spin.dz_hi = ctx->d_dz_hi;
     ctx->spin.xf = ctx->d_xf;
+    // fixed-point diagonal tables: DZ = round(dz * 2^-E_dz), |DZ_lo + DZ_hi| < 2^61
+    std::vector<double> lo(nlo), hi(nhi);
+    CKC(cudaMemcpy(lo.data(), ctx->d_dz_lo, nlo * sizeof(double), cudaMemcpyDeviceToHost), "download dz_lo");
+    CKC(cudaMemcpy(hi.data(), ctx->d_dz_hi, nhi * sizeof(double), cudaMemcpyDeviceToHost), "download dz_hi");
+    double mlo = 0.0, mhi = 0.0;
+    for (double v : lo) mlo = std::fmax(mlo, std::fabs(v));
+    for (double v : hi) mhi = std::fmax(mhi, std::fabs(v));
+    const double maxdz = (mlo + mhi) * (1.0 + 1e-12);
+    int E_dz = 0;
+    if (maxdz > 0.0) {
+      int ex = 0;
+      std::frexp(maxdz, &ex);          // maxdz < 2^ex
+      E_dz = ex - 60;                  // |DZ| < 2^60 each
+    }
+    std::vector<long long> dz((size_t)nlo + nhi);
+    for (size_t i = 0; i < nlo; ++i) dz[i] = std::llrint(std::ldexp(lo[i], -E_dz));
+    for (size_t i = 0; i < nhi; ++i) dz[nlo + i] = std::llrint(std::ldexp(hi[i], -E_dz));
+    CKC(cudaMalloc(&ctx->d_DZ, dz.size() * sizeof(long long)), "cudaMalloc(DZ)");
+    CKC(cudaMemcpy(ctx->d_DZ, dz.data(), dz.size() * sizeof(long long), cudaMemcpyHostToDevice), "upload DZ");
+    bool uniform = true;
+    for (int k = 0; k < nV; ++k)
+      for (int i = 1; i < N; ++i)
+        if (V[k].site_coeff[i] != V[k].site_coeff[0]) uniform = false;
+    ctx->spin_fx.N = N;
+    ctx->spin_fx.lo_bits = L;
+    ctx->spin_fx.E_dz = E_dz;
+    ctx->spin_fx.uniform = uniform ? 1 : 0;
+    ctx->spin_fx.DZ_lo = ctx->d_DZ;
+    ctx->spin_fx.DZ_hi = ctx->d_DZ + nlo;
+    ctx->spin_fx.maxdz = maxdz;
+    ctx->spin_fx.J2 = 2.0 * H0->J;
+    ctx->spin_fx.xf = ctx->d_xf;
   } else {
     std::vector<long long> off;
     std::vector<int> opidx;
@@ -398,21 +451,77 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
     ctx->dia.off = ctx->d_off;
     ctx->dia.opidx = ctx->d_opidx;
     ctx->dia.val = ctx->d_val;
+    // fixed-point values: one exponent per operator, |VAL| < 2^62; row bound
+    OpDiaFx& fx = ctx->dia_fx;
+    fx.ndiag = nd;
+    fx.nops = 1 + nV;
+    fx.off = ctx->d_off;
+    fx.opidx = ctx->d_opidx;
+    std::vector<long long> VAL((size_t)nd * dim);
+    int dcur = 0;
+    for (int k = -1; k < nV; ++k) {
+      const cfet_op& o2 = k < 0 ? *H0 : V[k];
+      const int oi = k + 1;
+      double vmax = 0.0;
+      std::vector<double> rowsum(dim, 0.0);
+      for (int d = 0; d < o2.ndiag; ++d)
+        for (int r = 0; r < dim; ++r) {
+          const long long c = (long long)r + o2.offsets[d];
+          const double v = (c >= 0 && c < dim) ? std::fabs(o2.values[(size_t)d * dim + r]) : 0.0;
+          vmax = std::fmax(vmax, v);
+          rowsum[r] += v;
+        }
+      int E_op = 0;
+      if (vmax > 0.0) {
+        int ex = 0;
+        std::frexp(vmax * (1.0 + 1e-12), &ex);
+        E_op = ex - 62;
+      }
+      double mrow = 0.0;
+      for (double v : rowsum) mrow = std::fmax(mrow, v);
+      fx.E_op[oi] = E_op;
+      fx.maxrow[oi] = mrow * (1.0 + 1e-12);
+      fx.dfirst[oi] = dcur;
+      fx.dcount[oi] = o2.ndiag;
+      for (int d = 0; d < o2.ndiag; ++d, ++dcur)
+        for (int r = 0; r < dim; ++r) {
+          const long long c = (long long)r + o2.offsets[d];
+          const double v = (c >= 0 && c < dim) ? o2.values[(size_t)d * dim + r] : 0.0;
+          VAL[(size_t)dcur * dim + r] = std::llrint(std::ldexp(v, -E_op));
+        }
+    }
+    CKC(cudaMalloc(&ctx->d_VAL, VAL.size() * sizeof(long long)), "cudaMalloc(VAL)");
+    CKC(cudaMemcpy(ctx->d_VAL, VAL.data(), VAL.size() * sizeof(long long), cudaMemcpyHostToDevice), "upload VAL");
+    fx.VAL = ctx->d_VAL;
   }
   // persistent grid: co-resident maximum, no more CTAs than needed to give
   // every thread at least one element
-  const int maxg = max_coresident_blocks(family, ctx->block);
+  const int maxg = ctx->precision == CFET_PREC_FX ? max_coresident_blocks_fx(family, ctx->block)
+                                                  : max_coresident_blocks(family, ctx->block);
   if (maxg < 1) {
     free_ctx(ctx);
     return fail(nullptr, CFET_ECUDA, "occupancy query failed for the persistent kernel");
   }
-  int want = (dim + ctx->block - 1) / ctx->block;
+  // element threads per CTA (the fixed-point kernel adds one control warp)
+  const int workers = ctx->precision == CFET_PREC_FX ? ctx->block - 32 : ctx->block;
+  int want = (dim + workers - 1) / workers;
   if (o.grid_size > 0) want = o.grid_size;
   ctx->grid = want < maxg ? want : maxg;
   if (ctx->grid < 1) ctx->grid = 1;
 
-  CKC(cudaMalloc(&ctx->d_basis, (size_t)o.m_max * dim * sizeof(double2)), "cudaMalloc(Krylov basis)");
-  CKC(cudaMalloc(&ctx->d_partials, 2 * (size_t)ctx->grid * sizeof(double)), "cudaMalloc(partials)");
+  if (ctx->precision == CFET_PREC_FX)
+    CKC(cudaMalloc(&ctx->d_qbasis, (size_t)(o.m_max + 1) * dim * sizeof(longlong2)), "cudaMalloc(Krylov basis)");
+  else
+    CKC(cudaMalloc(&ctx->d_basis, (size_t)o.m_max * dim * sizeof(double2)), "cudaMalloc(Krylov basis)");
+  if (ctx->precision == CFET_PREC_FX) {
+    // exact per-thread sums stay below 2^127 for at most 4096 elements per thread
+    const long long per_thread = ((long long)dim + (long long)ctx->grid * workers - 1) / ((long long)ctx->grid * workers);
+    if (per_thread > 4096) {
+      free_ctx(ctx);
+      return fail(nullptr, CFET_EINVAL, "fixed-point precision: dimension too large for the grid, use CFET_PREC_F64");
+    }
+  }
+  CKC(cudaMalloc(&ctx->d_partials, 9 * (size_t)ctx->grid * sizeof(double)), "cudaMalloc(partials)");
   CKC(cudaMalloc(&ctx->d_bar, 2 * sizeof(unsigned)), "cudaMalloc(barrier)");
   CKC(cudaMemset(ctx->d_bar, 0, 2 * sizeof(unsigned)), "barrier init");
   CKC(cudaMalloc(&ctx->d_st, sizeof(DevStatus)), "cudaMalloc(status)");

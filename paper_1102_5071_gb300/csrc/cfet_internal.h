@@ -55,6 +55,31 @@ struct OpDia {
   const double* val;     // [ndiag * dim]
 };
 
+// Fixed-point forms of the operator families (see kernels_fx.cu).
+struct OpSpinFx {
+  int N;
+  int lo_bits;
+  int E_dz;               // DZ tables hold dz * 2^-E_dz as int64, |DZ_lo + DZ_hi| < 2^61
+  int uniform;            // every drive field has the same coefficient on all sites
+  const long long* DZ_lo;
+  const long long* DZ_hi;
+  double maxdz;           // bound of |dz(x)| in real units
+  double J2;              // 2 J
+  const double* xf;       // [nV * N] per-field per-site X coefficients
+};
+
+struct OpDiaFx {
+  int ndiag;
+  int nops;               // 1 + nV
+  const long long* off;   // [ndiag]
+  const int* opidx;       // [ndiag], diagonals grouped by operator (non-decreasing)
+  const long long* VAL;   // [ndiag * dim]: val * 2^-E_op[opidx[d]], |VAL| < 2^62
+  int E_op[1 + kMaxDrives];
+  double maxrow[1 + kMaxDrives];  // max over rows of sum_{d in op} |val_d[r]|
+  int dfirst[1 + kMaxDrives];     // first diagonal of each operator
+  int dcount[1 + kMaxDrives];     // number of diagonals of each operator
+};
+
 struct PropParams {
   int dim;
   int nV;
@@ -74,6 +99,9 @@ struct PropParams {
   unsigned* bar;         // [2]: arrival count, generation
   DevStatus* st;
   long long timeout_ns;
+  // fixed-point path: Krylov vectors q_1 .. q_{m_max+1} as int64 (re, im)
+  // pairs; q_i at qbasis + (i-1)*dim.  partials then hold 4 * gridDim.x.
+  longlong2* qbasis;
 };
 
 // ---------------------------------------------------------------- launchers
@@ -86,6 +114,9 @@ int launch_apply_dia(const OpDia& op, int dim, const double* c, int nV, const do
                      void* stream);
 int launch_spin_tables(int N, int L, double J, double Delta, const double* h, double* dz_lo, double* dz_hi,
                        void* stream);
+int launch_propagate_spin_fx(const PropParams& p, const OpSpinFx& op, int grid, int block, void* stream);
+int launch_propagate_dia_fx(const PropParams& p, const OpDiaFx& op, int grid, int block, void* stream);
+int max_coresident_blocks_fx(int family, int block);
 int max_coresident_blocks(int family, int block);  // per device, for the persistent kernel
 size_t propagate_smem_bytes(int block);
 

@@ -1,0 +1,209 @@
+// Device helpers shared by the FP64 and fixed-point persistent kernels:
+// bounded grid barrier, CTA/grid reductions, and the small tridiagonal
+// exponential exp(-i tau T_k) e_1 with the Gershgorin spread of T_k.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "cfet_internal.h"
+
+namespace cfet {
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ long long global_timer_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_volatile_u32(const unsigned* p) {
+  return *reinterpret_cast<const volatile unsigned*>(p);
+}
+__device__ __forceinline__ int ld_volatile_i32(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
+
+// Bounded grid-wide barrier (arrival counter + generation).  Returns false in
+// every thread of the CTA when the wait limit expired or another CTA reported
+// an error; the first CTA to time out records CFET_ETIMEOUT.
+static __device__ bool grid_barrier(unsigned* bar, unsigned& gen, int* status, long long timeout_ns, int* s_ok) {
+  __syncthreads();
+  if (gridDim.x == 1) {
+    gen += 1;
+    return true;
+  }
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned target = gen + 1;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&bar[0], 1u) + 1u;
+    if (arrived == gridDim.x) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicExch(&bar[1], target);
+    } else {
+      const long long t0 = global_timer_ns();
+      unsigned spins = 0;
+      while (ld_volatile_u32(&bar[1]) != target) {
+        if ((++spins & 63u) == 0u) {
+          if (ld_volatile_i32(status) != 0) { ok = 0; break; }
+          if (global_timer_ns() - t0 > timeout_ns) {
+            atomicCAS(status, 0, (int)CFET_ETIMEOUT);
+            ok = 0;
+            break;
+          }
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    *s_ok = ok;
+  }
+  gen += 1;
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+// Sum over the CTA of one double per thread; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    for (int i = 0; i < nw; ++i) s += red[i];
+  }
+  return s;
+}
+
+// Deterministic sum of the per-CTA partials (same order in every CTA);
+// executed by warp 0, result returned to all lanes of warp 0.
+__device__ __forceinline__ double sum_partials(const double* part) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < (int)gridDim.x; i += 32) s += part[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// Maximum over the CTA of one double per thread; result valid in thread 0.
+__device__ __forceinline__ double block_max(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    for (int i = 0; i < nw; ++i) s = fmax(s, red[i]);
+  }
+  return s;
+}
+
+// Maximum of the per-CTA partials (warp 0, result in all lanes of warp 0).
+__device__ __forceinline__ double max_partials(const double* part) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < (int)gridDim.x; i += 32) s = fmax(s, part[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+  return s;
+}
+
+// ------------------------------------------------------------------ small problem
+// y = exp(-i ts T) e_1 for the k x k real symmetric tridiagonal T (diagonal
+// a[0..k-1], off-diagonal b[0..k-2]); executed by one warp, rows r = lane and
+// lane + 32.  Method: spectral shift by the Gershgorin centre sigma, S equal
+// substeps with |ts| rho / S <= 1 (rho the Gershgorin radius), each a Taylor
+// series of kSmallTaylorTerms terms; exp(-i ts T) = e^{-i ts sigma}
+// exp(-i ts (T - sigma)).
+static __device__ void small_expm_e1(int k, const double* a, const double* b, double ts, double* yr, double* yi,
+                              double* tr, double* ti) {
+  const int lane = threadIdx.x & 31;
+  double lo = 1e300, hi = -1e300;
+  for (int r = lane; r < k; r += 32) {
+    const double rad = (r > 0 ? fabs(b[r - 1]) : 0.0) + (r < k - 1 ? fabs(b[r]) : 0.0);
+    lo = fmin(lo, a[r] - rad);
+    hi = fmax(hi, a[r] + rad);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  const double sig = 0.5 * (lo + hi), rho = 0.5 * (hi - lo);
+  // number of Taylor substeps, bounded: a non-finite spread gives S = 1 (the
+  // result is then non-finite and rejected by the caller), a huge one 65536
+  const double sr = fabs(ts) * rho;
+  int S = 1;
+  if (sr == sr) S = sr < 65536.0 ? (int)ceil(sr) : 65536;
+  if (S < 1) S = 1;
+  const double hstep = ts / S;
+  // rows owned by this lane
+  const int r0 = lane, r1 = lane + 32;
+  double ar0 = 0, ai0 = 0, ar1 = 0, ai1 = 0;  // accumulators (current y)
+  if (r0 < k) { ar0 = (r0 == 0) ? 1.0 : 0.0; ai0 = 0.0; }
+  if (r1 < k) { ar1 = 0.0; ai1 = 0.0; }
+  for (int sidx = 0; sidx < S; ++sidx) {
+    double t_r0 = ar0, t_i0 = ai0, t_r1 = ar1, t_i1 = ai1;
+    if (r0 < k) { tr[r0] = t_r0; ti[r0] = t_i0; }
+    if (r1 < k) { tr[r1] = t_r1; ti[r1] = t_i1; }
+    __syncwarp();
+    for (int n = 1; n <= kSmallTaylorTerms; ++n) {
+      const double c = hstep / n;
+      double zr0 = 0, zi0 = 0, zr1 = 0, zi1 = 0;
+      if (r0 < k) {
+        zr0 = (a[r0] - sig) * t_r0;
+        zi0 = (a[r0] - sig) * t_i0;
+        if (r0 > 0) { zr0 = fma(b[r0 - 1], tr[r0 - 1], zr0); zi0 = fma(b[r0 - 1], ti[r0 - 1], zi0); }
+        if (r0 < k - 1) { zr0 = fma(b[r0], tr[r0 + 1], zr0); zi0 = fma(b[r0], ti[r0 + 1], zi0); }
+      }
+      if (r1 < k) {
+        zr1 = (a[r1] - sig) * t_r1;
+        zi1 = (a[r1] - sig) * t_i1;
+        zr1 = fma(b[r1 - 1], tr[r1 - 1], zr1);
+        zi1 = fma(b[r1 - 1], ti[r1 - 1], zi1);
+        if (r1 < k - 1) { zr1 = fma(b[r1], tr[r1 + 1], zr1); zi1 = fma(b[r1], ti[r1 + 1], zi1); }
+      }
+      __syncwarp();
+      // t <- (-i c) z
+      t_r0 = c * zi0; t_i0 = -c * zr0;
+      t_r1 = c * zi1; t_i1 = -c * zr1;
+      ar0 += t_r0; ai0 += t_i0; ar1 += t_r1; ai1 += t_i1;
+      if (r0 < k) { tr[r0] = t_r0; ti[r0] = t_i0; }
+      if (r1 < k) { tr[r1] = t_r1; ti[r1] = t_i1; }
+      __syncwarp();
+    }
+  }
+  double sn, cs;
+  sincos(ts * sig, &sn, &cs);
+  // multiply by e^{-i ts sig} = cs - i sn
+  if (r0 < k) { yr[r0] = ar0 * cs + ai0 * sn; yi[r0] = ai0 * cs - ar0 * sn; }
+  if (r1 < k) { yr[r1] = ar1 * cs + ai1 * sn; yi[r1] = ai1 * cs - ar1 * sn; }
+  __syncwarp();
+}
+
+// Gershgorin width of T (max of a_r + radius minus min of a_r - radius), an
+// upper bound of its eigenvalue spread; warp-uniform result.
+static __device__ double gersh_width(int k, const double* a, const double* b) {
+  const int lane = threadIdx.x & 31;
+  double lo = 1e300, hi = -1e300;
+  for (int r = lane; r < k; r += 32) {
+    const double rad = (r > 0 ? fabs(b[r - 1]) : 0.0) + (r < k - 1 ? fabs(b[r]) : 0.0);
+    lo = fmin(lo, a[r] - rad);
+    hi = fmax(hi, a[r] + rad);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  return hi - lo;
+}
+
+}  // namespace cfet

@@ -1,0 +1,837 @@
+// Fixed-point persistent Lanczos kernel (sm_103a).
+//
+// Same method and decisions as k_propagate (kernels.cu): the stage
+// exponential exp(-i tau H_j) psi of a CFET step (Alvermann & Fehske,
+// arXiv:1102.5071, Sec. 4 Eq. (Ucf), Sec. 7 Eq. (OmGLeg)) by the Lanczos /
+// Krylov method of Sec. 8.1 with the a-posteriori estimate, adaptive Krylov
+// dimension and substepping.  Two things differ.
+//
+// Number format.  On GB300 FP64 runs at 1/64 of the FP32 rate while 32-bit
+// integer add/logic/multiply-add run at full or half rate, so every Krylov
+// vector q_i is stored as int64 (re, im) mantissas with one exponent per
+// vector (value = M * 2^E_i, |M| < 2^57):
+//   * neighbour sums of the apply are exact integer additions (up to 32
+//     terms stay below 2^62);
+//   * a product of a real scalar (or a per-element table value) with a stored
+//     value or sum takes the high 64 bits of a 64x64 product of operands
+//     normalised to 62 bits, shifted (rounding) once to the result exponent;
+//   * the result exponent of each new vector comes from a rigorous bound
+//     built from the scalars and the measured maxima of the inputs, so no
+//     value overflows; the resolution is 2^-57 of that bound;
+//   * alpha, ||w||^2 and ||psi||^2 are exact 128-bit sums, reduced exactly
+//     over the CTA and the grid (order-independent, deterministic) and
+//     rounded to FP64 once.
+//
+// Work split.  Each CTA has NW worker warps doing only integer element work
+// and one control warp doing all FP64 scalar work: the global reductions,
+// the grid barrier, the per-pass constants, and the small tridiagonal
+// exponential of the error estimate.  The error estimate of iteration k runs
+// on the control warp while the workers already compute the apply of
+// iteration k+1; if it accepts k, that apply is discarded.  The accepted
+// estimate's y = exp(-i tau T_k) e_1 is reused for the reconstruction.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "cfet_internal.h"
+#include "device_common.cuh"
+
+namespace cfet {
+
+// ------------------------------------------------------------------ fixed-point helpers
+constexpr int kFxBits = 57;  // stored |M| < 2^57
+// Per-thread exact 128-bit sums of products (< 2^115 each, at most 4096 per
+// thread) are shifted right by kRedShift before the CTA and grid reductions,
+// so that up to 2^17 threads cannot overflow 127 bits; the dropped bits are
+// below 2^-68 of any non-zero sum of squares.
+constexpr int kRedShift = 24;
+
+__device__ __forceinline__ int fx_ilog2(double v) {  // floor(log2 v), v > 0 normal
+  return (int)((__double_as_longlong(v) >> 52) & 0x7ff) - 1023;
+}
+// Exponent E with bound < 2^(bits + E); a zero bound gives a very small E.
+__device__ __forceinline__ int fx_exp_for(double bound, int bits) {
+  if (!(bound > 1e-290) || !(bound < 1e290)) return -960;
+  return fx_ilog2(bound * (1.0 + 1e-12)) - (bits - 1);
+}
+// Left shift that brings a value of magnitude <= a (a >= 1) to < 2^62.
+__device__ __forceinline__ int fx_norm_shift(double a) {
+  if (!(a >= 1.0)) return 0;
+  const int p = 61 - fx_ilog2(a * (1.0 + 1e-12));
+  return p < 0 ? 0 : (p > 61 ? 61 : p);
+}
+
+// Exact decomposition v = m * 2^e with |m| in [2^61, 2^62) (m = 0 for 0).
+struct Mant {
+  long long m;
+  int e;
+};
+__device__ __forceinline__ Mant fx_mant(double v) {
+  Mant r;
+  const long long b = __double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex == 0) { r.m = 0; r.e = 0; return r; }  // zero (subnormals treated as zero)
+  const long long frac = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+  r.m = frac << 9;
+  r.e = ex - 1075 - 9;
+  if (b < 0) r.m = -r.m;
+  return r;
+}
+
+// h * 2^-s rounded (half up); s is uniform across the warp.
+__device__ __forceinline__ long long fx_rshr(long long h, int s) {
+  if (s <= 0) return s <= -62 ? 0LL : (h << (-s));
+  if (s >= 63) return 0LL;
+  return (h + (1LL << (s - 1))) >> s;
+}
+// round(m * x * 2^-(64 + s)); |m|, |x| < 2^62.
+__device__ __forceinline__ long long fx_mul(long long m, long long x, int s) {
+  return fx_rshr(__mul64hi(m, x), s);
+}
+// p * 2^-sh as int64 (truncated); callers guarantee the result fits.
+__device__ __forceinline__ long long fx_shr128(__int128 p, int sh) {
+  if (sh >= 127) return p < 0 ? -1LL : 0LL;
+  if (sh >= 0) return (long long)(p >> sh);
+  if (sh <= -63) return 0LL;
+  return (long long)(p << (-sh));
+}
+__device__ __forceinline__ long long fx_absmax(long long a, long long b) {
+  const long long x = a < 0 ? -a : a, y = b < 0 ? -b : b;
+  return x > y ? x : y;
+}
+
+// ------------------------------------------------------------------ exact reductions
+// Sum over a warp of (lo, hi) 128-bit values and max of an int64 (lane 0 result).
+__device__ __forceinline__ void fx_warp_reduce(unsigned long long& lo, long long& hi, long long& mx) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long lo2 = __shfl_down_sync(0xffffffffu, lo, o);
+    const long long hi2 = __shfl_down_sync(0xffffffffu, hi, o);
+    const long long mx2 = __shfl_down_sync(0xffffffffu, mx, o);
+    const unsigned long long s = lo + lo2;
+    hi = hi + hi2 + (s < lo ? 1 : 0);
+    lo = s;
+    mx = mx > mx2 ? mx : mx2;
+  }
+}
+__device__ __forceinline__ double fx_i128_to_double(unsigned long long lo, long long hi) {
+  // (hi * 2^64 + lo) * 2^kRedShift
+  return ldexp(fma(__ll2double_rn(hi), 18446744073709551616.0, __ull2double_rn(lo)), kRedShift);
+}
+
+// ------------------------------------------------------------------ shared state
+struct FxConstA {
+  // spin
+  long long m_cz, m_hop, m_x, m_p;
+  int s_d, s_diag, s_hop, s_x, s_p, s_nu;
+  int pk, ph, px, pp;
+  int use_prev;
+  // dia: per operator P_o = shr128(sum VAL q, sh_pre[o]); term = fx_mul(m_op[o], P_o, s_op[o])
+  long long m_op[1 + kMaxDrives];
+  int sh_pre[1 + kMaxDrives];
+  int s_op[1 + kMaxDrives];
+};
+
+struct SmemFx {
+  // per-warp partials of the workers
+  unsigned long long wlo[32];
+  long long whi[32];
+  long long wmx[32];
+  // Lanczos scalars (FP64) and vector metadata
+  double alpha[kMaxKrylov + 2];
+  double beta[kMaxKrylov + 2];
+  double scale[kMaxKrylov + 3];  // 1 / ||q_i||, real units
+  double A[kMaxKrylov + 3];      // max stored |M| of q_i
+  int E[kMaxKrylov + 3];         // exponent of q_i
+  double yr[kMaxKrylov], yi[kMaxKrylov];
+  double tr[kMaxKrylov], ti[kMaxKrylov];
+  // reconstruction constants
+  long long crm[kMaxKrylov], cim[kMaxKrylov];
+  int csr[kMaxKrylov], csi[kMaxKrylov], cp[kMaxKrylov];
+  // stage data
+  double scal[1 + kMaxDrives];
+  double bsite_raw[kMaxSites];
+  long long mb[kMaxSites];
+  FxConstA ca;
+  // phase B constants
+  long long m_a;
+  int s_a, sh_u, pk_b;
+  int Eu, Ew, Epsi;
+  // control flags
+  int abort_flag;     // leave the kernel
+  int stop_prev;      // the deferred check accepted the previous iteration
+  int accept_now;     // accepted at the current iteration
+  int pend;           // a check of the current iteration is deferred
+  int y_ready;        // yr/yi hold exp(-i ts T_k) e_1 for the accepted (k, ts)
+  int acc_h;
+  int final_rec;
+  double err_now, err_prev;
+  double beta0;
+};
+
+// ------------------------------------------------------------------ applies
+__device__ __forceinline__ longlong2 fx_apply_spin(const longlong2* q, const longlong2* qm, int x,
+                                                   const OpSpinFx& op, const FxConstA& c, const long long* mb) {
+  const int N = op.N, L = op.lo_bits;
+  const long long dz = __ldg(op.DZ_lo + (x & ((1 << L) - 1))) + __ldg(op.DZ_hi + (x >> (L - 1)));
+  const long long D = fx_mul(c.m_cz, dz << 1, c.s_d);  // |D| < 2^59
+  const long long Dp = D << 3;
+  const longlong2 v = q[x];
+  long long ur = fx_mul(Dp, v.x << c.pk, c.s_diag);
+  long long ui = fx_mul(Dp, v.y << c.pk, c.s_diag);
+  long long hr = 0, hi = 0;
+  const unsigned anti = ((unsigned)x ^ ((unsigned)x >> 1)) & ((1u << (N - 1)) - 1u);
+#pragma unroll 4
+  for (int i = 0; i < N - 1; ++i) {
+    if ((anti >> i) & 1u) {
+      const longlong2 w = q[x ^ (3 << i)];
+      hr += w.x;
+      hi += w.y;
+    }
+  }
+  ur += fx_mul(c.m_hop, hr << c.ph, c.s_hop);
+  ui += fx_mul(c.m_hop, hi << c.ph, c.s_hop);
+  if (op.uniform) {
+    long long xr = 0, xi = 0;
+#pragma unroll 4
+    for (int i = 0; i < N; ++i) {
+      const longlong2 w = q[x ^ (1 << i)];
+      xr += w.x;
+      xi += w.y;
+    }
+    ur += fx_mul(c.m_x, xr << c.px, c.s_x);
+    ui += fx_mul(c.m_x, xi << c.px, c.s_x);
+  } else {
+#pragma unroll 4
+    for (int i = 0; i < N; ++i) {
+      const longlong2 w = q[x ^ (1 << i)];
+      ur += fx_mul(mb[i], w.x << c.pk, c.s_nu);
+      ui += fx_mul(mb[i], w.y << c.pk, c.s_nu);
+    }
+  }
+  if (c.use_prev) {
+    const longlong2 w = qm[x];
+    ur += fx_mul(c.m_p, w.x << c.pp, c.s_p);
+    ui += fx_mul(c.m_p, w.y << c.pp, c.s_p);
+  }
+  return make_longlong2(ur, ui);
+}
+
+__device__ __forceinline__ longlong2 fx_apply_dia(const longlong2* q, const longlong2* qm, int r, int dim,
+                                                  const OpDiaFx& op, const FxConstA& c) {
+  long long ur = 0, ui = 0;
+  for (int o = 0; o < op.nops; ++o) {
+    __int128 ar = 0, ai = 0;
+    const int d0 = op.dfirst[o], d1 = d0 + op.dcount[o];
+    for (int d = d0; d < d1; ++d) {
+      const long long cidx = (long long)r + __ldg(op.off + d);
+      if (cidx >= 0 && cidx < dim) {
+        const long long a = __ldg(op.VAL + (size_t)d * dim + r);
+        const longlong2 w = q[cidx];
+        ar += (__int128)a * w.x;
+        ai += (__int128)a * w.y;
+      }
+    }
+    ur += fx_mul(c.m_op[o], fx_shr128(ar, c.sh_pre[o]), c.s_op[o]);
+    ui += fx_mul(c.m_op[o], fx_shr128(ai, c.sh_pre[o]), c.s_op[o]);
+  }
+  if (c.use_prev) {
+    const longlong2 w = qm[r];
+    ur += fx_mul(c.m_p, w.x << c.pp, c.s_p);
+    ui += fx_mul(c.m_p, w.y << c.pp, c.s_p);
+  }
+  return make_longlong2(ur, ui);
+}
+
+// ------------------------------------------------------------------ control-warp helpers
+// Bounded grid barrier executed by the control warp only (lane 0 spins).
+__device__ bool fx_ctl_barrier(unsigned* bar, unsigned& gen, int* status, long long timeout_ns) {
+  const int lane = threadIdx.x & 31;
+  int ok = 1;
+  if (gridDim.x > 1 && lane == 0) {
+    const unsigned target = gen + 1;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&bar[0], 1u) + 1u;
+    if (arrived == gridDim.x) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicExch(&bar[1], target);
+    } else {
+      const long long t0 = global_timer_ns();
+      unsigned spins = 0;
+      while (ld_volatile_u32(&bar[1]) != target) {
+        if ((++spins & 63u) == 0u) {
+          if (ld_volatile_i32(status) != 0) { ok = 0; break; }
+          if (global_timer_ns() - t0 > timeout_ns) {
+            atomicCAS(status, 0, (int)CFET_ETIMEOUT);
+            ok = 0;
+            break;
+          }
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  gen += 1;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  return ok != 0;
+}
+
+// Control warp: combine the workers' per-warp partials into this CTA's partial
+// (slot `part`), pass the grid barrier, and return the exact global sum (as
+// FP64) and the global max to all lanes.
+__device__ bool fx_ctl_reduce(SmemFx& S, int NW, long long* part, unsigned* bar, unsigned& gen, int* status,
+                              long long timeout_ns, double& sum, long long& mxi) {
+  const int lane = threadIdx.x & 31;
+  const int G = gridDim.x;
+  unsigned long long lo = 0;
+  long long hi = 0, m = 0;
+  if (lane < NW) { lo = S.wlo[lane]; hi = S.whi[lane]; m = S.wmx[lane]; }
+  fx_warp_reduce(lo, hi, m);
+  if (lane == 0) {
+    part[3 * blockIdx.x + 0] = (long long)lo;
+    part[3 * blockIdx.x + 1] = hi;
+    part[3 * blockIdx.x + 2] = m;
+  }
+  __syncwarp();
+  if (!fx_ctl_barrier(bar, gen, status, timeout_ns)) return false;
+  lo = 0; hi = 0; m = 0;
+  for (int i = lane; i < G; i += 32) {
+    const unsigned long long l2 = (unsigned long long)part[3 * i + 0];
+    const long long h2 = part[3 * i + 1];
+    const long long m2 = part[3 * i + 2];
+    const unsigned long long s = lo + l2;
+    hi = hi + h2 + (s < lo ? 1 : 0);
+    lo = s;
+    m = m > m2 ? m : m2;
+  }
+  fx_warp_reduce(lo, hi, m);
+  lo = __shfl_sync(0xffffffffu, lo, 0);
+  hi = __shfl_sync(0xffffffffu, hi, 0);
+  m = __shfl_sync(0xffffffffu, m, 0);
+  sum = fx_i128_to_double(lo, hi);
+  mxi = m;
+  return true;
+}
+
+// Worker warps: per-warp reduction of (int128 sum, int64 max) into shared memory.
+__device__ __forceinline__ void fx_worker_partial(SmemFx& S, __int128 acc, long long mx) {
+  acc >>= kRedShift;
+  unsigned long long lo = (unsigned long long)acc;
+  long long hi = (long long)(acc >> 64);
+  fx_warp_reduce(lo, hi, mx);
+  if ((threadIdx.x & 31) == 0) {
+    const int w = threadIdx.x >> 5;
+    S.wlo[w] = lo;
+    S.whi[w] = hi;
+    S.wmx[w] = mx;
+  }
+}
+
+// Phase-A constants (control lane 0): result exponent of
+// u = s_k H q_k - beta_{k-1} s_{k-1} q_{k-1} from the bound of every term,
+// normalising shifts and product shifts.
+template <int FAMILY, class Op>
+__device__ void fx_const_a(SmemFx& S, const Op& op, int it) {
+  FxConstA& c = S.ca;
+  const double sk = S.scale[it];
+  const int Ek = S.E[it];
+  const double Ak = S.A[it];
+  const double Akr = ldexp(Ak, Ek);
+  const double bp = it > 1 ? S.beta[it - 1] * S.scale[it - 1] : 0.0;
+  const double Apr = it > 1 ? ldexp(S.A[it - 1], S.E[it - 1]) : 0.0;
+  c.pk = fx_norm_shift(Ak);
+  double B = fabs(bp) * Apr;
+  if constexpr (FAMILY == kFamilySpin) {
+    const double cz = S.scal[0] * sk;
+    const double ch = cz * op.J2;
+    double bsum = 0.0, bmax = 0.0;
+    for (int i = 0; i < op.N; ++i) {
+      const double b = fabs(S.bsite_raw[i] * sk);
+      bsum += b;
+      bmax = fmax(bmax, b);
+    }
+    B += (fabs(cz) * op.maxdz + fabs(ch) * (op.N - 1) + bsum) * Akr;
+    const int Eu = fx_exp_for(B, kFxBits);
+    S.Eu = Eu;
+    const Mant mcz = fx_mant(cz);
+    const int ED = fx_exp_for(fabs(cz) * op.maxdz, 59);
+    c.m_cz = mcz.m;
+    c.s_d = ED - mcz.e - (op.E_dz - 1) - 64;
+    c.s_diag = Eu - (ED - 3) - (Ek - c.pk) - 64;
+    const Mant mh = fx_mant(ch);
+    c.ph = fx_norm_shift((op.N > 1 ? op.N - 1 : 1) * Ak);
+    c.m_hop = mh.m;
+    c.s_hop = Eu - mh.e - (Ek - c.ph) - 64;
+    if (op.uniform) {
+      const Mant mx = fx_mant(S.bsite_raw[0] * sk);
+      c.px = fx_norm_shift(op.N * Ak);
+      c.m_x = mx.m;
+      c.s_x = Eu - mx.e - (Ek - c.px) - 64;
+    } else {
+      const int eb = fx_exp_for(bmax, 62);
+      for (int i = 0; i < op.N; ++i) S.mb[i] = __double2ll_rn(ldexp(S.bsite_raw[i] * sk, -eb));
+      c.s_nu = Eu - eb - (Ek - c.pk) - 64;
+    }
+  } else {
+    for (int o = 0; o < op.nops; ++o) B += fabs(S.scal[o] * sk) * op.maxrow[o] * Akr;
+    const int Eu = fx_exp_for(B, kFxBits);
+    S.Eu = Eu;
+    for (int o = 0; o < op.nops; ++o) {
+      const int Epre = fx_exp_for(op.maxrow[o] * Akr, 62);  // |P_o| < 2^62
+      c.sh_pre[o] = Epre - op.E_op[o] - Ek;
+      const Mant m = fx_mant(S.scal[o] * sk);
+      c.m_op[o] = m.m;
+      c.s_op[o] = Eu - m.e - Epre - 64;
+    }
+  }
+  const Mant mp = fx_mant(-bp);
+  c.pp = it > 1 ? fx_norm_shift(S.A[it - 1]) : 0;
+  c.m_p = mp.m;
+  c.s_p = S.Eu - mp.e - (it > 1 ? S.E[it - 1] - c.pp : 0) - 64;
+  c.use_prev = it > 1;
+}
+
+// Error estimate of iteration k (control warp): err = beta0 beta_k |y_k| with
+// y = exp(-i ts T_k) e_1 left in S.yr/S.yi.
+__device__ double fx_estimate(SmemFx& S, int k, double ts) {
+  small_expm_e1(k, S.alpha + 1, S.beta + 1, ts, S.yr, S.yi, S.tr, S.ti);
+  return S.beta0 * S.beta[k] * hypot(S.yr[k - 1], S.yi[k - 1]);
+}
+
+// ------------------------------------------------------------------ the kernel
+template <int FAMILY, class Op>
+__global__ void __launch_bounds__(544, 1) k_propagate_fx(PropParams p, Op op) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmemFx& S = *reinterpret_cast<SmemFx*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int NW = (int)(blockDim.x >> 5) - 1;   // worker warps
+  const bool ctl = (tid >> 5) == NW;            // control warp
+  const int lane = tid & 31;
+  const bool lead = ctl && lane == 0;
+  const int dim = p.dim;
+  const int G = gridDim.x;
+  const int wstride = G * NW * 32;
+  const int wx0 = blockIdx.x * NW * 32 + tid;  // workers only
+  const int ncoef = 1 + p.nV;
+  unsigned gen = 0;
+  // three partial slots (phase A, phase B, reconstruction): two uses of one
+  // slot are always separated by a grid barrier on another slot
+  long long* partA = reinterpret_cast<long long*>(p.partials);
+  long long* partB = partA + 3 * G;
+  long long* partR = partA + 6 * G;
+  DevStatus* st = p.st;
+  const bool glead = (blockIdx.x == 0) && lead;
+  const bool fixed_k = p.tol <= 0.0;
+  const bool forced = p.f_nsub != nullptr;
+
+  long long fpos = st->forced_pos;
+  long long rpos = st->rec_pos;
+  long long n_app = 0, n_sub = 0;
+  int max_k = 0;
+  double max_err = 0.0;
+
+  auto Q = [&](int i) -> longlong2* { return p.qbasis + (size_t)(i - 1) * dim; };
+
+  // ---------------- psi (complex128) -> q_1
+  // pass 1: max |component| (as ordered bit patterns of |v|) and NaN/Inf detection
+  {
+    if (!ctl) {
+      long long mx = 0;
+      for (int x = wx0; x < dim; x += wstride) {
+        const double2 v = p.psi[x];
+        const long long a = __double_as_longlong(v.x) & 0x7FFFFFFFFFFFFFFFLL;
+        const long long b = __double_as_longlong(v.y) & 0x7FFFFFFFFFFFFFFFLL;
+        mx = max(mx, max(a, b));
+      }
+      fx_worker_partial(S, 0, mx);
+    }
+    __syncthreads();
+    if (ctl) {
+      // the max bit pattern is reduced in the int64 max lane
+      double sum;
+      long long bits;
+      if (!fx_ctl_reduce(S, NW, partA, p.bar, gen, &st->status, p.timeout_ns, sum, bits)) {
+        if (lane == 0) S.abort_flag = 1;
+      } else if (lane == 0) {
+        S.abort_flag = 0;
+        if (bits >= 0x7FF0000000000000LL) {
+          atomicCAS(&st->status, 0, (int)CFET_ENAN);
+          S.abort_flag = 1;
+        } else {
+          S.E[1] = fx_exp_for(__longlong_as_double(bits), kFxBits);
+        }
+      }
+    }
+    __syncthreads();
+    if (S.abort_flag) return;
+    // pass 2: convert and take ||q_1||^2, max |M|
+    if (!ctl) {
+      const double sc = ldexp(1.0, -S.E[1]);
+      __int128 a2 = 0;
+      long long mx = 0;
+      for (int x = wx0; x < dim; x += wstride) {
+        const double2 v = p.psi[x];
+        const longlong2 qv = make_longlong2(__double2ll_rn(v.x * sc), __double2ll_rn(v.y * sc));
+        Q(1)[x] = qv;
+        a2 += (__int128)qv.x * qv.x + (__int128)qv.y * qv.y;
+        mx = max(mx, fx_absmax(qv.x, qv.y));
+      }
+      fx_worker_partial(S, a2, mx);
+    }
+    __syncthreads();
+    if (ctl) {
+      double sum;
+      long long mxi;
+      if (!fx_ctl_reduce(S, NW, partB, p.bar, gen, &st->status, p.timeout_ns, sum, mxi)) {
+        if (lane == 0) S.abort_flag = 1;
+      } else if (lane == 0) {
+        S.beta0 = ldexp(sqrt(sum), S.E[1]);
+        S.A[1] = __ll2double_ru(mxi);
+      }
+    }
+    __syncthreads();
+    if (S.abort_flag) return;
+  }
+
+  for (long long e = 0; e < p.nexp; ++e) {
+    if (tid < ncoef) S.scal[tid] = p.scal[e * ncoef + tid];
+    __syncthreads();
+    if constexpr (FAMILY == kFamilySpin) {
+      if (tid < op.N) {
+        double bi = 0.0;
+        for (int k = 0; k < p.nV; ++k) bi = fma(S.scal[1 + k], __ldg(op.xf + k * op.N + tid), bi);
+        S.bsite_raw[tid] = bi;
+      }
+      __syncthreads();
+    }
+    const long long eg = p.exp_base + e;
+    const bool last_exp = (e == p.nexp - 1);
+    const int nforced = forced ? p.f_nsub[eg] : 0;
+    double remaining = p.tau;
+    int nsub_e = 0;
+    while (true) {
+      if (nsub_e >= p.max_substeps || (forced && nsub_e >= nforced)) {
+        if (glead) atomicCAS(&st->status, 0, (int)CFET_EKRYLOV);
+        return;
+      }
+      int kf = -1, hf = 0;
+      if (forced) {
+        kf = p.f_k[fpos];
+        hf = p.f_h[fpos];
+      }
+      const double beta0 = S.beta0;
+      int acc_k = 0, acc_h = 0;
+      double acc_err = 0.0;
+      if (beta0 != 0.0) {
+        const int klimit = forced ? kf : p.m_max;
+        if (lead) {
+          S.scale[1] = 1.0 / beta0;
+          S.pend = 0;
+          S.stop_prev = 0;
+          S.accept_now = 0;
+          S.y_ready = 0;
+          fx_const_a<FAMILY>(S, op, 1);
+        }
+        __syncthreads();
+        int it = 1;
+        for (;; ++it) {
+          // -------- phase A(it) on the workers; deferred estimate of it-1 on the control warp
+          const int pend = S.pend;
+          if (!ctl) {
+            const FxConstA& c = S.ca;
+            const longlong2* q = Q(it);
+            const longlong2* qm = it > 1 ? Q(it - 1) : q;
+            longlong2* u = Q(it + 1);
+            __int128 a2 = 0;
+            long long mx = 0;
+            for (int x = wx0; x < dim; x += wstride) {
+              longlong2 hv;
+              if constexpr (FAMILY == kFamilySpin) hv = fx_apply_spin(q, qm, x, op, c, S.mb);
+              else hv = fx_apply_dia(q, qm, x, dim, op, c);
+              u[x] = hv;
+              const longlong2 v = q[x];
+              a2 += (__int128)v.x * hv.x + (__int128)v.y * hv.y;
+              mx = max(mx, fx_absmax(hv.x, hv.y));
+            }
+            fx_worker_partial(S, a2, mx);
+          } else if (pend) {
+            const double err = fx_estimate(S, it - 1, remaining);
+            if (lane == 0) {
+              S.err_prev = err;
+              S.stop_prev = err <= p.tol * remaining / p.tau;
+              S.y_ready = S.stop_prev;
+            }
+            __syncwarp();
+          }
+          __syncthreads();
+          if (ctl) {
+            double sum;
+            long long mxi;
+            if (!fx_ctl_reduce(S, NW, partA, p.bar, gen, &st->status, p.timeout_ns, sum, mxi)) {
+              if (lane == 0) S.abort_flag = 1;
+            } else if (lane == 0 && !S.stop_prev) {
+              const double s_it = S.scale[it];
+              const double alpha = ldexp(sum, S.E[it] + S.Eu) * s_it;
+              S.alpha[it] = alpha;
+              // phase-B constants: w = u - alpha s_it q_it
+              const double am = alpha * s_it;
+              const double Bw = ldexp(__ll2double_ru(mxi), S.Eu) + fabs(am) * ldexp(S.A[it], S.E[it]);
+              const int Ew = fx_exp_for(Bw, kFxBits);
+              const Mant ma = fx_mant(-am);
+              const int pk = fx_norm_shift(S.A[it]);
+              S.Ew = Ew;
+              S.sh_u = Ew - S.Eu;
+              S.m_a = ma.m;
+              S.pk_b = pk;
+              S.s_a = Ew - ma.e - (S.E[it] - pk) - 64;
+              if (__ll2double_ru(mxi) >= 1.152921504606846976e18) {  // 2^60: fixed-point range exceeded (not expected)
+                atomicCAS(&st->status, 0, (int)CFET_ENAN);
+                S.abort_flag = 1;
+              }
+            }
+          }
+          __syncthreads();
+          if (S.abort_flag) return;
+          if (S.stop_prev) {  // the deferred estimate accepted it-1
+            it -= 1;
+            acc_err = S.err_prev;
+            break;
+          }
+          // -------- phase B(it): w = u - alpha s_it q_it, beta = ||w||
+          if (!ctl) {
+            const int sh_u = S.sh_u, s_a = S.s_a, pk = S.pk_b;
+            const long long m_a = S.m_a;
+            const longlong2* q = Q(it);
+            longlong2* u = Q(it + 1);
+            __int128 b2 = 0;
+            long long mx = 0;
+            for (int x = wx0; x < dim; x += wstride) {
+              const longlong2 v = q[x];
+              const longlong2 uu = u[x];
+              const long long wr = fx_rshr(uu.x, sh_u) + fx_mul(m_a, v.x << pk, s_a);
+              const long long wi = fx_rshr(uu.y, sh_u) + fx_mul(m_a, v.y << pk, s_a);
+              u[x] = make_longlong2(wr, wi);
+              b2 += (__int128)wr * wr + (__int128)wi * wi;
+              mx = max(mx, fx_absmax(wr, wi));
+            }
+            fx_worker_partial(S, b2, mx);
+          }
+          __syncthreads();
+          if (ctl) {
+            double sum;
+            long long mxi;
+            if (!fx_ctl_reduce(S, NW, partB, p.bar, gen, &st->status, p.timeout_ns, sum, mxi)) {
+              if (lane == 0) S.abort_flag = 1;
+            } else {
+              const double b = ldexp(sqrt(sum), S.Ew);
+              const double prev_b = it > 1 ? S.beta[it - 1] : 0.0;
+              const bool breakdown = b <= 1e-13 * (fabs(S.alpha[it]) + prev_b + 1.0);
+              if (lane == 0) {
+                S.beta[it] = b;
+                S.scale[it + 1] = 1.0 / b;
+                S.E[it + 1] = S.Ew;
+                S.A[it + 1] = __ll2double_ru(mxi);
+              }
+              __syncwarp();
+              int acc_flag = 0, pend_next = 0;
+              double err = 0.0;
+              if (forced) {
+                acc_flag = (it == kf);
+              } else if (fixed_k) {
+                acc_flag = (it == p.m_max) || breakdown;
+              } else if (breakdown) {
+                acc_flag = 1;
+              } else if (it >= p.m_min &&
+                         fabs(remaining) * gersh_width(it, S.alpha + 1, S.beta + 1) <= 2.0 * it) {
+                if (it < klimit) {
+                  pend_next = 1;  // estimate runs during the next apply
+                } else {
+                  err = fx_estimate(S, it, remaining);
+                  acc_flag = err <= p.tol * remaining / p.tau;
+                }
+              }
+              if (lane == 0) {
+                S.accept_now = acc_flag;
+                S.pend = pend_next;
+                S.err_now = err;
+                S.y_ready = acc_flag && !forced && !fixed_k && !breakdown;
+                if (!acc_flag && it < klimit) fx_const_a<FAMILY>(S, op, it + 1);
+              }
+            }
+          }
+          __syncthreads();
+          if (S.abort_flag) return;
+          if (S.accept_now) {
+            acc_err = S.err_now;
+            break;
+          }
+          if (it >= klimit) break;
+        }
+        acc_k = it;
+        const bool accepted = S.accept_now || S.stop_prev;
+        acc_h = 0;
+        if (forced) {
+          acc_h = hf;
+        } else if (!accepted) {
+          // halve the substep on the same basis until the estimate meets the
+          // proportional tolerance (control warp)
+          if (ctl) {
+            int hh = 0;
+            double err = 0.0;
+            const double width = gersh_width(it, S.alpha + 1, S.beta + 1);
+            for (int h = 1; h <= 40; ++h) {
+              const double ts = ldexp(remaining, -h);
+              if (!(fabs(ts) * width <= 2.0 * it)) continue;
+              err = fx_estimate(S, it, ts);
+              if (err <= p.tol * ts / p.tau) { hh = h; break; }
+            }
+            if (lane == 0) { S.acc_h = hh; S.err_now = err; S.y_ready = hh > 0; }
+          }
+          __syncthreads();
+          acc_h = S.acc_h;
+          acc_err = S.err_now;
+          if (acc_h == 0) {
+            if (glead) atomicCAS(&st->status, 0, (int)CFET_EKRYLOV);
+            return;
+          }
+        }
+        n_app += acc_k;
+      }
+      const double ts = ldexp(remaining, -acc_h);
+      const bool final_rec = last_exp && acc_h == 0;
+      if (acc_k > 0) {
+        // -------- reconstruct q_1 <- beta0 sum_i y_i s_i q_i
+        if (ctl) {
+          if (!S.y_ready) small_expm_e1(acc_k, S.alpha + 1, S.beta + 1, ts, S.yr, S.yi, S.tr, S.ti);
+          __syncwarp();
+          double bnd = 0.0;
+          for (int i = lane; i < acc_k; i += 32) {
+            const double f = beta0 * S.scale[i + 1];
+            const double cr = f * S.yr[i], ci = f * S.yi[i];
+            S.yr[i] = cr;
+            S.yi[i] = ci;
+            bnd += (fabs(cr) + fabs(ci)) * ldexp(S.A[i + 1], S.E[i + 1]);
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) bnd += __shfl_xor_sync(0xffffffffu, bnd, o);
+          const int Ep = fx_exp_for(bnd, kFxBits);
+          for (int i = lane; i < acc_k; i += 32) {
+            const Mant mr = fx_mant(S.yr[i]), mi = fx_mant(S.yi[i]);
+            const int pi = fx_norm_shift(S.A[i + 1]);
+            S.crm[i] = mr.m;
+            S.cim[i] = mi.m;
+            S.cp[i] = pi;
+            S.csr[i] = Ep - mr.e - (S.E[i + 1] - pi) - 64;
+            S.csi[i] = Ep - mi.e - (S.E[i + 1] - pi) - 64;
+          }
+          if (lane == 0) S.Epsi = Ep;
+        }
+        __syncthreads();
+        if (!ctl) {
+          const double outscale = ldexp(1.0, S.Epsi);
+          __int128 a2 = 0;
+          long long mx = 0;
+          for (int x = wx0; x < dim; x += wstride) {
+            long long re = 0, im = 0;
+            for (int i = 0; i < acc_k; ++i) {
+              const longlong2 v = Q(i + 1)[x];
+              const int pi = S.cp[i], sr = S.csr[i], si = S.csi[i];
+              const long long cr = S.crm[i], ci = S.cim[i];
+              const long long vr = v.x << pi, vi = v.y << pi;
+              re += fx_mul(cr, vr, sr) - fx_mul(ci, vi, si);
+              im += fx_mul(cr, vi, sr) + fx_mul(ci, vr, si);
+            }
+            Q(1)[x] = make_longlong2(re, im);
+            if (final_rec) p.psi[x] = make_double2(__ll2double_rn(re) * outscale, __ll2double_rn(im) * outscale);
+            a2 += (__int128)re * re + (__int128)im * im;
+            mx = max(mx, fx_absmax(re, im));
+          }
+          fx_worker_partial(S, a2, mx);
+        }
+        __syncthreads();
+        if (ctl) {
+          double sum;
+          long long mxi;
+          if (!fx_ctl_reduce(S, NW, partR, p.bar, gen, &st->status, p.timeout_ns, sum, mxi)) {
+            if (lane == 0) S.abort_flag = 1;
+          } else if (lane == 0) {
+            S.beta0 = ldexp(sqrt(sum), S.Epsi);
+            S.E[1] = S.Epsi;
+            S.A[1] = __ll2double_ru(mxi);
+          }
+        }
+        __syncthreads();
+        if (S.abort_flag) return;
+      }
+      if (glead && p.r_k != nullptr) {
+        if (rpos < p.r_cap) {
+          p.r_k[rpos] = acc_k;
+          p.r_h[rpos] = acc_h;
+        } else {
+          st->rec_overflow = 1;
+        }
+      }
+      rpos += 1;
+      if (forced) fpos += 1;
+      n_sub += 1;
+      nsub_e += 1;
+      if (acc_k > max_k) max_k = acc_k;
+      if (acc_err > max_err) max_err = acc_err;
+      if (acc_h == 0) break;
+      remaining -= ts;
+    }
+    if (glead && p.r_nsub != nullptr) p.r_nsub[eg] = nsub_e;
+  }
+  if (glead) {
+    st->forced_pos = fpos;
+    st->rec_pos = rpos;
+    st->n_exp += p.nexp;
+    st->n_sub += n_sub;
+    st->n_app += n_app;
+    if (max_k > st->max_k) st->max_k = max_k;
+    if (max_err > st->max_err) st->max_err = max_err;
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+template <int FAMILY, class Op>
+static int launch_prop_fx(const PropParams& p, const Op& op, int grid, int block, void* stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = sizeof(SmemFx);
+  cfg.stream = (cudaStream_t)stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return (int)cudaLaunchKernelEx(&cfg, k_propagate_fx<FAMILY, Op>, p, op);
+}
+
+int launch_propagate_spin_fx(const PropParams& p, const OpSpinFx& op, int grid, int block, void* stream) {
+  return launch_prop_fx<kFamilySpin>(p, op, grid, block, stream);
+}
+int launch_propagate_dia_fx(const PropParams& p, const OpDiaFx& op, int grid, int block, void* stream) {
+  return launch_prop_fx<kFamilyDia>(p, op, grid, block, stream);
+}
+
+int max_coresident_blocks_fx(int family, int block) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e;
+  if (family == kFamilySpin)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_fx<kFamilySpin, OpSpinFx>, block,
+                                                      sizeof(SmemFx));
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_fx<kFamilyDia, OpDiaFx>, block,
+                                                      sizeof(SmemFx));
+  if (e != cudaSuccess) return -1;
+  return per * nsm;
+}
+
+}  // namespace cfet

@@ -40,7 +40,7 @@ constexpr size_t kOffH = kOffDzHi + align256(sizeof(double) * (1 << (kStaticMaxS
 constexpr size_t kOffXf = kOffH + align256(sizeof(double) * kStaticMaxSites);
 constexpr size_t kOffScal = kOffXf + align256(sizeof(double) * kStaticMaxSites);
 constexpr size_t kOffPart = kOffScal + align256(sizeof(double) * 2);
-constexpr size_t kOffBar = kOffPart + align256(sizeof(double) * 2 * kStaticMaxGrid);
+constexpr size_t kOffBar = kOffPart + align256(sizeof(double) * 3 * kStaticMaxGrid);
 constexpr size_t kOffSt = kOffBar + align256(sizeof(unsigned) * 2);
 constexpr size_t kStaticBytes = kOffSt + align256(sizeof(DevStatus));
 

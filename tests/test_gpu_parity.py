@@ -39,6 +39,9 @@ def _host(t):
     return t.cpu().numpy()
 
 
+PRECS = ["fx", "f64"]
+
+
 def _spin(torch, N, nfields=1, J=1.0, Delta=0.5, seed=1, **kw):
     import paper_1102_5071_gb300 as P
     pr = W.spin_chain(N, J=J, Delta=Delta, h_seed=seed)
@@ -98,10 +101,11 @@ def test_apply_dia(torch_cuda, Nr, L):
 
 # ---------------------------------------------------------------- expv (a5-a7)
 @pytest.mark.parametrize("tau,tol,m", [(0.02, 1e-12, 16), (0.3, 1e-12, 24), (1.5, 1e-10, 12), (0.05, 0.0, 10)])
-def test_expv_spin(torch_cuda, tau, tol, m):
+@pytest.mark.parametrize("prec", PRECS)
+def test_expv_spin(torch_cuda, tau, tol, m, prec):
     torch = torch_cuda
     N = 10
-    prop, op, _, _ = _spin(torch, N, m_max=m, max_substeps=200)
+    prop, op, _, _ = _spin(torch, N, m_max=m, max_substeps=200, precision=prec)
     psi0 = W.random_state(3, 1 << N)
     c = np.array([0.7, 0.45])
     t = _dev(torch, psi0)
@@ -125,11 +129,12 @@ def _parity_run(prop, op, drives, psi0, t0, dt, nsteps, scheme_or_order, tol, m,
     return forced_err, adaptive_err, log, log2, stats, stats2, na
 
 
-def test_propagate_chain_n8_full_run(torch_cuda):
+@pytest.mark.parametrize("prec", PRECS)
+def test_propagate_chain_n8_full_run(torch_cuda, prec):
     # driven XXZ chain N = 8, Neel state, CF4:2, dt = 0.01, T = 10, m <= 16, tol 1e-12
     torch = torch_cuda
     cfg = W.CHAIN_SMALL
-    prop, op, drives, _ = _spin(torch, cfg["N"], m_max=cfg["m_max"], max_substeps=200)
+    prop, op, drives, _ = _spin(torch, cfg["N"], m_max=cfg["m_max"], max_substeps=200, precision=prec)
     psi0 = W.neel_state(cfg["N"])
     nsteps = int(round(cfg["T"] / cfg["dt"]))
     fe, ae, log, log2, st, st2, na = _parity_run(prop, op, drives, psi0, 0.0, cfg["dt"], nsteps, 4, cfg["tol"],
@@ -143,31 +148,34 @@ def test_propagate_chain_n8_full_run(torch_cuda):
 
 @pytest.mark.parametrize("scheme", ["CF2:1", "CF4:2", "CF4:3", "CF4:3Opt", "CF6:4", "CF6:5", "CF6:5b", "CF6:6",
                                     "CF6:5Imp", "CF6:5Opt", "CF6:6Opt", "CF8:11"])
-def test_propagate_every_scheme(torch_cuda, scheme):
+@pytest.mark.parametrize("prec", PRECS)
+def test_propagate_every_scheme(torch_cuda, scheme, prec):
     torch = torch_cuda
     N = 9
-    prop, op, drives, _ = _spin(torch, N, nfields=2, m_max=20, max_substeps=200)
+    prop, op, drives, _ = _spin(torch, N, nfields=2, m_max=20, max_substeps=200, precision=prec)
     psi0 = W.random_state(5, 1 << N)
     fe, ae, log, log2, *_ = _parity_run(prop, op, drives, psi0, 0.37, 0.05, 6, scheme, 1e-11, 20, torch)
     assert fe <= PARITY and ae <= PARITY, (fe, ae)
 
 
-def test_propagate_with_substeps(torch_cuda):
+@pytest.mark.parametrize("prec", PRECS)
+def test_propagate_with_substeps(torch_cuda, prec):
     # large dt and a small Krylov space force substepping (h > 0 records)
     torch = torch_cuda
     N = 10
-    prop, op, drives, _ = _spin(torch, N, m_max=8, max_substeps=400)
+    prop, op, drives, _ = _spin(torch, N, m_max=8, max_substeps=400, precision=prec)
     psi0 = W.random_state(6, 1 << N)
     fe, ae, log, log2, *_ = _parity_run(prop, op, drives, psi0, 0.0, 0.6, 3, 6, 1e-10, 8, torch)
     assert any(h > 0 for lg in log for _, h in lg)
     assert fe <= PARITY and ae <= PARITY, (fe, ae)
 
 
-def test_propagate_fixed_krylov_dimension(torch_cuda):
+@pytest.mark.parametrize("prec", PRECS)
+def test_propagate_fixed_krylov_dimension(torch_cuda, prec):
     # tol <= 0: fixed K = m_max (the paper's K-vector runs)
     torch = torch_cuda
     N = 10
-    prop, op, drives, _ = _spin(torch, N, m_max=10)
+    prop, op, drives, _ = _spin(torch, N, m_max=10, precision=prec)
     psi0 = W.random_state(8, 1 << N)
     ref = OC.propagate(op, psi0, 0.0, 0.02, 15, 6, drives, 0.0, 10)
     t = _dev(torch, psi0)
@@ -176,10 +184,11 @@ def test_propagate_fixed_krylov_dimension(torch_cuda):
     assert st["n_applies"] == 15 * 5 * 10
 
 
-def test_propagate_chain_n20_one_step(torch_cuda):
+@pytest.mark.parametrize("prec", PRECS)
+def test_propagate_chain_n20_one_step(torch_cuda, prec):
     # full-size chain (dim 2^20), one CF4:2 step at dt = 0.05, fixed K = 10
     torch = torch_cuda
-    prop, op, drives, pr = _spin(torch, 20, m_max=10)
+    prop, op, drives, pr = _spin(torch, 20, m_max=10, precision=prec)
     psi0 = W.random_state(2, 1 << 20)
     ref = OC.propagate(op, psi0, 0.0, 0.05, 1, 4, drives, 0.0, 10)
     t = _dev(torch, psi0)
@@ -187,13 +196,14 @@ def test_propagate_chain_n20_one_step(torch_cuda):
     assert np.linalg.norm(_host(t) - ref) <= PARITY
 
 
-def test_chain_n20_zero_coupling_factorises(torch_cuda):
+@pytest.mark.parametrize("prec", PRECS)
+def test_chain_n20_zero_coupling_factorises(torch_cuda, prec):
     # J = 0: exact product of single-spin CFET results at full size (any-size property)
     torch = torch_cuda
     import paper_1102_5071_gb300 as P
     N = 20
     pr = W.spin_chain(N, J=0.0, Delta=0.0, A=1.3, omega=1.7)
-    prop = P.Propagator(P.XXZChain(N, 0.0, 0.0, pr.h), [P.XField(N, pr.xfield)], [pr.drive], m_max=16)
+    prop = P.Propagator(P.XXZChain(N, 0.0, 0.0, pr.h), [P.XField(N, pr.xfield)], [pr.drive], m_max=16, precision=prec)
     psi0 = W.neel_state(N)
     nsteps, dt = 40, 0.05
     t = _dev(torch, psi0)
@@ -214,13 +224,14 @@ def test_chain_n20_zero_coupling_factorises(torch_cuda):
     assert abs(np.linalg.norm(out) - 1.0) < 1e-12
 
 
-def test_time_independent_matches_expm(torch_cuda):
+@pytest.mark.parametrize("prec", PRECS)
+def test_time_independent_matches_expm(torch_cuda, prec):
     torch = torch_cuda
     from scipy.linalg import expm
     import paper_1102_5071_gb300 as P
     N = 9
     pr = W.spin_chain(N)
-    prop = P.Propagator(P.XXZChain(N, pr.J, pr.Delta, pr.h), [P.XField(N, pr.xfield)], [lambda t: 0.0], m_max=30)
+    prop = P.Propagator(P.XXZChain(N, pr.J, pr.Delta, pr.h), [P.XField(N, pr.xfield)], [lambda t: 0.0], m_max=30, precision=prec)
     psi0 = W.random_state(4, 1 << N)
     t = _dev(torch, psi0)
     prop.propagate(t, 0.0, 0.1, 5, order=8, tol=1e-13)
@@ -229,19 +240,21 @@ def test_time_independent_matches_expm(torch_cuda):
 
 
 @pytest.mark.parametrize("Nr,L,nsteps,t0", [(120, 8, 3, 300.0)])
-def test_propagate_atom_reduced(torch_cuda, Nr, L, nsteps, t0):
+@pytest.mark.parametrize("prec", PRECS)
+def test_propagate_atom_reduced(torch_cuda, Nr, L, nsteps, t0, prec):
     torch = torch_cuda
-    prop, op, drives, p = _atom(torch, Nr, L, m_max=32, max_substeps=4000)
+    prop, op, drives, p = _atom(torch, Nr, L, m_max=32, max_substeps=4000, precision=prec)
     psi0, _ = W.atom_ground_state(p)
     fe, ae, log, log2, *_ = _parity_run(prop, op, drives, psi0, t0, 0.1, nsteps, 8, 1e-10, 32, torch)
     assert fe <= PARITY and ae <= PARITY, (fe, ae)
 
 
 # ---------------------------------------------------------------- edge cases
-def test_edge_cases(torch_cuda):
+@pytest.mark.parametrize("prec", PRECS)
+def test_edge_cases(torch_cuda, prec):
     torch = torch_cuda
     import paper_1102_5071_gb300 as P
-    prop, op, drives, _ = _spin(torch, 6)
+    prop, op, drives, _ = _spin(torch, 6, precision=prec)
     psi0 = W.random_state(1, 64)
     t = _dev(torch, psi0)
     st = prop.propagate(t, 0.0, 0.1, 0, order=4)                 # nsteps = 0: no-op
@@ -261,25 +274,27 @@ def test_edge_cases(torch_cuda):
     t = _dev(torch, psi0)
     prop.propagate(t, 0.0, 0.1, 1, order=4)
     # a spin chain of one site (dim 2)
-    prop1, op1, dr1, _ = _spin(torch, 1)
+    prop1, op1, dr1, _ = _spin(torch, 1, precision=prec)
     e = _dev(torch, np.array([0.6, 0.8j]))
     prop1.propagate(e, 0.0, 0.05, 10, order=8, tol=1e-13)
     ref = OC.propagate(op1, np.array([0.6, 0.8j]), 0.0, 0.05, 10, 8, dr1, 1e-13, 16)
     assert np.linalg.norm(_host(e) - ref) < PARITY
 
 
-def test_substep_cap_reports_ekrylov(torch_cuda):
+@pytest.mark.parametrize("prec", PRECS)
+def test_substep_cap_reports_ekrylov(torch_cuda, prec):
     torch = torch_cuda
     import paper_1102_5071_gb300 as P
-    prop, op, drives, _ = _spin(torch, 8, m_max=4, max_substeps=2)
+    prop, op, drives, _ = _spin(torch, 8, m_max=4, max_substeps=2, precision=prec)
     t = _dev(torch, W.random_state(2, 256))
     with pytest.raises(P.CfetError, match="EKRYLOV"):
         prop.propagate(t, 0.0, 2.0, 1, order=4, tol=1e-12)
 
 
-def test_e2e_host_entry_matches_device_entry(torch_cuda):
+@pytest.mark.parametrize("prec", PRECS)
+def test_e2e_host_entry_matches_device_entry(torch_cuda, prec):
     torch = torch_cuda
-    prop, op, drives, _ = _spin(torch, 12)
+    prop, op, drives, _ = _spin(torch, 12, precision=prec)
     psi0 = W.random_state(3, 1 << 12)
     t = _dev(torch, psi0)
     prop.propagate(t, 0.0, 0.02, 5, order=6, tol=1e-10)
