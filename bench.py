@@ -212,7 +212,7 @@ def run_gpu(args):
     pr, psi0 = problem()
     dim = 1 << N_SITES
     prop = P.Propagator(P.XXZChain(N_SITES, pr.J, pr.Delta, pr.h), [P.XField(N_SITES, pr.xfield)], [pr.drive],
-                        m_max=M_MAX, max_substeps=64, precision=args.precision)
+                        m_max=M_MAX, max_substeps=64, precision=args.precision, block_size=args.block_size)
     psi = torch.from_numpy(psi0).cuda()
     t0 = 0.0
     # warm-up steps (untimed)
@@ -314,7 +314,13 @@ def run_gpu(args):
             "data": "synthetic", "config": dict(workload_config(), precision=args.precision),
             "cfet_steps_per_s": args.steps * ws / (ms_max * 1e-3),
             "krylov": {"applies_per_step": n_app / args.steps, "substeps": stats["n_substeps"],
-                       "max_k": stats["max_k"], "max_err_est": stats["max_err_est"]},
+                       "max_k": stats["max_k"], "max_err_est": stats["max_err_est"],
+                       "phase_ms": {k: v * 1e-6 for k, v in zip(
+                           ("apply", "apply_reduce", "orth", "orth_reduce_decide", "reconstruct",
+                            "reconstruct_reduce"), stats.get("phase_ns", [0] * 6))},
+                       "phase_max_ms": {k: v * 1e-6 for k, v in zip(
+                           ("apply", "apply_reduce", "orth", "orth_reduce_decide", "reconstruct",
+                            "reconstruct_reduce"), stats.get("phase_max_ns", [0] * 6))}},
             "roofline": roofline,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 16 * dim, "d2h_bytes_per_step": 16 * dim,
                     "steps": e2e_steps},
@@ -403,6 +409,8 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="accuracy study: final-state error and throughput per (order, dt) over T")
     ap.add_argument("--sweep-T", type=float, default=20.0)
+    ap.add_argument("--block-size", type=int, default=0,
+                    help="threads per CTA of the FP64 kernel; the fixed-point kernel uses 2x this many workers + 1 control warp")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

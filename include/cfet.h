@@ -136,7 +136,9 @@ typedef struct cfet_options {
   int32_t m_max;             /* Krylov dimension limit (default 16, <= 64)    */
   int32_t m_min;             /* first dimension tested (default 2, >= 1)      */
   int32_t max_substeps;      /* per stage exponential (default 64)            */
-  int32_t block_size;        /* threads per CTA (0 = 256; multiple of 32)     */
+  int32_t block_size;        /* 0 = auto; FP64 kernel: threads per CTA (256);
+                                fixed-point kernel: 2 x block_size worker
+                                threads + one control warp (384 -> 800)      */
   int32_t grid_size;         /* CTAs of the persistent kernel (0 = auto,
                                 capped at the co-resident maximum)            */
   int32_t steps_per_launch;  /* CFET steps per persistent launch (0 = 256)    */
@@ -162,6 +164,15 @@ typedef struct cfet_stats {
   int32_t max_k;             /* largest Krylov dimension used                 */
   int32_t status;            /* device status word (a cfet_status)            */
   double max_err_est;        /* largest accepted error estimate               */
+  /* Trace of the fixed-point kernel, SM clock cycles per CTA (mean over CTAs
+   * in phase_ns, largest CTA in phase_max_ns; zero for the FP64 kernel):
+   * [0] worker loops of the apply passes, [1] control-warp work after them
+   * (reduction, scalar constants; barrier wait excluded), [2] worker loops of
+   * the orthogonalisation passes, [3] control work after them (reduction,
+   * error estimate, decisions, constants), [4] worker loops of the
+   * reconstructions, [5] time spent waiting in grid barriers.              */
+  int64_t phase_ns[6];
+  int64_t phase_max_ns[6];
 } cfet_stats;
 
 /* Per-exponential Krylov decisions, host arrays owned by the caller.  One

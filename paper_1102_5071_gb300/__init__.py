@@ -110,7 +110,7 @@ def _check_vec(t, dim, name):
 class Propagator:
     """CFET propagator for H(t) = H0 + sum_k f_k(t) V_k on the current CUDA device."""
 
-    def __init__(self, H0, V=(), drives=(), *, m_max=16, m_min=2, max_substeps=64, block_size=256,
+    def __init__(self, H0, V=(), drives=(), *, m_max=16, m_min=2, max_substeps=64, block_size=0,
                  grid_size=0, steps_per_launch=256, barrier_timeout_s=2.0, precision="default"):
         lib = _capi.load()
         V = list(V)

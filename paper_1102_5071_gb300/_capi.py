@@ -38,11 +38,14 @@ PRECISIONS = {"default": CFET_PREC_DEFAULT, "f64": CFET_PREC_F64, "fx": CFET_PRE
 
 class cfet_stats(C.Structure):
     _fields_ = [("n_exp", C.c_int64), ("n_substeps", C.c_int64), ("n_applies", C.c_int64),
-                ("max_k", C.c_int32), ("status", C.c_int32), ("max_err_est", C.c_double)]
+                ("max_k", C.c_int32), ("status", C.c_int32), ("max_err_est", C.c_double),
+                ("phase_ns", C.c_int64 * 6), ("phase_max_ns", C.c_int64 * 6)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
-
+        d = {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("phase")}
+        d["phase_ns"] = list(self.phase_ns)
+        d["phase_max_ns"] = list(self.phase_max_ns)
+        return d
 
 class cfet_decisions(C.Structure):
     _fields_ = [("n_exp", C.c_int64), ("n_sub", c_int32_p), ("k", c_int32_p), ("h", c_int32_p),

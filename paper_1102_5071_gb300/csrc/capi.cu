@@ -160,6 +160,10 @@ void fill_stats(const DevStatus& s, cfet_stats* out) {
   out->max_k = s.max_k;
   out->status = s.status;
   out->max_err_est = s.max_err;
+  for (int i = 0; i < 6; ++i) {
+    out->phase_ns[i] = s.n_exp > 0 && s.phase_ns[i] > 0 ? s.phase_ns[i] : 0;
+    out->phase_max_ns[i] = s.phase_max_ns[i];
+  }
 }
 
 // One persistent launch over exponentials [e0, e0 + ne).
@@ -238,7 +242,7 @@ void cfet_options_default(cfet_options* opt) {
   opt->m_max = 16;
   opt->m_min = 2;
   opt->max_substeps = 64;
-  opt->block_size = 256;
+  opt->block_size = 0;
   opt->grid_size = 0;
   opt->steps_per_launch = 256;
   opt->barrier_timeout_s = 2.0;
@@ -289,16 +293,22 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
   if (o.m_max < 1 || o.m_max > kMaxKrylov) return fail(nullptr, CFET_EINVAL, "m_max must be in [1, 64]");
   if (o.m_min < 1 || o.m_min > o.m_max) return fail(nullptr, CFET_EINVAL, "m_min must be in [1, m_max]");
   if (o.max_substeps < 1) return fail(nullptr, CFET_EINVAL, "max_substeps must be >= 1");
-  if (o.block_size == 0) o.block_size = 256;
-  if (o.block_size < 32 || o.block_size > 256 || o.block_size % 32)
-    return fail(nullptr, CFET_EINVAL, "block_size must be a multiple of 32 in [32, 256]");
+  if (o.precision == CFET_PREC_DEFAULT) o.precision = CFET_PREC_FX;
+  if (o.precision != CFET_PREC_F64 && o.precision != CFET_PREC_FX)
+    return fail(nullptr, CFET_EINVAL, "precision must be CFET_PREC_F64 or CFET_PREC_FX");
+  if (o.block_size == 0) o.block_size = (o.precision == CFET_PREC_F64) ? 256 : 384;
+  {
+    // FP64 kernel: block_size threads (<= 256); fixed-point kernel:
+    // 2 * block_size workers + one control warp (<= 1024 threads)
+    const int lim = (o.precision == CFET_PREC_F64) ? 256 : 480;
+    if (o.block_size < 32 || o.block_size > lim || o.block_size % 32)
+      return fail(nullptr, CFET_EINVAL, "block_size must be a multiple of 32 in [32, 256] (FP64) or [32, 480]");
+  }
   if (o.grid_size < 0) return fail(nullptr, CFET_EINVAL, "grid_size must be >= 0");
   if (o.steps_per_launch <= 0) o.steps_per_launch = 256;
   if (!(o.barrier_timeout_s > 0.0) || !is_finite_d(o.barrier_timeout_s))
     return fail(nullptr, CFET_EINVAL, "barrier_timeout_s must be positive");
-  if (o.precision == CFET_PREC_DEFAULT) o.precision = CFET_PREC_FX;
-  if (o.precision != CFET_PREC_F64 && o.precision != CFET_PREC_FX)
-    return fail(nullptr, CFET_EINVAL, "precision must be CFET_PREC_F64 or CFET_PREC_FX");
+
 
   int family = 0, dim = 0, nsites = 0;
   if (H0->kind == CFET_OP_XXZ_CHAIN) {

@@ -14,7 +14,7 @@ namespace cfet {
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ long long global_timer_ns() {
   long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t) : : "memory");
   return t;
 }
 

@@ -40,6 +40,12 @@
 namespace cfet {
 
 // ------------------------------------------------------------------ fixed-point helpers
+// SM cycle counter, ordered with respect to surrounding memory operations.
+__device__ __forceinline__ long long fx_clk() {
+  long long t;
+  asm volatile("mov.u64 %0, %%clock64;" : "=l"(t) : : "memory");
+  return t;
+}
 constexpr int kFxBits = 57;  // stored |M| < 2^57
 // Per-thread exact 128-bit sums of products (< 2^115 each, at most 4096 per
 // thread) are shifted right by kRedShift before the CTA and grid reductions,
@@ -47,19 +53,35 @@ constexpr int kFxBits = 57;  // stored |M| < 2^57
 // below 2^-68 of any non-zero sum of squares.
 constexpr int kRedShift = 24;
 
+// The scalar bookkeeping below uses integer operations on the bit patterns of
+// positive normal doubles (the FP64 units run at 1/64 rate).
 __device__ __forceinline__ int fx_ilog2(double v) {  // floor(log2 v), v > 0 normal
   return (int)((__double_as_longlong(v) >> 52) & 0x7ff) - 1023;
+}
+// floor(log2(v (1 + eps))) for a tiny eps > 0: values within 2^-40 below a power
+// of two count as that power (a safety margin for bounds computed in FP64).
+__device__ __forceinline__ int fx_ilog2_up(double v) {
+  const long long b = __double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  return ((b & 0xFFFFFFFFFFFFFLL) >= 0xFFFFFFFFFF000LL) ? e + 1 : e;
 }
 // Exponent E with bound < 2^(bits + E); a zero bound gives a very small E.
 __device__ __forceinline__ int fx_exp_for(double bound, int bits) {
   if (!(bound > 1e-290) || !(bound < 1e290)) return -960;
-  return fx_ilog2(bound * (1.0 + 1e-12)) - (bits - 1);
+  return fx_ilog2_up(bound) - (bits - 1);
 }
 // Left shift that brings a value of magnitude <= a (a >= 1) to < 2^62.
 __device__ __forceinline__ int fx_norm_shift(double a) {
   if (!(a >= 1.0)) return 0;
-  const int p = 61 - fx_ilog2(a * (1.0 + 1e-12));
+  const int p = 61 - fx_ilog2_up(a);
   return p < 0 ? 0 : (p > 61 ? 61 : p);
+}
+// x * 2^e exactly, by exponent arithmetic when the result stays normal.
+__device__ __forceinline__ double fx_scale2(double x, int e) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex == 0 || ex + e <= 0 || ex + e >= 2047) return ldexp(x, e);
+  return __longlong_as_double(b + ((long long)e << 52));
 }
 
 // Exact decomposition v = m * 2^e with |m| in [2^61, 2^62) (m = 0 for 0).
@@ -86,8 +108,27 @@ __device__ __forceinline__ long long fx_rshr(long long h, int s) {
   return (h + (1LL << (s - 1))) >> s;
 }
 // round(m * x * 2^-(64 + s)); |m|, |x| < 2^62.
+// High 64 bits of m * x from three 32x32 partial products (the dropped low
+// partial product changes the result by at most 2 units).
+__device__ __forceinline__ long long fx_mulhi(long long m, long long x) {
+  const int mh = (int)(m >> 32), xh = (int)(x >> 32);
+  const unsigned ml = (unsigned)m, xl = (unsigned)x;
+  // 32 x 32 -> 64-bit partial products; |mid| < 2^63 for |m|, |x| < 2^62
+  const long long mid = (long long)mh * (long long)xl + (long long)xh * (long long)ml;
+  return (long long)mh * (long long)xh + (mid >> 32);
+}
 __device__ __forceinline__ long long fx_mul(long long m, long long x, int s) {
-  return fx_rshr(__mul64hi(m, x), s);
+  return fx_rshr(fx_mulhi(m, x), s);
+}
+// Scalar mantissa with the product shift folded in: fx_mulhi(fx_fold(m, s), x)
+// ~= fx_mul(m, x, s).  For s <= 9 the fold is exact (the mantissa of a double
+// uses 53 of its 62 bits); for larger s the term is at most 2^-s of the result
+// bound and the dropped bits stay below 2^-62 of it.  s < 0 does not occur for
+// non-zero terms (the result bound covers every term); it is clamped.
+__device__ __forceinline__ long long fx_fold(long long m, int s) {
+  if (s <= 0) return m;
+  if (s >= 63) return 0;
+  return (m + (1LL << (s - 1))) >> s;
 }
 // p * 2^-sh as int64 (truncated); callers guarantee the result fits.
 __device__ __forceinline__ long long fx_shr128(__int128 p, int sh) {
@@ -117,7 +158,7 @@ __device__ __forceinline__ void fx_warp_reduce(unsigned long long& lo, long long
 }
 __device__ __forceinline__ double fx_i128_to_double(unsigned long long lo, long long hi) {
   // (hi * 2^64 + lo) * 2^kRedShift
-  return ldexp(fma(__ll2double_rn(hi), 18446744073709551616.0, __ull2double_rn(lo)), kRedShift);
+  return fma(__ll2double_rn(hi), 18446744073709551616.0, __ull2double_rn(lo)) * (double)(1 << kRedShift);
 }
 
 // ------------------------------------------------------------------ shared state
@@ -175,23 +216,23 @@ __device__ __forceinline__ longlong2 fx_apply_spin(const longlong2* q, const lon
                                                    const OpSpinFx& op, const FxConstA& c, const long long* mb) {
   const int N = op.N, L = op.lo_bits;
   const long long dz = __ldg(op.DZ_lo + (x & ((1 << L) - 1))) + __ldg(op.DZ_hi + (x >> (L - 1)));
-  const long long D = fx_mul(c.m_cz, dz << 1, c.s_d);  // |D| < 2^59
-  const long long Dp = D << 3;
+  // D = c0 s_k dz(x) 2^-s_diag (m_cz carries both shifts), then D * q_k[x]
+  const long long Dp = fx_mulhi(c.m_cz, dz << 1) << 3;
   const longlong2 v = q[x];
-  long long ur = fx_mul(Dp, v.x << c.pk, c.s_diag);
-  long long ui = fx_mul(Dp, v.y << c.pk, c.s_diag);
+  long long ur = fx_mulhi(Dp, v.x << c.pk);
+  long long ui = fx_mulhi(Dp, v.y << c.pk);
   long long hr = 0, hi = 0;
   const unsigned anti = ((unsigned)x ^ ((unsigned)x >> 1)) & ((1u << (N - 1)) - 1u);
 #pragma unroll 4
-  for (int i = 0; i < N - 1; ++i) {
+  for (int i = 0; i < N - 1; ++i) {  // antiparallel bonds only (predicated)
     if ((anti >> i) & 1u) {
       const longlong2 w = q[x ^ (3 << i)];
       hr += w.x;
       hi += w.y;
     }
   }
-  ur += fx_mul(c.m_hop, hr << c.ph, c.s_hop);
-  ui += fx_mul(c.m_hop, hi << c.ph, c.s_hop);
+  ur += fx_mulhi(c.m_hop, hr << c.ph);
+  ui += fx_mulhi(c.m_hop, hi << c.ph);
   if (op.uniform) {
     long long xr = 0, xi = 0;
 #pragma unroll 4
@@ -200,20 +241,20 @@ __device__ __forceinline__ longlong2 fx_apply_spin(const longlong2* q, const lon
       xr += w.x;
       xi += w.y;
     }
-    ur += fx_mul(c.m_x, xr << c.px, c.s_x);
-    ui += fx_mul(c.m_x, xi << c.px, c.s_x);
+    ur += fx_mulhi(c.m_x, xr << c.px);
+    ui += fx_mulhi(c.m_x, xi << c.px);
   } else {
 #pragma unroll 4
     for (int i = 0; i < N; ++i) {
       const longlong2 w = q[x ^ (1 << i)];
-      ur += fx_mul(mb[i], w.x << c.pk, c.s_nu);
-      ui += fx_mul(mb[i], w.y << c.pk, c.s_nu);
+      ur += fx_mulhi(mb[i], w.x << c.pk);
+      ui += fx_mulhi(mb[i], w.y << c.pk);
     }
   }
   if (c.use_prev) {
     const longlong2 w = qm[x];
-    ur += fx_mul(c.m_p, w.x << c.pp, c.s_p);
-    ui += fx_mul(c.m_p, w.y << c.pp, c.s_p);
+    ur += fx_mulhi(c.m_p, w.x << c.pp);
+    ui += fx_mulhi(c.m_p, w.y << c.pp);
   }
   return make_longlong2(ur, ui);
 }
@@ -233,23 +274,24 @@ __device__ __forceinline__ longlong2 fx_apply_dia(const longlong2* q, const long
         ai += (__int128)a * w.y;
       }
     }
-    ur += fx_mul(c.m_op[o], fx_shr128(ar, c.sh_pre[o]), c.s_op[o]);
-    ui += fx_mul(c.m_op[o], fx_shr128(ai, c.sh_pre[o]), c.s_op[o]);
+    ur += fx_mulhi(c.m_op[o], fx_shr128(ar, c.sh_pre[o]));
+    ui += fx_mulhi(c.m_op[o], fx_shr128(ai, c.sh_pre[o]));
   }
   if (c.use_prev) {
     const longlong2 w = qm[r];
-    ur += fx_mul(c.m_p, w.x << c.pp, c.s_p);
-    ui += fx_mul(c.m_p, w.y << c.pp, c.s_p);
+    ur += fx_mulhi(c.m_p, w.x << c.pp);
+    ui += fx_mulhi(c.m_p, w.y << c.pp);
   }
   return make_longlong2(ur, ui);
 }
 
 // ------------------------------------------------------------------ control-warp helpers
 // Bounded grid barrier executed by the control warp only (lane 0 spins).
-__device__ bool fx_ctl_barrier(unsigned* bar, unsigned& gen, int* status, long long timeout_ns) {
+__device__ bool fx_ctl_barrier(unsigned* bar, unsigned& gen, int* status, long long timeout_ns, long long& spin) {
   const int lane = threadIdx.x & 31;
   int ok = 1;
   if (gridDim.x > 1 && lane == 0) {
+    const long long c0 = fx_clk();
     const unsigned target = gen + 1;
     __threadfence();
     const unsigned arrived = atomicAdd(&bar[0], 1u) + 1u;
@@ -269,10 +311,10 @@ __device__ bool fx_ctl_barrier(unsigned* bar, unsigned& gen, int* status, long l
             break;
           }
         }
-        __nanosleep(32);
       }
     }
     __threadfence();
+    spin += fx_clk() - c0;
   }
   gen += 1;
   ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -283,7 +325,7 @@ __device__ bool fx_ctl_barrier(unsigned* bar, unsigned& gen, int* status, long l
 // (slot `part`), pass the grid barrier, and return the exact global sum (as
 // FP64) and the global max to all lanes.
 __device__ bool fx_ctl_reduce(SmemFx& S, int NW, long long* part, unsigned* bar, unsigned& gen, int* status,
-                              long long timeout_ns, double& sum, long long& mxi) {
+                              long long timeout_ns, double& sum, long long& mxi, long long& spin) {
   const int lane = threadIdx.x & 31;
   const int G = gridDim.x;
   unsigned long long lo = 0;
@@ -296,16 +338,26 @@ __device__ bool fx_ctl_reduce(SmemFx& S, int NW, long long* part, unsigned* bar,
     part[3 * blockIdx.x + 2] = m;
   }
   __syncwarp();
-  if (!fx_ctl_barrier(bar, gen, status, timeout_ns)) return false;
+  if (!fx_ctl_barrier(bar, gen, status, timeout_ns, spin)) return false;
   lo = 0; hi = 0; m = 0;
-  for (int i = lane; i < G; i += 32) {
-    const unsigned long long l2 = (unsigned long long)part[3 * i + 0];
-    const long long h2 = part[3 * i + 1];
-    const long long m2 = part[3 * i + 2];
-    const unsigned long long s = lo + l2;
-    hi = hi + h2 + (s < lo ? 1 : 0);
-    lo = s;
-    m = m > m2 ? m : m2;
+  for (int i0 = 0; i0 < G; i0 += 256) {
+    // issue all loads of this block of partials before combining them
+    unsigned long long l2[8];
+    long long h2[8], m2[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int i = i0 + lane + 32 * j;
+      l2[j] = i < G ? (unsigned long long)__ldcg(part + 3 * i + 0) : 0ull;
+      h2[j] = i < G ? __ldcg(part + 3 * i + 1) : 0ll;
+      m2[j] = i < G ? __ldcg(part + 3 * i + 2) : 0ll;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const unsigned long long s = lo + l2[j];
+      hi = hi + h2[j] + (s < lo ? 1 : 0);
+      lo = s;
+      m = m > m2[j] ? m : m2[j];
+    }
   }
   fx_warp_reduce(lo, hi, m);
   lo = __shfl_sync(0xffffffffu, lo, 0);
@@ -339,9 +391,9 @@ __device__ void fx_const_a(SmemFx& S, const Op& op, int it) {
   const double sk = S.scale[it];
   const int Ek = S.E[it];
   const double Ak = S.A[it];
-  const double Akr = ldexp(Ak, Ek);
+  const double Akr = fx_scale2(Ak, Ek);
   const double bp = it > 1 ? S.beta[it - 1] * S.scale[it - 1] : 0.0;
-  const double Apr = it > 1 ? ldexp(S.A[it - 1], S.E[it - 1]) : 0.0;
+  const double Apr = it > 1 ? fx_scale2(S.A[it - 1], S.E[it - 1]) : 0.0;
   c.pk = fx_norm_shift(Ak);
   double B = fabs(bp) * Apr;
   if constexpr (FAMILY == kFamilySpin) {
@@ -361,19 +413,23 @@ __device__ void fx_const_a(SmemFx& S, const Op& op, int it) {
     c.m_cz = mcz.m;
     c.s_d = ED - mcz.e - (op.E_dz - 1) - 64;
     c.s_diag = Eu - (ED - 3) - (Ek - c.pk) - 64;
+    c.m_cz = fx_fold(mcz.m, c.s_d + c.s_diag);
     const Mant mh = fx_mant(ch);
     c.ph = fx_norm_shift((op.N > 1 ? op.N - 1 : 1) * Ak);
     c.m_hop = mh.m;
     c.s_hop = Eu - mh.e - (Ek - c.ph) - 64;
+    c.m_hop = fx_fold(c.m_hop, c.s_hop);
     if (op.uniform) {
       const Mant mx = fx_mant(S.bsite_raw[0] * sk);
       c.px = fx_norm_shift(op.N * Ak);
       c.m_x = mx.m;
       c.s_x = Eu - mx.e - (Ek - c.px) - 64;
+      c.m_x = fx_fold(c.m_x, c.s_x);
     } else {
       const int eb = fx_exp_for(bmax, 62);
-      for (int i = 0; i < op.N; ++i) S.mb[i] = __double2ll_rn(ldexp(S.bsite_raw[i] * sk, -eb));
       c.s_nu = Eu - eb - (Ek - c.pk) - 64;
+      for (int i = 0; i < op.N; ++i)
+        S.mb[i] = fx_fold(__double2ll_rn(fx_scale2(S.bsite_raw[i] * sk, -eb)), c.s_nu);
     }
   } else {
     for (int o = 0; o < op.nops; ++o) B += fabs(S.scal[o] * sk) * op.maxrow[o] * Akr;
@@ -385,12 +441,14 @@ __device__ void fx_const_a(SmemFx& S, const Op& op, int it) {
       const Mant m = fx_mant(S.scal[o] * sk);
       c.m_op[o] = m.m;
       c.s_op[o] = Eu - m.e - Epre - 64;
+      c.m_op[o] = fx_fold(c.m_op[o], c.s_op[o]);
     }
   }
   const Mant mp = fx_mant(-bp);
   c.pp = it > 1 ? fx_norm_shift(S.A[it - 1]) : 0;
   c.m_p = mp.m;
   c.s_p = S.Eu - mp.e - (it > 1 ? S.E[it - 1] - c.pp : 0) - 64;
+  c.m_p = fx_fold(c.m_p, c.s_p);
   c.use_prev = it > 1;
 }
 
@@ -403,7 +461,7 @@ __device__ double fx_estimate(SmemFx& S, int k, double ts) {
 
 // ------------------------------------------------------------------ the kernel
 template <int FAMILY, class Op>
-__global__ void __launch_bounds__(544, 1) k_propagate_fx(PropParams p, Op op) {
+__global__ void __launch_bounds__(800, 1) k_propagate_fx(PropParams p, Op op) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmemFx& S = *reinterpret_cast<SmemFx*>(smem_raw);
   const int tid = threadIdx.x;
@@ -413,8 +471,12 @@ __global__ void __launch_bounds__(544, 1) k_propagate_fx(PropParams p, Op op) {
   const bool lead = ctl && lane == 0;
   const int dim = p.dim;
   const int G = gridDim.x;
-  const int wstride = G * NW * 32;
-  const int wx0 = blockIdx.x * NW * 32 + tid;  // workers only
+  // each CTA walks one contiguous chunk of the vectors, so that the
+  // neighbours of low-bit flips (and short band offsets) are found in L1
+  const int chunk = (dim + G - 1) / G;
+  const int wstep = NW * 32;
+  const int wx0 = blockIdx.x * chunk + tid;  // workers only
+  const int wxe = min(dim, (blockIdx.x + 1) * chunk);
   const int ncoef = 1 + p.nV;
   unsigned gen = 0;
   // three partial slots (phase A, phase B, reconstruction): two uses of one
@@ -424,6 +486,9 @@ __global__ void __launch_bounds__(544, 1) k_propagate_fx(PropParams p, Op op) {
   long long* partR = partA + 6 * G;
   DevStatus* st = p.st;
   const bool glead = (blockIdx.x == 0) && lead;
+  // trace (see cfet_stats.phase_ns): worker loop times by thread 0, control
+  // own-time and barrier waits by the control lane 0, in SM clock cycles
+  long long tacc[6] = {0, 0, 0, 0, 0, 0};
   const bool fixed_k = p.tol <= 0.0;
   const bool forced = p.f_nsub != nullptr;
 
@@ -440,7 +505,7 @@ __global__ void __launch_bounds__(544, 1) k_propagate_fx(PropParams p, Op op) {
   {
     if (!ctl) {
       long long mx = 0;
-      for (int x = wx0; x < dim; x += wstride) {
+      for (int x = wx0; x < wxe; x += wstep) {
         const double2 v = p.psi[x];
         const long long a = __double_as_longlong(v.x) & 0x7FFFFFFFFFFFFFFFLL;
         const long long b = __double_as_longlong(v.y) & 0x7FFFFFFFFFFFFFFFLL;
@@ -453,7 +518,7 @@ __global__ void __launch_bounds__(544, 1) k_propagate_fx(PropParams p, Op op) {
       // the max bit pattern is reduced in the int64 max lane
       double sum;
       long long bits;
-      if (!fx_ctl_reduce(S, NW, partA, p.bar, gen, &st->status, p.timeout_ns, sum, bits)) {
+      if (!fx_ctl_reduce(S, NW, partA, p.bar, gen, &st->status, p.timeout_ns, sum, bits, tacc[5])) {
         if (lane == 0) S.abort_flag = 1;
       } else if (lane == 0) {
         S.abort_flag = 0;
@@ -469,10 +534,10 @@ __global__ void __launch_bounds__(544, 1) k_propagate_fx(PropParams p, Op op) {
     if (S.abort_flag) return;
     // pass 2: convert and take ||q_1||^2, max |M|
     if (!ctl) {
-      const double sc = ldexp(1.0, -S.E[1]);
+      const double sc = fx_scale2(1.0, -S.E[1]);
       __int128 a2 = 0;
       long long mx = 0;
-      for (int x = wx0; x < dim; x += wstride) {
+      for (int x = wx0; x < wxe; x += wstep) {
         const double2 v = p.psi[x];
         const longlong2 qv = make_longlong2(__double2ll_rn(v.x * sc), __double2ll_rn(v.y * sc));
         Q(1)[x] = qv;
@@ -485,10 +550,10 @@ __global__ void __launch_bounds__(544, 1) k_propagate_fx(PropParams p, Op op) {
     if (ctl) {
       double sum;
       long long mxi;
-      if (!fx_ctl_reduce(S, NW, partB, p.bar, gen, &st->status, p.timeout_ns, sum, mxi)) {
+      if (!fx_ctl_reduce(S, NW, partB, p.bar, gen, &st->status, p.timeout_ns, sum, mxi, tacc[5])) {
         if (lane == 0) S.abort_flag = 1;
       } else if (lane == 0) {
-        S.beta0 = ldexp(sqrt(sum), S.E[1]);
+        S.beta0 = fx_scale2(sqrt(sum), S.E[1]);
         S.A[1] = __ll2double_ru(mxi);
       }
     }
@@ -547,7 +612,8 @@ __global__ void __launch_bounds__(544, 1) k_propagate_fx(PropParams p, Op op) {
             longlong2* u = Q(it + 1);
             __int128 a2 = 0;
             long long mx = 0;
-            for (int x = wx0; x < dim; x += wstride) {
+            const long long tw0 = fx_clk();
+            for (int x = wx0; x < wxe; x += wstep) {
               longlong2 hv;
               if constexpr (FAMILY == kFamilySpin) hv = fx_apply_spin(q, qm, x, op, c, S.mb);
               else hv = fx_apply_dia(q, qm, x, dim, op, c);
@@ -557,6 +623,7 @@ __global__ void __launch_bounds__(544, 1) k_propagate_fx(PropParams p, Op op) {
               mx = max(mx, fx_absmax(hv.x, hv.y));
             }
             fx_worker_partial(S, a2, mx);
+            if (tid == 0) tacc[0] += fx_clk() - tw0;
           } else if (pend) {
             const double err = fx_estimate(S, it - 1, remaining);
             if (lane == 0) {
@@ -568,17 +635,18 @@ __global__ void __launch_bounds__(544, 1) k_propagate_fx(PropParams p, Op op) {
           }
           __syncthreads();
           if (ctl) {
+            const long long tc0 = fx_clk(), sp0 = tacc[5];
             double sum;
             long long mxi;
-            if (!fx_ctl_reduce(S, NW, partA, p.bar, gen, &st->status, p.timeout_ns, sum, mxi)) {
+            if (!fx_ctl_reduce(S, NW, partA, p.bar, gen, &st->status, p.timeout_ns, sum, mxi, tacc[5])) {
               if (lane == 0) S.abort_flag = 1;
             } else if (lane == 0 && !S.stop_prev) {
               const double s_it = S.scale[it];
-              const double alpha = ldexp(sum, S.E[it] + S.Eu) * s_it;
+              const double alpha = fx_scale2(sum, S.E[it] + S.Eu) * s_it;
               S.alpha[it] = alpha;
               // phase-B constants: w = u - alpha s_it q_it
               const double am = alpha * s_it;
-              const double Bw = ldexp(__ll2double_ru(mxi), S.Eu) + fabs(am) * ldexp(S.A[it], S.E[it]);
+              const double Bw = fx_scale2(__ll2double_ru(mxi), S.Eu) + fabs(am) * fx_scale2(S.A[it], S.E[it]);
               const int Ew = fx_exp_for(Bw, kFxBits);
               const Mant ma = fx_mant(-am);
               const int pk = fx_norm_shift(S.A[it]);
@@ -587,11 +655,13 @@ __global__ void __launch_bounds__(544, 1) k_propagate_fx(PropParams p, Op op) {
               S.m_a = ma.m;
               S.pk_b = pk;
               S.s_a = Ew - ma.e - (S.E[it] - pk) - 64;
+              S.m_a = fx_fold(ma.m, S.s_a);
               if (__ll2double_ru(mxi) >= 1.152921504606846976e18) {  // 2^60: fixed-point range exceeded (not expected)
                 atomicCAS(&st->status, 0, (int)CFET_ENAN);
                 S.abort_flag = 1;
               }
             }
+            if (lane == 0) tacc[1] += fx_clk() - tc0 - (tacc[5] - sp0);
           }
           __syncthreads();
           if (S.abort_flag) return;
@@ -608,25 +678,28 @@ __global__ void __launch_bounds__(544, 1) k_propagate_fx(PropParams p, Op op) {
             longlong2* u = Q(it + 1);
             __int128 b2 = 0;
             long long mx = 0;
-            for (int x = wx0; x < dim; x += wstride) {
+            const long long tw0 = fx_clk();
+            for (int x = wx0; x < wxe; x += wstep) {
               const longlong2 v = q[x];
               const longlong2 uu = u[x];
-              const long long wr = fx_rshr(uu.x, sh_u) + fx_mul(m_a, v.x << pk, s_a);
-              const long long wi = fx_rshr(uu.y, sh_u) + fx_mul(m_a, v.y << pk, s_a);
+              const long long wr = fx_rshr(uu.x, sh_u) + fx_mulhi(m_a, v.x << pk);
+              const long long wi = fx_rshr(uu.y, sh_u) + fx_mulhi(m_a, v.y << pk);
               u[x] = make_longlong2(wr, wi);
               b2 += (__int128)wr * wr + (__int128)wi * wi;
               mx = max(mx, fx_absmax(wr, wi));
             }
             fx_worker_partial(S, b2, mx);
+            if (tid == 0) tacc[2] += fx_clk() - tw0;
           }
           __syncthreads();
           if (ctl) {
+            const long long tc0 = fx_clk(), sp0 = tacc[5];
             double sum;
             long long mxi;
-            if (!fx_ctl_reduce(S, NW, partB, p.bar, gen, &st->status, p.timeout_ns, sum, mxi)) {
+            if (!fx_ctl_reduce(S, NW, partB, p.bar, gen, &st->status, p.timeout_ns, sum, mxi, tacc[5])) {
               if (lane == 0) S.abort_flag = 1;
             } else {
-              const double b = ldexp(sqrt(sum), S.Ew);
+              const double b = fx_scale2(sqrt(sum), S.Ew);
               const double prev_b = it > 1 ? S.beta[it - 1] : 0.0;
               const bool breakdown = b <= 1e-13 * (fabs(S.alpha[it]) + prev_b + 1.0);
               if (lane == 0) {
@@ -661,6 +734,7 @@ __global__ void __launch_bounds__(544, 1) k_propagate_fx(PropParams p, Op op) {
                 if (!acc_flag && it < klimit) fx_const_a<FAMILY>(S, op, it + 1);
               }
             }
+            if (lane == 0) tacc[3] += fx_clk() - tc0 - (tacc[5] - sp0);
           }
           __syncthreads();
           if (S.abort_flag) return;
@@ -683,7 +757,7 @@ __global__ void __launch_bounds__(544, 1) k_propagate_fx(PropParams p, Op op) {
             double err = 0.0;
             const double width = gersh_width(it, S.alpha + 1, S.beta + 1);
             for (int h = 1; h <= 40; ++h) {
-              const double ts = ldexp(remaining, -h);
+              const double ts = fx_scale2(remaining, -h);
               if (!(fabs(ts) * width <= 2.0 * it)) continue;
               err = fx_estimate(S, it, ts);
               if (err <= p.tol * ts / p.tau) { hh = h; break; }
@@ -700,7 +774,7 @@ __global__ void __launch_bounds__(544, 1) k_propagate_fx(PropParams p, Op op) {
         }
         n_app += acc_k;
       }
-      const double ts = ldexp(remaining, -acc_h);
+      const double ts = fx_scale2(remaining, -acc_h);
       const bool final_rec = last_exp && acc_h == 0;
       if (acc_k > 0) {
         // -------- reconstruct q_1 <- beta0 sum_i y_i s_i q_i
@@ -713,7 +787,7 @@ __global__ void __launch_bounds__(544, 1) k_propagate_fx(PropParams p, Op op) {
             const double cr = f * S.yr[i], ci = f * S.yi[i];
             S.yr[i] = cr;
             S.yi[i] = ci;
-            bnd += (fabs(cr) + fabs(ci)) * ldexp(S.A[i + 1], S.E[i + 1]);
+            bnd += (fabs(cr) + fabs(ci)) * fx_scale2(S.A[i + 1], S.E[i + 1]);
           }
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) bnd += __shfl_xor_sync(0xffffffffu, bnd, o);
@@ -726,23 +800,30 @@ __global__ void __launch_bounds__(544, 1) k_propagate_fx(PropParams p, Op op) {
             S.cp[i] = pi;
             S.csr[i] = Ep - mr.e - (S.E[i + 1] - pi) - 64;
             S.csi[i] = Ep - mi.e - (S.E[i + 1] - pi) - 64;
+            S.crm[i] = fx_fold(mr.m, S.csr[i]);
+            S.cim[i] = fx_fold(mi.m, S.csi[i]);
           }
           if (lane == 0) S.Epsi = Ep;
         }
         __syncthreads();
         if (!ctl) {
-          const double outscale = ldexp(1.0, S.Epsi);
+          const double outscale = fx_scale2(1.0, S.Epsi);
           __int128 a2 = 0;
           long long mx = 0;
-          for (int x = wx0; x < dim; x += wstride) {
+          const long long tw0 = fx_clk();
+          for (int x = wx0; x < wxe; x += wstep) {
             long long re = 0, im = 0;
             for (int i = 0; i < acc_k; ++i) {
               const longlong2 v = Q(i + 1)[x];
-              const int pi = S.cp[i], sr = S.csr[i], si = S.csi[i];
+              const int pi = S.cp[i];
               const long long cr = S.crm[i], ci = S.cim[i];
               const long long vr = v.x << pi, vi = v.y << pi;
-              re += fx_mul(cr, vr, sr) - fx_mul(ci, vi, si);
-              im += fx_mul(cr, vi, sr) + fx_mul(ci, vr, si);
+              // (cr + i ci)(vr + i vi) with three products; the sums (< 2^63)
+              // are halved to stay in fx_mulhi's operand range
+              const long long p1 = fx_mulhi(cr, vr), p2 = fx_mulhi(ci, vi);
+              const long long p3 = fx_mulhi((cr + ci) >> 1, (vr + vi) >> 1) << 2;
+              re += p1 - p2;
+              im += p3 - p1 - p2;
             }
             Q(1)[x] = make_longlong2(re, im);
             if (final_rec) p.psi[x] = make_double2(__ll2double_rn(re) * outscale, __ll2double_rn(im) * outscale);
@@ -750,15 +831,16 @@ __global__ void __launch_bounds__(544, 1) k_propagate_fx(PropParams p, Op op) {
             mx = max(mx, fx_absmax(re, im));
           }
           fx_worker_partial(S, a2, mx);
+          if (tid == 0) tacc[4] += fx_clk() - tw0;
         }
         __syncthreads();
         if (ctl) {
           double sum;
           long long mxi;
-          if (!fx_ctl_reduce(S, NW, partR, p.bar, gen, &st->status, p.timeout_ns, sum, mxi)) {
+          if (!fx_ctl_reduce(S, NW, partR, p.bar, gen, &st->status, p.timeout_ns, sum, mxi, tacc[5])) {
             if (lane == 0) S.abort_flag = 1;
           } else if (lane == 0) {
-            S.beta0 = ldexp(sqrt(sum), S.Epsi);
+            S.beta0 = fx_scale2(sqrt(sum), S.Epsi);
             S.E[1] = S.Epsi;
             S.A[1] = __ll2double_ru(mxi);
           }
@@ -794,6 +876,12 @@ __global__ void __launch_bounds__(544, 1) k_propagate_fx(PropParams p, Op op) {
     if (max_k > st->max_k) st->max_k = max_k;
     if (max_err > st->max_err) st->max_err = max_err;
   }
+  if (tid == 0 || lead) {  // every CTA: mean and max of its phase times
+    for (int i = (tid == 0 ? 0 : 1); i < 6; i += 2) {
+      atomicAdd((unsigned long long*)&st->phase_ns[i], (unsigned long long)(tacc[i] / G));
+      atomicMax(&st->phase_max_ns[i], tacc[i]);
+    }
+  }
 }
 
 // ------------------------------------------------------------------ launchers
@@ -823,6 +911,10 @@ int max_coresident_blocks_fx(int family, int block) {
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  // the kernel needs only a few KB of shared memory: leave the rest of the
+  // unified L1/shared storage to L1, which holds each CTA's chunk
+  cudaFuncSetAttribute(k_propagate_fx<kFamilySpin, OpSpinFx>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  cudaFuncSetAttribute(k_propagate_fx<kFamilyDia, OpDiaFx>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaError_t e;
   if (family == kFamilySpin)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_fx<kFamilySpin, OpSpinFx>, block,

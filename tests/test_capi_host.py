@@ -97,7 +97,7 @@ def test_create_validates_arguments(lib):
 def test_options_default(lib):
     opt = _capi.cfet_options()
     lib.cfet_options_default(C.byref(opt))
-    assert (opt.m_max, opt.m_min, opt.max_substeps, opt.block_size) == (16, 2, 64, 256)
+    assert (opt.m_max, opt.m_min, opt.max_substeps, opt.block_size) == (16, 2, 64, 0)
     assert opt.barrier_timeout_s == 2.0
 
 
