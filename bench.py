@@ -71,20 +71,21 @@ def problem():
     return pr, psi0
 
 
-def algorithmic_counts(stats, dim, N=N_SITES):
+def algorithmic_counts(stats, dim, N=N_SITES, elem_bytes=16.0):
     """Algorithmic bytes and FP64 flops of the persistent kernel for the
     Lanczos iterations and reconstructions reported in stats.
 
     bytes: 48 B per element per Lanczos iteration (read v_k, v_{k-1}, write
       v_{k+1}) + 16 B per element per basis vector read in the reconstruction
-      + 16 B per element for the reconstructed psi: 16 dim (4 n_app + n_sub).
+      + 16 B per element for the reconstructed psi: 16 dim (4 n_app + n_sub)
+      (8 B instead of 16 B per vector element for complex64 vectors).
     flops: per element and iteration 5N+7 for the spin apply (diagonal 4,
       (N-1)/2 complex hop additions on average, 2 complex FMA for the hop
       scale, N complex FMA for the transverse field) + 16 for the three-term
       recurrence and the two reductions; per reconstruction 8k + 4.
     """
     n_app, n_sub = stats["n_applies"], stats["n_substeps"]
-    bytes_ = 16.0 * dim * (4 * n_app + n_sub)
+    bytes_ = elem_bytes * dim * (4 * n_app + n_sub)
     flops = dim * ((5 * N + 7 + 16 + 8) * n_app + 4 * n_sub)
     return bytes_, flops
 
@@ -251,7 +252,7 @@ def run_gpu(args):
     value = app_total / (ms_max * 1e-3)
 
     # roofline of the persistent kernel (one launch per 256 steps)
-    bytes_, flops = algorithmic_counts(stats, dim)
+    bytes_, flops = algorithmic_counts(stats, dim, elem_bytes=8.0 if args.precision == "c64" else 16.0)
     achieved_tflops = flops / (kernel_ms * 1e-3) / 1e12
     achieved_gbs = bytes_ / (kernel_ms * 1e-3) / 1e9
     peaks = {}
@@ -291,10 +292,12 @@ def run_gpu(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample()
 
-    if args.precision == "fx":
+    if args.precision in ("fx", "c64"):
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved_gbs / hbm_peak, "traffic": None,
-                    "kernel": "k_propagate_fx (persistent Lanczos, int64 fixed-point vectors)",
+                    "kernel": "k_propagate_fx (persistent Lanczos, int64 fixed-point vectors)"
+                    if args.precision == "fx" else
+                    "k_propagate_c64 (persistent Lanczos, complex64 vectors, FP64-class reductions)",
                     "kernel_ms": kernel_ms, "launches": math.ceil(args.steps / 256),
                     "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), burst figure",
                     "fp64_equivalent_tflops": achieved_tflops}
@@ -310,7 +313,8 @@ def run_gpu(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "i64" if args.precision == "fx" else "f64",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fx": "i64", "c64": "f32", "f64": "f64"}[args.precision],
             "data": "synthetic", "config": dict(workload_config(), precision=args.precision),
             "cfet_steps_per_s": args.steps * ws / (ms_max * 1e-3),
             "krylov": {"applies_per_step": n_app / args.steps, "substeps": stats["n_substeps"],
@@ -349,11 +353,11 @@ def run_sweep(args):
     pr, psi0 = problem()
     T = args.sweep_T
 
-    def make(m_max):
+    def make(m_max, precision):
         return P.Propagator(P.XXZChain(N_SITES, pr.J, pr.Delta, pr.h), [P.XField(N_SITES, pr.xfield)],
-                            [pr.drive], m_max=m_max, max_substeps=64, precision=args.precision)
+                            [pr.drive], m_max=m_max, max_substeps=64, precision=precision)
 
-    ref_prop = make(24)
+    ref_prop = make(24, "fx")   # the reference is always an FP64-class run
     ref = torch.from_numpy(psi0).cuda()
     dt_ref = 0.0025
     n_ref = int(round(T / dt_ref))
@@ -362,7 +366,7 @@ def run_sweep(args):
     ref_s = time.perf_counter() - t
     ref_prop.close()
     rows = []
-    prop = make(M_MAX)
+    prop = make(M_MAX, args.precision)
     for order in (4, 6, 8):
         for dt in (0.05, 0.02, 0.01):
             n = int(round(T / dt))
@@ -396,6 +400,88 @@ def run_sweep(args):
     return 0
 
 
+def _roofline_study_line(prop, stats, ms, dim, bytes_per_app, elem, label, extra):
+    """bytes_per_app: algorithmic bytes per element of one Lanczos iteration;
+    elem: bytes per vector element (reconstruction reads k vectors, writes 1)."""
+    n_app, n_sub = stats["n_applies"], stats["n_substeps"]
+    kernel_ms = prop.kernel_time_ms()
+    bytes_ = dim * (bytes_per_app * n_app + elem * (n_app + n_sub))
+    line = {"study": label, "H_applies": n_app, "substeps": n_sub, "exponentials": stats["n_exp"],
+            "substeps_per_exponential": n_sub / max(1, stats["n_exp"]), "max_k": stats["max_k"],
+            "H_applies_per_s": n_app / (ms * 1e-3), "ms": ms, "kernel_ms": kernel_ms,
+            "algorithmic_GBps": bytes_ / (kernel_ms * 1e-3) / 1e9}
+    line.update(extra)
+    print(json.dumps(line))
+
+
+def run_study_atom(args):
+    """The grid atom (Nr = 2000, l < 100, dim 200 000, CF8:11, dt = 0.1, m <= 64,
+    tol 1e-10) for --steps steps from t0 = 500 (peak of the pulse envelope),
+    starting from the discrete 1s state: H applies/s, substeps per stage
+    exponential and the projected cost of the full T = 1000 pulse."""
+    import torch
+    import paper_1102_5071_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    a = W.ATOM
+    p = W.grid_atom(Nr=a["Nr"], L=a["L"], dr=a["dr"], E0=a["E0"], omega=a["omega"], Tp=a["Tp"])
+    psi0, e0 = W.atom_ground_state(p)
+    prop = P.Propagator(P.DIA(p.H0_offsets, p.H0_values), [P.DIA(p.V_offsets, p.V_values)], [p.drive],
+                        m_max=a["m_max"], max_substeps=4000, precision=args.precision)
+    psi = torch.from_numpy(psi0).cuda()
+    t0 = 500.0
+    # warm-up: one apply (context, tables and graph set-up); a full atom step
+    # takes seconds, so the timed steps are not preceded by one
+    prop.apply(np.array([1.0, 0.0]), psi, torch.empty_like(psi))
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    st = prop.propagate(psi, t0, a["dt"], args.steps, order=a["order"], tol=a["tol"])
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    nfull = int(round(a["Tp"] / a["dt"]))
+    # per element and iteration: q_k, q_{k-1} read, u written + 5 real diagonals
+    elem, val = (8.0, 4.0) if args.precision == "c64" else (16.0, 8.0)
+    _roofline_study_line(prop, st, ms, p.dim, 3 * elem + 5 * val, elem, "grid atom Nr=2000 L=100 CF8:11 dt=0.1 m<=64 tol 1e-10",
+                         {"steps": args.steps, "t0": t0, "precision": args.precision,
+                          "norm_drift": abs(torch.linalg.vector_norm(psi).item() - 1.0),
+                          "full_pulse_steps": nfull,
+                          "full_pulse_projected_s": ms * 1e-3 / args.steps * nfull})
+    prop.close()
+    return 0
+
+
+def run_study_sizes(args):
+    """The driven chain of the bench at N = 20, 22, 24, 26 (vectors 16 MiB to
+    1 GiB, the larger ones far beyond L2): H applies/s and algorithmic HBM
+    GB/s of the persistent kernel for --steps CFET steps each."""
+    import torch
+    import paper_1102_5071_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    for n in (20, 22, 24, 26):
+        pr = W.spin_chain(n)
+        prop = P.Propagator(P.XXZChain(n, pr.J, pr.Delta, pr.h), [P.XField(n, pr.xfield)], [pr.drive],
+                            m_max=M_MAX, max_substeps=64, precision=args.precision)
+        psi = torch.from_numpy(W.random_state(PSI_SEED, 1 << n)).cuda()
+        prop.propagate(psi, 0.0, DT, 1, order=ORDER, tol=TOL)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        st = prop.propagate(psi, DT, DT, args.steps, order=ORDER, tol=TOL)
+        ev1.record()
+        torch.cuda.synchronize()
+        elem = 8.0 if args.precision == "c64" else 16.0
+        _roofline_study_line(prop, st, ev0.elapsed_time(ev1), 1 << n, 3 * elem, elem,
+                             f"driven XXZ chain N={n} {SCHEME} dt={DT} tol {TOL}",
+                             {"N": n, "steps": args.steps, "precision": args.precision})
+        prop.close()
+        del psi
+        torch.cuda.empty_cache()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -404,11 +490,13 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
-    ap.add_argument("--precision", default="fx", choices=["fx", "f64"],
-                    help="Krylov vector format: int64 fixed point (default) or FP64")
+    ap.add_argument("--precision", default="fx", choices=["fx", "f64", "c64"],
+                    help="Krylov vector format: int64 fixed point (default), FP64, or complex64 (mixed precision)")
     ap.add_argument("--sweep", action="store_true",
                     help="accuracy study: final-state error and throughput per (order, dt) over T")
     ap.add_argument("--sweep-T", type=float, default=20.0)
+    ap.add_argument("--study", choices=["atom", "sizes"],
+                    help="extra measurements: the grid atom, or the chain at N = 20..26")
     ap.add_argument("--block-size", type=int, default=0,
                     help="threads per CTA of the FP64 kernel; the fixed-point kernel uses 2x this many workers + 1 control warp")
     args = ap.parse_args()
@@ -418,6 +506,10 @@ def main():
         return run_reference(args)
     if args.sweep:
         return run_sweep(args)
+    if args.study == "atom":
+        return run_study_atom(args)
+    if args.study == "sizes":
+        return run_study_sizes(args)
     return run_gpu(args)
 
 

@@ -137,8 +137,9 @@ typedef struct cfet_options {
   int32_t m_min;             /* first dimension tested (default 2, >= 1)      */
   int32_t max_substeps;      /* per stage exponential (default 64)            */
   int32_t block_size;        /* 0 = auto; FP64 kernel: threads per CTA (256);
-                                fixed-point kernel: 2 x block_size worker
-                                threads + one control warp (384 -> 800)      */
+                                fixed-point and mixed-precision kernels:
+                                2 x block_size worker threads + one control
+                                warp (384 -> 800, the largest allowed)        */
   int32_t grid_size;         /* CTAs of the persistent kernel (0 = auto,
                                 capped at the co-resident maximum)            */
   int32_t steps_per_launch;  /* CFET steps per persistent launch (0 = 256)    */
@@ -146,7 +147,7 @@ typedef struct cfet_options {
   int32_t precision;         /* CFET_PREC_* (default CFET_PREC_FX)            */
 } cfet_options;
 
-/* Number format of the Krylov vectors on the device.  Both keep alpha, beta,
+/* Number format of the Krylov vectors on the device.  All keep alpha, beta,
  * the tridiagonal exponential and all decisions in FP64.
  *  CFET_PREC_F64: complex128 vectors, FP64 arithmetic throughout.
  *  CFET_PREC_FX : int64 (re, im) mantissas with one exponent per vector
@@ -154,8 +155,15 @@ typedef struct cfet_options {
  *                 64x64->128-bit scalar products, exact 128-bit dot products;
  *                 resolution finer than FP64 relative to each vector's
  *                 largest entry.  Uses integer units instead of the FP64
- *                 units, which run at 1/64 of the FP32 rate on GB300.     */
-enum { CFET_PREC_DEFAULT = 0, CFET_PREC_F64 = 1, CFET_PREC_FX = 2 };
+ *                 units, which run at 1/64 of the FP32 rate on GB300.
+ *  CFET_PREC_C64: complex64 vectors (half the bytes), FP32 apply, recurrence
+ *                 and reconstruction; alpha, ||w||^2 and ||psi||^2 are
+ *                 compensated (float-float) per thread and FP64 across
+ *                 threads.  psi stays complex128 at the boundary.  Results
+ *                 carry FP32 rounding (relative ~1e-7 per stage exponential),
+ *                 so Krylov tolerances below ~1e-7 no longer bound the
+ *                 error; meant for targets of about 1e-6.                   */
+enum { CFET_PREC_DEFAULT = 0, CFET_PREC_F64 = 1, CFET_PREC_FX = 2, CFET_PREC_C64 = 3 };
 
 typedef struct cfet_stats {
   int64_t n_exp;             /* stage exponentials evaluated                  */
@@ -164,7 +172,8 @@ typedef struct cfet_stats {
   int32_t max_k;             /* largest Krylov dimension used                 */
   int32_t status;            /* device status word (a cfet_status)            */
   double max_err_est;        /* largest accepted error estimate               */
-  /* Trace of the fixed-point kernel, SM clock cycles per CTA (mean over CTAs
+  /* Trace of the fixed-point and mixed-precision kernels, SM clock cycles
+   * per CTA (mean over CTAs
    * in phase_ns, largest CTA in phase_max_ns; zero for the FP64 kernel):
    * [0] worker loops of the apply passes, [1] control-warp work after them
    * (reduction, scalar constants; barrier wait excluded), [2] worker loops of

@@ -32,8 +32,8 @@ class cfet_options(C.Structure):
                 ("barrier_timeout_s", C.c_double), ("precision", C.c_int32)]
 
 
-CFET_PREC_DEFAULT, CFET_PREC_F64, CFET_PREC_FX = 0, 1, 2
-PRECISIONS = {"default": CFET_PREC_DEFAULT, "f64": CFET_PREC_F64, "fx": CFET_PREC_FX}
+CFET_PREC_DEFAULT, CFET_PREC_F64, CFET_PREC_FX, CFET_PREC_C64 = 0, 1, 2, 3
+PRECISIONS = {"default": CFET_PREC_DEFAULT, "f64": CFET_PREC_F64, "fx": CFET_PREC_FX, "c64": CFET_PREC_C64}
 
 
 class cfet_stats(C.Structure):

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(PKG, LIB_NAME)
 BUILD_DIR = os.path.join(PKG, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "kernels_fx.cu", "capi.cu", "schemes.cpp", "noalloc.cu"]
+SOURCES = ["kernels.cu", "kernels_fx.cu", "kernels_c64.cu", "capi.cu", "schemes.cpp", "noalloc.cu"]
 
 
 def _nvcc() -> str:

@@ -53,6 +53,12 @@ struct cfet_ctx {
   long long* d_DZ = nullptr;   // DZ_lo | DZ_hi
   long long* d_VAL = nullptr;
   longlong2* d_qbasis = nullptr;
+  // mixed-precision path
+  OpSpinC spin_c{};
+  OpDiaC dia_c{};
+  float* d_dz32 = nullptr;     // dz_lo | dz_hi in FP32
+  float* d_val32 = nullptr;
+  float2* d_qbasis32 = nullptr;
   double* d_partials = nullptr;
   unsigned* d_bar = nullptr;
   DevStatus* d_st = nullptr;
@@ -118,6 +124,7 @@ void free_ctx(cfet_ctx* c) {
   cudaFree(c->d_basis); cudaFree(c->d_partials); cudaFree(c->d_bar); cudaFree(c->d_st);
   cudaFree(c->d_scal); cudaFree(c->d_psi_e2e); cudaFree(c->d_dec);
   cudaFree(c->d_DZ); cudaFree(c->d_VAL); cudaFree(c->d_qbasis);
+  cudaFree(c->d_dz32); cudaFree(c->d_val32); cudaFree(c->d_qbasis32);
   if (c->h_st) cudaFreeHost(c->h_st);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   delete c;
@@ -176,6 +183,9 @@ cfet_status launch_chunk(cfet_ctx* ctx, const PropParams& base, long long e0, lo
   if (ctx->precision == CFET_PREC_FX)
     e = ctx->family == kFamilySpin ? launch_propagate_spin_fx(p, ctx->spin_fx, ctx->grid, ctx->block, s)
                                    : launch_propagate_dia_fx(p, ctx->dia_fx, ctx->grid, ctx->block, s);
+  else if (ctx->precision == CFET_PREC_C64)
+    e = ctx->family == kFamilySpin ? launch_propagate_spin_c64(p, ctx->spin_c, ctx->grid, ctx->block, s)
+                                   : launch_propagate_dia_c64(p, ctx->dia_c, ctx->grid, ctx->block, s);
   else
     e = ctx->family == kFamilySpin ? launch_propagate_spin(p, ctx->spin, ctx->grid, ctx->block, s)
                                    : launch_propagate_dia(p, ctx->dia, ctx->grid, ctx->block, s);
@@ -217,6 +227,7 @@ PropParams base_params(cfet_ctx* ctx, double2* psi, double tau, double tol) {
   p.st = ctx->d_st;
   p.timeout_ns = (long long)(ctx->opt.barrier_timeout_s * 1e9);
   p.qbasis = ctx->d_qbasis;
+  p.qbasis32 = ctx->d_qbasis32;
   return p;
 }
 
@@ -294,15 +305,16 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
   if (o.m_min < 1 || o.m_min > o.m_max) return fail(nullptr, CFET_EINVAL, "m_min must be in [1, m_max]");
   if (o.max_substeps < 1) return fail(nullptr, CFET_EINVAL, "max_substeps must be >= 1");
   if (o.precision == CFET_PREC_DEFAULT) o.precision = CFET_PREC_FX;
-  if (o.precision != CFET_PREC_F64 && o.precision != CFET_PREC_FX)
-    return fail(nullptr, CFET_EINVAL, "precision must be CFET_PREC_F64 or CFET_PREC_FX");
+  if (o.precision != CFET_PREC_F64 && o.precision != CFET_PREC_FX && o.precision != CFET_PREC_C64)
+    return fail(nullptr, CFET_EINVAL, "precision must be CFET_PREC_F64, CFET_PREC_FX or CFET_PREC_C64");
   if (o.block_size == 0) o.block_size = (o.precision == CFET_PREC_F64) ? 256 : 384;
   {
-    // FP64 kernel: block_size threads (<= 256); fixed-point kernel:
-    // 2 * block_size workers + one control warp (<= 1024 threads)
-    const int lim = (o.precision == CFET_PREC_F64) ? 256 : 480;
+    // FP64 kernel: block_size threads (<= 256); fixed-point and mixed-precision
+    // kernels: 2 * block_size workers + one control warp (<= 1024 threads)
+    // (the latter are compiled for at most 800 threads per CTA)
+    const int lim = (o.precision == CFET_PREC_F64) ? 256 : 384;
     if (o.block_size < 32 || o.block_size > lim || o.block_size % 32)
-      return fail(nullptr, CFET_EINVAL, "block_size must be a multiple of 32 in [32, 256] (FP64) or [32, 480]");
+      return fail(nullptr, CFET_EINVAL, "block_size must be a multiple of 32 in [32, 256] (FP64) or [32, 384]");
   }
   if (o.grid_size < 0) return fail(nullptr, CFET_EINVAL, "grid_size must be >= 0");
   if (o.steps_per_launch <= 0) o.steps_per_launch = 256;
@@ -359,9 +371,11 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
   ctx->dim = dim;
   ctx->nV = nV;
   ctx->opt = o;
-  // FP64 kernel: block_size threads; fixed-point kernel: 2 * block_size
-  // worker threads plus one control warp (default 512 + 32, one CTA per SM)
-  ctx->block = o.precision == CFET_PREC_FX ? 2 * o.block_size + 32 : o.block_size;
+  // FP64 kernel: block_size threads; fixed-point and mixed-precision kernels:
+  // 2 * block_size worker threads plus one control warp (default 768 + 32,
+  // one CTA per SM)
+  const bool ctl_warp = o.precision != CFET_PREC_F64;
+  ctx->block = ctl_warp ? 2 * o.block_size + 32 : o.block_size;
   ctx->precision = o.precision;
   for (int k = 0; k < nV; ++k) {
     ctx->f.push_back(f[k]);
@@ -434,6 +448,19 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
     ctx->spin_fx.maxdz = maxdz;
     ctx->spin_fx.J2 = 2.0 * H0->J;
     ctx->spin_fx.xf = ctx->d_xf;
+    // FP32 diagonal tables of the mixed-precision path
+    std::vector<float> dz32((size_t)nlo + nhi);
+    for (size_t i = 0; i < nlo; ++i) dz32[i] = (float)lo[i];
+    for (size_t i = 0; i < nhi; ++i) dz32[nlo + i] = (float)hi[i];
+    CKC(cudaMalloc(&ctx->d_dz32, dz32.size() * sizeof(float)), "cudaMalloc(dz32)");
+    CKC(cudaMemcpy(ctx->d_dz32, dz32.data(), dz32.size() * sizeof(float), cudaMemcpyHostToDevice), "upload dz32");
+    ctx->spin_c.N = N;
+    ctx->spin_c.lo_bits = L;
+    ctx->spin_c.uniform = uniform ? 1 : 0;
+    ctx->spin_c.J2 = 2.0 * H0->J;
+    ctx->spin_c.dz_lo = ctx->d_dz32;
+    ctx->spin_c.dz_hi = ctx->d_dz32 + nlo;
+    ctx->spin_c.xf = ctx->d_xf;
   } else {
     std::vector<long long> off;
     std::vector<int> opidx;
@@ -468,6 +495,11 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
     fx.off = ctx->d_off;
     fx.opidx = ctx->d_opidx;
     std::vector<long long> VAL((size_t)nd * dim);
+    std::vector<float> val32((size_t)nd * dim);
+    OpDiaC& dc = ctx->dia_c;
+    dc.ndiag = nd;
+    dc.nops = 1 + nV;
+    dc.off = ctx->d_off;
     int dcur = 0;
     for (int k = -1; k < nV; ++k) {
       const cfet_op& o2 = k < 0 ? *H0 : V[k];
@@ -493,27 +525,35 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
       fx.maxrow[oi] = mrow * (1.0 + 1e-12);
       fx.dfirst[oi] = dcur;
       fx.dcount[oi] = o2.ndiag;
+      dc.dfirst[oi] = dcur;
+      dc.dcount[oi] = o2.ndiag;
       for (int d = 0; d < o2.ndiag; ++d, ++dcur)
         for (int r = 0; r < dim; ++r) {
           const long long c = (long long)r + o2.offsets[d];
           const double v = (c >= 0 && c < dim) ? o2.values[(size_t)d * dim + r] : 0.0;
           VAL[(size_t)dcur * dim + r] = std::llrint(std::ldexp(v, -E_op));
+          val32[(size_t)dcur * dim + r] = (float)v;
         }
     }
     CKC(cudaMalloc(&ctx->d_VAL, VAL.size() * sizeof(long long)), "cudaMalloc(VAL)");
     CKC(cudaMemcpy(ctx->d_VAL, VAL.data(), VAL.size() * sizeof(long long), cudaMemcpyHostToDevice), "upload VAL");
     fx.VAL = ctx->d_VAL;
+    CKC(cudaMalloc(&ctx->d_val32, val32.size() * sizeof(float)), "cudaMalloc(val32)");
+    CKC(cudaMemcpy(ctx->d_val32, val32.data(), val32.size() * sizeof(float), cudaMemcpyHostToDevice),
+        "upload val32");
+    dc.val = ctx->d_val32;
   }
   // persistent grid: co-resident maximum, no more CTAs than needed to give
   // every thread at least one element
-  const int maxg = ctx->precision == CFET_PREC_FX ? max_coresident_blocks_fx(family, ctx->block)
-                                                  : max_coresident_blocks(family, ctx->block);
+  const int maxg = ctx->precision == CFET_PREC_FX    ? max_coresident_blocks_fx(family, ctx->block)
+                   : ctx->precision == CFET_PREC_C64 ? max_coresident_blocks_c64(family, ctx->block)
+                                                     : max_coresident_blocks(family, ctx->block);
   if (maxg < 1) {
     free_ctx(ctx);
     return fail(nullptr, CFET_ECUDA, "occupancy query failed for the persistent kernel");
   }
   // element threads per CTA (the fixed-point kernel adds one control warp)
-  const int workers = ctx->precision == CFET_PREC_FX ? ctx->block - 32 : ctx->block;
+  const int workers = ctl_warp ? ctx->block - 32 : ctx->block;
   int want = (dim + workers - 1) / workers;
   if (o.grid_size > 0) want = o.grid_size;
   ctx->grid = want < maxg ? want : maxg;
@@ -521,6 +561,8 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
 
   if (ctx->precision == CFET_PREC_FX)
     CKC(cudaMalloc(&ctx->d_qbasis, (size_t)(o.m_max + 1) * dim * sizeof(longlong2)), "cudaMalloc(Krylov basis)");
+  else if (ctx->precision == CFET_PREC_C64)
+    CKC(cudaMalloc(&ctx->d_qbasis32, (size_t)(o.m_max + 1) * dim * sizeof(float2)), "cudaMalloc(Krylov basis)");
   else
     CKC(cudaMalloc(&ctx->d_basis, (size_t)o.m_max * dim * sizeof(double2)), "cudaMalloc(Krylov basis)");
   if (ctx->precision == CFET_PREC_FX) {

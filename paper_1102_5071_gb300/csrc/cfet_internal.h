@@ -82,6 +82,26 @@ struct OpDiaFx {
   int dcount[1 + kMaxDrives];     // number of diagonals of each operator
 };
 
+// Mixed-precision forms (see kernels_c64.cu): FP32 operator data.
+struct OpSpinC {
+  int N;
+  int lo_bits;
+  int uniform;            // every drive field has the same coefficient on all sites
+  double J2;              // 2 J
+  const float* dz_lo;     // [2^L]        FP32 copy of OpSpin::dz_lo
+  const float* dz_hi;     // [2^(N-L+1)]  FP32 copy of OpSpin::dz_hi
+  const double* xf;       // [nV * N] per-field per-site X coefficients (FP64)
+};
+
+struct OpDiaC {
+  int ndiag;
+  int nops;               // 1 + nV
+  const long long* off;   // [ndiag], diagonals grouped by operator
+  const float* val;       // [ndiag * dim], zero where the column is outside [0, dim)
+  int dfirst[1 + kMaxDrives];
+  int dcount[1 + kMaxDrives];
+};
+
 struct PropParams {
   int dim;
   int nV;
@@ -104,6 +124,8 @@ struct PropParams {
   // fixed-point path: Krylov vectors q_1 .. q_{m_max+1} as int64 (re, im)
   // pairs; q_i at qbasis + (i-1)*dim.  partials then hold 4 * gridDim.x.
   longlong2* qbasis;
+  // mixed-precision path: complex64 Krylov vectors, q_i at qbasis32 + (i-1)*dim
+  float2* qbasis32;
 };
 
 // ---------------------------------------------------------------- launchers
@@ -119,6 +141,9 @@ int launch_spin_tables(int N, int L, double J, double Delta, const double* h, do
 int launch_propagate_spin_fx(const PropParams& p, const OpSpinFx& op, int grid, int block, void* stream);
 int launch_propagate_dia_fx(const PropParams& p, const OpDiaFx& op, int grid, int block, void* stream);
 int max_coresident_blocks_fx(int family, int block);
+int launch_propagate_spin_c64(const PropParams& p, const OpSpinC& op, int grid, int block, void* stream);
+int launch_propagate_dia_c64(const PropParams& p, const OpDiaC& op, int grid, int block, void* stream);
+int max_coresident_blocks_c64(int family, int block);
 int max_coresident_blocks(int family, int block);  // per device, for the persistent kernel
 size_t propagate_smem_bytes(int block);
 

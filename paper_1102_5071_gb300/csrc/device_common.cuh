@@ -23,6 +23,49 @@ __device__ __forceinline__ unsigned ld_volatile_u32(const unsigned* p) {
 }
 __device__ __forceinline__ int ld_volatile_i32(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
 
+// SM cycle counter, ordered with respect to surrounding memory operations.
+static __device__ __forceinline__ long long sm_clock() {
+  long long t;
+  asm volatile("mov.u64 %0, %%clock64;" : "=l"(t) : : "memory");
+  return t;
+}
+// Bounded grid barrier executed by one warp of each CTA (lane 0 arrives and
+// spins; `spin` accumulates its SM cycles).  Returns false in every lane when
+// the wait limit expired or another CTA reported an error.
+static __device__ bool warp_grid_barrier(unsigned* bar, unsigned& gen, int* status, long long timeout_ns, long long& spin) {
+  const int lane = threadIdx.x & 31;
+  int ok = 1;
+  if (gridDim.x > 1 && lane == 0) {
+    const long long c0 = sm_clock();
+    const unsigned target = gen + 1;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&bar[0], 1u) + 1u;
+    if (arrived == gridDim.x) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicExch(&bar[1], target);
+    } else {
+      const long long t0 = global_timer_ns();
+      unsigned spins = 0;
+      while (ld_volatile_u32(&bar[1]) != target) {
+        if ((++spins & 63u) == 0u) {
+          if (ld_volatile_i32(status) != 0) { ok = 0; break; }
+          if (global_timer_ns() - t0 > timeout_ns) {
+            atomicCAS(status, 0, (int)CFET_ETIMEOUT);
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    __threadfence();
+    spin += sm_clock() - c0;
+  }
+  gen += 1;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  return ok != 0;
+}
+
 // Bounded grid-wide barrier (arrival counter + generation).  Returns false in
 // every thread of the CTA when the wait limit expired or another CTA reported
 // an error; the first CTA to time out records CFET_ETIMEOUT.

@@ -1,0 +1,612 @@
+// Mixed-precision persistent Lanczos kernel (sm_103a): complex64 Krylov
+// vectors, FP64-class reductions and FP64 scalar work.
+//
+// Same method and decisions as k_propagate (kernels.cu) and k_propagate_fx
+// (kernels_fx.cu): the stage exponential exp(-i tau H_j) psi of a CFET step
+// (Alvermann & Fehske, arXiv:1102.5071, Sec. 4 Eq. (Ucf), Sec. 7
+// Eq. (OmGLeg)) by the Lanczos / Krylov method of Sec. 8.1 with the
+// a-posteriori estimate, adaptive Krylov dimension and substepping.
+//
+// Number format.  The Krylov vectors q_i are complex64 (8 B per element, half
+// the bytes of complex128) and the operator apply, the three-term recurrence
+// and the reconstruction run in FP32 (the GB300 FP32 rate is 64x its FP64
+// rate).  Everything that decides the method stays FP64-class:
+//   * alpha_k, ||w||^2 and ||psi||^2 are compensated FP32 dot products per
+//     thread (error-free product by FMA and error-free sum, i.e. the Dot2
+//     scheme of Ogita, Rump and Oishi, "Accurate sum and dot product", 2005),
+//     combined as float-float pairs over the warp and in FP64 over the CTA
+//     and the grid, in one fixed order (every CTA holds bit-identical sums);
+//   * the stage and Lanczos scalars, the tridiagonal exponential, the error
+//     estimate and all decisions are FP64 on the control warp;
+//   * psi enters and leaves as complex128; in between it is held as q_1.
+// The result differs from the FP64 method by FP32 rounding of the vectors
+// (relative 2^-24 per element and operation), not by the Krylov decisions.
+//
+// Work split: NW worker warps do element work only; one control warp does
+// the reductions, the bounded grid barrier, the per-pass scalars and the
+// small exponential (the estimate of iteration k runs while the workers
+// already apply H for iteration k+1, as in the fixed-point kernel).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "cfet_internal.h"
+#include "device_common.cuh"
+
+namespace cfet {
+
+// ------------------------------------------------------------------ compensated sums
+// (s, c): running sum s and accumulated rounding errors c.  The _rn
+// intrinsics keep the compiler from contracting the error-free steps.
+__device__ __forceinline__ void ff_two_sum(float& s, float& c, float p) {
+  const float t = __fadd_rn(s, p);
+  const float z = __fsub_rn(t, s);
+  const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  s = t;
+  c = __fadd_rn(c, e);
+}
+__device__ __forceinline__ void ff_add_prod(float& s, float& c, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);  // a b = p + e exactly
+  ff_two_sum(s, c, p);
+  c = __fadd_rn(c, e);
+}
+// Warp sum of (s, c) pairs (lane 0 result).
+__device__ __forceinline__ void ff_warp_sum(float& s, float& c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_down_sync(0xffffffffu, s, o);
+    const float c2 = __shfl_down_sync(0xffffffffu, c, o);
+    ff_two_sum(s, c, s2);
+    c = __fadd_rn(c, c2);
+  }
+}
+
+// ------------------------------------------------------------------ shared state
+struct CConst {
+  // phase A: u = s_k H_j q_k - beta_{k-1} s_{k-1} q_{k-1}
+  float cz, ch, cx, cp;          // spin: c0 s_k, 2 J c0 s_k, uniform field s_k, -beta s_{k-1}
+  float co[1 + kMaxDrives];      // dia: c_o s_k per operator
+  int use_prev;
+};
+
+struct SmemC {
+  float ws[32], wc[32];          // per-warp compensated partials of the workers
+  double alpha[kMaxKrylov + 2];
+  double beta[kMaxKrylov + 2];
+  double scale[kMaxKrylov + 3];  // 1 / ||q_i||
+  double yr[kMaxKrylov], yi[kMaxKrylov];
+  double tr[kMaxKrylov], ti[kMaxKrylov];
+  float cr[kMaxKrylov], ci[kMaxKrylov];  // reconstruction coefficients
+  double scal[1 + kMaxDrives];
+  double bsite_raw[kMaxSites];
+  float bx[kMaxSites];           // non-uniform fields: b_i s_k
+  CConst ca;
+  float am;                      // phase B: -alpha_k s_k
+  int abort_flag, stop_prev, accept_now, pend, y_ready, acc_h;
+  double err_now, err_prev;
+  double beta0;
+};
+
+// ------------------------------------------------------------------ applies
+__device__ __forceinline__ float2 c_apply_spin(const float2* __restrict__ q, const float2* __restrict__ qm, int x,
+                                               const OpSpinC& op, const CConst& c, const float* bx) {
+  const int N = op.N, L = op.lo_bits;
+  const float dz = __ldg(op.dz_lo + (x & ((1 << L) - 1))) + __ldg(op.dz_hi + (x >> (L - 1)));
+  const float d = c.cz * dz;
+  const float2 v = q[x];
+  float ur = d * v.x, ui = d * v.y;
+  float hr = 0.f, hi = 0.f;
+  const unsigned anti = ((unsigned)x ^ ((unsigned)x >> 1)) & ((1u << (N - 1)) - 1u);
+#pragma unroll 4
+  for (int i = 0; i < N - 1; ++i) {  // antiparallel bonds only (predicated)
+    if ((anti >> i) & 1u) {
+      const float2 w = q[x ^ (3 << i)];
+      hr += w.x;
+      hi += w.y;
+    }
+  }
+  ur = fmaf(c.ch, hr, ur);
+  ui = fmaf(c.ch, hi, ui);
+  if (op.uniform) {
+    float xr = 0.f, xi = 0.f;
+#pragma unroll 4
+    for (int i = 0; i < N; ++i) {
+      const float2 w = q[x ^ (1 << i)];
+      xr += w.x;
+      xi += w.y;
+    }
+    ur = fmaf(c.cx, xr, ur);
+    ui = fmaf(c.cx, xi, ui);
+  } else {
+#pragma unroll 4
+    for (int i = 0; i < N; ++i) {
+      const float2 w = q[x ^ (1 << i)];
+      ur = fmaf(bx[i], w.x, ur);
+      ui = fmaf(bx[i], w.y, ui);
+    }
+  }
+  if (c.use_prev) {
+    const float2 w = qm[x];
+    ur = fmaf(c.cp, w.x, ur);
+    ui = fmaf(c.cp, w.y, ui);
+  }
+  return make_float2(ur, ui);
+}
+
+__device__ __forceinline__ float2 c_apply_dia(const float2* __restrict__ q, const float2* __restrict__ qm, int r,
+                                              int dim, const OpDiaC& op, const CConst& c) {
+  float ur = 0.f, ui = 0.f;
+  for (int o = 0; o < op.nops; ++o) {
+    float ar = 0.f, ai = 0.f;
+    const int d0 = op.dfirst[o], d1 = d0 + op.dcount[o];
+    for (int d = d0; d < d1; ++d) {
+      const long long cidx = (long long)r + __ldg(op.off + d);
+      if (cidx >= 0 && cidx < dim) {
+        const float a = __ldg(op.val + (size_t)d * dim + r);
+        const float2 w = q[cidx];
+        ar = fmaf(a, w.x, ar);
+        ai = fmaf(a, w.y, ai);
+      }
+    }
+    ur = fmaf(c.co[o], ar, ur);
+    ui = fmaf(c.co[o], ai, ui);
+  }
+  if (c.use_prev) {
+    const float2 w = qm[r];
+    ur = fmaf(c.cp, w.x, ur);
+    ui = fmaf(c.cp, w.y, ui);
+  }
+  return make_float2(ur, ui);
+}
+
+// ------------------------------------------------------------------ control warp
+// Worker warps: compensated per-warp partial into shared memory.
+__device__ __forceinline__ void c_worker_partial(SmemC& S, float s, float c) {
+  ff_warp_sum(s, c);
+  if ((threadIdx.x & 31) == 0) {
+    S.ws[threadIdx.x >> 5] = s;
+    S.wc[threadIdx.x >> 5] = c;
+  }
+}
+
+// Control warp: CTA partial (FP64) into `part`, grid barrier, and the global
+// sum in one fixed order, returned to all lanes.
+__device__ bool c_ctl_reduce(SmemC& S, int NW, double* part, unsigned* bar, unsigned& gen, int* status,
+                             long long timeout_ns, double& sum, long long& spin) {
+  const int lane = threadIdx.x & 31;
+  const int G = gridDim.x;
+  double v = lane < NW ? (double)S.ws[lane] + (double)S.wc[lane] : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) part[blockIdx.x] = v;
+  __syncwarp();
+  if (!warp_grid_barrier(bar, gen, status, timeout_ns, spin)) return false;
+  double a[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int i = lane + 32 * j;
+    a[j] = i < G ? __ldcg(part + i) : 0.0;
+  }
+  double t = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) t += a[j];
+  for (int i = lane + 256; i < G; i += 32) t += __ldcg(part + i);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  sum = __shfl_sync(0xffffffffu, t, 0);
+  return true;
+}
+
+// Phase-A constants for iteration `it` (lane 0 scalars, per-site table over lanes).
+template <int FAMILY, class Op>
+__device__ void c_const_a(SmemC& S, const Op& op, int it) {
+  const int lane = threadIdx.x & 31;
+  const double sk = S.scale[it];
+  if (lane == 0) {
+    CConst& c = S.ca;
+    if constexpr (FAMILY == kFamilySpin) {
+      const double cz = S.scal[0] * sk;
+      c.cz = (float)cz;
+      c.ch = (float)(cz * op.J2);
+      c.cx = (float)(S.bsite_raw[0] * sk);
+    } else {
+      for (int o = 0; o < op.nops; ++o) c.co[o] = (float)(S.scal[o] * sk);
+    }
+    c.cp = it > 1 ? (float)(-S.beta[it - 1] * S.scale[it - 1]) : 0.f;
+    c.use_prev = it > 1;
+  }
+  if constexpr (FAMILY == kFamilySpin) {
+    if (!op.uniform)
+      for (int i = lane; i < op.N; i += 32) S.bx[i] = (float)(S.bsite_raw[i] * sk);
+  }
+}
+
+__device__ double c_estimate(SmemC& S, int k, double ts) {
+  small_expm_e1(k, S.alpha + 1, S.beta + 1, ts, S.yr, S.yi, S.tr, S.ti);
+  return S.beta0 * S.beta[k] * hypot(S.yr[k - 1], S.yi[k - 1]);
+}
+
+// ------------------------------------------------------------------ the kernel
+template <int FAMILY, class Op>
+__global__ void __launch_bounds__(800, 1) k_propagate_c64(PropParams p, Op op) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmemC& S = *reinterpret_cast<SmemC*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int NW = (int)(blockDim.x >> 5) - 1;
+  const bool ctl = (tid >> 5) == NW;
+  const int lane = tid & 31;
+  const bool lead = ctl && lane == 0;
+  const int dim = p.dim;
+  const int G = gridDim.x;
+  const int chunk = (dim + G - 1) / G;  // one contiguous chunk per CTA
+  const int wstep = NW * 32;
+  const int wx0 = blockIdx.x * chunk + tid;
+  const int wxe = min(dim, (blockIdx.x + 1) * chunk);
+  const int ncoef = 1 + p.nV;
+  unsigned gen = 0;
+  double* partA = p.partials;  // three slots: phase A, phase B, reconstruction
+  double* partB = partA + G;
+  double* partR = partA + 2 * G;
+  DevStatus* st = p.st;
+  const bool glead = (blockIdx.x == 0) && lead;
+  long long tacc[6] = {0, 0, 0, 0, 0, 0};
+  const bool fixed_k = p.tol <= 0.0;
+  const bool forced = p.f_nsub != nullptr;
+  long long fpos = st->forced_pos;
+  long long rpos = st->rec_pos;
+  long long n_app = 0, n_sub = 0;
+  int max_k = 0;
+  double max_err = 0.0;
+
+  auto Q = [&](int i) -> float2* { return p.qbasis32 + (size_t)(i - 1) * dim; };
+
+  // ---------------- psi (complex128) -> q_1 (complex64), ||q_1||^2, finiteness
+  {
+    if (!ctl) {
+      float s = 0.f, c = 0.f;
+      int bad = 0;
+      for (int x = wx0; x < wxe; x += wstep) {
+        const double2 v = p.psi[x];
+        bad |= !(isfinite(v.x) && isfinite(v.y));
+        const float2 f = make_float2((float)v.x, (float)v.y);
+        Q(1)[x] = f;
+        ff_add_prod(s, c, f.x, f.x);
+        ff_add_prod(s, c, f.y, f.y);
+      }
+      if (__any_sync(0xffffffffu, bad) && lane == 0) atomicCAS(&st->status, 0, (int)CFET_ENAN);
+      c_worker_partial(S, s, c);
+    }
+    __syncthreads();
+    if (ctl) {
+      double sum;
+      if (!c_ctl_reduce(S, NW, partB, p.bar, gen, &st->status, p.timeout_ns, sum, tacc[5])) {
+        if (lane == 0) S.abort_flag = 1;
+      } else if (lane == 0) {
+        S.abort_flag = ld_volatile_i32(&st->status) != 0;
+        S.beta0 = sqrt(sum);
+      }
+    }
+    __syncthreads();
+    if (S.abort_flag) return;
+  }
+
+  for (long long e = 0; e < p.nexp; ++e) {
+    if (tid < ncoef) S.scal[tid] = p.scal[e * ncoef + tid];
+    __syncthreads();
+    if constexpr (FAMILY == kFamilySpin) {
+      if (ctl && lane < op.N) {
+        double bi = 0.0;
+        for (int k = 0; k < p.nV; ++k) bi = fma(S.scal[1 + k], __ldg(op.xf + k * op.N + lane), bi);
+        S.bsite_raw[lane] = bi;
+      }
+      __syncthreads();
+    }
+    const long long eg = p.exp_base + e;
+    const bool last_exp = (e == p.nexp - 1);
+    const int nforced = forced ? p.f_nsub[eg] : 0;
+    double remaining = p.tau;
+    int nsub_e = 0;
+    while (true) {
+      if (nsub_e >= p.max_substeps || (forced && nsub_e >= nforced)) {
+        if (glead) atomicCAS(&st->status, 0, (int)CFET_EKRYLOV);
+        return;
+      }
+      int kf = -1, hf = 0;
+      if (forced) {
+        kf = p.f_k[fpos];
+        hf = p.f_h[fpos];
+      }
+      const double beta0 = S.beta0;
+      int acc_k = 0, acc_h = 0;
+      double acc_err = 0.0;
+      if (beta0 != 0.0) {
+        const int klimit = forced ? kf : p.m_max;
+        if (lead) {
+          S.scale[1] = 1.0 / beta0;
+          S.pend = 0;
+          S.stop_prev = 0;
+          S.accept_now = 0;
+          S.y_ready = 0;
+        }
+        if (ctl) {
+          __syncwarp();
+          c_const_a<FAMILY>(S, op, 1);
+        }
+        __syncthreads();
+        int it = 1;
+        for (;; ++it) {
+          // -------- phase A(it); deferred estimate of it-1 on the control warp
+          const int pend = S.pend;
+          if (!ctl) {
+            const CConst& c = S.ca;
+            const float2* q = Q(it);
+            const float2* qm = it > 1 ? Q(it - 1) : q;
+            float2* u = Q(it + 1);
+            float s = 0.f, cc = 0.f;
+            const long long tw0 = sm_clock();
+            for (int x = wx0; x < wxe; x += wstep) {
+              float2 hv;
+              if constexpr (FAMILY == kFamilySpin) hv = c_apply_spin(q, qm, x, op, c, S.bx);
+              else hv = c_apply_dia(q, qm, x, dim, op, c);
+              u[x] = hv;
+              const float2 v = q[x];
+              ff_add_prod(s, cc, v.x, hv.x);
+              ff_add_prod(s, cc, v.y, hv.y);
+            }
+            c_worker_partial(S, s, cc);
+            if (tid == 0) tacc[0] += sm_clock() - tw0;
+          } else if (pend) {
+            const double err = c_estimate(S, it - 1, remaining);
+            if (lane == 0) {
+              S.err_prev = err;
+              S.stop_prev = err <= p.tol * remaining / p.tau;
+              S.y_ready = S.stop_prev;
+            }
+            __syncwarp();
+          }
+          __syncthreads();
+          if (ctl) {
+            const long long tc0 = sm_clock(), sp0 = tacc[5];
+            double sum;
+            if (!c_ctl_reduce(S, NW, partA, p.bar, gen, &st->status, p.timeout_ns, sum, tacc[5])) {
+              if (lane == 0) S.abort_flag = 1;
+            } else if (lane == 0 && !S.stop_prev) {
+              // q_it holds the Lanczos vector times 1/scale[it]
+              const double s_it = S.scale[it];
+              const double alpha = sum * s_it;
+              S.alpha[it] = alpha;
+              S.am = (float)(-alpha * s_it);
+            }
+            if (lane == 0) tacc[1] += sm_clock() - tc0 - (tacc[5] - sp0);
+          }
+          __syncthreads();
+          if (S.abort_flag) return;
+          if (S.stop_prev) {  // the deferred estimate accepted it-1
+            it -= 1;
+            acc_err = S.err_prev;
+            break;
+          }
+          // -------- phase B(it): w = u - alpha s_it q_it, beta = ||w||
+          if (!ctl) {
+            const float am = S.am;
+            const float2* q = Q(it);
+            float2* u = Q(it + 1);
+            float s = 0.f, cc = 0.f;
+            const long long tw0 = sm_clock();
+            for (int x = wx0; x < wxe; x += wstep) {
+              const float2 v = q[x];
+              const float2 uu = u[x];
+              const float2 w = make_float2(fmaf(am, v.x, uu.x), fmaf(am, v.y, uu.y));
+              u[x] = w;
+              ff_add_prod(s, cc, w.x, w.x);
+              ff_add_prod(s, cc, w.y, w.y);
+            }
+            c_worker_partial(S, s, cc);
+            if (tid == 0) tacc[2] += sm_clock() - tw0;
+          }
+          __syncthreads();
+          if (ctl) {
+            const long long tc0 = sm_clock(), sp0 = tacc[5];
+            double sum;
+            if (!c_ctl_reduce(S, NW, partB, p.bar, gen, &st->status, p.timeout_ns, sum, tacc[5])) {
+              if (lane == 0) S.abort_flag = 1;
+            } else {
+              const double b = sqrt(sum);
+              const double prev_b = it > 1 ? S.beta[it - 1] : 0.0;
+              const bool breakdown = b <= 1e-13 * (fabs(S.alpha[it]) + prev_b + 1.0);
+              if (lane == 0) {
+                S.beta[it] = b;
+                S.scale[it + 1] = 1.0 / b;
+              }
+              __syncwarp();
+              int acc_flag = 0, pend_next = 0;
+              double err = 0.0;
+              if (forced) {
+                acc_flag = (it == kf);
+              } else if (fixed_k) {
+                acc_flag = (it == p.m_max) || breakdown;
+              } else if (breakdown) {
+                acc_flag = 1;
+              } else if (it >= p.m_min &&
+                         fabs(remaining) * gersh_width(it, S.alpha + 1, S.beta + 1) <= 2.0 * it) {
+                if (it < klimit) {
+                  pend_next = 1;  // estimate runs during the next apply
+                } else {
+                  err = c_estimate(S, it, remaining);
+                  acc_flag = err <= p.tol * remaining / p.tau;
+                }
+              }
+              if (lane == 0) {
+                S.accept_now = acc_flag;
+                S.pend = pend_next;
+                S.err_now = err;
+                S.y_ready = acc_flag && !forced && !fixed_k && !breakdown;
+              }
+              __syncwarp();
+              if (!acc_flag && it < klimit) c_const_a<FAMILY>(S, op, it + 1);
+            }
+            if (lane == 0) tacc[3] += sm_clock() - tc0 - (tacc[5] - sp0);
+          }
+          __syncthreads();
+          if (S.abort_flag) return;
+          if (S.accept_now) {
+            acc_err = S.err_now;
+            break;
+          }
+          if (it >= klimit) break;
+        }
+        acc_k = it;
+        const bool accepted = S.accept_now || S.stop_prev;
+        acc_h = 0;
+        if (forced) {
+          acc_h = hf;
+        } else if (!accepted) {
+          // halve the substep on the same basis until the estimate meets the
+          // proportional tolerance (control warp)
+          if (ctl) {
+            int hh = 0;
+            double err = 0.0;
+            const double width = gersh_width(it, S.alpha + 1, S.beta + 1);
+            for (int h = 1; h <= 40; ++h) {
+              const double ts = ldexp(remaining, -h);
+              if (!(fabs(ts) * width <= 2.0 * it)) continue;
+              err = c_estimate(S, it, ts);
+              if (err <= p.tol * ts / p.tau) { hh = h; break; }
+            }
+            if (lane == 0) { S.acc_h = hh; S.err_now = err; S.y_ready = hh > 0; }
+          }
+          __syncthreads();
+          acc_h = S.acc_h;
+          acc_err = S.err_now;
+          if (acc_h == 0) {
+            if (glead) atomicCAS(&st->status, 0, (int)CFET_EKRYLOV);
+            return;
+          }
+        }
+        n_app += acc_k;
+      }
+      const double ts = ldexp(remaining, -acc_h);
+      const bool final_rec = last_exp && acc_h == 0;
+      if (acc_k > 0) {
+        // -------- reconstruct q_1 <- beta0 sum_i y_i s_i q_i
+        if (ctl) {
+          if (!S.y_ready) small_expm_e1(acc_k, S.alpha + 1, S.beta + 1, ts, S.yr, S.yi, S.tr, S.ti);
+          __syncwarp();
+          for (int i = lane; i < acc_k; i += 32) {
+            const double f = beta0 * S.scale[i + 1];
+            S.cr[i] = (float)(f * S.yr[i]);
+            S.ci[i] = (float)(f * S.yi[i]);
+          }
+        }
+        __syncthreads();
+        if (!ctl) {
+          float s = 0.f, cc = 0.f;
+          const long long tw0 = sm_clock();
+          for (int x = wx0; x < wxe; x += wstep) {
+            float re = 0.f, im = 0.f;
+            for (int i = 0; i < acc_k; ++i) {
+              const float2 v = Q(i + 1)[x];
+              const float cr = S.cr[i], ci = S.ci[i];
+              re = fmaf(cr, v.x, fmaf(-ci, v.y, re));
+              im = fmaf(cr, v.y, fmaf(ci, v.x, im));
+            }
+            Q(1)[x] = make_float2(re, im);
+            if (final_rec) p.psi[x] = make_double2((double)re, (double)im);
+            ff_add_prod(s, cc, re, re);
+            ff_add_prod(s, cc, im, im);
+          }
+          c_worker_partial(S, s, cc);
+          if (tid == 0) tacc[4] += sm_clock() - tw0;
+        }
+        __syncthreads();
+        if (ctl) {
+          double sum;
+          if (!c_ctl_reduce(S, NW, partR, p.bar, gen, &st->status, p.timeout_ns, sum, tacc[5])) {
+            if (lane == 0) S.abort_flag = 1;
+          } else if (lane == 0) {
+            S.beta0 = sqrt(sum);
+          }
+        }
+        __syncthreads();
+        if (S.abort_flag) return;
+      }
+      if (glead && p.r_k != nullptr) {
+        if (rpos < p.r_cap) {
+          p.r_k[rpos] = acc_k;
+          p.r_h[rpos] = acc_h;
+        } else {
+          st->rec_overflow = 1;
+        }
+      }
+      rpos += 1;
+      if (forced) fpos += 1;
+      n_sub += 1;
+      nsub_e += 1;
+      if (acc_k > max_k) max_k = acc_k;
+      if (acc_err > max_err) max_err = acc_err;
+      if (acc_h == 0) break;
+      remaining -= ts;
+    }
+    if (glead && p.r_nsub != nullptr) p.r_nsub[eg] = nsub_e;
+  }
+  if (glead) {
+    st->forced_pos = fpos;
+    st->rec_pos = rpos;
+    st->n_exp += p.nexp;
+    st->n_sub += n_sub;
+    st->n_app += n_app;
+    if (max_k > st->max_k) st->max_k = max_k;
+    if (max_err > st->max_err) st->max_err = max_err;
+  }
+  if (tid == 0 || lead) {  // every CTA: mean and max of its phase times
+    for (int i = (tid == 0 ? 0 : 1); i < 6; i += 2) {
+      atomicAdd((unsigned long long*)&st->phase_ns[i], (unsigned long long)(tacc[i] / G));
+      atomicMax(&st->phase_max_ns[i], tacc[i]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+template <int FAMILY, class Op>
+static int launch_prop_c64(const PropParams& p, const Op& op, int grid, int block, void* stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = sizeof(SmemC);
+  cfg.stream = (cudaStream_t)stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return (int)cudaLaunchKernelEx(&cfg, k_propagate_c64<FAMILY, Op>, p, op);
+}
+
+int launch_propagate_spin_c64(const PropParams& p, const OpSpinC& op, int grid, int block, void* stream) {
+  return launch_prop_c64<kFamilySpin>(p, op, grid, block, stream);
+}
+int launch_propagate_dia_c64(const PropParams& p, const OpDiaC& op, int grid, int block, void* stream) {
+  return launch_prop_c64<kFamilyDia>(p, op, grid, block, stream);
+}
+
+int max_coresident_blocks_c64(int family, int block) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  // a few KB of shared memory: leave the unified storage to L1
+  cudaFuncSetAttribute(k_propagate_c64<kFamilySpin, OpSpinC>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  cudaFuncSetAttribute(k_propagate_c64<kFamilyDia, OpDiaC>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  cudaError_t e;
+  if (family == kFamilySpin)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_c64<kFamilySpin, OpSpinC>, block,
+                                                      sizeof(SmemC));
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_c64<kFamilyDia, OpDiaC>, block,
+                                                      sizeof(SmemC));
+  if (e != cudaSuccess) return -1;
+  return per * nsm;
+}
+
+}  // namespace cfet

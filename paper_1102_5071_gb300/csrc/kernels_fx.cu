@@ -40,12 +40,6 @@
 namespace cfet {
 
 // ------------------------------------------------------------------ fixed-point helpers
-// SM cycle counter, ordered with respect to surrounding memory operations.
-__device__ __forceinline__ long long fx_clk() {
-  long long t;
-  asm volatile("mov.u64 %0, %%clock64;" : "=l"(t) : : "memory");
-  return t;
-}
 constexpr int kFxBits = 57;  // stored |M| < 2^57
 // Per-thread exact 128-bit sums of products (< 2^115 each, at most 4096 per
 // thread) are shifted right by kRedShift before the CTA and grid reductions,
@@ -168,6 +162,7 @@ struct FxConstA {
   int s_d, s_diag, s_hop, s_x, s_p, s_nu;
   int pk, ph, px, pp;
   int use_prev;
+  int Eu;
   // dia: per operator P_o = shr128(sum VAL q, sh_pre[o]); term = fx_mul(m_op[o], P_o, s_op[o])
   long long m_op[1 + kMaxDrives];
   int sh_pre[1 + kMaxDrives];
@@ -193,6 +188,8 @@ struct SmemFx {
   // stage data
   double scal[1 + kMaxDrives];
   double bsite_raw[kMaxSites];
+  double bsum_raw, bmax_raw;  // sum and max over sites of |bsite_raw|
+  int eb;                     // exponent of the per-site table mb
   long long mb[kMaxSites];
   FxConstA ca;
   // phase B constants
@@ -286,41 +283,6 @@ __device__ __forceinline__ longlong2 fx_apply_dia(const longlong2* q, const long
 }
 
 // ------------------------------------------------------------------ control-warp helpers
-// Bounded grid barrier executed by the control warp only (lane 0 spins).
-__device__ bool fx_ctl_barrier(unsigned* bar, unsigned& gen, int* status, long long timeout_ns, long long& spin) {
-  const int lane = threadIdx.x & 31;
-  int ok = 1;
-  if (gridDim.x > 1 && lane == 0) {
-    const long long c0 = fx_clk();
-    const unsigned target = gen + 1;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&bar[0], 1u) + 1u;
-    if (arrived == gridDim.x) {
-      atomicExch(&bar[0], 0u);
-      __threadfence();
-      atomicExch(&bar[1], target);
-    } else {
-      const long long t0 = global_timer_ns();
-      unsigned spins = 0;
-      while (ld_volatile_u32(&bar[1]) != target) {
-        if ((++spins & 63u) == 0u) {
-          if (ld_volatile_i32(status) != 0) { ok = 0; break; }
-          if (global_timer_ns() - t0 > timeout_ns) {
-            atomicCAS(status, 0, (int)CFET_ETIMEOUT);
-            ok = 0;
-            break;
-          }
-        }
-      }
-    }
-    __threadfence();
-    spin += fx_clk() - c0;
-  }
-  gen += 1;
-  ok = __shfl_sync(0xffffffffu, ok, 0);
-  return ok != 0;
-}
-
 // Control warp: combine the workers' per-warp partials into this CTA's partial
 // (slot `part`), pass the grid barrier, and return the exact global sum (as
 // FP64) and the global max to all lanes.
@@ -338,7 +300,7 @@ __device__ bool fx_ctl_reduce(SmemFx& S, int NW, long long* part, unsigned* bar,
     part[3 * blockIdx.x + 2] = m;
   }
   __syncwarp();
-  if (!fx_ctl_barrier(bar, gen, status, timeout_ns, spin)) return false;
+  if (!warp_grid_barrier(bar, gen, status, timeout_ns, spin)) return false;
   lo = 0; hi = 0; m = 0;
   for (int i0 = 0; i0 < G; i0 += 256) {
     // issue all loads of this block of partials before combining them
@@ -382,11 +344,9 @@ __device__ __forceinline__ void fx_worker_partial(SmemFx& S, __int128 acc, long 
   }
 }
 
-// Phase-A constants (control lane 0): result exponent of
-// u = s_k H q_k - beta_{k-1} s_{k-1} q_{k-1} from the bound of every term,
-// normalising shifts and product shifts.
+// Scalar part of the phase-A constants (one lane).
 template <int FAMILY, class Op>
-__device__ void fx_const_a(SmemFx& S, const Op& op, int it) {
+__device__ void fx_const_a_scalars(SmemFx& S, const Op& op, int it) {
   FxConstA& c = S.ca;
   const double sk = S.scale[it];
   const int Ek = S.E[it];
@@ -399,15 +359,10 @@ __device__ void fx_const_a(SmemFx& S, const Op& op, int it) {
   if constexpr (FAMILY == kFamilySpin) {
     const double cz = S.scal[0] * sk;
     const double ch = cz * op.J2;
-    double bsum = 0.0, bmax = 0.0;
-    for (int i = 0; i < op.N; ++i) {
-      const double b = fabs(S.bsite_raw[i] * sk);
-      bsum += b;
-      bmax = fmax(bmax, b);
-    }
+    // sum and max of |b_i s_k| from the per-stage sums of |b_i|
+    const double bsum = fabs(sk) * S.bsum_raw, bmax = fabs(sk) * S.bmax_raw;
     B += (fabs(cz) * op.maxdz + fabs(ch) * (op.N - 1) + bsum) * Akr;
     const int Eu = fx_exp_for(B, kFxBits);
-    S.Eu = Eu;
     const Mant mcz = fx_mant(cz);
     const int ED = fx_exp_for(fabs(cz) * op.maxdz, 59);
     c.m_cz = mcz.m;
@@ -428,13 +383,13 @@ __device__ void fx_const_a(SmemFx& S, const Op& op, int it) {
     } else {
       const int eb = fx_exp_for(bmax, 62);
       c.s_nu = Eu - eb - (Ek - c.pk) - 64;
-      for (int i = 0; i < op.N; ++i)
-        S.mb[i] = fx_fold(__double2ll_rn(fx_scale2(S.bsite_raw[i] * sk, -eb)), c.s_nu);
+      S.eb = eb;
     }
+    c.Eu = Eu;
   } else {
     for (int o = 0; o < op.nops; ++o) B += fabs(S.scal[o] * sk) * op.maxrow[o] * Akr;
     const int Eu = fx_exp_for(B, kFxBits);
-    S.Eu = Eu;
+    c.Eu = Eu;
     for (int o = 0; o < op.nops; ++o) {
       const int Epre = fx_exp_for(op.maxrow[o] * Akr, 62);  // |P_o| < 2^62
       c.sh_pre[o] = Epre - op.E_op[o] - Ek;
@@ -447,9 +402,29 @@ __device__ void fx_const_a(SmemFx& S, const Op& op, int it) {
   const Mant mp = fx_mant(-bp);
   c.pp = it > 1 ? fx_norm_shift(S.A[it - 1]) : 0;
   c.m_p = mp.m;
-  c.s_p = S.Eu - mp.e - (it > 1 ? S.E[it - 1] - c.pp : 0) - 64;
+  c.s_p = c.Eu - mp.e - (it > 1 ? S.E[it - 1] - c.pp : 0) - 64;
   c.m_p = fx_fold(c.m_p, c.s_p);
   c.use_prev = it > 1;
+  S.Eu = c.Eu;
+}
+
+// Phase-A constants (called by the whole control warp: lane 0 computes the
+// scalars, the per-site table is split over the lanes): result exponent of
+// u = s_k H q_k - beta_{k-1} s_{k-1} q_{k-1} from the bound of every term,
+// normalising shifts and product shifts.
+template <int FAMILY, class Op>
+__device__ void fx_const_a(SmemFx& S, const Op& op, int it) {
+  const int lane = threadIdx.x & 31;
+  FxConstA& c = S.ca;
+  if (lane == 0) fx_const_a_scalars<FAMILY>(S, op, it);
+  __syncwarp();
+  if constexpr (FAMILY == kFamilySpin) {
+    if (!op.uniform) {
+      const double sk = S.scale[it];
+      for (int i = lane; i < op.N; i += 32)
+        S.mb[i] = fx_fold(__double2ll_rn(fx_scale2(S.bsite_raw[i] * sk, -S.eb)), c.s_nu);
+    }
+  }
 }
 
 // Error estimate of iteration k (control warp): err = beta0 beta_k |y_k| with
@@ -565,10 +540,22 @@ __global__ void __launch_bounds__(800, 1) k_propagate_fx(PropParams p, Op op) {
     if (tid < ncoef) S.scal[tid] = p.scal[e * ncoef + tid];
     __syncthreads();
     if constexpr (FAMILY == kFamilySpin) {
-      if (tid < op.N) {
+      if (ctl) {  // per-site transverse fields of this stage (N <= 30 lanes)
         double bi = 0.0;
-        for (int k = 0; k < p.nV; ++k) bi = fma(S.scal[1 + k], __ldg(op.xf + k * op.N + tid), bi);
-        S.bsite_raw[tid] = bi;
+        if (lane < op.N) {
+          for (int k = 0; k < p.nV; ++k) bi = fma(S.scal[1 + k], __ldg(op.xf + k * op.N + lane), bi);
+          S.bsite_raw[lane] = bi;
+        }
+        double bs = fabs(bi), bm = fabs(bi);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          bs += __shfl_xor_sync(0xffffffffu, bs, o);
+          bm = fmax(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+        }
+        if (lane == 0) {
+          S.bsum_raw = bs;
+          S.bmax_raw = bm;
+        }
       }
       __syncthreads();
     }
@@ -598,6 +585,9 @@ __global__ void __launch_bounds__(800, 1) k_propagate_fx(PropParams p, Op op) {
           S.stop_prev = 0;
           S.accept_now = 0;
           S.y_ready = 0;
+        }
+        if (ctl) {
+          __syncwarp();
           fx_const_a<FAMILY>(S, op, 1);
         }
         __syncthreads();
@@ -612,7 +602,7 @@ __global__ void __launch_bounds__(800, 1) k_propagate_fx(PropParams p, Op op) {
             longlong2* u = Q(it + 1);
             __int128 a2 = 0;
             long long mx = 0;
-            const long long tw0 = fx_clk();
+            const long long tw0 = sm_clock();
             for (int x = wx0; x < wxe; x += wstep) {
               longlong2 hv;
               if constexpr (FAMILY == kFamilySpin) hv = fx_apply_spin(q, qm, x, op, c, S.mb);
@@ -623,7 +613,7 @@ __global__ void __launch_bounds__(800, 1) k_propagate_fx(PropParams p, Op op) {
               mx = max(mx, fx_absmax(hv.x, hv.y));
             }
             fx_worker_partial(S, a2, mx);
-            if (tid == 0) tacc[0] += fx_clk() - tw0;
+            if (tid == 0) tacc[0] += sm_clock() - tw0;
           } else if (pend) {
             const double err = fx_estimate(S, it - 1, remaining);
             if (lane == 0) {
@@ -635,7 +625,7 @@ __global__ void __launch_bounds__(800, 1) k_propagate_fx(PropParams p, Op op) {
           }
           __syncthreads();
           if (ctl) {
-            const long long tc0 = fx_clk(), sp0 = tacc[5];
+            const long long tc0 = sm_clock(), sp0 = tacc[5];
             double sum;
             long long mxi;
             if (!fx_ctl_reduce(S, NW, partA, p.bar, gen, &st->status, p.timeout_ns, sum, mxi, tacc[5])) {
@@ -661,7 +651,7 @@ __global__ void __launch_bounds__(800, 1) k_propagate_fx(PropParams p, Op op) {
                 S.abort_flag = 1;
               }
             }
-            if (lane == 0) tacc[1] += fx_clk() - tc0 - (tacc[5] - sp0);
+            if (lane == 0) tacc[1] += sm_clock() - tc0 - (tacc[5] - sp0);
           }
           __syncthreads();
           if (S.abort_flag) return;
@@ -672,13 +662,13 @@ __global__ void __launch_bounds__(800, 1) k_propagate_fx(PropParams p, Op op) {
           }
           // -------- phase B(it): w = u - alpha s_it q_it, beta = ||w||
           if (!ctl) {
-            const int sh_u = S.sh_u, s_a = S.s_a, pk = S.pk_b;
+            const int sh_u = S.sh_u, pk = S.pk_b;
             const long long m_a = S.m_a;
             const longlong2* q = Q(it);
             longlong2* u = Q(it + 1);
             __int128 b2 = 0;
             long long mx = 0;
-            const long long tw0 = fx_clk();
+            const long long tw0 = sm_clock();
             for (int x = wx0; x < wxe; x += wstep) {
               const longlong2 v = q[x];
               const longlong2 uu = u[x];
@@ -689,11 +679,11 @@ __global__ void __launch_bounds__(800, 1) k_propagate_fx(PropParams p, Op op) {
               mx = max(mx, fx_absmax(wr, wi));
             }
             fx_worker_partial(S, b2, mx);
-            if (tid == 0) tacc[2] += fx_clk() - tw0;
+            if (tid == 0) tacc[2] += sm_clock() - tw0;
           }
           __syncthreads();
           if (ctl) {
-            const long long tc0 = fx_clk(), sp0 = tacc[5];
+            const long long tc0 = sm_clock(), sp0 = tacc[5];
             double sum;
             long long mxi;
             if (!fx_ctl_reduce(S, NW, partB, p.bar, gen, &st->status, p.timeout_ns, sum, mxi, tacc[5])) {
@@ -731,10 +721,11 @@ __global__ void __launch_bounds__(800, 1) k_propagate_fx(PropParams p, Op op) {
                 S.pend = pend_next;
                 S.err_now = err;
                 S.y_ready = acc_flag && !forced && !fixed_k && !breakdown;
-                if (!acc_flag && it < klimit) fx_const_a<FAMILY>(S, op, it + 1);
               }
+              __syncwarp();
+              if (!acc_flag && it < klimit) fx_const_a<FAMILY>(S, op, it + 1);
             }
-            if (lane == 0) tacc[3] += fx_clk() - tc0 - (tacc[5] - sp0);
+            if (lane == 0) tacc[3] += sm_clock() - tc0 - (tacc[5] - sp0);
           }
           __syncthreads();
           if (S.abort_flag) return;
@@ -810,7 +801,7 @@ __global__ void __launch_bounds__(800, 1) k_propagate_fx(PropParams p, Op op) {
           const double outscale = fx_scale2(1.0, S.Epsi);
           __int128 a2 = 0;
           long long mx = 0;
-          const long long tw0 = fx_clk();
+          const long long tw0 = sm_clock();
           for (int x = wx0; x < wxe; x += wstep) {
             long long re = 0, im = 0;
             for (int i = 0; i < acc_k; ++i) {
@@ -831,7 +822,7 @@ __global__ void __launch_bounds__(800, 1) k_propagate_fx(PropParams p, Op op) {
             mx = max(mx, fx_absmax(re, im));
           }
           fx_worker_partial(S, a2, mx);
-          if (tid == 0) tacc[4] += fx_clk() - tw0;
+          if (tid == 0) tacc[4] += sm_clock() - tw0;
         }
         __syncthreads();
         if (ctl) {

@@ -89,6 +89,14 @@ def test_create_validates_arguments(lib):
     assert _create(lib, ok_h0, [xf], [cb], opt)[0] == _capi.CFET_EINVAL
     opt.m_max, opt.block_size = 16, 48
     assert _create(lib, ok_h0, [xf], [cb], opt)[0] == _capi.CFET_EINVAL
+    # control-warp kernels (fixed point, complex64) take at most 2 x 384 + 32 threads
+    for prec in (_capi.CFET_PREC_FX, _capi.CFET_PREC_C64):
+        opt.block_size, opt.precision = 416, prec
+        assert _create(lib, ok_h0, [xf], [cb], opt)[0] == _capi.CFET_EINVAL
+    opt.block_size, opt.precision = 0, 7
+    st, _ = _create(lib, ok_h0, [xf], [cb], opt)
+    assert st == _capi.CFET_EINVAL and b"precision" in lib.cfet_last_error(None)
+    opt.precision = _capi.CFET_PREC_DEFAULT
     # DIA offsets out of range
     dia = P._op_struct(P.DIA(np.array([0, 7]), np.ones((2, 7))), keep)
     assert _create(lib, dia, [], [])[0] == _capi.CFET_EINVAL
