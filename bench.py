@@ -49,6 +49,10 @@ UNIT = "H_applies/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 flop x max SM clock
 
 
+# trace slots of the control-warp kernels (cfet_stats.phase_ns)
+PHASES = ("apply_loops", "apply_control", "orth_loops", "orth_control", "reconstruct_loops", "barrier_wait")
+
+
 def workload_config():
     return {
         "workload": f"driven XXZ chain N={N_SITES} (dim 2^{N_SITES}), {SCHEME} dt={DT}, Krylov tol={TOL}, "
@@ -319,12 +323,10 @@ def run_gpu(args):
             "cfet_steps_per_s": args.steps * ws / (ms_max * 1e-3),
             "krylov": {"applies_per_step": n_app / args.steps, "substeps": stats["n_substeps"],
                        "max_k": stats["max_k"], "max_err_est": stats["max_err_est"],
-                       "phase_ms": {k: v * 1e-6 for k, v in zip(
-                           ("apply", "apply_reduce", "orth", "orth_reduce_decide", "reconstruct",
-                            "reconstruct_reduce"), stats.get("phase_ns", [0] * 6))},
-                       "phase_max_ms": {k: v * 1e-6 for k, v in zip(
-                           ("apply", "apply_reduce", "orth", "orth_reduce_decide", "reconstruct",
-                            "reconstruct_reduce"), stats.get("phase_max_ns", [0] * 6))}},
+                       # SM clock cycles per CTA (mean, max over CTAs), in millions
+                       "phase_Mcycles": {k: v * 1e-6 for k, v in zip(PHASES, stats.get("phase_ns", [0] * 6))},
+                       "phase_max_Mcycles": {k: v * 1e-6 for k, v in zip(PHASES,
+                                                                           stats.get("phase_max_ns", [0] * 6))}},
             "roofline": roofline,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 16 * dim, "d2h_bytes_per_step": 16 * dim,
                     "steps": e2e_steps},

@@ -3,6 +3,8 @@
 Produces ``paper_1102_5071_gb300/libcfet_gb300.so`` from ``csrc/``.  Each
 translation unit is compiled in parallel, then linked with the static CUDA
 runtime.  Run ``python -m paper_1102_5071_gb300.build`` or call ``build()``.
+Extra nvcc flags (for example ``-DCFET_CTL_MAX_THREADS=544``) can be given in the
+environment variable ``CFET_NVCC_FLAGS``; a change of them triggers a rebuild.
 """
 
 from __future__ import annotations
@@ -22,6 +24,11 @@ LIB_PATH = os.path.join(PKG, LIB_NAME)
 BUILD_DIR = os.path.join(PKG, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS_STAMP = os.path.join(BUILD_DIR, "extra_flags.txt")
+
+
+def _extra_flags() -> list:
+    return os.environ.get("CFET_NVCC_FLAGS", "").split()
 SOURCES = ["kernels.cu", "kernels_fx.cu", "kernels_c64.cu", "capi.cu", "schemes.cpp", "noalloc.cu"]
 
 
@@ -35,7 +42,7 @@ def _nvcc() -> str:
 def _compile(nvcc: str, src: str, verbose: bool) -> str:
     obj = os.path.join(BUILD_DIR, os.path.splitext(src)[0] + ".o")
     cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3", "-I", INCLUDE,
-           "-c", os.path.join(CSRC, src), "-o", obj]
+           *_extra_flags(), "-c", os.path.join(CSRC, src), "-o", obj]
     if src.endswith(".cu"):
         cmd[1:1] = ["-Xptxas", "-v"] if verbose else []
     else:
@@ -50,6 +57,12 @@ def _compile(nvcc: str, src: str, verbose: bool) -> str:
 
 def _up_to_date() -> bool:
     if not os.path.exists(LIB_PATH):
+        return False
+    try:
+        with open(FLAGS_STAMP) as fh:
+            if fh.read() != " ".join(_extra_flags()):
+                return False
+    except OSError:
         return False
     t = os.path.getmtime(LIB_PATH)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "cfet.h"), __file__]
@@ -69,6 +82,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
     os.replace(tmp, LIB_PATH)
+    with open(FLAGS_STAMP, "w") as fh:
+        fh.write(" ".join(_extra_flags()))
     return LIB_PATH
 
 

@@ -15,6 +15,12 @@ constexpr int kMaxSites = 30;    // spin chains: dim = 2^N < 2^31
 constexpr int kMaxDiag = 32;     // DIA: stored diagonals over H0 and all V_k
 constexpr int kSmallTaylorTerms = 18;
 
+// Largest CTA (threads) of the kernels with a control warp (fixed point,
+// complex64): 2 x block_size workers + 32, block_size <= 384.
+#ifndef CFET_CTL_MAX_THREADS
+#define CFET_CTL_MAX_THREADS 800
+#endif
+
 // ---------------------------------------------------------------- schemes
 struct SchemeData {
   int id, order, s, M;

@@ -171,31 +171,39 @@ __device__ __forceinline__ void c_worker_partial(SmemC& S, float s, float c) {
   }
 }
 
-// Control warp: CTA partial (FP64) into `part`, grid barrier, and the global
-// sum in one fixed order, returned to all lanes.
-__device__ bool c_ctl_reduce(SmemC& S, int NW, double* part, unsigned* bar, unsigned& gen, int* status,
+// Control warp: the CTA's float-float partial into `part`, grid barrier, and
+// the global sum of all partials in one fixed order (float-float, rounded to
+// FP64 once), returned to all lanes.  Keeping the chain in FP32 pairs avoids
+// long dependent sequences on the 1/64-rate FP64 units.
+__device__ bool c_ctl_reduce(SmemC& S, int NW, float2* part, unsigned* bar, unsigned& gen, int* status,
                              long long timeout_ns, double& sum, long long& spin) {
   const int lane = threadIdx.x & 31;
   const int G = gridDim.x;
-  double v = lane < NW ? (double)S.ws[lane] + (double)S.wc[lane] : 0.0;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if (lane == 0) part[blockIdx.x] = v;
+  float s = lane < NW ? S.ws[lane] : 0.f, c = lane < NW ? S.wc[lane] : 0.f;
+  ff_warp_sum(s, c);
+  if (lane == 0) part[blockIdx.x] = make_float2(s, c);
   __syncwarp();
   if (!warp_grid_barrier(bar, gen, status, timeout_ns, spin)) return false;
-  double a[8];
+  float2 a[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int i = lane + 32 * j;
-    a[j] = i < G ? __ldcg(part + i) : 0.0;
+    a[j] = i < G ? __ldcg(part + i) : make_float2(0.f, 0.f);
   }
-  double t = 0.0;
+  s = 0.f;
+  c = 0.f;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) t += a[j];
-  for (int i = lane + 256; i < G; i += 32) t += __ldcg(part + i);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-  sum = __shfl_sync(0xffffffffu, t, 0);
+  for (int j = 0; j < 8; ++j) {
+    ff_two_sum(s, c, a[j].x);
+    c = __fadd_rn(c, a[j].y);
+  }
+  for (int i = lane + 256; i < G; i += 32) {
+    const float2 v = __ldcg(part + i);
+    ff_two_sum(s, c, v.x);
+    c = __fadd_rn(c, v.y);
+  }
+  ff_warp_sum(s, c);
+  sum = (double)__shfl_sync(0xffffffffu, s, 0) + (double)__shfl_sync(0xffffffffu, c, 0);
   return true;
 }
 
@@ -230,7 +238,7 @@ __device__ double c_estimate(SmemC& S, int k, double ts) {
 
 // ------------------------------------------------------------------ the kernel
 template <int FAMILY, class Op>
-__global__ void __launch_bounds__(800, 1) k_propagate_c64(PropParams p, Op op) {
+__global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropParams p, Op op) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmemC& S = *reinterpret_cast<SmemC*>(smem_raw);
   const int tid = threadIdx.x;
@@ -246,9 +254,10 @@ __global__ void __launch_bounds__(800, 1) k_propagate_c64(PropParams p, Op op) {
   const int wxe = min(dim, (blockIdx.x + 1) * chunk);
   const int ncoef = 1 + p.nV;
   unsigned gen = 0;
-  double* partA = p.partials;  // three slots: phase A, phase B, reconstruction
-  double* partB = partA + G;
-  double* partR = partA + 2 * G;
+  // three slots (phase A, phase B, reconstruction) of one float-float pair per CTA
+  float2* partA = reinterpret_cast<float2*>(p.partials);
+  float2* partB = partA + G;
+  float2* partR = partA + 2 * G;
   DevStatus* st = p.st;
   const bool glead = (blockIdx.x == 0) && lead;
   long long tacc[6] = {0, 0, 0, 0, 0, 0};
@@ -413,12 +422,14 @@ __global__ void __launch_bounds__(800, 1) k_propagate_c64(PropParams p, Op op) {
             if (!c_ctl_reduce(S, NW, partB, p.bar, gen, &st->status, p.timeout_ns, sum, tacc[5])) {
               if (lane == 0) S.abort_flag = 1;
             } else {
-              const double b = sqrt(sum);
+              // beta and 1/beta from one reciprocal square root
+              const double rb = sum > 0.0 ? rsqrt(sum) : 0.0;
+              const double b = sum * rb;
               const double prev_b = it > 1 ? S.beta[it - 1] : 0.0;
               const bool breakdown = b <= 1e-13 * (fabs(S.alpha[it]) + prev_b + 1.0);
               if (lane == 0) {
                 S.beta[it] = b;
-                S.scale[it + 1] = 1.0 / b;
+                S.scale[it + 1] = rb;
               }
               __syncwarp();
               int acc_flag = 0, pend_next = 0;

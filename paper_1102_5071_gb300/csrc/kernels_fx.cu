@@ -436,7 +436,7 @@ __device__ double fx_estimate(SmemFx& S, int k, double ts) {
 
 // ------------------------------------------------------------------ the kernel
 template <int FAMILY, class Op>
-__global__ void __launch_bounds__(800, 1) k_propagate_fx(PropParams p, Op op) {
+__global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropParams p, Op op) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmemFx& S = *reinterpret_cast<SmemFx*>(smem_raw);
   const int tid = threadIdx.x;
@@ -689,12 +689,14 @@ __global__ void __launch_bounds__(800, 1) k_propagate_fx(PropParams p, Op op) {
             if (!fx_ctl_reduce(S, NW, partB, p.bar, gen, &st->status, p.timeout_ns, sum, mxi, tacc[5])) {
               if (lane == 0) S.abort_flag = 1;
             } else {
-              const double b = fx_scale2(sqrt(sum), S.Ew);
+              // beta and 1/beta from one reciprocal square root
+              const double rb = sum > 0.0 ? rsqrt(sum) : 0.0;
+              const double b = fx_scale2(sum * rb, S.Ew);
               const double prev_b = it > 1 ? S.beta[it - 1] : 0.0;
               const bool breakdown = b <= 1e-13 * (fabs(S.alpha[it]) + prev_b + 1.0);
               if (lane == 0) {
                 S.beta[it] = b;
-                S.scale[it + 1] = 1.0 / b;
+                S.scale[it + 1] = fx_scale2(rb, -S.Ew);
                 S.E[it + 1] = S.Ew;
                 S.A[it + 1] = __ll2double_ru(mxi);
               }
