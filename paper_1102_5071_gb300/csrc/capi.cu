@@ -81,6 +81,11 @@ struct cfet_ctx {
 
 namespace {
 
+// Reduction / exchange scratch per CTA (8-byte words): the FP64 kernel uses 3
+// partials, the control-warp kernels 3 slots of at most 6 tagged words.
+constexpr size_t kPartialWordsPerCta = 18;
+constexpr int kMaxCtlGrid = 256;  // 32 lanes x 8 records per lane of the exchange
+
 thread_local std::string g_create_err;
 
 cfet_status fail(cfet_ctx* ctx, cfet_status s, const std::string& msg) {
@@ -199,6 +204,9 @@ cfet_status issue_sequence(cfet_ctx* ctx, const PropParams& base, long long nexp
   CK(cudaMemcpyAsync(ctx->d_scal, ctx->h_scal, table_bytes, cudaMemcpyHostToDevice, s), "scalar upload");
   CK(cudaMemsetAsync(ctx->d_st, 0, sizeof(DevStatus), s), "status reset");
   CK(cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned), s), "barrier reset");
+  // exchange records of the control-warp kernels: no stale tag may survive
+  CK(cudaMemsetAsync(ctx->d_partials, 0, kPartialWordsPerCta * (size_t)ctx->grid * sizeof(double), s),
+     "exchange reset");
   if (timed) CK(cudaEventRecordWithFlags(ctx->ev_k0, s, cudaEventRecordExternal), "timing event");
   for (long long e0 = 0; e0 < nexp; e0 += chunk) {
     const long long ne = (nexp - e0) < chunk ? (nexp - e0) : chunk;
@@ -557,6 +565,7 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
   int want = (dim + workers - 1) / workers;
   if (o.grid_size > 0) want = o.grid_size;
   ctx->grid = want < maxg ? want : maxg;
+  if (ctl_warp && ctx->grid > kMaxCtlGrid) ctx->grid = kMaxCtlGrid;  // record exchange limit
   if (ctx->grid < 1) ctx->grid = 1;
 
   if (ctx->precision == CFET_PREC_FX)
@@ -573,7 +582,8 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
       return fail(nullptr, CFET_EINVAL, "fixed-point precision: dimension too large for the grid, use CFET_PREC_F64");
     }
   }
-  CKC(cudaMalloc(&ctx->d_partials, 9 * (size_t)ctx->grid * sizeof(double)), "cudaMalloc(partials)");
+  CKC(cudaMalloc(&ctx->d_partials, kPartialWordsPerCta * (size_t)ctx->grid * sizeof(double)),
+      "cudaMalloc(partials)");
   CKC(cudaMalloc(&ctx->d_bar, 2 * sizeof(unsigned)), "cudaMalloc(barrier)");
   CKC(cudaMemset(ctx->d_bar, 0, 2 * sizeof(unsigned)), "barrier init");
   CKC(cudaMalloc(&ctx->d_st, sizeof(DevStatus)), "cudaMalloc(status)");

@@ -36,7 +36,7 @@ struct DevStatus {
   int status;          // cfet_status
   int max_k;
   int rec_overflow;
-  int pad;
+  unsigned tag_base;   // tags of the record exchange used so far (control-warp kernels)
   long long n_exp, n_sub, n_app;
   double max_err;
   long long rec_pos;   // next record slot

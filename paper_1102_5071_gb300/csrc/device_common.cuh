@@ -66,6 +66,86 @@ static __device__ bool warp_grid_barrier(unsigned* bar, unsigned& gen, int* stat
   return ok != 0;
 }
 
+// ------------------------------------------------------------------ tagged exchange
+// Grid-wide exchange of small per-CTA records, executed by one warp of each
+// CTA; it is the grid barrier of the kernels with a control warp.  A record is
+// W 32-bit payload words, each published as one 64-bit word
+// (tag << 32 | payload), so that a reader sees a payload together with its tag
+// (aligned 64-bit stores are single-copy atomic); readers wait until the words
+// of every CTA carry `tag`.  No atomics and no last-arriver step: one store and
+// one round of loads per exchange.  Lane l reads the records of CTAs
+// l, l + 32, ..., l + 32 (kExchMaxPerLane - 1) in that order and passes each to
+// acc.add(); acc.reset() starts every polling round.  `fence` orders the CTA's
+// earlier global stores before its record (writer) and the records before the
+// CTA's later loads (reader); it is needed when other CTAs will read vectors
+// written before the exchange.  Returns false in every lane when the wait
+// limit expired (CFET_ETIMEOUT recorded) or another CTA reported an error.
+constexpr int kExchMaxPerLane = 8;  // grids of at most 256 CTAs
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <int W, class Acc>
+static __device__ bool ctl_exchange(unsigned long long* rec, const unsigned (&mine)[W], unsigned tag, bool fence,
+                                    int* status, long long timeout_ns, long long& spin, Acc& acc) {
+  const int lane = threadIdx.x & 31;
+  const int G = gridDim.x;
+  const long long c0 = sm_clock();
+  if (lane == 0) {
+    if (fence) __threadfence();
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+      st_relaxed_u64(rec + (size_t)blockIdx.x * W + w, ((unsigned long long)tag << 32) | mine[w]);
+  }
+  __syncwarp();
+  int ok = 1;
+  const long long t0 = global_timer_ns();
+  unsigned rounds = 0;
+  while (true) {
+    acc.reset();
+    int ready = 1;
+#pragma unroll
+    for (int j = 0; j < kExchMaxPerLane; ++j) {
+      const int i = lane + 32 * j;
+      if (i < G) {
+        unsigned v[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          const unsigned long long x = ld_relaxed_u64(rec + (size_t)i * W + w);
+          v[w] = (unsigned)x;
+          ready &= (unsigned)(x >> 32) == tag;
+        }
+        acc.add(v);
+      }
+    }
+    if (__all_sync(0xffffffffu, ready)) break;
+    if ((++rounds & 15u) == 0u) {
+      int bad = 0;
+      if (lane == 0) {
+        if (ld_volatile_i32(status) != 0) {
+          bad = 1;
+        } else if (global_timer_ns() - t0 > timeout_ns) {
+          atomicCAS(status, 0, (int)CFET_ETIMEOUT);
+          bad = 1;
+        }
+      }
+      if (__shfl_sync(0xffffffffu, bad, 0)) {
+        ok = 0;
+        break;
+      }
+    }
+  }
+  if (fence) __threadfence();
+  if (lane == 0) spin += sm_clock() - c0;
+  return ok != 0;
+}
+
 // Bounded grid-wide barrier (arrival counter + generation).  Returns false in
 // every thread of the CTA when the wait limit expired or another CTA reported
 // an error; the first CTA to time out records CFET_ETIMEOUT.

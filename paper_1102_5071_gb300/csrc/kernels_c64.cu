@@ -171,37 +171,31 @@ __device__ __forceinline__ void c_worker_partial(SmemC& S, float s, float c) {
   }
 }
 
-// Control warp: the CTA's float-float partial into `part`, grid barrier, and
-// the global sum of all partials in one fixed order (float-float, rounded to
-// FP64 once), returned to all lanes.  Keeping the chain in FP32 pairs avoids
-// long dependent sequences on the 1/64-rate FP64 units.
-__device__ bool c_ctl_reduce(SmemC& S, int NW, float2* part, unsigned* bar, unsigned& gen, int* status,
+// Float-float accumulation of the exchanged CTA partials (fixed order per lane).
+struct FFAcc {
+  float s, c;
+  __device__ void reset() { s = 0.f; c = 0.f; }
+  __device__ void add(const unsigned (&v)[2]) {
+    ff_two_sum(s, c, __uint_as_float(v[0]));
+    c = __fadd_rn(c, __uint_as_float(v[1]));
+  }
+};
+
+// Control warp: publish the CTA's float-float partial, exchange records with
+// every CTA (the grid barrier), and return the global sum, accumulated in one
+// fixed order and rounded to FP64 once, to all lanes.  Keeping the chain in
+// FP32 pairs avoids long dependent sequences on the 1/64-rate FP64 units.
+__device__ bool c_ctl_reduce(SmemC& S, int NW, unsigned long long* part, unsigned tag, bool fence, int* status,
                              long long timeout_ns, double& sum, long long& spin) {
   const int lane = threadIdx.x & 31;
-  const int G = gridDim.x;
   float s = lane < NW ? S.ws[lane] : 0.f, c = lane < NW ? S.wc[lane] : 0.f;
   ff_warp_sum(s, c);
-  if (lane == 0) part[blockIdx.x] = make_float2(s, c);
-  __syncwarp();
-  if (!warp_grid_barrier(bar, gen, status, timeout_ns, spin)) return false;
-  float2 a[8];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int i = lane + 32 * j;
-    a[j] = i < G ? __ldcg(part + i) : make_float2(0.f, 0.f);
-  }
-  s = 0.f;
-  c = 0.f;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    ff_two_sum(s, c, a[j].x);
-    c = __fadd_rn(c, a[j].y);
-  }
-  for (int i = lane + 256; i < G; i += 32) {
-    const float2 v = __ldcg(part + i);
-    ff_two_sum(s, c, v.x);
-    c = __fadd_rn(c, v.y);
-  }
+  const unsigned mine[2] = {__float_as_uint(__shfl_sync(0xffffffffu, s, 0)),
+                            __float_as_uint(__shfl_sync(0xffffffffu, c, 0))};
+  FFAcc acc;
+  if (!ctl_exchange<2>(part, mine, tag, fence, status, timeout_ns, spin, acc)) return false;
+  s = acc.s;
+  c = acc.c;
   ff_warp_sum(s, c);
   sum = (double)__shfl_sync(0xffffffffu, s, 0) + (double)__shfl_sync(0xffffffffu, c, 0);
   return true;
@@ -253,11 +247,13 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
   const int wx0 = blockIdx.x * chunk + tid;
   const int wxe = min(dim, (blockIdx.x + 1) * chunk);
   const int ncoef = 1 + p.nV;
+  // record exchange: three slots (phase A, phase B, reconstruction) of one
+  // float-float pair (two tagged words) per CTA; tags continue across launches
+  const unsigned tag0 = (unsigned)ld_volatile_i32((const int*)&p.st->tag_base);
   unsigned gen = 0;
-  // three slots (phase A, phase B, reconstruction) of one float-float pair per CTA
-  float2* partA = reinterpret_cast<float2*>(p.partials);
-  float2* partB = partA + G;
-  float2* partR = partA + 2 * G;
+  unsigned long long* partA = reinterpret_cast<unsigned long long*>(p.partials);
+  unsigned long long* partB = partA + 2 * G;
+  unsigned long long* partR = partA + 4 * G;
   DevStatus* st = p.st;
   const bool glead = (blockIdx.x == 0) && lead;
   long long tacc[6] = {0, 0, 0, 0, 0, 0};
@@ -290,7 +286,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
     __syncthreads();
     if (ctl) {
       double sum;
-      if (!c_ctl_reduce(S, NW, partB, p.bar, gen, &st->status, p.timeout_ns, sum, tacc[5])) {
+      if (!c_ctl_reduce(S, NW, partB, tag0 + (++gen), true, &st->status, p.timeout_ns, sum, tacc[5])) {
         if (lane == 0) S.abort_flag = 1;
       } else if (lane == 0) {
         S.abort_flag = ld_volatile_i32(&st->status) != 0;
@@ -379,7 +375,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
           if (ctl) {
             const long long tc0 = sm_clock(), sp0 = tacc[5];
             double sum;
-            if (!c_ctl_reduce(S, NW, partA, p.bar, gen, &st->status, p.timeout_ns, sum, tacc[5])) {
+            if (!c_ctl_reduce(S, NW, partA, tag0 + (++gen), false, &st->status, p.timeout_ns, sum, tacc[5])) {
               if (lane == 0) S.abort_flag = 1;
             } else if (lane == 0 && !S.stop_prev) {
               // q_it holds the Lanczos vector times 1/scale[it]
@@ -419,7 +415,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
           if (ctl) {
             const long long tc0 = sm_clock(), sp0 = tacc[5];
             double sum;
-            if (!c_ctl_reduce(S, NW, partB, p.bar, gen, &st->status, p.timeout_ns, sum, tacc[5])) {
+            if (!c_ctl_reduce(S, NW, partB, tag0 + (++gen), true, &st->status, p.timeout_ns, sum, tacc[5])) {
               if (lane == 0) S.abort_flag = 1;
             } else {
               // beta and 1/beta from one reciprocal square root
@@ -534,7 +530,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
         __syncthreads();
         if (ctl) {
           double sum;
-          if (!c_ctl_reduce(S, NW, partR, p.bar, gen, &st->status, p.timeout_ns, sum, tacc[5])) {
+          if (!c_ctl_reduce(S, NW, partR, tag0 + (++gen), true, &st->status, p.timeout_ns, sum, tacc[5])) {
             if (lane == 0) S.abort_flag = 1;
           } else if (lane == 0) {
             S.beta0 = sqrt(sum);
@@ -563,6 +559,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
     if (glead && p.r_nsub != nullptr) p.r_nsub[eg] = nsub_e;
   }
   if (glead) {
+    st->tag_base = tag0 + gen;
     st->forced_pos = fpos;
     st->rec_pos = rpos;
     st->n_exp += p.nexp;

@@ -283,44 +283,44 @@ __device__ __forceinline__ longlong2 fx_apply_dia(const longlong2* q, const long
 }
 
 // ------------------------------------------------------------------ control-warp helpers
-// Control warp: combine the workers' per-warp partials into this CTA's partial
-// (slot `part`), pass the grid barrier, and return the exact global sum (as
-// FP64) and the global max to all lanes.
-__device__ bool fx_ctl_reduce(SmemFx& S, int NW, long long* part, unsigned* bar, unsigned& gen, int* status,
+// Exact accumulation of exchanged CTA records: 128-bit sum (words 0-3) and
+// int64 max (words 4-5).
+struct FxAcc {
+  unsigned long long lo;
+  long long hi, m;
+  __device__ void reset() { lo = 0; hi = 0; m = 0; }
+  __device__ void add(const unsigned (&v)[6]) {
+    const unsigned long long l2 = ((unsigned long long)v[1] << 32) | v[0];
+    const long long h2 = (long long)(((unsigned long long)v[3] << 32) | v[2]);
+    const long long m2 = (long long)(((unsigned long long)v[5] << 32) | v[4]);
+    const unsigned long long t = lo + l2;
+    hi = hi + h2 + (t < lo ? 1 : 0);
+    lo = t;
+    m = m > m2 ? m : m2;
+  }
+};
+
+// Control warp: combine the workers' per-warp partials into this CTA's record,
+// exchange records with every CTA (the grid barrier), and return the exact
+// global sum (as FP64) and the global max to all lanes.
+__device__ bool fx_ctl_reduce(SmemFx& S, int NW, unsigned long long* part, unsigned tag, bool fence, int* status,
                               long long timeout_ns, double& sum, long long& mxi, long long& spin) {
   const int lane = threadIdx.x & 31;
-  const int G = gridDim.x;
   unsigned long long lo = 0;
   long long hi = 0, m = 0;
   if (lane < NW) { lo = S.wlo[lane]; hi = S.whi[lane]; m = S.wmx[lane]; }
   fx_warp_reduce(lo, hi, m);
-  if (lane == 0) {
-    part[3 * blockIdx.x + 0] = (long long)lo;
-    part[3 * blockIdx.x + 1] = hi;
-    part[3 * blockIdx.x + 2] = m;
-  }
-  __syncwarp();
-  if (!warp_grid_barrier(bar, gen, status, timeout_ns, spin)) return false;
-  lo = 0; hi = 0; m = 0;
-  for (int i0 = 0; i0 < G; i0 += 256) {
-    // issue all loads of this block of partials before combining them
-    unsigned long long l2[8];
-    long long h2[8], m2[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int i = i0 + lane + 32 * j;
-      l2[j] = i < G ? (unsigned long long)__ldcg(part + 3 * i + 0) : 0ull;
-      h2[j] = i < G ? __ldcg(part + 3 * i + 1) : 0ll;
-      m2[j] = i < G ? __ldcg(part + 3 * i + 2) : 0ll;
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const unsigned long long s = lo + l2[j];
-      hi = hi + h2[j] + (s < lo ? 1 : 0);
-      lo = s;
-      m = m > m2[j] ? m : m2[j];
-    }
-  }
+  lo = __shfl_sync(0xffffffffu, lo, 0);
+  hi = __shfl_sync(0xffffffffu, hi, 0);
+  m = __shfl_sync(0xffffffffu, m, 0);
+  const unsigned mine[6] = {(unsigned)lo, (unsigned)(lo >> 32), (unsigned)hi,
+                            (unsigned)((unsigned long long)hi >> 32), (unsigned)m,
+                            (unsigned)((unsigned long long)m >> 32)};
+  FxAcc acc;
+  if (!ctl_exchange<6>(part, mine, tag, fence, status, timeout_ns, spin, acc)) return false;
+  lo = acc.lo;
+  hi = acc.hi;
+  m = acc.m;
   fx_warp_reduce(lo, hi, m);
   lo = __shfl_sync(0xffffffffu, lo, 0);
   hi = __shfl_sync(0xffffffffu, hi, 0);
@@ -453,12 +453,14 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
   const int wx0 = blockIdx.x * chunk + tid;  // workers only
   const int wxe = min(dim, (blockIdx.x + 1) * chunk);
   const int ncoef = 1 + p.nV;
+  // record exchange: three slots (phase A, phase B, reconstruction) of six
+  // tagged words per CTA; two uses of one slot are always separated by an
+  // exchange on another slot; tags continue across launches
+  const unsigned tag0 = (unsigned)ld_volatile_i32((const int*)&p.st->tag_base);
   unsigned gen = 0;
-  // three partial slots (phase A, phase B, reconstruction): two uses of one
-  // slot are always separated by a grid barrier on another slot
-  long long* partA = reinterpret_cast<long long*>(p.partials);
-  long long* partB = partA + 3 * G;
-  long long* partR = partA + 6 * G;
+  unsigned long long* partA = reinterpret_cast<unsigned long long*>(p.partials);
+  unsigned long long* partB = partA + 6 * G;
+  unsigned long long* partR = partA + 12 * G;
   DevStatus* st = p.st;
   const bool glead = (blockIdx.x == 0) && lead;
   // trace (see cfet_stats.phase_ns): worker loop times by thread 0, control
@@ -493,7 +495,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
       // the max bit pattern is reduced in the int64 max lane
       double sum;
       long long bits;
-      if (!fx_ctl_reduce(S, NW, partA, p.bar, gen, &st->status, p.timeout_ns, sum, bits, tacc[5])) {
+      if (!fx_ctl_reduce(S, NW, partA, tag0 + (++gen), false, &st->status, p.timeout_ns, sum, bits, tacc[5])) {
         if (lane == 0) S.abort_flag = 1;
       } else if (lane == 0) {
         S.abort_flag = 0;
@@ -525,7 +527,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
     if (ctl) {
       double sum;
       long long mxi;
-      if (!fx_ctl_reduce(S, NW, partB, p.bar, gen, &st->status, p.timeout_ns, sum, mxi, tacc[5])) {
+      if (!fx_ctl_reduce(S, NW, partB, tag0 + (++gen), true, &st->status, p.timeout_ns, sum, mxi, tacc[5])) {
         if (lane == 0) S.abort_flag = 1;
       } else if (lane == 0) {
         S.beta0 = fx_scale2(sqrt(sum), S.E[1]);
@@ -628,7 +630,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
             const long long tc0 = sm_clock(), sp0 = tacc[5];
             double sum;
             long long mxi;
-            if (!fx_ctl_reduce(S, NW, partA, p.bar, gen, &st->status, p.timeout_ns, sum, mxi, tacc[5])) {
+            if (!fx_ctl_reduce(S, NW, partA, tag0 + (++gen), false, &st->status, p.timeout_ns, sum, mxi, tacc[5])) {
               if (lane == 0) S.abort_flag = 1;
             } else if (lane == 0 && !S.stop_prev) {
               const double s_it = S.scale[it];
@@ -686,7 +688,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
             const long long tc0 = sm_clock(), sp0 = tacc[5];
             double sum;
             long long mxi;
-            if (!fx_ctl_reduce(S, NW, partB, p.bar, gen, &st->status, p.timeout_ns, sum, mxi, tacc[5])) {
+            if (!fx_ctl_reduce(S, NW, partB, tag0 + (++gen), true, &st->status, p.timeout_ns, sum, mxi, tacc[5])) {
               if (lane == 0) S.abort_flag = 1;
             } else {
               // beta and 1/beta from one reciprocal square root
@@ -830,7 +832,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
         if (ctl) {
           double sum;
           long long mxi;
-          if (!fx_ctl_reduce(S, NW, partR, p.bar, gen, &st->status, p.timeout_ns, sum, mxi, tacc[5])) {
+          if (!fx_ctl_reduce(S, NW, partR, tag0 + (++gen), true, &st->status, p.timeout_ns, sum, mxi, tacc[5])) {
             if (lane == 0) S.abort_flag = 1;
           } else if (lane == 0) {
             S.beta0 = fx_scale2(sqrt(sum), S.Epsi);
@@ -861,6 +863,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
     if (glead && p.r_nsub != nullptr) p.r_nsub[eg] = nsub_e;
   }
   if (glead) {
+    st->tag_base = tag0 + gen;
     st->forced_pos = fpos;
     st->rec_pos = rpos;
     st->n_exp += p.nexp;
