@@ -49,6 +49,12 @@ UNIT = "H_applies/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 flop x max SM clock
 
 
+# DRAM bytes (read + write) per Lanczos iteration of the persistent kernel,
+# from one ncu capture of the same kernel build on the 2-step case (76
+# iterations): see profiles/.  Must be reset to None whenever the kernel
+# changes and re-measured.
+DRAM_BYTES_PER_ITERATION = {"fx": 2.831831e9 / 76, "c64": 0.838948e9 / 76, "f64": None}
+
 # trace slots of the control-warp kernels (cfet_stats.phase_ns)
 PHASES = ("apply_loops", "apply_control", "orth_loops", "orth_control", "reconstruct_loops", "barrier_wait")
 
@@ -297,8 +303,13 @@ def run_gpu(args):
         cpu = cpu_baseline_sample()
 
     if args.precision in ("fx", "c64"):
+        per_it = DRAM_BYTES_PER_ITERATION[args.precision]
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": achieved_gbs / hbm_peak, "traffic": None,
+                    "frac": achieved_gbs / hbm_peak,
+                    "traffic": per_it * n_app / math.ceil(args.steps / 256) if per_it is not None else None,
+                    "traffic_note": "per launch: ncu DRAM read+write bytes per Lanczos iteration (2-step "
+                                    "capture) x the launch's iterations; algorithmic bytes per launch: %.4g"
+                                    % (bytes_ / math.ceil(args.steps / 256)),
                     "kernel": "k_propagate_fx (persistent Lanczos, int64 fixed-point vectors)"
                     if args.precision == "fx" else
                     "k_propagate_c64 (persistent Lanczos, complex64 vectors, FP64-class reductions)",
