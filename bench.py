@@ -495,6 +495,78 @@ def run_study_sizes(args):
     return 0
 
 
+def run_study_batch(args):
+    """256 driven XXZ chains with N uniform in {10..16} (dims 1024..65536),
+    per-instance fields, A ~ U[0.5, 2], omega ~ U[1, 3], CF6:5Opt, dt = 0.02,
+    --steps steps (500 = T 10), tol 1e-10: the batched launch in FP64 and
+    complex64 after the autotuner picked each plan, against the single-instance
+    FP64 propagator run instance by instance (timed over --baseline-steps steps
+    and scaled per step).  Final-state error of the complex64 batch is stated
+    against the FP64 batch."""
+    import torch
+    import paper_1102_5071_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    cfg = W.BATCH
+    insts = W.chain_batch(cfg["n"], cfg["n_lo"], cfg["n_hi"])
+    chains = [P.Chain(c.N, c.J, c.Delta, c.h, c.xfield, None, c.A, c.omega, 0.0) for c in insts]
+    host = [W.random_state(c.psi_seed, 1 << c.N) for c in insts]
+    dims = np.array([1 << c.N for c in insts], dtype=np.float64)
+    order, dt, tol, nsteps = cfg["order"], cfg["dt"], cfg["tol"], args.steps
+    out = {}
+    finals = {}
+    for prec in ("f64", "c64"):
+        bp = P.BatchPropagator(chains, m_max=cfg["m_max"], precision=prec)
+        t = time.perf_counter()
+        plan = bp.tune(0.0, dt, order=order, tol=tol, nsteps=1)
+        tune_s = time.perf_counter() - t
+        dev = [torch.from_numpy(h).cuda() for h in host]
+        bp.propagate(dev, 0.0, dt, 1, order=order, tol=tol)        # warm-up step
+        dev = [torch.from_numpy(h).cuda() for h in host]
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        st = bp.propagate(dev, 0.0, dt, nsteps, order=order, tol=tol)
+        wall = time.perf_counter() - t
+        kms = bp.kernel_time_ms()
+        n_app = np.array([x["n_applies"] for x in st], dtype=np.float64)
+        finals[prec] = [d.cpu().numpy() for d in dev]
+        out[prec] = {"plan": plan, "tune_s": tune_s, "kernel_ms": kms, "wall_s": wall,
+                     "H_applies": float(n_app.sum()), "H_applies_per_s": float(n_app.sum()) / (kms * 1e-3),
+                     "element_applies_per_s": float((n_app * dims).sum()) / (kms * 1e-3),
+                     "cfet_steps_per_s": nsteps * len(insts) / (kms * 1e-3),
+                     "max_k": max(x["max_k"] for x in st)}
+        bp.close()
+        del dev
+    err = max(np.linalg.norm(a - b) for a, b in zip(finals["c64"], finals["f64"]))
+    out["c64"]["final_state_error_vs_f64_batch_max"] = float(err)
+    # single-instance FP64 propagator, instance by instance
+    nb = args.baseline_steps
+    tot_ms, tot_app = 0.0, 0.0
+    for c, h in zip(insts, host):
+        prop = P.Propagator(P.XXZChain(c.N, c.J, c.Delta, c.h), [P.XField(c.N, c.xfield)], [c.drive],
+                            m_max=cfg["m_max"], precision="f64")
+        x = torch.from_numpy(h).cuda()
+        prop.propagate(x, 0.0, dt, 1, order=order, tol=tol)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        s2 = prop.propagate(x, dt, dt, nb, order=order, tol=tol)
+        ev1.record()
+        torch.cuda.synchronize()
+        tot_ms += ev0.elapsed_time(ev1)
+        tot_app += s2["n_applies"]
+        prop.close()
+    single_ms_per_step = tot_ms / nb
+    out["single_instance_f64"] = {"ms_per_batch_step": single_ms_per_step, "steps_timed": nb,
+                                  "H_applies_per_s": tot_app / (tot_ms * 1e-3)}
+    for prec in ("f64", "c64"):
+        out[prec]["speedup_vs_single_instance_f64"] = single_ms_per_step * nsteps / out[prec]["kernel_ms"]
+    print(json.dumps({"study": "batch: %d driven XXZ chains N=%d..%d, CF6:5Opt dt=%g, %d steps, tol %g, m<=%d"
+                      % (len(insts), cfg["n_lo"], cfg["n_hi"], dt, nsteps, tol, cfg["m_max"]),
+                      "sum_dims": float(dims.sum()), **out}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -508,8 +580,10 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="accuracy study: final-state error and throughput per (order, dt) over T")
     ap.add_argument("--sweep-T", type=float, default=20.0)
-    ap.add_argument("--study", choices=["atom", "sizes"],
-                    help="extra measurements: the grid atom, or the chain at N = 20..26")
+    ap.add_argument("--study", choices=["atom", "sizes", "batch"],
+                    help="extra measurements: the grid atom, the chain at N = 20..26, the 256-chain batch")
+    ap.add_argument("--baseline-steps", type=int, default=10,
+                    help="batch study: steps of the single-instance baseline per instance")
     ap.add_argument("--block-size", type=int, default=0,
                     help="threads per CTA of the FP64 kernel; the fixed-point kernel uses 2x this many workers + 1 control warp")
     args = ap.parse_args()
@@ -523,6 +597,8 @@ def main():
         return run_study_atom(args)
     if args.study == "sizes":
         return run_study_sizes(args)
+    if args.study == "batch":
+        return run_study_batch(args)
     return run_gpu(args)
 
 

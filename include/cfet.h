@@ -290,6 +290,82 @@ cfet_status cfet_expv_chain_static(int32_t nsites, double J, double Delta, const
                                    double c0, double c1, double tau, void* psi, double tol, int32_t m_max,
                                    void* stream, cfet_stats* stats);
 
+/* ------------------------------------------------------------------------ */
+/* Batched propagation of many driven XXZ chains                            */
+/* ------------------------------------------------------------------------ */
+/* Many independent instances of uneven Hilbert dimension, each a CFET
+ * propagation exactly as cfet_propagate (Sec. 4 Eq. (Ucf), Sec. 7
+ * Eq. (OmGLeg), Sec. 8.1 Krylov with its own adaptive dimensions and
+ * substeps), run in one persistent launch (no counterpart in the paper).
+ *
+ * One instance: the open XXZ chain of CFET_OP_XXZ_CHAIN (nsites, J, Delta,
+ * h[nsites]) driven by f(t) sum_i a_i X_i.  The drive is the host callback
+ * f(t, user) when f is non-NULL, else the built-in A cos(omega t + phase)
+ * (evaluated on the host in FP64, once per Gauss-Legendre node and step).
+ * h and a are copied at create.                                             */
+typedef struct cfet_chain {
+  int32_t nsites;            /* [1, 24]                                      */
+  double J, Delta;
+  const double* h;           /* [nsites]                                     */
+  const double* a;           /* [nsites]                                     */
+  cfet_drive_fn f;           /* NULL: built-in cosine drive                  */
+  void* user;
+  double A, omega, phase;
+} cfet_chain;
+
+typedef struct cfet_batch cfet_batch;  /* opaque, owned by the library     */
+
+/* Schedule of a batched launch.  The grid is a set of thread-block clusters
+ * of cluster_size CTAs with `threads` threads each that take work items in
+ * order of decreasing work.  An instance with at least coop_min_sites sites
+ * is one item spread over all CTAs of a cluster (cluster-wide reductions in
+ * distributed shared memory); smaller instances are grouped cluster_size to
+ * an item, one per CTA.  tuned_ms: kernel time of the tuning run that chose
+ * the plan (0 when set by hand or default).                                 */
+typedef struct cfet_batch_plan {
+  int32_t cluster_size;      /* 1, 2, 4 or 8                                 */
+  int32_t threads;           /* 128, 256 or 512                              */
+  int32_t coop_min_sites;
+  float tuned_ms;
+} cfet_batch_plan;
+
+/* Create a batch of n chains.  opt: m_max, m_min, max_substeps as for
+ * cfet_create; precision CFET_PREC_F64 (also for CFET_PREC_DEFAULT and a
+ * NULL opt) or CFET_PREC_C64 (CFET_PREC_FX: CFET_EINVAL); other fields
+ * ignored.  The library owns all device memory
+ * (Krylov bases of (m_max + 1) x 2^nsites elements per instance).  Errors:
+ * CFET_EINVAL (argument), CFET_ENODEV, CFET_ENOMEM; message in
+ * cfet_batch_last_error(NULL).                                              */
+cfet_status cfet_batch_create(cfet_batch** out, int32_t n, const cfet_chain* chains, const cfet_options* opt);
+void cfet_batch_destroy(cfet_batch* b);
+const char* cfet_batch_last_error(const cfet_batch* b);
+int32_t cfet_batch_size(const cfet_batch* b);
+
+/* nsteps CFET steps of order `order` (2, 4, 6, 8; default schemes as
+ * cfet_propagate) from t0 with step dt for every instance.  psi: host array
+ * of n device pointers, psi[i] complex128[2^nsites_i], 16-byte aligned,
+ * caller-owned, updated in place.  forced / record: NULL or arrays of n
+ * decision logs as in cfet_propagate_ex (per instance).  stats: NULL or
+ * cfet_stats[n].  Synchronises `stream`.  Returns the first non-OK device
+ * status over the instances (CFET_EKRYLOV, CFET_ENAN); the per-instance
+ * statuses are in stats.                                                    */
+cfet_status cfet_batch_propagate(cfet_batch* b, void* const* psi, double t0, double dt, int64_t nsteps,
+                                 int32_t order, double krylov_tol, void* stream, const cfet_decisions* forced,
+                                 cfet_decisions* record, cfet_stats* stats);
+
+/* Autotuner: runs nsteps steps of the given propagation on internal states
+ * (normalised pseudo-random vectors, reset before every candidate) for every
+ * candidate plan (cluster size 1, 2, 4, 8 x 128, 256, 512 threads x three
+ * thresholds) that fits on the device, keeps the fastest as the batch's plan
+ * and returns it in `chosen` (may be NULL).  Caller states are not touched. */
+cfet_status cfet_batch_tune(cfet_batch* b, double t0, double dt, int32_t order, double krylov_tol, int64_t nsteps,
+                            void* stream, cfet_batch_plan* chosen);
+cfet_status cfet_batch_get_plan(const cfet_batch* b, cfet_batch_plan* plan);
+cfet_status cfet_batch_set_plan(cfet_batch* b, const cfet_batch_plan* plan);
+
+/* Device time in milliseconds of the last batched launch.                  */
+cfet_status cfet_batch_kernel_time_ms(cfet_batch* b, float* ms);
+
 /* Dimension and drive-operator count of ctx (for bindings).                 */
 int64_t cfet_dim(const cfet_ctx* ctx);
 int32_t cfet_num_drives(const cfet_ctx* ctx);

@@ -263,9 +263,153 @@ class Propagator:
         return stats.as_dict()
 
 
+# ---------------------------------------------------------------- batches
+@dataclass
+class Chain:
+    """One instance of a batch: the open XXZ chain (N, J, Delta, h) driven by
+    f(t) sum_i a_i X_i with f a Python callable, or, when drive is None, the
+    built-in A cos(omega t + phase) evaluated by the library."""
+    N: int
+    J: float
+    Delta: float
+    h: np.ndarray
+    a: np.ndarray
+    drive: object = None
+    A: float = 0.0
+    omega: float = 0.0
+    phase: float = 0.0
+
+
+def _decisions(nexp, log, keep):
+    nsub = np.array([len(x) for x in log], dtype=np.int32)
+    ks = np.array([k for x in log for k, _ in x], dtype=np.int32)
+    hs = np.array([h for x in log for _, h in x], dtype=np.int32)
+    keep += [nsub, ks, hs]
+    return _capi.cfet_decisions(nexp, nsub.ctypes.data_as(_capi.c_int32_p), ks.ctypes.data_as(_capi.c_int32_p),
+                                hs.ctypes.data_as(_capi.c_int32_p), len(ks), len(ks))
+
+
+class BatchPropagator:
+    """Many driven XXZ chains of uneven size propagated in one persistent launch
+    (thread-block clusters for the large instances, a measured plan)."""
+
+    def __init__(self, chains, *, m_max=16, m_min=2, max_substeps=64, precision="f64"):
+        lib = _capi.load()
+        self._keep = []
+        arr = (_capi.cfet_chain * len(chains))()
+        self._cbs = []
+        self.dims = []
+        for i, c in enumerate(chains):
+            h = np.ascontiguousarray(c.h, dtype=np.float64)
+            a = np.ascontiguousarray(c.a, dtype=np.float64)
+            self._keep += [h, a]
+            s = arr[i]
+            s.nsites, s.J, s.Delta = c.N, c.J, c.Delta
+            s.h = h.ctypes.data_as(_capi.c_double_p)
+            s.a = a.ctypes.data_as(_capi.c_double_p)
+            if c.drive is not None:
+                cb = _capi.DRIVE_FN(lambda t, u, fn=c.drive: float(fn(t)))
+                self._cbs.append(cb)
+                s.f = cb
+            s.A, s.omega, s.phase = c.A, c.omega, c.phase
+            self.dims.append(1 << c.N)
+        self._arr = arr
+        opt = _capi.cfet_options()
+        lib.cfet_options_default(C.byref(opt))
+        opt.m_max, opt.m_min, opt.max_substeps = m_max, m_min, max_substeps
+        opt.precision = _capi.PRECISIONS[precision]
+        b = C.c_void_p()
+        st = lib.cfet_batch_create(C.byref(b), len(chains), arr, C.byref(opt))
+        if st != 0:
+            raise CfetError(st, lib.cfet_batch_last_error(None).decode())
+        self._lib, self._b, self.n = lib, b, len(chains)
+        self.max_substeps = max_substeps
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.cfet_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _raise(self, st):
+        if st != 0:
+            raise CfetError(st, self._lib.cfet_batch_last_error(self._b).decode())
+
+    @property
+    def plan(self):
+        p = _capi.cfet_batch_plan()
+        self._raise(self._lib.cfet_batch_get_plan(self._b, C.byref(p)))
+        return {"cluster_size": p.cluster_size, "threads": p.threads, "coop_min_sites": p.coop_min_sites,
+                "tuned_ms": p.tuned_ms}
+
+    def set_plan(self, cluster_size, threads, coop_min_sites):
+        p = _capi.cfet_batch_plan(cluster_size, threads, coop_min_sites, 0.0)
+        self._raise(self._lib.cfet_batch_set_plan(self._b, C.byref(p)))
+
+    def tune(self, t0, dt, order=6, tol=1e-10, nsteps=1, stream=None):
+        p = _capi.cfet_batch_plan()
+        self._raise(self._lib.cfet_batch_tune(self._b, float(t0), float(dt), int(order), float(tol), int(nsteps),
+                                              _stream_handle(stream), C.byref(p)))
+        return self.plan
+
+    def propagate(self, psis, t0, dt, nsteps, order=6, tol=1e-10, stream=None, forced=None, record=False):
+        """psis: list of CUDA complex128 tensors (one per instance), updated in
+        place.  forced: per-instance decision logs to replay; record: also
+        return the per-instance logs.  Returns per-instance stats."""
+        if len(psis) != self.n:
+            raise ValueError(f"expected {self.n} states")
+        for t, d in zip(psis, self.dims):
+            _check_vec(t, d, "psi")
+        ptrs = (C.c_void_p * self.n)(*[t.data_ptr() for t in psis])
+        s = {2: 1, 4: 2, 6: 5, 8: 11}.get(order, 1)
+        nexp = int(nsteps) * s
+        keep = []
+        fd = None
+        if forced is not None:
+            fd = (_capi.cfet_decisions * self.n)(*[_decisions(nexp, lg, keep) for lg in forced])
+        rd = None
+        if record:
+            rd = (_capi.cfet_decisions * self.n)()
+            bufs = []
+            for i in range(self.n):
+                cap = max(1, nexp * self.max_substeps)
+                rn, rk, rh = (np.zeros(nexp, np.int32), np.zeros(cap, np.int32), np.zeros(cap, np.int32))
+                bufs.append((rn, rk, rh))
+                rd[i] = _capi.cfet_decisions(nexp, rn.ctypes.data_as(_capi.c_int32_p),
+                                             rk.ctypes.data_as(_capi.c_int32_p), rh.ctypes.data_as(_capi.c_int32_p),
+                                             cap, 0)
+        stats = (_capi.cfet_stats * self.n)()
+        st = self._lib.cfet_batch_propagate(self._b, ptrs, float(t0), float(dt), int(nsteps), int(order), float(tol),
+                                            _stream_handle(stream), fd, rd, stats)
+        self._raise(st)
+        out = [stats[i].as_dict() for i in range(self.n)]
+        if record:
+            logs = []
+            for i, (rn, rk, rh) in enumerate(bufs):
+                lg, pos = [], 0
+                for e in range(nexp):
+                    m = int(rn[e])
+                    lg.append([(int(rk[pos + q]), int(rh[pos + q])) for q in range(m)])
+                    pos += m
+                logs.append(lg)
+            return out, logs
+        return out
+
+    def kernel_time_ms(self):
+        ms = C.c_float()
+        self._raise(self._lib.cfet_batch_kernel_time_ms(self._b, C.byref(ms)))
+        return float(ms.value)
+
+
 def build():
     from .build import build as _b
     return _b()
 
 
-__all__ = ["Propagator", "XXZChain", "XField", "DIA", "scheme_info", "CfetError", "SCHEME_IDS", "build"]
+__all__ = ["Propagator", "BatchPropagator", "Chain", "XXZChain", "XField", "DIA", "scheme_info", "CfetError",
+           "SCHEME_IDS", "build"]

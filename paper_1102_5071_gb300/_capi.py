@@ -54,6 +54,17 @@ class cfet_decisions(C.Structure):
 
 DRIVE_FN = C.CFUNCTYPE(C.c_double, C.c_double, C.c_void_p)
 
+
+class cfet_chain(C.Structure):
+    _fields_ = [("nsites", C.c_int32), ("J", C.c_double), ("Delta", C.c_double), ("h", c_double_p),
+                ("a", c_double_p), ("f", DRIVE_FN), ("user", C.c_void_p), ("A", C.c_double),
+                ("omega", C.c_double), ("phase", C.c_double)]
+
+
+class cfet_batch_plan(C.Structure):
+    _fields_ = [("cluster_size", C.c_int32), ("threads", C.c_int32), ("coop_min_sites", C.c_int32),
+                ("tuned_ms", C.c_float)]
+
 _lib = None
 
 
@@ -93,6 +104,18 @@ def load() -> C.CDLL:
         "cfet_expv_chain_static": (C.c_int, [C.c_int32, C.c_double, C.c_double, c_double_p, c_double_p,
                                              C.c_double, C.c_double, C.c_double, vp, C.c_double, C.c_int32, vp,
                                              C.POINTER(cfet_stats)]),
+        "cfet_batch_create": (C.c_int, [C.POINTER(vp), C.c_int32, C.POINTER(cfet_chain), C.POINTER(cfet_options)]),
+        "cfet_batch_destroy": (None, [vp]),
+        "cfet_batch_last_error": (C.c_char_p, [vp]),
+        "cfet_batch_size": (C.c_int32, [vp]),
+        "cfet_batch_propagate": (C.c_int, [vp, C.POINTER(vp), C.c_double, C.c_double, C.c_int64, C.c_int32,
+                                           C.c_double, vp, C.POINTER(cfet_decisions), C.POINTER(cfet_decisions),
+                                           C.POINTER(cfet_stats)]),
+        "cfet_batch_tune": (C.c_int, [vp, C.c_double, C.c_double, C.c_int32, C.c_double, C.c_int64, vp,
+                                      C.POINTER(cfet_batch_plan)]),
+        "cfet_batch_get_plan": (C.c_int, [vp, C.POINTER(cfet_batch_plan)]),
+        "cfet_batch_set_plan": (C.c_int, [vp, C.POINTER(cfet_batch_plan)]),
+        "cfet_batch_kernel_time_ms": (C.c_int, [vp, C.POINTER(C.c_float)]),
         "cfet_dim": (C.c_int64, [vp]),
         "cfet_num_drives": (C.c_int32, [vp]),
     }
@@ -107,4 +130,7 @@ def load() -> C.CDLL:
 EXPORTED = ["cfet_options_default", "cfet_scheme_info", "cfet_create", "cfet_destroy", "cfet_last_error",
             "cfet_apply", "cfet_expv", "cfet_propagate", "cfet_propagate_ex", "cfet_propagate_host", "cfet_sync",
             "cfet_kernel_time_ms", "cfet_expv_chain_static",
+            "cfet_batch_create", "cfet_batch_destroy", "cfet_batch_last_error", "cfet_batch_size",
+            "cfet_batch_propagate", "cfet_batch_tune", "cfet_batch_get_plan", "cfet_batch_set_plan",
+            "cfet_batch_kernel_time_ms",
             "cfet_dim", "cfet_num_drives"]

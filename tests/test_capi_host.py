@@ -124,3 +124,45 @@ def test_binding_refuses_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_capi, "library_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="missing"):
         _capi.load()
+
+
+def _chain_arr(specs, keep):
+    arr = (_capi.cfet_chain * len(specs))()
+    for i, (N, h, a) in enumerate(specs):
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        keep += [h, a]
+        arr[i].nsites, arr[i].J, arr[i].Delta = N, 1.0, 0.5
+        arr[i].h = h.ctypes.data_as(_capi.c_double_p) if h.size else None
+        arr[i].a = a.ctypes.data_as(_capi.c_double_p)
+        arr[i].A, arr[i].omega = 1.0, 2.0
+    return arr
+
+
+def test_batch_create_validates_arguments(lib):
+    keep = []
+    b = C.c_void_p()
+    ok = _chain_arr([(4, np.zeros(4), np.ones(4))], keep)
+    assert lib.cfet_batch_create(C.byref(b), 0, ok, None) == _capi.CFET_EINVAL
+    big = _chain_arr([(25, np.zeros(25), np.ones(25))], keep)
+    assert lib.cfet_batch_create(C.byref(b), 1, big, None) == _capi.CFET_EINVAL
+    assert b"nsites" in lib.cfet_batch_last_error(None)
+    nan = _chain_arr([(3, np.array([0.0, np.nan, 0.0]), np.ones(3))], keep)
+    assert lib.cfet_batch_create(C.byref(b), 1, nan, None) == _capi.CFET_EINVAL
+    nul = _chain_arr([(3, np.zeros(0), np.ones(3))], keep)
+    assert lib.cfet_batch_create(C.byref(b), 1, nul, None) == _capi.CFET_EINVAL
+    opt = _capi.cfet_options()
+    lib.cfet_options_default(C.byref(opt))
+    opt.precision = _capi.CFET_PREC_FX      # batches run FP64 or complex64
+    assert lib.cfet_batch_create(C.byref(b), 1, ok, C.byref(opt)) == _capi.CFET_EINVAL
+    assert not b.value
+
+
+def test_batch_no_device_gives_enodev(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    keep = []
+    b = C.c_void_p()
+    ok = _chain_arr([(4, np.zeros(4), np.ones(4)), (6, np.zeros(6), np.ones(6))], keep)
+    assert lib.cfet_batch_create(C.byref(b), 2, ok, None) == _capi.CFET_ENODEV and not b.value

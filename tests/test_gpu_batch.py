@@ -1,0 +1,194 @@
+"""GPU parity of the batched launch (many driven XXZ chains of uneven size in
+one persistent launch) against the FP64 oracle run instance by instance.
+
+Every plan kind is exercised: one CTA per instance, instances spread over
+thread-block clusters of 2, 4 and 8 CTAs (cluster-wide reductions), and
+mixtures.  FP64 results are compared by ||psi_gpu - psi_oracle||_2 <= 1e-10
+per instance with the oracle's Krylov decisions replayed; complex64 results
+by the rounding budget n_substeps * 64 * 2^-24 derived in test_gpu_c64.py.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import cfet as OC, operators as O
+
+pytestmark = pytest.mark.gpu
+
+PARITY = 1e-10
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1102_5071_gb300.build import build
+    build()
+    return torch
+
+
+def _instances(sizes, seed=3):
+    u = W.uniform(seed, 2 * len(sizes))
+    out = []
+    for i, N in enumerate(sizes):
+        out.append(W.ChainInstance(N, 1.0, 0.5, W.uniform(200 + i, N, -1, 1), 0.5 + 1.5 * u[i],
+                                   1.0 + 2.0 * u[len(sizes) + i], 300 + i))
+    return out
+
+
+def _batch(insts, **kw):
+    import paper_1102_5071_gb300 as P
+    chains = [P.Chain(c.N, c.J, c.Delta, c.h, c.xfield, None, c.A, c.omega, 0.0) for c in insts]
+    return P.BatchPropagator(chains, **kw)
+
+
+def _oracle(c, psi0, t0, dt, nsteps, order, tol, m, log=True):
+    op = O.SpinChain(c.N, c.J, c.Delta, c.h, [c.xfield])
+    return OC.propagate(op, psi0, t0, dt, nsteps, order, [c.drive], tol, m, return_log=log, max_substeps=200)
+
+
+def _states(torch, insts):
+    host = [W.random_state(c.psi_seed, 1 << c.N) for c in insts]
+    return host, [torch.from_numpy(h).cuda() for h in host]
+
+
+SIZES = [1, 3, 5, 8, 9, 10, 10, 11]
+PLANS = [(1, 128, 99), (2, 256, 10), (4, 512, 9), (8, 128, 1), (4, 256, 99)]
+
+
+@pytest.mark.parametrize("plan", PLANS)
+def test_batch_f64_forced_matches_oracle(torch_cuda, plan):
+    insts = _instances(SIZES)
+    bp = _batch(insts, m_max=16, max_substeps=200, precision="f64")
+    bp.set_plan(*plan)
+    host, dev = _states(torch_cuda, insts)
+    t0, dt, n, order, tol = 0.3, 0.05, 4, 4, 1e-11
+    refs, logs = [], []
+    for c, h in zip(insts, host):
+        r, lg, _ = _oracle(c, h, t0, dt, n, order, tol, 16)
+        refs.append(r)
+        logs.append(lg)
+    stats = bp.propagate(dev, t0, dt, n, order=order, tol=tol, forced=logs)
+    for i, (c, r) in enumerate(zip(insts, refs)):
+        err = np.linalg.norm(dev[i].cpu().numpy() - r)
+        assert err <= PARITY, (i, c.N, err)
+        assert stats[i]["n_exp"] == n * 2 and stats[i]["status"] == 0
+
+
+@pytest.mark.parametrize("plan", [(1, 256, 99), (4, 256, 9)])
+def test_batch_f64_adaptive_decisions(torch_cuda, plan):
+    insts = _instances([6, 9, 10, 12])
+    bp = _batch(insts, m_max=16, max_substeps=200, precision="f64")
+    bp.set_plan(*plan)
+    host, dev = _states(torch_cuda, insts)
+    t0, dt, n, order, tol = 0.0, 0.02, 5, 6, 1e-10
+    stats, logs = bp.propagate(dev, t0, dt, n, order=order, tol=tol, record=True)
+    for i, (c, h) in enumerate(zip(insts, host)):
+        r, lg, na = _oracle(c, h, t0, dt, n, order, tol, 16)
+        same = sum(a == b for a, b in zip(lg, logs[i])) / len(lg)
+        assert same >= 0.95, (i, same)
+        if lg == logs[i]:
+            assert np.linalg.norm(dev[i].cpu().numpy() - r) <= PARITY
+            assert stats[i]["n_applies"] == na
+
+
+@pytest.mark.parametrize("plan", [(1, 128, 99), (4, 256, 10)])
+def test_batch_c64_within_budget(torch_cuda, plan):
+    insts = _instances([4, 7, 10, 11])
+    bp = _batch(insts, m_max=16, max_substeps=200, precision="c64")
+    bp.set_plan(*plan)
+    host, dev = _states(torch_cuda, insts)
+    t0, dt, n, order, tol = 0.1, 0.05, 5, 6, 1e-9
+    logs, refs = [], []
+    for c, h in zip(insts, host):
+        r, lg, _ = _oracle(c, h, t0, dt, n, order, tol, 16)
+        refs.append(r)
+        logs.append(lg)
+    stats = bp.propagate(dev, t0, dt, n, order=order, tol=tol, forced=logs)
+    for i in range(len(insts)):
+        err = np.linalg.norm(dev[i].cpu().numpy() - refs[i])
+        assert err <= stats[i]["n_substeps"] * 64 * 2.0 ** -24, (i, err)
+
+
+def test_batch_callback_drive_and_site_fields(torch_cuda):
+    import paper_1102_5071_gb300 as P
+    N = 9
+    h = W.uniform(11, N, -1, 1)
+    a = W.uniform(12, N, 0.2, 1.0)       # site-dependent field: non-uniform path
+    drive = lambda t: 0.7 * math.sin(1.3 * t) + 0.2
+    bp = P.BatchPropagator([P.Chain(N, 0.8, 1.2, h, a, drive), P.Chain(5, 1.0, 0.0, h[:5], a[:5], None, 1.0, 2.0, 0.3)],
+                           m_max=20, max_substeps=200, precision="f64")
+    bp.set_plan(2, 128, 9)
+    psi = [W.random_state(21, 1 << N), W.random_state(22, 32)]
+    dev = [torch_cuda.from_numpy(x).cuda() for x in psi]
+    ops = [O.SpinChain(N, 0.8, 1.2, h, [a]), O.SpinChain(5, 1.0, 0.0, h[:5], [a[:5]])]
+    drives = [[drive], [lambda t: 1.0 * math.cos(2.0 * t + 0.3)]]
+    refs, logs = [], []
+    for op, d, x in zip(ops, drives, psi):
+        r, lg, _ = OC.propagate(op, x, 0.0, 0.04, 6, 8, d, 1e-11, 20, return_log=True, max_substeps=200)
+        refs.append(r)
+        logs.append(lg)
+    bp.propagate(dev, 0.0, 0.04, 6, order=8, tol=1e-11, forced=logs)
+    for i in range(2):
+        assert np.linalg.norm(dev[i].cpu().numpy() - refs[i]) <= PARITY
+
+
+def test_batch_tune_then_propagate(torch_cuda):
+    insts = _instances([8, 10, 10, 12, 12, 13])
+    bp = _batch(insts, m_max=16, precision="f64")
+    host, dev = _states(torch_cuda, insts)
+    plan = bp.tune(0.0, 0.02, order=6, tol=1e-10, nsteps=1)
+    assert plan["tuned_ms"] > 0 and plan["cluster_size"] in (1, 2, 4, 8) and plan["threads"] in (128, 256, 512)
+    assert [np.array_equal(d.cpu().numpy(), h) for d, h in zip(dev, host)] == [True] * len(host)  # untouched
+    logs, refs = [], []
+    for c, h in zip(insts, host):
+        r, lg, _ = _oracle(c, h, 0.0, 0.02, 3, 6, 1e-10, 16)
+        refs.append(r)
+        logs.append(lg)
+    bp.propagate(dev, 0.0, 0.02, 3, order=6, tol=1e-10, forced=logs)
+    for i in range(len(insts)):
+        assert np.linalg.norm(dev[i].cpu().numpy() - refs[i]) <= PARITY
+
+
+def test_batch_matches_single_instance_path(torch_cuda):
+    import paper_1102_5071_gb300 as P
+    insts = _instances([10, 12])
+    bp = _batch(insts, m_max=16, precision="f64")
+    bp.set_plan(4, 256, 12)
+    host, dev = _states(torch_cuda, insts)
+    bp.propagate(dev, 0.0, 0.02, 4, order=6, tol=0.0)   # fixed K: no decision can differ
+    for c, h, d in zip(insts, host, dev):
+        prop = P.Propagator(P.XXZChain(c.N, c.J, c.Delta, c.h), [P.XField(c.N, c.xfield)], [c.drive], m_max=16,
+                            precision="f64")
+        t = torch_cuda.from_numpy(h).cuda()
+        prop.propagate(t, 0.0, 0.02, 4, order=6, tol=0.0)
+        assert np.linalg.norm(t.cpu().numpy() - d.cpu().numpy()) <= 1e-12
+
+
+def test_batch_edge_cases(torch_cuda):
+    torch = torch_cuda
+    import paper_1102_5071_gb300 as P
+    insts = _instances([3, 6, 8])
+    bp = _batch(insts, m_max=8, max_substeps=3, precision="f64")
+    host, dev = _states(torch, insts)
+    st = bp.propagate(dev, 0.0, 0.1, 0, order=4)                       # no-op
+    assert all(np.array_equal(d.cpu().numpy(), h) for d, h in zip(dev, host)) and st[0]["n_exp"] == 0
+    z = [torch.zeros(1 << c.N, dtype=torch.complex128, device="cuda") for c in insts]
+    bp.propagate(z, 0.0, 0.1, 2, order=6)                             # zero states stay zero
+    assert all(torch.count_nonzero(x).item() == 0 for x in z)
+    bad = [d.clone() for d in dev]
+    bad[1][5] = complex(float("nan"), 0.0)
+    with pytest.raises(P.CfetError, match="ENAN"):
+        bp.propagate(bad, 0.0, 0.1, 1, order=4)
+    with pytest.raises(P.CfetError, match="EKRYLOV"):                # substep cap
+        bp.propagate(dev, 0.0, 3.0, 1, order=4, tol=1e-12)
+    with pytest.raises(P.CfetError, match="EINVAL"):
+        bp.propagate(dev, 0.0, 0.1, 1, order=5)
+    dev = [torch.from_numpy(h).cuda() for h in host]                  # still usable
+    bp.propagate(dev, 0.0, 0.02, 1, order=4)
+    with pytest.raises(P.CfetError, match="EINVAL"):
+        bp.set_plan(3, 256, 9)

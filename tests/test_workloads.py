@@ -38,3 +38,14 @@ def test_grid_atom_shapes():
     # radial hop cut at l-block edges, dipole zero outside the l range
     assert p.H0_values[1, 49] == 0.0 and p.H0_values[2, 50] == 0.0
     assert np.all(p.V_values[0, 150:] == 0.0) and np.all(p.V_values[1, :50] == 0.0)
+
+
+def test_chain_batch_recipe():
+    b = W.chain_batch()
+    assert len(b) == 256
+    assert {c.N for c in b} == set(range(10, 17))
+    assert all(0.5 <= c.A <= 2.0 and 1.0 <= c.omega <= 3.0 for c in b)
+    assert all(np.all(np.abs(c.h) <= 1.0) and c.h.shape == (c.N,) for c in b)
+    b2 = W.chain_batch()
+    assert all(np.array_equal(x.h, y.h) and x.A == y.A for x, y in zip(b, b2))   # seeded
+    assert len({c.psi_seed for c in b}) == 256

@@ -163,11 +163,48 @@ def atom_ground_state(p: GridAtomProblem):
 
 
 # ---------------------------------------------------------------------------
+# Batch of driven XXZ chains of uneven size: N uniform in {n_lo..n_hi},
+# per-instance field seed, A ~ U[0.5, 2], omega ~ U[1, 3]; drive A cos(omega t)
+# on sum_i X_i; psi0 a random normalised complex Gaussian state per instance.
+# ---------------------------------------------------------------------------
+@dataclass
+class ChainInstance:
+    N: int
+    J: float
+    Delta: float
+    h: np.ndarray
+    A: float
+    omega: float
+    psi_seed: int
+
+    @property
+    def xfield(self) -> np.ndarray:
+        return np.ones(self.N)
+
+    def drive(self, t: float) -> float:
+        return self.A * math.cos(self.omega * t)
+
+
+def chain_batch(n: int = 256, n_lo: int = 10, n_hi: int = 16, seed: int = 7, J: float = 1.0,
+                Delta: float = 0.5):
+    u = uniform(seed, 3 * n)
+    out = []
+    for i in range(n):
+        N = n_lo + min(int(u[i] * (n_hi - n_lo + 1)), n_hi - n_lo)
+        A = 0.5 + 1.5 * u[n + i]
+        omega = 1.0 + 2.0 * u[2 * n + i]
+        h = uniform(1000 + i, N, -1.0, 1.0)
+        out.append(ChainInstance(N, J, Delta, h, A, omega, 5000 + i))
+    return out
+
+
+# ---------------------------------------------------------------------------
 # Named workloads (sizes of the driven-chain and grid-atom experiments)
 # ---------------------------------------------------------------------------
 CHAIN_SMALL = dict(N=8, J=1.0, Delta=0.5, A=1.0, omega=2.0, h_seed=1, order=4, dt=0.01, T=10.0,
                    m_max=16, tol=1e-12, psi0="neel")
 CHAIN_LARGE = dict(N=20, J=1.0, Delta=0.5, A=1.0, omega=2.0, h_seed=1, orders=(4, 6, 8),
                    dts=(0.05, 0.02, 0.01), T=20.0, m_max=16, tol=1e-10, psi_seed=2)
+BATCH = dict(n=256, n_lo=10, n_hi=16, order=6, dt=0.02, T=10.0, m_max=16, tol=1e-10)
 ATOM = dict(Nr=2000, L=100, dr=0.1, E0=0.05, omega=0.057, Tp=1000.0, order=8, dt=0.1, m_max=64,
             tol=1e-10)
