@@ -20,12 +20,17 @@ krylov     Lanczos / Krylov evaluation of exp(-i tau H) psi (Sec. 7.1) with
            the a-posteriori error estimate and time substepping.
 cfet       the CFET time step (Eq. Ucf with Eq. OmGLeg) and time stepping
            (Sec. 6.1).
+adjoint    fidelity loss 1 - |<phi|psi(T)>|^2 of a CFET propagation with a
+           piecewise-constant drive amplitude and its exact gradient (dense
+           stage exponentials and Frechet derivatives; small systems).  The
+           paper has no gradients: this is the plain definition.
 
 Parity status: every function listed above is pinned by ``tests/test_oracle_*``
 against closed forms or library routines, except the whole-pipeline result at
 the driven-chain and grid-atom workloads, which no closed form covers; those
 are pinned only through properties (factorisation at J=0, time-independent
-exactness, order slopes, unitarity).
+exactness, order slopes, unitarity).  The gradient of ``adjoint`` is pinned by
+central finite differences of its loss and by its vanishing at an optimum.
 """
 
-__all__ = ["schemes", "operators", "krylov", "cfet"]
+__all__ = ["schemes", "operators", "krylov", "cfet", "adjoint"]
