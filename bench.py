@@ -567,6 +567,58 @@ def run_study_batch(args):
     return 0
 
 
+def run_study_adjoint(args):
+    """Gradient of the fidelity loss for the N=18 chain (dim 2^18), 64
+    piecewise-constant amplitude segments ~ U[-1, 1] over T = 16, CF4:2,
+    dt = 0.01, drive A_k cos(2 t) sum_i X_i, tol 1e-10: the adjoint sweep
+    (forward with checkpoints every 25 steps + FP64 backward) against the
+    gradient by central differences with the plain FP64 propagator
+    (2 x 64 forward runs, timed on one and scaled)."""
+    import torch
+    import paper_1102_5071_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    N, nseg, T, dt, omega, tol = 18, 64, 16.0, 0.01, 2.0, 1e-10
+    nsteps = int(round(T / dt))
+    pr = W.spin_chain(N)
+    psi0 = torch.from_numpy(W.random_state(3, 1 << N)).cuda()
+    phi = torch.from_numpy(W.random_state(13, 1 << N)).cuda()
+    amps = W.uniform(7, nseg, -1.0, 1.0)
+    out = {}
+    for prec in ("fx", "f64"):
+        prop = P.Propagator(P.XXZChain(N, pr.J, pr.Delta, pr.h), [P.XField(N, np.ones(N))], [lambda t: 0.0],
+                            m_max=16, precision=prec)
+        prop.fidelity_grad(psi0, phi, 0.0, dt, 50, amps[:2], omega, tol=tol, checkpoint_every=25)   # warm-up
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        L, g, st = prop.fidelity_grad(psi0, phi, 0.0, dt, nsteps, amps, omega, tol=tol, checkpoint_every=25)
+        wall = time.perf_counter() - t
+        out["adjoint_forward_" + prec] = {"loss": L, "wall_s": wall, **st, "grad_norm": float(np.linalg.norm(g))}
+        prop.close()
+    # one plain FP64 forward propagation (a central-difference gradient needs 2 x 64 of them)
+    from oracle import adjoint as OA
+    f = OA.pwc_drive(amps, omega, 0.0, 0.0, dt, nsteps // nseg)
+    prop = P.Propagator(P.XXZChain(N, pr.J, pr.Delta, pr.h), [P.XField(N, np.ones(N))], [f], m_max=16,
+                        precision="f64")
+    x = psi0.clone()
+    prop.propagate(x, 0.0, dt, 10, order=4, tol=tol)
+    x = psi0.clone()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    prop.propagate(x, 0.0, dt, nsteps, order=4, tol=tol)
+    torch.cuda.synchronize()
+    fwd_s = time.perf_counter() - t
+    prop.close()
+    out["f64_forward_s"] = fwd_s
+    out["central_difference_gradient_s"] = 2 * nseg * fwd_s
+    for prec in ("fx", "f64"):
+        out["adjoint_forward_" + prec]["speedup_vs_central_differences_f64"] = (
+            2 * nseg * fwd_s / out["adjoint_forward_" + prec]["wall_s"])
+    print(json.dumps({"study": "fidelity gradient: N=18 chain, 64 segments, T=16, CF4:2 dt=0.01, tol 1e-10",
+                      **out}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -580,8 +632,9 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="accuracy study: final-state error and throughput per (order, dt) over T")
     ap.add_argument("--sweep-T", type=float, default=20.0)
-    ap.add_argument("--study", choices=["atom", "sizes", "batch"],
-                    help="extra measurements: the grid atom, the chain at N = 20..26, the 256-chain batch")
+    ap.add_argument("--study", choices=["atom", "sizes", "batch", "adjoint"],
+                    help="extra measurements: the grid atom, the chain at N = 20..26, the 256-chain batch, "
+                         "the fidelity gradient")
     ap.add_argument("--baseline-steps", type=int, default=10,
                     help="batch study: steps of the single-instance baseline per instance")
     ap.add_argument("--block-size", type=int, default=0,
@@ -599,6 +652,8 @@ def main():
         return run_study_sizes(args)
     if args.study == "batch":
         return run_study_batch(args)
+    if args.study == "adjoint":
+        return run_study_adjoint(args)
     return run_gpu(args)
 
 

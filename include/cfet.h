@@ -366,6 +366,42 @@ cfet_status cfet_batch_set_plan(cfet_batch* b, const cfet_batch_plan* plan);
 /* Device time in milliseconds of the last batched launch.                  */
 cfet_status cfet_batch_kernel_time_ms(cfet_batch* b, float* ms);
 
+/* ------------------------------------------------------------------------ */
+/* Gradient of the fidelity loss (adjoint sweep)                             */
+/* ------------------------------------------------------------------------ */
+typedef struct cfet_grad_stats {
+  double overlap_re, overlap_im;   /* <phi|psi(T)>                            */
+  double max_drift;                /* largest ||psi_recovered - checkpoint||  */
+  int64_t n_applies_forward;       /* H applications of the forward pass      */
+  int64_t n_applies_backward;      /* H applications of the adjoint sweep      */
+  float forward_ms, backward_ms;   /* device time of both passes              */
+} cfet_grad_stats;
+
+/* L = 1 - |<phi|psi(T)>|^2 and dL/dA_k for the drive of ctx's single X field
+ * replaced by the piecewise-constant amplitude f(t) = amps[k] cos(omega t +
+ * phase) on segment k (nseg segments of nsteps / nseg CFET steps each, so
+ * the Gauss-Legendre nodes of a step lie in one segment); psi(T) is the CFET
+ * propagation of psi0 over nsteps steps of dt from t0 (order 2, 4, 6, 8;
+ * Sec. 4 Eq. (Ucf), Sec. 7 Eq. (OmGLeg)).  No counterpart in the paper.
+ * The forward pass runs ctx's propagator (its precision) and stores psi every
+ * checkpoint_every steps; the backward sweep (FP64) undoes each stage
+ * exponential with the inverse unitary step in the Krylov space of the
+ * current state while propagating the adjoint state, and takes each stage's
+ * derivative d/dc exp(-i dt (c0 H0 + c V)) as the exact time integral of
+ * e^{i r H} V e^{i r H}-type terms inside the two Krylov spaces (Gauss-Legendre
+ * in r); at every checkpoint the recovered state is replaced by the stored one
+ * (max_drift reports the largest difference).  Requirements: ctx is an XXZ
+ * chain with exactly one X-field drive operator, ctx's m_max <= 16, every
+ * stage exponential of the sweep needs no substeps (else CFET_EKRYLOV).
+ * psi0, phi: device complex128[dim], unchanged.  amps: host [nseg].  loss:
+ * host scalar; grad: host [nseg].  Synchronises `stream`; gstats may be NULL.
+ * Device memory of about (nsteps / checkpoint_every + 34) x dim x 16 bytes is
+ * allocated on first use and kept by ctx.                                    */
+cfet_status cfet_fidelity_grad(cfet_ctx* ctx, const void* psi0, const void* phi, double t0, double dt,
+                               int64_t nsteps, int32_t order, double krylov_tol, int32_t nseg, const double* amps,
+                               double omega, double phase, int64_t checkpoint_every, void* stream, double* loss,
+                               double* grad, cfet_grad_stats* gstats);
+
 /* Dimension and drive-operator count of ctx (for bindings).                 */
 int64_t cfet_dim(const cfet_ctx* ctx);
 int32_t cfet_num_drives(const cfet_ctx* ctx);

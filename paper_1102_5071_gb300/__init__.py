@@ -257,6 +257,25 @@ class Propagator:
         self._raise(self._lib.cfet_kernel_time_ms(self._ctx, C.byref(ms)))
         return float(ms.value)
 
+    def fidelity_grad(self, psi0, phi, t0, dt, nsteps, amps, omega, phase=0.0, order=4, tol=1e-10,
+                      checkpoint_every=None, stream=None):
+        """L = 1 - |<phi|psi(T)>|^2 and dL/dA for the single X-field drive
+        replaced by f(t) = amps[k] cos(omega t + phase) on segment k (see
+        cfet_fidelity_grad).  Returns (loss, grad ndarray, stats dict)."""
+        _check_vec(psi0, self.dim, "psi0")
+        _check_vec(phi, self.dim, "phi")
+        a = np.ascontiguousarray(amps, dtype=np.float64)
+        g = np.zeros(a.size)
+        loss = C.c_double()
+        gs = _capi.cfet_grad_stats()
+        ce = int(checkpoint_every) if checkpoint_every else max(1, int(nsteps) // max(1, a.size))
+        self._raise(self._lib.cfet_fidelity_grad(
+            self._ctx, C.c_void_p(psi0.data_ptr()), C.c_void_p(phi.data_ptr()), float(t0), float(dt), int(nsteps),
+            int(order), float(tol), a.size, a.ctypes.data_as(_capi.c_double_p), float(omega), float(phase), ce,
+            _stream_handle(stream), C.byref(loss), g.ctypes.data_as(_capi.c_double_p), C.byref(gs)))
+        stats = {f: getattr(gs, f) for f, _ in gs._fields_}
+        return loss.value, g, stats
+
     def sync(self, stream=None):
         stats = _capi.cfet_stats()
         self._raise(self._lib.cfet_sync(self._ctx, _stream_handle(stream), C.byref(stats)))
@@ -406,10 +425,33 @@ class BatchPropagator:
         return float(ms.value)
 
 
+def fidelity_loss(prop, amps, psi0, phi, t0, dt, nsteps, omega, phase=0.0, order=4, tol=1e-10,
+                  checkpoint_every=None):
+    """Differentiable L(amps) = 1 - |<phi|psi(T)>|^2 (torch scalar, float64):
+    the forward call runs cfet_fidelity_grad once and keeps the gradient for
+    the backward call."""
+    import torch
+
+    class _Fidelity(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, a):
+            loss, grad, _ = prop.fidelity_grad(psi0, phi, t0, dt, nsteps, a.detach().cpu().numpy(), omega, phase,
+                                               order, tol, checkpoint_every)
+            ctx.save_for_backward(torch.from_numpy(grad).to(a.device, a.dtype))
+            return torch.tensor(loss, dtype=a.dtype, device=a.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            (grad,) = ctx.saved_tensors
+            return g * grad
+
+    return _Fidelity.apply(amps)
+
+
 def build():
     from .build import build as _b
     return _b()
 
 
-__all__ = ["Propagator", "BatchPropagator", "Chain", "XXZChain", "XField", "DIA", "scheme_info", "CfetError",
+__all__ = ["Propagator", "BatchPropagator", "Chain", "fidelity_loss", "XXZChain", "XField", "DIA", "scheme_info", "CfetError",
            "SCHEME_IDS", "build"]

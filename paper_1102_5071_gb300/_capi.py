@@ -55,6 +55,12 @@ class cfet_decisions(C.Structure):
 DRIVE_FN = C.CFUNCTYPE(C.c_double, C.c_double, C.c_void_p)
 
 
+class cfet_grad_stats(C.Structure):
+    _fields_ = [("overlap_re", C.c_double), ("overlap_im", C.c_double), ("max_drift", C.c_double),
+                ("n_applies_forward", C.c_int64), ("n_applies_backward", C.c_int64), ("forward_ms", C.c_float),
+                ("backward_ms", C.c_float)]
+
+
 class cfet_chain(C.Structure):
     _fields_ = [("nsites", C.c_int32), ("J", C.c_double), ("Delta", C.c_double), ("h", c_double_p),
                 ("a", c_double_p), ("f", DRIVE_FN), ("user", C.c_void_p), ("A", C.c_double),
@@ -116,6 +122,9 @@ def load() -> C.CDLL:
         "cfet_batch_get_plan": (C.c_int, [vp, C.POINTER(cfet_batch_plan)]),
         "cfet_batch_set_plan": (C.c_int, [vp, C.POINTER(cfet_batch_plan)]),
         "cfet_batch_kernel_time_ms": (C.c_int, [vp, C.POINTER(C.c_float)]),
+        "cfet_fidelity_grad": (C.c_int, [vp, vp, vp, C.c_double, C.c_double, C.c_int64, C.c_int32, C.c_double,
+                                         C.c_int32, c_double_p, C.c_double, C.c_double, C.c_int64, vp, c_double_p,
+                                         c_double_p, C.POINTER(cfet_grad_stats)]),
         "cfet_dim": (C.c_int64, [vp]),
         "cfet_num_drives": (C.c_int32, [vp]),
     }
@@ -132,5 +141,5 @@ EXPORTED = ["cfet_options_default", "cfet_scheme_info", "cfet_create", "cfet_des
             "cfet_kernel_time_ms", "cfet_expv_chain_static",
             "cfet_batch_create", "cfet_batch_destroy", "cfet_batch_last_error", "cfet_batch_size",
             "cfet_batch_propagate", "cfet_batch_tune", "cfet_batch_get_plan", "cfet_batch_set_plan",
-            "cfet_batch_kernel_time_ms",
+            "cfet_batch_kernel_time_ms", "cfet_fidelity_grad",
             "cfet_dim", "cfet_num_drives"]

@@ -29,7 +29,7 @@ FLAGS_STAMP = os.path.join(BUILD_DIR, "extra_flags.txt")
 
 def _extra_flags() -> list:
     return os.environ.get("CFET_NVCC_FLAGS", "").split()
-SOURCES = ["kernels.cu", "kernels_fx.cu", "kernels_c64.cu", "capi.cu", "schemes.cpp", "noalloc.cu", "batch.cu"]
+SOURCES = ["kernels.cu", "kernels_fx.cu", "kernels_c64.cu", "capi.cu", "schemes.cpp", "noalloc.cu", "batch.cu", "adjoint.cu"]
 
 
 def _nvcc() -> str:

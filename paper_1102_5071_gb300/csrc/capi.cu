@@ -70,6 +70,17 @@ struct cfet_ctx {
   // decisions
   int* d_dec = nullptr;  // [f_nsub | f_k | f_h | r_nsub | r_k | r_h]
   size_t dec_cap = 0;    // ints
+  // fidelity gradient (adjoint sweep) workspace
+  double2* d_adj_ckpt = nullptr;   // checkpoints of the forward states
+  size_t adj_ckpt_n = 0;
+  double2* d_adj_vec = nullptr;    // psi, lambda, Krylov bases of both
+  double* d_adj_part = nullptr;
+  double* d_adj_tab = nullptr;     // c0 | c1 | gamma per exponential, then GL nodes and weights
+  int* d_adj_seg = nullptr;
+  size_t adj_tab_n = 0;
+  double* d_adj_acc = nullptr;     // gradient accumulators [2 nseg] then out [4]
+  int adj_nseg_cap = 0;
+  int adj_grid = 0;
   // graph driver
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -130,6 +141,8 @@ void free_ctx(cfet_ctx* c) {
   cudaFree(c->d_scal); cudaFree(c->d_psi_e2e); cudaFree(c->d_dec);
   cudaFree(c->d_DZ); cudaFree(c->d_VAL); cudaFree(c->d_qbasis);
   cudaFree(c->d_dz32); cudaFree(c->d_val32); cudaFree(c->d_qbasis32);
+  cudaFree(c->d_adj_ckpt); cudaFree(c->d_adj_vec); cudaFree(c->d_adj_part); cudaFree(c->d_adj_tab);
+  cudaFree(c->d_adj_seg); cudaFree(c->d_adj_acc);
   if (c->h_st) cudaFreeHost(c->h_st);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   delete c;
@@ -249,6 +262,57 @@ cfet_status finish(cfet_ctx* ctx, cudaStream_t s, cfet_stats* stats) {
   if (code == CFET_ENAN) return fail(ctx, CFET_ENAN, "psi norm is not finite");
   if (code != 0) return fail(ctx, (cfet_status)code, "device error");
   return CFET_OK;
+}
+
+// Gauss-Legendre nodes and weights on [0, 1] by Newton's method on the
+// Legendre polynomial P_n (three-term recurrence); weights 1 / ((1 - z^2) P_n'(z)^2).
+void gauss_legendre_01(int n, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), p1 = 0.0, dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0;
+      p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-15) break;
+    }
+    {
+      double p0 = 1.0;
+      p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+    }
+    x[i] = 0.5 * (1.0 - z);
+    w[i] = 1.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Piecewise-constant drive amplitude: f(t) = amps[k] cos(omega t + phase), k the
+// segment of the step that contains t.
+struct PwcDrive {
+  const double* amps;
+  int nseg;
+  double omega, phase, t0, dt;
+  long long steps_per_seg;
+};
+
+double pwc_eval(double t, void* user) {
+  const PwcDrive* d = static_cast<const PwcDrive*>(user);
+  long long n = (long long)std::floor((t - d->t0) / d->dt);
+  long long k = n / d->steps_per_seg;
+  if (k < 0) k = 0;
+  if (k >= d->nseg) k = d->nseg - 1;
+  return d->amps[k] * std::cos(d->omega * t + d->phase);
 }
 
 }  // namespace
@@ -837,6 +901,209 @@ cfet_status cfet_sync(cfet_ctx* ctx, void* stream, cfet_stats* stats) {
   if (!ctx) return CFET_EINVAL;
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   return finish(ctx, (cudaStream_t)stream, stats);
+}
+
+cfet_status cfet_fidelity_grad(cfet_ctx* ctx, const void* psi0, const void* phi, double t0, double dt,
+                               int64_t nsteps, int32_t order, double krylov_tol, int32_t nseg, const double* amps,
+                               double omega, double phase, int64_t checkpoint_every, void* stream, double* loss,
+                               double* grad, cfet_grad_stats* gstats) {
+  if (!ctx) return CFET_EINVAL;
+  if (ctx->family != kFamilySpin || ctx->nV != 1)
+    return fail(ctx, CFET_EINVAL, "fidelity gradient: needs an XXZ chain with exactly one X-field drive");
+  cfet_status s = check_psi(ctx, psi0);
+  if (s != CFET_OK) return s;
+  if ((s = check_psi(ctx, phi)) != CFET_OK) return s;
+  if (!loss || !grad || !amps) return fail(ctx, CFET_EINVAL, "loss, grad and amps are required");
+  if (!is_finite_d(t0) || !is_finite_d(dt) || dt == 0.0 || !is_finite_d(krylov_tol) || !is_finite_d(omega) ||
+      !is_finite_d(phase))
+    return fail(ctx, CFET_EINVAL, "t0, dt, tol, omega, phase must be finite, dt != 0");
+  if (nsteps < 1 || nseg < 1 || nsteps % nseg != 0)
+    return fail(ctx, CFET_EINVAL, "nsteps must be a positive multiple of nseg");
+  for (int k = 0; k < nseg; ++k)
+    if (!is_finite_d(amps[k])) return fail(ctx, CFET_EINVAL, "amplitude not finite");
+  if (checkpoint_every < 1) return fail(ctx, CFET_EINVAL, "checkpoint_every must be >= 1");
+  if (ctx->opt.m_max > kAdjMaxK) return fail(ctx, CFET_EINVAL, "fidelity gradient: m_max must be <= 16");
+  const int id = default_scheme_for_order(order);
+  if (!id) return fail(ctx, CFET_EINVAL, "order must be 2, 4, 6 or 8");
+  SchemeData sd;
+  build_scheme(id, &sd);
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int dim = ctx->dim;
+  const long long nexp = nsteps * (long long)sd.s;
+  const long long nch = (nsteps + checkpoint_every - 1) / checkpoint_every;
+  // ---- workspace
+  if (ctx->ev_pending) { cudaEventSynchronize(ctx->ev_done); ctx->ev_pending = false; }
+  if ((size_t)(nch + 1) > ctx->adj_ckpt_n) {
+    cudaFree(ctx->d_adj_ckpt);
+    ctx->d_adj_ckpt = nullptr;
+    ctx->adj_ckpt_n = 0;
+    CK(cudaMalloc(&ctx->d_adj_ckpt, (size_t)(nch + 1) * dim * sizeof(double2)), "cudaMalloc(checkpoints)");
+    ctx->adj_ckpt_n = (size_t)(nch + 1);
+  }
+  if (!ctx->d_adj_vec) {
+    CK(cudaMalloc(&ctx->d_adj_vec, (size_t)(2 + 2 * kAdjMaxK) * dim * sizeof(double2)), "cudaMalloc(adjoint)");
+    int g = max_coresident_blocks_adjoint(256);
+    if (g < 1) return fail(ctx, CFET_ECUDA, "occupancy query failed for the adjoint kernel");
+    const int want = (dim + 255) / 256;
+    ctx->adj_grid = want < g ? want : g;
+    CK(cudaMalloc(&ctx->d_adj_part, 2 * (2 * kAdjMaxK + 2) * (size_t)ctx->adj_grid * sizeof(double)),
+       "cudaMalloc(adjoint partials)");
+  }
+  const int nql = 6 + 12 + 24;
+  if ((size_t)(3 * nexp + 2 * nql) > ctx->adj_tab_n) {
+    cudaFree(ctx->d_adj_tab);
+    cudaFree(ctx->d_adj_seg);
+    ctx->d_adj_tab = nullptr;
+    ctx->d_adj_seg = nullptr;
+    ctx->adj_tab_n = 0;
+    CK(cudaMalloc(&ctx->d_adj_tab, (size_t)(3 * nexp + 2 * nql) * sizeof(double)), "cudaMalloc(adjoint tables)");
+    CK(cudaMalloc(&ctx->d_adj_seg, (size_t)nexp * sizeof(int)), "cudaMalloc(adjoint tables)");
+    ctx->adj_tab_n = (size_t)(3 * nexp + 2 * nql);
+  }
+  if (nseg > ctx->adj_nseg_cap) {
+    cudaFree(ctx->d_adj_acc);
+    ctx->d_adj_acc = nullptr;
+    ctx->adj_nseg_cap = 0;
+    CK(cudaMalloc(&ctx->d_adj_acc, (2 * (size_t)nseg + 4) * sizeof(double)), "cudaMalloc(gradient)");
+    ctx->adj_nseg_cap = nseg;
+  }
+  double2* d_psi = ctx->d_adj_vec;
+  double2* d_lam = ctx->d_adj_vec + dim;
+  double2* d_Vp = ctx->d_adj_vec + 2 * (size_t)dim;
+  double2* d_Vl = d_Vp + (size_t)kAdjMaxK * dim;
+  // ---- per-exponential tables (application order) and quadrature rules
+  const long long sps = nsteps / nseg;
+  std::vector<double> tab(3 * nexp + 2 * nql);
+  std::vector<int> segv(nexp);
+  for (long long n = 0; n < nsteps; ++n) {
+    const double t = t0 + (double)n * dt;
+    for (int jj = 0; jj < sd.s; ++jj) {
+      const int j = sd.s - 1 - jj;  // exp(Omega_s) acts first
+      double c0 = 0.0, gm = 0.0;
+      for (int m = 0; m < sd.M; ++m) {
+        c0 += sd.g[j][m];
+        gm += sd.g[j][m] * std::cos(omega * (t + sd.x[m] * dt) + phase);
+      }
+      const long long e = n * sd.s + jj;
+      const int k = (int)(n / sps);
+      tab[e] = c0;
+      tab[nexp + e] = amps[k] * gm;
+      tab[2 * nexp + e] = gm;
+      segv[e] = k;
+    }
+  }
+  double* glx = tab.data() + 3 * nexp;
+  double* glw = glx + nql;
+  gauss_legendre_01(6, glx, glw);
+  gauss_legendre_01(12, glx + 6, glw + 6);
+  gauss_legendre_01(24, glx + 18, glw + 18);
+  CK(cudaMemcpyAsync(ctx->d_adj_tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, st),
+     "adjoint table upload");
+  CK(cudaMemcpyAsync(ctx->d_adj_seg, segv.data(), segv.size() * sizeof(int), cudaMemcpyHostToDevice, st),
+     "adjoint table upload");
+  // ---- forward pass with checkpoints (the context's own propagator)
+  cudaEvent_t e0, e1, e2;
+  CK(cudaEventCreate(&e0), "event");
+  CK(cudaEventCreate(&e1), "event");
+  CK(cudaEventCreate(&e2), "event");
+  struct EvGuard {
+    cudaEvent_t a, b, c;
+    ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); cudaEventDestroy(c); }
+  } evg{e0, e1, e2};
+  CK(cudaEventRecord(e0, st), "event");
+  CK(cudaMemcpyAsync(d_psi, psi0, (size_t)dim * sizeof(double2), cudaMemcpyDeviceToDevice, st), "copy psi0");
+  CK(cudaMemcpyAsync(ctx->d_adj_ckpt, psi0, (size_t)dim * sizeof(double2), cudaMemcpyDeviceToDevice, st),
+     "checkpoint");
+  PwcDrive pd{amps, nseg, omega, phase, t0, dt, sps};
+  const cfet_drive_fn f_saved = ctx->f[0];
+  void* const u_saved = ctx->f_user[0];
+  ctx->f[0] = pwc_eval;
+  ctx->f_user[0] = &pd;
+  long long fwd_app = 0;
+  for (long long c = 0; c < nch; ++c) {
+    const long long n0 = c * checkpoint_every;
+    const long long nc = (nsteps - n0) < checkpoint_every ? (nsteps - n0) : checkpoint_every;
+    cfet_stats fs;
+    s = cfet_propagate_ex(ctx, d_psi, t0 + (double)n0 * dt, dt, nc, order, CFET_SCHEME_DEFAULT, krylov_tol, stream,
+                          nullptr, nullptr, &fs);
+    if (s != CFET_OK) break;
+    fwd_app += fs.n_applies;
+    cudaError_t ce = cudaMemcpyAsync(ctx->d_adj_ckpt + (size_t)(c + 1) * dim, d_psi, (size_t)dim * sizeof(double2),
+                                     cudaMemcpyDeviceToDevice, st);
+    if (ce != cudaSuccess) {
+      s = cuda_fail(ctx, ce, "checkpoint");
+      break;
+    }
+  }
+  ctx->f[0] = f_saved;
+  ctx->f_user[0] = u_saved;
+  if (s != CFET_OK) return s;
+  CK(cudaEventRecord(e1, st), "event");
+  // ---- backward sweep, one launch per checkpoint interval
+  CK(cudaMemsetAsync(ctx->d_adj_acc, 0, (2 * (size_t)nseg + 4) * sizeof(double), st), "gradient reset");
+  CK(cudaMemsetAsync(ctx->d_st, 0, sizeof(DevStatus), st), "status reset");
+  for (long long c = nch - 1; c >= 0; --c) {
+    const long long n0 = c * checkpoint_every;
+    const long long n1 = (n0 + checkpoint_every) < nsteps ? (n0 + checkpoint_every) : nsteps;
+    AdjParams p{};
+    p.dim = dim;
+    p.m_min = ctx->opt.m_min;
+    p.m_max = ctx->opt.m_max;
+    p.tau = dt;
+    p.tol = krylov_tol;
+    p.psi = d_psi;
+    p.ckpt = ctx->d_adj_ckpt + (size_t)(c + 1) * dim;
+    p.lam = d_lam;
+    p.phi = (c == nch - 1) ? (const double2*)phi : nullptr;
+    p.Vp = d_Vp;
+    p.Vl = d_Vl;
+    p.c0 = ctx->d_adj_tab;
+    p.c1 = ctx->d_adj_tab + nexp;
+    p.gam = ctx->d_adj_tab + 2 * nexp;
+    p.seg = ctx->d_adj_seg;
+    p.e_lo = n0 * sd.s;
+    p.e_hi = n1 * sd.s;
+    p.nq6 = 0;
+    p.nq12 = 6;
+    p.nq24 = 18;
+    p.glx = ctx->d_adj_tab + 3 * nexp;
+    p.glw = p.glx + nql;
+    p.grad = ctx->d_adj_acc;
+    p.out = ctx->d_adj_acc + 2 * nseg;
+    p.partials = ctx->d_adj_part;
+    p.bar = ctx->d_bar;
+    p.st = ctx->d_st;
+    p.timeout_ns = (long long)(ctx->opt.barrier_timeout_s * 1e9);
+    CK(cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned), st), "barrier reset");
+    const int e = launch_adjoint_spin(p, ctx->spin, ctx->adj_grid, 256, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, (cudaError_t)e, "adjoint kernel launch");
+  }
+  CK(cudaEventRecord(e2, st), "event");
+  std::vector<double> acc(2 * (size_t)nseg + 4);
+  CK(cudaMemcpyAsync(acc.data(), ctx->d_adj_acc, acc.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
+     "gradient read-back");
+  CK(cudaMemcpyAsync(ctx->h_st, ctx->d_st, sizeof(DevStatus), cudaMemcpyDeviceToHost, st), "status read-back");
+  CK(cudaStreamSynchronize(st), "stream synchronize");
+  const int code = ctx->h_st->status;
+  if (code == CFET_EKRYLOV)
+    return fail(ctx, CFET_EKRYLOV, "adjoint sweep: a stage exponential needs more than m_max Krylov vectors");
+  if (code == CFET_ETIMEOUT) return fail(ctx, CFET_ETIMEOUT, "device grid barrier timed out");
+  if (code == CFET_ENAN) return fail(ctx, CFET_ENAN, "state not finite");
+  if (code != 0) return fail(ctx, (cfet_status)code, "device error");
+  const double ore = acc[2 * nseg], oim = acc[2 * nseg + 1];
+  *loss = 1.0 - (ore * ore + oim * oim);
+  for (int k = 0; k < nseg; ++k) grad[k] = -2.0 * (ore * acc[2 * k] + oim * acc[2 * k + 1]);
+  if (gstats) {
+    gstats->overlap_re = ore;
+    gstats->overlap_im = oim;
+    gstats->max_drift = acc[2 * nseg + 2];
+    gstats->n_applies_forward = fwd_app;
+    gstats->n_applies_backward = (int64_t)acc[2 * nseg + 3];
+    cudaEventElapsedTime(&gstats->forward_ms, e0, e1);
+    cudaEventElapsedTime(&gstats->backward_ms, e1, e2);
+  }
+  return CFET_OK;
 }
 
 }  // extern "C"

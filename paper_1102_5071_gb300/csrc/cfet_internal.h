@@ -134,6 +134,38 @@ struct PropParams {
   float2* qbasis32;
 };
 
+// Backward (adjoint) sweep of the fidelity gradient (see adjoint.cu).
+constexpr int kAdjMaxK = 16;     // Krylov dimension limit of the adjoint sweep
+constexpr int kAdjMaxNodes = 24; // Gauss-Legendre nodes of the stage integral
+
+struct AdjParams {
+  int dim;
+  int m_min, m_max;
+  int pad0;
+  double tau, tol;
+  double2* psi;            // in: state after exponential e_hi - 1; out: state before e_lo
+  const double2* ckpt;     // nullable: stored forward state replacing psi on entry
+  double2* lam;            // adjoint state, in / out
+  const double2* phi;      // nullable (first launch): lam = phi, overlap <phi|psi>
+  double2* Vp;             // Krylov vectors q_2 .. q_{m_max+1} of psi
+  double2* Vl;             // Krylov vectors of lam
+  const double* c0;        // per exponential (application order): H0 coefficient
+  const double* c1;        //   V coefficient (amplitude x gamma)
+  const double* gam;       //   d c1 / d amplitude
+  const int* seg;          //   amplitude segment
+  long long e_lo, e_hi;    // exponentials e_hi - 1 down to e_lo are undone
+  int nq6, nq12, nq24;     // offsets of the 6-, 12-, 24-node rules in glx / glw
+  int pad1;
+  const double* glx;       // Gauss-Legendre nodes on [0, 1]
+  const double* glw;
+  double* grad;            // [2 nseg]: accumulated d<phi|psi(T)>/dA_k (re, im)
+  double* out;             // [4]: re, im of the overlap (first launch), max drift, n_applies
+  double* partials;        // [2 slots x 34 values x grid]
+  unsigned* bar;
+  DevStatus* st;
+  long long timeout_ns;
+};
+
 // ---------------------------------------------------------------- launchers
 // (defined in kernels.cu; return a cudaError_t as int)
 int launch_propagate_spin(const PropParams& p, const OpSpin& op, int grid, int block, void* stream);
@@ -150,6 +182,8 @@ int max_coresident_blocks_fx(int family, int block);
 int launch_propagate_spin_c64(const PropParams& p, const OpSpinC& op, int grid, int block, void* stream);
 int launch_propagate_dia_c64(const PropParams& p, const OpDiaC& op, int grid, int block, void* stream);
 int max_coresident_blocks_c64(int family, int block);
+int launch_adjoint_spin(const AdjParams& p, const OpSpin& op, int grid, int block, void* stream);
+int max_coresident_blocks_adjoint(int block);
 int max_coresident_blocks(int family, int block);  // per device, for the persistent kernel
 size_t propagate_smem_bytes(int block);
 

@@ -30,40 +30,6 @@ struct Coefs {
 };
 
 // ------------------------------------------------------------------ apply
-// Spin family:  (c0 H0 + sum_k c_k V_k) v at index x, everything pre-scaled.
-//   diag   cz * dz(x) v[x],             dz(x) = J Delta sum s_i s_{i+1} + sum h_i s_i
-//   hop    cxx * sum_{antiparallel bonds i} v[x ^ (3 << i)]     (cxx = 2 J c0)
-//   field  sum_i b_i v[x ^ (1 << i)]                             (b_i = sum_k c_k a_{k,i})
-struct SpinScaled {
-  double cz, cxx;
-};
-
-__device__ __forceinline__ double2 apply_spin_at(const double2* q, int x, const OpSpin& op, const SpinScaled& sc,
-                                                 const double* bsite) {
-  const int N = op.N, L = op.lo_bits;
-  const double dz = __ldg(op.dz_lo + (x & ((1 << L) - 1))) + __ldg(op.dz_hi + (x >> (L - 1)));
-  const double2 v = q[x];
-  const double cd = sc.cz * dz;
-  double2 acc = make_double2(cd * v.x, cd * v.y);
-  double hx = 0.0, hy = 0.0;
-  unsigned anti = ((unsigned)x ^ ((unsigned)x >> 1)) & ((1u << (N - 1)) - 1u);
-  while (anti) {
-    const int i = __ffs(anti) - 1;
-    anti &= anti - 1u;
-    const double2 w = q[x ^ (3 << i)];
-    hx += w.x;
-    hy += w.y;
-  }
-  acc.x = fma(sc.cxx, hx, acc.x);
-  acc.y = fma(sc.cxx, hy, acc.y);
-  for (int i = 0; i < N; ++i) {
-    const double2 w = q[x ^ (1 << i)];
-    acc.x = fma(bsite[i], w.x, acc.x);
-    acc.y = fma(bsite[i], w.y, acc.y);
-  }
-  return acc;
-}
-
 // DIA family: sum_d coef[opidx[d]] * val[d][r] * v[r + off[d]], coef pre-scaled.
 __device__ __forceinline__ double2 apply_dia_at(const double2* q, int r, int dim, const OpDia& op,
                                                 const double* copf) {
