@@ -596,8 +596,10 @@ def run_study_adjoint(args):
         out["adjoint_forward_" + prec] = {"loss": L, "wall_s": wall, **st, "grad_norm": float(np.linalg.norm(g))}
         prop.close()
     # one plain FP64 forward propagation (a central-difference gradient needs 2 x 64 of them)
-    from oracle import adjoint as OA
-    f = OA.pwc_drive(amps, omega, 0.0, 0.0, dt, nsteps // nseg)
+    sps = nsteps // nseg
+
+    def f(t):   # the same piecewise-constant drive, segment of the step containing t
+        return amps[min(int(math.floor(t / dt)) // sps, nseg - 1)] * math.cos(omega * t)
     prop = P.Propagator(P.XXZChain(N, pr.J, pr.Delta, pr.h), [P.XField(N, np.ones(N))], [f], m_max=16,
                         precision="f64")
     x = psi0.clone()
