@@ -53,10 +53,11 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 fl
 # from one ncu capture of the same kernel build on the 2-step case (76
 # iterations): see profiles/.  Must be reset to None whenever the kernel
 # changes and re-measured.
-DRAM_BYTES_PER_ITERATION = {"fx": 2.831831e9 / 76, "c64": 0.838948e9 / 76, "f64": None}
+DRAM_BYTES_PER_ITERATION = {"fx": None, "c64": None, "f64": None}
 
 # trace slots of the control-warp kernels (cfet_stats.phase_ns)
-PHASES = ("apply_loops", "apply_control", "orth_loops", "orth_control", "reconstruct_loops", "barrier_wait")
+PHASES = ("apply_loops", "apply_control", "orth_loops", "orth_control", "reconstruct_loops", "barrier_wait",
+          "overlapped_control", "worker_wait")
 
 
 def workload_config():
@@ -335,9 +336,9 @@ def run_gpu(args):
             "krylov": {"applies_per_step": n_app / args.steps, "substeps": stats["n_substeps"],
                        "max_k": stats["max_k"], "max_err_est": stats["max_err_est"],
                        # SM clock cycles per CTA (mean, max over CTAs), in millions
-                       "phase_Mcycles": {k: v * 1e-6 for k, v in zip(PHASES, stats.get("phase_ns", [0] * 6))},
+                       "phase_Mcycles": {k: v * 1e-6 for k, v in zip(PHASES, stats.get("phase_ns", [0] * 8))},
                        "phase_max_Mcycles": {k: v * 1e-6 for k, v in zip(PHASES,
-                                                                           stats.get("phase_max_ns", [0] * 6))}},
+                                                                           stats.get("phase_max_ns", [0] * 8))}},
             "roofline": roofline,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 16 * dim, "d2h_bytes_per_step": 16 * dim,
                     "steps": e2e_steps},

@@ -179,9 +179,12 @@ typedef struct cfet_stats {
    * (reduction, scalar constants; barrier wait excluded), [2] worker loops of
    * the orthogonalisation passes, [3] control work after them (reduction,
    * error estimate, decisions, constants), [4] worker loops of the
-   * reconstructions, [5] time spent waiting in grid barriers.              */
-  int64_t phase_ns[6];
-  int64_t phase_max_ns[6];
+   * reconstructions, [5] time spent waiting in grid barriers, [6] control
+   * work overlapped with the worker loops (speculative error estimates,
+   * reconstruction coefficients), [7] time the workers wait at CTA barriers
+   * for the control warp (after their loops, until released).               */
+  int64_t phase_ns[8];
+  int64_t phase_max_ns[8];
 } cfet_stats;
 
 /* Per-exponential Krylov decisions, host arrays owned by the caller.  One

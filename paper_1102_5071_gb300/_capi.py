@@ -39,7 +39,7 @@ PRECISIONS = {"default": CFET_PREC_DEFAULT, "f64": CFET_PREC_F64, "fx": CFET_PRE
 class cfet_stats(C.Structure):
     _fields_ = [("n_exp", C.c_int64), ("n_substeps", C.c_int64), ("n_applies", C.c_int64),
                 ("max_k", C.c_int32), ("status", C.c_int32), ("max_err_est", C.c_double),
-                ("phase_ns", C.c_int64 * 6), ("phase_max_ns", C.c_int64 * 6)]
+                ("phase_ns", C.c_int64 * 8), ("phase_max_ns", C.c_int64 * 8)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("phase")}

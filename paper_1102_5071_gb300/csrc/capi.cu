@@ -185,7 +185,7 @@ void fill_stats(const DevStatus& s, cfet_stats* out) {
   out->max_k = s.max_k;
   out->status = s.status;
   out->max_err_est = s.max_err;
-  for (int i = 0; i < 6; ++i) {
+  for (int i = 0; i < 8; ++i) {
     out->phase_ns[i] = s.n_exp > 0 && s.phase_ns[i] > 0 ? s.phase_ns[i] : 0;
     out->phase_max_ns[i] = s.phase_max_ns[i];
   }
@@ -383,8 +383,8 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
   {
     // FP64 kernel: block_size threads (<= 256); fixed-point and mixed-precision
     // kernels: 2 * block_size workers + one control warp (<= 1024 threads)
-    // (the latter are compiled for at most 800 threads per CTA)
-    const int lim = (o.precision == CFET_PREC_F64) ? 256 : 384;
+    // (the latter are compiled for at most CFET_CTL_MAX_THREADS threads per CTA)
+    const int lim = (o.precision == CFET_PREC_F64) ? 256 : ((CFET_CTL_MAX_THREADS - 32) / 2) & ~31;
     if (o.block_size < 32 || o.block_size > lim || o.block_size % 32)
       return fail(nullptr, CFET_EINVAL, "block_size must be a multiple of 32 in [32, 256] (FP64) or [32, 384]");
   }

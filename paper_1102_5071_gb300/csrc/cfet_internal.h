@@ -41,8 +41,8 @@ struct DevStatus {
   double max_err;
   long long rec_pos;   // next record slot
   long long forced_pos;  // next forced slot
-  long long phase_ns[6];      // see cfet_stats.phase_ns (sum over CTAs)
-  long long phase_max_ns[6];  // max over CTAs
+  long long phase_ns[8];      // see cfet_stats.phase_ns (sum over CTAs)
+  long long phase_max_ns[8];  // max over CTAs
 };
 
 // Spin chain operator family: H0 = XXZ chain, V_k = transverse fields.

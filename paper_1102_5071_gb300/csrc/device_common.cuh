@@ -277,11 +277,20 @@ static __device__ __forceinline__ double2 apply_spin_at(const double2* q, int x,
 // y = exp(-i ts T) e_1 for the k x k real symmetric tridiagonal T (diagonal
 // a[0..k-1], off-diagonal b[0..k-2]); executed by one warp, rows r = lane and
 // lane + 32.  Method: spectral shift by the Gershgorin centre sigma, S equal
-// substeps with |ts| rho / S <= 1 (rho the Gershgorin radius), each a Taylor
-// series of kSmallTaylorTerms terms; exp(-i ts T) = e^{-i ts sigma}
-// exp(-i ts (T - sigma)).
+// substeps with x = |ts| rho / S <= 1 (rho the Gershgorin radius), each a
+// Taylor series of n(x) terms, n(x) the smallest count in {10, 12, 15,
+// kSmallTaylorTerms} with x^(n+1) / (n+1)! below 1e-17 for the x range;
+// exp(-i ts T) = e^{-i ts sigma} exp(-i ts (T - sigma)).
+// The FP64 units of this GPU issue one warp instruction per many cycles, so
+// the per-term work is kept to one multiply and two FMAs per row and part:
+// the shifted diagonal and both couplings of a row stay in registers and the
+// term factors hstep / n come from a table of reciprocals.
+__constant__ double kInvN[kSmallTaylorTerms + 1] = {
+    0.0, 1.0, 1.0 / 2, 1.0 / 3, 1.0 / 4, 1.0 / 5, 1.0 / 6, 1.0 / 7, 1.0 / 8, 1.0 / 9, 1.0 / 10,
+    1.0 / 11, 1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15, 1.0 / 16, 1.0 / 17, 1.0 / 18};
+
 static __device__ void small_expm_e1(int k, const double* a, const double* b, double ts, double* yr, double* yi,
-                              double* tr, double* ti) {
+                                     double* tr, double* ti) {
   const int lane = threadIdx.x & 31;
   double lo = 1e300, hi = -1e300;
   for (int r = lane; r < k; r += 32) {
@@ -302,47 +311,50 @@ static __device__ void small_expm_e1(int k, const double* a, const double* b, do
   if (sr == sr) S = sr < 65536.0 ? (int)ceil(sr) : 65536;
   if (S < 1) S = 1;
   const double hstep = ts / S;
-  // rows owned by this lane
+  const double x = sr / S;
+  const int nterms = x > 0.5 ? kSmallTaylorTerms : (x > 0.25 ? 15 : (x > 0.1 ? 12 : 10));
+  // rows owned by this lane: shifted diagonal and couplings in registers
   const int r0 = lane, r1 = lane + 32;
-  double ar0 = 0, ai0 = 0, ar1 = 0, ai1 = 0;  // accumulators (current y)
-  if (r0 < k) { ar0 = (r0 == 0) ? 1.0 : 0.0; ai0 = 0.0; }
-  if (r1 < k) { ar1 = 0.0; ai1 = 0.0; }
+  const bool on0 = r0 < k, on1 = r1 < k;
+  const double d0 = on0 ? a[r0] - sig : 0.0, d1 = on1 ? a[r1] - sig : 0.0;
+  const double bl0 = (on0 && r0 > 0) ? b[r0 - 1] : 0.0, br0 = (on0 && r0 < k - 1) ? b[r0] : 0.0;
+  const double bl1 = on1 ? b[r1 - 1] : 0.0, br1 = (on1 && r1 < k - 1) ? b[r1] : 0.0;
+  double ar0 = (r0 == 0) ? 1.0 : 0.0, ai0 = 0.0, ar1 = 0.0, ai1 = 0.0;  // current y
   for (int sidx = 0; sidx < S; ++sidx) {
     double t_r0 = ar0, t_i0 = ai0, t_r1 = ar1, t_i1 = ai1;
-    if (r0 < k) { tr[r0] = t_r0; ti[r0] = t_i0; }
-    if (r1 < k) { tr[r1] = t_r1; ti[r1] = t_i1; }
+    if (on0) { tr[r0] = t_r0; ti[r0] = t_i0; }
+    if (on1) { tr[r1] = t_r1; ti[r1] = t_i1; }
     __syncwarp();
-    for (int n = 1; n <= kSmallTaylorTerms; ++n) {
-      const double c = hstep / n;
+    for (int n = 1; n <= nterms; ++n) {
+      const double c = hstep * kInvN[n];
       double zr0 = 0, zi0 = 0, zr1 = 0, zi1 = 0;
-      if (r0 < k) {
-        zr0 = (a[r0] - sig) * t_r0;
-        zi0 = (a[r0] - sig) * t_i0;
-        if (r0 > 0) { zr0 = fma(b[r0 - 1], tr[r0 - 1], zr0); zi0 = fma(b[r0 - 1], ti[r0 - 1], zi0); }
-        if (r0 < k - 1) { zr0 = fma(b[r0], tr[r0 + 1], zr0); zi0 = fma(b[r0], ti[r0 + 1], zi0); }
+      if (on0) {
+        const double lr = r0 > 0 ? tr[r0 - 1] : 0.0, li = r0 > 0 ? ti[r0 - 1] : 0.0;
+        const double rr = r0 < k - 1 ? tr[r0 + 1] : 0.0, ri = r0 < k - 1 ? ti[r0 + 1] : 0.0;
+        zr0 = fma(br0, rr, fma(bl0, lr, d0 * t_r0));
+        zi0 = fma(br0, ri, fma(bl0, li, d0 * t_i0));
       }
-      if (r1 < k) {
-        zr1 = (a[r1] - sig) * t_r1;
-        zi1 = (a[r1] - sig) * t_i1;
-        zr1 = fma(b[r1 - 1], tr[r1 - 1], zr1);
-        zi1 = fma(b[r1 - 1], ti[r1 - 1], zi1);
-        if (r1 < k - 1) { zr1 = fma(b[r1], tr[r1 + 1], zr1); zi1 = fma(b[r1], ti[r1 + 1], zi1); }
+      if (on1) {
+        const double lr = tr[r1 - 1], li = ti[r1 - 1];
+        const double rr = r1 < k - 1 ? tr[r1 + 1] : 0.0, ri = r1 < k - 1 ? ti[r1 + 1] : 0.0;
+        zr1 = fma(br1, rr, fma(bl1, lr, d1 * t_r1));
+        zi1 = fma(br1, ri, fma(bl1, li, d1 * t_i1));
       }
       __syncwarp();
       // t <- (-i c) z
       t_r0 = c * zi0; t_i0 = -c * zr0;
       t_r1 = c * zi1; t_i1 = -c * zr1;
       ar0 += t_r0; ai0 += t_i0; ar1 += t_r1; ai1 += t_i1;
-      if (r0 < k) { tr[r0] = t_r0; ti[r0] = t_i0; }
-      if (r1 < k) { tr[r1] = t_r1; ti[r1] = t_i1; }
+      if (on0) { tr[r0] = t_r0; ti[r0] = t_i0; }
+      if (on1) { tr[r1] = t_r1; ti[r1] = t_i1; }
       __syncwarp();
     }
   }
   double sn, cs;
   sincos(ts * sig, &sn, &cs);
   // multiply by e^{-i ts sig} = cs - i sn
-  if (r0 < k) { yr[r0] = ar0 * cs + ai0 * sn; yi[r0] = ai0 * cs - ar0 * sn; }
-  if (r1 < k) { yr[r1] = ar1 * cs + ai1 * sn; yi[r1] = ai1 * cs - ar1 * sn; }
+  if (on0) { yr[r0] = ar0 * cs + ai0 * sn; yi[r0] = ai0 * cs - ar0 * sn; }
+  if (on1) { yr[r1] = ar1 * cs + ai1 * sn; yi[r1] = ai1 * cs - ar1 * sn; }
   __syncwarp();
 }
 

@@ -34,6 +34,12 @@
 #include "cfet_internal.h"
 #include "device_common.cuh"
 
+// Spin apply on two elements per thread and loop iteration (twice the
+// independent neighbour loads per warp; 1 = on).
+#ifndef CFET_C64_PAIRS
+#define CFET_C64_PAIRS 1
+#endif
+
 namespace cfet {
 
 // ------------------------------------------------------------------ compensated sums
@@ -133,6 +139,74 @@ __device__ __forceinline__ float2 c_apply_spin(const float2* __restrict__ q, con
     ui = fmaf(c.cp, w.y, ui);
   }
   return make_float2(ur, ui);
+}
+
+// Two elements x and x2 per call: the neighbour loads of both are issued in
+// the same loop iterations (twice the independent requests per warp).
+__device__ __forceinline__ void c_apply_spin2(const float2* __restrict__ q, const float2* __restrict__ qm, int x,
+                                              int x2, const OpSpinC& op, const CConst& c, const float* bx,
+                                              float2& r1, float2& r2) {
+  const int N = op.N, L = op.lo_bits;
+  const float d1 = c.cz * (__ldg(op.dz_lo + (x & ((1 << L) - 1))) + __ldg(op.dz_hi + (x >> (L - 1))));
+  const float d2 = c.cz * (__ldg(op.dz_lo + (x2 & ((1 << L) - 1))) + __ldg(op.dz_hi + (x2 >> (L - 1))));
+  const float2 v1 = q[x], v2 = q[x2];
+  float ur1 = d1 * v1.x, ui1 = d1 * v1.y, ur2 = d2 * v2.x, ui2 = d2 * v2.y;
+  float hr1 = 0.f, hi1 = 0.f, hr2 = 0.f, hi2 = 0.f;
+  const unsigned mask = (1u << (N - 1)) - 1u;
+  const unsigned anti1 = ((unsigned)x ^ ((unsigned)x >> 1)) & mask;
+  const unsigned anti2 = ((unsigned)x2 ^ ((unsigned)x2 >> 1)) & mask;
+#pragma unroll 4
+  for (int i = 0; i < N - 1; ++i) {
+    if ((anti1 >> i) & 1u) {
+      const float2 w = q[x ^ (3 << i)];
+      hr1 += w.x;
+      hi1 += w.y;
+    }
+    if ((anti2 >> i) & 1u) {
+      const float2 w = q[x2 ^ (3 << i)];
+      hr2 += w.x;
+      hi2 += w.y;
+    }
+  }
+  ur1 = fmaf(c.ch, hr1, ur1);
+  ui1 = fmaf(c.ch, hi1, ui1);
+  ur2 = fmaf(c.ch, hr2, ur2);
+  ui2 = fmaf(c.ch, hi2, ui2);
+  if (op.uniform) {
+    float xr1 = 0.f, xi1 = 0.f, xr2 = 0.f, xi2 = 0.f;
+#pragma unroll 4
+    for (int i = 0; i < N; ++i) {
+      const float2 w1 = q[x ^ (1 << i)];
+      const float2 w2 = q[x2 ^ (1 << i)];
+      xr1 += w1.x;
+      xi1 += w1.y;
+      xr2 += w2.x;
+      xi2 += w2.y;
+    }
+    ur1 = fmaf(c.cx, xr1, ur1);
+    ui1 = fmaf(c.cx, xi1, ui1);
+    ur2 = fmaf(c.cx, xr2, ur2);
+    ui2 = fmaf(c.cx, xi2, ui2);
+  } else {
+#pragma unroll 4
+    for (int i = 0; i < N; ++i) {
+      const float2 w1 = q[x ^ (1 << i)];
+      const float2 w2 = q[x2 ^ (1 << i)];
+      ur1 = fmaf(bx[i], w1.x, ur1);
+      ui1 = fmaf(bx[i], w1.y, ui1);
+      ur2 = fmaf(bx[i], w2.x, ur2);
+      ui2 = fmaf(bx[i], w2.y, ui2);
+    }
+  }
+  if (c.use_prev) {
+    const float2 w1 = qm[x], w2 = qm[x2];
+    ur1 = fmaf(c.cp, w1.x, ur1);
+    ui1 = fmaf(c.cp, w1.y, ui1);
+    ur2 = fmaf(c.cp, w2.x, ur2);
+    ui2 = fmaf(c.cp, w2.y, ui2);
+  }
+  r1 = make_float2(ur1, ui1);
+  r2 = make_float2(ur2, ui2);
 }
 
 __device__ __forceinline__ float2 c_apply_dia(const float2* __restrict__ q, const float2* __restrict__ qm, int r,
@@ -256,7 +330,8 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
   unsigned long long* partR = partA + 4 * G;
   DevStatus* st = p.st;
   const bool glead = (blockIdx.x == 0) && lead;
-  long long tacc[6] = {0, 0, 0, 0, 0, 0};
+  long long tacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long twe = 0;  // thread 0: end of its last worker loop
   const bool fixed_k = p.tol <= 0.0;
   const bool forced = p.f_nsub != nullptr;
   long long fpos = st->forced_pos;
@@ -351,7 +426,23 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
             float2* u = Q(it + 1);
             float s = 0.f, cc = 0.f;
             const long long tw0 = sm_clock();
-            for (int x = wx0; x < wxe; x += wstep) {
+            int x = wx0;
+#if CFET_C64_PAIRS
+            if constexpr (FAMILY == kFamilySpin) {
+              for (; x + wstep < wxe; x += 2 * wstep) {
+                float2 h1, h2;
+                c_apply_spin2(q, qm, x, x + wstep, op, c, S.bx, h1, h2);
+                u[x] = h1;
+                u[x + wstep] = h2;
+                const float2 v1 = q[x], v2 = q[x + wstep];
+                ff_add_prod(s, cc, v1.x, h1.x);
+                ff_add_prod(s, cc, v1.y, h1.y);
+                ff_add_prod(s, cc, v2.x, h2.x);
+                ff_add_prod(s, cc, v2.y, h2.y);
+              }
+            }
+#endif
+            for (; x < wxe; x += wstep) {
               float2 hv;
               if constexpr (FAMILY == kFamilySpin) hv = c_apply_spin(q, qm, x, op, c, S.bx);
               else hv = c_apply_dia(q, qm, x, dim, op, c);
@@ -361,13 +452,18 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
               ff_add_prod(s, cc, v.y, hv.y);
             }
             c_worker_partial(S, s, cc);
-            if (tid == 0) tacc[0] += sm_clock() - tw0;
+            if (tid == 0) {
+              twe = sm_clock();
+              tacc[0] += twe - tw0;
+            }
           } else if (pend) {
+            const long long te0 = sm_clock();
             const double err = c_estimate(S, it - 1, remaining);
             if (lane == 0) {
               S.err_prev = err;
               S.stop_prev = err <= p.tol * remaining / p.tau;
               S.y_ready = S.stop_prev;
+              tacc[6] += sm_clock() - te0;
             }
             __syncwarp();
           }
@@ -387,6 +483,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
             if (lane == 0) tacc[1] += sm_clock() - tc0 - (tacc[5] - sp0);
           }
           __syncthreads();
+          if (tid == 0) tacc[7] += sm_clock() - twe;
           if (S.abort_flag) return;
           if (S.stop_prev) {  // the deferred estimate accepted it-1
             it -= 1;
@@ -409,7 +506,10 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
               ff_add_prod(s, cc, w.y, w.y);
             }
             c_worker_partial(S, s, cc);
-            if (tid == 0) tacc[2] += sm_clock() - tw0;
+            if (tid == 0) {
+              twe = sm_clock();
+              tacc[2] += twe - tw0;
+            }
           }
           __syncthreads();
           if (ctl) {
@@ -457,6 +557,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
             if (lane == 0) tacc[3] += sm_clock() - tc0 - (tacc[5] - sp0);
           }
           __syncthreads();
+          if (tid == 0) tacc[7] += sm_clock() - twe;
           if (S.abort_flag) return;
           if (S.accept_now) {
             acc_err = S.err_now;
@@ -499,6 +600,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
       if (acc_k > 0) {
         // -------- reconstruct q_1 <- beta0 sum_i y_i s_i q_i
         if (ctl) {
+          const long long tr0 = sm_clock();
           if (!S.y_ready) small_expm_e1(acc_k, S.alpha + 1, S.beta + 1, ts, S.yr, S.yi, S.tr, S.ti);
           __syncwarp();
           for (int i = lane; i < acc_k; i += 32) {
@@ -506,6 +608,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
             S.cr[i] = (float)(f * S.yr[i]);
             S.ci[i] = (float)(f * S.yi[i]);
           }
+          if (lane == 0) tacc[6] += sm_clock() - tr0;
         }
         __syncthreads();
         if (!ctl) {
@@ -525,7 +628,10 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
             ff_add_prod(s, cc, im, im);
           }
           c_worker_partial(S, s, cc);
-          if (tid == 0) tacc[4] += sm_clock() - tw0;
+          if (tid == 0) {
+              twe = sm_clock();
+              tacc[4] += twe - tw0;
+            }
         }
         __syncthreads();
         if (ctl) {
@@ -537,6 +643,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
           }
         }
         __syncthreads();
+        if (tid == 0) tacc[7] += sm_clock() - twe;
         if (S.abort_flag) return;
       }
       if (glead && p.r_k != nullptr) {
@@ -569,7 +676,10 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
     if (max_err > st->max_err) st->max_err = max_err;
   }
   if (tid == 0 || lead) {  // every CTA: mean and max of its phase times
-    for (int i = (tid == 0 ? 0 : 1); i < 6; i += 2) {
+    // thread 0 holds the worker slots 0, 2, 4, 7; the control lane 1, 3, 5, 6
+    const int mine[2][4] = {{0, 2, 4, 7}, {1, 3, 5, 6}};
+    for (int j = 0; j < 4; ++j) {
+      const int i = mine[tid == 0 ? 0 : 1][j];
       atomicAdd((unsigned long long*)&st->phase_ns[i], (unsigned long long)(tacc[i] / G));
       atomicMax(&st->phase_max_ns[i], tacc[i]);
     }

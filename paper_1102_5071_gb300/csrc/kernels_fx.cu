@@ -37,6 +37,11 @@
 #include "cfet_internal.h"
 #include "device_common.cuh"
 
+// Spin apply on two elements per thread and loop iteration (1 = on).
+#ifndef CFET_FX_PAIRS
+#define CFET_FX_PAIRS 1
+#endif
+
 namespace cfet {
 
 // ------------------------------------------------------------------ fixed-point helpers
@@ -256,6 +261,77 @@ __device__ __forceinline__ longlong2 fx_apply_spin(const longlong2* q, const lon
   return make_longlong2(ur, ui);
 }
 
+// Two elements x and x2 per call: the neighbour loads of both are issued in
+// the same loop iterations (twice the independent requests per warp).
+__device__ __forceinline__ void fx_apply_spin2(const longlong2* q, const longlong2* qm, int x, int x2,
+                                               const OpSpinFx& op, const FxConstA& c, const long long* mb,
+                                               longlong2& r1, longlong2& r2) {
+  const int N = op.N, L = op.lo_bits;
+  const long long dz1 = __ldg(op.DZ_lo + (x & ((1 << L) - 1))) + __ldg(op.DZ_hi + (x >> (L - 1)));
+  const long long dz2 = __ldg(op.DZ_lo + (x2 & ((1 << L) - 1))) + __ldg(op.DZ_hi + (x2 >> (L - 1)));
+  const long long Dp1 = fx_mulhi(c.m_cz, dz1 << 1) << 3;
+  const long long Dp2 = fx_mulhi(c.m_cz, dz2 << 1) << 3;
+  const longlong2 v1 = q[x], v2 = q[x2];
+  long long ur1 = fx_mulhi(Dp1, v1.x << c.pk), ui1 = fx_mulhi(Dp1, v1.y << c.pk);
+  long long ur2 = fx_mulhi(Dp2, v2.x << c.pk), ui2 = fx_mulhi(Dp2, v2.y << c.pk);
+  long long hr1 = 0, hi1 = 0, hr2 = 0, hi2 = 0;
+  const unsigned mask = (1u << (N - 1)) - 1u;
+  const unsigned anti1 = ((unsigned)x ^ ((unsigned)x >> 1)) & mask;
+  const unsigned anti2 = ((unsigned)x2 ^ ((unsigned)x2 >> 1)) & mask;
+#pragma unroll 4
+  for (int i = 0; i < N - 1; ++i) {
+    if ((anti1 >> i) & 1u) {
+      const longlong2 w = q[x ^ (3 << i)];
+      hr1 += w.x;
+      hi1 += w.y;
+    }
+    if ((anti2 >> i) & 1u) {
+      const longlong2 w = q[x2 ^ (3 << i)];
+      hr2 += w.x;
+      hi2 += w.y;
+    }
+  }
+  ur1 += fx_mulhi(c.m_hop, hr1 << c.ph);
+  ui1 += fx_mulhi(c.m_hop, hi1 << c.ph);
+  ur2 += fx_mulhi(c.m_hop, hr2 << c.ph);
+  ui2 += fx_mulhi(c.m_hop, hi2 << c.ph);
+  if (op.uniform) {
+    long long xr1 = 0, xi1 = 0, xr2 = 0, xi2 = 0;
+#pragma unroll 4
+    for (int i = 0; i < N; ++i) {
+      const longlong2 w1 = q[x ^ (1 << i)];
+      const longlong2 w2 = q[x2 ^ (1 << i)];
+      xr1 += w1.x;
+      xi1 += w1.y;
+      xr2 += w2.x;
+      xi2 += w2.y;
+    }
+    ur1 += fx_mulhi(c.m_x, xr1 << c.px);
+    ui1 += fx_mulhi(c.m_x, xi1 << c.px);
+    ur2 += fx_mulhi(c.m_x, xr2 << c.px);
+    ui2 += fx_mulhi(c.m_x, xi2 << c.px);
+  } else {
+#pragma unroll 4
+    for (int i = 0; i < N; ++i) {
+      const longlong2 w1 = q[x ^ (1 << i)];
+      const longlong2 w2 = q[x2 ^ (1 << i)];
+      ur1 += fx_mulhi(mb[i], w1.x << c.pk);
+      ui1 += fx_mulhi(mb[i], w1.y << c.pk);
+      ur2 += fx_mulhi(mb[i], w2.x << c.pk);
+      ui2 += fx_mulhi(mb[i], w2.y << c.pk);
+    }
+  }
+  if (c.use_prev) {
+    const longlong2 w1 = qm[x], w2 = qm[x2];
+    ur1 += fx_mulhi(c.m_p, w1.x << c.pp);
+    ui1 += fx_mulhi(c.m_p, w1.y << c.pp);
+    ur2 += fx_mulhi(c.m_p, w2.x << c.pp);
+    ui2 += fx_mulhi(c.m_p, w2.y << c.pp);
+  }
+  r1 = make_longlong2(ur1, ui1);
+  r2 = make_longlong2(ur2, ui2);
+}
+
 __device__ __forceinline__ longlong2 fx_apply_dia(const longlong2* q, const longlong2* qm, int r, int dim,
                                                   const OpDiaFx& op, const FxConstA& c) {
   long long ur = 0, ui = 0;
@@ -465,7 +541,8 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
   const bool glead = (blockIdx.x == 0) && lead;
   // trace (see cfet_stats.phase_ns): worker loop times by thread 0, control
   // own-time and barrier waits by the control lane 0, in SM clock cycles
-  long long tacc[6] = {0, 0, 0, 0, 0, 0};
+  long long tacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long twe = 0;  // thread 0: end of its last worker loop
   const bool fixed_k = p.tol <= 0.0;
   const bool forced = p.f_nsub != nullptr;
 
@@ -605,7 +682,22 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
             __int128 a2 = 0;
             long long mx = 0;
             const long long tw0 = sm_clock();
-            for (int x = wx0; x < wxe; x += wstep) {
+            int x = wx0;
+#if CFET_FX_PAIRS
+            if constexpr (FAMILY == kFamilySpin) {
+              for (; x + wstep < wxe; x += 2 * wstep) {
+                longlong2 h1, h2;
+                fx_apply_spin2(q, qm, x, x + wstep, op, c, S.mb, h1, h2);
+                u[x] = h1;
+                u[x + wstep] = h2;
+                const longlong2 v1 = q[x], v2 = q[x + wstep];
+                a2 += (__int128)v1.x * h1.x + (__int128)v1.y * h1.y;
+                a2 += (__int128)v2.x * h2.x + (__int128)v2.y * h2.y;
+                mx = max(mx, max(fx_absmax(h1.x, h1.y), fx_absmax(h2.x, h2.y)));
+              }
+            }
+#endif
+            for (; x < wxe; x += wstep) {
               longlong2 hv;
               if constexpr (FAMILY == kFamilySpin) hv = fx_apply_spin(q, qm, x, op, c, S.mb);
               else hv = fx_apply_dia(q, qm, x, dim, op, c);
@@ -615,13 +707,18 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
               mx = max(mx, fx_absmax(hv.x, hv.y));
             }
             fx_worker_partial(S, a2, mx);
-            if (tid == 0) tacc[0] += sm_clock() - tw0;
+            if (tid == 0) {
+              twe = sm_clock();
+              tacc[0] += twe - tw0;
+            }
           } else if (pend) {
+            const long long te0 = sm_clock();
             const double err = fx_estimate(S, it - 1, remaining);
             if (lane == 0) {
               S.err_prev = err;
               S.stop_prev = err <= p.tol * remaining / p.tau;
               S.y_ready = S.stop_prev;
+              tacc[6] += sm_clock() - te0;
             }
             __syncwarp();
           }
@@ -656,6 +753,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
             if (lane == 0) tacc[1] += sm_clock() - tc0 - (tacc[5] - sp0);
           }
           __syncthreads();
+          if (tid == 0) tacc[7] += sm_clock() - twe;
           if (S.abort_flag) return;
           if (S.stop_prev) {  // the deferred estimate accepted it-1
             it -= 1;
@@ -681,7 +779,10 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
               mx = max(mx, fx_absmax(wr, wi));
             }
             fx_worker_partial(S, b2, mx);
-            if (tid == 0) tacc[2] += sm_clock() - tw0;
+            if (tid == 0) {
+              twe = sm_clock();
+              tacc[2] += twe - tw0;
+            }
           }
           __syncthreads();
           if (ctl) {
@@ -732,6 +833,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
             if (lane == 0) tacc[3] += sm_clock() - tc0 - (tacc[5] - sp0);
           }
           __syncthreads();
+          if (tid == 0) tacc[7] += sm_clock() - twe;
           if (S.abort_flag) return;
           if (S.accept_now) {
             acc_err = S.err_now;
@@ -774,6 +876,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
       if (acc_k > 0) {
         // -------- reconstruct q_1 <- beta0 sum_i y_i s_i q_i
         if (ctl) {
+          const long long tr0 = sm_clock();
           if (!S.y_ready) small_expm_e1(acc_k, S.alpha + 1, S.beta + 1, ts, S.yr, S.yi, S.tr, S.ti);
           __syncwarp();
           double bnd = 0.0;
@@ -798,7 +901,10 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
             S.crm[i] = fx_fold(mr.m, S.csr[i]);
             S.cim[i] = fx_fold(mi.m, S.csi[i]);
           }
-          if (lane == 0) S.Epsi = Ep;
+          if (lane == 0) {
+            S.Epsi = Ep;
+            tacc[6] += sm_clock() - tr0;
+          }
         }
         __syncthreads();
         if (!ctl) {
@@ -826,7 +932,10 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
             mx = max(mx, fx_absmax(re, im));
           }
           fx_worker_partial(S, a2, mx);
-          if (tid == 0) tacc[4] += sm_clock() - tw0;
+          if (tid == 0) {
+              twe = sm_clock();
+              tacc[4] += twe - tw0;
+            }
         }
         __syncthreads();
         if (ctl) {
@@ -841,6 +950,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
           }
         }
         __syncthreads();
+        if (tid == 0) tacc[7] += sm_clock() - twe;
         if (S.abort_flag) return;
       }
       if (glead && p.r_k != nullptr) {
@@ -873,7 +983,10 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
     if (max_err > st->max_err) st->max_err = max_err;
   }
   if (tid == 0 || lead) {  // every CTA: mean and max of its phase times
-    for (int i = (tid == 0 ? 0 : 1); i < 6; i += 2) {
+    // thread 0 holds the worker slots 0, 2, 4, 7; the control lane 1, 3, 5, 6
+    const int mine[2][4] = {{0, 2, 4, 7}, {1, 3, 5, 6}};
+    for (int j = 0; j < 4; ++j) {
+      const int i = mine[tid == 0 ? 0 : 1][j];
       atomicAdd((unsigned long long*)&st->phase_ns[i], (unsigned long long)(tacc[i] / G));
       atomicMax(&st->phase_max_ns[i], tacc[i]);
     }

@@ -165,7 +165,7 @@ extern "C" cfet_status cfet_expv_chain_static(int32_t nsites, double J, double D
     stats->max_k = hs.max_k;
     stats->status = hs.status;
     stats->max_err_est = hs.max_err;
-    for (int i = 0; i < 6; ++i) {
+    for (int i = 0; i < 8; ++i) {
       stats->phase_ns[i] = hs.phase_ns[i];
       stats->phase_max_ns[i] = hs.phase_max_ns[i];
     }
