@@ -405,6 +405,15 @@ cfet_status cfet_fidelity_grad(cfet_ctx* ctx, const void* psi0, const void* phi,
                                double omega, double phase, int64_t checkpoint_every, void* stream, double* loss,
                                double* grad, cfet_grad_stats* gstats);
 
+/* Diagnostic of the bounded device waits (no counterpart in the paper): two
+ * CTAs, of which one enters a grid-wide wait that the other never joins —
+ * which = 0: the record exchange of the fixed-point / complex64 kernels,
+ * 1: the grid barrier of the FP64 kernel.  The wait must give up after
+ * timeout_s (in (0, 10] s), record CFET_ETIMEOUT and return; no fault, no
+ * hang.  Returns CFET_OK when the device status read back (device_status) is
+ * CFET_ETIMEOUT, CFET_ECUDA otherwise.  Synchronises the device.            */
+cfet_status cfet_selftest_wait_timeout(int32_t which, double timeout_s, int32_t* device_status);
+
 /* Dimension and drive-operator count of ctx (for bindings).                 */
 int64_t cfet_dim(const cfet_ctx* ctx);
 int32_t cfet_num_drives(const cfet_ctx* ctx);

@@ -125,6 +125,7 @@ def load() -> C.CDLL:
         "cfet_fidelity_grad": (C.c_int, [vp, vp, vp, C.c_double, C.c_double, C.c_int64, C.c_int32, C.c_double,
                                          C.c_int32, c_double_p, C.c_double, C.c_double, C.c_int64, vp, c_double_p,
                                          c_double_p, C.POINTER(cfet_grad_stats)]),
+        "cfet_selftest_wait_timeout": (C.c_int, [C.c_int32, C.c_double, c_int32_p]),
         "cfet_dim": (C.c_int64, [vp]),
         "cfet_num_drives": (C.c_int32, [vp]),
     }
@@ -141,5 +142,5 @@ EXPORTED = ["cfet_options_default", "cfet_scheme_info", "cfet_create", "cfet_des
             "cfet_kernel_time_ms", "cfet_expv_chain_static",
             "cfet_batch_create", "cfet_batch_destroy", "cfet_batch_last_error", "cfet_batch_size",
             "cfet_batch_propagate", "cfet_batch_tune", "cfet_batch_get_plan", "cfet_batch_set_plan",
-            "cfet_batch_kernel_time_ms", "cfet_fidelity_grad",
+            "cfet_batch_kernel_time_ms", "cfet_fidelity_grad", "cfet_selftest_wait_timeout",
             "cfet_dim", "cfet_num_drives"]

@@ -903,6 +903,32 @@ cfet_status cfet_sync(cfet_ctx* ctx, void* stream, cfet_stats* stats) {
   return finish(ctx, (cudaStream_t)stream, stats);
 }
 
+cfet_status cfet_selftest_wait_timeout(int32_t which, double timeout_s, int32_t* device_status) {
+  if ((which != 0 && which != 1) || !(timeout_s > 0.0) || timeout_s > 10.0 || !device_status)
+    return fail(nullptr, CFET_EINVAL, "selftest: which in {0, 1}, timeout in (0, 10] s, device_status required");
+  cfet_status s = device_available(nullptr);
+  if (s != CFET_OK) return s;
+  unsigned long long* rec = nullptr;
+  unsigned* bar = nullptr;
+  int* st = nullptr;
+  cudaError_t e = cudaMalloc(&rec, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&bar, 2 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMalloc(&st, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(rec, 0, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(bar, 0, 2 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(st, 0, sizeof(int));
+  if (e == cudaSuccess) e = (cudaError_t)launch_wait_selftest(which, rec, bar, st, (long long)(timeout_s * 1e9));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, st, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(rec);
+  cudaFree(bar);
+  cudaFree(st);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "wait self test");
+  *device_status = h;
+  return h == CFET_ETIMEOUT ? CFET_OK : fail(nullptr, CFET_ECUDA, "wait self test: the wait did not time out");
+}
+
 cfet_status cfet_fidelity_grad(cfet_ctx* ctx, const void* psi0, const void* phi, double t0, double dt,
                                int64_t nsteps, int32_t order, double krylov_tol, int32_t nseg, const double* amps,
                                double omega, double phase, int64_t checkpoint_every, void* stream, double* loss,

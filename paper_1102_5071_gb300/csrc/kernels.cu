@@ -482,3 +482,35 @@ int launch_spin_tables(int N, int L, double J, double Delta, const double* h, do
 }
 
 }  // namespace cfet
+
+// ------------------------------------------------------------------ wait-limit self test
+namespace cfet {
+namespace {
+// Two CTAs of one warp: CTA 0 enters a grid-wide wait (record exchange or
+// grid barrier) that CTA 1 never joins; the wait gives up after timeout_ns,
+// records CFET_ETIMEOUT and returns.  Exercises the bounded-wait path of the
+// persistent kernels without a fault or a hang.
+__global__ void k_wait_selftest(int which, unsigned long long* rec, unsigned* bar, int* status,
+                                long long timeout_ns) {
+  __shared__ int s_ok;
+  if (blockIdx.x != 0) return;  // never publishes, never arrives
+  if (which == 0) {
+    struct NoAcc {
+      __device__ void reset() {}
+      __device__ void add(const unsigned (&)[1]) {}
+    } acc;
+    const unsigned mine[1] = {0u};
+    long long spin = 0;
+    ctl_exchange<1>(rec, mine, 1u, false, status, timeout_ns, spin, acc);
+  } else {
+    unsigned gen = 0;
+    grid_barrier(bar, gen, status, timeout_ns, &s_ok);
+  }
+}
+}  // namespace
+
+int launch_wait_selftest(int which, unsigned long long* rec, unsigned* bar, int* status, long long timeout_ns) {
+  k_wait_selftest<<<2, 32>>>(which, rec, bar, status, timeout_ns);
+  return (int)cudaGetLastError();
+}
+}  // namespace cfet

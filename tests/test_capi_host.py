@@ -166,3 +166,11 @@ def test_batch_no_device_gives_enodev(lib):
     b = C.c_void_p()
     ok = _chain_arr([(4, np.zeros(4), np.ones(4)), (6, np.zeros(6), np.ones(6))], keep)
     assert lib.cfet_batch_create(C.byref(b), 2, ok, None) == _capi.CFET_ENODEV and not b.value
+
+
+def test_wait_selftest_validates(lib):
+    st = C.c_int32(0)
+    assert lib.cfet_selftest_wait_timeout(2, 0.1, C.byref(st)) == _capi.CFET_EINVAL
+    assert lib.cfet_selftest_wait_timeout(0, 0.0, C.byref(st)) == _capi.CFET_EINVAL
+    assert lib.cfet_selftest_wait_timeout(0, 20.0, C.byref(st)) == _capi.CFET_EINVAL
+    assert lib.cfet_selftest_wait_timeout(0, 0.1, None) == _capi.CFET_EINVAL
