@@ -172,6 +172,22 @@ def cpu_baseline_sample():
                       f"{platform.machine()} {os.cpu_count()} cores)"}
 
 
+def aggregate_over_ranks(ms, units, device="cuda"):
+    """Whole-job figures of a replicated run: (slowest rank's time in ms, sum of
+    the units over ranks).  With one process it returns its own numbers; under
+    torch.distributed every rank contributes (any backend: nccl on the GPU,
+    gloo in the host tests)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(units)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -250,16 +266,7 @@ def run_gpu(args):
     kernel_ms = prop.kernel_time_ms()
     clocks = clk.summary()
     n_app = stats["n_applies"]
-    times = torch.tensor([ms, float(n_app), kernel_ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        import torch.distributed as dist
-        tmax = times.clone()
-        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-        tot = times.clone()
-        dist.all_reduce(tot[1:2], op=dist.ReduceOp.SUM)
-        ms_max, app_total = float(tmax[0]), float(tot[1])
-    else:
-        ms_max, app_total = ms, float(n_app)
+    ms_max, app_total = aggregate_over_ranks(ms, n_app)
     value = app_total / (ms_max * 1e-3)
 
     # roofline of the persistent kernel (one launch per 256 steps)
@@ -292,12 +299,8 @@ def run_gpu(args):
     e2e_s = time.perf_counter() - te
     e2e_val = e2e_app / e2e_s if e2e_steps else None
     if ws > 1 and e2e_steps:
-        import torch.distributed as dist
-        tt = torch.tensor([e2e_s, float(e2e_app)], dtype=torch.float64, device="cuda")
-        tm = tt.clone()
-        dist.all_reduce(tm[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt[1:2], op=dist.ReduceOp.SUM)
-        e2e_val = float(tt[1]) / float(tm[0])
+        s_max, app_all = aggregate_over_ranks(e2e_s, e2e_app)
+        e2e_val = app_all / s_max
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
