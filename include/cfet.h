@@ -215,7 +215,8 @@ void cfet_options_default(cfet_options* opt);
  *  f, f_user: nV drive callbacks and their user pointers (f_user may be NULL)
  *  opt     : options (NULL = defaults)
  * Copies all operator data to the device and allocates the Krylov workspace
- * ((m_max) x dim complex128) on the current CUDA device.  Errors: CFET_EINVAL
+ * on the current CUDA device: m_max x dim x 16 bytes (FP64), (m_max + 1) x
+ * dim x 16 bytes (fixed point) or x 8 bytes (complex64).  Errors: CFET_EINVAL
  * (inconsistent operators or options), CFET_ENOMEM, CFET_ENODEV.            */
 cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfet_op* V,
                         const cfet_drive_fn* f, void* const* f_user, const cfet_options* opt);
@@ -230,17 +231,20 @@ const char* cfet_last_error(const cfet_ctx* ctx);
 /* Hot path                                                                  */
 /* ------------------------------------------------------------------------ */
 /* Stage operator apply (Sec. 8):  v_out = (c[0] H0 + sum_k c[1+k] V_k) v_in.
- * c: host array of 1+nV doubles.  v_in, v_out: device, dim, must not overlap. */
+ * c: host array of 1+nV doubles.  v_in, v_out: device, dim complex128, must
+ * not overlap.  Always evaluated in FP64, whatever ctx's precision.        */
 cfet_status cfet_apply(cfet_ctx* ctx, const double* c, const void* v_in, void* v_out, void* stream);
 
 /* One stage exponential psi <- exp(-i tau (c[0] H0 + sum_k c[1+k] V_k)) psi by
- * the device Lanczos loop (Sec. 8.1) with Krylov tolerance tol (tol <= 0:
- * fixed Krylov dimension m_max, no substeps).  stats may be NULL.           */
+ * the device Lanczos loop (Sec. 8.1) in ctx's precision, with Krylov
+ * tolerance tol (tol <= 0: fixed Krylov dimension m_max, no substeps).
+ * stats may be NULL.                                                         */
 cfet_status cfet_expv(cfet_ctx* ctx, const double* c, double tau, void* psi, double tol,
                       void* stream, cfet_stats* stats);
 
 /* nsteps CFET steps of length dt from time t0 with the default scheme of
- * `order` (2, 4, 6 or 8): psi(t0 + nsteps dt) <- U psi(t0).  Step n uses
+ * `order` (2, 4, 6 or 8): psi(t0 + nsteps dt) <- U psi(t0), in ctx's
+ * precision (psi is complex128 at the boundary in every precision).  Step n uses
  * t0 + n dt, so a run can be resumed exactly from (psi, t0 + n dt).
  * krylov_tol: absolute Krylov tolerance per stage exponential (<= 0: fixed
  * dimension m_max).  stats may be NULL (then the call does not synchronise). */
