@@ -78,7 +78,7 @@ struct CConst {
 };
 
 struct SmemC {
-  float ws[32], wc[32];          // per-warp compensated partials of the workers
+  float ws[2][32], wc[2][32];    // per-warp compensated partials of the workers (up to 2 sums)
   double alpha[kMaxKrylov + 2];
   double beta[kMaxKrylov + 2];
   double scale[kMaxKrylov + 3];  // 1 / ||q_i||
@@ -90,6 +90,7 @@ struct SmemC {
   float bx[kMaxSites];           // non-uniform fields: b_i s_k
   CConst ca;
   float am;                      // phase B: -alpha_k s_k
+  double wnorm2;                 // ||w||^2 of the current iteration (from the phase-A sums)
   int abort_flag, stop_prev, accept_now, pend, y_ready, acc_h;
   double err_now, err_prev;
   double beta0;
@@ -236,42 +237,63 @@ __device__ __forceinline__ float2 c_apply_dia(const float2* __restrict__ q, cons
 }
 
 // ------------------------------------------------------------------ control warp
-// Worker warps: compensated per-warp partial into shared memory.
-__device__ __forceinline__ void c_worker_partial(SmemC& S, float s, float c) {
+// Worker warps: compensated per-warp partial of sum j into shared memory.
+__device__ __forceinline__ void c_worker_partial(SmemC& S, float s, float c, int j = 0) {
   ff_warp_sum(s, c);
   if ((threadIdx.x & 31) == 0) {
-    S.ws[threadIdx.x >> 5] = s;
-    S.wc[threadIdx.x >> 5] = c;
+    S.ws[j][threadIdx.x >> 5] = s;
+    S.wc[j][threadIdx.x >> 5] = c;
   }
 }
 
 // Float-float accumulation of the exchanged CTA partials (fixed order per lane).
+template <int NS>
 struct FFAcc {
-  float s, c;
-  __device__ void reset() { s = 0.f; c = 0.f; }
-  __device__ void add(const unsigned (&v)[2]) {
-    ff_two_sum(s, c, __uint_as_float(v[0]));
-    c = __fadd_rn(c, __uint_as_float(v[1]));
+  float s[NS], c[NS];
+  __device__ void reset() {
+    for (int j = 0; j < NS; ++j) s[j] = c[j] = 0.f;
+  }
+  __device__ void add(const unsigned (&v)[2 * NS]) {
+    for (int j = 0; j < NS; ++j) {
+      ff_two_sum(s[j], c[j], __uint_as_float(v[2 * j]));
+      c[j] = __fadd_rn(c[j], __uint_as_float(v[2 * j + 1]));
+    }
   }
 };
 
-// Control warp: publish the CTA's float-float partial, exchange records with
-// every CTA (the grid barrier), and return the global sum, accumulated in one
-// fixed order and rounded to FP64 once, to all lanes.  Keeping the chain in
-// FP32 pairs avoids long dependent sequences on the 1/64-rate FP64 units.
+// Control warp: publish the CTA's float-float partials of NS sums, exchange
+// records with every CTA (the grid barrier), and return the global sums,
+// accumulated in one fixed order and rounded to FP64 once, to all lanes.
+// Keeping the chain in FP32 pairs avoids long dependent sequences on the
+// 1/64-rate FP64 units.  NS = 0: a pure grid barrier.
+template <int NS>
 __device__ bool c_ctl_reduce(SmemC& S, int NW, unsigned long long* part, unsigned tag, bool fence, int* status,
-                             long long timeout_ns, double& sum, long long& spin) {
+                             long long timeout_ns, double* sum, long long& spin) {
   const int lane = threadIdx.x & 31;
-  float s = lane < NW ? S.ws[lane] : 0.f, c = lane < NW ? S.wc[lane] : 0.f;
-  ff_warp_sum(s, c);
-  const unsigned mine[2] = {__float_as_uint(__shfl_sync(0xffffffffu, s, 0)),
-                            __float_as_uint(__shfl_sync(0xffffffffu, c, 0))};
-  FFAcc acc;
-  if (!ctl_exchange<2>(part, mine, tag, fence, status, timeout_ns, spin, acc)) return false;
-  s = acc.s;
-  c = acc.c;
-  ff_warp_sum(s, c);
-  sum = (double)__shfl_sync(0xffffffffu, s, 0) + (double)__shfl_sync(0xffffffffu, c, 0);
+  constexpr int W = NS > 0 ? 2 * NS : 1;
+  unsigned mine[W];
+  mine[0] = 0u;
+  for (int j = 0; j < NS; ++j) {
+    float s = lane < NW ? S.ws[j][lane] : 0.f, c = lane < NW ? S.wc[j][lane] : 0.f;
+    ff_warp_sum(s, c);
+    mine[2 * j] = __float_as_uint(__shfl_sync(0xffffffffu, s, 0));
+    mine[2 * j + 1] = __float_as_uint(__shfl_sync(0xffffffffu, c, 0));
+  }
+  if constexpr (NS > 0) {
+    FFAcc<NS> acc;
+    if (!ctl_exchange<W>(part, mine, tag, fence, status, timeout_ns, spin, acc)) return false;
+    for (int j = 0; j < NS; ++j) {
+      float s = acc.s[j], c = acc.c[j];
+      ff_warp_sum(s, c);
+      sum[j] = (double)__shfl_sync(0xffffffffu, s, 0) + (double)__shfl_sync(0xffffffffu, c, 0);
+    }
+  } else {
+    struct NoAcc {
+      __device__ void reset() {}
+      __device__ void add(const unsigned (&)[1]) {}
+    } acc;
+    if (!ctl_exchange<1>(part, mine, tag, fence, status, timeout_ns, spin, acc)) return false;
+  }
   return true;
 }
 
@@ -325,9 +347,9 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
   // float-float pair (two tagged words) per CTA; tags continue across launches
   const unsigned tag0 = (unsigned)ld_volatile_i32((const int*)&p.st->tag_base);
   unsigned gen = 0;
-  unsigned long long* partA = reinterpret_cast<unsigned long long*>(p.partials);
-  unsigned long long* partB = partA + 2 * G;
-  unsigned long long* partR = partA + 4 * G;
+  unsigned long long* partA = reinterpret_cast<unsigned long long*>(p.partials);  // 3 sums: 6 words
+  unsigned long long* partB = partA + 6 * G;                                        // barrier: 1 word
+  unsigned long long* partR = partA + 12 * G;                                       // 1 sum: 2 words
   DevStatus* st = p.st;
   const bool glead = (blockIdx.x == 0) && lead;
   long long tacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -360,12 +382,12 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
     }
     __syncthreads();
     if (ctl) {
-      double sum;
-      if (!c_ctl_reduce(S, NW, partB, tag0 + (++gen), true, &st->status, p.timeout_ns, sum, tacc[5])) {
+      double sum[1];
+      if (!c_ctl_reduce<1>(S, NW, partR, tag0 + (++gen), true, &st->status, p.timeout_ns, sum, tacc[5])) {
         if (lane == 0) S.abort_flag = 1;
       } else if (lane == 0) {
         S.abort_flag = ld_volatile_i32(&st->status) != 0;
-        S.beta0 = sqrt(sum);
+        S.beta0 = sqrt(sum[0]);
       }
     }
     __syncthreads();
@@ -424,7 +446,10 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
             const float2* q = Q(it);
             const float2* qm = it > 1 ? Q(it - 1) : q;
             float2* u = Q(it + 1);
-            float s = 0.f, cc = 0.f;
+            // <q,u> and ||u||^2: alpha and ||u - alpha s q||^2 follow from these
+            // two sums (s q is a unit vector: s = 1 / ||q||), so the
+            // orthogonalisation pass needs no reduction of its own
+            float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
             const long long tw0 = sm_clock();
             int x = wx0;
 #if CFET_C64_PAIRS
@@ -435,10 +460,14 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
                 u[x] = h1;
                 u[x + wstep] = h2;
                 const float2 v1 = q[x], v2 = q[x + wstep];
-                ff_add_prod(s, cc, v1.x, h1.x);
-                ff_add_prod(s, cc, v1.y, h1.y);
-                ff_add_prod(s, cc, v2.x, h2.x);
-                ff_add_prod(s, cc, v2.y, h2.y);
+                ff_add_prod(s0, c0, v1.x, h1.x);
+                ff_add_prod(s0, c0, v1.y, h1.y);
+                ff_add_prod(s0, c0, v2.x, h2.x);
+                ff_add_prod(s0, c0, v2.y, h2.y);
+                ff_add_prod(s1, c1, h1.x, h1.x);
+                ff_add_prod(s1, c1, h1.y, h1.y);
+                ff_add_prod(s1, c1, h2.x, h2.x);
+                ff_add_prod(s1, c1, h2.y, h2.y);
               }
             }
 #endif
@@ -448,10 +477,13 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
               else hv = c_apply_dia(q, qm, x, dim, op, c);
               u[x] = hv;
               const float2 v = q[x];
-              ff_add_prod(s, cc, v.x, hv.x);
-              ff_add_prod(s, cc, v.y, hv.y);
+              ff_add_prod(s0, c0, v.x, hv.x);
+              ff_add_prod(s0, c0, v.y, hv.y);
+              ff_add_prod(s1, c1, hv.x, hv.x);
+              ff_add_prod(s1, c1, hv.y, hv.y);
             }
-            c_worker_partial(S, s, cc);
+            c_worker_partial(S, s0, c0, 0);
+            c_worker_partial(S, s1, c1, 1);
             if (tid == 0) {
               twe = sm_clock();
               tacc[0] += twe - tw0;
@@ -470,15 +502,17 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
           __syncthreads();
           if (ctl) {
             const long long tc0 = sm_clock(), sp0 = tacc[5];
-            double sum;
-            if (!c_ctl_reduce(S, NW, partA, tag0 + (++gen), false, &st->status, p.timeout_ns, sum, tacc[5])) {
+            double sum[2];
+            if (!c_ctl_reduce<2>(S, NW, partA, tag0 + (++gen), false, &st->status, p.timeout_ns, sum, tacc[5])) {
               if (lane == 0) S.abort_flag = 1;
             } else if (lane == 0 && !S.stop_prev) {
-              // q_it holds the Lanczos vector times 1/scale[it]
+              // q_it holds the Lanczos vector v_it times 1/scale[it]:
+              // alpha = <v, u>,  ||w||^2 = ||u - alpha v||^2 = ||u||^2 - alpha^2
               const double s_it = S.scale[it];
-              const double alpha = sum * s_it;
+              const double alpha = sum[0] * s_it;
               S.alpha[it] = alpha;
               S.am = (float)(-alpha * s_it);
+              S.wnorm2 = sum[1] - alpha * alpha;
             }
             if (lane == 0) tacc[1] += sm_clock() - tc0 - (tacc[5] - sp0);
           }
@@ -490,73 +524,75 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
             acc_err = S.err_prev;
             break;
           }
-          // -------- phase B(it): w = u - alpha s_it q_it, beta = ||w||
+          // -------- phase B(it): w = u - alpha s_it q_it on the workers; beta
+          // (known from the phase-A sums), the decisions and the next
+          // iteration's constants on the control warp at the same time
           if (!ctl) {
             const float am = S.am;
             const float2* q = Q(it);
             float2* u = Q(it + 1);
-            float s = 0.f, cc = 0.f;
             const long long tw0 = sm_clock();
             for (int x = wx0; x < wxe; x += wstep) {
               const float2 v = q[x];
               const float2 uu = u[x];
-              const float2 w = make_float2(fmaf(am, v.x, uu.x), fmaf(am, v.y, uu.y));
-              u[x] = w;
-              ff_add_prod(s, cc, w.x, w.x);
-              ff_add_prod(s, cc, w.y, w.y);
+              u[x] = make_float2(fmaf(am, v.x, uu.x), fmaf(am, v.y, uu.y));
             }
-            c_worker_partial(S, s, cc);
             if (tid == 0) {
               twe = sm_clock();
               tacc[2] += twe - tw0;
             }
-          }
-          __syncthreads();
-          if (ctl) {
-            const long long tc0 = sm_clock(), sp0 = tacc[5];
-            double sum;
-            if (!c_ctl_reduce(S, NW, partB, tag0 + (++gen), true, &st->status, p.timeout_ns, sum, tacc[5])) {
-              if (lane == 0) S.abort_flag = 1;
-            } else {
-              // beta and 1/beta from one reciprocal square root
-              const double rb = sum > 0.0 ? rsqrt(sum) : 0.0;
-              const double b = sum * rb;
-              const double prev_b = it > 1 ? S.beta[it - 1] : 0.0;
-              const bool breakdown = b <= 1e-13 * (fabs(S.alpha[it]) + prev_b + 1.0);
-              if (lane == 0) {
-                S.beta[it] = b;
-                S.scale[it + 1] = rb;
-              }
-              __syncwarp();
-              int acc_flag = 0, pend_next = 0;
-              double err = 0.0;
-              if (forced) {
-                acc_flag = (it == kf);
-              } else if (fixed_k) {
-                acc_flag = (it == p.m_max) || breakdown;
-              } else if (breakdown) {
-                acc_flag = 1;
-              } else if (it >= p.m_min &&
-                         fabs(remaining) * gersh_width(it, S.alpha + 1, S.beta + 1) <= 2.0 * it) {
-                if (it < klimit) {
-                  pend_next = 1;  // estimate runs during the next apply
-                } else {
-                  err = c_estimate(S, it, remaining);
-                  acc_flag = err <= p.tol * remaining / p.tau;
-                }
-              }
-              if (lane == 0) {
-                S.accept_now = acc_flag;
-                S.pend = pend_next;
-                S.err_now = err;
-                S.y_ready = acc_flag && !forced && !fixed_k && !breakdown;
-              }
-              __syncwarp();
-              if (!acc_flag && it < klimit) c_const_a<FAMILY>(S, op, it + 1);
+          } else {
+            const long long tc0 = sm_clock();
+            // beta and 1/beta from one reciprocal square root (a rounding-level
+            // negative ||w||^2 is an exact breakdown)
+            const double wn = S.wnorm2;
+            const double rb = wn > 0.0 ? rsqrt(wn) : 0.0;
+            const double b = wn > 0.0 ? wn * rb : 0.0;
+            const double prev_b = it > 1 ? S.beta[it - 1] : 0.0;
+            const bool breakdown = b <= 1e-13 * (fabs(S.alpha[it]) + prev_b + 1.0);
+            if (lane == 0) {
+              S.beta[it] = b;
+              S.scale[it + 1] = rb;
             }
-            if (lane == 0) tacc[3] += sm_clock() - tc0 - (tacc[5] - sp0);
+            __syncwarp();
+            int acc_flag = 0, pend_next = 0;
+            double err = 0.0;
+            if (forced) {
+              acc_flag = (it == kf);
+            } else if (fixed_k) {
+              acc_flag = (it == p.m_max) || breakdown;
+            } else if (breakdown) {
+              acc_flag = 1;
+            } else if (it >= p.m_min &&
+                       fabs(remaining) * gersh_width(it, S.alpha + 1, S.beta + 1) <= 2.0 * it) {
+              if (it < klimit) {
+                pend_next = 1;  // estimate runs during the next apply
+              } else {
+                err = c_estimate(S, it, remaining);
+                acc_flag = err <= p.tol * remaining / p.tau;
+              }
+            }
+            if (lane == 0) {
+              S.accept_now = acc_flag;
+              S.pend = pend_next;
+              S.err_now = err;
+              S.y_ready = acc_flag && !forced && !fixed_k && !breakdown;
+            }
+            __syncwarp();
+            if (!acc_flag && it < klimit) c_const_a<FAMILY>(S, op, it + 1);
+            if (lane == 0) tacc[3] += sm_clock() - tc0;
           }
           __syncthreads();
+          const bool last_it = S.accept_now || it >= klimit;
+          if (!last_it) {
+            // every CTA's w must be visible before the next apply reads it
+            if (ctl) {
+              double none[1];
+              if (!c_ctl_reduce<0>(S, NW, partB, tag0 + (++gen), true, &st->status, p.timeout_ns, none, tacc[5]))
+                if (lane == 0) S.abort_flag = 1;
+            }
+            __syncthreads();
+          }
           if (tid == 0) tacc[7] += sm_clock() - twe;
           if (S.abort_flag) return;
           if (S.accept_now) {
@@ -635,11 +671,11 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
         }
         __syncthreads();
         if (ctl) {
-          double sum;
-          if (!c_ctl_reduce(S, NW, partR, tag0 + (++gen), true, &st->status, p.timeout_ns, sum, tacc[5])) {
+          double sum[1];
+          if (!c_ctl_reduce<1>(S, NW, partR, tag0 + (++gen), true, &st->status, p.timeout_ns, sum, tacc[5])) {
             if (lane == 0) S.abort_flag = 1;
           } else if (lane == 0) {
-            S.beta0 = sqrt(sum);
+            S.beta0 = sqrt(sum[0]);
           }
         }
         __syncthreads();
