@@ -192,3 +192,26 @@ def test_batch_edge_cases(torch_cuda):
     bp.propagate(dev, 0.0, 0.02, 1, order=4)
     with pytest.raises(P.CfetError, match="EINVAL"):
         bp.set_plan(3, 256, 9)
+
+
+def test_full_batch_workload_sampled_against_oracle(torch_cuda):
+    # the 256-chain workload (N uniform in 10..16, CF6:5Opt, dt 0.02), tuned
+    # plan, 2 steps; instances of every size compared with the oracle
+    torch = torch_cuda
+    cfg = W.BATCH
+    insts = W.chain_batch(cfg["n"], cfg["n_lo"], cfg["n_hi"])
+    bp = _batch(insts, m_max=cfg["m_max"], precision="f64")
+    bp.tune(0.0, cfg["dt"], order=cfg["order"], tol=cfg["tol"], nsteps=1)
+    host, dev = _states(torch, insts)
+    stats, logs = bp.propagate(dev, 0.0, cfg["dt"], 2, order=cfg["order"], tol=cfg["tol"], record=True)
+    assert all(s["status"] == 0 for s in stats)
+    picked = {}
+    for i, c in enumerate(insts):
+        picked.setdefault(c.N, i)
+    for N, i in sorted(picked.items()):
+        c = insts[i]
+        r, lg, _ = _oracle(c, host[i], 0.0, cfg["dt"], 2, cfg["order"], cfg["tol"], cfg["m_max"])
+        if lg == logs[i]:
+            assert np.linalg.norm(dev[i].cpu().numpy() - r) <= PARITY, (N, i)
+        else:   # a rounding-level decision flip: the result stays within the Krylov tolerance
+            assert np.linalg.norm(dev[i].cpu().numpy() - r) <= 10 * cfg["tol"], (N, i)

@@ -301,3 +301,23 @@ def test_e2e_host_entry_matches_device_entry(torch_cuda, prec):
     h = psi0.copy()
     prop.propagate_host(h, 0.0, 0.02, 5, order=6, tol=1e-10)
     assert np.array_equal(h, _host(t))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_size_atom_without_field_keeps_the_1s_state(torch_cuda, prec):
+    # full-size grid atom (dim 200 000, CF8:11, dt = 0.1, m <= 64) with E0 = 0:
+    # the discrete 1s state is an eigenvector of H0, so exp(-i H0 t) psi_1s =
+    # exp(-i E_1s t) psi_1s exactly (an any-size property, checked at every
+    # element)
+    torch = torch_cuda
+    import paper_1102_5071_gb300 as P
+    a = W.ATOM
+    p = W.grid_atom(Nr=a["Nr"], L=a["L"], dr=a["dr"], E0=0.0, omega=a["omega"], Tp=a["Tp"])
+    prop = P.Propagator(P.DIA(p.H0_offsets, p.H0_values), [P.DIA(p.V_offsets, p.V_values)], [p.drive],
+                        m_max=a["m_max"], max_substeps=4000, precision=prec)
+    psi0, e1s = W.atom_ground_state(p)
+    x = _dev(torch, psi0)
+    nsteps = 3
+    prop.propagate(x, 500.0, a["dt"], nsteps, order=a["order"], tol=1e-12)
+    ref = np.exp(-1j * e1s * a["dt"] * nsteps) * psi0
+    assert np.linalg.norm(_host(x) - ref) <= PARITY
