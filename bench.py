@@ -53,8 +53,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 fl
 # from one ncu capture of the same kernel build on the 2-step case (76
 # iterations): see profiles/.  Must be reset to None whenever the kernel
 # changes and re-measured.
-DRAM_BYTES_PER_ITERATION = {"fx": (1.194820e9 + 1.627267e9) / 76, "c64": (0.190869e9 + 0.648927e9) / 76,
-                            "f64": None}
+DRAM_BYTES_PER_ITERATION = {"fx": (1.194820e9 + 1.627267e9) / 76, "c64": None, "f64": None}
 
 # trace slots of the control-warp kernels (cfet_stats.phase_ns)
 PHASES = ("apply_loops", "apply_control", "orth_loops", "orth_control", "reconstruct_loops", "barrier_wait",
@@ -427,7 +426,8 @@ def _roofline_study_line(prop, stats, ms, dim, bytes_per_app, elem, label, extra
     line = {"study": label, "H_applies": n_app, "substeps": n_sub, "exponentials": stats["n_exp"],
             "substeps_per_exponential": n_sub / max(1, stats["n_exp"]), "max_k": stats["max_k"],
             "H_applies_per_s": n_app / (ms * 1e-3), "ms": ms, "kernel_ms": kernel_ms,
-            "algorithmic_GBps": bytes_ / (kernel_ms * 1e-3) / 1e9}
+            "algorithmic_GBps": bytes_ / (kernel_ms * 1e-3) / 1e9,
+            "phase_Mcycles": {k: v * 1e-6 for k, v in zip(PHASES, stats.get("phase_ns", [0] * 8))}}
     line.update(extra)
     print(json.dumps(line))
 

@@ -281,10 +281,20 @@ static __device__ __forceinline__ double2 apply_spin_at(const double2* q, int x,
 // Taylor series of n(x) terms, n(x) the smallest count in {10, 12, 15,
 // kSmallTaylorTerms} with x^(n+1) / (n+1)! below 1e-17 for the x range;
 // exp(-i ts T) = e^{-i ts sigma} exp(-i ts (T - sigma)).
+// For a = |ts| rho > kChebyshevFrom the Taylor substeps would cost about 18 a
+// matrix-vector products; the Chebyshev expansion (Jacobi-Anger)
+//   e^{-i s a x} = J_0(a) + 2 sum_{n>=1} (-i s)^n J_n(a) T_n(x),  x in [-1, 1],
+// needs about a + 12 a^(1/3) + 24 terms.  It is summed with Clenshaw's
+// backward recurrence on X = (T - sigma) / rho, fused with Miller's backward
+// recurrence J_{n-1} = (2n/a) J_n - J_{n+1} for the Bessel values from a tiny
+// start, normalised at the end by J_0 + 2 sum_k J_2k = 1 (the sum is linear in
+// the coefficients, so one scale fixes both).
 // The FP64 units of this GPU issue one warp instruction per many cycles, so
 // the per-term work is kept to one multiply and two FMAs per row and part:
 // the shifted diagonal and both couplings of a row stay in registers and the
 // term factors hstep / n come from a table of reciprocals.
+constexpr double kChebyshevFrom = 8.0;
+
 __constant__ double kInvN[kSmallTaylorTerms + 1] = {
     0.0, 1.0, 1.0 / 2, 1.0 / 3, 1.0 / 4, 1.0 / 5, 1.0 / 6, 1.0 / 7, 1.0 / 8, 1.0 / 9, 1.0 / 10,
     1.0 / 11, 1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15, 1.0 / 16, 1.0 / 17, 1.0 / 18};
@@ -319,6 +329,74 @@ static __device__ void small_expm_e1(int k, const double* a, const double* b, do
   const double d0 = on0 ? a[r0] - sig : 0.0, d1 = on1 ? a[r1] - sig : 0.0;
   const double bl0 = (on0 && r0 > 0) ? b[r0 - 1] : 0.0, br0 = (on0 && r0 < k - 1) ? b[r0] : 0.0;
   const double bl1 = on1 ? b[r1 - 1] : 0.0, br1 = (on1 && r1 < k - 1) ? b[r1] : 0.0;
+  if (sr > kChebyshevFrom && sr < 4096.0) {
+    const double a_ = sr, inv_a = 1.0 / a_, inv_rho = 1.0 / rho;
+    const bool neg = ts < 0.0;  // (-i s)^n with s = sign(ts)
+    const double x0 = d0 * inv_rho, xl0 = bl0 * inv_rho, xr0 = br0 * inv_rho;
+    const double x1 = d1 * inv_rho, xl1 = bl1 * inv_rho, xr1 = br1 * inv_rho;
+    const int nstart = (int)ceil(a_ + 12.0 * cbrt(a_) + 24.0);
+    double jn1 = 0.0, jn = 1e-200, norm = 0.0;  // J_{n+1}, J_n (unscaled)
+    // Clenshaw state b_{n+1}, b_{n+2} (real and imaginary parts) of each row
+    double pr0 = 0, qr0 = 0, pi0 = 0, qi0 = 0, pr1 = 0, qr1 = 0, pi1 = 0, qi1 = 0;
+    for (int n = nstart; n >= 1; --n) {
+      // coefficient 2 (-i s)^n J_n: the phase (-i)^m, m = n or -n mod 4
+      const int m = neg ? ((4 - (n & 3)) & 3) : (n & 3);
+      const double c = 2.0 * jn;
+      const double cre = m == 0 ? c : (m == 2 ? -c : 0.0);
+      const double cim = m == 1 ? -c : (m == 3 ? c : 0.0);
+      if (on0) { tr[r0] = pr0; ti[r0] = pi0; }
+      if (on1) { tr[r1] = pr1; ti[r1] = pi1; }
+      __syncwarp();
+      double nr0 = 0, ni0 = 0, nr1 = 0, ni1 = 0;
+      if (on0) {
+        const double lr = r0 > 0 ? tr[r0 - 1] : 0.0, li = r0 > 0 ? ti[r0 - 1] : 0.0;
+        const double rr = r0 < k - 1 ? tr[r0 + 1] : 0.0, ri = r0 < k - 1 ? ti[r0 + 1] : 0.0;
+        nr0 = 2.0 * fma(xr0, rr, fma(xl0, lr, x0 * pr0)) - qr0 + (r0 == 0 ? cre : 0.0);
+        ni0 = 2.0 * fma(xr0, ri, fma(xl0, li, x0 * pi0)) - qi0 + (r0 == 0 ? cim : 0.0);
+      }
+      if (on1) {
+        const double lr = tr[r1 - 1], li = ti[r1 - 1];
+        const double rr = r1 < k - 1 ? tr[r1 + 1] : 0.0, ri = r1 < k - 1 ? ti[r1 + 1] : 0.0;
+        nr1 = 2.0 * fma(xr1, rr, fma(xl1, lr, x1 * pr1)) - qr1;
+        ni1 = 2.0 * fma(xr1, ri, fma(xl1, li, x1 * pi1)) - qi1;
+      }
+      __syncwarp();
+      qr0 = pr0; qi0 = pi0; pr0 = nr0; pi0 = ni0;
+      qr1 = pr1; qi1 = pi1; pr1 = nr1; pi1 = ni1;
+      // Miller step and the normalisation sum J_0 + 2 sum_k J_2k
+      if ((n & 1) == 0) norm += 2.0 * jn;
+      const double jm = 2.0 * n * inv_a * jn - jn1;
+      jn1 = jn;
+      jn = jm;
+    }
+    norm += jn;  // J_0
+    // S = J_0 e_1 + X b_1 - b_2
+    if (on0) { tr[r0] = pr0; ti[r0] = pi0; }
+    if (on1) { tr[r1] = pr1; ti[r1] = pi1; }
+    __syncwarp();
+    double sr0 = 0, si0 = 0, sr1 = 0, si1 = 0;
+    if (on0) {
+      const double lr = r0 > 0 ? tr[r0 - 1] : 0.0, li = r0 > 0 ? ti[r0 - 1] : 0.0;
+      const double rr = r0 < k - 1 ? tr[r0 + 1] : 0.0, ri = r0 < k - 1 ? ti[r0 + 1] : 0.0;
+      sr0 = fma(xr0, rr, fma(xl0, lr, x0 * pr0)) - qr0 + (r0 == 0 ? jn : 0.0);
+      si0 = fma(xr0, ri, fma(xl0, li, x0 * pi0)) - qi0;
+    }
+    if (on1) {
+      const double lr = tr[r1 - 1], li = ti[r1 - 1];
+      const double rr = r1 < k - 1 ? tr[r1 + 1] : 0.0, ri = r1 < k - 1 ? ti[r1 + 1] : 0.0;
+      sr1 = fma(xr1, rr, fma(xl1, lr, x1 * pr1)) - qr1;
+      si1 = fma(xr1, ri, fma(xl1, li, x1 * pi1)) - qi1;
+    }
+    __syncwarp();
+    const double inv_norm = 1.0 / norm;
+    double sn, cs;
+    sincos(ts * sig, &sn, &cs);
+    // y = e^{-i ts sig} S / norm, e^{-i ts sig} = cs - i sn
+    if (on0) { yr[r0] = (sr0 * cs + si0 * sn) * inv_norm; yi[r0] = (si0 * cs - sr0 * sn) * inv_norm; }
+    if (on1) { yr[r1] = (sr1 * cs + si1 * sn) * inv_norm; yi[r1] = (si1 * cs - sr1 * sn) * inv_norm; }
+    __syncwarp();
+    return;
+  }
   double ar0 = (r0 == 0) ? 1.0 : 0.0, ai0 = 0.0, ar1 = 0.0, ai1 = 0.0;  // current y
   for (int sidx = 0; sidx < S; ++sidx) {
     double t_r0 = ar0, t_i0 = ai0, t_r1 = ar1, t_i1 = ai1;

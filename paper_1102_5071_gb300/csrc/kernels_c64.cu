@@ -91,6 +91,7 @@ struct SmemC {
   CConst ca;
   float am;                      // phase B: -alpha_k s_k
   double wnorm2;                 // ||w||^2 of the current iteration (from the phase-A sums)
+  double qnorm2[kMaxKrylov + 3]; // ||q_i||^2 of the stored vectors (reduced after they are written)
   int abort_flag, stop_prev, accept_now, pend, y_ready, acc_h;
   double err_now, err_prev;
   double beta0;
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
   const unsigned tag0 = (unsigned)ld_volatile_i32((const int*)&p.st->tag_base);
   unsigned gen = 0;
   unsigned long long* partA = reinterpret_cast<unsigned long long*>(p.partials);  // 3 sums: 6 words
-  unsigned long long* partB = partA + 6 * G;                                        // barrier: 1 word
+  unsigned long long* partB = partA + 6 * G;                                        // 1 sum: 2 words
   unsigned long long* partR = partA + 12 * G;                                       // 1 sum: 2 words
   DevStatus* st = p.st;
   const bool glead = (blockIdx.x == 0) && lead;
@@ -388,6 +389,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
       } else if (lane == 0) {
         S.abort_flag = ld_volatile_i32(&st->status) != 0;
         S.beta0 = sqrt(sum[0]);
+        S.qnorm2[1] = sum[0];
       }
     }
     __syncthreads();
@@ -446,9 +448,9 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
             const float2* q = Q(it);
             const float2* qm = it > 1 ? Q(it - 1) : q;
             float2* u = Q(it + 1);
-            // <q,u> and ||u||^2: alpha and ||u - alpha s q||^2 follow from these
-            // two sums (s q is a unit vector: s = 1 / ||q||), so the
-            // orthogonalisation pass needs no reduction of its own
+            // <q,u> and ||u||^2: with ||q||^2 (reduced when q was written) they
+            // give alpha and ||u - alpha s q||^2, so the decisions need not wait
+            // for the orthogonalisation pass
             float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
             const long long tw0 = sm_clock();
             int x = wx0;
@@ -507,12 +509,15 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
               if (lane == 0) S.abort_flag = 1;
             } else if (lane == 0 && !S.stop_prev) {
               // q_it holds the Lanczos vector v_it times 1/scale[it]:
-              // alpha = <v, u>,  ||w||^2 = ||u - alpha v||^2 = ||u||^2 - alpha^2
+              // alpha = <v, u>,  ||w||^2 = ||u - alpha v||^2
+              //       = ||u||^2 - alpha^2 (2 - s^2 ||q||^2)
+              // (the stored q is a unit vector only to FP32 rounding, which the
+              // last factor keeps out of the cancellation)
               const double s_it = S.scale[it];
               const double alpha = sum[0] * s_it;
               S.alpha[it] = alpha;
               S.am = (float)(-alpha * s_it);
-              S.wnorm2 = sum[1] - alpha * alpha;
+              S.wnorm2 = sum[1] - alpha * alpha * (2.0 - s_it * s_it * S.qnorm2[it]);
             }
             if (lane == 0) tacc[1] += sm_clock() - tc0 - (tacc[5] - sp0);
           }
@@ -531,12 +536,17 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
             const float am = S.am;
             const float2* q = Q(it);
             float2* u = Q(it + 1);
+            float s0 = 0.f, c0 = 0.f;  // ||w||^2 of the stored w, for the next iteration
             const long long tw0 = sm_clock();
             for (int x = wx0; x < wxe; x += wstep) {
               const float2 v = q[x];
               const float2 uu = u[x];
-              u[x] = make_float2(fmaf(am, v.x, uu.x), fmaf(am, v.y, uu.y));
+              const float2 w = make_float2(fmaf(am, v.x, uu.x), fmaf(am, v.y, uu.y));
+              u[x] = w;
+              ff_add_prod(s0, c0, w.x, w.x);
+              ff_add_prod(s0, c0, w.y, w.y);
             }
+            c_worker_partial(S, s0, c0, 0);
             if (tid == 0) {
               twe = sm_clock();
               tacc[2] += twe - tw0;
@@ -585,11 +595,15 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
           __syncthreads();
           const bool last_it = S.accept_now || it >= klimit;
           if (!last_it) {
-            // every CTA's w must be visible before the next apply reads it
+            // every CTA's w must be visible before the next apply reads it; the
+            // exchange also carries ||w||^2 of the stored w
             if (ctl) {
-              double none[1];
-              if (!c_ctl_reduce<0>(S, NW, partB, tag0 + (++gen), true, &st->status, p.timeout_ns, none, tacc[5]))
+              double wsum[1];
+              if (!c_ctl_reduce<1>(S, NW, partB, tag0 + (++gen), true, &st->status, p.timeout_ns, wsum, tacc[5])) {
                 if (lane == 0) S.abort_flag = 1;
+              } else if (lane == 0) {
+                S.qnorm2[it + 1] = wsum[0];
+              }
             }
             __syncthreads();
           }
@@ -676,6 +690,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
             if (lane == 0) S.abort_flag = 1;
           } else if (lane == 0) {
             S.beta0 = sqrt(sum[0]);
+            S.qnorm2[1] = sum[0];
           }
         }
         __syncthreads();

@@ -200,3 +200,20 @@ def test_c64_host_entry_matches_device_entry(torch_cuda):
     h = psi0.copy()
     prop.propagate_host(h, 0.0, 0.02, 5, order=6, tol=1e-8)
     assert np.array_equal(h, t.cpu().numpy())
+
+
+def test_c64_full_size_atom_without_field_keeps_the_1s_state(torch_cuda):
+    # stiff spectrum (H0 up to 5e5): the full-size grid atom with E0 = 0 keeps
+    # its discrete 1s eigenstate up to the phase exp(-i E_1s t); the complex64
+    # result must stay within single-precision rounding of it (a wrong beta
+    # from cancellation would show up as a much larger error)
+    import paper_1102_5071_gb300 as P
+    a = W.ATOM
+    p = W.grid_atom(Nr=a["Nr"], L=a["L"], dr=a["dr"], E0=0.0, omega=a["omega"], Tp=a["Tp"])
+    prop = P.Propagator(P.DIA(p.H0_offsets, p.H0_values), [P.DIA(p.V_offsets, p.V_values)], [p.drive],
+                        m_max=a["m_max"], max_substeps=4000, precision="c64")
+    psi0, e1s = W.atom_ground_state(p)
+    x = _dev(torch_cuda, psi0)
+    st = prop.propagate(x, 500.0, a["dt"], 2, order=a["order"], tol=1e-9)
+    ref = np.exp(-1j * e1s * a["dt"] * 2) * psi0
+    assert np.linalg.norm(x.cpu().numpy() - ref) <= 1e-4, st
