@@ -240,7 +240,8 @@ def run_gpu(args):
     pr, psi0 = problem()
     dim = 1 << N_SITES
     prop = P.Propagator(P.XXZChain(N_SITES, pr.J, pr.Delta, pr.h), [P.XField(N_SITES, pr.xfield)], [pr.drive],
-                        m_max=M_MAX, max_substeps=64, precision=args.precision, block_size=args.block_size)
+                        m_max=M_MAX, max_substeps=64, precision=args.precision, block_size=args.block_size,
+                        grid_size=args.grid_size)
     psi = torch.from_numpy(psi0).cuda()
     t0 = 0.0
     # warm-up steps (untimed)
@@ -445,7 +446,7 @@ def run_study_atom(args):
     p = W.grid_atom(Nr=a["Nr"], L=a["L"], dr=a["dr"], E0=a["E0"], omega=a["omega"], Tp=a["Tp"])
     psi0, e0 = W.atom_ground_state(p)
     prop = P.Propagator(P.DIA(p.H0_offsets, p.H0_values), [P.DIA(p.V_offsets, p.V_values)], [p.drive],
-                        m_max=a["m_max"], max_substeps=4000, precision=args.precision)
+                        m_max=a["m_max"], max_substeps=4000, precision=args.precision, grid_size=args.grid_size)
     psi = torch.from_numpy(psi0).cuda()
     t0 = 500.0
     # warm-up: one apply (context, tables and graph set-up); a full atom step
@@ -644,6 +645,8 @@ def main():
                          "the fidelity gradient")
     ap.add_argument("--baseline-steps", type=int, default=10,
                     help="batch study: steps of the single-instance baseline per instance")
+    ap.add_argument("--grid-size", type=int, default=0,
+                    help="CTAs of the persistent kernel (0 = co-resident maximum)")
     ap.add_argument("--block-size", type=int, default=0,
                     help="threads per CTA of the FP64 kernel; the fixed-point kernel uses 2x this many workers + 1 control warp")
     args = ap.parse_args()
