@@ -20,6 +20,10 @@ krylov     Lanczos / Krylov evaluation of exp(-i tau H) psi (Sec. 7.1) with
            the a-posteriori error estimate and time substepping.
 cfet       the CFET time step (Eq. Ucf with Eq. OmGLeg) and time stepping
            (Sec. 6.1).
+chebyshev  Chebyshev evaluation of exp(-i tau H) psi (the alternative technique
+           of Sec. 8.1/8.2): Gershgorin intervals combined by Weyl's
+           inequality, Jacobi-Anger coefficients, truncation by the Bessel
+           tail bound, three-term recurrence; CFET stepping with it.
 adjoint    fidelity loss 1 - |<phi|psi(T)>|^2 of a CFET propagation with a
            piecewise-constant drive amplitude and its exact gradient (dense
            stage exponentials and Frechet derivatives; small systems).  The
@@ -31,6 +35,9 @@ the driven-chain and grid-atom workloads, which no closed form covers; those
 are pinned only through properties (factorisation at J=0, time-independent
 exactness, order slopes, unitarity).  The gradient of ``adjoint`` is pinned by
 central finite differences of its loss and by its vanishing at an optimum.
+``chebyshev`` is pinned by dense expm, the closed forms of the Sec. 8.2
+harmonic-oscillator example and of the Jacobi-Anger series, and dense
+Gershgorin intervals.
 """
 
-__all__ = ["schemes", "operators", "krylov", "cfet", "adjoint"]
+__all__ = ["schemes", "operators", "krylov", "cfet", "chebyshev", "adjoint"]
