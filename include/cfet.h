@@ -129,6 +129,16 @@ enum {
 cfet_status cfet_scheme_info(int32_t scheme, int32_t* order, int32_t* s, int32_t* M,
                              double* f, double* x, double* w, double* g, int32_t capacity);
 
+/* Chebyshev expansion coefficients of exp(-i z x) on [-1, 1] (Jacobi-Anger;
+ * the CFET_EXPM_CHEBYSHEV path): r[k] = (2 - delta_k0) J_k(z), k = 0..K, with
+ * K the smallest order whose tail bound 2 sum_{k>K} |J_k(z)| is <= tol
+ * (2^-52 for tol <= 0).  The Bessel values come from Miller's backward
+ * recurrence normalised by J_0 + 2 sum J_{2k} = 1.  r may be NULL (query K
+ * and the tail only); otherwise cap >= K + 1 is required.  Host only; no
+ * device needed.  Errors: CFET_EINVAL (non-finite z or tol, |z| > 1e8, cap
+ * too small).                                                               */
+cfet_status cfet_chebyshev_coefficients(double z, double tol, int32_t cap, double* r, int32_t* K, double* tail);
+
 /* ------------------------------------------------------------------------ */
 /* Context                                                                   */
 /* ------------------------------------------------------------------------ */
@@ -145,6 +155,7 @@ typedef struct cfet_options {
   int32_t steps_per_launch;  /* CFET steps per persistent launch (0 = 256)    */
   double barrier_timeout_s;  /* device barrier wait limit (default 2.0 s)     */
   int32_t precision;         /* CFET_PREC_* (default CFET_PREC_FX)            */
+  int32_t expm;              /* CFET_EXPM_* (default CFET_EXPM_KRYLOV)        */
 } cfet_options;
 
 /* Number format of the Krylov vectors on the device.  All keep alpha, beta,
@@ -164,6 +175,27 @@ typedef struct cfet_options {
  *                 so Krylov tolerances below ~1e-7 no longer bound the
  *                 error; meant for targets of about 1e-6.                   */
 enum { CFET_PREC_DEFAULT = 0, CFET_PREC_F64 = 1, CFET_PREC_FX = 2, CFET_PREC_C64 = 3 };
+
+/* How cfet_propagate evaluates each stage exponential exp(-i dt H_j) psi.
+ *  KRYLOV    : the Lanczos/Krylov loop (Sec. 8.1) with the a-posteriori error
+ *              estimate, adaptive dimension and substeps (every precision).
+ *  CHEBYSHEV : the Chebyshev technique named in Sec. 8.1 (Tal-Ezer-Kosloff):
+ *              exp(-i dt H_j) psi = exp(-i dt b) sum_{k<=K} (2 - delta_k0)
+ *              (-i)^k J_k(dt a) T_k((H_j - b) / a) psi, where [b - a, b + a]
+ *              bounds the spectrum of H_j (Gershgorin intervals of H0 and of
+ *              each V_k combined by Weyl's inequality) and K is the smallest
+ *              order whose Bessel tail bound 2 sum_{k>K} |J_k(dt a)| is at most
+ *              krylov_tol (2^-52 for krylov_tol <= 0).  Fixed-point precision
+ *              only (CFET_PREC_FX, the default); no decision logs (forced /
+ *              record must be NULL); K <= m_max * max_substeps per
+ *              exponential (else CFET_EKRYLOV before any device work);
+ *              |b| <= 1.5 a required (else CFET_EINVAL).  cfet_stats: n_substeps
+ *              = n_exp, n_applies = sum of K, max_k = largest K, max_err_est =
+ *              largest tail bound.                                          */
+enum {
+  CFET_EXPM_KRYLOV = 0,
+  CFET_EXPM_CHEBYSHEV = 1
+};
 
 typedef struct cfet_stats {
   int64_t n_exp;             /* stage exponentials evaluated                  */

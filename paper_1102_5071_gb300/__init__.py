@@ -92,6 +92,23 @@ def scheme_info(name_or_id):
     return order.value, s_, M_, f[: s_ * M_].reshape(s_, M_), x[:M_].copy(), w[:M_].copy(), g[: s_ * M_].reshape(s_, M_)
 
 
+def chebyshev_coefficients(z, tol):
+    """(r[0..K], K, tail) of the Chebyshev expansion of exp(-i z x) on [-1, 1]
+    used by the CFET_EXPM_CHEBYSHEV path: r_k = (2 - delta_k0) J_k(z), K the
+    smallest order whose Bessel tail bound 2 sum_{k>K} |J_k(z)| is <= tol."""
+    lib = _capi.load()
+    K, tail = C.c_int32(), C.c_double()
+    st = lib.cfet_chebyshev_coefficients(float(z), float(tol), 0, None, C.byref(K), C.byref(tail))
+    if st != 0:
+        raise CfetError(st, "invalid Chebyshev argument")
+    r = np.zeros(K.value + 1)
+    st = lib.cfet_chebyshev_coefficients(float(z), float(tol), len(r), r.ctypes.data_as(_capi.c_double_p),
+                                         C.byref(K), C.byref(tail))
+    if st != 0:
+        raise CfetError(st, "invalid Chebyshev argument")
+    return r, K.value, tail.value
+
+
 def _stream_handle(stream):
     import torch
     if stream is None:
@@ -111,7 +128,7 @@ class Propagator:
     """CFET propagator for H(t) = H0 + sum_k f_k(t) V_k on the current CUDA device."""
 
     def __init__(self, H0, V=(), drives=(), *, m_max=16, m_min=2, max_substeps=64, block_size=0,
-                 grid_size=0, steps_per_launch=256, barrier_timeout_s=2.0, precision="default"):
+                 grid_size=0, steps_per_launch=256, barrier_timeout_s=2.0, precision="default", expm="krylov"):
         lib = _capi.load()
         V = list(V)
         drives = list(drives)
@@ -128,6 +145,7 @@ class Propagator:
         opt.block_size, opt.grid_size, opt.steps_per_launch = block_size, grid_size, steps_per_launch
         opt.barrier_timeout_s = barrier_timeout_s
         opt.precision = _capi.PRECISIONS[precision]
+        opt.expm = _capi.EXPM[expm]
         ctx = C.c_void_p()
         st = lib.cfet_create(C.byref(ctx), C.byref(h0), len(V), varr, fns, None, C.byref(opt))
         if st != 0:

@@ -29,11 +29,13 @@ class cfet_op(C.Structure):
 class cfet_options(C.Structure):
     _fields_ = [("m_max", C.c_int32), ("m_min", C.c_int32), ("max_substeps", C.c_int32),
                 ("block_size", C.c_int32), ("grid_size", C.c_int32), ("steps_per_launch", C.c_int32),
-                ("barrier_timeout_s", C.c_double), ("precision", C.c_int32)]
+                ("barrier_timeout_s", C.c_double), ("precision", C.c_int32), ("expm", C.c_int32)]
 
 
 CFET_PREC_DEFAULT, CFET_PREC_F64, CFET_PREC_FX, CFET_PREC_C64 = 0, 1, 2, 3
 PRECISIONS = {"default": CFET_PREC_DEFAULT, "f64": CFET_PREC_F64, "fx": CFET_PREC_FX, "c64": CFET_PREC_C64}
+CFET_EXPM_KRYLOV, CFET_EXPM_CHEBYSHEV = 0, 1
+EXPM = {"krylov": CFET_EXPM_KRYLOV, "chebyshev": CFET_EXPM_CHEBYSHEV}
 
 
 class cfet_stats(C.Structure):
@@ -92,6 +94,8 @@ def load() -> C.CDLL:
         "cfet_options_default": (None, [C.POINTER(cfet_options)]),
         "cfet_scheme_info": (C.c_int, [C.c_int32, c_int32_p, c_int32_p, c_int32_p, c_double_p, c_double_p,
                                        c_double_p, c_double_p, C.c_int32]),
+        "cfet_chebyshev_coefficients": (C.c_int, [C.c_double, C.c_double, C.c_int32, c_double_p, c_int32_p,
+                                                  c_double_p]),
         "cfet_create": (C.c_int, [C.POINTER(vp), C.POINTER(cfet_op), C.c_int32, C.POINTER(cfet_op),
                                   C.POINTER(DRIVE_FN), C.POINTER(vp), C.POINTER(cfet_options)]),
         "cfet_destroy": (None, [vp]),
@@ -137,7 +141,7 @@ def load() -> C.CDLL:
     return lib
 
 
-EXPORTED = ["cfet_options_default", "cfet_scheme_info", "cfet_create", "cfet_destroy", "cfet_last_error",
+EXPORTED = ["cfet_options_default", "cfet_scheme_info", "cfet_chebyshev_coefficients", "cfet_create", "cfet_destroy", "cfet_last_error",
             "cfet_apply", "cfet_expv", "cfet_propagate", "cfet_propagate_ex", "cfet_propagate_host", "cfet_sync",
             "cfet_kernel_time_ms", "cfet_expv_chain_static",
             "cfet_batch_create", "cfet_batch_destroy", "cfet_batch_last_error", "cfet_batch_size",

@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -39,6 +40,8 @@ struct cfet_ctx {
   // operators
   OpSpin spin{};
   OpDia dia{};
+  // Gershgorin intervals of H0 and of every V_k (Chebyshev stage exponentials)
+  double op_lo[1 + kMaxDrives] = {}, op_hi[1 + kMaxDrives] = {};
   double* d_dz_lo = nullptr;
   double* d_dz_hi = nullptr;
   double* d_xf = nullptr;
@@ -212,7 +215,10 @@ cfet_status launch_chunk(cfet_ctx* ctx, const PropParams& base, long long e0, lo
   p.nexp = ne;
   p.exp_base = e0;
   int e;
-  if (ctx->precision == CFET_PREC_FX)
+  if (ctx->opt.expm == CFET_EXPM_CHEBYSHEV)
+    e = ctx->family == kFamilySpin ? launch_cheb_spin_fx(p, ctx->spin_fx, ctx->grid, ctx->block - 32, s)
+                                   : launch_cheb_dia_fx(p, ctx->dia_fx, ctx->grid, ctx->block - 32, s);
+  else if (ctx->precision == CFET_PREC_FX)
     e = ctx->family == kFamilySpin ? launch_propagate_spin_fx(p, ctx->spin_fx, ctx->grid, ctx->block, s)
                                    : launch_propagate_dia_fx(p, ctx->dia_fx, ctx->grid, ctx->block, s);
   else if (ctx->precision == CFET_PREC_C64)
@@ -264,6 +270,72 @@ PropParams base_params(cfet_ctx* ctx, double2* psi, double tau, double tol) {
   p.qbasis = ctx->d_qbasis;
   p.qbasis32 = ctx->d_qbasis32;
   return p;
+}
+
+// Chebyshev records (kChebRec doubles each) and concatenated coefficients of
+// nexp stage exponentials exp(-i tau H_e) whose scalar rows (1 + nV doubles
+// each) are `rows`: spectral interval of H_e by Weyl's inequality from the
+// operators' Gershgorin intervals, a = half width, b = centre, K and r_k from
+// the Bessel tail bound (chebyshev.cpp).
+constexpr size_t kMaxChebCoef = size_t(1) << 27;
+cfet_status build_cheb(cfet_ctx* ctx, const double* rows, long long nexp, double tau, double tol,
+                       std::vector<double>& rec, std::vector<double>& coef) {
+  const int ncoef = 1 + ctx->nV;
+  const long long kcap = (long long)ctx->opt.m_max * ctx->opt.max_substeps;
+  rec.assign((size_t)nexp * kChebRec, 0.0);
+  coef.clear();
+  std::vector<double> r;
+  for (long long e = 0; e < nexp; ++e) {
+    double lo = 0.0, hi = 0.0;
+    stage_interval(ncoef, ctx->op_lo, ctx->op_hi, rows + e * ncoef, &lo, &hi);
+    const double a = 0.5 * (hi - lo), b = 0.5 * (hi + lo);
+    double* R = rec.data() + (size_t)e * kChebRec;
+    double tail = 0.0;
+    int K = 0;
+    if (a > 0.0) {
+      if (std::fabs(b) > 1.5 * a)
+        return fail(ctx, CFET_EINVAL, "Chebyshev: spectral centre |b| > 1.5 a (shift H0 by a multiple of the identity)");
+      if (!(std::fabs(tau * a) <= 1e8)) return fail(ctx, CFET_EKRYLOV, "Chebyshev: dt * a too large");
+      K = cheb_series(tau * a, tol, &r, &tail);
+      if (K > kcap) return fail(ctx, CFET_EKRYLOV, "Chebyshev: a stage exponential needs more than m_max * max_substeps terms");
+      R[0] = 1.0 / a;
+      R[1] = b / a;
+    } else {
+      r.assign(1, 1.0);
+    }
+    double sum = 0.0;
+    for (double v : r) sum += std::fabs(v);
+    R[2] = (double)K;
+    R[3] = (double)coef.size();
+    R[4] = sum;
+    R[5] = std::cos(tau * b);
+    R[6] = -std::sin(tau * b);
+    R[7] = tail;
+    coef.insert(coef.end(), r.begin(), r.end());
+    if (coef.size() > kMaxChebCoef)
+      return fail(ctx, CFET_EINVAL, "Chebyshev: more than 2^27 coefficients in one call; propagate in shorter calls");
+  }
+  return CFET_OK;
+}
+
+// Append the Chebyshev table behind the nexp scalar rows in ctx->h_scal;
+// returns the total table length (doubles) in *n.
+cfet_status stage_cheb_table(cfet_ctx* ctx, long long nexp, double tau, double tol, size_t* n) {
+  const size_t nrows = (size_t)nexp * (1 + ctx->nV);
+  std::vector<double> rows(ctx->h_scal, ctx->h_scal + nrows), rec, coef;
+  cfet_status s = build_cheb(ctx, rows.data(), nexp, tau, tol, rec, coef);
+  if (s != CFET_OK) return s;
+  *n = nrows + rec.size() + coef.size();
+  if ((s = ensure_scal(ctx, *n)) != CFET_OK) return s;
+  std::memcpy(ctx->h_scal, rows.data(), nrows * sizeof(double));
+  std::memcpy(ctx->h_scal + nrows, rec.data(), rec.size() * sizeof(double));
+  std::memcpy(ctx->h_scal + nrows + rec.size(), coef.data(), coef.size() * sizeof(double));
+  return CFET_OK;
+}
+
+void set_cheb_params(cfet_ctx* ctx, PropParams& p, long long nexp) {
+  p.cheb = ctx->d_scal + (size_t)nexp * (1 + ctx->nV);
+  p.cheb_coef = p.cheb + (size_t)nexp * kChebRec;
 }
 
 cfet_status finish(cfet_ctx* ctx, cudaStream_t s, cfet_stats* stats) {
@@ -344,6 +416,7 @@ void cfet_options_default(cfet_options* opt) {
   opt->steps_per_launch = 256;
   opt->barrier_timeout_s = 2.0;
   opt->precision = CFET_PREC_FX;
+  opt->expm = CFET_EXPM_KRYLOV;
 }
 
 cfet_status cfet_scheme_info(int32_t scheme, int32_t* order, int32_t* s, int32_t* M, double* f, double* x,
@@ -393,6 +466,10 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
   if (o.precision == CFET_PREC_DEFAULT) o.precision = CFET_PREC_FX;
   if (o.precision != CFET_PREC_F64 && o.precision != CFET_PREC_FX && o.precision != CFET_PREC_C64)
     return fail(nullptr, CFET_EINVAL, "precision must be CFET_PREC_F64, CFET_PREC_FX or CFET_PREC_C64");
+  if (o.expm != CFET_EXPM_KRYLOV && o.expm != CFET_EXPM_CHEBYSHEV)
+    return fail(nullptr, CFET_EINVAL, "expm must be CFET_EXPM_KRYLOV or CFET_EXPM_CHEBYSHEV");
+  if (o.expm == CFET_EXPM_CHEBYSHEV && o.precision != CFET_PREC_FX)
+    return fail(nullptr, CFET_EINVAL, "CFET_EXPM_CHEBYSHEV requires CFET_PREC_FX");
   if (o.block_size == 0) o.block_size = (o.precision == CFET_PREC_F64) ? 256 : 384;
   {
     // FP64 kernel: block_size threads (<= 256); fixed-point and mixed-precision
@@ -547,6 +624,8 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
     ctx->spin_c.dz_lo = ctx->d_dz32;
     ctx->spin_c.dz_hi = ctx->d_dz32 + nlo;
     ctx->spin_c.xf = ctx->d_xf;
+    spin_h0_interval(N, H0->J, H0->Delta, H0->site_coeff, &ctx->op_lo[0], &ctx->op_hi[0]);
+    for (int k = 0; k < nV; ++k) xfield_interval(N, V[k].site_coeff, &ctx->op_lo[1 + k], &ctx->op_hi[1 + k]);
   } else {
     std::vector<long long> off;
     std::vector<int> opidx;
@@ -628,15 +707,27 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
     CKC(cudaMemcpy(ctx->d_val32, val32.data(), val32.size() * sizeof(float), cudaMemcpyHostToDevice),
         "upload val32");
     dc.val = ctx->d_val32;
+    for (int k = -1; k < nV; ++k) {
+      const cfet_op& o2 = k < 0 ? *H0 : V[k];
+      dia_interval(o2.offsets, o2.values, o2.ndiag, dim, &ctx->op_lo[k + 1], &ctx->op_hi[k + 1]);
+    }
   }
   // persistent grid: co-resident maximum, no more CTAs than needed to give
   // every thread at least one element
-  const int maxg = ctx->precision == CFET_PREC_FX    ? max_coresident_blocks_fx(family, ctx->block)
+  int maxg = ctx->precision == CFET_PREC_FX    ? max_coresident_blocks_fx(family, ctx->block)
                    : ctx->precision == CFET_PREC_C64 ? max_coresident_blocks_c64(family, ctx->block)
                                                      : max_coresident_blocks(family, ctx->block);
   if (maxg < 1) {
     free_ctx(ctx);
     return fail(nullptr, CFET_ECUDA, "occupancy query failed for the persistent kernel");
+  }
+  if (o.expm == CFET_EXPM_CHEBYSHEV) {  // the Chebyshev kernel: the same workers, no control warp
+    const int mc = max_coresident_blocks_cheb(family, ctx->block - 32);
+    if (mc < 1) {
+      free_ctx(ctx);
+      return fail(nullptr, CFET_ECUDA, "occupancy query failed for the Chebyshev kernel");
+    }
+    if (mc < maxg) maxg = mc;
   }
   // element threads per CTA (the fixed-point kernel adds one control warp)
   const int workers = ctl_warp ? ctx->block - 32 : ctx->block;
@@ -646,8 +737,9 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
   if (ctl_warp && ctx->grid > kMaxCtlGrid) ctx->grid = kMaxCtlGrid;  // record exchange limit
   if (ctx->grid < 1) ctx->grid = 1;
 
-  if (ctx->precision == CFET_PREC_FX)
-    CKC(cudaMalloc(&ctx->d_qbasis, (size_t)(o.m_max + 1) * dim * sizeof(longlong2)), "cudaMalloc(Krylov basis)");
+  if (ctx->precision == CFET_PREC_FX)  // (the Chebyshev kernel uses three of these vectors)
+    CKC(cudaMalloc(&ctx->d_qbasis, (size_t)std::max(o.m_max + 1, 3) * dim * sizeof(longlong2)),
+        "cudaMalloc(Krylov basis)");
   else if (ctx->precision == CFET_PREC_C64)
     CKC(cudaMalloc(&ctx->d_qbasis32, (size_t)(o.m_max + 1) * dim * sizeof(float2)), "cudaMalloc(Krylov basis)");
   else
@@ -718,9 +810,13 @@ cfet_status cfet_expv(cfet_ctx* ctx, const double* c, double tau, void* psi, dou
   if ((s = ensure_scal(ctx, 1 + ctx->nV)) != CFET_OK) return s;
   if (ctx->ev_pending) { cudaEventSynchronize(ctx->ev_done); ctx->ev_pending = false; }
   for (int i = 0; i <= ctx->nV; ++i) ctx->h_scal[i] = c[i];
+  size_t table_n = 1 + ctx->nV;
+  const bool cheb = ctx->opt.expm == CFET_EXPM_CHEBYSHEV;
+  if (cheb && (s = stage_cheb_table(ctx, 1, tau, tol, &table_n)) != CFET_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
   PropParams p = base_params(ctx, (double2*)psi, tau, tol);
-  if ((s = issue_sequence(ctx, p, 1, 1, (1 + ctx->nV) * sizeof(double), st, false)) != CFET_OK) return s;
+  if (cheb) set_cheb_params(ctx, p, 1);
+  if ((s = issue_sequence(ctx, p, 1, 1, table_n * sizeof(double), st, false)) != CFET_OK) return s;
   CK(cudaEventRecord(ctx->ev_done, st), "event record");
   ctx->ev_pending = true;
   if (stats) return finish(ctx, st, stats);
@@ -751,6 +847,9 @@ cfet_status cfet_propagate_ex(cfet_ctx* ctx, void* psi, double t0, double dt, in
   }
   const long long nexp = nsteps * (long long)sd.s;
   const int ncoef = 1 + ctx->nV;
+  const bool cheb = ctx->opt.expm == CFET_EXPM_CHEBYSHEV;
+  if (cheb && (forced || record))
+    return fail(ctx, CFET_EINVAL, "Chebyshev stage exponentials take no Krylov decision logs");
   if (forced) {
     if (forced->n_exp != nexp || !forced->n_sub || !forced->k || !forced->h || forced->len < nexp)
       return fail(ctx, CFET_EINVAL, "forced decisions do not cover nsteps * s exponentials");
@@ -800,6 +899,8 @@ cfet_status cfet_propagate_ex(cfet_ctx* ctx, void* psi, double t0, double dt, in
       }
     }
   }
+  size_t table_n = (size_t)nexp * ncoef;
+  if (cheb && (s = stage_cheb_table(ctx, nexp, dt, krylov_tol, &table_n)) != CFET_OK) return s;
   // ---- forced decisions blob (host staging)
   std::vector<int> fblob;
   if (forced) {
@@ -812,6 +913,7 @@ cfet_status cfet_propagate_ex(cfet_ctx* ctx, void* psi, double t0, double dt, in
   }
   if (forced) CK(cudaMemcpy(ctx->d_dec, fblob.data(), nf * sizeof(int), cudaMemcpyHostToDevice), "decision upload");
   PropParams p = base_params(ctx, (double2*)psi, dt, krylov_tol);
+  if (cheb) set_cheb_params(ctx, p, nexp);
   if (forced) {
     p.f_nsub = ctx->d_dec;
     p.f_k = ctx->d_dec + nexp;
@@ -837,7 +939,7 @@ cfet_status cfet_propagate_ex(cfet_ctx* ctx, void* psi, double t0, double dt, in
   key.chunk = chunk;
   key.flen = (long long)flen;
   key.rcap = (long long)rcap;
-  key.table_bytes = (size_t)nexp * ncoef * sizeof(double);
+  key.table_bytes = table_n * sizeof(double);
   key.nf = nf;
   key.tau = dt;
   key.tol = krylov_tol;
@@ -847,7 +949,7 @@ cfet_status cfet_propagate_ex(cfet_ctx* ctx, void* psi, double t0, double dt, in
     ctx->gkey = cfet_ctx::GraphKey();
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-    s = issue_sequence(ctx, p, nexp, chunk, (size_t)nexp * ncoef * sizeof(double), ctx->cap_stream, true);
+    s = issue_sequence(ctx, p, nexp, chunk, table_n * sizeof(double), ctx->cap_stream, true);
     cudaError_t ec = cudaStreamEndCapture(ctx->cap_stream, &graph);
     if (s != CFET_OK) {
       if (graph) cudaGraphDestroy(graph);
@@ -967,6 +1069,8 @@ cfet_status cfet_fidelity_grad(cfet_ctx* ctx, const void* psi0, const void* phi,
                                int64_t nsteps, int32_t order, double krylov_tol, int32_t nseg, const double* amps,
                                double omega, double phase, int64_t checkpoint_every, void* stream, double* loss,
                                double* grad, cfet_grad_stats* gstats) {
+  if (ctx && ctx->opt.expm != CFET_EXPM_KRYLOV)
+    return fail(ctx, CFET_EINVAL, "fidelity gradient: the context must use CFET_EXPM_KRYLOV");
   if (!ctx) return CFET_EINVAL;
   if (ctx->family != kFamilySpin || ctx->nV != 1)
     return fail(ctx, CFET_EINVAL, "fidelity gradient: needs an XXZ chain with exactly one X-field drive");

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 
 #include <vector_types.h>
 
@@ -132,7 +133,25 @@ struct PropParams {
   longlong2* qbasis;
   // mixed-precision path: complex64 Krylov vectors, q_i at qbasis32 + (i-1)*dim
   float2* qbasis32;
+  // Chebyshev path: kChebRec doubles per exponential (global index) and the
+  // concatenated expansion coefficients r_k
+  const double* cheb;
+  const double* cheb_coef;
 };
+
+// Chebyshev record of one stage exponential (host-computed, see chebyshev.cpp):
+// 1/a, b/a, K, offset of r_0 in cheb_coef, sum_k |r_k|, cos(dt b), -sin(dt b),
+// tail bound
+constexpr int kChebRec = 8;
+int cheb_kmax(double z);
+int cheb_series(double z, double tol, std::vector<double>* r, double* tail);
+void spin_h0_interval(int N, double J, double Delta, const double* h, double* lo, double* hi);
+void xfield_interval(int N, const double* a, double* lo, double* hi);
+void dia_interval(const int64_t* offsets, const double* values, int ndiag, int dim, double* lo, double* hi);
+void stage_interval(int nops, const double* op_lo, const double* op_hi, const double* s, double* lo, double* hi);
+int launch_cheb_spin_fx(const PropParams& p, const OpSpinFx& op, int grid, int block, void* stream);
+int launch_cheb_dia_fx(const PropParams& p, const OpDiaFx& op, int grid, int block, void* stream);
+int max_coresident_blocks_cheb(int family, int block);
 
 // Backward (adjoint) sweep of the fidelity gradient (see adjoint.cu).
 constexpr int kAdjMaxK = 16;     // Krylov dimension limit of the adjoint sweep

@@ -97,6 +97,14 @@ def test_create_validates_arguments(lib):
     st, _ = _create(lib, ok_h0, [xf], [cb], opt)
     assert st == _capi.CFET_EINVAL and b"precision" in lib.cfet_last_error(None)
     opt.precision = _capi.CFET_PREC_DEFAULT
+    # expansion method: known values only; Chebyshev is fixed point only
+    opt.expm = 5
+    st, _ = _create(lib, ok_h0, [xf], [cb], opt)
+    assert st == _capi.CFET_EINVAL and b"expm" in lib.cfet_last_error(None)
+    opt.expm, opt.precision = _capi.CFET_EXPM_CHEBYSHEV, _capi.CFET_PREC_C64
+    st, _ = _create(lib, ok_h0, [xf], [cb], opt)
+    assert st == _capi.CFET_EINVAL and b"CHEBYSHEV" in lib.cfet_last_error(None)
+    opt.expm, opt.precision = _capi.CFET_EXPM_KRYLOV, _capi.CFET_PREC_DEFAULT
     # DIA offsets out of range
     dia = P._op_struct(P.DIA(np.array([0, 7]), np.ones((2, 7))), keep)
     assert _create(lib, dia, [], [])[0] == _capi.CFET_EINVAL
@@ -107,6 +115,7 @@ def test_options_default(lib):
     lib.cfet_options_default(C.byref(opt))
     assert (opt.m_max, opt.m_min, opt.max_substeps, opt.block_size) == (16, 2, 64, 0)
     assert opt.barrier_timeout_s == 2.0
+    assert opt.expm == _capi.CFET_EXPM_KRYLOV
 
 
 def test_no_device_gives_enodev(lib):
@@ -174,3 +183,41 @@ def test_wait_selftest_validates(lib):
     assert lib.cfet_selftest_wait_timeout(0, 0.0, C.byref(st)) == _capi.CFET_EINVAL
     assert lib.cfet_selftest_wait_timeout(0, 20.0, C.byref(st)) == _capi.CFET_EINVAL
     assert lib.cfet_selftest_wait_timeout(0, 0.1, None) == _capi.CFET_EINVAL
+
+
+# ---------------------------------------------------------------- Chebyshev coefficients (host only)
+@pytest.mark.parametrize("z", [1e-3, 0.5, 3.0, -7.3, 40.0, 300.0])
+@pytest.mark.parametrize("tol", [1e-6, 1e-10, 0.0])
+def test_chebyshev_coefficients_match_library_bessel(lib, z, tol):
+    # r_k = (2 - delta_k0) J_k(z) from Miller's recurrence against scipy's J_k,
+    # and the same truncation order as the oracle's rule
+    from scipy import special
+    from oracle import chebyshev as CH
+    r, K, tail = P.chebyshev_coefficients(z, tol)
+    ref = special.jv(np.arange(K + 1), z)
+    ref[1:] *= 2.0
+    assert np.max(np.abs(r - ref)) <= 1e-14 * max(1.0, abs(z)) ** 0.5
+    r_o, K_o, tail_o = CH.coefficients(z, tol)
+    assert K == K_o and abs(tail - tail_o) <= 1e-14
+    assert tail <= (tol if tol > 0 else 2.0 ** -52)
+
+
+def test_chebyshev_coefficients_closed_forms(lib):
+    # z = 0: exp(0) = T_0 only; the normalisation J_0 + 2 sum J_2k = 1 and
+    # sum_k r_k (-i)^k T_k(1) = exp(-i z) (Jacobi-Anger at x = 1)
+    r, K, tail = P.chebyshev_coefficients(0.0, 1e-12)
+    assert K == 0 and r.tolist() == [1.0] and tail == 0.0
+    for z in (0.9, 12.0, 150.0):
+        r, K, _ = P.chebyshev_coefficients(z, 0.0)
+        assert abs(r[0] + r[2::2].sum() - 1.0) <= 1e-14
+        s = sum(r[k] * (-1j) ** k for k in range(K + 1))
+        assert abs(s - np.exp(-1j * z)) <= 1e-13
+
+
+def test_chebyshev_coefficients_validate(lib):
+    K, tail = C.c_int32(), C.c_double()
+    assert lib.cfet_chebyshev_coefficients(float("nan"), 1e-8, 0, None, C.byref(K), C.byref(tail)) == _capi.CFET_EINVAL
+    assert lib.cfet_chebyshev_coefficients(2e8, 1e-8, 0, None, C.byref(K), C.byref(tail)) == _capi.CFET_EINVAL
+    buf = np.zeros(2)
+    st = lib.cfet_chebyshev_coefficients(10.0, 1e-8, 2, buf.ctypes.data_as(_capi.c_double_p), C.byref(K), C.byref(tail))
+    assert st == _capi.CFET_EINVAL and K.value > 1
