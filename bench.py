@@ -628,6 +628,83 @@ def run_study_adjoint(args):
     return 0
 
 
+def run_study_expm(args):
+    """Krylov (Sec. 8.1, the default) against the Chebyshev technique (Sec. 8.1/8.2)
+    for the stage exponentials, both in the fixed-point format at the same
+    tolerance: the N=20 chain over T = --sweep-T with CF6:5Opt at dt in
+    {0.05, 0.02, 0.01}, each run compared with a reference (CF8:11, dt 0.0025,
+    tol 1e-13, Krylov) by ||psi - psi_ref||_2 (Chebyshev also at tolerances
+    1e-12 and 1e-14); then the grid atom (CF8:11,
+    dt 0.1, from t = 500) for --steps steps with both methods.  One JSON line
+    per run.  Chebyshev algorithmic bytes per element and term: read v_k,
+    v_{k-1} and the partial sum, write v_{k+1} and the partial sum (80 B)."""
+    import torch
+    import paper_1102_5071_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    pr, psi0 = problem()
+    T = args.sweep_T
+
+    def chain(expm, m_max=M_MAX):
+        return P.Propagator(P.XXZChain(N_SITES, pr.J, pr.Delta, pr.h), [P.XField(N_SITES, pr.xfield)],
+                            [pr.drive], m_max=m_max, max_substeps=64, expm=expm)
+
+    def timed(prop, psi, *a, **kw):
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        st = prop.propagate(psi, *a, **kw)
+        ev1.record()
+        torch.cuda.synchronize()
+        return st, ev0.elapsed_time(ev1)
+
+    ref_prop = chain("krylov", 24)
+    ref = torch.from_numpy(psi0).cuda()
+    ref_prop.propagate(ref, 0.0, 0.0025, int(round(T / 0.0025)), order=8, tol=1e-13)
+    ref_prop.close()
+    dim = 1 << N_SITES
+    # the Chebyshev tail bound is nearly attained and its stage errors add up,
+    # while the Krylov estimate is pessimistic: Chebyshev runs at three tolerances
+    for expm, tols in (("krylov", (TOL,)), ("chebyshev", (TOL, 1e-12, 1e-14))):
+        prop = chain(expm)
+        for dt, tol in [(dt, tol) for dt in (0.05, 0.02, 0.01) for tol in tols]:
+            n = int(round(T / dt))
+            psi = torch.from_numpy(psi0).cuda()
+            prop.propagate(psi, 0.0, dt, 2, order=6, tol=tol)        # warm-up (graph, tables)
+            psi = torch.from_numpy(psi0).cuda()
+            st, ms = timed(prop, psi, 0.0, dt, n, order=6, tol=tol)
+            kms = prop.kernel_time_ms()
+            row = {"study": "expm", "workload": "driven XXZ chain N=20 CF6:5Opt T=%g tol %g" % (T, tol),
+                   "expm": expm, "dt": dt, "steps": n, "H_applies": st["n_applies"],
+                   "applies_per_exponential": st["n_applies"] / st["n_exp"], "max_k": st["max_k"],
+                   "H_applies_per_s": st["n_applies"] / (ms * 1e-3), "cfet_steps_per_s": n / (ms * 1e-3),
+                   "time_s": ms * 1e-3, "final_state_error": torch.linalg.vector_norm(psi - ref).item()}
+            if expm == "chebyshev":
+                row["algorithmic_GBps"] = dim * 80.0 * st["n_applies"] / (kms * 1e-3) / 1e9
+            print(json.dumps(row))
+        prop.close()
+    a = W.ATOM
+    p = W.grid_atom(Nr=a["Nr"], L=a["L"], dr=a["dr"], E0=a["E0"], omega=a["omega"], Tp=a["Tp"])
+    psi0a, _ = W.atom_ground_state(p)
+    outs = {}
+    for expm in ("krylov", "chebyshev"):
+        prop = P.Propagator(P.DIA(p.H0_offsets, p.H0_values), [P.DIA(p.V_offsets, p.V_values)], [p.drive],
+                            m_max=a["m_max"], max_substeps=4000, expm=expm)
+        psi = torch.from_numpy(psi0a).cuda()
+        prop.apply(np.array([1.0, 0.0]), psi, torch.empty_like(psi))
+        st, ms = timed(prop, psi, 500.0, a["dt"], args.steps, order=a["order"], tol=a["tol"])
+        outs[expm] = psi
+        print(json.dumps({"study": "expm", "workload": "grid atom Nr=2000 L=100 CF8:11 dt=0.1 tol %g from t=500"
+                          % a["tol"], "expm": expm, "steps": args.steps, "H_applies": st["n_applies"],
+                          "applies_per_exponential": st["n_applies"] / st["n_exp"], "max_k": st["max_k"],
+                          "H_applies_per_s": st["n_applies"] / (ms * 1e-3), "time_s": ms * 1e-3,
+                          "ms_per_step": ms / args.steps}))
+        prop.close()
+    print(json.dumps({"study": "expm", "atom_krylov_vs_chebyshev_difference":
+                      torch.linalg.vector_norm(outs["krylov"] - outs["chebyshev"]).item()}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -641,9 +718,9 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="accuracy study: final-state error and throughput per (order, dt) over T")
     ap.add_argument("--sweep-T", type=float, default=20.0)
-    ap.add_argument("--study", choices=["atom", "sizes", "batch", "adjoint"],
+    ap.add_argument("--study", choices=["atom", "sizes", "batch", "adjoint", "expm"],
                     help="extra measurements: the grid atom, the chain at N = 20..26, the 256-chain batch, "
-                         "the fidelity gradient")
+                         "the fidelity gradient, Krylov against Chebyshev stage exponentials")
     ap.add_argument("--baseline-steps", type=int, default=10,
                     help="batch study: steps of the single-instance baseline per instance")
     ap.add_argument("--grid-size", type=int, default=0,
@@ -665,6 +742,8 @@ def main():
         return run_study_batch(args)
     if args.study == "adjoint":
         return run_study_adjoint(args)
+    if args.study == "expm":
+        return run_study_expm(args)
     return run_gpu(args)
 
 

@@ -39,27 +39,35 @@
 namespace cfet {
 
 constexpr int kChebThreads = 768;   // launch bound of the kernel
-constexpr double kChebA = 4503599627370496.0;  // 2^52: bound of every stored |v_k| mantissa
 
 struct SmemCheb {
-  FxConstA c[2];                  // term 1 (Htilde, no v_{k-1}) and terms k >= 2 (2 Htilde, -v_{k-1})
-  long long mb[2][kMaxSites];     // per-site field tables of both (non-uniform fields)
-  long long m_s[2];               // shift terms -b/a v and -2b/a v
+  // constants of the current term
+  FxConstA c;
+  long long mb[kMaxSites];        // per-site field table (site-dependent fields)
+  long long m_s;                  // shift term -g b v
+  long long m_r, m_r0;            // r_k (-i)^k y and r_0 v_0 into the sum
+  int py, p0;                     // normalising shifts of y and v_0 in those products
+  int sa;                         // right shift of the stored sum before this term's addition
+  int E_acc;                      // exponent of the sum after this term
+  int E_out;                      // exponent of this term's output
+  long long m_cs, m_sn;           // conversion of the sum to v_0: cos(tau b), -sin(tau b)
+  int L_rot;
+  // per exponential
   double scal[1 + kMaxDrives];
   double bsite[kMaxSites];
   double bsum, bmax;
-  // accumulation and rotation
-  long long m_cs, m_sn;           // cos(tau b), -sin(tau b) at the conversion of the sum to v_0
-  int ea, L_rot, K;
-  int E;
-  // reductions of the initial pass
+  // vectors: exponent and measured max |mantissa| of the three slots
+  int Ev[3];
+  long long Av[3];
+  long long accmax;               // measured max |mantissa| of the sum
+  // reductions
+  unsigned long long wmy[32], wma[32];
   double wsum[32];
-  unsigned long long wmax[32];
   int abort_flag;
 };
 
-// Exchange accumulators (records of 4, 2 or 1 words).
-struct ChebSumMax {
+// Exchange accumulators.
+struct ChebSumMax {  // FP64 sum + max (the initial pass)
   double s;
   unsigned long long m;
   __device__ void reset() { s = 0.0; m = 0; }
@@ -69,100 +77,98 @@ struct ChebSumMax {
     m = x > m ? x : m;
   }
 };
-struct ChebMax {
-  unsigned long long m;
-  __device__ void reset() { m = 0; }
-  __device__ void add(const unsigned (&v)[2]) {
+struct ChebMax2 {    // two maxima
+  unsigned long long a, b;
+  __device__ void reset() { a = 0; b = 0; }
+  __device__ void add(const unsigned (&v)[4]) {
     const unsigned long long x = ((unsigned long long)v[1] << 32) | v[0];
-    m = x > m ? x : m;
+    const unsigned long long y = ((unsigned long long)v[3] << 32) | v[2];
+    a = x > a ? x : a;
+    b = y > b ? y : b;
   }
 };
-struct ChebNone {
-  __device__ void reset() {}
-  __device__ void add(const unsigned (&)[1]) {}
-};
 
-// Fixed-point constants of  y = g H_j v - g b v - use_prev v_prev  with v,
-// v_prev mantissas below 2^52 at exponent E and y at exponent E (scalar part on
-// lane 0 of warp 0, per-site table over the lanes).  Returns false when the
-// term bound does not fit the format at exponent E (not expected: the
-// Gershgorin interval bounds every row).
+// Constants of the term  y = g H_j v - g b v - use_prev * v_prev  (lane 0 of
+// warp 0 for the scalars, the lanes for the per-site table): v has measured
+// max |mantissa| Ak at exponent Ek, v_prev Apr at Epr; y gets the exponent of
+// the rigorous bound B of its terms (returned in real units), as in the Krylov
+// kernel (kernels_fx.cu).  Returns B.
 template <int FAMILY, class Op>
-__device__ bool cheb_const(SmemCheb& S, int slot, const Op& op, double g, double gb, int use_prev, int E) {
+__device__ double cheb_term_const(SmemCheb& S, const Op& op, double g, double gb, int use_prev, long long Ak, int Ek,
+                                  long long Apr, int Epr) {
   const int lane = threadIdx.x & 31;
-  FxConstA& c = S.c[slot];
-  int ok = 1;
+  FxConstA& c = S.c;
+  double B = 0.0;
+  int eb = 0;
   if (lane == 0) {
-    const double Ak = kChebA;
-    const double Akr = fx_scale2(Ak, E);
-    c.pk = fx_norm_shift(Ak);
-    double B = (use_prev ? Akr : 0.0) + fabs(gb) * Akr;
+    const double A = (double)Ak;
+    const double Akr = fx_scale2(A, Ek);
+    const double Aprr = use_prev ? fx_scale2((double)Apr, Epr) : 0.0;
+    c.pk = fx_norm_shift(A);
+    B = Aprr + fabs(gb) * Akr;
     if constexpr (FAMILY == kFamilySpin) {
       const double cz = S.scal[0] * g;
       const double ch = cz * op.J2;
       B += (fabs(cz) * op.maxdz + fabs(ch) * (op.N - 1) + fabs(g) * S.bsum) * Akr;
-    } else {
-      for (int o = 0; o < op.nops; ++o) B += fabs(S.scal[o] * g) * op.maxrow[o] * Akr;
-    }
-    if (fx_exp_for(B, kFxBits) > E) ok = 0;
-    const int Eu = E;
-    if constexpr (FAMILY == kFamilySpin) {
-      const double cz = S.scal[0] * g;
-      const double ch = cz * op.J2;
+      const int Eu = fx_exp_for(B, kFxBits);
+      c.Eu = Eu;
       const Mant mcz = fx_mant(cz);
       const int ED = fx_exp_for(fabs(cz) * op.maxdz, 59);
       c.s_d = ED - mcz.e - (op.E_dz - 1) - 64;
-      c.s_diag = Eu - (ED - 3) - (E - c.pk) - 64;
+      c.s_diag = Eu - (ED - 3) - (Ek - c.pk) - 64;
       c.m_cz = fx_fold(mcz.m, c.s_d + c.s_diag);
       const Mant mh = fx_mant(ch);
-      c.ph = fx_norm_shift((op.N > 1 ? op.N - 1 : 1) * Ak);
-      c.s_hop = Eu - mh.e - (E - c.ph) - 64;
+      c.ph = fx_norm_shift((op.N > 1 ? op.N - 1 : 1) * A);
+      c.s_hop = Eu - mh.e - (Ek - c.ph) - 64;
       c.m_hop = fx_fold(mh.m, c.s_hop);
       if (op.uniform) {
         const Mant mx = fx_mant(S.bsite[0] * g);
-        c.px = fx_norm_shift(op.N * Ak);
-        c.s_x = Eu - mx.e - (E - c.px) - 64;
+        c.px = fx_norm_shift(op.N * A);
+        c.s_x = Eu - mx.e - (Ek - c.px) - 64;
         c.m_x = fx_fold(mx.m, c.s_x);
       } else {
-        const int eb = fx_exp_for(fabs(g) * S.bmax, 62);
-        c.s_nu = Eu - eb - (E - c.pk) - 64;
-        c.Eu = eb;  // carried to the lanes below
+        eb = fx_exp_for(fabs(g) * S.bmax, 62);
+        c.s_nu = Eu - eb - (Ek - c.pk) - 64;
       }
     } else {
+      for (int o = 0; o < op.nops; ++o) B += fabs(S.scal[o] * g) * op.maxrow[o] * Akr;
+      const int Eu = fx_exp_for(B, kFxBits);
+      c.Eu = Eu;
       for (int o = 0; o < op.nops; ++o) {
         const int Epre = fx_exp_for(op.maxrow[o] * Akr, 62);  // |P_o| < 2^62
-        c.sh_pre[o] = Epre - op.E_op[o] - E;
+        c.sh_pre[o] = Epre - op.E_op[o] - Ek;
         const Mant m = fx_mant(S.scal[o] * g);
         c.s_op[o] = Eu - m.e - Epre - 64;
         c.m_op[o] = fx_fold(m.m, c.s_op[o]);
       }
     }
     const Mant mp = fx_mant(-1.0);
-    c.pp = c.pk;
-    c.s_p = Eu - mp.e - (E - c.pp) - 64;
-    c.m_p = fx_fold(mp.m, c.s_p);
+    c.pp = use_prev ? fx_norm_shift((double)Apr) : 0;
+    c.s_p = c.Eu - mp.e - (Epr - c.pp) - 64;
+    c.m_p = use_prev ? fx_fold(mp.m, c.s_p) : 0;
     c.use_prev = use_prev;
     const Mant ms = fx_mant(-gb);
-    S.m_s[slot] = ms.m == 0 ? 0 : fx_fold(ms.m, Eu - ms.e - (E - c.pk) - 64);
+    S.m_s = ms.m == 0 ? 0 : fx_fold(ms.m, c.Eu - ms.e - (Ek - c.pk) - 64);
   }
-  __syncwarp();
   if constexpr (FAMILY == kFamilySpin) {
     if (!op.uniform) {
-      const int eb = c.Eu;
+      eb = __shfl_sync(0xffffffffu, eb, 0);
+      __syncwarp();
+      const int s_nu = c.s_nu;
       for (int i = lane; i < op.N; i += 32)
-        S.mb[slot][i] = fx_fold(__double2ll_rn(fx_scale2(S.bsite[i] * g, -eb)), c.s_nu);
+        S.mb[i] = fx_fold(__double2ll_rn(fx_scale2(S.bsite[i] * g, -eb)), s_nu);
     }
   }
   __syncwarp();
-  c.Eu = E;
-  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+  return __shfl_sync(0xffffffffu, B, 0);
 }
 
-// acc-term constant: r * y (y mantissa < 2^52 at E) at exponent E + ea.
-__device__ __forceinline__ long long cheb_rk(double r, int ea, int py) {
+// fx_mulhi(fold(mant(r)), x << p) = r * x * 2^(Ex - Eout) for x at exponent Ex
+// (|x| normalised by p), result at exponent Eout.
+__device__ __forceinline__ long long cheb_coef(double r, int Eout, int Ex, int p) {
   const Mant m = fx_mant(r);
   if (m.m == 0) return 0;
-  return fx_fold(m.m, ea - m.e - (-py) - 64);
+  return fx_fold(m.m, Eout - m.e - (Ex - p) - 64);
 }
 
 // (-i)^k (yr + i yi)
@@ -175,7 +181,6 @@ __device__ __forceinline__ void cheb_rot(int k, long long yr, long long yi, long
   }
 }
 
-// One element of a term: y = (apply) + shift; returns y.
 template <int FAMILY, class Op>
 __device__ __forceinline__ longlong2 cheb_apply1(const longlong2* cur, const longlong2* prev, int x, int dim,
                                                  const Op& op, const FxConstA& c, const long long* mb, long long m_s) {
@@ -188,6 +193,54 @@ __device__ __forceinline__ longlong2 cheb_apply1(const longlong2* cur, const lon
     y.y += fx_mulhi(m_s, v.y << c.pk);
   }
   return y;
+}
+
+// One term over this thread's elements: y = apply (APPLY), the sum updated
+// (FIRST: r_0 v_0 + r_1 (-i) y; else shifted old sum + r_k (-i)^k y) and
+// either stored with y (not LAST) or converted to the next v_0 (LAST; written
+// to dst, or in place for the phase-only case, and to psi at the end).
+template <int FAMILY, bool FIRST, bool LAST, bool APPLY, class Op>
+__device__ __forceinline__ void cheb_pass(const SmemCheb& S, const Op& op, const PropParams& p, int k,
+                                          const longlong2* cur, const longlong2* prev, longlong2* dst,
+                                          longlong2* acc, const longlong2* v0, int wx0, int wxe, int wstep,
+                                          bool last_exp, long long& my, long long& ma) {
+  const int dim = p.dim;
+  for (int x = wx0; x < wxe; x += wstep) {
+    long long ar, ai;
+    longlong2 y = make_longlong2(0, 0);
+    if (FIRST) {
+      const longlong2 v = v0[x];
+      ar = fx_mulhi(S.m_r0, v.x << S.p0);
+      ai = fx_mulhi(S.m_r0, v.y << S.p0);
+    } else {
+      const longlong2 a = acc[x];
+      ar = fx_rshr(a.x, S.sa);
+      ai = fx_rshr(a.y, S.sa);
+    }
+    if (APPLY) {
+      y = cheb_apply1<FAMILY>(cur, prev, x, dim, op, S.c, S.mb, S.m_s);
+      long long zr, zi;
+      cheb_rot(k, y.x, y.y, zr, zi);
+      ar += fx_mulhi(S.m_r, zr << S.py);
+      ai += fx_mulhi(S.m_r, zi << S.py);
+    }
+    if (!LAST) {
+      dst[x] = y;
+      acc[x] = make_longlong2(ar, ai);
+      my = max(my, fx_absmax(y.x, y.y));
+      ma = max(ma, fx_absmax(ar, ai));
+    } else {
+      const int L = S.L_rot;
+      const long long nr = (fx_mulhi(S.m_cs, ar << 4) - fx_mulhi(S.m_sn, ai << 4)) << L;
+      const long long ni = (fx_mulhi(S.m_sn, ar << 4) + fx_mulhi(S.m_cs, ai << 4)) << L;
+      dst[x] = make_longlong2(nr, ni);
+      my = max(my, fx_absmax(nr, ni));
+      if (last_exp) {
+        const double osc = fx_scale2(1.0, S.E_out);
+        p.psi[x] = make_double2(__ll2double_rn(nr) * osc, __ll2double_rn(ni) * osc);
+      }
+    }
+  }
 }
 
 template <int FAMILY, class Op>
@@ -211,98 +264,86 @@ __global__ void __launch_bounds__(kChebThreads, 1) k_cheb_fx(PropParams p, Op op
   DevStatus* st = p.st;
   const bool glead = blockIdx.x == 0 && tid == 0;
   long long t_loop = 0, t_wait = 0;
-  // vectors: three slots of the fixed-point workspace
   longlong2* V[3] = {p.qbasis, p.qbasis + dim, p.qbasis + 2 * (size_t)dim};
   int sA = 0, sB = 1;
   const int sC = 2;  // the sum
 
-  // exchange by warp 0 after all element work of the CTA; every thread learns
-  // the outcome from S.abort_flag
-  auto exchange1 = [&](bool fence) -> bool {
+  // CTA maxima of |y| and |sum| -> grid maxima (exchange by warp 0); false on abort
+  auto exchange_max = [&](long long my, long long ma, bool fence, unsigned long long& gy,
+                          unsigned long long& ga) -> bool {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      my = max(my, __shfl_xor_sync(0xffffffffu, my, o));
+      ma = max(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+    }
+    if (lane == 0) {
+      S.wmy[warp] = (unsigned long long)my;
+      S.wma[warp] = (unsigned long long)ma;
+    }
     __syncthreads();
     if (warp == 0) {
-      const unsigned mine[1] = {0u};
-      ChebNone acc;
-      const bool ok = ctl_exchange<1>(rec + (size_t)slot * 4 * G, mine, tag0 + (++gen), fence, &st->status,
+      unsigned long long cy = lane < NW ? S.wmy[lane] : 0, ca = lane < NW ? S.wma[lane] : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        cy = max(cy, __shfl_xor_sync(0xffffffffu, cy, o));
+        ca = max(ca, __shfl_xor_sync(0xffffffffu, ca, o));
+      }
+      const unsigned mine[4] = {(unsigned)cy, (unsigned)(cy >> 32), (unsigned)ca, (unsigned)(ca >> 32)};
+      ChebMax2 acc;
+      const bool ok = ctl_exchange<4>(rec + (size_t)slot * 4 * G, mine, tag0 + (++gen), fence, &st->status,
                                       p.timeout_ns, t_wait, acc);
+      unsigned long long ty = acc.a, ta = acc.b;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ty = max(ty, __shfl_xor_sync(0xffffffffu, ty, o));
+        ta = max(ta, __shfl_xor_sync(0xffffffffu, ta, o));
+      }
+      gy = ty;
+      ga = ta;
       if (lane == 0 && !ok) S.abort_flag = 1;
     } else {
       ++gen;
     }
     slot ^= 1;
-    __syncthreads();
-    return S.abort_flag == 0;
+    return true;
   };
 
-  // ---------------- psi: NaN check and ||psi||^2 -> E; convert to v_0
+  // ---------------- psi: NaN check and max |psi| -> E_0; convert to v_0
   {
     if (tid == 0) S.abort_flag = 0;
-    double s2 = 0.0;
     unsigned long long mx = 0;
     for (int x = wx0; x < wxe; x += wstep) {
       const double2 v = p.psi[x];
       const unsigned long long a = (unsigned long long)__double_as_longlong(v.x) & 0x7FFFFFFFFFFFFFFFULL;
       const unsigned long long b = (unsigned long long)__double_as_longlong(v.y) & 0x7FFFFFFFFFFFFFFFULL;
       mx = max(mx, max(a, b));
-      s2 = fma(v.x, v.x, fma(v.y, v.y, s2));
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-      const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, mx, o);
-      mx = m2 > mx ? m2 : mx;
-    }
-    if (lane == 0) {
-      S.wsum[warp] = s2;
-      S.wmax[warp] = mx;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      double cs = lane < NW ? S.wsum[lane] : 0.0;
-      unsigned long long cm = lane < NW ? S.wmax[lane] : 0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        cs += __shfl_xor_sync(0xffffffffu, cs, o);
-        const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, cm, o);
-        cm = m2 > cm ? m2 : cm;
+    unsigned long long gm = 0, unused = 0;
+    exchange_max((long long)mx, 0, false, gm, unused);
+    if (warp == 0 && lane == 0 && !S.abort_flag) {
+      if (gm >= 0x7FF0000000000000ULL) {
+        atomicCAS(&st->status, 0, (int)CFET_ENAN);
+        S.abort_flag = 1;
+      } else {
+        S.Ev[sA] = fx_exp_for(__longlong_as_double((long long)gm), kFxBits);
       }
-      const unsigned long long cb = (unsigned long long)__double_as_longlong(cs);
-      const unsigned mine[4] = {(unsigned)cb, (unsigned)(cb >> 32), (unsigned)cm, (unsigned)(cm >> 32)};
-      ChebSumMax acc;
-      const bool ok = ctl_exchange<4>(rec + (size_t)slot * 4 * G, mine, tag0 + (++gen), false, &st->status,
-                                      p.timeout_ns, t_wait, acc);
-      double ts = acc.s;
-      unsigned long long tm = acc.m;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        ts += __shfl_xor_sync(0xffffffffu, ts, o);
-        const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, tm, o);
-        tm = m2 > tm ? m2 : tm;
-      }
-      if (lane == 0) {
-        if (!ok) {
-          S.abort_flag = 1;
-        } else if (tm >= 0x7FF0000000000000ULL || !(ts < 1e300)) {
-          atomicCAS(&st->status, 0, (int)CFET_ENAN);
-          S.abort_flag = 1;
-        } else {
-          S.E = fx_exp_for(32.0 * sqrt(ts), kFxBits);
-        }
-      }
-    } else {
-      ++gen;
     }
-    slot ^= 1;
     __syncthreads();
     if (S.abort_flag) return;
-    const double sc = fx_scale2(1.0, -S.E);
+    const double sc = fx_scale2(1.0, -S.Ev[sA]);
+    long long my = 0;
     for (int x = wx0; x < wxe; x += wstep) {
       const double2 v = p.psi[x];
-      V[sA][x] = make_longlong2(__double2ll_rn(v.x * sc), __double2ll_rn(v.y * sc));
+      const longlong2 q = make_longlong2(__double2ll_rn(v.x * sc), __double2ll_rn(v.y * sc));
+      V[sA][x] = q;
+      my = max(my, fx_absmax(q.x, q.y));
     }
-    if (!exchange1(true)) return;
+    unsigned long long gy = 0;
+    exchange_max(my, 0, true, gy, unused);
+    if (warp == 0 && lane == 0) S.Av[sA] = (long long)gy;
+    __syncthreads();
+    if (S.abort_flag) return;
   }
-  const int E = S.E;
 
   long long n_app = 0;
   int max_k = 0;
@@ -313,11 +354,10 @@ __global__ void __launch_bounds__(kChebThreads, 1) k_cheb_fx(PropParams p, Op op
     const int K = (int)R[2];
     const double* rk = p.cheb_coef + (long long)R[3];
     const bool last_exp = e == p.nexp - 1;
-    // ---- constants of this exponential (warp 0)
     if (tid < ncoef) S.scal[tid] = p.scal[e * ncoef + tid];
     __syncthreads();
-    if (warp == 0) {
-      if constexpr (FAMILY == kFamilySpin) {
+    if constexpr (FAMILY == kFamilySpin) {
+      if (warp == 0) {  // per-site transverse fields of this stage
         double bi = 0.0;
         if (lane < op.N) {
           for (int k = 0; k < p.nV; ++k) bi = fma(S.scal[1 + k], __ldg(op.xf + k * op.N + lane), bi);
@@ -335,90 +375,99 @@ __global__ void __launch_bounds__(kChebThreads, 1) k_cheb_fx(PropParams p, Op op
         }
         __syncwarp();
       }
-      const double g1 = R[0], ba = R[1];
-      bool ok = cheb_const<FAMILY>(S, 0, op, g1, ba, 0, E);
-      ok = cheb_const<FAMILY>(S, 1, op, 2.0 * g1, 2.0 * ba, 1, E) && ok;
-      if (lane == 0) {
-        // the sum lives at exponent E + ea with |mantissa| < 2^57
-        const int ea = fx_exp_for(R[4] * kChebA, kFxBits);
-        S.ea = ea;
-        S.K = K;
-        // conversion v_0 = rot(sum) * 2^ea: products fx_mulhi(m, sum << 4) << L_rot
-        const Mant mc = fx_mant(R[5]), ms = fx_mant(R[6]);
-        int sc_ = mc.m ? -ea - mc.e - 60 : 1 << 20, ss_ = ms.m ? -ea - ms.e - 60 : 1 << 20;
-        int L = 0;
-        if (-sc_ > L) L = -sc_;
-        if (-ss_ > L) L = -ss_;
-        S.L_rot = L;
-        S.m_cs = mc.m ? fx_fold(mc.m, sc_ + L) : 0;
-        S.m_sn = ms.m ? fx_fold(ms.m, ss_ + L) : 0;
-        if (!ok) {
-          atomicCAS(&st->status, 0, (int)CFET_EINVAL);
-          S.abort_flag = 1;
-        }
-      }
     }
-    __syncthreads();
-    if (S.abort_flag) return;
-    const int ea = S.ea, L_rot = S.L_rot;
-    const long long m_cs = S.m_cs, m_sn = S.m_sn;
     const long long t0 = sm_clock();
-    // ---- terms k = 1..K (K = 0: the phase only)
     for (int k = (K == 0 ? 0 : 1); k <= K; ++k) {
       const bool last = k == K;
       const bool first = k <= 1;
-      const FxConstA& c = S.c[first ? 0 : 1];
-      const long long* mb = S.mb[first ? 0 : 1];
-      const long long m_s = S.m_s[first ? 0 : 1];
       // v_{k-1} is in (k-1 even ? sA : sB), v_{k-2} in the other; y = v_k goes to v_{k-2}'s slot
-      const longlong2* cur = V[((k - 1) & 1) ? sB : sA];
-      longlong2* dst = V[((k - 1) & 1) ? sA : sB];
-      const longlong2* prev = k >= 2 ? dst : cur;
-      longlong2* acc = V[sC];
-      const long long mr = cheb_rk(k == 0 ? 0.0 : __ldg(rk + k), ea, fx_norm_shift(kChebA));
-      const long long m0 = cheb_rk(__ldg(rk), ea, fx_norm_shift(kChebA));
-      const int py = fx_norm_shift(kChebA);
-      for (int x = wx0; x < wxe; x += wstep) {
-        long long ar, ai;
-        if (k == 0) {
-          const longlong2 v = V[sA][x];
-          ar = fx_mulhi(m0, v.x << py);
-          ai = fx_mulhi(m0, v.y << py);
-        } else {
-          const longlong2 y = cheb_apply1<FAMILY>(cur, prev, x, dim, op, c, mb, m_s);
-          long long zr, zi;
-          cheb_rot(k, y.x, y.y, zr, zi);
+      const int scur = ((k - 1) & 1) ? sB : sA;
+      const int sdst = ((k - 1) & 1) ? sA : sB;
+      // ---- constants of this term (warp 0)
+      if (warp == 0) {
+        double By = 0.0;  // bound of |y| (real units)
+        if (k >= 1) {
+          const double g = first ? R[0] : 2.0 * R[0];
+          const double gb = first ? R[1] : 2.0 * R[1];
+          By = cheb_term_const<FAMILY>(S, op, g, gb, first ? 0 : 1, S.Av[scur], S.Ev[scur],
+                                       first ? 0 : S.Av[sdst], first ? 0 : S.Ev[sdst]);
+        }
+        if (lane == 0) {
+          const int Ey = S.c.Eu;
+          S.py = fx_norm_shift(k >= 1 ? fx_scale2(By, -Ey) : 0.0);
+          // the sum: old part (measured) plus this term's bound
+          double Bacc;
+          int Eacc;
           if (first) {
-            const longlong2 v = cur[x];
-            ar = fx_mulhi(m0, v.x << py);
-            ai = fx_mulhi(m0, v.y << py);
+            const double A0r = fx_scale2((double)S.Av[sA], S.Ev[sA]);
+            Bacc = fabs(rk[0]) * A0r + (k >= 1 ? fabs(rk[1]) * By : 0.0);
+            Eacc = fx_exp_for(Bacc, kFxBits);
+            S.sa = 0;
+            S.p0 = fx_norm_shift((double)S.Av[sA]);
+            S.m_r0 = cheb_coef(rk[0], Eacc, S.Ev[sA], S.p0);
           } else {
-            const longlong2 a = acc[x];
-            ar = a.x;
-            ai = a.y;
+            Bacc = fx_scale2((double)S.accmax, S.E_acc) + fabs(rk[k]) * By;
+            Eacc = max(S.E_acc, fx_exp_for(Bacc, kFxBits));
+            S.sa = Eacc - S.E_acc;
           }
-          ar += fx_mulhi(mr, zr << py);
-          ai += fx_mulhi(mr, zi << py);
-          if (!last) {
-            dst[x] = y;
-            acc[x] = make_longlong2(ar, ai);
-          }
-        }
-        if (last) {
-          // v_0 of the next exponential: (cos - i sin)(ar + i ai) 2^ea at exponent E
-          const long long nr = (fx_mulhi(m_cs, ar << 4) - fx_mulhi(m_sn, ai << 4)) << L_rot;
-          const long long ni = (fx_mulhi(m_sn, ar << 4) + fx_mulhi(m_cs, ai << 4)) << L_rot;
-          if (k == 0) V[sA][x] = make_longlong2(nr, ni);
-          else dst[x] = make_longlong2(nr, ni);
-          if (last_exp) {
-            const double osc = fx_scale2(1.0, E);
-            p.psi[x] = make_double2(__ll2double_rn(nr) * osc, __ll2double_rn(ni) * osc);
+          S.m_r = k >= 1 ? cheb_coef(rk[k], Eacc, Ey, S.py) : 0;
+          S.E_acc = Eacc;
+          if (last) {
+            // v_0 of the next exponential: (cos - i sin) sum, |component| <= sqrt(2) Bacc
+            const int E0 = fx_exp_for(1.4142135623730951 * Bacc * (1.0 + 1e-12), kFxBits);
+            S.E_out = E0;
+            const Mant mc = fx_mant(R[5]), ms = fx_mant(R[6]);
+            // fx_mulhi(m, sum << 4) << L = value at E0
+            const int sc_ = mc.m ? E0 - mc.e - (Eacc - 4) - 64 : 1 << 20;
+            const int ss_ = ms.m ? E0 - ms.e - (Eacc - 4) - 64 : 1 << 20;
+            int L = 0;
+            if (-sc_ > L) L = -sc_;
+            if (-ss_ > L) L = -ss_;
+            S.L_rot = L;
+            S.m_cs = mc.m ? fx_fold(mc.m, sc_ + L) : 0;
+            S.m_sn = ms.m ? fx_fold(ms.m, ss_ + L) : 0;
+          } else {
+            S.E_out = Ey;
           }
         }
       }
-      if (!(last && last_exp)) {
-        if (!exchange1(true)) return;
+      __syncthreads();
+      long long my = 0, ma = 0;
+      {
+        const longlong2* cur = V[scur];
+        longlong2* dst = V[sdst];
+        const longlong2* prev = k >= 2 ? dst : cur;
+        if (k == 0)
+          cheb_pass<FAMILY, true, true, false>(S, op, p, 0, V[sA], V[sA], V[sA], V[sC], V[sA], wx0, wxe, wstep,
+                                               last_exp, my, ma);
+        else if (first && last)
+          cheb_pass<FAMILY, true, true, true>(S, op, p, k, cur, prev, dst, V[sC], V[sA], wx0, wxe, wstep, last_exp,
+                                              my, ma);
+        else if (first)
+          cheb_pass<FAMILY, true, false, true>(S, op, p, k, cur, prev, dst, V[sC], V[sA], wx0, wxe, wstep, last_exp,
+                                               my, ma);
+        else if (last)
+          cheb_pass<FAMILY, false, true, true>(S, op, p, k, cur, prev, dst, V[sC], V[sA], wx0, wxe, wstep, last_exp,
+                                               my, ma);
+        else
+          cheb_pass<FAMILY, false, false, true>(S, op, p, k, cur, prev, dst, V[sC], V[sA], wx0, wxe, wstep,
+                                                last_exp, my, ma);
       }
+      if (last && last_exp) break;
+      unsigned long long gy = 0, ga = 0;
+      exchange_max(my, ma, true, gy, ga);
+      if (warp == 0 && lane == 0) {
+        const int sw = (k == 0) ? sA : sdst;
+        S.Ev[sw] = S.E_out;
+        S.Av[sw] = (long long)gy;
+        S.accmax = (long long)ga;
+        if (gy >= (1ULL << 60)) {  // fixed-point range exceeded (not expected)
+          atomicCAS(&st->status, 0, (int)CFET_ENAN);
+          S.abort_flag = 1;
+        }
+      }
+      __syncthreads();
+      if (S.abort_flag) return;
     }
     if (tid == 0) t_loop += sm_clock() - t0;
     // the new v_0 is where the last term wrote
