@@ -56,6 +56,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 fl
 DRAM_BYTES_PER_ITERATION = {"fx": (1.194820e9 + 1.627267e9) / 76, "c64": (191.0784e6 + 649.152256e6) / 76,
                             "f64": None}
 
+# ncu DRAM read+write bytes per term of the Chebyshev kernel (2-step capture: 66 terms)
+DRAM_BYTES_PER_TERM_CHEB = (17.072384e6 + 26.479104e6) / 66
+
 # trace slots of the control-warp kernels (cfet_stats.phase_ns)
 PHASES = ("apply_loops", "apply_control", "orth_loops", "orth_control", "reconstruct_loops", "barrier_wait",
           "overlapped_control", "worker_wait")
@@ -240,9 +243,10 @@ def run_gpu(args):
     P.build()
     pr, psi0 = problem()
     dim = 1 << N_SITES
+    cheb = args.expm == "chebyshev"
     prop = P.Propagator(P.XXZChain(N_SITES, pr.J, pr.Delta, pr.h), [P.XField(N_SITES, pr.xfield)], [pr.drive],
                         m_max=M_MAX, max_substeps=64, precision=args.precision, block_size=args.block_size,
-                        grid_size=args.grid_size)
+                        grid_size=args.grid_size, expm=args.expm)
     psi = torch.from_numpy(psi0).cuda()
     t0 = 0.0
     # warm-up steps (untimed)
@@ -273,6 +277,10 @@ def run_gpu(args):
 
     # roofline of the persistent kernel (one launch per 256 steps)
     bytes_, flops = algorithmic_counts(stats, dim, elem_bytes=8.0 if args.precision == "c64" else 16.0)
+    if cheb:
+        # per element and term: read v_k, v_{k-1}, the sum; write v_{k+1}, the sum (80 B); the first
+        # term of an exponential reads v_0 and writes v_1 and the sum (48 B), the last writes v_0 only (64 B)
+        bytes_ = dim * (80.0 * n_app - 48.0 * stats["n_exp"])
     achieved_tflops = flops / (kernel_ms * 1e-3) / 1e12
     achieved_gbs = bytes_ / (kernel_ms * 1e-3) / 1e9
     peaks = {}
@@ -308,7 +316,18 @@ def run_gpu(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample()
 
-    if args.precision in ("fx", "c64"):
+    if cheb:
+        per_t = DRAM_BYTES_PER_TERM_CHEB
+        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved_gbs / hbm_peak,
+                    "traffic": per_t * n_app / math.ceil(args.steps / 256) if per_t is not None else None,
+                    "traffic_note": "per launch: ncu DRAM read+write bytes per Chebyshev term (2-step capture) x "
+                                    "the launch's terms; algorithmic bytes per launch: %.4g"
+                                    % (bytes_ / math.ceil(args.steps / 256)),
+                    "kernel": "k_cheb_fx (persistent Chebyshev recurrence, int64 fixed-point vectors)",
+                    "kernel_ms": kernel_ms, "launches": math.ceil(args.steps / 256),
+                    "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), burst figure"}
+    elif args.precision in ("fx", "c64"):
         per_it = DRAM_BYTES_PER_ITERATION[args.precision]
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved_gbs / hbm_peak,
@@ -336,7 +355,7 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fx": "i64", "c64": "f32", "f64": "f64"}[args.precision],
-            "data": "synthetic", "config": dict(workload_config(), precision=args.precision),
+            "data": "synthetic", "config": dict(workload_config(), precision=args.precision, expm=args.expm),
             "cfet_steps_per_s": args.steps * ws / (ms_max * 1e-3),
             "krylov": {"applies_per_step": n_app / args.steps, "substeps": stats["n_substeps"],
                        "max_k": stats["max_k"], "max_err_est": stats["max_err_est"],
@@ -715,6 +734,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
     ap.add_argument("--precision", default="fx", choices=["fx", "f64", "c64"],
                     help="Krylov vector format: int64 fixed point (default), FP64, or complex64 (mixed precision)")
+    ap.add_argument("--expm", default="krylov", choices=["krylov", "chebyshev"],
+                    help="stage exponentials: Krylov (default) or the Chebyshev expansion (fixed point only)")
     ap.add_argument("--sweep", action="store_true",
                     help="accuracy study: final-state error and throughput per (order, dt) over T")
     ap.add_argument("--sweep-T", type=float, default=20.0)

@@ -140,6 +140,21 @@ def test_cheb_atom_reduced(torch_cuda):
     assert st["n_applies"] == ost["n_applies"]
 
 
+def test_cheb_atom_long_expansion(torch_cuda):
+    # a stiffer grid (l < 20, H0 up to ~2e4): about 500 terms per exponential,
+    # where rounding in the recurrence would show (each vector keeps its own
+    # exponent from its measured maximum)
+    import paper_1102_5071_gb300 as P
+    p = W.grid_atom(Nr=400, L=20)
+    prop = P.Propagator(P.DIA(p.H0_offsets, p.H0_values), [P.DIA(p.V_offsets, p.V_values)], [p.drive],
+                        m_max=64, max_substeps=4000, expm="chebyshev")
+    op = O.Banded((p.H0_offsets, p.H0_values), [(p.V_offsets, p.V_values)])
+    psi0, _ = W.atom_ground_state(p)
+    err, st, ost = _compare(torch_cuda, prop, op, [p.drive], psi0, 500.0, 0.1, 1, 8, 1e-10)
+    assert st["max_k"] >= 400
+    assert err <= PARITY, err
+
+
 def test_cheb_expv_matches_oracle(torch_cuda):
     prop, op, drives = _spin(11, nfields=2)
     c = np.array([0.8, -0.35, 0.2])
