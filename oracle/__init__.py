@@ -24,6 +24,9 @@ chebyshev  Chebyshev evaluation of exp(-i tau H) psi (the alternative technique
            of Sec. 8.1/8.2): Gershgorin intervals combined by Weyl's
            inequality, Jacobi-Anger coefficients, truncation by the Bessel
            tail bound, three-term recurrence; CFET stepping with it.
+timestep   time-step selection (Sec. 6.3): error constant from two step
+           sizes, the step for an accuracy goal, adaptive stepping by the
+           per-step estimate.
 adjoint    fidelity loss 1 - |<phi|psi(T)>|^2 of a CFET propagation with a
            piecewise-constant drive amplitude and its exact gradient (dense
            stage exponentials and Frechet derivatives; small systems).  The
@@ -37,7 +40,9 @@ exactness, order slopes, unitarity).  The gradient of ``adjoint`` is pinned by
 central finite differences of its loss and by its vanishing at an optimum.
 ``chebyshev`` is pinned by dense expm, the closed forms of the Sec. 8.2
 harmonic-oscillator example and of the Jacobi-Anger series, and dense
-Gershgorin intervals.
+Gershgorin intervals.  ``timestep`` is pinned by the driven two-level system's
+exact propagator (predicted against true errors, goals met) and by the
+time invariance of its local constant.
 """
 
-__all__ = ["schemes", "operators", "krylov", "cfet", "chebyshev", "adjoint"]
+__all__ = ["schemes", "operators", "krylov", "cfet", "chebyshev", "timestep", "adjoint"]
