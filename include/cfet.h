@@ -330,6 +330,53 @@ cfet_status cfet_expv_chain_static(int32_t nsites, double J, double Delta, const
                                    void* stream, cfet_stats* stats);
 
 /* ------------------------------------------------------------------------ */
+/* Time-step selection (Sec. 6.6)                                            */
+/* ------------------------------------------------------------------------ */
+/* The error model of an Nth-order CFET is eps = c T dt^N.  These calls
+ * estimate c from two propagations and pick dt for an accuracy goal; each
+ * propagation is a cfet_propagate_ex call of ctx (its precision and stage
+ * exponential method).  order / scheme as in cfet_propagate_ex (N is the
+ * scheme's order).  All three synchronise `stream`.  Device memory of
+ * 2 x dim x 16 bytes is allocated on first use and kept by ctx.            */
+
+/* c from two runs of psi0 (device, unchanged) over [t0, t0 + T]: n1 steps of
+ * dt1 = T / n1 and n2 = round(n1 ratio^(1/N)) (at least n1 + 1) steps of
+ * dt2 = T / n2, c = ||x1(T) - x2(T)||_2 / (T |dt1^N - dt2^N|) (the two grids
+ * meet at the end of the interval; the paper suggests ratio 2 ... 3).
+ * Outputs: c; diff (the norm; may be NULL); dt2 (may be NULL).  Errors:
+ * CFET_EINVAL (T <= 0, n1 < 1, ratio <= 1, invalid order), the errors of
+ * cfet_propagate_ex.                                                       */
+cfet_status cfet_error_constant(cfet_ctx* ctx, const void* psi0, double t0, double T, int64_t n1, int32_t order,
+                                int32_t scheme, double krylov_tol, double ratio, void* stream, double* c,
+                                double* diff, double* dt2);
+
+/* Step for the goal `target` over a run of length T: c from
+ * cfet_error_constant over [t0, t0 + T_probe] with n_probe steps, then
+ * dt = (target / (c T))^(1/N) shortened to T / ceil(T / dt).  Outputs dt,
+ * nsteps (= T / dt), c (may be NULL); c = 0 gives dt = T.                  */
+cfet_status cfet_select_dt(cfet_ctx* ctx, const void* psi0, double t0, double T, double target, double T_probe,
+                           int64_t n_probe, int32_t order, int32_t scheme, double krylov_tol, double ratio,
+                           void* stream, double* dt, int64_t* nsteps, double* c);
+
+/* Adaptive propagation of psi (device, in place) over [t0, t0 + T]: from the
+ * state at t with trial step h, one step of h and two of h/2; the local
+ * constant c = ||x_h - x_{h/2}|| / (h (h^N - (h/2)^N)); the step is accepted
+ * (psi <- the two-half-step result) when c T (h/2)^N <= target or h <= h_min;
+ * the next trial step is min(2h, 1.8 (target / (c T))^(1/N)) clipped to
+ * [h_min, h_max] and to the remaining time.  forced_h: NULL, or n_forced
+ * accepted steps to replay (two steps of h/2 each, no estimate).  h_log:
+ * NULL or h_cap doubles receiving the accepted steps; n_steps, n_trials (may
+ * be NULL): accepted and tried steps; stats: summed over every propagation
+ * (may be NULL).  Errors: CFET_EINVAL (T <= 0, target <= 0, not
+ * 0 < h_min <= h0 <= h_max), CFET_EKRYLOV (more than max_steps accepted
+ * steps), the errors of cfet_propagate_ex.                                 */
+cfet_status cfet_propagate_adaptive(cfet_ctx* ctx, void* psi, double t0, double T, int32_t order, int32_t scheme,
+                                    double krylov_tol, double target, double h0, double h_min, double h_max,
+                                    int64_t max_steps, const double* forced_h, int64_t n_forced, double* h_log,
+                                    int64_t h_cap, int64_t* n_steps, int64_t* n_trials, void* stream,
+                                    cfet_stats* stats);
+
+/* ------------------------------------------------------------------------ */
 /* Batched propagation of many driven XXZ chains                            */
 /* ------------------------------------------------------------------------ */
 /* Many independent instances of uneven Hilbert dimension, each a CFET

@@ -24,7 +24,7 @@ chebyshev  Chebyshev evaluation of exp(-i tau H) psi (the alternative technique
            of Sec. 8.1/8.2): Gershgorin intervals combined by Weyl's
            inequality, Jacobi-Anger coefficients, truncation by the Bessel
            tail bound, three-term recurrence; CFET stepping with it.
-timestep   time-step selection (Sec. 6.3): error constant from two step
+timestep   time-step selection (Sec. 6.6): error constant from two step
            sizes, the step for an accuracy goal, adaptive stepping by the
            per-step estimate.
 adjoint    fidelity loss 1 - |<phi|psi(T)>|^2 of a CFET propagation with a

@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE (oracle): see ``oracle/__init__.py``.
 
-Sec. 6.3 (time-step selection) uses the error model of an Nth-order CFET,
+Sec. 6.6 (time-step selection) uses the error model of an Nth-order CFET,
 epsilon = c T dt^N, and estimates the constant c from two propagations over
 the same interval with steps dt_1 and dt_2:
     max_t ||x_1(t) - x_2(t)|| = c T |dt_1^N - dt_2^N|,

@@ -294,6 +294,52 @@ class Propagator:
         stats = {f: getattr(gs, f) for f, _ in gs._fields_}
         return loss.value, g, stats
 
+    # -------------------------------------------------- time-step selection (Sec. 6.6)
+    @staticmethod
+    def _sid(scheme):
+        return 0 if scheme is None else (SCHEME_IDS[scheme] if isinstance(scheme, str) else int(scheme))
+
+    def error_constant(self, psi0, t0, T, n1, order=4, tol=1e-10, scheme=None, ratio=2.0, stream=None):
+        """Error constant c of eps = c T dt^N from runs with n1 and
+        round(n1 ratio^(1/N)) steps over [t0, t0 + T]; returns (c, diff, dt2)."""
+        _check_vec(psi0, self.dim, "psi0")
+        c, d, h2 = C.c_double(), C.c_double(), C.c_double()
+        self._raise(self._lib.cfet_error_constant(self._ctx, C.c_void_p(psi0.data_ptr()), float(t0), float(T), int(n1),
+                                                  int(order), self._sid(scheme), float(tol), float(ratio),
+                                                  _stream_handle(stream), C.byref(c), C.byref(d), C.byref(h2)))
+        return c.value, d.value, h2.value
+
+    def select_dt(self, psi0, t0, T, target, T_probe, n_probe, order=4, tol=1e-10, scheme=None, ratio=2.0,
+                  stream=None):
+        """(dt, nsteps, c) for the accuracy goal `target` over a run of length T."""
+        _check_vec(psi0, self.dim, "psi0")
+        dt, n, c = C.c_double(), C.c_int64(), C.c_double()
+        self._raise(self._lib.cfet_select_dt(self._ctx, C.c_void_p(psi0.data_ptr()), float(t0), float(T),
+                                             float(target), float(T_probe), int(n_probe), int(order),
+                                             self._sid(scheme), float(tol), float(ratio), _stream_handle(stream),
+                                             C.byref(dt), C.byref(n), C.byref(c)))
+        return dt.value, n.value, c.value
+
+    def propagate_adaptive(self, psi, t0, T, target, h0, h_min, h_max, order=4, tol=1e-10, scheme=None,
+                           max_steps=100000, forced_h=None, stream=None):
+        """Adaptive CFET stepping of psi (in place) over [t0, t0 + T] for the
+        goal `target` (cfet_propagate_adaptive);
+        forced_h replays accepted steps.  Returns (accepted steps, trials, stats)."""
+        _check_vec(psi, self.dim, "psi")
+        cap = int(max_steps) if forced_h is None else len(forced_h)
+        hlog = np.zeros(max(1, cap))
+        fh = None if forced_h is None else np.ascontiguousarray(forced_h, dtype=np.float64)
+        ns, nt = C.c_int64(), C.c_int64()
+        st = _capi.cfet_stats()
+        self._raise(self._lib.cfet_propagate_adaptive(
+            self._ctx, C.c_void_p(psi.data_ptr()), float(t0), float(T), int(order), self._sid(scheme), float(tol),
+            float(target), float(h0), float(h_min), float(h_max), int(max_steps),
+            fh.ctypes.data_as(_capi.c_double_p) if fh is not None else None, 0 if fh is None else fh.size,
+            hlog.ctypes.data_as(_capi.c_double_p), hlog.size, C.byref(ns), C.byref(nt), _stream_handle(stream),
+            C.byref(st)))
+        hs = list(fh) if fh is not None else hlog[: ns.value].tolist()
+        return hs, nt.value, st.as_dict()
+
     def sync(self, stream=None):
         stats = _capi.cfet_stats()
         self._raise(self._lib.cfet_sync(self._ctx, _stream_handle(stream), C.byref(stats)))

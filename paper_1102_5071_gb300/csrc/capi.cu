@@ -84,6 +84,9 @@ struct cfet_ctx {
   double* d_adj_acc = nullptr;     // gradient accumulators [2 nseg] then out [4]
   int adj_nseg_cap = 0;
   int adj_grid = 0;
+  // time-step selection: two trial states and the difference-norm partials
+  double2* d_ts = nullptr;
+  double* d_ts_part = nullptr;
   // graph driver
   struct GraphKey {  // everything the captured sequence depends on
     const void* psi = nullptr;
@@ -160,6 +163,7 @@ void free_ctx(cfet_ctx* c) {
   cudaFree(c->d_dz32); cudaFree(c->d_val32); cudaFree(c->d_qbasis32);
   cudaFree(c->d_adj_ckpt); cudaFree(c->d_adj_vec); cudaFree(c->d_adj_part); cudaFree(c->d_adj_tab);
   cudaFree(c->d_adj_seg); cudaFree(c->d_adj_acc);
+  cudaFree(c->d_ts); cudaFree(c->d_ts_part);
   if (c->h_st) cudaFreeHost(c->h_st);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   delete c;
@@ -1267,6 +1271,190 @@ cfet_status cfet_fidelity_grad(cfet_ctx* ctx, const void* psi0, const void* phi,
     cudaEventElapsedTime(&gstats->forward_ms, e0, e1);
     cudaEventElapsedTime(&gstats->backward_ms, e1, e2);
   }
+  return CFET_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ time-step selection (Sec. 6.6)
+namespace {
+
+// CFET order of (order, scheme) as cfet_propagate_ex resolves them; 0 if invalid.
+int resolve_order(int32_t order, int32_t scheme) {
+  int id = scheme;
+  if (id == CFET_SCHEME_DEFAULT) id = default_scheme_for_order(order);
+  SchemeData sd;
+  if (!id || !build_scheme(id, &sd)) return 0;
+  if (scheme != CFET_SCHEME_DEFAULT && order != 0 && order != sd.order) return 0;
+  return sd.order;
+}
+
+cfet_status ensure_ts(cfet_ctx* ctx) {
+  if (!ctx->d_ts) CK(cudaMalloc(&ctx->d_ts, 2 * (size_t)ctx->dim * sizeof(double2)), "cudaMalloc(trial states)");
+  if (!ctx->d_ts_part) CK(cudaMalloc(&ctx->d_ts_part, kDiffBlocks * sizeof(double)), "cudaMalloc(partials)");
+  return CFET_OK;
+}
+
+// ||a - b||_2 (synchronises the stream)
+cfet_status diff_norm(cfet_ctx* ctx, const double2* a, const double2* b, cudaStream_t s, double* out) {
+  int e = launch_diff_norm2(a, b, ctx->dim, ctx->d_ts_part, kDiffBlocks, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, (cudaError_t)e, "difference norm kernel");
+  double part[kDiffBlocks];
+  CK(cudaMemcpyAsync(part, ctx->d_ts_part, sizeof(part), cudaMemcpyDeviceToHost, s), "partials read-back");
+  CK(cudaStreamSynchronize(s), "stream synchronize");
+  double sum = 0.0;
+  for (int i = 0; i < kDiffBlocks; ++i) sum += part[i];
+  *out = std::sqrt(sum);
+  return CFET_OK;
+}
+
+void add_stats(cfet_stats* acc, const cfet_stats& s) {
+  acc->n_exp += s.n_exp;
+  acc->n_substeps += s.n_substeps;
+  acc->n_applies += s.n_applies;
+  if (s.max_k > acc->max_k) acc->max_k = s.max_k;
+  if (s.max_err_est > acc->max_err_est) acc->max_err_est = s.max_err_est;
+}
+
+// one or more CFET steps of x (device) from t with step h, stats accumulated
+cfet_status run_steps(cfet_ctx* ctx, double2* x, double t, double h, int64_t n, int32_t order, int32_t scheme,
+                      double tol, void* stream, cfet_stats* acc) {
+  cfet_stats st;
+  cfet_status s = cfet_propagate_ex(ctx, x, t, h, n, order, scheme, tol, stream, nullptr, nullptr, &st);
+  if (s == CFET_OK) add_stats(acc, st);
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+cfet_status cfet_error_constant(cfet_ctx* ctx, const void* psi0, double t0, double T, int64_t n1, int32_t order,
+                                int32_t scheme, double krylov_tol, double ratio, void* stream, double* c,
+                                double* diff, double* dt2) {
+  if (!ctx) return CFET_EINVAL;
+  cfet_status s = check_psi(ctx, psi0);
+  if (s != CFET_OK) return s;
+  const int N = resolve_order(order, scheme);
+  if (!N) return fail(ctx, CFET_EINVAL, "order / scheme invalid");
+  if (!is_finite_d(t0) || !is_finite_d(T) || !(T > 0.0)) return fail(ctx, CFET_EINVAL, "T must be finite and > 0");
+  if (n1 < 1) return fail(ctx, CFET_EINVAL, "n1 must be >= 1");
+  if (!is_finite_d(ratio) || !(ratio > 1.0)) return fail(ctx, CFET_EINVAL, "ratio must be > 1");
+  if (!c) return fail(ctx, CFET_EINVAL, "c is NULL");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if ((s = ensure_ts(ctx)) != CFET_OK) return s;
+  int64_t n2 = (int64_t)std::llround((double)n1 * std::pow(ratio, 1.0 / N));
+  if (n2 <= n1) n2 = n1 + 1;
+  const double h1 = T / (double)n1, h2 = T / (double)n2;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)ctx->dim * sizeof(double2);
+  double2* x1 = ctx->d_ts;
+  double2* x2 = ctx->d_ts + ctx->dim;
+  CK(cudaMemcpyAsync(x1, psi0, bytes, cudaMemcpyDeviceToDevice, st), "copy psi0");
+  CK(cudaMemcpyAsync(x2, psi0, bytes, cudaMemcpyDeviceToDevice, st), "copy psi0");
+  cfet_stats acc{};
+  if ((s = run_steps(ctx, x1, t0, h1, n1, order, scheme, krylov_tol, stream, &acc)) != CFET_OK) return s;
+  if ((s = run_steps(ctx, x2, t0, h2, n2, order, scheme, krylov_tol, stream, &acc)) != CFET_OK) return s;
+  double e = 0.0;
+  if ((s = diff_norm(ctx, x1, x2, st, &e)) != CFET_OK) return s;
+  *c = e / (T * std::fabs(std::pow(h1, N) - std::pow(h2, N)));
+  if (diff) *diff = e;
+  if (dt2) *dt2 = h2;
+  return CFET_OK;
+}
+
+cfet_status cfet_select_dt(cfet_ctx* ctx, const void* psi0, double t0, double T, double target, double T_probe,
+                           int64_t n_probe, int32_t order, int32_t scheme, double krylov_tol, double ratio,
+                           void* stream, double* dt, int64_t* nsteps, double* c) {
+  if (!ctx) return CFET_EINVAL;
+  if (!is_finite_d(T) || !(T > 0.0) || !is_finite_d(target) || !(target > 0.0))
+    return fail(ctx, CFET_EINVAL, "T and target must be finite and > 0");
+  if (!dt || !nsteps) return fail(ctx, CFET_EINVAL, "dt / nsteps is NULL");
+  double cc = 0.0;
+  cfet_status s = cfet_error_constant(ctx, psi0, t0, T_probe, n_probe, order, scheme, krylov_tol, ratio, stream, &cc,
+                                      nullptr, nullptr);
+  if (s != CFET_OK) return s;
+  const int N = resolve_order(order, scheme);
+  if (c) *c = cc;
+  if (!(cc > 0.0)) {
+    *dt = T;
+    *nsteps = 1;
+    return CFET_OK;
+  }
+  const double h = std::pow(target / (cc * T), 1.0 / N);
+  const double n = std::ceil(T / h);
+  if (!(n <= 9.0e15)) return fail(ctx, CFET_EINVAL, "selected step too small");
+  *nsteps = (int64_t)n;
+  *dt = T / n;
+  return CFET_OK;
+}
+
+cfet_status cfet_propagate_adaptive(cfet_ctx* ctx, void* psi, double t0, double T, int32_t order, int32_t scheme,
+                                    double krylov_tol, double target, double h0, double h_min, double h_max,
+                                    int64_t max_steps, const double* forced_h, int64_t n_forced, double* h_log,
+                                    int64_t h_cap, int64_t* n_steps, int64_t* n_trials, void* stream,
+                                    cfet_stats* stats) {
+  if (!ctx) return CFET_EINVAL;
+  cfet_status s = check_psi(ctx, psi);
+  if (s != CFET_OK) return s;
+  const int N = resolve_order(order, scheme);
+  if (!N) return fail(ctx, CFET_EINVAL, "order / scheme invalid");
+  if (!is_finite_d(t0) || !is_finite_d(T) || !(T > 0.0)) return fail(ctx, CFET_EINVAL, "T must be finite and > 0");
+  cfet_stats acc{};
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  double2* x = (double2*)psi;
+  if (forced_h) {
+    if (n_forced < 0) return fail(ctx, CFET_EINVAL, "n_forced < 0");
+    for (int64_t i = 0; i < n_forced; ++i)
+      if (!is_finite_d(forced_h[i]) || !(forced_h[i] > 0.0)) return fail(ctx, CFET_EINVAL, "forced step not > 0");
+    double t = t0;
+    for (int64_t i = 0; i < n_forced; ++i) {
+      if ((s = run_steps(ctx, x, t, forced_h[i] / 2.0, 2, order, scheme, krylov_tol, stream, &acc)) != CFET_OK)
+        return s;
+      t += forced_h[i];
+    }
+    if (n_steps) *n_steps = n_forced;
+    if (n_trials) *n_trials = 0;
+    if (stats) *stats = acc;
+    return CFET_OK;
+  }
+  if (!is_finite_d(target) || !(target > 0.0)) return fail(ctx, CFET_EINVAL, "target must be > 0");
+  if (!(h_min > 0.0) || !(h0 >= h_min) || !(h_max >= h0) || !is_finite_d(h_max))
+    return fail(ctx, CFET_EINVAL, "steps must satisfy 0 < h_min <= h0 <= h_max < inf");
+  if (max_steps < 1) return fail(ctx, CFET_EINVAL, "max_steps must be >= 1");
+  if ((s = ensure_ts(ctx)) != CFET_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)ctx->dim * sizeof(double2);
+  double2* x1 = ctx->d_ts;
+  double2* x2 = ctx->d_ts + ctx->dim;
+  const double t_end = t0 + T;
+  double t = t0, h = h0;
+  int64_t ns = 0, nt = 0;
+  while (t_end - t > 1e-12 * std::fmax(1.0, std::fabs(t_end))) {
+    if (ns >= max_steps) return fail(ctx, CFET_EKRYLOV, "adaptive stepping: more than max_steps steps");
+    const double rem = t_end - t;
+    h = std::fmin(h, rem);
+    ++nt;
+    CK(cudaMemcpyAsync(x1, x, bytes, cudaMemcpyDeviceToDevice, st), "copy state");
+    CK(cudaMemcpyAsync(x2, x, bytes, cudaMemcpyDeviceToDevice, st), "copy state");
+    if ((s = run_steps(ctx, x1, t, h, 1, order, scheme, krylov_tol, stream, &acc)) != CFET_OK) return s;
+    if ((s = run_steps(ctx, x2, t, h / 2.0, 2, order, scheme, krylov_tol, stream, &acc)) != CFET_OK) return s;
+    double e = 0.0;
+    if ((s = diff_norm(ctx, x1, x2, st, &e)) != CFET_OK) return s;
+    const double c = e / (h * (std::pow(h, N) - std::pow(h / 2.0, N)));
+    if (c * T * std::pow(h / 2.0, N) <= target || h <= h_min) {
+      CK(cudaMemcpyAsync(x, x2, bytes, cudaMemcpyDeviceToDevice, st), "accept state");
+      t = h < rem ? t + h : t_end;
+      if (h_log && ns < h_cap) h_log[ns] = h;
+      ++ns;
+    }
+    const double h_new = c <= 0.0 ? 2.0 * h : std::fmin(2.0 * h, 1.8 * std::pow(target / (c * T), 1.0 / N));
+    h = std::fmin(std::fmax(h_new, h_min), h_max);
+  }
+  CK(cudaStreamSynchronize(st), "stream synchronize");
+  if (n_steps) *n_steps = ns;
+  if (n_trials) *n_trials = nt;
+  if (stats) *stats = acc;
   return CFET_OK;
 }
 

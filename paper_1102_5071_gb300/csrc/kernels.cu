@@ -513,4 +513,30 @@ int launch_wait_selftest(int which, unsigned long long* rec, unsigned* bar, int*
   k_wait_selftest<<<2, 32>>>(which, rec, bar, status, timeout_ns);
   return (int)cudaGetLastError();
 }
+// ||a - b||_2^2 partial sums: block j writes the sum over its grid-stride
+// elements (tree in shared memory, fixed order) to part[j]; the host adds the
+// partials in block order.  Used by the time-step selection (Sec. 6.6).
+__global__ void __launch_bounds__(256) k_diff_norm2(const double2* __restrict__ a, const double2* __restrict__ b,
+                                                    int n, double* __restrict__ part) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double2 x = a[i], y = b[i];
+    const double dr = x.x - y.x, di = x.y - y.y;
+    s = fma(dr, dr, fma(di, di, s));
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+int launch_diff_norm2(const double2* a, const double2* b, int n, double* part, int nblk, void* stream) {
+  k_diff_norm2<<<nblk, 256, 0, (cudaStream_t)stream>>>(a, b, n, part);
+  return (int)cudaGetLastError();
+}
+
 }  // namespace cfet

@@ -1,4 +1,4 @@
-"""Pins for oracle/timestep.py (Sec. 6.3 time-step selection) against the
+"""Pins for oracle/timestep.py (Sec. 6.6 time-step selection) against the
 driven two-level system with its exact propagator (Eq. (TwoLevelU)) and a
 fine-step reference for a chirped drive."""
 
