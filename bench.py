@@ -724,6 +724,70 @@ def run_study_expm(args):
     return 0
 
 
+def run_study_timestep(args):
+    """Time-step selection (Sec. 6.6) on the N=20 chain over T = --sweep-T,
+    order 4 (CF4:2), Krylov tol 1e-12: (a) cfet_select_dt with c probed over
+    T/10 for goals 1e-6, 1e-8, 1e-10, then the run with the selected step,
+    its error against a reference (CF8:11, dt T/1600, tol 1e-13) and the cost
+    including the probe; (b) a chirped drive 0.8 cos(0.5 t + 0.15 t^2):
+    cfet_propagate_adaptive for goal 1e-8 against a uniform grid with as many
+    steps as the adaptive run took (trial steps included)."""
+    import torch
+    import paper_1102_5071_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    pr, psi0 = problem()
+    T = args.sweep_T
+
+    def chain(drive):
+        return P.Propagator(P.XXZChain(N_SITES, pr.J, pr.Delta, pr.h), [P.XField(N_SITES, pr.xfield)], [drive],
+                            m_max=M_MAX, max_substeps=64)
+
+    def reference(prop):
+        ref = torch.from_numpy(psi0).cuda()
+        prop.propagate(ref, 0.0, T / 1600, 1600, order=8, tol=1e-13)
+        return ref
+
+    prop = chain(pr.drive)
+    ref = reference(prop)
+    for target in (1e-6, 1e-8, 1e-10):
+        x = torch.from_numpy(psi0).cuda()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        dt, n, c = prop.select_dt(x, 0.0, T, target, T / 10, 8, order=4, tol=1e-12)
+        tp = time.perf_counter() - t
+        st = prop.propagate(x, 0.0, dt, n, order=4, tol=1e-12)
+        torch.cuda.synchronize()
+        tt = time.perf_counter() - t
+        print(json.dumps({"study": "timestep", "workload": "driven XXZ chain N=20 CF4:2 T=%g" % T, "goal": target,
+                          "c": c, "dt": dt, "steps": n, "final_state_error": torch.linalg.vector_norm(x - ref).item(),
+                          "probe_s": tp, "total_s": tt, "H_applies": st["n_applies"]}))
+    prop.close()
+
+    def chirp(t):
+        return 0.8 * math.cos(0.5 * t + 0.15 * t * t)
+
+    prop = chain(chirp)
+    ref = reference(prop)
+    x = torch.from_numpy(psi0).cuda()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    hs, trials, st = prop.propagate_adaptive(x, 0.0, T, 1e-8, 0.05, 1e-4, 1.0, order=4, tol=1e-12)
+    torch.cuda.synchronize()
+    ta = time.perf_counter() - t
+    err_a = torch.linalg.vector_norm(x - ref).item()
+    n_uni = 3 * trials        # every trial costs one step of h and two of h/2
+    y = torch.from_numpy(psi0).cuda()
+    prop.propagate(y, 0.0, T / n_uni, n_uni, order=4, tol=1e-12)
+    err_u = torch.linalg.vector_norm(y - ref).item()
+    print(json.dumps({"study": "timestep", "workload": "driven XXZ chain N=20, chirped drive, CF4:2 T=%g" % T,
+                      "goal": 1e-8, "accepted_steps": len(hs), "trial_steps": trials,
+                      "h_first_last": [hs[0], hs[len(hs) // 2], hs[-1]], "adaptive_error": err_a, "adaptive_s": ta,
+                      "uniform_steps_same_cost": n_uni, "uniform_error": err_u}))
+    prop.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -739,9 +803,9 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="accuracy study: final-state error and throughput per (order, dt) over T")
     ap.add_argument("--sweep-T", type=float, default=20.0)
-    ap.add_argument("--study", choices=["atom", "sizes", "batch", "adjoint", "expm"],
+    ap.add_argument("--study", choices=["atom", "sizes", "batch", "adjoint", "expm", "timestep"],
                     help="extra measurements: the grid atom, the chain at N = 20..26, the 256-chain batch, "
-                         "the fidelity gradient, Krylov against Chebyshev stage exponentials")
+                         "the fidelity gradient, Krylov against Chebyshev stage exponentials, time-step selection")
     ap.add_argument("--baseline-steps", type=int, default=10,
                     help="batch study: steps of the single-instance baseline per instance")
     ap.add_argument("--grid-size", type=int, default=0,
@@ -765,6 +829,8 @@ def main():
         return run_study_adjoint(args)
     if args.study == "expm":
         return run_study_expm(args)
+    if args.study == "timestep":
+        return run_study_timestep(args)
     return run_gpu(args)
 
 
