@@ -27,6 +27,9 @@ chebyshev  Chebyshev evaluation of exp(-i tau H) psi (the alternative technique
 timestep   time-step selection (Sec. 6.6): error constant from two step
            sizes, the step for an accuracy goal, adaptive stepping by the
            per-step estimate.
+interaction  CFET stepping in the interaction picture of the constant diagonal
+           of H0 (Secs. 9.3, 9.4): stage operators sum_m g_{j,m} e^{i H_d t_m}
+           H_b(t_m) e^{-i H_d t_m} applied by that definition.
 adjoint    fidelity loss 1 - |<phi|psi(T)>|^2 of a CFET propagation with a
            piecewise-constant drive amplitude and its exact gradient (dense
            stage exponentials and Frechet derivatives; small systems).  The
@@ -42,7 +45,10 @@ central finite differences of its loss and by its vanishing at an optimum.
 harmonic-oscillator example and of the Jacobi-Anger series, and dense
 Gershgorin intervals.  ``timestep`` is pinned by the driven two-level system's
 exact propagator (predicted against true errors, goals met) and by the
-time invariance of its local constant.
+time invariance of its local constant.  ``interaction`` is pinned by exactness
+without off-diagonal terms, the resonant two-level system (constant
+interaction-picture Hamiltonian, Eq. (TwoLevelU)), the order slope against
+the Schroedinger picture and the dense stage operator.
 """
 
-__all__ = ["schemes", "operators", "krylov", "cfet", "chebyshev", "timestep", "adjoint"]
+__all__ = ["schemes", "operators", "krylov", "cfet", "chebyshev", "timestep", "interaction", "adjoint"]
