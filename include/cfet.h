@@ -156,6 +156,7 @@ typedef struct cfet_options {
   double barrier_timeout_s;  /* device barrier wait limit (default 2.0 s)     */
   int32_t precision;         /* CFET_PREC_* (default CFET_PREC_FX)            */
   int32_t expm;              /* CFET_EXPM_* (default CFET_EXPM_KRYLOV)        */
+  int32_t picture;           /* CFET_PICTURE_* (default SCHROEDINGER)         */
 } cfet_options;
 
 /* Number format of the Krylov vectors on the device.  All keep alpha, beta,
@@ -195,6 +196,25 @@ enum { CFET_PREC_DEFAULT = 0, CFET_PREC_F64 = 1, CFET_PREC_FX = 2, CFET_PREC_C64
 enum {
   CFET_EXPM_KRYLOV = 0,
   CFET_EXPM_CHEBYSHEV = 1
+};
+
+/* Picture of the CFET stepping in cfet_propagate / cfet_propagate_ex.
+ *  SCHROEDINGER : the stage operators of H(t) itself.
+ *  INTERACTION  : the interaction picture of the diagonal H_d of H0
+ *                 (Secs. 9.3, 9.4): psi^I(t) = e^{i H_d t} psi(t) is
+ *                 propagated with H^I(t) = e^{i H_d t} (H(t) - H_d) e^{-i H_d t},
+ *                 whose stage operators sum_m g_{j,m} H^I(t + x_m dt) have the
+ *                 off-diagonal pattern of H with entries multiplied by phases
+ *                 e^{i (d(x) - d(y)) t_m}; psi enters and leaves in the
+ *                 Schroedinger picture (time measured from t = 0).  Removes the
+ *                 diagonal from the Krylov matrices at the price of faster time
+ *                 dependence.  XXZ chains only, CFET_PREC_F64 and
+ *                 CFET_EXPM_KRYLOV only (else CFET_EINVAL at create);
+ *                 cfet_apply and cfet_expv of such a context still act in the
+ *                 Schroedinger picture; cfet_fidelity_grad is refused.      */
+enum {
+  CFET_PICTURE_SCHROEDINGER = 0,
+  CFET_PICTURE_INTERACTION = 1
 };
 
 typedef struct cfet_stats {

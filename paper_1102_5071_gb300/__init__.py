@@ -128,7 +128,8 @@ class Propagator:
     """CFET propagator for H(t) = H0 + sum_k f_k(t) V_k on the current CUDA device."""
 
     def __init__(self, H0, V=(), drives=(), *, m_max=16, m_min=2, max_substeps=64, block_size=0,
-                 grid_size=0, steps_per_launch=256, barrier_timeout_s=2.0, precision="default", expm="krylov"):
+                 grid_size=0, steps_per_launch=256, barrier_timeout_s=2.0, precision="default", expm="krylov",
+                 picture="schroedinger"):
         lib = _capi.load()
         V = list(V)
         drives = list(drives)
@@ -146,6 +147,7 @@ class Propagator:
         opt.barrier_timeout_s = barrier_timeout_s
         opt.precision = _capi.PRECISIONS[precision]
         opt.expm = _capi.EXPM[expm]
+        opt.picture = _capi.PICTURES[picture]
         ctx = C.c_void_p()
         st = lib.cfet_create(C.byref(ctx), C.byref(h0), len(V), varr, fns, None, C.byref(opt))
         if st != 0:

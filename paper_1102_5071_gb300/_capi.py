@@ -29,13 +29,16 @@ class cfet_op(C.Structure):
 class cfet_options(C.Structure):
     _fields_ = [("m_max", C.c_int32), ("m_min", C.c_int32), ("max_substeps", C.c_int32),
                 ("block_size", C.c_int32), ("grid_size", C.c_int32), ("steps_per_launch", C.c_int32),
-                ("barrier_timeout_s", C.c_double), ("precision", C.c_int32), ("expm", C.c_int32)]
+                ("barrier_timeout_s", C.c_double), ("precision", C.c_int32), ("expm", C.c_int32),
+                ("picture", C.c_int32)]
 
 
 CFET_PREC_DEFAULT, CFET_PREC_F64, CFET_PREC_FX, CFET_PREC_C64 = 0, 1, 2, 3
 PRECISIONS = {"default": CFET_PREC_DEFAULT, "f64": CFET_PREC_F64, "fx": CFET_PREC_FX, "c64": CFET_PREC_C64}
 CFET_EXPM_KRYLOV, CFET_EXPM_CHEBYSHEV = 0, 1
 EXPM = {"krylov": CFET_EXPM_KRYLOV, "chebyshev": CFET_EXPM_CHEBYSHEV}
+CFET_PICTURE_SCHROEDINGER, CFET_PICTURE_INTERACTION = 0, 1
+PICTURES = {"schroedinger": CFET_PICTURE_SCHROEDINGER, "interaction": CFET_PICTURE_INTERACTION}
 
 
 class cfet_stats(C.Structure):

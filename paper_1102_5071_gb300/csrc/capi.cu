@@ -40,6 +40,9 @@ struct cfet_ctx {
   // operators
   OpSpin spin{};
   OpDia dia{};
+  // interaction picture: host copies of the chain (stage weight tables)
+  double ip_J = 0.0, ip_Delta = 0.0;
+  std::vector<double> ip_h, ip_xf;
   // Gershgorin intervals of H0 and of every V_k (Chebyshev stage exponentials)
   double op_lo[1 + kMaxDrives] = {}, op_hi[1 + kMaxDrives] = {};
   double* d_dz_lo = nullptr;
@@ -219,7 +222,10 @@ cfet_status launch_chunk(cfet_ctx* ctx, const PropParams& base, long long e0, lo
   p.nexp = ne;
   p.exp_base = e0;
   int e;
-  if (ctx->opt.expm == CFET_EXPM_CHEBYSHEV)
+  if (p.ip_w) {
+    OpSpinIP op{ctx->spin.N, p.ip_nw, p.ip_w};
+    e = launch_propagate_spin_ip(p, op, ctx->grid, ctx->block, s);
+  } else if (ctx->opt.expm == CFET_EXPM_CHEBYSHEV)
     e = ctx->family == kFamilySpin ? launch_cheb_spin_fx(p, ctx->spin_fx, ctx->grid, ctx->block - 32, s)
                                    : launch_cheb_dia_fx(p, ctx->dia_fx, ctx->grid, ctx->block - 32, s);
   else if (ctx->precision == CFET_PREC_FX)
@@ -245,10 +251,18 @@ cfet_status issue_sequence(cfet_ctx* ctx, const PropParams& base, long long nexp
   CK(cudaMemsetAsync(ctx->d_partials, 0, kPartialWordsPerCta * (size_t)ctx->grid * sizeof(double), s),
      "exchange reset");
   if (timed) CK(cudaEventRecordWithFlags(ctx->ev_k0, s, cudaEventRecordExternal), "timing event");
+  if (base.ip_w) {  // into the interaction picture at t0
+    const int e = launch_phase_diag(base.psi, ctx->spin, ctx->dim, base.ip_times, 0, 1.0, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, (cudaError_t)e, "phase kernel launch");
+  }
   for (long long e0 = 0; e0 < nexp; e0 += chunk) {
     const long long ne = (nexp - e0) < chunk ? (nexp - e0) : chunk;
     cfet_status st = launch_chunk(ctx, base, e0, ne, s);
     if (st != CFET_OK) return st;
+  }
+  if (base.ip_w) {  // back to the Schroedinger picture at t_end
+    const int e = launch_phase_diag(base.psi, ctx->spin, ctx->dim, base.ip_times, 1, -1.0, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, (cudaError_t)e, "phase kernel launch");
   }
   if (timed) CK(cudaEventRecordWithFlags(ctx->ev_k1, s, cudaEventRecordExternal), "timing event");
   CK(cudaMemcpyAsync(ctx->h_st, ctx->d_st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s), "status read-back");
@@ -342,6 +356,59 @@ void set_cheb_params(cfet_ctx* ctx, PropParams& p, long long nexp) {
   p.cheb_coef = p.cheb + (size_t)nexp * kChebRec;
 }
 
+// Interaction-picture stage weights of one CFET step from t (Secs. 9.3, 9.4):
+// for every stage (execution order, exp(Omega_s) first) the table of OpSpinIP,
+//   flip  of site i, spin bit b, n = s_{i-1} + s_{i+1}:
+//         sum_m g_{j,m} b_i(t_m) e^{i 2 s (h_i + J Delta n) t_m},  b_i(t) = sum_k f_k(t) a_{k,i}
+//   hop   of bond (i, i+1), bit b of site i, m = s_{i-1} - s_{i+2}:
+//         sum_m g_{j,m} 2J e^{i 2 s (h_i - h_{i+1} + J Delta m) t_m},
+// s = 1 - 2b; the exponents are d(x) - d(partner) for the diagonal d of H0.
+// fval: drives at the nodes, [m * nV + k].
+void ip_step_weights(const cfet_ctx* ctx, const SchemeData& sd, double t, double dt, const std::vector<double>& fval,
+                     double* out) {
+  const int N = ctx->spin.N, nV = ctx->nV;
+  const double JD = ctx->ip_J * ctx->ip_Delta;
+  const int nw = kIPWeightsPerSite * (2 * N - 1);
+  std::vector<double> tm(sd.M), bs((size_t)sd.M * N, 0.0);
+  for (int m = 0; m < sd.M; ++m) {
+    tm[m] = t + sd.x[m] * dt;
+    for (int i = 0; i < N; ++i)
+      for (int k = 0; k < nV; ++k) bs[(size_t)m * N + i] += fval[(size_t)m * nV + k] * ctx->ip_xf[(size_t)k * N + i];
+  }
+  for (int jj = 0; jj < sd.s; ++jj) {
+    const int j = sd.s - 1 - jj;
+    double* w = out + (size_t)jj * nw * 2;
+    for (int i = 0; i < N; ++i)
+      for (int b = 0; b < 2; ++b)
+        for (int n = -2; n <= 2; ++n) {
+          const double dd = 2.0 * (1 - 2 * b) * (ctx->ip_h[i] + JD * n);
+          double re = 0.0, im = 0.0;
+          for (int m = 0; m < sd.M; ++m) {
+            const double a = sd.g[j][m] * bs[(size_t)m * N + i];
+            re += a * std::cos(dd * tm[m]);
+            im += a * std::sin(dd * tm[m]);
+          }
+          const size_t idx = (size_t)i * kIPWeightsPerSite + b * 5 + (n + 2);
+          w[2 * idx] = re;
+          w[2 * idx + 1] = im;
+        }
+    for (int i = 0; i + 1 < N; ++i)
+      for (int b = 0; b < 2; ++b)
+        for (int mm = -2; mm <= 2; ++mm) {
+          const double dd = 2.0 * (1 - 2 * b) * (ctx->ip_h[i] - ctx->ip_h[i + 1] + JD * mm);
+          double re = 0.0, im = 0.0;
+          for (int m = 0; m < sd.M; ++m) {
+            const double a = sd.g[j][m] * 2.0 * ctx->ip_J;
+            re += a * std::cos(dd * tm[m]);
+            im += a * std::sin(dd * tm[m]);
+          }
+          const size_t idx = (size_t)N * kIPWeightsPerSite + (size_t)i * kIPWeightsPerSite + b * 5 + (mm + 2);
+          w[2 * idx] = re;
+          w[2 * idx + 1] = im;
+        }
+  }
+}
+
 cfet_status finish(cfet_ctx* ctx, cudaStream_t s, cfet_stats* stats) {
   CK(cudaStreamSynchronize(s), "stream synchronize");
   ctx->ev_pending = false;
@@ -421,6 +488,7 @@ void cfet_options_default(cfet_options* opt) {
   opt->barrier_timeout_s = 2.0;
   opt->precision = CFET_PREC_FX;
   opt->expm = CFET_EXPM_KRYLOV;
+  opt->picture = CFET_PICTURE_SCHROEDINGER;
 }
 
 cfet_status cfet_scheme_info(int32_t scheme, int32_t* order, int32_t* s, int32_t* M, double* f, double* x,
@@ -474,6 +542,11 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
     return fail(nullptr, CFET_EINVAL, "expm must be CFET_EXPM_KRYLOV or CFET_EXPM_CHEBYSHEV");
   if (o.expm == CFET_EXPM_CHEBYSHEV && o.precision != CFET_PREC_FX)
     return fail(nullptr, CFET_EINVAL, "CFET_EXPM_CHEBYSHEV requires CFET_PREC_FX");
+  if (o.picture != CFET_PICTURE_SCHROEDINGER && o.picture != CFET_PICTURE_INTERACTION)
+    return fail(nullptr, CFET_EINVAL, "picture must be CFET_PICTURE_SCHROEDINGER or CFET_PICTURE_INTERACTION");
+  if (o.picture == CFET_PICTURE_INTERACTION &&
+      (o.precision != CFET_PREC_F64 || o.expm != CFET_EXPM_KRYLOV || H0->kind != CFET_OP_XXZ_CHAIN))
+    return fail(nullptr, CFET_EINVAL, "CFET_PICTURE_INTERACTION requires an XXZ chain, CFET_PREC_F64 and CFET_EXPM_KRYLOV");
   if (o.block_size == 0) o.block_size = (o.precision == CFET_PREC_F64) ? 256 : 384;
   {
     // FP64 kernel: block_size threads (<= 256); fixed-point and mixed-precision
@@ -629,6 +702,10 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
     ctx->spin_c.dz_hi = ctx->d_dz32 + nlo;
     ctx->spin_c.xf = ctx->d_xf;
     spin_h0_interval(N, H0->J, H0->Delta, H0->site_coeff, &ctx->op_lo[0], &ctx->op_hi[0]);
+    ctx->ip_J = H0->J;
+    ctx->ip_Delta = H0->Delta;
+    ctx->ip_h.assign(H0->site_coeff, H0->site_coeff + N);
+    ctx->ip_xf = xf;
     for (int k = 0; k < nV; ++k) xfield_interval(N, V[k].site_coeff, &ctx->op_lo[1 + k], &ctx->op_hi[1 + k]);
   } else {
     std::vector<long long> off;
@@ -724,6 +801,14 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
   if (maxg < 1) {
     free_ctx(ctx);
     return fail(nullptr, CFET_ECUDA, "occupancy query failed for the persistent kernel");
+  }
+  if (o.picture == CFET_PICTURE_INTERACTION) {  // the interaction-picture form of the FP64 kernel
+    const int mi = max_coresident_blocks_ip(ctx->block, kIPWeightsPerSite * (2 * nsites - 1));
+    if (mi < 1) {
+      free_ctx(ctx);
+      return fail(nullptr, CFET_ECUDA, "occupancy query failed for the interaction-picture kernel");
+    }
+    if (mi < maxg) maxg = mi;
   }
   if (o.expm == CFET_EXPM_CHEBYSHEV) {  // the Chebyshev kernel: the same workers, no control warp
     const int mc = max_coresident_blocks_cheb(family, ctx->block - 32);
@@ -880,6 +965,9 @@ cfet_status cfet_propagate_ex(cfet_ctx* ctx, void* psi, double t0, double dt, in
   // the previous call's graph may still read the pinned table
   if (ctx->ev_pending) { cudaEventSynchronize(ctx->ev_done); ctx->ev_pending = false; }
 
+  const bool ip = ctx->opt.picture == CFET_PICTURE_INTERACTION;
+  const int ipnw = ip ? kIPWeightsPerSite * (2 * ctx->spin.N - 1) : 0;
+  std::vector<double> ipw(ip ? (size_t)nexp * ipnw * 2 : 0);
   // ---- stage scalars (host): drives at the Gauss-Legendre nodes of each step
   std::vector<double> fval((size_t)sd.M * (ctx->nV > 0 ? ctx->nV : 1));
   for (long long n = 0; n < nsteps; ++n) {
@@ -890,6 +978,7 @@ cfet_status cfet_propagate_ex(cfet_ctx* ctx, void* psi, double t0, double dt, in
         if (!is_finite_d(v)) return fail(ctx, CFET_EINVAL, "drive returned a non-finite value");
         fval[(size_t)m * ctx->nV + k] = v;
       }
+    if (ip) ip_step_weights(ctx, sd, t, dt, fval, ipw.data() + (size_t)n * sd.s * ipnw * 2);
     for (int jj = 0; jj < sd.s; ++jj) {
       const int j = sd.s - 1 - jj;  // exp(Omega_s) acts first
       double* row = ctx->h_scal + ((size_t)n * sd.s + jj) * ncoef;
@@ -905,6 +994,19 @@ cfet_status cfet_propagate_ex(cfet_ctx* ctx, void* psi, double t0, double dt, in
   }
   size_t table_n = (size_t)nexp * ncoef;
   if (cheb && (s = stage_cheb_table(ctx, nexp, dt, krylov_tol, &table_n)) != CFET_OK) return s;
+  size_t ip_off_t = 0, ip_off_w = 0;
+  if (ip) {  // [rows][pad][t0, t_end][weights], the weights 16-byte aligned
+    ip_off_t = (table_n + 1) & ~size_t(1);
+    ip_off_w = ip_off_t + 2;
+    const size_t total = ip_off_w + ipw.size();
+    std::vector<double> rows(ctx->h_scal, ctx->h_scal + table_n);
+    if ((s = ensure_scal(ctx, total)) != CFET_OK) return s;
+    std::memcpy(ctx->h_scal, rows.data(), rows.size() * sizeof(double));
+    ctx->h_scal[ip_off_t] = t0;
+    ctx->h_scal[ip_off_t + 1] = t0 + (double)nsteps * dt;
+    std::memcpy(ctx->h_scal + ip_off_w, ipw.data(), ipw.size() * sizeof(double));
+    table_n = total;
+  }
   // ---- forced decisions blob (host staging)
   std::vector<int> fblob;
   if (forced) {
@@ -918,6 +1020,11 @@ cfet_status cfet_propagate_ex(cfet_ctx* ctx, void* psi, double t0, double dt, in
   if (forced) CK(cudaMemcpy(ctx->d_dec, fblob.data(), nf * sizeof(int), cudaMemcpyHostToDevice), "decision upload");
   PropParams p = base_params(ctx, (double2*)psi, dt, krylov_tol);
   if (cheb) set_cheb_params(ctx, p, nexp);
+  if (ip) {
+    p.ip_times = ctx->d_scal + ip_off_t;
+    p.ip_w = reinterpret_cast<const double2*>(ctx->d_scal + ip_off_w);
+    p.ip_nw = ipnw;
+  }
   if (forced) {
     p.f_nsub = ctx->d_dec;
     p.f_k = ctx->d_dec + nexp;
@@ -1073,8 +1180,8 @@ cfet_status cfet_fidelity_grad(cfet_ctx* ctx, const void* psi0, const void* phi,
                                int64_t nsteps, int32_t order, double krylov_tol, int32_t nseg, const double* amps,
                                double omega, double phase, int64_t checkpoint_every, void* stream, double* loss,
                                double* grad, cfet_grad_stats* gstats) {
-  if (ctx && ctx->opt.expm != CFET_EXPM_KRYLOV)
-    return fail(ctx, CFET_EINVAL, "fidelity gradient: the context must use CFET_EXPM_KRYLOV");
+  if (ctx && (ctx->opt.expm != CFET_EXPM_KRYLOV || ctx->opt.picture != CFET_PICTURE_SCHROEDINGER))
+    return fail(ctx, CFET_EINVAL, "fidelity gradient: the context must use CFET_EXPM_KRYLOV, Schroedinger picture");
   if (!ctx) return CFET_EINVAL;
   if (ctx->family != kFamilySpin || ctx->nV != 1)
     return fail(ctx, CFET_EINVAL, "fidelity gradient: needs an XXZ chain with exactly one X-field drive");

@@ -56,6 +56,20 @@ struct OpSpin {
   const double* xf;    // [nV * N] per-field per-site X coefficients
 };
 
+// Spin chain in the interaction picture of the diagonal of H0 (Secs. 9.3,
+// 9.4): stage operator entries are the off-diagonal entries of H(t_m) times
+// e^{i (d(x) - d(y)) t_m}, summed over the Gauss-Legendre nodes with g_{j,m}.
+// They depend only on a few neighbouring spins, so each stage comes as a table
+// of complex weights (host-computed): flip of site i, index i*10 + b*5 + n + 2
+// (b = bit i of x, n = s_{i-1} + s_{i+1} over existing neighbours), then hop
+// of bond (i, i+1), index 10 N + i*10 + b*5 + m + 2 (m = s_{i-1} - s_{i+2}).
+constexpr int kIPWeightsPerSite = 10;
+struct OpSpinIP {
+  int N;
+  int nw;              // complex weights per exponential: 10 N + 10 (N - 1)
+  const double2* w;    // [nexp of the call][nw] (global exponential index)
+};
+
 // Banded family: all operators in DIA form, concatenated.
 struct OpDia {
   int ndiag;
@@ -137,6 +151,11 @@ struct PropParams {
   // concatenated expansion coefficients r_k
   const double* cheb;
   const double* cheb_coef;
+  // interaction picture (propagate only): stage weights [nexp][ip_nw] of
+  // OpSpinIP and the times {t0, t_end} of the picture changes; NULL otherwise
+  const double2* ip_w;
+  const double* ip_times;
+  int ip_nw;
 };
 
 // Chebyshev record of one stage exponential (host-computed, see chebyshev.cpp):
@@ -189,6 +208,10 @@ struct AdjParams {
 // (defined in kernels.cu; return a cudaError_t as int)
 int launch_propagate_spin(const PropParams& p, const OpSpin& op, int grid, int block, void* stream);
 int launch_propagate_dia(const PropParams& p, const OpDia& op, int grid, int block, void* stream);
+int launch_propagate_spin_ip(const PropParams& p, const OpSpinIP& op, int grid, int block, void* stream);
+int max_coresident_blocks_ip(int block, int nw);
+// psi[x] *= exp(i sign d(x) t[which]) with d the diagonal of the XXZ chain H0
+int launch_phase_diag(double2* psi, const OpSpin& op, int dim, const double* t, int which, double sign, void* stream);
 int launch_apply_spin(const OpSpin& op, int dim, const double* c, int nV, const double2* vin, double2* vout,
                       void* stream);
 int launch_apply_dia(const OpDia& op, int dim, const double* c, int nV, const double2* vin, double2* vout,
@@ -209,6 +232,6 @@ int max_coresident_blocks_adjoint(int block);
 int max_coresident_blocks(int family, int block);  // per device, for the persistent kernel
 size_t propagate_smem_bytes(int block);
 
-enum Family { kFamilySpin = 1, kFamilyDia = 2 };
+enum Family { kFamilySpin = 1, kFamilyDia = 2, kFamilySpinIP = 3 };
 
 }  // namespace cfet

@@ -46,6 +46,42 @@ __device__ __forceinline__ double2 apply_dia_at(const double2* q, int r, int dim
   return acc;
 }
 
+// Interaction-picture spin apply at index x (OpSpinIP): sum over the single
+// flips and the antiparallel-bond hops of x of the stage weight of the local
+// spin configuration times the partner's amplitude (complex products).
+__device__ __forceinline__ double2 apply_spin_ip_at(const double2* q, int x, int N, const double2* W) {
+  double ar = 0.0, ai = 0.0;
+  const unsigned ux = (unsigned)x;
+  for (int i = 0; i < N; ++i) {
+    const int b = (ux >> i) & 1u;
+    int n = 0;  // s_{i-1} + s_{i+1} over existing neighbours, s = 1 - 2 bit
+    if (i > 0) n += 1 - 2 * (int)((ux >> (i - 1)) & 1u);
+    if (i < N - 1) n += 1 - 2 * (int)((ux >> (i + 1)) & 1u);
+    const double2 w = W[i * kIPWeightsPerSite + b * 5 + n + 2];
+    const double2 v = q[x ^ (1 << i)];
+    ar = fma(w.x, v.x, fma(-w.y, v.y, ar));
+    ai = fma(w.x, v.y, fma(w.y, v.x, ai));
+  }
+  unsigned anti = (ux ^ (ux >> 1)) & ((1u << (N - 1)) - 1u);
+  while (anti) {
+    const int i = __ffs(anti) - 1;
+    anti &= anti - 1u;
+    const int b = (ux >> i) & 1u;
+    int m = 0;  // s_{i-1} - s_{i+2} over existing sites
+    if (i > 0) m += 1 - 2 * (int)((ux >> (i - 1)) & 1u);
+    if (i + 2 < N) m -= 1 - 2 * (int)((ux >> (i + 2)) & 1u);
+    const double2 w = W[N * kIPWeightsPerSite + i * kIPWeightsPerSite + b * 5 + m + 2];
+    const double2 v = q[x ^ (3 << i)];
+    ar = fma(w.x, v.x, fma(-w.y, v.y, ar));
+    ai = fma(w.x, v.y, fma(w.y, v.x, ai));
+  }
+  return make_double2(ar, ai);
+}
+
+// Offset of the interaction-picture weight table behind SmemLayout (16-byte aligned).
+template <class L>
+__host__ __device__ constexpr size_t ip_table_offset() { return (sizeof(L) + 15) & ~size_t(15); }
+
 // ------------------------------------------------------------------ shared layout
 struct SmemLayout {
   double red[32];
@@ -124,6 +160,12 @@ __global__ void __launch_bounds__(256) k_propagate(PropParams p, Op op) {
       }
       __syncthreads();
     }
+    if constexpr (FAMILY == kFamilySpinIP) {  // this exponential's stage weights
+      double2* Wt = reinterpret_cast<double2*>(smem_raw + ip_table_offset<SmemLayout>());
+      const double2* src = op.w + (size_t)(p.exp_base + e) * op.nw;
+      for (int i = tid; i < op.nw; i += blockDim.x) Wt[i] = src[i];
+      __syncthreads();
+    }
     const long long eg = p.exp_base + e;
     const int nforced = forced ? p.f_nsub[eg] : 0;
     double remaining = p.tau;
@@ -173,6 +215,21 @@ __global__ void __launch_bounds__(256) k_propagate(PropParams p, Op op) {
             sc.cxx = S.scal[0] * s_it * op.J2;
             for (int x = x0; x < dim; x += stride) {
               double2 hv = apply_spin_at(q, x, op, sc, S.bsite);
+              if (qm) {
+                const double2 w = qm[x];
+                hv.x = fma(-bm, w.x, hv.x);
+                hv.y = fma(-bm, w.y, hv.y);
+              }
+              u[x] = hv;
+              const double2 v = q[x];
+              acc = fma(v.x, hv.x, fma(v.y, hv.y, acc));
+            }
+          } else if constexpr (FAMILY == kFamilySpinIP) {
+            const double2* Wt = reinterpret_cast<const double2*>(smem_raw + ip_table_offset<SmemLayout>());
+            for (int x = x0; x < dim; x += stride) {
+              double2 hv = apply_spin_ip_at(q, x, op.N, Wt);
+              hv.x *= s_it;
+              hv.y *= s_it;
               if (qm) {
                 const double2 w = qm[x];
                 hv.x = fma(-bm, w.x, hv.x);
@@ -441,6 +498,39 @@ int launch_propagate_spin(const PropParams& p, const OpSpin& op, int grid, int b
 int launch_propagate_dia(const PropParams& p, const OpDia& op, int grid, int block, void* stream) {
   return launch_prop<kFamilyDia>(p, op, grid, block, stream);
 }
+int launch_propagate_spin_ip(const PropParams& p, const OpSpinIP& op, int grid, int block, void* stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = ip_table_offset<SmemLayout>() + (size_t)op.nw * sizeof(double2);
+  cfg.stream = (cudaStream_t)stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return (int)cudaLaunchKernelEx(&cfg, k_propagate<kFamilySpinIP, OpSpinIP>, p, op);
+}
+
+// psi[x] *= exp(i sign d(x) t[which]), d = diagonal of the XXZ chain H0
+__global__ void k_phase_diag(double2* psi, OpSpin op, int dim, const double* t, int which, double sign) {
+  const double tt = sign * t[which];
+  const int L = op.lo_bits;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < dim; x += gridDim.x * blockDim.x) {
+    const double d = __ldg(op.dz_lo + (x & ((1 << L) - 1))) + __ldg(op.dz_hi + (x >> (L - 1)));
+    double sn, cs;
+    sincos(d * tt, &sn, &cs);
+    const double2 v = psi[x];
+    psi[x] = make_double2(cs * v.x - sn * v.y, sn * v.x + cs * v.y);
+  }
+}
+
+int launch_phase_diag(double2* psi, const OpSpin& op, int dim, const double* t, int which, double sign, void* stream) {
+  int g = (dim + 255) / 256;
+  g = g < 1 ? 1 : (g > 4096 ? 4096 : g);
+  k_phase_diag<<<g, 256, 0, (cudaStream_t)stream>>>(psi, op, dim, t, which, sign);
+  return (int)cudaGetLastError();
+}
 
 int max_coresident_blocks(int family, int block) {
   int dev = 0, nsm = 0, per = 0;
@@ -452,6 +542,17 @@ int max_coresident_blocks(int family, int block) {
   else
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate<kFamilyDia, OpDia>, block, sizeof(SmemLayout));
   if (e != cudaSuccess) return -1;
+  return per * nsm;
+}
+
+int max_coresident_blocks_ip(int block, int nw) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = ip_table_offset<SmemLayout>() + (size_t)nw * sizeof(double2);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate<kFamilySpinIP, OpSpinIP>, block, smem) !=
+      cudaSuccess)
+    return -1;
   return per * nsm;
 }
 

@@ -105,6 +105,18 @@ def test_create_validates_arguments(lib):
     st, _ = _create(lib, ok_h0, [xf], [cb], opt)
     assert st == _capi.CFET_EINVAL and b"CHEBYSHEV" in lib.cfet_last_error(None)
     opt.expm, opt.precision = _capi.CFET_EXPM_KRYLOV, _capi.CFET_PREC_DEFAULT
+    # picture: known values; the interaction picture needs FP64, Krylov, a chain
+    opt.picture = 3
+    st, _ = _create(lib, ok_h0, [xf], [cb], opt)
+    assert st == _capi.CFET_EINVAL and b"picture" in lib.cfet_last_error(None)
+    opt.picture = _capi.CFET_PICTURE_INTERACTION    # with the default fixed-point precision
+    st, _ = _create(lib, ok_h0, [xf], [cb], opt)
+    assert st == _capi.CFET_EINVAL and b"INTERACTION" in lib.cfet_last_error(None)
+    opt.precision = _capi.CFET_PREC_F64
+    dia_ip = P._op_struct(P.DIA(np.array([0]), np.ones((1, 8))), keep)
+    st, _ = _create(lib, dia_ip, [], [], opt)
+    assert st == _capi.CFET_EINVAL and b"INTERACTION" in lib.cfet_last_error(None)
+    opt.picture, opt.precision = _capi.CFET_PICTURE_SCHROEDINGER, _capi.CFET_PREC_DEFAULT
     # DIA offsets out of range
     dia = P._op_struct(P.DIA(np.array([0, 7]), np.ones((2, 7))), keep)
     assert _create(lib, dia, [], [])[0] == _capi.CFET_EINVAL
@@ -115,7 +127,7 @@ def test_options_default(lib):
     lib.cfet_options_default(C.byref(opt))
     assert (opt.m_max, opt.m_min, opt.max_substeps, opt.block_size) == (16, 2, 64, 0)
     assert opt.barrier_timeout_s == 2.0
-    assert opt.expm == _capi.CFET_EXPM_KRYLOV
+    assert opt.expm == _capi.CFET_EXPM_KRYLOV and opt.picture == _capi.CFET_PICTURE_SCHROEDINGER
 
 
 def test_no_device_gives_enodev(lib):
