@@ -788,6 +788,50 @@ def run_study_timestep(args):
     return 0
 
 
+def run_study_picture(args):
+    """Interaction against Schroedinger picture (Secs. 9.3, 9.4), FP64 Krylov,
+    N=20 chain, CF6:5Opt, tol 1e-10, m <= 16, over T = --sweep-T: the default
+    chain (|h_i| <= 1, J Delta = 0.5) and one with a strong diagonal (h_i in
+    [-8, 8], Delta = 4): Krylov applies per exponential, time, and the error of
+    each against a fine Schroedinger-picture reference (fixed point, CF8:11,
+    dt T/400, tol 1e-13)."""
+    import torch
+    import paper_1102_5071_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    T = args.sweep_T
+    psi0 = W.random_state(PSI_SEED, 1 << N_SITES)
+    for label, h_scale, Delta in (("default chain", 1.0, 0.5), ("strong diagonal", 8.0, 4.0)):
+        pr = W.spin_chain(N_SITES, Delta=Delta)
+        h = pr.h * h_scale
+
+        def make(picture, m_max=M_MAX, precision="f64"):
+            return P.Propagator(P.XXZChain(N_SITES, pr.J, Delta, h), [P.XField(N_SITES, pr.xfield)], [pr.drive],
+                                m_max=m_max, max_substeps=200, precision=precision, picture=picture)
+
+        ref_p = make("schroedinger", 30, "fx")
+        ref = torch.from_numpy(psi0).cuda()
+        ref_p.propagate(ref, 0.0, T / 400, 400, order=8, tol=1e-13)
+        ref_p.close()
+        for picture in ("schroedinger", "interaction"):
+            prop = make(picture)
+            for dt in (0.02, 0.005):
+                n = int(round(T / dt))
+                x = torch.from_numpy(psi0).cuda()
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                st = prop.propagate(x, 0.0, dt, n, order=6, tol=TOL)
+                torch.cuda.synchronize()
+                el = time.perf_counter() - t
+                print(json.dumps({"study": "picture", "workload": "N=20 chain, %s, CF6:5Opt T=%g" % (label, T),
+                                  "picture": picture, "dt": dt, "steps": n,
+                                  "applies_per_exponential": st["n_applies"] / st["n_exp"],
+                                  "substeps_per_exponential": st["n_substeps"] / st["n_exp"],
+                                  "time_s": el, "final_state_error": torch.linalg.vector_norm(x - ref).item()}))
+            prop.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -803,9 +847,10 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="accuracy study: final-state error and throughput per (order, dt) over T")
     ap.add_argument("--sweep-T", type=float, default=20.0)
-    ap.add_argument("--study", choices=["atom", "sizes", "batch", "adjoint", "expm", "timestep"],
+    ap.add_argument("--study", choices=["atom", "sizes", "batch", "adjoint", "expm", "timestep", "picture"],
                     help="extra measurements: the grid atom, the chain at N = 20..26, the 256-chain batch, "
-                         "the fidelity gradient, Krylov against Chebyshev stage exponentials, time-step selection")
+                         "the fidelity gradient, Krylov against Chebyshev stage exponentials, time-step selection, "
+                         "interaction against Schroedinger picture")
     ap.add_argument("--baseline-steps", type=int, default=10,
                     help="batch study: steps of the single-instance baseline per instance")
     ap.add_argument("--grid-size", type=int, default=0,
@@ -831,6 +876,8 @@ def main():
         return run_study_expm(args)
     if args.study == "timestep":
         return run_study_timestep(args)
+    if args.study == "picture":
+        return run_study_picture(args)
     return run_gpu(args)
 
 
