@@ -63,6 +63,7 @@ struct SmemCheb {
   // reductions
   unsigned long long wmy[32], wma[32];
   double wsum[32];
+  long long t_const, t_pass;      // trace (SM cycles): term constants (warp 0), element passes (thread 0)
   int abort_flag;
 };
 
@@ -310,7 +311,11 @@ __global__ void __launch_bounds__(kChebThreads, 1) k_cheb_fx(PropParams p, Op op
 
   // ---------------- psi: NaN check and max |psi| -> E_0; convert to v_0
   {
-    if (tid == 0) S.abort_flag = 0;
+    if (tid == 0) {
+      S.abort_flag = 0;
+      S.t_const = 0;
+      S.t_pass = 0;
+    }
     unsigned long long mx = 0;
     for (int x = wx0; x < wxe; x += wstep) {
       const double2 v = p.psi[x];
@@ -385,6 +390,7 @@ __global__ void __launch_bounds__(kChebThreads, 1) k_cheb_fx(PropParams p, Op op
       const int sdst = ((k - 1) & 1) ? sA : sB;
       // ---- constants of this term (warp 0)
       if (warp == 0) {
+        const long long tc0 = sm_clock();
         double By = 0.0;  // bound of |y| (real units)
         if (k >= 1) {
           const double g = first ? R[0] : 2.0 * R[0];
@@ -429,9 +435,11 @@ __global__ void __launch_bounds__(kChebThreads, 1) k_cheb_fx(PropParams p, Op op
           } else {
             S.E_out = Ey;
           }
+          S.t_const += sm_clock() - tc0;
         }
       }
       __syncthreads();
+      const long long tp0 = sm_clock();
       long long my = 0, ma = 0;
       {
         const longlong2* cur = V[scur];
@@ -453,6 +461,7 @@ __global__ void __launch_bounds__(kChebThreads, 1) k_cheb_fx(PropParams p, Op op
           cheb_pass<FAMILY, false, false, true>(S, op, p, k, cur, prev, dst, V[sC], V[sA], wx0, wxe, wstep,
                                                 last_exp, my, ma);
       }
+      if (tid == 0) S.t_pass += sm_clock() - tp0;
       if (last && last_exp) break;
       unsigned long long gy = 0, ga = 0;
       exchange_max(my, ma, true, gy, ga);
@@ -488,11 +497,13 @@ __global__ void __launch_bounds__(kChebThreads, 1) k_cheb_fx(PropParams p, Op op
     if (max_k > st->max_k) st->max_k = max_k;
     if (max_tail > st->max_err) st->max_err = max_tail;
   }
-  if (tid == 0) {
-    atomicAdd((unsigned long long*)&st->phase_ns[0], (unsigned long long)(t_loop / G));
-    atomicMax(&st->phase_max_ns[0], t_loop);
-    atomicAdd((unsigned long long*)&st->phase_ns[5], (unsigned long long)(t_wait / G));
-    atomicMax(&st->phase_max_ns[5], t_wait);
+  if (tid == 0) {  // trace: [0] term loops, [1] term constants, [2] element passes, [5] exchange waits
+    const long long v[4] = {t_loop, S.t_const, S.t_pass, t_wait};
+    const int slot_of[4] = {0, 1, 2, 5};
+    for (int j = 0; j < 4; ++j) {
+      atomicAdd((unsigned long long*)&st->phase_ns[slot_of[j]], (unsigned long long)(v[j] / G));
+      atomicMax(&st->phase_max_ns[slot_of[j]], v[j]);
+    }
   }
 }
 
