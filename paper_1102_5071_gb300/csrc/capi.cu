@@ -226,8 +226,8 @@ cfet_status launch_chunk(cfet_ctx* ctx, const PropParams& base, long long e0, lo
     OpSpinIP op{ctx->spin.N, p.ip_nw, p.ip_w};
     e = launch_propagate_spin_ip(p, op, ctx->grid, ctx->block, s);
   } else if (ctx->opt.expm == CFET_EXPM_CHEBYSHEV)
-    e = ctx->family == kFamilySpin ? launch_cheb_spin_fx(p, ctx->spin_fx, ctx->grid, ctx->block - 32, s)
-                                   : launch_cheb_dia_fx(p, ctx->dia_fx, ctx->grid, ctx->block - 32, s);
+    e = ctx->family == kFamilySpin ? launch_cheb_spin_fx(p, ctx->spin_fx, ctx->grid, cheb_threads(ctx->block - 32), s)
+                                   : launch_cheb_dia_fx(p, ctx->dia_fx, ctx->grid, cheb_threads(ctx->block - 32), s);
   else if (ctx->precision == CFET_PREC_FX)
     e = ctx->family == kFamilySpin ? launch_propagate_spin_fx(p, ctx->spin_fx, ctx->grid, ctx->block, s)
                                    : launch_propagate_dia_fx(p, ctx->dia_fx, ctx->grid, ctx->block, s);
@@ -811,7 +811,7 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
     if (mi < maxg) maxg = mi;
   }
   if (o.expm == CFET_EXPM_CHEBYSHEV) {  // the Chebyshev kernel: the same workers, no control warp
-    const int mc = max_coresident_blocks_cheb(family, ctx->block - 32);
+    const int mc = max_coresident_blocks_cheb(family, cheb_threads(ctx->block - 32));
     if (mc < 1) {
       free_ctx(ctx);
       return fail(nullptr, CFET_ECUDA, "occupancy query failed for the Chebyshev kernel");

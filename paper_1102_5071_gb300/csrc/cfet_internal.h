@@ -171,6 +171,7 @@ void stage_interval(int nops, const double* op_lo, const double* op_hi, const do
 int launch_cheb_spin_fx(const PropParams& p, const OpSpinFx& op, int grid, int block, void* stream);
 int launch_cheb_dia_fx(const PropParams& p, const OpDiaFx& op, int grid, int block, void* stream);
 int max_coresident_blocks_cheb(int family, int block);
+int cheb_threads(int workers);  // threads per CTA of the Chebyshev kernel for `workers` element threads
 
 // Backward (adjoint) sweep of the fidelity gradient (see adjoint.cu).
 constexpr int kAdjMaxK = 16;     // Krylov dimension limit of the adjoint sweep

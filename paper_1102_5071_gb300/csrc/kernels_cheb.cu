@@ -38,7 +38,14 @@
 
 namespace cfet {
 
-constexpr int kChebThreads = 768;   // launch bound of the kernel
+// Threads per CTA (launch bound) and two-element pairs in the spin pass.
+#ifndef CFET_CHEB_THREADS
+#define CFET_CHEB_THREADS 768
+#endif
+#ifndef CFET_CHEB_PAIRS
+#define CFET_CHEB_PAIRS 0  // measured: no gain at 768 threads (register-bound), a loss at 640
+#endif
+constexpr int kChebThreads = CFET_CHEB_THREADS;
 
 struct SmemCheb {
   // constants of the current term
@@ -56,6 +63,15 @@ struct SmemCheb {
   double scal[1 + kMaxDrives];
   double bsite[kMaxSites];
   double bsum, bmax;
+  // per exponential and kind of term (0: first, Htilde; 1: later, 2 Htilde):
+  // mantissas of the scalars and the coefficient sum of the output bound
+  struct TermScalars {
+    double csum;                 // B = A_prev + csum * A_k (real units)
+    Mant mcz, mh, mx, ms;        // c0 g, c0 g 2J, b_0 g (uniform fields), -g b
+    int ED, eb;                  // exponent of the diagonal bound; of the per-site table
+    Mant mop[1 + kMaxDrives];    // DIA: scal[o] g
+    long long mbraw[kMaxSites];  // per-site table before the product shift
+  } ts[2];
   // vectors: exponent and measured max |mantissa| of the three slots
   int Ev[3];
   long long Av[3];
@@ -89,75 +105,96 @@ struct ChebMax2 {    // two maxima
   }
 };
 
-// Constants of the term  y = g H_j v - g b v - use_prev * v_prev  (lane 0 of
-// warp 0 for the scalars, the lanes for the per-site table): v has measured
-// max |mantissa| Ak at exponent Ek, v_prev Apr at Epr; y gets the exponent of
-// the rigorous bound B of its terms (returned in real units), as in the Krylov
-// kernel (kernels_fx.cu).  Returns B.
+// Per-exponential part of the term constants (warp 0: lane 0 for the scalars,
+// the lanes for the per-site table) for the term kind `slot` with
+// y = g H_j v - g b v - use_prev v_prev.
 template <int FAMILY, class Op>
-__device__ double cheb_term_const(SmemCheb& S, const Op& op, double g, double gb, int use_prev, long long Ak, int Ek,
-                                  long long Apr, int Epr) {
+__device__ void cheb_exp_scalars(SmemCheb& S, int slot, const Op& op, double g, double gb) {
   const int lane = threadIdx.x & 31;
-  FxConstA& c = S.c;
-  double B = 0.0;
-  int eb = 0;
+  SmemCheb::TermScalars& T = S.ts[slot];
   if (lane == 0) {
-    const double A = (double)Ak;
-    const double Akr = fx_scale2(A, Ek);
-    const double Aprr = use_prev ? fx_scale2((double)Apr, Epr) : 0.0;
-    c.pk = fx_norm_shift(A);
-    B = Aprr + fabs(gb) * Akr;
+    T.ms = fx_mant(-gb);
+    double cs = fabs(gb);
     if constexpr (FAMILY == kFamilySpin) {
       const double cz = S.scal[0] * g;
       const double ch = cz * op.J2;
-      B += (fabs(cz) * op.maxdz + fabs(ch) * (op.N - 1) + fabs(g) * S.bsum) * Akr;
-      const int Eu = fx_exp_for(B, kFxBits);
-      c.Eu = Eu;
-      const Mant mcz = fx_mant(cz);
-      const int ED = fx_exp_for(fabs(cz) * op.maxdz, 59);
-      c.s_d = ED - mcz.e - (op.E_dz - 1) - 64;
-      c.s_diag = Eu - (ED - 3) - (Ek - c.pk) - 64;
-      c.m_cz = fx_fold(mcz.m, c.s_d + c.s_diag);
-      const Mant mh = fx_mant(ch);
-      c.ph = fx_norm_shift((op.N > 1 ? op.N - 1 : 1) * A);
-      c.s_hop = Eu - mh.e - (Ek - c.ph) - 64;
-      c.m_hop = fx_fold(mh.m, c.s_hop);
-      if (op.uniform) {
-        const Mant mx = fx_mant(S.bsite[0] * g);
-        c.px = fx_norm_shift(op.N * A);
-        c.s_x = Eu - mx.e - (Ek - c.px) - 64;
-        c.m_x = fx_fold(mx.m, c.s_x);
-      } else {
-        eb = fx_exp_for(fabs(g) * S.bmax, 62);
-        c.s_nu = Eu - eb - (Ek - c.pk) - 64;
-      }
+      cs += fabs(cz) * op.maxdz + fabs(ch) * (op.N - 1) + fabs(g) * S.bsum;
+      T.mcz = fx_mant(cz);
+      T.ED = fx_exp_for(fabs(cz) * op.maxdz, 59);
+      T.mh = fx_mant(ch);
+      if (op.uniform) T.mx = fx_mant(S.bsite[0] * g);
+      else T.eb = fx_exp_for(fabs(g) * S.bmax, 62);
     } else {
-      for (int o = 0; o < op.nops; ++o) B += fabs(S.scal[o] * g) * op.maxrow[o] * Akr;
-      const int Eu = fx_exp_for(B, kFxBits);
-      c.Eu = Eu;
       for (int o = 0; o < op.nops; ++o) {
-        const int Epre = fx_exp_for(op.maxrow[o] * Akr, 62);  // |P_o| < 2^62
-        c.sh_pre[o] = Epre - op.E_op[o] - Ek;
-        const Mant m = fx_mant(S.scal[o] * g);
-        c.s_op[o] = Eu - m.e - Epre - 64;
-        c.m_op[o] = fx_fold(m.m, c.s_op[o]);
+        cs += fabs(S.scal[o] * g) * op.maxrow[o];
+        T.mop[o] = fx_mant(S.scal[o] * g);
       }
     }
-    const Mant mp = fx_mant(-1.0);
-    c.pp = use_prev ? fx_norm_shift((double)Apr) : 0;
-    c.s_p = c.Eu - mp.e - (Epr - c.pp) - 64;
-    c.m_p = use_prev ? fx_fold(mp.m, c.s_p) : 0;
-    c.use_prev = use_prev;
-    const Mant ms = fx_mant(-gb);
-    S.m_s = ms.m == 0 ? 0 : fx_fold(ms.m, c.Eu - ms.e - (Ek - c.pk) - 64);
+    T.csum = cs;
   }
   if constexpr (FAMILY == kFamilySpin) {
     if (!op.uniform) {
-      eb = __shfl_sync(0xffffffffu, eb, 0);
+      __syncwarp();
+      const int eb = T.eb;
+      for (int i = lane; i < op.N; i += 32) T.mbraw[i] = __double2ll_rn(fx_scale2(S.bsite[i] * g, -eb));
+    }
+  }
+  __syncwarp();
+}
+
+// Constants of the term  y = g H_j v - g b v - use_prev * v_prev  (warp 0):
+// v has measured max |mantissa| Ak at exponent Ek, v_prev Apr at Epr; y gets
+// the exponent of the rigorous bound B of its terms (returned in real units),
+// as in the Krylov kernel (kernels_fx.cu).  Uses the per-exponential scalars
+// of cheb_exp_scalars; only shifts and folds depend on the term.
+template <int FAMILY, class Op>
+__device__ double cheb_term_const(SmemCheb& S, int slot, const Op& op, int use_prev, long long Ak, int Ek,
+                                  long long Apr, int Epr) {
+  const int lane = threadIdx.x & 31;
+  FxConstA& c = S.c;
+  const SmemCheb::TermScalars& T = S.ts[slot];
+  double B = 0.0;
+  if (lane == 0) {
+    const double A = (double)Ak;
+    const double Akr = fx_scale2(A, Ek);
+    c.pk = fx_norm_shift(A);
+    B = (use_prev ? fx_scale2((double)Apr, Epr) : 0.0) + T.csum * Akr;
+    const int Eu = fx_exp_for(B, kFxBits);
+    c.Eu = Eu;
+    if constexpr (FAMILY == kFamilySpin) {
+      c.s_d = T.ED - T.mcz.e - (op.E_dz - 1) - 64;
+      c.s_diag = Eu - (T.ED - 3) - (Ek - c.pk) - 64;
+      c.m_cz = fx_fold(T.mcz.m, c.s_d + c.s_diag);
+      c.ph = fx_norm_shift((op.N > 1 ? op.N - 1 : 1) * A);
+      c.s_hop = Eu - T.mh.e - (Ek - c.ph) - 64;
+      c.m_hop = fx_fold(T.mh.m, c.s_hop);
+      if (op.uniform) {
+        c.px = fx_norm_shift(op.N * A);
+        c.s_x = Eu - T.mx.e - (Ek - c.px) - 64;
+        c.m_x = fx_fold(T.mx.m, c.s_x);
+      } else {
+        c.s_nu = Eu - T.eb - (Ek - c.pk) - 64;
+      }
+    } else {
+      for (int o = 0; o < op.nops; ++o) {
+        const int Epre = fx_exp_for(op.maxrow[o] * Akr, 62);  // |P_o| < 2^62
+        c.sh_pre[o] = Epre - op.E_op[o] - Ek;
+        c.s_op[o] = Eu - T.mop[o].e - Epre - 64;
+        c.m_op[o] = fx_fold(T.mop[o].m, c.s_op[o]);
+      }
+    }
+    // -v_prev: mantissa of -1 is -2^61 at exponent -61
+    c.pp = use_prev ? fx_norm_shift((double)Apr) : 0;
+    c.s_p = Eu + 61 - (Epr - c.pp) - 64;
+    c.m_p = use_prev ? fx_fold(-(1LL << 61), c.s_p) : 0;
+    c.use_prev = use_prev;
+    S.m_s = T.ms.m == 0 ? 0 : fx_fold(T.ms.m, Eu - T.ms.e - (Ek - c.pk) - 64);
+  }
+  if constexpr (FAMILY == kFamilySpin) {
+    if (!op.uniform) {
       __syncwarp();
       const int s_nu = c.s_nu;
-      for (int i = lane; i < op.N; i += 32)
-        S.mb[i] = fx_fold(__double2ll_rn(fx_scale2(S.bsite[i] * g, -eb)), s_nu);
+      for (int i = lane; i < op.N; i += 32) S.mb[i] = fx_fold(T.mbraw[i], s_nu);
     }
   }
   __syncwarp();
@@ -206,9 +243,9 @@ __device__ __forceinline__ void cheb_pass(const SmemCheb& S, const Op& op, const
                                           longlong2* acc, const longlong2* v0, int wx0, int wxe, int wstep,
                                           bool last_exp, long long& my, long long& ma) {
   const int dim = p.dim;
-  for (int x = wx0; x < wxe; x += wstep) {
+  // the sum and the outputs of one element, given its y
+  auto elem = [&](int x, const longlong2 y) {
     long long ar, ai;
-    longlong2 y = make_longlong2(0, 0);
     if (FIRST) {
       const longlong2 v = v0[x];
       ar = fx_mulhi(S.m_r0, v.x << S.p0);
@@ -219,7 +256,6 @@ __device__ __forceinline__ void cheb_pass(const SmemCheb& S, const Op& op, const
       ai = fx_rshr(a.y, S.sa);
     }
     if (APPLY) {
-      y = cheb_apply1<FAMILY>(cur, prev, x, dim, op, S.c, S.mb, S.m_s);
       long long zr, zi;
       cheb_rot(k, y.x, y.y, zr, zi);
       ar += fx_mulhi(S.m_r, zr << S.py);
@@ -241,6 +277,31 @@ __device__ __forceinline__ void cheb_pass(const SmemCheb& S, const Op& op, const
         p.psi[x] = make_double2(__ll2double_rn(nr) * osc, __ll2double_rn(ni) * osc);
       }
     }
+  };
+  int x = wx0;
+#if CFET_CHEB_PAIRS
+  if constexpr (FAMILY == kFamilySpin && APPLY) {  // two elements per loop iteration
+    for (; x + wstep < wxe; x += 2 * wstep) {
+      longlong2 y1, y2;
+      fx_apply_spin2(cur, prev, x, x + wstep, op, S.c, S.mb, y1, y2);
+      const long long m_s = S.m_s;
+      if (m_s != 0) {
+        const longlong2 v1 = cur[x], v2 = cur[x + wstep];
+        const int pk = S.c.pk;
+        y1.x += fx_mulhi(m_s, v1.x << pk);
+        y1.y += fx_mulhi(m_s, v1.y << pk);
+        y2.x += fx_mulhi(m_s, v2.x << pk);
+        y2.y += fx_mulhi(m_s, v2.y << pk);
+      }
+      elem(x, y1);
+      elem(x + wstep, y2);
+    }
+  }
+#endif
+  for (; x < wxe; x += wstep) {
+    longlong2 y = make_longlong2(0, 0);
+    if (APPLY) y = cheb_apply1<FAMILY>(cur, prev, x, dim, op, S.c, S.mb, S.m_s);
+    elem(x, y);
   }
 }
 
@@ -381,6 +442,10 @@ __global__ void __launch_bounds__(kChebThreads, 1) k_cheb_fx(PropParams p, Op op
         __syncwarp();
       }
     }
+    if (warp == 0 && K >= 1) {
+      cheb_exp_scalars<FAMILY>(S, 0, op, R[0], R[1]);
+      if (K >= 2) cheb_exp_scalars<FAMILY>(S, 1, op, 2.0 * R[0], 2.0 * R[1]);
+    }
     const long long t0 = sm_clock();
     for (int k = (K == 0 ? 0 : 1); k <= K; ++k) {
       const bool last = k == K;
@@ -392,12 +457,9 @@ __global__ void __launch_bounds__(kChebThreads, 1) k_cheb_fx(PropParams p, Op op
       if (warp == 0) {
         const long long tc0 = sm_clock();
         double By = 0.0;  // bound of |y| (real units)
-        if (k >= 1) {
-          const double g = first ? R[0] : 2.0 * R[0];
-          const double gb = first ? R[1] : 2.0 * R[1];
-          By = cheb_term_const<FAMILY>(S, op, g, gb, first ? 0 : 1, S.Av[scur], S.Ev[scur],
+        if (k >= 1)
+          By = cheb_term_const<FAMILY>(S, first ? 0 : 1, op, first ? 0 : 1, S.Av[scur], S.Ev[scur],
                                        first ? 0 : S.Av[sdst], first ? 0 : S.Ev[sdst]);
-        }
         if (lane == 0) {
           const int Ey = S.c.Eu;
           S.py = fx_norm_shift(k >= 1 ? fx_scale2(By, -Ey) : 0.0);
@@ -529,6 +591,8 @@ int launch_cheb_spin_fx(const PropParams& p, const OpSpinFx& op, int grid, int b
 int launch_cheb_dia_fx(const PropParams& p, const OpDiaFx& op, int grid, int block, void* stream) {
   return launch_cheb<kFamilyDia>(p, op, grid, block, stream);
 }
+
+int cheb_threads(int workers) { return workers < kChebThreads ? workers : kChebThreads; }
 
 int max_coresident_blocks_cheb(int family, int block) {
   int dev = 0, nsm = 0, per = 0;
