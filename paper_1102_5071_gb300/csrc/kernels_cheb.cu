@@ -251,7 +251,7 @@ __device__ __forceinline__ void cheb_pass(const SmemCheb& S, const Op& op, const
       ar = fx_mulhi(S.m_r0, v.x << S.p0);
       ai = fx_mulhi(S.m_r0, v.y << S.p0);
     } else {
-      const longlong2 a = acc[x];
+      const longlong2 a = fx_ld_stream(acc + x);
       ar = fx_rshr(a.x, S.sa);
       ai = fx_rshr(a.y, S.sa);
     }
@@ -263,7 +263,7 @@ __device__ __forceinline__ void cheb_pass(const SmemCheb& S, const Op& op, const
     }
     if (!LAST) {
       dst[x] = y;
-      acc[x] = make_longlong2(ar, ai);
+      fx_st_stream(acc + x, make_longlong2(ar, ai));
       my = max(my, fx_absmax(y.x, y.y));
       ma = max(ma, fx_absmax(ar, ai));
     } else {
