@@ -116,8 +116,8 @@ struct cfet_ctx {
 namespace {
 
 // Reduction / exchange scratch per CTA (8-byte words): the FP64 kernel uses 3
-// partials, the control-warp kernels 3 slots of at most 6 tagged words.
-constexpr size_t kPartialWordsPerCta = 18;
+// partials, the control-warp kernels 3 slots of at most 8 tagged words.
+constexpr size_t kPartialWordsPerCta = 24;
 constexpr int kMaxCtlGrid = 256;  // 32 lanes x 8 records per lane of the exchange
 
 thread_local std::string g_create_err;

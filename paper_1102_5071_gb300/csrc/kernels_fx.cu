@@ -257,8 +257,8 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
   const unsigned tag0 = (unsigned)ld_volatile_i32((const int*)&p.st->tag_base);
   unsigned gen = 0;
   unsigned long long* partA = reinterpret_cast<unsigned long long*>(p.partials);
-  unsigned long long* partB = partA + 6 * G;
-  unsigned long long* partR = partA + 12 * G;
+  unsigned long long* partB = partA + 8 * G;
+  unsigned long long* partR = partA + 16 * G;
   DevStatus* st = p.st;
   const bool glead = (blockIdx.x == 0) && lead;
   // trace (see cfet_stats.phase_ns): worker loop times by thread 0, control
