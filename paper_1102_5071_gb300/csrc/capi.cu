@@ -116,8 +116,10 @@ struct cfet_ctx {
 namespace {
 
 // Reduction / exchange scratch per CTA (8-byte words): the FP64 kernel uses 3
-// partials, the control-warp kernels 3 slots of at most 8 tagged words.
-constexpr size_t kPartialWordsPerCta = 24;
+// partials, the control-warp kernels slots of tagged words: the two-pass
+// fixed-point and complex64 kernels 3 slots of at most 8 words, the one-pass
+// fixed-point kernel two 16-word slots and three 8-word slots.
+constexpr size_t kPartialWordsPerCta = 56;
 constexpr int kMaxCtlGrid = 256;  // 32 lanes x 8 records per lane of the exchange
 
 thread_local std::string g_create_err;
@@ -228,6 +230,9 @@ cfet_status launch_chunk(cfet_ctx* ctx, const PropParams& base, long long e0, lo
   } else if (ctx->opt.expm == CFET_EXPM_CHEBYSHEV)
     e = ctx->family == kFamilySpin ? launch_cheb_spin_fx(p, ctx->spin_fx, ctx->grid, cheb_threads(ctx->block - 32), s)
                                    : launch_cheb_dia_fx(p, ctx->dia_fx, ctx->grid, cheb_threads(ctx->block - 32), s);
+  else if (ctx->precision == CFET_PREC_FX && CFET_FX_ONEPASS)
+    e = ctx->family == kFamilySpin ? launch_propagate_spin_fx1(p, ctx->spin_fx, ctx->grid, ctx->block, s)
+                                   : launch_propagate_dia_fx1(p, ctx->dia_fx, ctx->grid, ctx->block, s);
   else if (ctx->precision == CFET_PREC_FX)
     e = ctx->family == kFamilySpin ? launch_propagate_spin_fx(p, ctx->spin_fx, ctx->grid, ctx->block, s)
                                    : launch_propagate_dia_fx(p, ctx->dia_fx, ctx->grid, ctx->block, s);
@@ -795,7 +800,8 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
   }
   // persistent grid: co-resident maximum, no more CTAs than needed to give
   // every thread at least one element
-  int maxg = ctx->precision == CFET_PREC_FX    ? max_coresident_blocks_fx(family, ctx->block)
+  int maxg = ctx->precision == CFET_PREC_FX    ? (CFET_FX_ONEPASS ? max_coresident_blocks_fx1(family, ctx->block)
+                                                                  : max_coresident_blocks_fx(family, ctx->block))
                    : ctx->precision == CFET_PREC_C64 ? max_coresident_blocks_c64(family, ctx->block)
                                                      : max_coresident_blocks(family, ctx->block);
   if (maxg < 1) {
@@ -826,9 +832,8 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
   if (ctl_warp && ctx->grid > kMaxCtlGrid) ctx->grid = kMaxCtlGrid;  // record exchange limit
   if (ctx->grid < 1) ctx->grid = 1;
 
-  if (ctx->precision == CFET_PREC_FX)  // (the Chebyshev kernel uses three of these vectors)
-    CKC(cudaMalloc(&ctx->d_qbasis, (size_t)std::max(o.m_max + 1, 3) * dim * sizeof(longlong2)),
-        "cudaMalloc(Krylov basis)");
+  if (ctx->precision == CFET_PREC_FX)  // basis q_1..q_{m_max+1} and the two u_k of the one-pass kernel
+    CKC(cudaMalloc(&ctx->d_qbasis, (size_t)(o.m_max + 3) * dim * sizeof(longlong2)), "cudaMalloc(Krylov basis)");
   else if (ctx->precision == CFET_PREC_C64)
     CKC(cudaMalloc(&ctx->d_qbasis32, (size_t)(o.m_max + 1) * dim * sizeof(float2)), "cudaMalloc(Krylov basis)");
   else
