@@ -133,7 +133,7 @@ struct PropParams {
   long long exp_base;    // global index of exponential 0 of this launch
   double tau, tol;
   int m_min, m_max, max_substeps;
-  int pad0;
+  int tiled;             // complex64 spin chains: window-tiled apply (kernels_c64.cu)
   // decisions (device arrays, nullable)
   const int* f_nsub; const int* f_k; const int* f_h;
   int* r_nsub; int* r_k; int* r_h; long long r_cap;
@@ -231,7 +231,11 @@ int max_coresident_blocks_fx1(int family, int block);
 int max_coresident_blocks_fx(int family, int block);
 int launch_propagate_spin_c64(const PropParams& p, const OpSpinC& op, int grid, int block, void* stream);
 int launch_propagate_dia_c64(const PropParams& p, const OpDiaC& op, int grid, int block, void* stream);
-int max_coresident_blocks_c64(int family, int block);
+int max_coresident_blocks_c64(int family, int block, bool tiled);
+// Chains of at least this many sites take the window-tiled complex64 apply;
+// the environment variable CFET_C64_TILED (0 or 1) overrides the choice.
+constexpr int kC64TiledMinSites = 24;
+constexpr int kC64TiledMaxSites = 34;  // four windows of bits
 int launch_adjoint_spin(const AdjParams& p, const OpSpin& op, int grid, int block, void* stream);
 int launch_wait_selftest(int which, unsigned long long* rec, unsigned* bar, int* status, long long timeout_ns);
 constexpr int kDiffBlocks = 152;  // blocks (partials) of the difference norm

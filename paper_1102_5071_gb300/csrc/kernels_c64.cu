@@ -327,6 +327,158 @@ __device__ double c_estimate(SmemC& S, int k, double ts) {
   return S.beta0 * S.beta[k] * hypot(S.yr[k - 1], S.yi[k - 1]);
 }
 
+// ------------------------------------------------------------------ tiled apply (large chains)
+// For chains whose vectors leave L2 every far-bit neighbour gather of the
+// element-wise apply reads DRAM.  The tiled form splits the bits of the index
+// into windows and runs one pass per window over tiles of 2^13 elements staged
+// in shared memory (cp.async, double-buffered): window 0 takes contiguous tiles
+// (bits 0..12: diagonal, previous vector, flips of bits 0..12, hops of bonds
+// (i, i+1), i <= 11); window w >= 1 takes strided tiles made of 2^c contiguous
+// elements times the 2^width values of its bits [b0, b0 + width) (flips of bits
+// b0+1 .. b0+width-1, hops of bonds b0 .. b0+width-2), reads the partial u of
+// its elements, adds its terms and writes u back; the last window also takes
+// <q, u> and ||u||^2.  Windows are separated by grid-wide exchanges.
+constexpr int kTileBits = 13;                 // 2^13 complex64 = 64 KB per tile buffer
+constexpr int kTileElems = 1 << kTileBits;
+constexpr int kHighWindow = 8;                // bits of a high window, its first shared with the window before
+constexpr int kTiledMaxWindows = 4;           // chains of up to 13 + 3 * 7 = 34 sites
+
+struct TileWin {
+  int b0, width, c;
+};
+
+__device__ __forceinline__ int c_tiled_windows(int N, TileWin (&W)[kTiledMaxWindows]) {
+  int n = 1;
+  for (int b0 = kTileBits - 1; b0 + 1 < N && n < kTiledMaxWindows; b0 += kHighWindow - 1, ++n) {
+    const int width = (N - b0) < kHighWindow ? (N - b0) : kHighWindow;
+    W[n].b0 = b0;
+    W[n].width = width;
+    W[n].c = kTileBits - width;
+  }
+  return n;
+}
+
+// element index of slot j of strided tile t of window W (N sites)
+__device__ __forceinline__ int c_tile_x(const TileWin& W, int t, int j) {
+  const int nb = W.b0 - W.c;  // bits [c, b0) come from t
+  const int tl = t & ((1 << nb) - 1), th = t >> nb;
+  return (j & ((1 << W.c) - 1)) | (tl << W.c) | ((j >> W.c) << W.b0) | (th << (W.b0 + W.width));
+}
+
+__device__ __forceinline__ void c_cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void c_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void c_cp_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// barrier of the worker warps only (named barrier 1)
+__device__ __forceinline__ void c_workers_sync(int n) { asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory"); }
+
+// One window pass of this CTA's worker threads over its tiles.
+template <bool FIRST, bool LAST>
+__device__ void c_tiled_pass(float2* buf0, float2* buf1, const OpSpinC& op, const CConst& c, const float* bx,
+                             const float2* __restrict__ q, const float2* __restrict__ qm, float2* __restrict__ u,
+                             const TileWin& W, int nworkers, float& s0, float& c0, float& s1, float& c1) {
+  const int tid = threadIdx.x;
+  const int G = gridDim.x;
+  const int N = op.N;
+  const int ntiles = 1 << (N - kTileBits);
+  auto xof = [&](int t, int j) { return FIRST ? (t << kTileBits) | j : c_tile_x(W, t, j); };
+  auto load = [&](float2* buf, int t) {
+    for (int unit = tid; unit < kTileElems / 2; unit += nworkers) c_cp16(buf + 2 * unit, q + xof(t, 2 * unit));
+    c_cp_commit();
+  };
+  int t = blockIdx.x;
+  if (t < ntiles) load(buf0, t);
+  for (int k = 0; t < ntiles; ++k, t += G) {
+    const float2* cur = (k & 1) ? buf1 : buf0;
+    float2* nxt = (k & 1) ? buf0 : buf1;
+    c_cp_wait();
+    c_workers_sync(nworkers);
+    if (t + G < ntiles) load(nxt, t + G);
+    for (int j = tid; j < kTileElems; j += nworkers) {
+      const int x = xof(t, j);
+      float ur, ui, hr = 0.f, hi = 0.f, fr = 0.f, fi = 0.f;
+      if (FIRST) {
+        const int L = op.lo_bits;
+        const float dz = __ldg(op.dz_lo + (x & ((1 << L) - 1))) + __ldg(op.dz_hi + (x >> (L - 1)));
+        const float d = c.cz * dz;
+        const float2 v = cur[j];
+        ur = d * v.x;
+        ui = d * v.y;
+        const unsigned anti = ((unsigned)j ^ ((unsigned)j >> 1)) & ((1u << (kTileBits - 1)) - 1u);
+#pragma unroll
+        for (int i = 0; i < kTileBits - 1; ++i)
+          if ((anti >> i) & 1u) {
+            const float2 w = cur[j ^ (3 << i)];
+            hr += w.x;
+            hi += w.y;
+          }
+        if (op.uniform) {
+#pragma unroll
+          for (int i = 0; i < kTileBits; ++i) {
+            const float2 w = cur[j ^ (1 << i)];
+            fr += w.x;
+            fi += w.y;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < kTileBits; ++i) {
+            const float2 w = cur[j ^ (1 << i)];
+            ur = fmaf(bx[i], w.x, ur);
+            ui = fmaf(bx[i], w.y, ui);
+          }
+        }
+        if (c.use_prev) {
+          const float2 w = qm[x];
+          ur = fmaf(c.cp, w.x, ur);
+          ui = fmaf(c.cp, w.y, ui);
+        }
+      } else {
+        const float2 a = u[x];
+        ur = a.x;
+        ui = a.y;
+        const unsigned jh = (unsigned)j >> W.c;  // bits b0 .. b0+width-1 of x
+        const unsigned anti = (jh ^ (jh >> 1)) & ((1u << (W.width - 1)) - 1u);
+        for (int i = 0; i < W.width - 1; ++i)
+          if ((anti >> i) & 1u) {
+            const float2 w = cur[j ^ (3 << (W.c + i))];
+            hr += w.x;
+            hi += w.y;
+          }
+        if (op.uniform) {
+          for (int i = 1; i < W.width; ++i) {
+            const float2 w = cur[j ^ (1 << (W.c + i))];
+            fr += w.x;
+            fi += w.y;
+          }
+        } else {
+          for (int i = 1; i < W.width; ++i) {
+            const float2 w = cur[j ^ (1 << (W.c + i))];
+            ur = fmaf(bx[W.b0 + i], w.x, ur);
+            ui = fmaf(bx[W.b0 + i], w.y, ui);
+          }
+        }
+      }
+      ur = fmaf(c.ch, hr, ur);
+      ui = fmaf(c.ch, hi, ui);
+      if (op.uniform) {
+        ur = fmaf(c.cx, fr, ur);
+        ui = fmaf(c.cx, fi, ui);
+      }
+      u[x] = make_float2(ur, ui);
+      if (LAST) {
+        const float2 v = cur[j];
+        ff_add_prod(s0, c0, v.x, ur);
+        ff_add_prod(s0, c0, v.y, ui);
+        ff_add_prod(s1, c1, ur, ur);
+        ff_add_prod(s1, c1, ui, ui);
+      }
+    }
+  }
+  c_cp_wait();
+}
+
 // ------------------------------------------------------------------ the kernel
 template <int FAMILY, class Op>
 __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropParams p, Op op) {
@@ -351,6 +503,16 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
   unsigned long long* partA = reinterpret_cast<unsigned long long*>(p.partials);  // 3 sums: 6 words
   unsigned long long* partB = partA + 6 * G;                                        // 1 sum: 2 words
   unsigned long long* partR = partA + 12 * G;                                       // 1 sum: 2 words
+  unsigned long long* partW = partA + 18 * G;  // window barriers of the tiled apply: two 1-word slots
+  // tiled apply (spin chains with p.tiled): windows and the two tile buffers behind SmemC
+  TileWin win[kTiledMaxWindows] = {};
+  int nwin = 1;
+  if constexpr (FAMILY == kFamilySpin) {
+    if (p.tiled) nwin = c_tiled_windows(op.N, win);
+  }
+  float2* tbuf0 = reinterpret_cast<float2*>(smem_raw + ((sizeof(SmemC) + 127) & ~size_t(127)));
+  float2* tbuf1 = tbuf0 + kTileElems;
+  int wslot = 0;
   DevStatus* st = p.st;
   const bool glead = (blockIdx.x == 0) && lead;
   long long tacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -454,6 +616,25 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
             float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
             const long long tw0 = sm_clock();
             int x = wx0;
+            if constexpr (FAMILY == kFamilySpin) {
+              if (p.tiled) {  // window passes, grid exchanges between them (control warp)
+                for (int w = 0; w < nwin; ++w) {
+                  if (w == 0) {
+                    if (nwin == 1) c_tiled_pass<true, true>(tbuf0, tbuf1, op, c, S.bx, q, qm, u, win[0], wstep, s0, c0, s1, c1);
+                    else c_tiled_pass<true, false>(tbuf0, tbuf1, op, c, S.bx, q, qm, u, win[0], wstep, s0, c0, s1, c1);
+                  } else if (w == nwin - 1) {
+                    c_tiled_pass<false, true>(tbuf0, tbuf1, op, c, S.bx, q, qm, u, win[w], wstep, s0, c0, s1, c1);
+                  } else {
+                    c_tiled_pass<false, false>(tbuf0, tbuf1, op, c, S.bx, q, qm, u, win[w], wstep, s0, c0, s1, c1);
+                  }
+                  if (w + 1 < nwin) {
+                    asm volatile("bar.sync 2;" ::: "memory");  // all threads: window w written
+                    asm volatile("bar.sync 3;" ::: "memory");  // all threads: the grid exchange passed
+                  }
+                }
+                x = wxe;  // nothing left for the element loops
+              }
+            }
 #if CFET_C64_PAIRS
             if constexpr (FAMILY == kFamilySpin) {
               for (; x + wstep < wxe; x += 2 * wstep) {
@@ -490,22 +671,42 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
               twe = sm_clock();
               tacc[0] += twe - tw0;
             }
-          } else if (pend) {
-            const long long te0 = sm_clock();
-            const double err = c_estimate(S, it - 1, remaining);
-            if (lane == 0) {
-              S.err_prev = err;
-              S.stop_prev = err <= p.tol * remaining / p.tau;
-              S.y_ready = S.stop_prev;
-              tacc[6] += sm_clock() - te0;
+          } else {
+            if (pend) {
+              const long long te0 = sm_clock();
+              const double err = c_estimate(S, it - 1, remaining);
+              if (lane == 0) {
+                S.err_prev = err;
+                S.stop_prev = err <= p.tol * remaining / p.tau;
+                S.y_ready = S.stop_prev;
+                tacc[6] += sm_clock() - te0;
+              }
+              __syncwarp();
             }
-            __syncwarp();
+            if constexpr (FAMILY == kFamilySpin) {
+              if (p.tiled) {  // grid exchanges between the window passes of the workers
+                for (int w = 0; w + 1 < nwin; ++w) {
+                  asm volatile("bar.sync 2;" ::: "memory");
+                  double none[1];
+                  const bool ok = !S.abort_flag && c_ctl_reduce<0>(S, NW, partW + (size_t)wslot * G, tag0 + (++gen),
+                                                                   true, &st->status, p.timeout_ns, none, tacc[5]);
+                  __syncwarp();
+                  if (!ok && lane == 0) S.abort_flag = 1;
+                  wslot ^= 1;
+                  asm volatile("bar.sync 3;" ::: "memory");
+                }
+              }
+            }
           }
           __syncthreads();
           if (ctl) {
             const long long tc0 = sm_clock(), sp0 = tacc[5];
             double sum[2];
-            if (!c_ctl_reduce<2>(S, NW, partA, tag0 + (++gen), false, &st->status, p.timeout_ns, sum, tacc[5])) {
+            // (the tiled apply leaves u written by other CTAs: fence)
+            constexpr bool kMayTile = FAMILY == kFamilySpin;
+            if ((kMayTile && S.abort_flag) ||
+                !c_ctl_reduce<2>(S, NW, partA, tag0 + (++gen), kMayTile && p.tiled != 0, &st->status, p.timeout_ns,
+                                 sum, tacc[5])) {
               if (lane == 0) S.abort_flag = 1;
             } else if (lane == 0 && !S.stop_prev) {
               // q_it holds the Lanczos vector v_it times 1/scale[it]:
@@ -738,12 +939,14 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
 }
 
 // ------------------------------------------------------------------ launchers
+size_t c64_tiled_smem_bytes() { return ((sizeof(SmemC) + 127) & ~size_t(127)) + 2 * kTileElems * sizeof(float2); }
+
 template <int FAMILY, class Op>
 static int launch_prop_c64(const PropParams& p, const Op& op, int grid, int block, void* stream) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = sizeof(SmemC);
+  cfg.dynamicSmemBytes = p.tiled ? c64_tiled_smem_bytes() : sizeof(SmemC);
   cfg.stream = (cudaStream_t)stream;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeCooperative;
@@ -760,17 +963,20 @@ int launch_propagate_dia_c64(const PropParams& p, const OpDiaC& op, int grid, in
   return launch_prop_c64<kFamilyDia>(p, op, grid, block, stream);
 }
 
-int max_coresident_blocks_c64(int family, int block) {
+int max_coresident_blocks_c64(int family, int block, bool tiled) {
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  // a few KB of shared memory: leave the unified storage to L1
+  // a few KB of shared memory: leave the unified storage to L1 (a tiled launch
+  // asks for its tile buffers and gets the shared-memory split it needs)
   cudaFuncSetAttribute(k_propagate_c64<kFamilySpin, OpSpinC>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaFuncSetAttribute(k_propagate_c64<kFamilyDia, OpDiaC>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  cudaFuncSetAttribute(k_propagate_c64<kFamilySpin, OpSpinC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)c64_tiled_smem_bytes());
   cudaError_t e;
   if (family == kFamilySpin)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_c64<kFamilySpin, OpSpinC>, block,
-                                                      sizeof(SmemC));
+                                                      tiled ? c64_tiled_smem_bytes() : sizeof(SmemC));
   else
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_c64<kFamilyDia, OpDiaC>, block,
                                                       sizeof(SmemC));

@@ -217,3 +217,131 @@ def test_c64_full_size_atom_without_field_keeps_the_1s_state(torch_cuda):
     st = prop.propagate(x, 500.0, a["dt"], 2, order=a["order"], tol=1e-9)
     ref = np.exp(-1j * e1s * a["dt"] * 2) * psi0
     assert np.linalg.norm(x.cpu().numpy() - ref) <= 1e-4, st
+
+
+# ---------------------------------------------------------------- window-tiled apply
+# Long chains take the window-tiled apply (shared-memory tiles of 2^13
+# elements, one pass per window of index bits; the environment variable
+# CFET_C64_TILED forces it on or off when the context is created).  Chains of
+# 14..20 sites have two windows, 21..27 three, 28..30 four.
+
+@pytest.mark.parametrize("N,nfields", [(13, 1), (14, 2), (16, 1), (17, 2)])
+def test_c64_tiled_matches_oracle(torch_cuda, monkeypatch, N, nfields):
+    monkeypatch.setenv("CFET_C64_TILED", "1")
+    prop, op, drives = _spin(N, nfields=nfields, m_max=16, max_substeps=200)
+    err, same, st, aerr = _run(torch_cuda, prop, op, drives, W.random_state(11, 1 << N), 0.2, 0.05, 3, "CF6:5Opt",
+                               1e-9, 16)
+    assert err <= budget(st["n_substeps"]), (err, st["n_substeps"])
+    assert same >= 0.95 and aerr <= budget(st["n_substeps"]) + 1e-9
+
+
+def _one_magnon_hamiltonian(N, J, Delta, h):
+    # XXZ chain (bit i of the index = site i, bit 1 = spin down) restricted to
+    # the states with one spin down: site k down has the diagonal
+    # J Delta sum_i z_i z_{i+1} + sum_i h_i z_i (z = +1 up, -1 down), and the
+    # exchange term J (XX + YY) moves the down spin by one site with amplitude 2J
+    H = np.zeros((N, N))
+    for k in range(N):
+        z = np.ones(N)
+        z[k] = -1.0
+        H[k, k] = J * Delta * np.dot(z[:-1], z[1:]) + np.dot(h, z)
+        if k + 1 < N:
+            H[k, k + 1] = H[k + 1, k] = 2.0 * J
+    return H
+
+
+@pytest.mark.parametrize("N", [22, 23])
+def test_c64_tiled_one_magnon_sector_is_exact(torch_cuda, monkeypatch, N):
+    # without an x field the one-magnon sector is closed: a chain of 22 or 23
+    # sites (three windows) started with one spin down must follow the N x N
+    # problem exactly and leave every other amplitude at zero; hops across all
+    # window boundaries and the diagonal at every site enter
+    from scipy.linalg import expm
+    import paper_1102_5071_gb300 as P
+    h6 = W.uniform(3, 6, -1, 1)
+    H6 = O.xxz_dense(6, 0.8, 0.6, h6)
+    idx6 = [1 << k for k in range(6)]
+    assert np.allclose(H6[np.ix_(idx6, idx6)], _one_magnon_hamiltonian(6, 0.8, 0.6, h6), atol=1e-14)
+    monkeypatch.setenv("CFET_C64_TILED", "1")
+    J, Dl = 0.8, 0.6
+    h = W.uniform(4, N, -1, 1)
+    prop = P.Propagator(P.XXZChain(N, J, Dl, h), [P.XField(N, np.zeros(N))], [lambda t: 0.0], m_max=24,
+                        max_substeps=400, precision="c64")
+    k0, T = N // 2 - 1, 3.0
+    psi0 = np.zeros(1 << N, dtype=np.complex128)
+    psi0[1 << k0] = 1.0
+    x = _dev(torch_cuda, psi0)
+    st = prop.propagate(x, 0.0, 0.25, 12, order=4, tol=1e-9)
+    out = x.cpu().numpy()
+    e = np.zeros(N)
+    e[k0] = 1.0
+    ref = expm(-1j * T * _one_magnon_hamiltonian(N, J, Dl, h)) @ e
+    sector = np.array([1 << k for k in range(N)])
+    bound = budget(st["n_substeps"]) + st["n_substeps"] * 1e-9
+    assert np.linalg.norm(out[sector] - ref) <= bound, (np.linalg.norm(out[sector] - ref), bound)
+    rest = out.copy()
+    rest[sector] = 0.0
+    assert np.linalg.norm(rest) == 0.0
+
+
+def test_c64_tiled_zero_coupling_factorises_n22(torch_cuda, monkeypatch):
+    # J = 0 with two site-dependent x fields: the chain of 22 sites (three
+    # windows) factorises into driven two-level systems (flips of every bit,
+    # per-site field coefficients, diagonal); sampled amplitudes against the
+    # product of the oracle's single-site propagations
+    import paper_1102_5071_gb300 as P
+    monkeypatch.setenv("CFET_C64_TILED", "1")
+    N = 22
+    pr = W.spin_chain(N, J=0.0, Delta=0.0, A=1.3, omega=1.7)
+    a1, a2 = W.uniform(21, N, 0.5, 1.5), W.uniform(22, N, -1, 1)
+
+    def g(t):
+        return 0.4 * math.sin(0.9 * t)
+
+    prop = P.Propagator(P.XXZChain(N, 0.0, 0.0, pr.h), [P.XField(N, a1), P.XField(N, a2)], [pr.drive, g],
+                        m_max=16, precision="c64")
+    psi0 = W.neel_state(N)
+    nsteps, dt = 30, 0.05
+    x = _dev(torch_cuda, psi0)
+    st = prop.propagate(x, 0.0, dt, nsteps, order=6, tol=1e-10)
+    out = x.cpu().numpy()
+    x0 = int(np.argmax(np.abs(psi0)))
+    single = []
+    for i in range(N):
+        e = np.zeros(2, dtype=np.complex128)
+        e[(x0 >> i) & 1] = 1.0
+        single.append(OC.propagate(O.Dense(pr.h[i] * O.SZ, [a1[i] * O.SX, a2[i] * O.SX]), e, 0.0, dt, nsteps, 6,
+                                   [pr.drive, g], 1e-14, 2))
+    idx = np.random.default_rng(1).integers(0, 1 << N, 4000)
+    amp = np.ones(len(idx), dtype=np.complex128)
+    for i in range(N):
+        amp *= np.where((idx >> i) & 1, single[i][1], single[i][0])
+    assert np.max(np.abs(out[idx] - amp)) <= budget(st["n_substeps"])
+    assert abs(np.linalg.norm(out) - 1.0) <= budget(st["n_substeps"])
+
+
+def test_c64_tiled_matches_elementwise_and_fixed_point_n22(torch_cuda, monkeypatch):
+    # the driven chain of 22 sites: tiled and element-wise complex64 applies
+    # replaying the fixed-point path's decisions agree within twice the
+    # rounding budget, and each within the budget of the fixed-point result
+    # (which matches the oracle to 1e-10 at the sizes the oracle reaches)
+    import paper_1102_5071_gb300 as P
+    N = 22
+    pr = W.spin_chain(N)
+    psi0 = W.random_state(12, 1 << N)
+    kw = dict(m_max=16, max_substeps=200)
+    fx = P.Propagator(P.XXZChain(N, pr.J, pr.Delta, pr.h), [P.XField(N, pr.xfield)], [pr.drive], precision="fx",
+                      **kw)
+    xf = _dev(torch_cuda, psi0)
+    _, log = fx.propagate(xf, 0.1, 0.04, 2, order=6, tol=1e-9, record=True)
+    outs = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("CFET_C64_TILED", flag)
+        prop, _, _ = _spin(N, **kw)
+        x = _dev(torch_cuda, psi0)
+        st = prop.propagate(x, 0.1, 0.04, 2, order=6, tol=1e-9, forced=log)
+        outs[flag] = x.cpu().numpy()
+    ref = xf.cpu().numpy()
+    b = budget(st["n_substeps"])
+    assert np.linalg.norm(outs["1"] - outs["0"]) <= 2 * b
+    assert np.linalg.norm(outs["1"] - ref) <= b and np.linalg.norm(outs["0"] - ref) <= b
