@@ -234,8 +234,8 @@ int launch_propagate_dia_c64(const PropParams& p, const OpDiaC& op, int grid, in
 int max_coresident_blocks_c64(int family, int block, bool tiled);
 // Chains of at least this many sites take the window-tiled complex64 apply;
 // the environment variable CFET_C64_TILED (0 or 1) overrides the choice.
-constexpr int kC64TiledMinSites = 24;
-constexpr int kC64TiledMaxSites = 34;  // four windows of bits
+constexpr int kC64TiledMinSites = 23;
+constexpr int kC64TiledMaxSites = 33;  // four windows of bits (tiles of 2^12)
 int launch_adjoint_spin(const AdjParams& p, const OpSpin& op, int grid, int block, void* stream);
 int launch_wait_selftest(int which, unsigned long long* rec, unsigned* bar, int* status, long long timeout_ns);
 constexpr int kDiffBlocks = 152;  // blocks (partials) of the difference norm

@@ -330,18 +330,21 @@ __device__ double c_estimate(SmemC& S, int k, double ts) {
 // ------------------------------------------------------------------ tiled apply (large chains)
 // For chains whose vectors leave L2 every far-bit neighbour gather of the
 // element-wise apply reads DRAM.  The tiled form splits the bits of the index
-// into windows and runs one pass per window over tiles of 2^13 elements staged
+// into windows and runs one pass per window over tiles of 2^B elements staged
 // in shared memory (cp.async, double-buffered): window 0 takes contiguous tiles
-// (bits 0..12: diagonal, previous vector, flips of bits 0..12, hops of bonds
-// (i, i+1), i <= 11); window w >= 1 takes strided tiles made of 2^c contiguous
+// (bits 0..B-1: diagonal, previous vector, flips of bits 0..B-1, hops of bonds
+// (i, i+1), i <= B-2); window w >= 1 takes strided tiles made of 2^c contiguous
 // elements times the 2^width values of its bits [b0, b0 + width) (flips of bits
 // b0+1 .. b0+width-1, hops of bonds b0 .. b0+width-2), reads the partial u of
 // its elements, adds its terms and writes u back; the last window also takes
 // <q, u> and ||u||^2.  Windows are separated by grid-wide exchanges.
-constexpr int kTileBits = 13;                 // 2^13 complex64 = 64 KB per tile buffer
+// The vector each element reads for itself (q_{k-1} in window 0, the partial u
+// after it) is staged with the tile, so the loop touches global memory only to
+// store u: two q tiles and two such tiles of 2^12 elements (128 KB).
+constexpr int kTileBits = 12;
 constexpr int kTileElems = 1 << kTileBits;
 constexpr int kHighWindow = 8;                // bits of a high window, its first shared with the window before
-constexpr int kTiledMaxWindows = 4;           // chains of up to 13 + 3 * 7 = 34 sites
+constexpr int kTiledMaxWindows = 4;           // chains of up to B + 3 * 7 sites
 
 struct TileWin {
   int b0, width, c;
@@ -375,27 +378,36 @@ __device__ __forceinline__ void c_cp_wait() { asm volatile("cp.async.wait_group 
 __device__ __forceinline__ void c_workers_sync(int n) { asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory"); }
 
 // One window pass of this CTA's worker threads over its tiles.
+// buf: q tiles [2][kTileElems], then the staged own-element vector [2][kTileElems].
 template <bool FIRST, bool LAST>
-__device__ void c_tiled_pass(float2* buf0, float2* buf1, const OpSpinC& op, const CConst& c, const float* bx,
+__device__ void c_tiled_pass(float2* buf, const OpSpinC& op, const CConst& c, const float* bx,
                              const float2* __restrict__ q, const float2* __restrict__ qm, float2* __restrict__ u,
                              const TileWin& W, int nworkers, float& s0, float& c0, float& s1, float& c1) {
   const int tid = threadIdx.x;
   const int G = gridDim.x;
   const int N = op.N;
   const int ntiles = 1 << (N - kTileBits);
+  const bool aux = !FIRST || c.use_prev;
+  const float2* asrc = FIRST ? qm : u;
   auto xof = [&](int t, int j) { return FIRST ? (t << kTileBits) | j : c_tile_x(W, t, j); };
-  auto load = [&](float2* buf, int t) {
-    for (int unit = tid; unit < kTileElems / 2; unit += nworkers) c_cp16(buf + 2 * unit, q + xof(t, 2 * unit));
+  auto load = [&](int slot, int t) {
+    float2* qb = buf + slot * kTileElems;
+    float2* ab = buf + (2 + slot) * kTileElems;
+    for (int unit = tid; unit < kTileElems / 2; unit += nworkers) {
+      const int x = xof(t, 2 * unit);
+      c_cp16(qb + 2 * unit, q + x);
+      if (aux) c_cp16(ab + 2 * unit, asrc + x);
+    }
     c_cp_commit();
   };
   int t = blockIdx.x;
-  if (t < ntiles) load(buf0, t);
+  if (t < ntiles) load(0, t);
   for (int k = 0; t < ntiles; ++k, t += G) {
-    const float2* cur = (k & 1) ? buf1 : buf0;
-    float2* nxt = (k & 1) ? buf0 : buf1;
+    const float2* cur = buf + (k & 1) * kTileElems;
+    const float2* acur = buf + (2 + (k & 1)) * kTileElems;
     c_cp_wait();
     c_workers_sync(nworkers);
-    if (t + G < ntiles) load(nxt, t + G);
+    if (t + G < ntiles) load((k + 1) & 1, t + G);
     for (int j = tid; j < kTileElems; j += nworkers) {
       const int x = xof(t, j);
       float ur, ui, hr = 0.f, hi = 0.f, fr = 0.f, fi = 0.f;
@@ -430,12 +442,12 @@ __device__ void c_tiled_pass(float2* buf0, float2* buf1, const OpSpinC& op, cons
           }
         }
         if (c.use_prev) {
-          const float2 w = qm[x];
+          const float2 w = acur[j];
           ur = fmaf(c.cp, w.x, ur);
           ui = fmaf(c.cp, w.y, ui);
         }
       } else {
-        const float2 a = u[x];
+        const float2 a = acur[j];
         ur = a.x;
         ui = a.y;
         const unsigned jh = (unsigned)j >> W.c;  // bits b0 .. b0+width-1 of x
@@ -510,8 +522,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
   if constexpr (FAMILY == kFamilySpin) {
     if (p.tiled) nwin = c_tiled_windows(op.N, win);
   }
-  float2* tbuf0 = reinterpret_cast<float2*>(smem_raw + ((sizeof(SmemC) + 127) & ~size_t(127)));
-  float2* tbuf1 = tbuf0 + kTileElems;
+  float2* tbuf = reinterpret_cast<float2*>(smem_raw + ((sizeof(SmemC) + 127) & ~size_t(127)));
   int wslot = 0;
   DevStatus* st = p.st;
   const bool glead = (blockIdx.x == 0) && lead;
@@ -620,12 +631,12 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
               if (p.tiled) {  // window passes, grid exchanges between them (control warp)
                 for (int w = 0; w < nwin; ++w) {
                   if (w == 0) {
-                    if (nwin == 1) c_tiled_pass<true, true>(tbuf0, tbuf1, op, c, S.bx, q, qm, u, win[0], wstep, s0, c0, s1, c1);
-                    else c_tiled_pass<true, false>(tbuf0, tbuf1, op, c, S.bx, q, qm, u, win[0], wstep, s0, c0, s1, c1);
+                    if (nwin == 1) c_tiled_pass<true, true>(tbuf, op, c, S.bx, q, qm, u, win[0], wstep, s0, c0, s1, c1);
+                    else c_tiled_pass<true, false>(tbuf, op, c, S.bx, q, qm, u, win[0], wstep, s0, c0, s1, c1);
                   } else if (w == nwin - 1) {
-                    c_tiled_pass<false, true>(tbuf0, tbuf1, op, c, S.bx, q, qm, u, win[w], wstep, s0, c0, s1, c1);
+                    c_tiled_pass<false, true>(tbuf, op, c, S.bx, q, qm, u, win[w], wstep, s0, c0, s1, c1);
                   } else {
-                    c_tiled_pass<false, false>(tbuf0, tbuf1, op, c, S.bx, q, qm, u, win[w], wstep, s0, c0, s1, c1);
+                    c_tiled_pass<false, false>(tbuf, op, c, S.bx, q, qm, u, win[w], wstep, s0, c0, s1, c1);
                   }
                   if (w + 1 < nwin) {
                     asm volatile("bar.sync 2;" ::: "memory");  // all threads: window w written
@@ -939,7 +950,9 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
 }
 
 // ------------------------------------------------------------------ launchers
-size_t c64_tiled_smem_bytes() { return ((sizeof(SmemC) + 127) & ~size_t(127)) + 2 * kTileElems * sizeof(float2); }
+size_t c64_tiled_smem_bytes() {
+  return ((sizeof(SmemC) + 127) & ~size_t(127)) + 4 * kTileElems * sizeof(float2);
+}
 
 template <int FAMILY, class Op>
 static int launch_prop_c64(const PropParams& p, const Op& op, int grid, int block, void* stream) {

@@ -220,10 +220,10 @@ def test_c64_full_size_atom_without_field_keeps_the_1s_state(torch_cuda):
 
 
 # ---------------------------------------------------------------- window-tiled apply
-# Long chains take the window-tiled apply (shared-memory tiles of 2^13
+# Long chains take the window-tiled apply (shared-memory tiles of 2^12
 # elements, one pass per window of index bits; the environment variable
 # CFET_C64_TILED forces it on or off when the context is created).  Chains of
-# 14..20 sites have two windows, 21..27 three, 28..30 four.
+# 13..19 sites have two windows, 20..26 three, 27..30 four.
 
 @pytest.mark.parametrize("N,nfields", [(13, 1), (14, 2), (16, 1), (17, 2)])
 def test_c64_tiled_matches_oracle(torch_cuda, monkeypatch, N, nfields):
@@ -250,10 +250,10 @@ def _one_magnon_hamiltonian(N, J, Delta, h):
     return H
 
 
-@pytest.mark.parametrize("N", [22, 23])
+@pytest.mark.parametrize("N", [22, 23, 27])
 def test_c64_tiled_one_magnon_sector_is_exact(torch_cuda, monkeypatch, N):
-    # without an x field the one-magnon sector is closed: a chain of 22 or 23
-    # sites (three windows) started with one spin down must follow the N x N
+    # without an x field the one-magnon sector is closed: a chain of 22, 23
+    # (three windows) or 27 sites (four) started with one spin down must follow the N x N
     # problem exactly and leave every other amplitude at zero; hops across all
     # window boundaries and the diagonal at every site enter
     from scipy.linalg import expm
