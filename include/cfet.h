@@ -174,13 +174,13 @@ typedef struct cfet_options {
  *                 threads.  psi stays complex128 at the boundary.  Results
  *                 carry FP32 rounding (relative ~1e-7 per stage exponential),
  *                 so Krylov tolerances below ~1e-7 no longer bound the
- *                 error; meant for targets of about 1e-6.  XXZ chains of 23
- *                 or more sites (vectors of 64 MiB and more, the basis far
- *                 beyond the 129 MB L2) apply H in passes over shared-memory
- *                 tiles of 2^12 elements, one per window of index bits; the
- *                 environment variable CFET_C64_TILED=0 or 1, read when the
- *                 context is created, forces the element-wise or the tiled
- *                 form (13..30 sites).                                      */
+ *                 error; meant for targets of about 1e-6.
+ * CFET_PREC_FX and CFET_PREC_C64 on XXZ chains of 23 or more sites (Krylov
+ * bases far beyond the 129 MB L2) apply H in passes over shared-memory tiles
+ * (2^11 fixed-point or 2^12 complex64 elements), one pass per window of index
+ * bits, instead of gathering far-bit neighbours from DRAM; the environment
+ * variable CFET_TILED=0 or 1, read when the context is created, forces the
+ * element-wise or the tiled form (13..30 sites).                            */
 enum { CFET_PREC_DEFAULT = 0, CFET_PREC_F64 = 1, CFET_PREC_FX = 2, CFET_PREC_C64 = 3 };
 
 /* How cfet_propagate evaluates each stage exponential exp(-i dt H_j) psi.

@@ -66,7 +66,7 @@ struct cfet_ctx {
   float* d_dz32 = nullptr;     // dz_lo | dz_hi in FP32
   float* d_val32 = nullptr;
   float2* d_qbasis32 = nullptr;
-  bool c64_tiled = false;      // window-tiled complex64 apply (long chains)
+  bool tiled = false;          // window-tiled apply (long chains, complex64 and fixed point)
   double* d_partials = nullptr;
   unsigned* d_bar = nullptr;
   DevStatus* d_st = nullptr;
@@ -294,7 +294,7 @@ PropParams base_params(cfet_ctx* ctx, double2* psi, double tau, double tol) {
   p.timeout_ns = (long long)(ctx->opt.barrier_timeout_s * 1e9);
   p.qbasis = ctx->d_qbasis;
   p.qbasis32 = ctx->d_qbasis32;
-  p.tiled = ctx->c64_tiled ? 1 : 0;
+  p.tiled = ctx->tiled ? 1 : 0;
   return p;
 }
 
@@ -801,17 +801,19 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
       dia_interval(o2.offsets, o2.values, o2.ndiag, dim, &ctx->op_lo[k + 1], &ctx->op_hi[k + 1]);
     }
   }
-  // long complex64 chains: the window-tiled apply (its tiles need 2^13 elements)
-  if (ctx->precision == CFET_PREC_C64 && family == kFamilySpin) {
-    const char* env = std::getenv("CFET_C64_TILED");
-    const bool want_tiled = env && *env ? std::atoi(env) != 0 : nsites >= kC64TiledMinSites;
-    ctx->c64_tiled = want_tiled && nsites >= 13 && nsites <= kC64TiledMaxSites;
+  // long chains: the window-tiled apply of the complex64 and fixed-point
+  // Krylov kernels (not the one-pass fixed-point form)
+  if (family == kFamilySpin && (ctx->precision == CFET_PREC_C64 || (ctx->precision == CFET_PREC_FX && !CFET_FX_ONEPASS))) {
+    const char* env = std::getenv("CFET_TILED");
+    const int min_sites = ctx->precision == CFET_PREC_C64 ? kC64TiledMinSites : kFxTiledMinSites;
+    const bool want_tiled = env && *env ? std::atoi(env) != 0 : nsites >= min_sites;
+    ctx->tiled = want_tiled && nsites >= kTiledMinSites && nsites <= kTiledMaxSites;
   }
   // persistent grid: co-resident maximum, no more CTAs than needed to give
   // every thread at least one element
   int maxg = ctx->precision == CFET_PREC_FX    ? (CFET_FX_ONEPASS ? max_coresident_blocks_fx1(family, ctx->block)
-                                                                  : max_coresident_blocks_fx(family, ctx->block))
-                   : ctx->precision == CFET_PREC_C64 ? max_coresident_blocks_c64(family, ctx->block, ctx->c64_tiled)
+                                                                  : max_coresident_blocks_fx(family, ctx->block, ctx->tiled))
+                   : ctx->precision == CFET_PREC_C64 ? max_coresident_blocks_c64(family, ctx->block, ctx->tiled)
                                                      : max_coresident_blocks(family, ctx->block);
   if (maxg < 1) {
     free_ctx(ctx);

@@ -133,7 +133,7 @@ struct PropParams {
   long long exp_base;    // global index of exponential 0 of this launch
   double tau, tol;
   int m_min, m_max, max_substeps;
-  int tiled;             // complex64 spin chains: window-tiled apply (kernels_c64.cu)
+  int tiled;             // spin chains: window-tiled apply (complex64 and fixed-point kernels)
   // decisions (device arrays, nullable)
   const int* f_nsub; const int* f_k; const int* f_h;
   int* r_nsub; int* r_k; int* r_h; long long r_cap;
@@ -228,14 +228,17 @@ int launch_propagate_dia_fx(const PropParams& p, const OpDiaFx& op, int grid, in
 int launch_propagate_spin_fx1(const PropParams& p, const OpSpinFx& op, int grid, int block, void* stream);
 int launch_propagate_dia_fx1(const PropParams& p, const OpDiaFx& op, int grid, int block, void* stream);
 int max_coresident_blocks_fx1(int family, int block);
-int max_coresident_blocks_fx(int family, int block);
+int max_coresident_blocks_fx(int family, int block, bool tiled);
 int launch_propagate_spin_c64(const PropParams& p, const OpSpinC& op, int grid, int block, void* stream);
 int launch_propagate_dia_c64(const PropParams& p, const OpDiaC& op, int grid, int block, void* stream);
 int max_coresident_blocks_c64(int family, int block, bool tiled);
-// Chains of at least this many sites take the window-tiled complex64 apply;
-// the environment variable CFET_C64_TILED (0 or 1) overrides the choice.
+// Chains of at least this many sites take the window-tiled apply
+// (tiled_common.cuh) in the complex64 and fixed-point kernels; the environment
+// variable CFET_TILED (0 or 1) overrides the choice when a context is created.
 constexpr int kC64TiledMinSites = 23;
-constexpr int kC64TiledMaxSites = 33;  // four windows of bits (tiles of 2^12)
+constexpr int kFxTiledMinSites = 23;
+constexpr int kTiledMinSites = 13;  // tiles of up to 2^12 elements
+constexpr int kTiledMaxSites = 30;  // four windows cover 32 sites at 2^11-element tiles
 int launch_adjoint_spin(const AdjParams& p, const OpSpin& op, int grid, int block, void* stream);
 int launch_wait_selftest(int which, unsigned long long* rec, unsigned* bar, int* status, long long timeout_ns);
 constexpr int kDiffBlocks = 152;  // blocks (partials) of the difference norm

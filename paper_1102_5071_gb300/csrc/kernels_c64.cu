@@ -33,6 +33,7 @@
 
 #include "cfet_internal.h"
 #include "device_common.cuh"
+#include "tiled_common.cuh"
 
 // Spin apply on two elements per thread and loop iteration (twice the
 // independent neighbour loads per warp; 1 = on).
@@ -328,54 +329,13 @@ __device__ double c_estimate(SmemC& S, int k, double ts) {
 }
 
 // ------------------------------------------------------------------ tiled apply (large chains)
-// For chains whose vectors leave L2 every far-bit neighbour gather of the
-// element-wise apply reads DRAM.  The tiled form splits the bits of the index
-// into windows and runs one pass per window over tiles of 2^B elements staged
-// in shared memory (cp.async, double-buffered): window 0 takes contiguous tiles
-// (bits 0..B-1: diagonal, previous vector, flips of bits 0..B-1, hops of bonds
-// (i, i+1), i <= B-2); window w >= 1 takes strided tiles made of 2^c contiguous
-// elements times the 2^width values of its bits [b0, b0 + width) (flips of bits
-// b0+1 .. b0+width-1, hops of bonds b0 .. b0+width-2), reads the partial u of
-// its elements, adds its terms and writes u back; the last window also takes
-// <q, u> and ||u||^2.  Windows are separated by grid-wide exchanges.
-// The vector each element reads for itself (q_{k-1} in window 0, the partial u
-// after it) is staged with the tile, so the loop touches global memory only to
-// store u: two q tiles and two such tiles of 2^12 elements (128 KB).
+// Window tiling of tiled_common.cuh.  The vector each element reads for
+// itself (q_{k-1} in window 0, the partial u after it) is staged with the
+// tile, so the loop touches global memory only to store u: two q tiles and two
+// such tiles of 2^12 complex64 elements (128 KB).  The last window also takes
+// <q, u> and ||u||^2.
 constexpr int kTileBits = 12;
 constexpr int kTileElems = 1 << kTileBits;
-constexpr int kHighWindow = 8;                // bits of a high window, its first shared with the window before
-constexpr int kTiledMaxWindows = 4;           // chains of up to B + 3 * 7 sites
-
-struct TileWin {
-  int b0, width, c;
-};
-
-__device__ __forceinline__ int c_tiled_windows(int N, TileWin (&W)[kTiledMaxWindows]) {
-  int n = 1;
-  for (int b0 = kTileBits - 1; b0 + 1 < N && n < kTiledMaxWindows; b0 += kHighWindow - 1, ++n) {
-    const int width = (N - b0) < kHighWindow ? (N - b0) : kHighWindow;
-    W[n].b0 = b0;
-    W[n].width = width;
-    W[n].c = kTileBits - width;
-  }
-  return n;
-}
-
-// element index of slot j of strided tile t of window W (N sites)
-__device__ __forceinline__ int c_tile_x(const TileWin& W, int t, int j) {
-  const int nb = W.b0 - W.c;  // bits [c, b0) come from t
-  const int tl = t & ((1 << nb) - 1), th = t >> nb;
-  return (j & ((1 << W.c) - 1)) | (tl << W.c) | ((j >> W.c) << W.b0) | (th << (W.b0 + W.width));
-}
-
-__device__ __forceinline__ void c_cp16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void c_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void c_cp_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-// barrier of the worker warps only (named barrier 1)
-__device__ __forceinline__ void c_workers_sync(int n) { asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory"); }
 
 // One window pass of this CTA's worker threads over its tiles.
 // buf: q tiles [2][kTileElems], then the staged own-element vector [2][kTileElems].
@@ -389,24 +349,24 @@ __device__ void c_tiled_pass(float2* buf, const OpSpinC& op, const CConst& c, co
   const int ntiles = 1 << (N - kTileBits);
   const bool aux = !FIRST || c.use_prev;
   const float2* asrc = FIRST ? qm : u;
-  auto xof = [&](int t, int j) { return FIRST ? (t << kTileBits) | j : c_tile_x(W, t, j); };
+  auto xof = [&](int t, int j) { return FIRST ? (t << kTileBits) | j : tile_x(W, t, j); };
   auto load = [&](int slot, int t) {
     float2* qb = buf + slot * kTileElems;
     float2* ab = buf + (2 + slot) * kTileElems;
     for (int unit = tid; unit < kTileElems / 2; unit += nworkers) {
       const int x = xof(t, 2 * unit);
-      c_cp16(qb + 2 * unit, q + x);
-      if (aux) c_cp16(ab + 2 * unit, asrc + x);
+      cp_async16(qb + 2 * unit, q + x);
+      if (aux) cp_async16(ab + 2 * unit, asrc + x);
     }
-    c_cp_commit();
+    cp_async_commit();
   };
   int t = blockIdx.x;
   if (t < ntiles) load(0, t);
   for (int k = 0; t < ntiles; ++k, t += G) {
     const float2* cur = buf + (k & 1) * kTileElems;
     const float2* acur = buf + (2 + (k & 1)) * kTileElems;
-    c_cp_wait();
-    c_workers_sync(nworkers);
+    cp_async_wait_all();
+    workers_sync(nworkers);
     if (t + G < ntiles) load((k + 1) & 1, t + G);
     for (int j = tid; j < kTileElems; j += nworkers) {
       const int x = xof(t, j);
@@ -488,11 +448,13 @@ __device__ void c_tiled_pass(float2* buf, const OpSpinC& op, const CConst& c, co
       }
     }
   }
-  c_cp_wait();
+  cp_async_wait_all();
 }
 
 // ------------------------------------------------------------------ the kernel
-template <int FAMILY, class Op>
+// TILED: the window-tiled apply of long spin chains (a separate instantiation,
+// so that the element-wise kernel carries none of its code).
+template <int FAMILY, class Op, bool TILED = false>
 __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropParams p, Op op) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmemC& S = *reinterpret_cast<SmemC*>(smem_raw);
@@ -516,11 +478,11 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
   unsigned long long* partB = partA + 6 * G;                                        // 1 sum: 2 words
   unsigned long long* partR = partA + 12 * G;                                       // 1 sum: 2 words
   unsigned long long* partW = partA + 18 * G;  // window barriers of the tiled apply: two 1-word slots
-  // tiled apply (spin chains with p.tiled): windows and the two tile buffers behind SmemC
+  // tiled apply: windows and the tile buffers behind SmemC
   TileWin win[kTiledMaxWindows] = {};
   int nwin = 1;
-  if constexpr (FAMILY == kFamilySpin) {
-    if (p.tiled) nwin = c_tiled_windows(op.N, win);
+  if constexpr (TILED) {
+    nwin = tiled_windows<kTileBits>(op.N, win);
   }
   float2* tbuf = reinterpret_cast<float2*>(smem_raw + ((sizeof(SmemC) + 127) & ~size_t(127)));
   int wslot = 0;
@@ -627,8 +589,8 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
             float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
             const long long tw0 = sm_clock();
             int x = wx0;
-            if constexpr (FAMILY == kFamilySpin) {
-              if (p.tiled) {  // window passes, grid exchanges between them (control warp)
+            if constexpr (TILED) {
+              {  // window passes, grid exchanges between them (control warp)
                 for (int w = 0; w < nwin; ++w) {
                   if (w == 0) {
                     if (nwin == 1) c_tiled_pass<true, true>(tbuf, op, c, S.bx, q, qm, u, win[0], wstep, s0, c0, s1, c1);
@@ -639,8 +601,8 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
                     c_tiled_pass<false, false>(tbuf, op, c, S.bx, q, qm, u, win[w], wstep, s0, c0, s1, c1);
                   }
                   if (w + 1 < nwin) {
-                    asm volatile("bar.sync 2;" ::: "memory");  // all threads: window w written
-                    asm volatile("bar.sync 3;" ::: "memory");  // all threads: the grid exchange passed
+                    window_written_sync();    // all threads: window w written
+                    window_exchanged_sync();  // all threads: the grid exchange passed
                   }
                 }
                 x = wxe;  // nothing left for the element loops
@@ -694,17 +656,17 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
               }
               __syncwarp();
             }
-            if constexpr (FAMILY == kFamilySpin) {
-              if (p.tiled) {  // grid exchanges between the window passes of the workers
+            if constexpr (TILED) {
+              {  // grid exchanges between the window passes of the workers
                 for (int w = 0; w + 1 < nwin; ++w) {
-                  asm volatile("bar.sync 2;" ::: "memory");
+                  window_written_sync();
                   double none[1];
                   const bool ok = !S.abort_flag && c_ctl_reduce<0>(S, NW, partW + (size_t)wslot * G, tag0 + (++gen),
                                                                    true, &st->status, p.timeout_ns, none, tacc[5]);
                   __syncwarp();
                   if (!ok && lane == 0) S.abort_flag = 1;
                   wslot ^= 1;
-                  asm volatile("bar.sync 3;" ::: "memory");
+                  window_exchanged_sync();
                 }
               }
             }
@@ -714,9 +676,9 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
             const long long tc0 = sm_clock(), sp0 = tacc[5];
             double sum[2];
             // (the tiled apply leaves u written by other CTAs: fence)
-            constexpr bool kMayTile = FAMILY == kFamilySpin;
+            constexpr bool kMayTile = TILED;
             if ((kMayTile && S.abort_flag) ||
-                !c_ctl_reduce<2>(S, NW, partA, tag0 + (++gen), kMayTile && p.tiled != 0, &st->status, p.timeout_ns,
+                !c_ctl_reduce<2>(S, NW, partA, tag0 + (++gen), kMayTile, &st->status, p.timeout_ns,
                                  sum, tacc[5])) {
               if (lane == 0) S.abort_flag = 1;
             } else if (lane == 0 && !S.stop_prev) {
@@ -966,6 +928,9 @@ static int launch_prop_c64(const PropParams& p, const Op& op, int grid, int bloc
   at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
+  if constexpr (FAMILY == kFamilySpin) {
+    if (p.tiled) return (int)cudaLaunchKernelEx(&cfg, k_propagate_c64<FAMILY, Op, true>, p, op);
+  }
   return (int)cudaLaunchKernelEx(&cfg, k_propagate_c64<FAMILY, Op>, p, op);
 }
 
@@ -984,12 +949,13 @@ int max_coresident_blocks_c64(int family, int block, bool tiled) {
   // asks for its tile buffers and gets the shared-memory split it needs)
   cudaFuncSetAttribute(k_propagate_c64<kFamilySpin, OpSpinC>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaFuncSetAttribute(k_propagate_c64<kFamilyDia, OpDiaC>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-  cudaFuncSetAttribute(k_propagate_c64<kFamilySpin, OpSpinC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_propagate_c64<kFamilySpin, OpSpinC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)c64_tiled_smem_bytes());
   cudaError_t e;
   if (family == kFamilySpin)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_c64<kFamilySpin, OpSpinC>, block,
-                                                      tiled ? c64_tiled_smem_bytes() : sizeof(SmemC));
+    e = tiled ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_c64<kFamilySpin, OpSpinC, true>, block,
+                                                              c64_tiled_smem_bytes())
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_c64<kFamilySpin, OpSpinC>, block, sizeof(SmemC));
   else
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_c64<kFamilyDia, OpDiaC>, block,
                                                       sizeof(SmemC));

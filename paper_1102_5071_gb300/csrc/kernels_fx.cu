@@ -37,6 +37,7 @@
 #include "cfet_internal.h"
 #include "device_common.cuh"
 #include "fx_common.cuh"
+#include "tiled_common.cuh"
 
 namespace cfet {
 
@@ -142,6 +143,145 @@ __device__ __forceinline__ void fx_worker_partial(SmemFx& S, __int128 acc, long 
   }
 }
 
+// Control warp: a grid-wide exchange of one tagged word per CTA (a barrier),
+// with the fences that make the vectors written before it visible after it.
+__device__ bool fx_ctl_barrier(unsigned long long* part, unsigned tag, int* status, long long timeout_ns,
+                               long long& spin) {
+  struct NoAcc {
+    __device__ void reset() {}
+    __device__ void add(const unsigned (&)[1]) {}
+  } acc;
+  const unsigned mine[1] = {0u};
+  return ctl_exchange<1>(part, mine, tag, true, status, timeout_ns, spin, acc);
+}
+
+// ------------------------------------------------------------------ tiled apply (long chains)
+// Window tiling of tiled_common.cuh with tiles of 2^11 elements (32 KB of
+// int64 pairs): two q tiles and two tiles of the vector each element reads
+// for itself (q_{k-1} in window 0, the partial u after it), 128 KB, staged by
+// cp.async and double-buffered.  Every window adds its terms in the format of
+// the apply above (exact integer neighbour sums, one rounded product per sum
+// and window), so the result differs from the element-wise apply by the
+// rounding of the extra products (units of the last place of u).  The last
+// window takes <q, u> exactly and max |u|.
+constexpr int kFxTileBits = 11;
+constexpr int kFxTileElems = 1 << kFxTileBits;
+
+size_t fx_tiled_smem_bytes();
+
+template <bool FIRST, bool LAST>
+__device__ void fx_tiled_pass(longlong2* buf, const OpSpinFx& op, const FxConstA& c, const long long* mb,
+                              const longlong2* __restrict__ q, const longlong2* __restrict__ qm,
+                              longlong2* __restrict__ u, const TileWin& W, int nworkers, __int128& a2,
+                              long long& mx) {
+  const int tid = threadIdx.x;
+  const int G = gridDim.x;
+  const int ntiles = 1 << (op.N - kFxTileBits);
+  const bool aux = !FIRST || c.use_prev;
+  const longlong2* asrc = FIRST ? qm : u;
+  auto xof = [&](int t, int j) { return FIRST ? (t << kFxTileBits) | j : tile_x(W, t, j); };
+  auto load = [&](int slot, int t) {
+    longlong2* qb = buf + slot * kFxTileElems;
+    longlong2* ab = buf + (2 + slot) * kFxTileElems;
+    for (int j = tid; j < kFxTileElems; j += nworkers) {
+      const int x = xof(t, j);
+      cp_async16(qb + j, q + x);
+      if (aux) cp_async16(ab + j, asrc + x);
+    }
+    cp_async_commit();
+  };
+  int t = blockIdx.x;
+  if (t < ntiles) load(0, t);
+  for (int k = 0; t < ntiles; ++k, t += G) {
+    const longlong2* cur = buf + (k & 1) * kFxTileElems;
+    const longlong2* acur = buf + (2 + (k & 1)) * kFxTileElems;
+    cp_async_wait_all();
+    workers_sync(nworkers);
+    if (t + G < ntiles) load((k + 1) & 1, t + G);
+    for (int j = tid; j < kFxTileElems; j += nworkers) {
+      const int x = xof(t, j);
+      long long ur, ui, hr = 0, hi = 0;
+      if (FIRST) {
+        const int L = op.lo_bits;
+        const long long dz = __ldg(op.DZ_lo + (x & ((1 << L) - 1))) + __ldg(op.DZ_hi + (x >> (L - 1)));
+        const long long Dp = fx_mulhi(c.m_cz, dz << 1) << 3;
+        const longlong2 v = cur[j];
+        ur = fx_mulhi(Dp, v.x << c.pk);
+        ui = fx_mulhi(Dp, v.y << c.pk);
+        const unsigned anti = ((unsigned)j ^ ((unsigned)j >> 1)) & ((1u << (kFxTileBits - 1)) - 1u);
+#pragma unroll
+        for (int i = 0; i < kFxTileBits - 1; ++i)
+          if ((anti >> i) & 1u) {
+            const longlong2 w = cur[j ^ (3 << i)];
+            hr += w.x;
+            hi += w.y;
+          }
+        if (op.uniform) {
+          long long xr = 0, xi = 0;
+#pragma unroll
+          for (int i = 0; i < kFxTileBits; ++i) {
+            const longlong2 w = cur[j ^ (1 << i)];
+            xr += w.x;
+            xi += w.y;
+          }
+          ur += fx_mulhi(c.m_x, xr << c.px);
+          ui += fx_mulhi(c.m_x, xi << c.px);
+        } else {
+#pragma unroll
+          for (int i = 0; i < kFxTileBits; ++i) {
+            const longlong2 w = cur[j ^ (1 << i)];
+            ur += fx_mulhi(mb[i], w.x << c.pk);
+            ui += fx_mulhi(mb[i], w.y << c.pk);
+          }
+        }
+        if (c.use_prev) {
+          const longlong2 w = acur[j];
+          ur += fx_mulhi(c.m_p, w.x << c.pp);
+          ui += fx_mulhi(c.m_p, w.y << c.pp);
+        }
+      } else {
+        const longlong2 a = acur[j];
+        ur = a.x;
+        ui = a.y;
+        const unsigned jh = (unsigned)j >> W.c;  // bits b0 .. b0+width-1 of x
+        const unsigned anti = (jh ^ (jh >> 1)) & ((1u << (W.width - 1)) - 1u);
+        for (int i = 0; i < W.width - 1; ++i)
+          if ((anti >> i) & 1u) {
+            const longlong2 w = cur[j ^ (3 << (W.c + i))];
+            hr += w.x;
+            hi += w.y;
+          }
+        if (op.uniform) {
+          long long xr = 0, xi = 0;
+          for (int i = 1; i < W.width; ++i) {
+            const longlong2 w = cur[j ^ (1 << (W.c + i))];
+            xr += w.x;
+            xi += w.y;
+          }
+          ur += fx_mulhi(c.m_x, xr << c.px);
+          ui += fx_mulhi(c.m_x, xi << c.px);
+        } else {
+          for (int i = 1; i < W.width; ++i) {
+            const longlong2 w = cur[j ^ (1 << (W.c + i))];
+            ur += fx_mulhi(mb[W.b0 + i], w.x << c.pk);
+            ui += fx_mulhi(mb[W.b0 + i], w.y << c.pk);
+          }
+        }
+      }
+      ur += fx_mulhi(c.m_hop, hr << c.ph);
+      ui += fx_mulhi(c.m_hop, hi << c.ph);
+      const longlong2 hv = make_longlong2(ur, ui);
+      u[x] = hv;
+      if (LAST) {
+        const longlong2 v = cur[j];
+        a2 += (__int128)v.x * hv.x + (__int128)v.y * hv.y;
+        mx = max(mx, fx_absmax(hv.x, hv.y));
+      }
+    }
+  }
+  cp_async_wait_all();
+}
+
 // Scalar part of the phase-A constants (one lane).
 template <int FAMILY, class Op>
 __device__ void fx_const_a_scalars(SmemFx& S, const Op& op, int it) {
@@ -233,7 +373,9 @@ __device__ double fx_estimate(SmemFx& S, int k, double ts) {
 }
 
 // ------------------------------------------------------------------ the kernel
-template <int FAMILY, class Op>
+// TILED: the window-tiled apply of long spin chains (a separate instantiation,
+// so that the element-wise kernel carries none of its code).
+template <int FAMILY, class Op, bool TILED = false>
 __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropParams p, Op op) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmemFx& S = *reinterpret_cast<SmemFx*>(smem_raw);
@@ -259,6 +401,15 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
   unsigned long long* partA = reinterpret_cast<unsigned long long*>(p.partials);
   unsigned long long* partB = partA + 8 * G;
   unsigned long long* partR = partA + 16 * G;
+  unsigned long long* partW = partA + 24 * G;  // window exchanges of the tiled apply: two 1-word slots
+  // tiled apply: windows and the tile buffers behind SmemFx
+  TileWin win[kTiledMaxWindows] = {};
+  int nwin = 1;
+  if constexpr (TILED) {
+    nwin = tiled_windows<kFxTileBits>(op.N, win);
+  }
+  longlong2* tbuf = reinterpret_cast<longlong2*>(smem_raw + ((sizeof(SmemFx) + 127) & ~size_t(127)));
+  int wslot = 0;
   DevStatus* st = p.st;
   const bool glead = (blockIdx.x == 0) && lead;
   // trace (see cfet_stats.phase_ns): worker loop times by thread 0, control
@@ -405,6 +556,25 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
             long long mx = 0;
             const long long tw0 = sm_clock();
             int x = wx0;
+            if constexpr (TILED) {
+              {  // window passes, grid exchanges between them (control warp)
+                for (int w = 0; w < nwin; ++w) {
+                  if (w == 0) {
+                    if (nwin == 1) fx_tiled_pass<true, true>(tbuf, op, c, S.mb, q, qm, u, win[0], wstep, a2, mx);
+                    else fx_tiled_pass<true, false>(tbuf, op, c, S.mb, q, qm, u, win[0], wstep, a2, mx);
+                  } else if (w == nwin - 1) {
+                    fx_tiled_pass<false, true>(tbuf, op, c, S.mb, q, qm, u, win[w], wstep, a2, mx);
+                  } else {
+                    fx_tiled_pass<false, false>(tbuf, op, c, S.mb, q, qm, u, win[w], wstep, a2, mx);
+                  }
+                  if (w + 1 < nwin) {
+                    window_written_sync();    // all threads: window w written
+                    window_exchanged_sync();  // all threads: the grid exchange passed
+                  }
+                }
+                x = wxe;  // nothing left for the element loops
+              }
+            }
 #if CFET_FX_PAIRS
             if constexpr (FAMILY == kFamilySpin) {
               for (; x + wstep < wxe; x += 2 * wstep) {
@@ -433,23 +603,42 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
               twe = sm_clock();
               tacc[0] += twe - tw0;
             }
-          } else if (pend) {
-            const long long te0 = sm_clock();
-            const double err = fx_estimate(S, it - 1, remaining);
-            if (lane == 0) {
-              S.err_prev = err;
-              S.stop_prev = err <= p.tol * remaining / p.tau;
-              S.y_ready = S.stop_prev;
-              tacc[6] += sm_clock() - te0;
+          } else {
+            if (pend) {
+              const long long te0 = sm_clock();
+              const double err = fx_estimate(S, it - 1, remaining);
+              if (lane == 0) {
+                S.err_prev = err;
+                S.stop_prev = err <= p.tol * remaining / p.tau;
+                S.y_ready = S.stop_prev;
+                tacc[6] += sm_clock() - te0;
+              }
+              __syncwarp();
             }
-            __syncwarp();
+            if constexpr (TILED) {
+              {  // grid exchanges between the window passes of the workers
+                for (int w = 0; w + 1 < nwin; ++w) {
+                  window_written_sync();
+                  const bool ok = !S.abort_flag && fx_ctl_barrier(partW + (size_t)wslot * G, tag0 + (++gen),
+                                                                  &st->status, p.timeout_ns, tacc[5]);
+                  __syncwarp();
+                  if (!ok && lane == 0) S.abort_flag = 1;
+                  wslot ^= 1;
+                  window_exchanged_sync();
+                }
+              }
+            }
           }
           __syncthreads();
           if (ctl) {
             const long long tc0 = sm_clock(), sp0 = tacc[5];
             double sum;
             long long mxi;
-            if (!fx_ctl_reduce(S, NW, partA, tag0 + (++gen), false, &st->status, p.timeout_ns, sum, mxi, tacc[5])) {
+            // (the tiled apply leaves u written by other CTAs: fence)
+            constexpr bool kMayTile = TILED;
+            if ((kMayTile && S.abort_flag) ||
+                !fx_ctl_reduce(S, NW, partA, tag0 + (++gen), kMayTile, &st->status, p.timeout_ns,
+                               sum, mxi, tacc[5])) {
               if (lane == 0) S.abort_flag = 1;
             } else if (lane == 0 && !S.stop_prev) {
               const double s_it = S.scale[it];
@@ -721,13 +910,16 @@ static int launch_prop_fx(const PropParams& p, const Op& op, int grid, int block
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = sizeof(SmemFx);
+  cfg.dynamicSmemBytes = p.tiled ? fx_tiled_smem_bytes() : sizeof(SmemFx);
   cfg.stream = (cudaStream_t)stream;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeCooperative;
   at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
+  if constexpr (FAMILY == kFamilySpin) {
+    if (p.tiled) return (int)cudaLaunchKernelEx(&cfg, k_propagate_fx<FAMILY, Op, true>, p, op);
+  }
   return (int)cudaLaunchKernelEx(&cfg, k_propagate_fx<FAMILY, Op>, p, op);
 }
 
@@ -738,18 +930,24 @@ int launch_propagate_dia_fx(const PropParams& p, const OpDiaFx& op, int grid, in
   return launch_prop_fx<kFamilyDia>(p, op, grid, block, stream);
 }
 
-int max_coresident_blocks_fx(int family, int block) {
+size_t fx_tiled_smem_bytes() { return ((sizeof(SmemFx) + 127) & ~size_t(127)) + 4 * kFxTileElems * sizeof(longlong2); }
+
+int max_coresident_blocks_fx(int family, int block, bool tiled) {
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  // the kernel needs only a few KB of shared memory: leave the rest of the
-  // unified L1/shared storage to L1, which holds each CTA's chunk
+  // the element-wise kernel needs only a few KB of shared memory: leave the
+  // rest of the unified L1/shared storage to L1, which holds each CTA's chunk
+  // (a tiled launch asks for its tile buffers and gets the split it needs)
   cudaFuncSetAttribute(k_propagate_fx<kFamilySpin, OpSpinFx>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaFuncSetAttribute(k_propagate_fx<kFamilyDia, OpDiaFx>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  cudaFuncSetAttribute(k_propagate_fx<kFamilySpin, OpSpinFx, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)fx_tiled_smem_bytes());
   cudaError_t e;
   if (family == kFamilySpin)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_fx<kFamilySpin, OpSpinFx>, block,
-                                                      sizeof(SmemFx));
+    e = tiled ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_fx<kFamilySpin, OpSpinFx, true>, block,
+                                                              fx_tiled_smem_bytes())
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_fx<kFamilySpin, OpSpinFx>, block, sizeof(SmemFx));
   else
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_fx<kFamilyDia, OpDiaFx>, block,
                                                       sizeof(SmemFx));

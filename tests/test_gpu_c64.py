@@ -222,12 +222,12 @@ def test_c64_full_size_atom_without_field_keeps_the_1s_state(torch_cuda):
 # ---------------------------------------------------------------- window-tiled apply
 # Long chains take the window-tiled apply (shared-memory tiles of 2^12
 # elements, one pass per window of index bits; the environment variable
-# CFET_C64_TILED forces it on or off when the context is created).  Chains of
+# CFET_TILED forces it on or off when the context is created).  Chains of
 # 13..19 sites have two windows, 20..26 three, 27..30 four.
 
 @pytest.mark.parametrize("N,nfields", [(13, 1), (14, 2), (16, 1), (17, 2)])
 def test_c64_tiled_matches_oracle(torch_cuda, monkeypatch, N, nfields):
-    monkeypatch.setenv("CFET_C64_TILED", "1")
+    monkeypatch.setenv("CFET_TILED", "1")
     prop, op, drives = _spin(N, nfields=nfields, m_max=16, max_substeps=200)
     err, same, st, aerr = _run(torch_cuda, prop, op, drives, W.random_state(11, 1 << N), 0.2, 0.05, 3, "CF6:5Opt",
                                1e-9, 16)
@@ -262,7 +262,7 @@ def test_c64_tiled_one_magnon_sector_is_exact(torch_cuda, monkeypatch, N):
     H6 = O.xxz_dense(6, 0.8, 0.6, h6)
     idx6 = [1 << k for k in range(6)]
     assert np.allclose(H6[np.ix_(idx6, idx6)], _one_magnon_hamiltonian(6, 0.8, 0.6, h6), atol=1e-14)
-    monkeypatch.setenv("CFET_C64_TILED", "1")
+    monkeypatch.setenv("CFET_TILED", "1")
     J, Dl = 0.8, 0.6
     h = W.uniform(4, N, -1, 1)
     prop = P.Propagator(P.XXZChain(N, J, Dl, h), [P.XField(N, np.zeros(N))], [lambda t: 0.0], m_max=24,
@@ -290,7 +290,7 @@ def test_c64_tiled_zero_coupling_factorises_n22(torch_cuda, monkeypatch):
     # per-site field coefficients, diagonal); sampled amplitudes against the
     # product of the oracle's single-site propagations
     import paper_1102_5071_gb300 as P
-    monkeypatch.setenv("CFET_C64_TILED", "1")
+    monkeypatch.setenv("CFET_TILED", "1")
     N = 22
     pr = W.spin_chain(N, J=0.0, Delta=0.0, A=1.3, omega=1.7)
     a1, a2 = W.uniform(21, N, 0.5, 1.5), W.uniform(22, N, -1, 1)
@@ -336,7 +336,7 @@ def test_c64_tiled_matches_elementwise_and_fixed_point_n22(torch_cuda, monkeypat
     _, log = fx.propagate(xf, 0.1, 0.04, 2, order=6, tol=1e-9, record=True)
     outs = {}
     for flag in ("1", "0"):
-        monkeypatch.setenv("CFET_C64_TILED", flag)
+        monkeypatch.setenv("CFET_TILED", flag)
         prop, _, _ = _spin(N, **kw)
         x = _dev(torch_cuda, psi0)
         st = prop.propagate(x, 0.1, 0.04, 2, order=6, tol=1e-9, forced=log)
