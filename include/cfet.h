@@ -81,7 +81,20 @@ enum {
    * terms with r + offsets[d] outside [0, dim) are absent.  uses dim, ndiag,
    * offsets[ndiag] (host, int64, copied), values[ndiag*dim] (host, copied,
    * row-aligned).  The caller guarantees the operator is symmetric.        */
-  CFET_OP_DIA = 3
+  CFET_OP_DIA = 3,
+  /* real combination of Pauli strings on a chain of nsites spins:
+   *   P = sum_t coeff[t] * i^popc(xmask[t] & zmask[t]) * X^xmask[t] Z^zmask[t]
+   * (X^x Z^z = product over the set bits; the phase makes every string a
+   * tensor product of X, Y = i X Z and Z on the sites of x | z, hence
+   * Hermitian); (P v)[y] = sum_t coeff[t] i^popc(x&z) (-1)^popc((y^x)&z)
+   * v[y ^ x].  uses nsites, dim = 2^nsites, nterms, xmask[nterms],
+   * zmask[nterms] (bits below nsites only), coeff[nterms] (host, copied).
+   * When H0 or any V_k is a Pauli sum, every operator of the context must be
+   * a Pauli sum, an XXZ chain or an X field of the same chain (the latter two
+   * are expanded into Pauli strings), the total number of strings is at most
+   * 4096, and the context computes in CFET_PREC_F64 (CFET_PREC_DEFAULT
+   * selects it; CFET_PREC_FX and CFET_PREC_C64 give CFET_EINVAL).           */
+  CFET_OP_PAULI = 4
 };
 
 typedef struct cfet_op {
@@ -93,6 +106,10 @@ typedef struct cfet_op {
   int32_t ndiag;              /* DIA: number of stored diagonals              */
   const int64_t* offsets;     /* DIA: offsets[ndiag] (host)                   */
   const double* values;       /* DIA: values[ndiag*dim] (host)                */
+  int32_t nterms;             /* PAULI: number of strings                     */
+  const uint64_t* xmask;      /* PAULI: X part of string t (host)             */
+  const uint64_t* zmask;      /* PAULI: Z part of string t (host)             */
+  const double* coeff;        /* PAULI: real coefficient of string t (host)   */
 } cfet_op;
 
 /* Drive f_k(t), called on the host only at the Gauss-Legendre nodes
@@ -154,7 +171,8 @@ typedef struct cfet_options {
                                 capped at the co-resident maximum)            */
   int32_t steps_per_launch;  /* CFET steps per persistent launch (0 = 256)    */
   double barrier_timeout_s;  /* device barrier wait limit (default 2.0 s)     */
-  int32_t precision;         /* CFET_PREC_* (default CFET_PREC_FX)            */
+  int32_t precision;         /* CFET_PREC_* (default CFET_PREC_DEFAULT: the
+                                fixed point, FP64 for Pauli sums)              */
   int32_t expm;              /* CFET_EXPM_* (default CFET_EXPM_KRYLOV)        */
   int32_t picture;           /* CFET_PICTURE_* (default SCHROEDINGER)         */
 } cfet_options;

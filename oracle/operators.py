@@ -110,6 +110,54 @@ class SpinChain:
         return out
 
 
+def pauli_ops(label):
+    """{site: letter} of a Pauli string given as a string over 'IXYZ'
+    (character i acts on site i) or as a dict {site: letter}."""
+    items = enumerate(label) if isinstance(label, str) else label.items()
+    out = {}
+    for site, letter in items:
+        letter = letter.upper()
+        if letter not in "IXYZ":
+            raise ValueError(f"unknown Pauli letter {letter!r}")
+        if letter != "I":
+            out[int(site)] = letter
+    return out
+
+
+def pauli_string_apply(v, N, ops):
+    """S v for the Pauli string S = product of the single-site operators in
+    ops ({site: letter}); they act on different sites, so their order is free."""
+    single = {"X": apply_x, "Y": apply_y, "Z": apply_z}
+    out = v
+    for site, letter in ops.items():
+        out = single[letter](out, site, N)
+    return out
+
+
+class PauliSum:
+    """H(t) = H0 + sum_k f_k(t) V_k with every operator a real combination of
+    Pauli strings on N spins: terms = [(c, label), ...] (label as in pauli_ops).
+    Real coefficients on tensor products of Hermitian Pauli matrices make every
+    operator Hermitian."""
+
+    def __init__(self, N, H0_terms, V_terms):
+        self.N = int(N)
+        self.dim = 1 << self.N
+        self.H0 = [(float(c), pauli_ops(lb)) for c, lb in H0_terms]
+        self.Vs = [[(float(c), pauli_ops(lb)) for c, lb in terms] for terms in V_terms]
+
+    @property
+    def nV(self):
+        return len(self.Vs)
+
+    def apply(self, coeffs, v):
+        out = np.zeros_like(v)
+        for k, terms in enumerate([self.H0] + self.Vs):
+            for c, ops in terms:
+                out = out + (coeffs[k] * c) * pauli_string_apply(v, self.N, ops)
+        return out
+
+
 class Banded:
     """H(t) = H0 + sum_k f_k(t) V_k with every operator in DIA form."""
 
@@ -185,4 +233,17 @@ def xfield_dense(N, a):
     H = np.zeros((1 << N, 1 << N), dtype=np.complex128)
     for i in range(N):
         H += a[i] * site_op(SX, i, N)
+    return H
+
+
+def pauli_dense(N, terms):
+    """Dense sum_t c_t S_t from Kronecker products of the 2x2 Pauli matrices
+    (independent of the bit formulas of pauli_string_apply)."""
+    mats = {"X": SX, "Y": SY, "Z": SZ}
+    H = np.zeros((1 << N, 1 << N), dtype=np.complex128)
+    for c, label in terms:
+        S = np.eye(1 << N, dtype=np.complex128)
+        for site, letter in pauli_ops(label).items():
+            S = S @ site_op(mats[letter], site, N)
+        H += c * S
     return H

@@ -43,6 +43,38 @@ class XField:
     a: np.ndarray
 
 
+class PauliSum:
+    """P = sum_t c_t S_t on a chain of N spins, every S_t a tensor product of
+    X, Y, Z on some sites (a Pauli string).  terms: (c, label) pairs with label
+    a string over 'IXYZ' whose character i acts on site i (site 0 first), or a
+    dict {site: 'X' | 'Y' | 'Z'}.  Passed to the library as X and Z bit masks
+    with Y_i = i X_i Z_i (the phase i^popc(x & z) of the C ABI)."""
+
+    def __init__(self, N, terms):
+        self.N = int(N)
+        xs, zs, cs = [], [], []
+        for c, label in terms:
+            ops = dict(enumerate(label)) if isinstance(label, str) else dict(label)
+            x = z = 0
+            for site, letter in ops.items():
+                site = int(site)
+                if not 0 <= site < self.N:
+                    raise ValueError(f"site {site} outside the chain of {self.N}")
+                letter = letter.upper()
+                if letter in ("X", "Y"):
+                    x |= 1 << site
+                if letter in ("Z", "Y"):
+                    z |= 1 << site
+                if letter not in ("I", "X", "Y", "Z"):
+                    raise ValueError(f"unknown Pauli letter {letter!r}")
+            xs.append(x)
+            zs.append(z)
+            cs.append(float(c))
+        self.xmask = np.array(xs, dtype=np.uint64)
+        self.zmask = np.array(zs, dtype=np.uint64)
+        self.coeff = np.array(cs, dtype=np.float64)
+
+
 @dataclass
 class DIA:
     """(D v)[r] = sum_d values[d, r] v[r + offsets[d]] (real, symmetric)."""
@@ -70,6 +102,13 @@ def _op_struct(op, keep):
         s.kind, s.dim, s.ndiag = _capi.CFET_OP_DIA, val.shape[1], val.shape[0]
         s.offsets = off.ctypes.data_as(_capi.c_int64_p)
         s.values = val.ctypes.data_as(_capi.c_double_p)
+    elif isinstance(op, PauliSum):
+        xm, zm, c = (np.ascontiguousarray(a) for a in (op.xmask, op.zmask, op.coeff))
+        keep += [xm, zm, c]
+        s.kind, s.nsites, s.dim, s.nterms = _capi.CFET_OP_PAULI, op.N, 1 << op.N, len(c)
+        s.xmask = xm.ctypes.data_as(_capi.c_uint64_p)
+        s.zmask = zm.ctypes.data_as(_capi.c_uint64_p)
+        s.coeff = c.ctypes.data_as(_capi.c_double_p)
     else:
         raise TypeError(f"unsupported operator {type(op).__name__}")
     return s
@@ -519,5 +558,6 @@ def build():
     return _b()
 
 
-__all__ = ["Propagator", "BatchPropagator", "Chain", "fidelity_loss", "XXZChain", "XField", "DIA", "scheme_info", "CfetError",
+__all__ = ["Propagator", "BatchPropagator", "Chain", "fidelity_loss", "XXZChain", "XField", "DIA", "PauliSum",
+           "scheme_info", "CfetError",
            "SCHEME_IDS", "build"]

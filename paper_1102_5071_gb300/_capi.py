@@ -14,7 +14,8 @@ c_int64_p = C.POINTER(C.c_int64)
 CFET_OK, CFET_EINVAL, CFET_ENOMEM, CFET_ECUDA, CFET_EKRYLOV, CFET_ETIMEOUT, CFET_ENAN, CFET_ENODEV = range(8)
 STATUS_NAMES = ["CFET_OK", "CFET_EINVAL", "CFET_ENOMEM", "CFET_ECUDA", "CFET_EKRYLOV", "CFET_ETIMEOUT",
                 "CFET_ENAN", "CFET_ENODEV"]
-CFET_OP_XXZ_CHAIN, CFET_OP_X_FIELD, CFET_OP_DIA = 1, 2, 3
+CFET_OP_XXZ_CHAIN, CFET_OP_X_FIELD, CFET_OP_DIA, CFET_OP_PAULI = 1, 2, 3, 4
+c_uint64_p = C.POINTER(C.c_uint64)
 
 SCHEME_IDS = {"CF2:1": 1, "CF4:2": 2, "CF4:3": 3, "CF4:3Opt": 4, "CF6:4": 5, "CF6:5": 6, "CF6:5b": 7,
               "CF6:6": 8, "CF6:5Imp": 9, "CF6:5Opt": 10, "CF6:6Opt": 11, "CF8:11": 12}
@@ -23,7 +24,8 @@ SCHEME_IDS = {"CF2:1": 1, "CF4:2": 2, "CF4:3": 3, "CF4:3Opt": 4, "CF6:4": 5, "CF
 class cfet_op(C.Structure):
     _fields_ = [("kind", C.c_int32), ("nsites", C.c_int32), ("dim", C.c_int64), ("J", C.c_double),
                 ("Delta", C.c_double), ("site_coeff", c_double_p), ("ndiag", C.c_int32),
-                ("offsets", c_int64_p), ("values", c_double_p)]
+                ("offsets", c_int64_p), ("values", c_double_p), ("nterms", C.c_int32),
+                ("xmask", c_uint64_p), ("zmask", c_uint64_p), ("coeff", c_double_p)]
 
 
 class cfet_options(C.Structure):

@@ -67,6 +67,9 @@ struct cfet_ctx {
   float* d_val32 = nullptr;
   float2* d_qbasis32 = nullptr;
   bool tiled = false;          // window-tiled apply (long chains, complex64 and fixed point)
+  // Pauli-sum family (FP64): strings grouped by X mask
+  OpPauli pauli{};
+  void* d_pauli = nullptr;     // one allocation: gx | gstart | tz | top | tc | tim
   double* d_partials = nullptr;
   unsigned* d_bar = nullptr;
   DevStatus* d_st = nullptr;
@@ -171,6 +174,7 @@ void free_ctx(cfet_ctx* c) {
   cudaFree(c->d_adj_ckpt); cudaFree(c->d_adj_vec); cudaFree(c->d_adj_part); cudaFree(c->d_adj_tab);
   cudaFree(c->d_adj_seg); cudaFree(c->d_adj_acc);
   cudaFree(c->d_ts); cudaFree(c->d_ts_part);
+  cudaFree(c->d_pauli);
   if (c->h_st) cudaFreeHost(c->h_st);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   delete c;
@@ -241,6 +245,8 @@ cfet_status launch_chunk(cfet_ctx* ctx, const PropParams& base, long long e0, lo
   else if (ctx->precision == CFET_PREC_C64)
     e = ctx->family == kFamilySpin ? launch_propagate_spin_c64(p, ctx->spin_c, ctx->grid, ctx->block, s)
                                    : launch_propagate_dia_c64(p, ctx->dia_c, ctx->grid, ctx->block, s);
+  else if (ctx->family == kFamilyPauli)
+    e = launch_propagate_pauli(p, ctx->pauli, ctx->grid, ctx->block, s);
   else
     e = ctx->family == kFamilySpin ? launch_propagate_spin(p, ctx->spin, ctx->grid, ctx->block, s)
                                    : launch_propagate_dia(p, ctx->dia, ctx->grid, ctx->block, s);
@@ -494,7 +500,7 @@ void cfet_options_default(cfet_options* opt) {
   opt->grid_size = 0;
   opt->steps_per_launch = 256;
   opt->barrier_timeout_s = 2.0;
-  opt->precision = CFET_PREC_FX;
+  opt->precision = CFET_PREC_DEFAULT;  // fixed point; FP64 for Pauli sums
   opt->expm = CFET_EXPM_KRYLOV;
   opt->picture = CFET_PICTURE_SCHROEDINGER;
 }
@@ -543,7 +549,12 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
   if (o.m_max < 1 || o.m_max > kMaxKrylov) return fail(nullptr, CFET_EINVAL, "m_max must be in [1, 64]");
   if (o.m_min < 1 || o.m_min > o.m_max) return fail(nullptr, CFET_EINVAL, "m_min must be in [1, m_max]");
   if (o.max_substeps < 1) return fail(nullptr, CFET_EINVAL, "max_substeps must be >= 1");
-  if (o.precision == CFET_PREC_DEFAULT) o.precision = CFET_PREC_FX;
+  // a Pauli sum anywhere makes the context a Pauli-sum context (FP64 only)
+  bool pauli = H0->kind == CFET_OP_PAULI;
+  for (int k = 0; k < nV; ++k) pauli = pauli || V[k].kind == CFET_OP_PAULI;
+  if (o.precision == CFET_PREC_DEFAULT) o.precision = pauli ? CFET_PREC_F64 : CFET_PREC_FX;
+  if (pauli && o.precision != CFET_PREC_F64)
+    return fail(nullptr, CFET_EINVAL, "Pauli-sum operators compute in CFET_PREC_F64 only");
   if (o.precision != CFET_PREC_F64 && o.precision != CFET_PREC_FX && o.precision != CFET_PREC_C64)
     return fail(nullptr, CFET_EINVAL, "precision must be CFET_PREC_F64, CFET_PREC_FX or CFET_PREC_C64");
   if (o.expm != CFET_EXPM_KRYLOV && o.expm != CFET_EXPM_CHEBYSHEV)
@@ -553,7 +564,7 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
   if (o.picture != CFET_PICTURE_SCHROEDINGER && o.picture != CFET_PICTURE_INTERACTION)
     return fail(nullptr, CFET_EINVAL, "picture must be CFET_PICTURE_SCHROEDINGER or CFET_PICTURE_INTERACTION");
   if (o.picture == CFET_PICTURE_INTERACTION &&
-      (o.precision != CFET_PREC_F64 || o.expm != CFET_EXPM_KRYLOV || H0->kind != CFET_OP_XXZ_CHAIN))
+      (o.precision != CFET_PREC_F64 || o.expm != CFET_EXPM_KRYLOV || H0->kind != CFET_OP_XXZ_CHAIN || pauli))
     return fail(nullptr, CFET_EINVAL, "CFET_PICTURE_INTERACTION requires an XXZ chain, CFET_PREC_F64 and CFET_EXPM_KRYLOV");
   if (o.block_size == 0) o.block_size = (o.precision == CFET_PREC_F64) ? 256 : 384;
   {
@@ -571,7 +582,56 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
 
 
   int family = 0, dim = 0, nsites = 0;
-  if (H0->kind == CFET_OP_XXZ_CHAIN) {
+  // Pauli-sum family: every operator expanded into strings (x, z, coefficient, operator)
+  struct PString {
+    unsigned x, z;
+    double c;
+    int op;
+  };
+  std::vector<PString> strings;
+  if (pauli) {
+    family = kFamilyPauli;
+    nsites = H0->nsites;
+    if (nsites < 1 || nsites > kMaxSites) return fail(nullptr, CFET_EINVAL, "nsites must be in [1, 30]");
+    for (int k = -1; k < nV; ++k) {
+      const cfet_op& o2 = k < 0 ? *H0 : V[k];
+      if (o2.nsites != nsites || o2.dim != (int64_t(1) << nsites))
+        return fail(nullptr, CFET_EINVAL, "Pauli sums: every operator on the same chain, dim = 2^nsites");
+      const int oi = k + 1;
+      if (o2.kind == CFET_OP_PAULI) {
+        if (o2.nterms < 0 || (o2.nterms > 0 && (!o2.xmask || !o2.zmask || !o2.coeff)))
+          return fail(nullptr, CFET_EINVAL, "Pauli sum: nterms < 0 or missing arrays");
+        for (int t = 0; t < o2.nterms; ++t) {
+          if ((o2.xmask[t] | o2.zmask[t]) >> nsites) return fail(nullptr, CFET_EINVAL, "Pauli sum: mask beyond nsites");
+          if (!is_finite_d(o2.coeff[t])) return fail(nullptr, CFET_EINVAL, "Pauli sum: coefficient not finite");
+          strings.push_back({(unsigned)o2.xmask[t], (unsigned)o2.zmask[t], o2.coeff[t], oi});
+        }
+      } else if (o2.kind == CFET_OP_XXZ_CHAIN) {
+        if (!o2.site_coeff || !is_finite_d(o2.J) || !is_finite_d(o2.Delta))
+          return fail(nullptr, CFET_EINVAL, "XXZ chain: missing or non-finite parameters");
+        for (int i = 0; i + 1 < nsites; ++i) {
+          const unsigned b = 3u << i;
+          strings.push_back({b, 0u, o2.J, oi});              // X_i X_{i+1}
+          strings.push_back({b, b, o2.J, oi});               // Y_i Y_{i+1} = i^2 X X Z Z
+          strings.push_back({0u, b, o2.J * o2.Delta, oi});   // Z_i Z_{i+1}
+        }
+        for (int i = 0; i < nsites; ++i) {
+          if (!is_finite_d(o2.site_coeff[i])) return fail(nullptr, CFET_EINVAL, "XXZ chain: h not finite");
+          strings.push_back({0u, 1u << i, o2.site_coeff[i], oi});
+        }
+      } else if (o2.kind == CFET_OP_X_FIELD) {
+        if (!o2.site_coeff) return fail(nullptr, CFET_EINVAL, "X field: site_coeff is NULL");
+        for (int i = 0; i < nsites; ++i) {
+          if (!is_finite_d(o2.site_coeff[i])) return fail(nullptr, CFET_EINVAL, "X field coefficient not finite");
+          strings.push_back({1u << i, 0u, o2.site_coeff[i], oi});
+        }
+      } else {
+        return fail(nullptr, CFET_EINVAL, "Pauli sums combine only with XXZ chains and X fields");
+      }
+    }
+    if (strings.size() > (size_t)kMaxPauliTerms) return fail(nullptr, CFET_EINVAL, "Pauli sums: more than 4096 strings");
+    dim = 1 << nsites;
+  } else if (H0->kind == CFET_OP_XXZ_CHAIN) {
     family = kFamilySpin;
     nsites = H0->nsites;
     if (nsites < 1 || nsites > kMaxSites) return fail(nullptr, CFET_EINVAL, "nsites must be in [1, 30]");
@@ -606,7 +666,7 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
     }
     if (total > kMaxDiag) return fail(nullptr, CFET_EINVAL, "DIA: more than 32 diagonals in total");
   } else {
-    return fail(nullptr, CFET_EINVAL, "H0 must be an XXZ chain or a DIA operator");
+    return fail(nullptr, CFET_EINVAL, "H0 must be an XXZ chain, a Pauli sum or a DIA operator");
   }
   {
     cfet_status s = device_available(nullptr);
@@ -639,6 +699,57 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
     }                                                            \
   } while (0)
 
+  if (family == kFamilyPauli) {
+    // group the strings by X mask (stable: the order within a group is the input order)
+    std::stable_sort(strings.begin(), strings.end(), [](const PString& a, const PString& b) { return a.x < b.x; });
+    const int nt = (int)strings.size();
+    std::vector<unsigned> gx, tz(nt);
+    std::vector<int> gstart, top(nt);
+    std::vector<double> tc(nt);
+    std::vector<unsigned char> tim(nt);
+    for (int t = 0; t < nt; ++t) {
+      const PString& ps = strings[t];
+      if (t == 0 || ps.x != strings[t - 1].x) {
+        gx.push_back(ps.x);
+        gstart.push_back(t);
+      }
+      const int ph = __builtin_popcount(ps.x & ps.z) & 3;  // the string's phase i^ph
+      tz[t] = ps.z;
+      top[t] = ps.op;
+      tc[t] = ph >= 2 ? -ps.c : ps.c;
+      tim[t] = (unsigned char)(ph & 1);
+    }
+    gstart.push_back(nt);
+    const int ng = (int)gx.size();
+    // one allocation, 8-byte aligned pieces
+    const size_t o_gx = 0, o_gs = o_gx + 8 * ((ng * sizeof(unsigned) + 7) / 8);
+    const size_t o_tz = o_gs + 8 * (((ng + 1) * sizeof(int) + 7) / 8);
+    const size_t o_top = o_tz + 8 * ((nt * sizeof(unsigned) + 7) / 8);
+    const size_t o_tc = o_top + 8 * ((nt * sizeof(int) + 7) / 8);
+    const size_t o_tim = o_tc + (size_t)nt * sizeof(double);
+    const size_t bytes = o_tim + (size_t)nt + 8;
+    std::vector<unsigned char> blob(bytes, 0);
+    if (ng) std::memcpy(blob.data() + o_gx, gx.data(), ng * sizeof(unsigned));
+    std::memcpy(blob.data() + o_gs, gstart.data(), (ng + 1) * sizeof(int));
+    if (nt) {
+      std::memcpy(blob.data() + o_tz, tz.data(), nt * sizeof(unsigned));
+      std::memcpy(blob.data() + o_top, top.data(), nt * sizeof(int));
+      std::memcpy(blob.data() + o_tc, tc.data(), nt * sizeof(double));
+      std::memcpy(blob.data() + o_tim, tim.data(), nt);
+    }
+    CKC(cudaMalloc(&ctx->d_pauli, bytes), "cudaMalloc(Pauli tables)");
+    CKC(cudaMemcpy(ctx->d_pauli, blob.data(), bytes, cudaMemcpyHostToDevice), "upload Pauli tables");
+    unsigned char* base = (unsigned char*)ctx->d_pauli;
+    ctx->pauli.N = nsites;
+    ctx->pauli.ngroups = ng;
+    ctx->pauli.nterms = nt;
+    ctx->pauli.gx = (const unsigned*)(base + o_gx);
+    ctx->pauli.gstart = (const int*)(base + o_gs);
+    ctx->pauli.tz = (const unsigned*)(base + o_tz);
+    ctx->pauli.top = (const int*)(base + o_top);
+    ctx->pauli.tc = (const double*)(base + o_tc);
+    ctx->pauli.tim = base + o_tim;
+  }
   if (family == kFamilySpin) {
     const int N = nsites;
     const int L = N < 10 ? N : 10;
@@ -715,7 +826,7 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
     ctx->ip_h.assign(H0->site_coeff, H0->site_coeff + N);
     ctx->ip_xf = xf;
     for (int k = 0; k < nV; ++k) xfield_interval(N, V[k].site_coeff, &ctx->op_lo[1 + k], &ctx->op_hi[1 + k]);
-  } else {
+  } else if (family == kFamilyDia) {
     std::vector<long long> off;
     std::vector<int> opidx;
     for (int k = -1; k < nV; ++k) {
@@ -814,6 +925,7 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
   int maxg = ctx->precision == CFET_PREC_FX    ? (CFET_FX_ONEPASS ? max_coresident_blocks_fx1(family, ctx->block)
                                                                   : max_coresident_blocks_fx(family, ctx->block, ctx->tiled))
                    : ctx->precision == CFET_PREC_C64 ? max_coresident_blocks_c64(family, ctx->block, ctx->tiled)
+                   : family == kFamilyPauli          ? max_coresident_blocks_pauli(ctx->block, ctx->pauli.nterms)
                                                      : max_coresident_blocks(family, ctx->block);
   if (maxg < 1) {
     free_ctx(ctx);
@@ -896,6 +1008,8 @@ cfet_status cfet_apply(cfet_ctx* ctx, const double* c, const void* v_in, void* v
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   int e = ctx->family == kFamilySpin
               ? launch_apply_spin(ctx->spin, ctx->dim, c, ctx->nV, (const double2*)v_in, (double2*)v_out, stream)
+          : ctx->family == kFamilyPauli
+              ? launch_apply_pauli(ctx->pauli, ctx->dim, c, ctx->nV, (const double2*)v_in, (double2*)v_out, stream)
               : launch_apply_dia(ctx->dia, ctx->dim, c, ctx->nV, (const double2*)v_in, (double2*)v_out, stream);
   if (e != cudaSuccess) return cuda_fail(ctx, (cudaError_t)e, "apply kernel launch");
   return CFET_OK;

@@ -70,6 +70,24 @@ struct OpSpinIP {
   const double2* w;    // [nexp of the call][nw] (global exponential index)
 };
 
+// Pauli-sum family (FP64 kernel): the strings of all operators grouped by
+// their X mask; string t of group g contributes
+//   pc[t] (-1)^popc((y ^ gx[g]) & tz[t]) (i if tim[t]) v[y ^ gx[g]]
+// with pc[t] = c_{top[t]} tc[t] for the stage scalars c (tc folds the sign of
+// i^popc(x&z) into the coefficient, tim marks an odd popcount).
+constexpr int kMaxPauliTerms = 4096;
+struct OpPauli {
+  int N;
+  int ngroups;
+  int nterms;
+  const unsigned* gx;        // [ngroups]
+  const int* gstart;         // [ngroups + 1]
+  const unsigned* tz;        // [nterms]
+  const int* top;            // [nterms]: 0 = H0, 1 + k = V_k
+  const double* tc;          // [nterms]
+  const unsigned char* tim;  // [nterms]
+};
+
 // Banded family: all operators in DIA form, concatenated.
 struct OpDia {
   int ndiag;
@@ -211,6 +229,10 @@ int launch_propagate_spin(const PropParams& p, const OpSpin& op, int grid, int b
 int launch_propagate_dia(const PropParams& p, const OpDia& op, int grid, int block, void* stream);
 int launch_propagate_spin_ip(const PropParams& p, const OpSpinIP& op, int grid, int block, void* stream);
 int max_coresident_blocks_ip(int block, int nw);
+int launch_propagate_pauli(const PropParams& p, const OpPauli& op, int grid, int block, void* stream);
+int max_coresident_blocks_pauli(int block, int nterms);
+int launch_apply_pauli(const OpPauli& op, int dim, const double* c, int nV, const double2* vin, double2* vout,
+                       void* stream);
 // psi[x] *= exp(i sign d(x) t[which]) with d the diagonal of the XXZ chain H0
 int launch_phase_diag(double2* psi, const OpSpin& op, int dim, const double* t, int which, double sign, void* stream);
 int launch_apply_spin(const OpSpin& op, int dim, const double* c, int nV, const double2* vin, double2* vout,
@@ -247,6 +269,6 @@ int max_coresident_blocks_adjoint(int block);
 int max_coresident_blocks(int family, int block);  // per device, for the persistent kernel
 size_t propagate_smem_bytes(int block);
 
-enum Family { kFamilySpin = 1, kFamilyDia = 2, kFamilySpinIP = 3 };
+enum Family { kFamilySpin = 1, kFamilyDia = 2, kFamilySpinIP = 3, kFamilyPauli = 4 };
 
 }  // namespace cfet

@@ -46,6 +46,29 @@ __device__ __forceinline__ double2 apply_dia_at(const double2* q, int r, int dim
   return acc;
 }
 
+// Pauli-sum family at index y: for every group of strings with X mask xm,
+// the partner y ^ xm weighted by sum_t pc[t] (-1)^popc((y ^ xm) & z_t), with
+// the strings of odd popc(x & z) contributing an imaginary weight (the phase
+// i^popc(x & z) of the string; its sign is folded into pc).
+__device__ __forceinline__ double2 apply_pauli_at(const double2* q, int y, const OpPauli& op, const double* pc) {
+  double ar = 0.0, ai = 0.0;
+  int t = __ldg(op.gstart);
+  for (int g = 0; g < op.ngroups; ++g) {
+    const unsigned b = (unsigned)y ^ __ldg(op.gx + g);
+    const int t1 = __ldg(op.gstart + g + 1);
+    double cr = 0.0, ci = 0.0;
+    for (; t < t1; ++t) {
+      const double c = (__popc(b & __ldg(op.tz + t)) & 1) ? -pc[t] : pc[t];
+      if (__ldg(op.tim + t)) ci += c;
+      else cr += c;
+    }
+    const double2 w = q[b];
+    ar = fma(cr, w.x, fma(-ci, w.y, ar));
+    ai = fma(cr, w.y, fma(ci, w.x, ai));
+  }
+  return make_double2(ar, ai);
+}
+
 // Interaction-picture spin apply at index x (OpSpinIP): sum over the single
 // flips and the antiparallel-bond hops of x of the stage weight of the local
 // spin configuration times the partner's amplitude (complex products).
@@ -160,6 +183,11 @@ __global__ void __launch_bounds__(256) k_propagate(PropParams p, Op op) {
       }
       __syncthreads();
     }
+    if constexpr (FAMILY == kFamilyPauli) {  // string coefficients c_{top[t]} tc[t] of this exponential
+      double* pc = reinterpret_cast<double*>(smem_raw + ip_table_offset<SmemLayout>());
+      for (int t = tid; t < op.nterms; t += blockDim.x) pc[t] = S.scal[__ldg(op.top + t)] * __ldg(op.tc + t);
+      __syncthreads();
+    }
     if constexpr (FAMILY == kFamilySpinIP) {  // this exponential's stage weights
       double2* Wt = reinterpret_cast<double2*>(smem_raw + ip_table_offset<SmemLayout>());
       const double2* src = op.w + (size_t)(p.exp_base + e) * op.nw;
@@ -215,6 +243,21 @@ __global__ void __launch_bounds__(256) k_propagate(PropParams p, Op op) {
             sc.cxx = S.scal[0] * s_it * op.J2;
             for (int x = x0; x < dim; x += stride) {
               double2 hv = apply_spin_at(q, x, op, sc, S.bsite);
+              if (qm) {
+                const double2 w = qm[x];
+                hv.x = fma(-bm, w.x, hv.x);
+                hv.y = fma(-bm, w.y, hv.y);
+              }
+              u[x] = hv;
+              const double2 v = q[x];
+              acc = fma(v.x, hv.x, fma(v.y, hv.y, acc));
+            }
+          } else if constexpr (FAMILY == kFamilyPauli) {
+            const double* pc = reinterpret_cast<const double*>(smem_raw + ip_table_offset<SmemLayout>());
+            for (int x = x0; x < dim; x += stride) {
+              double2 hv = apply_pauli_at(q, x, op, pc);
+              hv.x *= s_it;
+              hv.y *= s_it;
               if (qm) {
                 const double2 w = qm[x];
                 hv.x = fma(-bm, w.x, hv.x);
@@ -422,7 +465,10 @@ template <int FAMILY, class Op>
 __global__ void k_apply(Op op, int dim, Coefs c, int nV, const double2* __restrict__ vin, double2* __restrict__ vout) {
   __shared__ double bsite[kMaxSites];
   __shared__ double copf[1 + kMaxDrives];
-  if constexpr (FAMILY == kFamilySpin) {
+  extern __shared__ double pc[];  // Pauli family: string coefficients
+  if constexpr (FAMILY == kFamilyPauli) {
+    for (int t = threadIdx.x; t < op.nterms; t += blockDim.x) pc[t] = c.c[op.top[t]] * op.tc[t];
+  } else if constexpr (FAMILY == kFamilySpin) {
     if (threadIdx.x < (unsigned)op.N) {
       double bi = 0.0;
       for (int k = 0; k < nV; ++k) bi = fma(c.c[1 + k], op.xf[k * op.N + threadIdx.x], bi);
@@ -439,6 +485,8 @@ __global__ void k_apply(Op op, int dim, Coefs c, int nV, const double2* __restri
       sc.cz = c.c[0];
       sc.cxx = c.c[0] * op.J2;
       vout[x] = apply_spin_at(vin, x, op, sc, bsite);
+    } else if constexpr (FAMILY == kFamilyPauli) {
+      vout[x] = apply_pauli_at(vin, x, op, pc);
     } else {
       vout[x] = apply_dia_at(vin, x, dim, op, copf);
     }
@@ -498,6 +546,19 @@ int launch_propagate_spin(const PropParams& p, const OpSpin& op, int grid, int b
 int launch_propagate_dia(const PropParams& p, const OpDia& op, int grid, int block, void* stream) {
   return launch_prop<kFamilyDia>(p, op, grid, block, stream);
 }
+int launch_propagate_pauli(const PropParams& p, const OpPauli& op, int grid, int block, void* stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = ip_table_offset<SmemLayout>() + (size_t)op.nterms * sizeof(double);
+  cfg.stream = (cudaStream_t)stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return (int)cudaLaunchKernelEx(&cfg, k_propagate<kFamilyPauli, OpPauli>, p, op);
+}
 int launch_propagate_spin_ip(const PropParams& p, const OpSpinIP& op, int grid, int block, void* stream) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -556,6 +617,17 @@ int max_coresident_blocks_ip(int block, int nw) {
   return per * nsm;
 }
 
+int max_coresident_blocks_pauli(int block, int nterms) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = ip_table_offset<SmemLayout>() + (size_t)nterms * sizeof(double);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate<kFamilyPauli, OpPauli>, block, smem) !=
+      cudaSuccess)
+    return -1;
+  return per * nsm;
+}
+
 static int apply_grid(int dim, int block) {
   int g = (dim + block - 1) / block;
   return g < 1 ? 1 : (g > 65535 ? 65535 : g);
@@ -573,6 +645,14 @@ int launch_apply_dia(const OpDia& op, int dim, const double* c, int nV, const do
   Coefs cc = {};
   for (int i = 0; i < 1 + nV; ++i) cc.c[i] = c[i];
   k_apply<kFamilyDia, OpDia><<<apply_grid(dim, 256), 256, 0, (cudaStream_t)stream>>>(op, dim, cc, nV, vin, vout);
+  return (int)cudaGetLastError();
+}
+int launch_apply_pauli(const OpPauli& op, int dim, const double* c, int nV, const double2* vin, double2* vout,
+                       void* stream) {
+  Coefs cc = {};
+  for (int i = 0; i < 1 + nV; ++i) cc.c[i] = c[i];
+  k_apply<kFamilyPauli, OpPauli><<<apply_grid(dim, 256), 256, (size_t)op.nterms * sizeof(double),
+                                   (cudaStream_t)stream>>>(op, dim, cc, nV, vin, vout);
   return (int)cudaGetLastError();
 }
 int launch_spin_tables(int N, int L, double J, double Delta, const double* h, double* dz_lo, double* dz_hi,

@@ -122,6 +122,54 @@ def test_create_validates_arguments(lib):
     assert _create(lib, dia, [], [])[0] == _capi.CFET_EINVAL
 
 
+def test_create_validates_pauli_sums(lib):
+    # CFET_OP_PAULI: FP64 only, masks below nsites, finite coefficients, at most
+    # 4096 strings, only with chains and X fields, no interaction picture; all
+    # checked before any device work
+    keep = []
+    cb = _capi.DRIVE_FN(lambda t, u: 0.0)
+    ps = P._op_struct(P.PauliSum(4, [(0.5, "XYZI"), (-0.3, "IIZZ")]), keep)
+    xf = P._op_struct(P.XField(4, np.ones(4)), keep)
+    opt = _capi.cfet_options()
+    lib.cfet_options_default(C.byref(opt))
+    for prec in (_capi.CFET_PREC_FX, _capi.CFET_PREC_C64):
+        opt.precision = prec
+        st, _ = _create(lib, ps, [xf], [cb], opt)
+        assert st == _capi.CFET_EINVAL and b"CFET_PREC_F64" in lib.cfet_last_error(None)
+    opt.precision = _capi.CFET_PREC_DEFAULT
+    opt.expm = _capi.CFET_EXPM_CHEBYSHEV            # the default precision of a Pauli sum is FP64
+    st, _ = _create(lib, ps, [xf], [cb], opt)
+    assert st == _capi.CFET_EINVAL and b"CHEBYSHEV" in lib.cfet_last_error(None)
+    opt.expm, opt.precision, opt.picture = _capi.CFET_EXPM_KRYLOV, _capi.CFET_PREC_F64, _capi.CFET_PICTURE_INTERACTION
+    chain = P._op_struct(P.XXZChain(4, 1.0, 0.5, np.zeros(4)), keep)
+    st, _ = _create(lib, chain, [ps], [cb], opt)       # a Pauli drive makes it a Pauli-sum context
+    assert st == _capi.CFET_EINVAL and b"INTERACTION" in lib.cfet_last_error(None)
+    bad = P._op_struct(P.PauliSum(4, [(0.5, "XYZI")]), keep)
+    bad.xmask[0] = 1 << 4                              # beyond the chain
+    st, _ = _create(lib, bad, [], [])
+    assert st == _capi.CFET_EINVAL and b"mask" in lib.cfet_last_error(None)
+    nan = P._op_struct(P.PauliSum(4, [(float("nan"), "XIII")]), keep)
+    assert _create(lib, nan, [], [])[0] == _capi.CFET_EINVAL
+    big = P._op_struct(P.PauliSum(4, [(0.1, "ZIII")] * 4097), keep)
+    st, _ = _create(lib, big, [], [])
+    assert st == _capi.CFET_EINVAL and b"4096" in lib.cfet_last_error(None)
+    other = P._op_struct(P.PauliSum(5, [(0.5, "XIIII")]), keep)   # another chain length
+    assert _create(lib, ps, [other], [cb])[0] == _capi.CFET_EINVAL
+    dia = P._op_struct(P.DIA(np.array([0]), np.ones((1, 16))), keep)
+    st, _ = _create(lib, ps, [dia], [cb])
+    assert st == _capi.CFET_EINVAL and b"Pauli" in lib.cfet_last_error(None)
+
+
+def test_pauli_labels_give_masks():
+    ps = P.PauliSum(5, [(0.5, "XYZII"), (1.5, {4: "Y", 1: "z"}), (-2.0, "IIIII")])
+    assert list(ps.xmask) == [0b00011, 0b10000, 0] and list(ps.zmask) == [0b00110, 0b10010, 0]
+    assert list(ps.coeff) == [0.5, 1.5, -2.0]
+    with pytest.raises(ValueError):
+        P.PauliSum(3, [(1.0, {3: "X"})])
+    with pytest.raises(ValueError):
+        P.PauliSum(3, [(1.0, "XQZ")])
+
+
 def test_options_default(lib):
     opt = _capi.cfet_options()
     lib.cfet_options_default(C.byref(opt))
