@@ -38,7 +38,7 @@ def _random_terms(seed, N, n, max_weight=4):
     rng = np.random.default_rng(seed)
     terms = []
     for _ in range(n):
-        w = int(rng.integers(1, max_weight + 1))
+        w = int(rng.integers(1, min(max_weight, N) + 1))
         sites = rng.choice(N, size=w, replace=False)
         label = {int(s): str(rng.choice(list("XYZ"))) for s in sites}
         terms.append((float(rng.uniform(-1, 1)), label))
