@@ -788,6 +788,50 @@ def run_study_timestep(args):
     return 0
 
 
+def run_study_pauli(args):
+    """The N=20 driven chain through the general Pauli-sum kernel (97 strings:
+    XX, YY, ZZ per bond, Z and X per site) against the FP64 chain kernel,
+    CF6:5Opt, dt 0.02, tol 1e-10, m <= 16, --steps steps: H applies/s of each
+    and the difference of their final states."""
+    import torch
+    import paper_1102_5071_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    N = N_SITES
+    pr = W.spin_chain(N)
+    terms = []
+    for i in range(N - 1):
+        terms += [(pr.J, {i: "X", i + 1: "X"}), (pr.J, {i: "Y", i + 1: "Y"}), (pr.J * pr.Delta, {i: "Z", i + 1: "Z"})]
+    terms += [(float(pr.h[i]), {i: "Z"}) for i in range(N)]
+    forms = {
+        "chain kernel (FP64)": lambda: P.Propagator(P.XXZChain(N, pr.J, pr.Delta, pr.h), [P.XField(N, pr.xfield)],
+                                                    [pr.drive], m_max=M_MAX, precision="f64"),
+        "Pauli-sum kernel (FP64)": lambda: P.Propagator(P.PauliSum(N, terms),
+                                                        [P.PauliSum(N, [(float(pr.xfield[i]), {i: "X"})
+                                                                        for i in range(N)])],
+                                                        [pr.drive], m_max=M_MAX),
+    }
+    outs = []
+    for name, make in forms.items():
+        prop = make()
+        psi = torch.from_numpy(W.random_state(PSI_SEED, 1 << N)).cuda()
+        prop.propagate(psi, 0.0, DT, 1, order=ORDER, tol=TOL)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        st = prop.propagate(psi, DT, DT, args.steps, order=ORDER, tol=TOL)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        outs.append(psi)
+        print(json.dumps({"study": "pauli", "workload": f"driven XXZ chain N={N} {SCHEME} dt={DT} tol {TOL}",
+                          "form": name, "steps": args.steps, "H_applies": st["n_applies"], "ms": ms,
+                          "H_applies_per_s": st["n_applies"] / ms * 1e3}))
+        prop.close()
+    print(json.dumps({"study": "pauli", "final_state_difference": torch.linalg.vector_norm(outs[0] - outs[1]).item()}))
+    return 0
+
+
 def run_study_picture(args):
     """Interaction against Schroedinger picture (Secs. 9.3, 9.4), FP64 Krylov,
     N=20 chain, CF6:5Opt, tol 1e-10, m <= 16, over T = --sweep-T: the default
@@ -847,7 +891,7 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="accuracy study: final-state error and throughput per (order, dt) over T")
     ap.add_argument("--sweep-T", type=float, default=20.0)
-    ap.add_argument("--study", choices=["atom", "sizes", "batch", "adjoint", "expm", "timestep", "picture"],
+    ap.add_argument("--study", choices=["atom", "sizes", "batch", "adjoint", "expm", "timestep", "picture", "pauli"],
                     help="extra measurements: the grid atom, the chain at N = 20..26, the 256-chain batch, "
                          "the fidelity gradient, Krylov against Chebyshev stage exponentials, time-step selection, "
                          "interaction against Schroedinger picture")
@@ -878,6 +922,8 @@ def main():
         return run_study_timestep(args)
     if args.study == "picture":
         return run_study_picture(args)
+    if args.study == "pauli":
+        return run_study_pauli(args)
     return run_gpu(args)
 
 
