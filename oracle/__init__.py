@@ -14,7 +14,8 @@ schemes    coefficient tables f_{i,n} (Tables 1-5), the symmetric expansion
            rule R1 (Eq. FSymm), shifted Legendre polynomials (Sec. 3.1),
            Gauss-Legendre points/weights (Table 6) and g_{i,m} (Eq. OmGLeg).
 operators  H v for the driven XXZ chain (Pauli-string definitions, Eq. 53-54
-           style spin operators), the transverse field, banded (DIA) and dense
+           style spin operators), the transverse field, general real sums of
+           Pauli strings applied site by site, banded (DIA) and dense
            operators.
 krylov     Lanczos / Krylov evaluation of exp(-i tau H) psi (Sec. 7.1) with
            the a-posteriori error estimate and time substepping.
@@ -41,7 +42,9 @@ the driven-chain and grid-atom workloads, which no closed form covers; those
 are pinned only through properties (factorisation at J=0, time-independent
 exactness, order slopes, unitarity).  The gradient of ``adjoint`` is pinned by
 central finite differences of its loss and by its vanishing at an optimum.
-``chebyshev`` is pinned by dense expm, the closed forms of the Sec. 8.2
+``operators.PauliSum`` is pinned by Kronecker products of the 2x2 Pauli
+matrices, the XXZ chain written as strings, and the closed forms of
+exp(-i t b Y) and exp(-i t J Y Y).  ``chebyshev`` is pinned by dense expm, the closed forms of the Sec. 8.2
 harmonic-oscillator example and of the Jacobi-Anger series, and dense
 Gershgorin intervals.  ``timestep`` is pinned by the driven two-level system's
 exact propagator (predicted against true errors, goals met) and by the
