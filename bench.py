@@ -53,7 +53,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 fl
 # from one ncu capture of the same kernel build on the 2-step case (76
 # iterations): see profiles/.  Must be reset to None whenever the kernel
 # changes and re-measured.
-DRAM_BYTES_PER_ITERATION = {"fx": (1.201513e9 + 1.633189e9) / 76, "c64": (191.0784e6 + 649.152256e6) / 76,
+DRAM_BYTES_PER_ITERATION = {"fx": (1.207240448e9 + 1.633021184e9) / 76, "c64": (191.0784e6 + 649.152256e6) / 76,
                             "f64": None}
 
 # ncu DRAM read+write bytes per term of the Chebyshev kernel (2-step capture: 66 terms)
