@@ -175,6 +175,12 @@ typedef struct cfet_options {
                                 fixed point, FP64 for Pauli sums)              */
   int32_t expm;              /* CFET_EXPM_* (default CFET_EXPM_KRYLOV)        */
   int32_t picture;           /* CFET_PICTURE_* (default SCHROEDINGER)         */
+  int32_t reorth;            /* 1: full re-orthogonalisation of every Lanczos
+                                vector (one classical Gram-Schmidt sweep
+                                against all earlier ones before beta_k);
+                                CFET_PREC_F64 and CFET_EXPM_KRYLOV only
+                                (otherwise CFET_EINVAL).  Default 0: the
+                                three-term recurrence alone.                  */
 } cfet_options;
 
 /* Number format of the Krylov vectors on the device.  All keep alpha, beta,

@@ -39,7 +39,7 @@ def stage_coefficients(scheme, t, dt, drives):
 
 
 def propagate(op, psi0, t0, dt, nsteps, scheme, drives, tol, m_max, m_min=2,
-              max_substeps=64, forced_log=None, return_log=False):
+              max_substeps=64, forced_log=None, return_log=False, reorth=False):
     """Propagate psi0 from t0 over nsteps CFET steps of length dt.
 
     op: an operator family with .apply(coeffs, v) (oracle.operators).
@@ -47,6 +47,7 @@ def propagate(op, psi0, t0, dt, nsteps, scheme, drives, tol, m_max, m_min=2,
     drives: list of callables f_k(t), one per drive operator V_k.
     forced_log: optional decision log (list over stage exponentials, in
       execution order, of lists of (k, h)) to replay.
+    reorth: full re-orthogonalisation of the Lanczos vectors (krylov.expv).
     Returns psi (and the decision log and the number of H applications when
     return_log is true).
     """
@@ -65,7 +66,7 @@ def propagate(op, psi0, t0, dt, nsteps, scheme, drives, tol, m_max, m_min=2,
             cj = c[j].copy()
             forced = forced_log[idx] if forced_log is not None else None
             psi, lg, na = krylov.expv(lambda v, cj=cj: op.apply(cj, v), psi, dt, tol, m_max,
-                                      m_min=m_min, max_substeps=max_substeps, forced=forced)
+                                      m_min=m_min, max_substeps=max_substeps, forced=forced, reorth=reorth)
             log.append(lg)
             n_applies += na
             idx += 1

@@ -17,6 +17,10 @@ reading (the CUDA path implements the same rule):
 * Lanczos ordering (three-term recurrence, no re-orthogonalisation):
     u = H v_k - beta_{k-1} v_{k-1};  alpha_k = Re<v_k, u>;
     w = u - alpha_k v_k;             beta_k  = ||w||;  v_{k+1} = w / beta_k.
+  Option (the paper is silent on it): full re-orthogonalisation by one
+  classical Gram-Schmidt sweep, w <- w - sum_{i<=k} v_i <v_i, w> with all
+  coefficients taken from the same w, before beta_k = ||w||; T_k keeps the
+  recurrence's alpha and beta.
 * a-posteriori estimate for the Krylov error of a (sub)step of length tau_s:
     y = exp(-i tau_s T_k) e_1   (eigendecomposition of T_k),
     err_k = beta_0 * beta_k * |y_k|   (beta_0 = ||psi||, y_k the last entry).
@@ -81,11 +85,40 @@ def gershgorin_width(alpha, beta):
     return hi - lo
 
 
-def expv(apply, psi, tau, tol, m_max, m_min=2, max_substeps=64, forced=None):
+def gram_schmidt(V, w):
+    """One classical Gram-Schmidt sweep: w - sum_i V_i <V_i, w>."""
+    coeffs = [np.vdot(v, w) for v in V]
+    for c, v in zip(coeffs, V):
+        w = w - c * v
+    return w
+
+
+def lanczos(apply, psi, k, reorth=False):
+    """k steps of the recurrence above from psi / ||psi|| without any test:
+    the basis V (k + 1 vectors), alpha[k], beta[k]."""
+    V = [np.asarray(psi, dtype=np.complex128) / np.linalg.norm(psi)]
+    alpha, beta = [], []
+    for j in range(1, k + 1):
+        u = apply(V[j - 1])
+        if j > 1:
+            u = u - beta[j - 2] * V[j - 2]
+        a = float(np.real(np.vdot(V[j - 1], u)))
+        w = u - a * V[j - 1]
+        if reorth:
+            w = gram_schmidt(V, w)
+        b = float(np.linalg.norm(w))
+        alpha.append(a)
+        beta.append(b)
+        V.append(w / b)
+    return V, alpha, beta
+
+
+def expv(apply, psi, tau, tol, m_max, m_min=2, max_substeps=64, forced=None, reorth=False):
     """exp(-i tau H) psi by Lanczos with substepping.
 
     apply(v) -> H v.  Returns (psi_new, log, n_applies) with log a list of
     (k, h) decisions.  ``forced``: optional list of (k, h) to replay.
+    ``reorth``: full re-orthogonalisation (classical Gram-Schmidt) of every w.
     """
     psi = np.array(psi, dtype=np.complex128, copy=True)
     log = []
@@ -118,6 +151,8 @@ def expv(apply, psi, tau, tol, m_max, m_min=2, max_substeps=64, forced=None):
                 u = u - beta[k - 2] * V[k - 2]
             a = float(np.real(np.vdot(V[k - 1], u)))
             w = u - a * V[k - 1]
+            if reorth:
+                w = gram_schmidt(V, w)
             b = float(np.linalg.norm(w))
             alpha.append(a)
             beta.append(b)

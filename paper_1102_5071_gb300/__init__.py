@@ -168,7 +168,7 @@ class Propagator:
 
     def __init__(self, H0, V=(), drives=(), *, m_max=16, m_min=2, max_substeps=64, block_size=0,
                  grid_size=0, steps_per_launch=256, barrier_timeout_s=2.0, precision="default", expm="krylov",
-                 picture="schroedinger"):
+                 picture="schroedinger", reorth=False):
         lib = _capi.load()
         V = list(V)
         drives = list(drives)
@@ -187,6 +187,7 @@ class Propagator:
         opt.precision = _capi.PRECISIONS[precision]
         opt.expm = _capi.EXPM[expm]
         opt.picture = _capi.PICTURES[picture]
+        opt.reorth = 1 if reorth else 0
         ctx = C.c_void_p()
         st = lib.cfet_create(C.byref(ctx), C.byref(h0), len(V), varr, fns, None, C.byref(opt))
         if st != 0:

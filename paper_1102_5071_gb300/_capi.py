@@ -32,7 +32,7 @@ class cfet_options(C.Structure):
     _fields_ = [("m_max", C.c_int32), ("m_min", C.c_int32), ("max_substeps", C.c_int32),
                 ("block_size", C.c_int32), ("grid_size", C.c_int32), ("steps_per_launch", C.c_int32),
                 ("barrier_timeout_s", C.c_double), ("precision", C.c_int32), ("expm", C.c_int32),
-                ("picture", C.c_int32)]
+                ("picture", C.c_int32), ("reorth", C.c_int32)]
 
 
 CFET_PREC_DEFAULT, CFET_PREC_F64, CFET_PREC_FX, CFET_PREC_C64 = 0, 1, 2, 3

@@ -126,6 +126,11 @@ namespace {
 // fixed-point kernel two 16-word slots and three 8-word slots.
 constexpr size_t kPartialWordsPerCta = 56;
 constexpr int kMaxCtlGrid = 256;  // 32 lanes x 8 records per lane of the exchange
+// FP64 kernel with full re-orthogonalisation: 3 slots + 2 m_max Gram-Schmidt coefficients per CTA
+static size_t partial_words_per_cta(const cfet_ctx* ctx) {
+  const size_t need = ctx->opt.reorth ? 3 + 2 * (size_t)ctx->opt.m_max : 0;
+  return need > kPartialWordsPerCta ? need : kPartialWordsPerCta;
+}
 
 thread_local std::string g_create_err;
 
@@ -261,7 +266,7 @@ cfet_status issue_sequence(cfet_ctx* ctx, const PropParams& base, long long nexp
   CK(cudaMemsetAsync(ctx->d_st, 0, sizeof(DevStatus), s), "status reset");
   CK(cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned), s), "barrier reset");
   // exchange records of the control-warp kernels: no stale tag may survive
-  CK(cudaMemsetAsync(ctx->d_partials, 0, kPartialWordsPerCta * (size_t)ctx->grid * sizeof(double), s),
+  CK(cudaMemsetAsync(ctx->d_partials, 0, partial_words_per_cta(ctx) * (size_t)ctx->grid * sizeof(double), s),
      "exchange reset");
   if (timed) CK(cudaEventRecordWithFlags(ctx->ev_k0, s, cudaEventRecordExternal), "timing event");
   if (base.ip_w) {  // into the interaction picture at t0
@@ -301,6 +306,7 @@ PropParams base_params(cfet_ctx* ctx, double2* psi, double tau, double tol) {
   p.qbasis = ctx->d_qbasis;
   p.qbasis32 = ctx->d_qbasis32;
   p.tiled = ctx->tiled ? 1 : 0;
+  p.reorth = ctx->opt.reorth;
   return p;
 }
 
@@ -503,6 +509,7 @@ void cfet_options_default(cfet_options* opt) {
   opt->precision = CFET_PREC_DEFAULT;  // fixed point; FP64 for Pauli sums
   opt->expm = CFET_EXPM_KRYLOV;
   opt->picture = CFET_PICTURE_SCHROEDINGER;
+  opt->reorth = 0;
 }
 
 cfet_status cfet_scheme_info(int32_t scheme, int32_t* order, int32_t* s, int32_t* M, double* f, double* x,
@@ -566,6 +573,9 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
   if (o.picture == CFET_PICTURE_INTERACTION &&
       (o.precision != CFET_PREC_F64 || o.expm != CFET_EXPM_KRYLOV || H0->kind != CFET_OP_XXZ_CHAIN || pauli))
     return fail(nullptr, CFET_EINVAL, "CFET_PICTURE_INTERACTION requires an XXZ chain, CFET_PREC_F64 and CFET_EXPM_KRYLOV");
+  if (o.reorth != 0 && o.reorth != 1) return fail(nullptr, CFET_EINVAL, "reorth must be 0 or 1");
+  if (o.reorth && (o.precision != CFET_PREC_F64 || o.expm != CFET_EXPM_KRYLOV))
+    return fail(nullptr, CFET_EINVAL, "reorth requires CFET_PREC_F64 and CFET_EXPM_KRYLOV");
   if (o.block_size == 0) o.block_size = (o.precision == CFET_PREC_F64) ? 256 : 384;
   {
     // FP64 kernel: block_size threads (<= 256); fixed-point and mixed-precision
@@ -969,7 +979,7 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
       return fail(nullptr, CFET_EINVAL, "fixed-point precision: dimension too large for the grid, use CFET_PREC_F64");
     }
   }
-  CKC(cudaMalloc(&ctx->d_partials, kPartialWordsPerCta * (size_t)ctx->grid * sizeof(double)),
+  CKC(cudaMalloc(&ctx->d_partials, partial_words_per_cta(ctx) * (size_t)ctx->grid * sizeof(double)),
       "cudaMalloc(partials)");
   CKC(cudaMalloc(&ctx->d_bar, 2 * sizeof(unsigned)), "cudaMalloc(barrier)");
   CKC(cudaMemset(ctx->d_bar, 0, 2 * sizeof(unsigned)), "barrier init");

@@ -152,6 +152,8 @@ struct PropParams {
   double tau, tol;
   int m_min, m_max, max_substeps;
   int tiled;             // spin chains: window-tiled apply (complex64 and fixed-point kernels)
+  int reorth;            // FP64 kernel: full re-orthogonalisation of every Lanczos vector
+  int pad1;
   // decisions (device arrays, nullable)
   const int* f_nsub; const int* f_k; const int* f_h;
   int* r_nsub; int* r_k; int* r_h; long long r_cap;

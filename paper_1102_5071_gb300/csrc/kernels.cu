@@ -321,6 +321,59 @@ __global__ void __launch_bounds__(256) k_propagate(PropParams p, Op op) {
             if (tid == 0) part1[blockIdx.x] = s;
           }
           if (!grid_barrier(p.bar, gen, &st->status, p.timeout_ns, &S.ok)) return;
+          if (p.reorth) {
+            // ---------------- full re-orthogonalisation (option): one classical
+            // Gram-Schmidt sweep w <- w - sum_i v_i <v_i, w> over the stored
+            // q_i = v_i / scale[i]; ||w||^2 is then taken again into part1
+            double* partQ = p.partials + 3 * (size_t)G;  // 2 it doubles per CTA
+            for (int i = 1; i <= it; ++i) {
+              const double2* qi = vec(i);
+              double ar = 0.0, ai = 0.0;
+              for (int x = x0; x < dim; x += stride) {
+                const double2 a = qi[x], w = u[x];
+                ar = fma(a.x, w.x, fma(a.y, w.y, ar));   // conj(q_i) w
+                ai = fma(a.x, w.y, fma(-a.y, w.x, ai));
+              }
+              const double sr = block_sum(ar, S.red);
+              __syncthreads();
+              const double si = block_sum(ai, S.red);
+              if (tid == 0) {
+                partQ[(size_t)(2 * (i - 1)) * G + blockIdx.x] = sr;
+                partQ[(size_t)(2 * (i - 1) + 1) * G + blockIdx.x] = si;
+              }
+              __syncthreads();
+            }
+            if (!grid_barrier(p.bar, gen, &st->status, p.timeout_ns, &S.ok)) return;
+            if (tid < 32) {
+              for (int i = 1; i <= it; ++i) {
+                const double sc2 = S.scale[i] * S.scale[i];
+                const double cr = sum_partials(partQ + (size_t)(2 * (i - 1)) * G) * sc2;
+                const double ci = sum_partials(partQ + (size_t)(2 * (i - 1) + 1) * G) * sc2;
+                if (tid == 0) {
+                  S.cre[i - 1] = cr;
+                  S.cim[i - 1] = ci;
+                }
+              }
+            }
+            __syncthreads();
+            acc = 0.0;
+            for (int x = x0; x < dim; x += stride) {
+              double2 w = u[x];
+              for (int i = 1; i <= it; ++i) {
+                const double2 a = vec(i)[x];
+                const double cr = S.cre[i - 1], ci = S.cim[i - 1];
+                w.x -= cr * a.x - ci * a.y;
+                w.y -= cr * a.y + ci * a.x;
+              }
+              u[x] = w;
+              acc = fma(w.x, w.x, fma(w.y, w.y, acc));
+            }
+            {
+              const double s2 = block_sum(acc, S.red);
+              if (tid == 0) part1[blockIdx.x] = s2;
+            }
+            if (!grid_barrier(p.bar, gen, &st->status, p.timeout_ns, &S.ok)) return;
+          }
           // ---------------- decision (warp 0)
           if (tid < 32) {
             const double t = sum_partials(part1);

@@ -117,6 +117,14 @@ def test_create_validates_arguments(lib):
     st, _ = _create(lib, dia_ip, [], [], opt)
     assert st == _capi.CFET_EINVAL and b"INTERACTION" in lib.cfet_last_error(None)
     opt.picture, opt.precision = _capi.CFET_PICTURE_SCHROEDINGER, _capi.CFET_PREC_DEFAULT
+    # re-orthogonalisation: 0 or 1, FP64 Krylov only
+    opt.reorth = 2
+    st, _ = _create(lib, ok_h0, [xf], [cb], opt)
+    assert st == _capi.CFET_EINVAL and b"reorth" in lib.cfet_last_error(None)
+    opt.reorth = 1                                    # with the default fixed-point precision
+    st, _ = _create(lib, ok_h0, [xf], [cb], opt)
+    assert st == _capi.CFET_EINVAL and b"reorth" in lib.cfet_last_error(None)
+    opt.reorth = 0
     # DIA offsets out of range
     dia = P._op_struct(P.DIA(np.array([0, 7]), np.ones((2, 7))), keep)
     assert _create(lib, dia, [], [])[0] == _capi.CFET_EINVAL
@@ -176,6 +184,7 @@ def test_options_default(lib):
     assert (opt.m_max, opt.m_min, opt.max_substeps, opt.block_size) == (16, 2, 64, 0)
     assert opt.barrier_timeout_s == 2.0
     assert opt.expm == _capi.CFET_EXPM_KRYLOV and opt.picture == _capi.CFET_PICTURE_SCHROEDINGER
+    assert opt.precision == _capi.CFET_PREC_DEFAULT and opt.reorth == 0
 
 
 def test_no_device_gives_enodev(lib):

@@ -90,3 +90,56 @@ def test_expv_substep_cap_raises():
     psi = W.random_state(5, 200)
     with pytest.raises(K.KrylovError):
         K.expv(lambda v: 50.0 * n * v, psi, 1.0, tol=1e-12, m_max=4, max_substeps=3)
+
+
+# ---------------------------------------------------------------- full re-orthogonalisation (option)
+def _gram_defect(V):
+    M = np.array(V)
+    return np.abs(M.conj() @ M.T - np.eye(len(V))).max()
+
+
+def test_reorth_keeps_the_basis_orthonormal():
+    # a spectrum with outliers: once the outlying Ritz values converge, the
+    # three-term recurrence loses orthogonality (Paige); one classical
+    # Gram-Schmidt sweep per step keeps the basis orthonormal to rounding
+    lam = np.concatenate([np.linspace(0.0, 1.0, 300), [50.0, 100.0, 200.0]])
+    psi = W.random_state(3, len(lam))
+    V0, _, _ = K.lanczos(lambda v: lam * v, psi, 60)
+    V1, _, _ = K.lanczos(lambda v: lam * v, psi, 60, reorth=True)
+    assert _gram_defect(V0[:-1]) > 1e-2
+    assert _gram_defect(V1) < 1e-13
+
+
+@pytest.mark.parametrize("reorth", [False, True])
+def test_lanczos_helper_is_the_expv_recurrence(reorth):
+    # expv with a fixed K reconstructs beta_0 V_K exp(-i tau T_K) e_1 from the
+    # same recurrence as the helper
+    H = _herm(48, 31)
+    psi = W.random_state(32, 48)
+    out, _, _ = K.expv(lambda v: H @ v, psi, 0.3, tol=0.0, m_max=12, reorth=reorth)
+    V, a, b = K.lanczos(lambda v: H @ v, psi, 12, reorth=reorth)
+    y = K.tridiag_expm_e1(a, b[:11], 0.3)
+    assert np.linalg.norm(out - np.linalg.norm(psi) * sum(y[i] * V[i] for i in range(12))) < 1e-14
+
+
+@pytest.mark.parametrize("tau", [0.4, 3.0])
+def test_expv_reorth_matches_expm_and_the_plain_recurrence(tau):
+    # results agree with the dense exponential and across the two modes within
+    # the tolerance
+    H = _herm(64, 11)
+    psi = W.random_state(12, 64)
+    a, _, _ = K.expv(lambda v: H @ v, psi, tau, tol=1e-12, m_max=30, reorth=True)
+    b, _, _ = K.expv(lambda v: H @ v, psi, tau, tol=1e-12, m_max=30)
+    ref = expm(-1j * tau * H) @ psi
+    assert np.linalg.norm(a - ref) < 1e-10 and np.linalg.norm(a - b) < 1e-10
+
+
+def test_expv_reorth_on_the_outlier_spectrum():
+    # the spectrum that breaks orthogonality: with a large Krylov space and a
+    # long step both modes still meet the tolerance against the exact result
+    lam = np.concatenate([np.linspace(0.0, 1.0, 300), [50.0, 100.0, 200.0]])
+    psi = W.random_state(4, len(lam))
+    exact = np.exp(-1j * 0.05 * lam) * psi
+    for reorth in (False, True):
+        out, log, _ = K.expv(lambda v: lam * v, psi, 0.05, tol=1e-12, m_max=60, reorth=reorth, max_substeps=50)
+        assert np.linalg.norm(out - exact) < 1e-10, (reorth, log)
