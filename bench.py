@@ -832,6 +832,38 @@ def run_study_pauli(args):
     return 0
 
 
+def run_study_reorth(args):
+    """Cost of full re-orthogonalisation: the N=20 chain in FP64 (CF6:5Opt,
+    dt 0.02, tol 1e-10, m <= 16) with the plain three-term recurrence and with
+    one classical Gram-Schmidt sweep per Lanczos vector, --steps steps: H
+    applies/s of each and the difference of their final states."""
+    import torch
+    import paper_1102_5071_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    pr = W.spin_chain(N_SITES)
+    outs = []
+    for reorth in (False, True):
+        prop = P.Propagator(P.XXZChain(N_SITES, pr.J, pr.Delta, pr.h), [P.XField(N_SITES, pr.xfield)], [pr.drive],
+                            m_max=M_MAX, precision="f64", reorth=reorth)
+        psi = torch.from_numpy(W.random_state(PSI_SEED, 1 << N_SITES)).cuda()
+        prop.propagate(psi, 0.0, DT, 1, order=ORDER, tol=TOL)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        st = prop.propagate(psi, DT, DT, args.steps, order=ORDER, tol=TOL)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        outs.append(psi)
+        print(json.dumps({"study": "reorth", "workload": f"driven XXZ chain N={N_SITES} {SCHEME} dt={DT} tol {TOL}",
+                          "reorth": reorth, "steps": args.steps, "H_applies": st["n_applies"], "ms": ms,
+                          "H_applies_per_s": st["n_applies"] / ms * 1e3}))
+        prop.close()
+    print(json.dumps({"study": "reorth", "final_state_difference": torch.linalg.vector_norm(outs[0] - outs[1]).item()}))
+    return 0
+
+
 def run_study_picture(args):
     """Interaction against Schroedinger picture (Secs. 9.3, 9.4), FP64 Krylov,
     N=20 chain, CF6:5Opt, tol 1e-10, m <= 16, over T = --sweep-T: the default
@@ -891,7 +923,8 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="accuracy study: final-state error and throughput per (order, dt) over T")
     ap.add_argument("--sweep-T", type=float, default=20.0)
-    ap.add_argument("--study", choices=["atom", "sizes", "batch", "adjoint", "expm", "timestep", "picture", "pauli"],
+    ap.add_argument("--study", choices=["atom", "sizes", "batch", "adjoint", "expm", "timestep", "picture", "pauli",
+                                        "reorth"],
                     help="extra measurements: the grid atom, the chain at N = 20..26, the 256-chain batch, "
                          "the fidelity gradient, Krylov against Chebyshev stage exponentials, time-step selection, "
                          "interaction against Schroedinger picture")
@@ -924,6 +957,8 @@ def main():
         return run_study_picture(args)
     if args.study == "pauli":
         return run_study_pauli(args)
+    if args.study == "reorth":
+        return run_study_reorth(args)
     return run_gpu(args)
 
 
