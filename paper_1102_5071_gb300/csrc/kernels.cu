@@ -15,6 +15,9 @@
 // same fixed order, so all CTAs hold bit-identical alpha/beta and take the
 // same adaptive decisions without a broadcast.  Warp 0 of each CTA evaluates
 // the small exponential exp(-i tau T_k) e_1 of the tridiagonal Lanczos matrix.
+// Operator families: XXZ chain with X fields, DIA, general Pauli sums, and
+// the chain in the interaction picture; optionally every Lanczos vector is
+// re-orthogonalised against all earlier ones (classical Gram-Schmidt).
 #include <cuda_runtime.h>
 
 #include <cmath>

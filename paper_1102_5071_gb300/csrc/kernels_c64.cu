@@ -26,6 +26,9 @@
 // the reductions, the bounded grid barrier, the per-pass scalars and the
 // small exponential (the estimate of iteration k runs while the workers
 // already apply H for iteration k+1, as in the fixed-point kernel).
+//
+// Long chains: the TILED instantiation applies H in window passes over
+// shared-memory tiles (tiled_common.cuh) instead of element by element.
 #include <cuda_runtime.h>
 
 #include <cmath>

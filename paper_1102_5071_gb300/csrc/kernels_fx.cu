@@ -29,6 +29,10 @@
 // on the control warp while the workers already compute the apply of
 // iteration k+1; if it accepts k, that apply is discarded.  The accepted
 // estimate's y = exp(-i tau T_k) e_1 is reused for the reconstruction.
+//
+// Long chains.  The TILED instantiation replaces the element-wise spin apply
+// by window passes over shared-memory tiles (tiled_common.cuh) separated by
+// grid exchanges, for chains whose vectors leave L2.
 #include <cuda_runtime.h>
 
 #include <cmath>
