@@ -611,6 +611,8 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
       if (o2.kind == CFET_OP_PAULI) {
         if (o2.nterms < 0 || (o2.nterms > 0 && (!o2.xmask || !o2.zmask || !o2.coeff)))
           return fail(nullptr, CFET_EINVAL, "Pauli sum: nterms < 0 or missing arrays");
+        if (strings.size() + (size_t)o2.nterms > (size_t)kMaxPauliTerms)
+          return fail(nullptr, CFET_EINVAL, "Pauli sums: more than 4096 strings");
         for (int t = 0; t < o2.nterms; ++t) {
           if ((o2.xmask[t] | o2.zmask[t]) >> nsites) return fail(nullptr, CFET_EINVAL, "Pauli sum: mask beyond nsites");
           if (!is_finite_d(o2.coeff[t])) return fail(nullptr, CFET_EINVAL, "Pauli sum: coefficient not finite");
