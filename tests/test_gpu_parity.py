@@ -321,3 +321,31 @@ def test_full_size_atom_without_field_keeps_the_1s_state(torch_cuda, prec):
     prop.propagate(x, 500.0, a["dt"], nsteps, order=a["order"], tol=1e-12)
     ref = np.exp(-1j * e1s * a["dt"] * nsteps) * psi0
     assert np.linalg.norm(_host(x) - ref) <= PARITY
+
+
+@pytest.mark.parametrize("prec", PRECS + ["c64"])
+def test_chain_n20_without_field_conserves_magnetisation(torch_cuda, prec):
+    # with the x field switched off (A = 0) the XXZ chain conserves the number
+    # of down spins: a random state on the half-filled sector of the N = 20
+    # chain (popcount 10, 184 756 states) keeps every amplitude outside the
+    # sector exactly zero and its norm to the Krylov tolerance (complex64: to
+    # its FP32 rounding)
+    import paper_1102_5071_gb300 as P
+    torch = torch_cuda
+    N = 20
+    pr = W.spin_chain(N)
+    x = np.arange(1 << N, dtype=np.int64)
+    pop = np.zeros(1 << N, dtype=np.int64)
+    for i in range(N):
+        pop += (x >> i) & 1
+    sector = pop == N // 2
+    psi0 = W.random_state(13, 1 << N)
+    psi0[~sector] = 0.0
+    psi0 /= np.linalg.norm(psi0)
+    prop = P.Propagator(P.XXZChain(N, pr.J, pr.Delta, pr.h), [P.XField(N, pr.xfield)], [lambda t: 0.0], m_max=16,
+                        precision=prec)
+    t = _dev(torch, psi0)
+    st = prop.propagate(t, 0.0, 0.05, 10, order=6, tol=1e-10)
+    out = t.cpu().numpy()
+    assert np.count_nonzero(out[~sector]) == 0
+    assert abs(np.linalg.norm(out[sector]) - 1.0) <= (1e-5 if prec == "c64" else st["n_substeps"] * 1e-10)
