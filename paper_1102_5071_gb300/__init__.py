@@ -164,7 +164,14 @@ def _check_vec(t, dim, name):
 
 
 class Propagator:
-    """CFET propagator for H(t) = H0 + sum_k f_k(t) V_k on the current CUDA device."""
+    """CFET propagator for H(t) = H0 + sum_k f_k(t) V_k on the current CUDA device.
+
+    H0, V: XXZChain / XField, DIA, or PauliSum operators (see include/cfet.h);
+    drives: one callable f_k(t) per V_k.  precision: "default" (fixed point;
+    FP64 when a PauliSum is involved), "fx", "f64" or "c64"; expm: "krylov" or
+    "chebyshev" (fixed point); picture: "schroedinger" or "interaction" (FP64
+    chains); reorth: full re-orthogonalisation of the Lanczos vectors (FP64).
+    """
 
     def __init__(self, H0, V=(), drives=(), *, m_max=16, m_min=2, max_substeps=64, block_size=0,
                  grid_size=0, steps_per_launch=256, barrier_timeout_s=2.0, precision="default", expm="krylov",
