@@ -547,6 +547,17 @@ cfet_status cfet_fidelity_grad(cfet_ctx* ctx, const void* psi0, const void* phi,
  * CFET_ETIMEOUT, CFET_ECUDA otherwise.  Synchronises the device.            */
 cfet_status cfet_selftest_wait_timeout(int32_t which, double timeout_s, int32_t* device_status);
 
+/* Host-only check (no device needed) of the index arithmetic of the
+ * window-tiled apply of long chains (CFET_PREC_FX uses tile_bits 11,
+ * CFET_PREC_C64 12): for an nsites chain, every basis index appears in
+ * exactly one tile slot per window, every single-site flip and every bond
+ * (i, i+1) is applied in exactly one window, and tile slots pair up into
+ * contiguous 16-byte copy units.  *checked receives the number of
+ * (window, index) pairs visited.  Returns CFET_EINVAL for tile_bits other
+ * than 11, 12 or nsites outside [tile_bits, 27], CFET_ECUDA when the tiling
+ * is inconsistent.                                                          */
+cfet_status cfet_selftest_tiling(int32_t nsites, int32_t tile_bits, int64_t* checked);
+
 /* Dimension and drive-operator count of ctx (for bindings).                 */
 int64_t cfet_dim(const cfet_ctx* ctx);
 int32_t cfet_num_drives(const cfet_ctx* ctx);

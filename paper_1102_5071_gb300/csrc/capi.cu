@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "cfet_internal.h"
+#include "tiled_common.cuh"
 
 using namespace cfet;
 
@@ -1290,6 +1291,63 @@ cfet_status cfet_sync(cfet_ctx* ctx, void* stream, cfet_stats* stats) {
   if (!ctx) return CFET_EINVAL;
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   return finish(ctx, (cudaStream_t)stream, stats);
+}
+
+// Host check of the window tiling of the long-chain kernels (tiled_common.cuh,
+// tiles of 2^tile_bits elements): every element in exactly one tile slot per
+// window, every flip and every bond in exactly one window, the 16-byte copy
+// units of complex64 tiles (element pairs) contiguous and aligned, and the
+// window count within its bound.
+extern "C++" {
+template <int TB>
+static bool check_tiling(int N, int64_t* checked) {
+  TileWin W[kTiledMaxWindows] = {};
+  const int nwin = tiled_windows<TB>(N, W);
+  const int64_t dim = int64_t(1) << N;
+  const int ntiles = 1 << (N - TB);
+  std::vector<unsigned char> seen((size_t)dim);
+  std::vector<int> flips(N, 0), bonds(N, 0);
+  for (int w = 0; w < nwin; ++w) {
+    std::fill(seen.begin(), seen.end(), 0);
+    if (w == 0) {
+      for (int i = 0; i < TB; ++i) ++flips[i];
+      for (int i = 0; i + 1 < TB; ++i) ++bonds[i];
+    } else {
+      if (W[w].width < 2 || W[w].c < 1 || W[w].c + W[w].width != TB) return false;
+      for (int i = 1; i < W[w].width; ++i) ++flips[W[w].b0 + i];
+      for (int i = 0; i + 1 < W[w].width; ++i) ++bonds[W[w].b0 + i];
+    }
+    for (int t = 0; t < ntiles; ++t)
+      for (int j = 0; j < (1 << TB); ++j) {
+        const int64_t x = w == 0 ? ((int64_t)t << TB) | j : tile_x(W[w], t, j);
+        if (x < 0 || x >= dim || seen[(size_t)x]) return false;
+        seen[(size_t)x] = 1;
+        if (w > 0) {
+          // copy units: slots j, j + 1 (j even) hold x, x + 1
+          if ((j & 1) == 0 && tile_x(W[w], t, j + 1) != x + 1) return false;
+          // the window's own bits: slot j ^ 2^(c+i) holds x ^ 2^(b0+i)
+          for (int i = 0; i < W[w].width; ++i)
+            if (tile_x(W[w], t, j ^ (1 << (W[w].c + i))) != (x ^ (int64_t(1) << (W[w].b0 + i)))) return false;
+        }
+        ++*checked;
+      }
+  }
+  for (int i = 0; i < N; ++i)
+    if (flips[i] != 1) return false;
+  for (int i = 0; i + 1 < N; ++i)
+    if (bonds[i] != 1) return false;
+  return true;
+}
+}  // extern "C++"
+
+cfet_status cfet_selftest_tiling(int32_t nsites, int32_t tile_bits, int64_t* checked) {
+  if (!checked) return fail(nullptr, CFET_EINVAL, "checked is NULL");
+  *checked = 0;
+  if ((tile_bits != 11 && tile_bits != 12) || nsites < tile_bits || nsites > kTiledMaxSites || nsites > 27)
+    return fail(nullptr, CFET_EINVAL, "tiling self-test: tile_bits 11 or 12, nsites in [tile_bits, 27]");
+  const bool ok = tile_bits == 11 ? check_tiling<11>(nsites, checked) : check_tiling<12>(nsites, checked);
+  if (!ok) return fail(nullptr, CFET_ECUDA, "tiling self-test: window tiling inconsistent");
+  return CFET_OK;
 }
 
 cfet_status cfet_selftest_wait_timeout(int32_t which, double timeout_s, int32_t* device_status) {

@@ -28,9 +28,10 @@ struct TileWin {
 };
 
 // Windows 1.. of an N-site chain with tiles of 2^TB elements; returns the
-// number of windows including window 0 (W[0] unused).
+// number of windows including window 0 (W[0] unused).  This and tile_x also
+// compile for the host, where cfet_selftest_tiling checks them.
 template <int TB>
-__device__ __forceinline__ int tiled_windows(int N, TileWin (&W)[kTiledMaxWindows]) {
+__host__ __device__ __forceinline__ int tiled_windows(int N, TileWin (&W)[kTiledMaxWindows]) {
   int n = 1;
   for (int b0 = TB - 1; b0 + 1 < N && n < kTiledMaxWindows; b0 += kHighWindow - 1, ++n) {
     const int width = (N - b0) < kHighWindow ? (N - b0) : kHighWindow;
@@ -42,7 +43,7 @@ __device__ __forceinline__ int tiled_windows(int N, TileWin (&W)[kTiledMaxWindow
 }
 
 // Element index of slot j of strided tile t of window W.
-__device__ __forceinline__ int tile_x(const TileWin& W, int t, int j) {
+__host__ __device__ __forceinline__ int tile_x(const TileWin& W, int t, int j) {
   const int nb = W.b0 - W.c;  // bits [c, b0) come from t
   const int tl = t & ((1 << nb) - 1), th = t >> nb;
   return (j & ((1 << W.c) - 1)) | (tl << W.c) | ((j >> W.c) << W.b0) | (th << (W.b0 + W.width));

@@ -178,6 +178,26 @@ def test_pauli_labels_give_masks():
         P.PauliSum(3, [(1.0, "XQZ")])
 
 
+@pytest.mark.parametrize("tile_bits,nsites,windows", [(11, 13, 2), (11, 19, 3), (11, 26, 4),
+                                                      (12, 13, 2), (12, 20, 3), (12, 27, 4)])
+def test_window_tiling_of_long_chains(lib, tile_bits, nsites, windows):
+    # the index arithmetic of the tiled apply (fixed point: tiles of 2^11,
+    # complex64: 2^12), run on the host from the kernels' own header: every
+    # index once per window, every flip and bond in one window, copy units
+    # contiguous; `windows` passes visit windows * 2^nsites indices
+    n = C.c_int64()
+    assert lib.cfet_selftest_tiling(nsites, tile_bits, C.byref(n)) == _capi.CFET_OK, lib.cfet_last_error(None)
+    assert n.value == windows << nsites
+
+
+def test_window_tiling_selftest_validates(lib):
+    n = C.c_int64()
+    assert lib.cfet_selftest_tiling(20, 10, C.byref(n)) == _capi.CFET_EINVAL
+    assert lib.cfet_selftest_tiling(10, 11, C.byref(n)) == _capi.CFET_EINVAL
+    assert lib.cfet_selftest_tiling(28, 12, C.byref(n)) == _capi.CFET_EINVAL
+    assert lib.cfet_selftest_tiling(20, 12, None) == _capi.CFET_EINVAL
+
+
 def test_options_default(lib):
     opt = _capi.cfet_options()
     lib.cfet_options_default(C.byref(opt))
