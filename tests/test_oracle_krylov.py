@@ -143,3 +143,19 @@ def test_expv_reorth_on_the_outlier_spectrum():
     for reorth in (False, True):
         out, log, _ = K.expv(lambda v: lam * v, psi, 0.05, tol=1e-12, m_max=60, reorth=reorth, max_substeps=50)
         assert np.linalg.norm(out - exact) < 1e-10, (reorth, log)
+
+
+def test_planted_conjugation_error_in_gram_schmidt_is_caught(monkeypatch):
+    # Gram-Schmidt coefficients <w, v_i> instead of <v_i, w>: the basis is no
+    # longer orthonormal on the outlier spectrum
+    def bad(V, w):
+        for v in V:
+            w = w - np.vdot(w, v) * v
+        return w
+
+    monkeypatch.setattr(K, "gram_schmidt", bad)
+    lam = np.concatenate([np.linspace(0.0, 1.0, 300), [50.0, 100.0, 200.0]])
+    psi = W.random_state(3, len(lam)) * np.exp(1j * np.linspace(0, 3, len(lam)))
+    V, _, _ = K.lanczos(lambda v: lam * v, psi, 40, reorth=True)
+    M = np.array(V)
+    assert np.abs(M.conj() @ M.T - np.eye(len(V))).max() > 1e-8

@@ -86,3 +86,32 @@ def test_time_independent_pauli_sum_matches_expm():
     out = cfet.propagate(op, psi0, 0.0, 0.1, 6, 8, [], 1e-13, 30)
     ref = expm(-1j * 0.6 * O.pauli_dense(N, terms)) @ psi0
     assert np.linalg.norm(out - ref) <= 1e-11
+
+
+# ---------------------------------------------------------------- planted mistakes
+def test_planted_sign_error_in_y_is_caught(monkeypatch):
+    # Y with the sign of its matrix elements flipped (i.e. -Y): the Kronecker
+    # pin and the Y-rotation closed form must both notice
+    good_y = O.apply_y
+    monkeypatch.setattr(O, "apply_y", lambda v, i, N: -good_y(v, i, N))
+    N = 3
+    terms = [(0.7, "YIZ"), (0.4, "XYI")]
+    v = W.random_state(5, 1 << N)
+    assert not np.allclose(O.PauliSum(N, terms, []).apply([1.0], v), O.pauli_dense(N, terms) @ v, atol=1e-10)
+    op = O.PauliSum(1, [(0.9, "Y")], [])
+    out = cfet.propagate(op, np.array([1.0, 0.0], dtype=np.complex128), 0.0, 0.5, 2, 4, [], 1e-14, 2)
+    assert not np.allclose(out, [math.cos(0.9), math.sin(0.9)], atol=1e-6)
+
+
+def test_planted_site_reversal_is_caught(monkeypatch):
+    # labels read from the last site backwards: the dict-against-string pin
+    # and the chain-as-strings pin must notice
+    good = O.pauli_ops
+    monkeypatch.setattr(O, "pauli_ops",
+                        lambda lb: good(lb[::-1]) if isinstance(lb, str) else good(lb))
+    N = 4
+    a = O.PauliSum(N, [(0.7, "XYIZ")], [])
+    b = O.PauliSum(N, [(0.7, {0: "X", 1: "Y", 3: "Z"})], [])
+    v = W.random_state(1, 16)
+    assert not np.allclose(a.apply([1.0], v), b.apply([1.0], v), atol=1e-10)
+
