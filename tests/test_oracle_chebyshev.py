@@ -143,3 +143,44 @@ def test_propagate_agrees_with_the_krylov_oracle():
     # both evaluate every stage exponential to 1e-12: the CFET steps agree
     assert np.linalg.norm(a - b) <= 40 * 2 * 1e-12
     assert st["n_applies"] == sum(st["K"]) and len(st["K"]) == 40
+
+
+# ---------------------------------------------------------------- planted mistakes
+def test_planted_missing_factor_two_is_caught(monkeypatch):
+    # Jacobi-Anger with r_k = J_k(z) for every k (the factor 2 - delta_k0
+    # dropped): the dense-expm pin must notice
+    good = CH.coefficients
+
+    def bad(z, tol):
+        r, K, tail = good(z, tol)
+        r = r.copy()
+        r[1:] /= 2.0
+        return r, K, tail
+
+    monkeypatch.setattr(CH, "coefficients", bad)
+    pr, op, fields = _chain(6, nfields=2)
+    c = (0.8, -0.35, 0.2)
+    Hm = c[0] * O.xxz_dense(6, pr.J, pr.Delta, pr.h) + sum(ck * O.xfield_dense(6, a) for ck, a in zip(c[1:], fields))
+    lo, hi = CH.stage_interval(CH.operator_intervals(op), c)
+    psi = W.random_state(3, 64)
+    out, *_ = CH.expv(lambda v: op.apply(c, v), psi, 0.5, lo, hi, 1e-12)
+    assert np.linalg.norm(out - expm(-0.5j * Hm) @ psi) > 1e-3
+
+
+def test_planted_weyl_sign_error_is_caught(monkeypatch):
+    # negative stage scalars without swapping the interval ends: the interval
+    # no longer contains the spectrum
+    def bad(intervals, coeffs):
+        lo = hi = 0.0
+        for (l, h), s in zip(intervals, coeffs):
+            lo += s * l
+            hi += s * h
+        return lo, hi
+
+    monkeypatch.setattr(CH, "stage_interval", bad)
+    pr, op, fields = _chain(6, nfields=2)
+    c = (-0.8, 0.35, -0.2)
+    Hm = c[0] * O.xxz_dense(6, pr.J, pr.Delta, pr.h) + sum(ck * O.xfield_dense(6, a) for ck, a in zip(c[1:], fields))
+    lo, hi = CH.stage_interval(CH.operator_intervals(op), c)
+    ev = np.linalg.eigvalsh(Hm)
+    assert not (lo <= ev.min() + 1e-12 and ev.max() <= hi + 1e-12)

@@ -88,3 +88,26 @@ def test_stage_operator_is_hermitian_and_matches_the_dense_definition():
     u, v = W.random_state(1, 32), W.random_state(2, 32)
     assert np.allclose(apply(v), M @ v, atol=1e-13)
     assert abs(np.vdot(u, apply(v)) - np.conj(np.vdot(v, apply(u)))) <= 1e-13
+
+
+# ---------------------------------------------------------------- planted mistakes
+def test_planted_phase_sign_error_is_caught(monkeypatch):
+    # stage operators built with e^{-i d t} H_b e^{+i d t} (the picture's
+    # phases reversed): the resonant two-level system is no longer exact
+    def bad(d, offdiag, g_row, t_nodes, fvals):
+        def apply(v):
+            out = np.zeros_like(v)
+            for gm, tm, fm in zip(g_row, t_nodes, fvals):
+                ph = np.exp(-1j * d * tm)
+                out += gm * (ph * offdiag([1.0] + list(fm), np.conj(ph) * v))
+            return out
+        return apply
+
+    monkeypatch.setattr(IP, "stage_apply", bad)
+    Dl, V, w = 1.3, 0.4, 1.3
+    op = O.Dense(Dl * O.SZ, [O.SX, O.SY])
+    drives = [lambda t: V * math.cos(2 * w * t), lambda t: V * math.sin(2 * w * t)]
+    psi0 = np.array([0.6, 0.8j])
+    T = 4.0
+    out = IP.propagate(op, psi0, 0.0, T / 4, 4, "CF4:2", drives, 1e-14, 2)
+    assert np.linalg.norm(out - _exact_two_level(T, Dl, V, w) @ psi0) > 1e-6

@@ -111,3 +111,44 @@ def test_adaptive_replay_is_identical_and_fixed_step_is_worse_at_equal_cost():
     n = 2 * len(hs)
     z = step(PSI0, 0.0, T / n, n)
     assert np.linalg.norm(x - ref) < np.linalg.norm(z - ref)
+
+
+# ---------------------------------------------------------------- planted mistakes
+def test_planted_missing_step_factor_is_caught(monkeypatch):
+    # the local constant without its factor h (model h^N instead of h^(N+1)
+    # per step): halving h no longer leaves c unchanged
+    def bad(step, psi, t, h, order):
+        N = int(order)
+        x1 = step(np.array(psi, dtype=np.complex128), t, h, 1)
+        x2 = step(np.array(psi, dtype=np.complex128), t, h / 2.0, 2)
+        return float(np.linalg.norm(x1 - x2)) / (h ** N - (h / 2.0) ** N), x2
+
+    monkeypatch.setattr(TS, "local_error_constant", bad)
+    op, drives = _problem()
+    step = _stepper(op, drives, "CF4:2")
+    c1 = TS.local_error_constant(step, PSI0, 0.0, 0.2, 4)[0]
+    c2 = TS.local_error_constant(step, PSI0, 0.0, 0.1, 4)[0]
+    assert abs(c2 / c1 - 1.0) > 0.1
+
+
+def test_planted_missing_run_length_is_caught(monkeypatch):
+    # the two-run constant without the run length T in the model
+    # eps = c T dt^N: it no longer predicts the true error of a third step
+    def bad(step, psi0, t0, T, n1, order, ratio=2.0):
+        N = int(order)
+        n2 = int(round(n1 * ratio ** (1.0 / N)))
+        dt1, dt2 = T / n1, T / n2
+        x1 = step(np.array(psi0, dtype=np.complex128), t0, dt1, n1)
+        x2 = step(np.array(psi0, dtype=np.complex128), t0, dt2, n2)
+        e = float(np.linalg.norm(x1 - x2))
+        return e / abs(dt1 ** N - dt2 ** N), e, dt2
+
+    monkeypatch.setattr(TS, "error_constant", bad)
+    Dl, V, w = 2.0, 0.5, 1.0
+    op, drives = _problem(Dl, V, w)
+    step = _stepper(op, drives, "CF4:2")
+    T = 5 * math.pi
+    c, _, _ = TS.error_constant(step, PSI0, 0.0, T, 200, 4)
+    n = 120
+    true_err = np.linalg.norm(step(PSI0, 0.0, T / n, n) - _exact(T, Dl, V, w) @ PSI0)
+    assert not 0.7 <= c * T * (T / n) ** 4 / true_err <= 1.3
