@@ -196,3 +196,43 @@ def test_g_sums(name):
     g, x, w, f = S.g_coefficients(S.SCHEMES[name])
     assert np.allclose(g.sum(axis=0), w, atol=5e-16)
     assert np.allclose(g.sum(axis=1), f[:, 0], atol=5e-16)
+
+
+# ---------------------------------------------------------------- planted mistakes
+def test_planted_mirror_sign_error_is_caught(monkeypatch):
+    # rule (R1) with the sign (-1)^n instead of (-1)^(n+1): the second-order
+    # condition and the printed CF4:2 factors must notice
+    def bad(scheme):
+        s, nA = scheme.s, scheme.nA
+        f = np.zeros((s, nA))
+        for i, row in enumerate(scheme.half):
+            for n0, val in enumerate(row):
+                f[i, n0] = val
+                if s - 1 - i != i:
+                    f[s - 1 - i, n0] = (-1.0) ** (n0 + 1) * val
+        return f
+
+    monkeypatch.setattr(S, "full_table", bad)
+    f = S.full_table(S.SCHEMES["CF4:2"])
+    s = f.shape[0]
+    val = sum(f[i, 0] * f[j, 1] - f[j, 0] * f[i, 1] for i in range(s) for j in range(i + 1, s))
+    assert abs(val + 1.0 / 3.0) > 1e-3
+    assert not np.allclose(f, [[0.5, 1 / 3], [0.5, -1 / 3]], atol=0)
+
+
+def test_planted_legendre_weight_error_is_caught(monkeypatch):
+    # g_{i,m} without the factor (2n - 1): the printed CF4:2 weights of
+    # Eq. (UCF4Gauss) must notice
+    def bad(scheme):
+        f = S.full_table(scheme)
+        x, w = S.gauss_legendre(scheme.nA)
+        g = np.zeros((scheme.s, len(x)))
+        for i in range(scheme.s):
+            for m in range(len(x)):
+                g[i, m] = w[m] * sum(S.legendre_shifted(n, x[m]) * f[i, n] for n in range(scheme.nA))
+        return g, x, w, f
+
+    monkeypatch.setattr(S, "g_coefficients", bad)
+    g, x, w, f = S.g_coefficients(S.SCHEMES["CF4:2"])
+    a, b = (3 - 2 * math.sqrt(3)) / 12, (3 + 2 * math.sqrt(3)) / 12
+    assert not np.allclose(g, [[a, b], [b, a]], atol=1e-12)
