@@ -159,3 +159,15 @@ def test_planted_conjugation_error_in_gram_schmidt_is_caught(monkeypatch):
     V, _, _ = K.lanczos(lambda v: lam * v, psi, 40, reorth=True)
     M = np.array(V)
     assert np.abs(M.conj() @ M.T - np.eye(len(V))).max() > 1e-8
+
+
+@pytest.mark.parametrize("tau", [0.3, 1.0])
+def test_expv_tolerance_is_absolute_for_unnormalised_states(tau):
+    # the estimate carries beta_0 = ||psi||: for ||psi|| = 1000 the absolute
+    # error still meets tol (without beta_0 the accepted Krylov spaces are
+    # smaller and the error here exceeds 1e-9)
+    a = W.complex_gaussian(11, 200 * 200).reshape(200, 200)
+    H = 0.5 * (a + a.conj().T)
+    psi = 1000.0 * W.random_state(12, 200)
+    out, log, _ = K.expv(lambda v: H @ v, psi, tau, tol=1e-9, m_max=40)
+    assert np.linalg.norm(out - expm(-1j * tau * H) @ psi) <= 1e-9
