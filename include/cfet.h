@@ -181,6 +181,9 @@ typedef struct cfet_options {
                                 CFET_PREC_F64 and CFET_EXPM_KRYLOV only
                                 (otherwise CFET_EINVAL).  Default 0: the
                                 three-term recurrence alone.                  */
+  int32_t apply_form;        /* CFET_APPLY_* (default CFET_APPLY_AUTO): how the
+                                fixed-point and complex64 kernels apply an
+                                XXZ chain (see below)                         */
 } cfet_options;
 
 /* Number format of the Krylov vectors on the device.  All keep alpha, beta,
@@ -202,10 +205,17 @@ typedef struct cfet_options {
  * CFET_PREC_FX and CFET_PREC_C64 on XXZ chains of 23 or more sites (Krylov
  * bases far beyond the 129 MB L2) apply H in passes over shared-memory tiles
  * (2^11 fixed-point or 2^12 complex64 elements), one pass per window of index
- * bits, instead of gathering far-bit neighbours from DRAM; the environment
- * variable CFET_TILED=0 or 1, read when the context is created, forces the
- * element-wise or the tiled form (13..30 sites).                            */
+ * bits, instead of gathering far-bit neighbours from DRAM.                  */
 enum { CFET_PREC_DEFAULT = 0, CFET_PREC_F64 = 1, CFET_PREC_FX = 2, CFET_PREC_C64 = 3 };
+
+/* cfet_options.apply_form: the form of the XXZ-chain apply in the fixed-point
+ * and complex64 Krylov kernels.
+ *  AUTO        : element-wise below 23 sites, window-tiled from 23 sites.
+ *  ELEMENTWISE : every element gathers its neighbours from global memory.
+ *  TILED       : window passes over shared-memory tiles; chains of 13..30
+ *                sites (other sizes, operators and precisions keep the
+ *                element-wise form).  Any other value: CFET_EINVAL.         */
+enum { CFET_APPLY_AUTO = 0, CFET_APPLY_ELEMENTWISE = 1, CFET_APPLY_TILED = 2 };
 
 /* How cfet_propagate evaluates each stage exponential exp(-i dt H_j) psi.
  *  KRYLOV    : the Lanczos/Krylov loop (Sec. 8.1) with the a-posteriori error

@@ -170,12 +170,14 @@ class Propagator:
     drives: one callable f_k(t) per V_k.  precision: "default" (fixed point;
     FP64 when a PauliSum is involved), "fx", "f64" or "c64"; expm: "krylov" or
     "chebyshev" (fixed point); picture: "schroedinger" or "interaction" (FP64
-    chains); reorth: full re-orthogonalisation of the Lanczos vectors (FP64).
+    chains); reorth: full re-orthogonalisation of the Lanczos vectors (FP64);
+    apply_form: "auto", "elementwise" or "tiled" (XXZ chains in the fixed-point
+    and complex64 kernels).
     """
 
     def __init__(self, H0, V=(), drives=(), *, m_max=16, m_min=2, max_substeps=64, block_size=0,
                  grid_size=0, steps_per_launch=256, barrier_timeout_s=2.0, precision="default", expm="krylov",
-                 picture="schroedinger", reorth=False):
+                 picture="schroedinger", reorth=False, apply_form="auto"):
         lib = _capi.load()
         V = list(V)
         drives = list(drives)
@@ -195,6 +197,7 @@ class Propagator:
         opt.expm = _capi.EXPM[expm]
         opt.picture = _capi.PICTURES[picture]
         opt.reorth = 1 if reorth else 0
+        opt.apply_form = _capi.APPLY_FORMS[apply_form]
         ctx = C.c_void_p()
         st = lib.cfet_create(C.byref(ctx), C.byref(h0), len(V), varr, fns, None, C.byref(opt))
         if st != 0:

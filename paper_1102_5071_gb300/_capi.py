@@ -32,7 +32,8 @@ class cfet_options(C.Structure):
     _fields_ = [("m_max", C.c_int32), ("m_min", C.c_int32), ("max_substeps", C.c_int32),
                 ("block_size", C.c_int32), ("grid_size", C.c_int32), ("steps_per_launch", C.c_int32),
                 ("barrier_timeout_s", C.c_double), ("precision", C.c_int32), ("expm", C.c_int32),
-                ("picture", C.c_int32), ("reorth", C.c_int32)]
+                ("picture", C.c_int32), ("reorth", C.c_int32),
+                ("apply_form", C.c_int32)]
 
 
 CFET_PREC_DEFAULT, CFET_PREC_F64, CFET_PREC_FX, CFET_PREC_C64 = 0, 1, 2, 3
@@ -41,6 +42,8 @@ CFET_EXPM_KRYLOV, CFET_EXPM_CHEBYSHEV = 0, 1
 EXPM = {"krylov": CFET_EXPM_KRYLOV, "chebyshev": CFET_EXPM_CHEBYSHEV}
 CFET_PICTURE_SCHROEDINGER, CFET_PICTURE_INTERACTION = 0, 1
 PICTURES = {"schroedinger": CFET_PICTURE_SCHROEDINGER, "interaction": CFET_PICTURE_INTERACTION}
+CFET_APPLY_AUTO, CFET_APPLY_ELEMENTWISE, CFET_APPLY_TILED = 0, 1, 2
+APPLY_FORMS = {"auto": CFET_APPLY_AUTO, "elementwise": CFET_APPLY_ELEMENTWISE, "tiled": CFET_APPLY_TILED}
 
 
 class cfet_stats(C.Structure):

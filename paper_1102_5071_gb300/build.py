@@ -29,7 +29,7 @@ FLAGS_STAMP = os.path.join(BUILD_DIR, "extra_flags.txt")
 
 def _extra_flags() -> list:
     return os.environ.get("CFET_NVCC_FLAGS", "").split()
-SOURCES = ["kernels.cu", "kernels_fx.cu", "kernels_fx1.cu", "kernels_c64.cu", "kernels_cheb.cu", "capi.cu", "schemes.cpp", "chebyshev.cpp",
+SOURCES = ["kernels.cu", "kernels_fx.cu", "kernels_c64.cu", "kernels_cheb.cu", "capi.cu", "schemes.cpp", "chebyshev.cpp",
            "noalloc.cu", "batch.cu", "adjoint.cu"]
 
 

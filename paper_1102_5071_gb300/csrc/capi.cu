@@ -242,9 +242,6 @@ cfet_status launch_chunk(cfet_ctx* ctx, const PropParams& base, long long e0, lo
   } else if (ctx->opt.expm == CFET_EXPM_CHEBYSHEV)
     e = ctx->family == kFamilySpin ? launch_cheb_spin_fx(p, ctx->spin_fx, ctx->grid, cheb_threads(ctx->block - 32), s)
                                    : launch_cheb_dia_fx(p, ctx->dia_fx, ctx->grid, cheb_threads(ctx->block - 32), s);
-  else if (ctx->precision == CFET_PREC_FX && CFET_FX_ONEPASS)
-    e = ctx->family == kFamilySpin ? launch_propagate_spin_fx1(p, ctx->spin_fx, ctx->grid, ctx->block, s)
-                                   : launch_propagate_dia_fx1(p, ctx->dia_fx, ctx->grid, ctx->block, s);
   else if (ctx->precision == CFET_PREC_FX)
     e = ctx->family == kFamilySpin ? launch_propagate_spin_fx(p, ctx->spin_fx, ctx->grid, ctx->block, s)
                                    : launch_propagate_dia_fx(p, ctx->dia_fx, ctx->grid, ctx->block, s);
@@ -511,6 +508,7 @@ void cfet_options_default(cfet_options* opt) {
   opt->expm = CFET_EXPM_KRYLOV;
   opt->picture = CFET_PICTURE_SCHROEDINGER;
   opt->reorth = 0;
+  opt->apply_form = CFET_APPLY_AUTO;
 }
 
 cfet_status cfet_scheme_info(int32_t scheme, int32_t* order, int32_t* s, int32_t* M, double* f, double* x,
@@ -577,6 +575,8 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
   if (o.reorth != 0 && o.reorth != 1) return fail(nullptr, CFET_EINVAL, "reorth must be 0 or 1");
   if (o.reorth && (o.precision != CFET_PREC_F64 || o.expm != CFET_EXPM_KRYLOV))
     return fail(nullptr, CFET_EINVAL, "reorth requires CFET_PREC_F64 and CFET_EXPM_KRYLOV");
+  if (o.apply_form != CFET_APPLY_AUTO && o.apply_form != CFET_APPLY_ELEMENTWISE && o.apply_form != CFET_APPLY_TILED)
+    return fail(nullptr, CFET_EINVAL, "apply_form must be CFET_APPLY_AUTO, CFET_APPLY_ELEMENTWISE or CFET_APPLY_TILED");
   if (o.block_size == 0) o.block_size = (o.precision == CFET_PREC_F64) ? 256 : 384;
   {
     // FP64 kernel: block_size threads (<= 256); fixed-point and mixed-precision
@@ -926,17 +926,15 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
     }
   }
   // long chains: the window-tiled apply of the complex64 and fixed-point
-  // Krylov kernels (not the one-pass fixed-point form)
-  if (family == kFamilySpin && (ctx->precision == CFET_PREC_C64 || (ctx->precision == CFET_PREC_FX && !CFET_FX_ONEPASS))) {
-    const char* env = std::getenv("CFET_TILED");
+  // Krylov kernels
+  if (family == kFamilySpin && (ctx->precision == CFET_PREC_C64 || ctx->precision == CFET_PREC_FX)) {
     const int min_sites = ctx->precision == CFET_PREC_C64 ? kC64TiledMinSites : kFxTiledMinSites;
-    const bool want_tiled = env && *env ? std::atoi(env) != 0 : nsites >= min_sites;
+    const bool want_tiled = o.apply_form == CFET_APPLY_AUTO ? nsites >= min_sites : o.apply_form == CFET_APPLY_TILED;
     ctx->tiled = want_tiled && nsites >= kTiledMinSites && nsites <= kTiledMaxSites;
   }
   // persistent grid: co-resident maximum, no more CTAs than needed to give
   // every thread at least one element
-  int maxg = ctx->precision == CFET_PREC_FX    ? (CFET_FX_ONEPASS ? max_coresident_blocks_fx1(family, ctx->block)
-                                                                  : max_coresident_blocks_fx(family, ctx->block, ctx->tiled))
+  int maxg = ctx->precision == CFET_PREC_FX    ? max_coresident_blocks_fx(family, ctx->block, ctx->tiled)
                    : ctx->precision == CFET_PREC_C64 ? max_coresident_blocks_c64(family, ctx->block, ctx->tiled)
                    : family == kFamilyPauli          ? max_coresident_blocks_pauli(ctx->block, ctx->pauli.nterms)
                                                      : max_coresident_blocks(family, ctx->block);

@@ -245,20 +245,13 @@ int launch_spin_tables(int N, int L, double J, double Delta, const double* h, do
                        void* stream);
 int launch_propagate_spin_fx(const PropParams& p, const OpSpinFx& op, int grid, int block, void* stream);
 int launch_propagate_dia_fx(const PropParams& p, const OpDiaFx& op, int grid, int block, void* stream);
-// one-pass form of the fixed-point Lanczos kernel (kernels_fx1.cu)
-#ifndef CFET_FX_ONEPASS
-#define CFET_FX_ONEPASS 0
-#endif
-int launch_propagate_spin_fx1(const PropParams& p, const OpSpinFx& op, int grid, int block, void* stream);
-int launch_propagate_dia_fx1(const PropParams& p, const OpDiaFx& op, int grid, int block, void* stream);
-int max_coresident_blocks_fx1(int family, int block);
 int max_coresident_blocks_fx(int family, int block, bool tiled);
 int launch_propagate_spin_c64(const PropParams& p, const OpSpinC& op, int grid, int block, void* stream);
 int launch_propagate_dia_c64(const PropParams& p, const OpDiaC& op, int grid, int block, void* stream);
 int max_coresident_blocks_c64(int family, int block, bool tiled);
 // Chains of at least this many sites take the window-tiled apply
-// (tiled_common.cuh) in the complex64 and fixed-point kernels; the environment
-// variable CFET_TILED (0 or 1) overrides the choice when a context is created.
+// (tiled_common.cuh) in the complex64 and fixed-point kernels, unless
+// cfet_options.apply_form asks for one form.
 constexpr int kC64TiledMinSites = 23;
 constexpr int kFxTiledMinSites = 23;
 constexpr int kTiledMinSites = 13;  // tiles of up to 2^12 elements

@@ -12,34 +12,7 @@
 
 #include "cfet_internal.h"
 
-// Spin apply on two elements per thread and loop iteration (1 = on).
-#ifndef CFET_FX_PAIRS
-#define CFET_FX_PAIRS 1
-#endif
-
-// Streaming cache hints for vectors read or written once per pass (the
-// previous Krylov vector in the apply, the apply output), so that L1 keeps the
-// current vector for the neighbour gathers (1 = on).
-#ifndef CFET_FX_STREAM
-#define CFET_FX_STREAM 0
-#endif
-
 namespace cfet {
-
-__device__ __forceinline__ longlong2 fx_ld_stream(const longlong2* p) {
-#if CFET_FX_STREAM
-  return __ldcs(p);
-#else
-  return *p;
-#endif
-}
-__device__ __forceinline__ void fx_st_stream(longlong2* p, longlong2 v) {
-#if CFET_FX_STREAM
-  __stcs(p, v);
-#else
-  *p = v;
-#endif
-}
 
 // ------------------------------------------------------------------ fixed-point helpers
 constexpr int kFxBits = 57;  // stored |M| < 2^57
@@ -213,7 +186,7 @@ __device__ __forceinline__ longlong2 fx_apply_spin(const longlong2* q, const lon
     }
   }
   if (c.use_prev) {
-    const longlong2 w = fx_ld_stream(qm + x);
+    const longlong2 w = qm[x];
     ur += fx_mulhi(c.m_p, w.x << c.pp);
     ui += fx_mulhi(c.m_p, w.y << c.pp);
   }
@@ -281,7 +254,7 @@ __device__ __forceinline__ void fx_apply_spin2(const longlong2* q, const longlon
     }
   }
   if (c.use_prev) {
-    const longlong2 w1 = fx_ld_stream(qm + x), w2 = fx_ld_stream(qm + x2);
+    const longlong2 w1 = qm[x], w2 = qm[x2];
     ur1 += fx_mulhi(c.m_p, w1.x << c.pp);
     ui1 += fx_mulhi(c.m_p, w1.y << c.pp);
     ur2 += fx_mulhi(c.m_p, w2.x << c.pp);

@@ -38,12 +38,9 @@
 
 namespace cfet {
 
-// Threads per CTA (launch bound) and two-element pairs in the spin pass.
+// Threads per CTA (launch bound).
 #ifndef CFET_CHEB_THREADS
 #define CFET_CHEB_THREADS 768
-#endif
-#ifndef CFET_CHEB_PAIRS
-#define CFET_CHEB_PAIRS 0  // measured: no gain at 768 threads (register-bound), a loss at 640
 #endif
 constexpr int kChebThreads = CFET_CHEB_THREADS;
 
@@ -251,7 +248,7 @@ __device__ __forceinline__ void cheb_pass(const SmemCheb& S, const Op& op, const
       ar = fx_mulhi(S.m_r0, v.x << S.p0);
       ai = fx_mulhi(S.m_r0, v.y << S.p0);
     } else {
-      const longlong2 a = fx_ld_stream(acc + x);
+      const longlong2 a = acc[x];
       ar = fx_rshr(a.x, S.sa);
       ai = fx_rshr(a.y, S.sa);
     }
@@ -263,7 +260,7 @@ __device__ __forceinline__ void cheb_pass(const SmemCheb& S, const Op& op, const
     }
     if (!LAST) {
       dst[x] = y;
-      fx_st_stream(acc + x, make_longlong2(ar, ai));
+      acc[x] = make_longlong2(ar, ai);
       my = max(my, fx_absmax(y.x, y.y));
       ma = max(ma, fx_absmax(ar, ai));
     } else {
@@ -279,25 +276,6 @@ __device__ __forceinline__ void cheb_pass(const SmemCheb& S, const Op& op, const
     }
   };
   int x = wx0;
-#if CFET_CHEB_PAIRS
-  if constexpr (FAMILY == kFamilySpin && APPLY) {  // two elements per loop iteration
-    for (; x + wstep < wxe; x += 2 * wstep) {
-      longlong2 y1, y2;
-      fx_apply_spin2(cur, prev, x, x + wstep, op, S.c, S.mb, y1, y2);
-      const long long m_s = S.m_s;
-      if (m_s != 0) {
-        const longlong2 v1 = cur[x], v2 = cur[x + wstep];
-        const int pk = S.c.pk;
-        y1.x += fx_mulhi(m_s, v1.x << pk);
-        y1.y += fx_mulhi(m_s, v1.y << pk);
-        y2.x += fx_mulhi(m_s, v2.x << pk);
-        y2.y += fx_mulhi(m_s, v2.y << pk);
-      }
-      elem(x, y1);
-      elem(x + wstep, y2);
-    }
-  }
-#endif
   for (; x < wxe; x += wstep) {
     longlong2 y = make_longlong2(0, 0);
     if (APPLY) y = cheb_apply1<FAMILY>(cur, prev, x, dim, op, S.c, S.mb, S.m_s);

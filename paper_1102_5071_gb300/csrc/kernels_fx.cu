@@ -579,25 +579,23 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
                 x = wxe;  // nothing left for the element loops
               }
             }
-#if CFET_FX_PAIRS
             if constexpr (FAMILY == kFamilySpin) {
               for (; x + wstep < wxe; x += 2 * wstep) {
                 longlong2 h1, h2;
                 fx_apply_spin2(q, qm, x, x + wstep, op, c, S.mb, h1, h2);
-                fx_st_stream(u + x, h1);
-                fx_st_stream(u + x + wstep, h2);
+                u[x] = h1;
+                u[x + wstep] = h2;
                 const longlong2 v1 = q[x], v2 = q[x + wstep];
                 a2 += (__int128)v1.x * h1.x + (__int128)v1.y * h1.y;
                 a2 += (__int128)v2.x * h2.x + (__int128)v2.y * h2.y;
                 mx = max(mx, max(fx_absmax(h1.x, h1.y), fx_absmax(h2.x, h2.y)));
               }
             }
-#endif
             for (; x < wxe; x += wstep) {
               longlong2 hv;
               if constexpr (FAMILY == kFamilySpin) hv = fx_apply_spin(q, qm, x, op, c, S.mb);
               else hv = fx_apply_dia(q, qm, x, dim, op, c);
-              fx_st_stream(u + x, hv);
+              u[x] = hv;
               const longlong2 v = q[x];
               a2 += (__int128)v.x * hv.x + (__int128)v.y * hv.y;
               mx = max(mx, fx_absmax(hv.x, hv.y));
@@ -685,7 +683,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
             long long mx = 0;
             const long long tw0 = sm_clock();
             for (int x = wx0; x < wxe; x += wstep) {
-              const longlong2 v = fx_ld_stream(q + x);
+              const longlong2 v = q[x];
               const longlong2 uu = u[x];
               const long long wr = fx_rshr(uu.x, sh_u) + fx_mulhi(m_a, v.x << pk);
               const long long wi = fx_rshr(uu.y, sh_u) + fx_mulhi(m_a, v.y << pk);

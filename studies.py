@@ -1,0 +1,590 @@
+"""Measurement studies of the GB300 CFET/Krylov propagator, beside the
+headline benchmark of bench.py: accuracy against cost per (order, dt), chain
+sizes 20..26, the grid atom, the batched launch, the fidelity gradient,
+Krylov against Chebyshev stage exponentials, time-step selection, Pauli sums,
+re-orthogonalisation, interaction against Schroedinger picture, and speed-ups
+of the mixed-precision, batched and adjoint forms at equal final-state error.
+
+    python studies.py --sweep [--sweep-T T] [--precision fx|f64|c64]
+    python studies.py --study atom|sizes|batch|adjoint|expm|timestep|pauli|reorth|picture|equal_error
+
+Each prints JSON lines.  Nothing here is part of the timed headline path.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+from bench import (DT, M_MAX, N_SITES, ORDER, PHASES, PSI_SEED, SCHEME, TOL, algorithmic_counts,  # noqa: E402
+                   problem)
+
+
+def run_sweep(args):
+    """Accuracy study behind "at fixed final-state error": the N=20 chain over
+    T = 20 with orders 4, 6, 8 (default schemes) and dt in {0.05, 0.02, 0.01},
+    each compared with a reference run (CF8:11, dt = 0.0025, tol 1e-13, m <= 24)
+    by ||psi - psi_ref||_2.  Prints one JSON line per run and a summary line."""
+    import torch
+    import paper_1102_5071_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    pr, psi0 = problem()
+    T = args.sweep_T
+
+    def make(m_max, precision):
+        return P.Propagator(P.XXZChain(N_SITES, pr.J, pr.Delta, pr.h), [P.XField(N_SITES, pr.xfield)],
+                            [pr.drive], m_max=m_max, max_substeps=64, precision=precision)
+
+    ref_prop = make(24, "fx")   # the reference is always an FP64-class run
+    ref = torch.from_numpy(psi0).cuda()
+    dt_ref = 0.0025
+    n_ref = int(round(T / dt_ref))
+    t = time.perf_counter()
+    st_ref = ref_prop.propagate(ref, 0.0, dt_ref, n_ref, order=8, tol=1e-13)
+    ref_s = time.perf_counter() - t
+    ref_prop.close()
+    rows = []
+    prop = make(M_MAX, args.precision)
+    for order in (4, 6, 8):
+        for dt in (0.05, 0.02, 0.01):
+            n = int(round(T / dt))
+            psi = torch.from_numpy(psi0).cuda()
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            st = prop.propagate(psi, 0.0, dt, n, order=order, tol=TOL)
+            ev1.record()
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1)
+            err = torch.linalg.vector_norm(psi - ref).item()
+            row = {"order": order, "dt": dt, "steps": n, "final_state_error": err,
+                   "H_applies": st["n_applies"], "H_applies_per_s": st["n_applies"] / (ms * 1e-3),
+                   "cfet_steps_per_s": n / (ms * 1e-3), "time_s": ms * 1e-3,
+                   "norm_drift": abs(torch.linalg.vector_norm(psi).item() - 1.0)}
+            rows.append(row)
+            print(json.dumps(row))
+    prop.close()
+    summary = {"sweep": "driven XXZ chain N=20, T=%g, tol %g, m_max %d, precision %s" % (T, TOL, M_MAX, args.precision),
+               "reference": {"scheme": "CF8:11", "dt": dt_ref, "tol": 1e-13, "m_max": 24,
+                             "H_applies": st_ref["n_applies"], "time_s": ref_s},
+               "cheapest_for_error": {}}
+    for target in (1e-4, 1e-6, 1e-8):
+        ok = [r for r in rows if r["final_state_error"] <= target]
+        if ok:
+            best = min(ok, key=lambda r: r["time_s"])
+            summary["cheapest_for_error"][f"{target:g}"] = {k: best[k] for k in ("order", "dt", "time_s",
+                                                                                 "final_state_error")}
+    print(json.dumps(summary))
+    return 0
+
+
+def _roofline_study_line(prop, stats, ms, dim, bytes_per_app, elem, label, extra):
+    """bytes_per_app: algorithmic bytes per element of one Lanczos iteration;
+    elem: bytes per vector element (reconstruction reads k vectors, writes 1)."""
+    n_app, n_sub = stats["n_applies"], stats["n_substeps"]
+    kernel_ms = prop.kernel_time_ms()
+    bytes_ = dim * (bytes_per_app * n_app + elem * (n_app + n_sub))
+    line = {"study": label, "H_applies": n_app, "substeps": n_sub, "exponentials": stats["n_exp"],
+            "substeps_per_exponential": n_sub / max(1, stats["n_exp"]), "max_k": stats["max_k"],
+            "H_applies_per_s": n_app / (ms * 1e-3), "ms": ms, "kernel_ms": kernel_ms,
+            "algorithmic_GBps": bytes_ / (kernel_ms * 1e-3) / 1e9,
+            "phase_Mcycles": {k: v * 1e-6 for k, v in zip(PHASES, stats.get("phase_ns", [0] * 8))}}
+    line.update(extra)
+    print(json.dumps(line))
+
+
+def run_study_atom(args):
+    """The grid atom (Nr = 2000, l < 100, dim 200 000, CF8:11, dt = 0.1, m <= 64,
+    tol 1e-10) for --steps steps from t0 = 500 (peak of the pulse envelope),
+    starting from the discrete 1s state: H applies/s, substeps per stage
+    exponential and the projected cost of the full T = 1000 pulse."""
+    import torch
+    import paper_1102_5071_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    a = W.ATOM
+    p = W.grid_atom(Nr=a["Nr"], L=a["L"], dr=a["dr"], E0=a["E0"], omega=a["omega"], Tp=a["Tp"])
+    psi0, e0 = W.atom_ground_state(p)
+    prop = P.Propagator(P.DIA(p.H0_offsets, p.H0_values), [P.DIA(p.V_offsets, p.V_values)], [p.drive],
+                        m_max=a["m_max"], max_substeps=4000, precision=args.precision, grid_size=args.grid_size)
+    psi = torch.from_numpy(psi0).cuda()
+    t0 = 500.0
+    # warm-up: one apply (context, tables and graph set-up); a full atom step
+    # takes seconds, so the timed steps are not preceded by one
+    prop.apply(np.array([1.0, 0.0]), psi, torch.empty_like(psi))
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    st = prop.propagate(psi, t0, a["dt"], args.steps, order=a["order"], tol=a["tol"])
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    nfull = int(round(a["Tp"] / a["dt"]))
+    # per element and iteration: q_k, q_{k-1} read, u written + 5 real diagonals
+    elem, val = (8.0, 4.0) if args.precision == "c64" else (16.0, 8.0)
+    _roofline_study_line(prop, st, ms, p.dim, 3 * elem + 5 * val, elem, "grid atom Nr=2000 L=100 CF8:11 dt=0.1 m<=64 tol 1e-10",
+                         {"steps": args.steps, "t0": t0, "precision": args.precision,
+                          "norm_drift": abs(torch.linalg.vector_norm(psi).item() - 1.0),
+                          "full_pulse_steps": nfull,
+                          "full_pulse_projected_s": ms * 1e-3 / args.steps * nfull})
+    prop.close()
+    return 0
+
+
+def run_study_sizes(args):
+    """The driven chain of the bench at N = 20, 22, 24, 26 (vectors 16 MiB to
+    1 GiB, the larger ones far beyond L2): H applies/s and algorithmic HBM
+    GB/s of the persistent kernel for --steps CFET steps each."""
+    import torch
+    import paper_1102_5071_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    for n in (20, 22, 24, 26):
+        pr = W.spin_chain(n)
+        prop = P.Propagator(P.XXZChain(n, pr.J, pr.Delta, pr.h), [P.XField(n, pr.xfield)], [pr.drive],
+                            m_max=M_MAX, max_substeps=64, precision=args.precision, apply_form=args.apply_form)
+        psi = torch.from_numpy(W.random_state(PSI_SEED, 1 << n)).cuda()
+        prop.propagate(psi, 0.0, DT, 1, order=ORDER, tol=TOL)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        st = prop.propagate(psi, DT, DT, args.steps, order=ORDER, tol=TOL)
+        ev1.record()
+        torch.cuda.synchronize()
+        elem = 8.0 if args.precision == "c64" else 16.0
+        _roofline_study_line(prop, st, ev0.elapsed_time(ev1), 1 << n, 3 * elem, elem,
+                             f"driven XXZ chain N={n} {SCHEME} dt={DT} tol {TOL}",
+                             {"N": n, "steps": args.steps, "precision": args.precision,
+                              "apply_form": args.apply_form})
+        prop.close()
+        del psi
+        torch.cuda.empty_cache()
+    return 0
+
+
+def run_study_batch(args):
+    """256 driven XXZ chains with N uniform in {10..16} (dims 1024..65536),
+    per-instance fields, A ~ U[0.5, 2], omega ~ U[1, 3], CF6:5Opt, dt = 0.02,
+    --steps steps (500 = T 10), tol 1e-10: the batched launch in FP64 and
+    complex64 after the autotuner picked each plan, against the single-instance
+    FP64 propagator run instance by instance (timed over --baseline-steps steps
+    and scaled per step).  Final-state error of the complex64 batch is stated
+    against the FP64 batch."""
+    import torch
+    import paper_1102_5071_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    cfg = W.BATCH
+    insts = W.chain_batch(cfg["n"], cfg["n_lo"], cfg["n_hi"])
+    chains = [P.Chain(c.N, c.J, c.Delta, c.h, c.xfield, None, c.A, c.omega, 0.0) for c in insts]
+    host = [W.random_state(c.psi_seed, 1 << c.N) for c in insts]
+    dims = np.array([1 << c.N for c in insts], dtype=np.float64)
+    order, dt, tol, nsteps = cfg["order"], cfg["dt"], cfg["tol"], args.steps
+    out = {}
+    finals = {}
+    for prec in ("f64", "c64"):
+        bp = P.BatchPropagator(chains, m_max=cfg["m_max"], precision=prec)
+        t = time.perf_counter()
+        plan = bp.tune(0.0, dt, order=order, tol=tol, nsteps=1)
+        tune_s = time.perf_counter() - t
+        dev = [torch.from_numpy(h).cuda() for h in host]
+        bp.propagate(dev, 0.0, dt, 1, order=order, tol=tol)        # warm-up step
+        dev = [torch.from_numpy(h).cuda() for h in host]
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        st = bp.propagate(dev, 0.0, dt, nsteps, order=order, tol=tol)
+        wall = time.perf_counter() - t
+        kms = bp.kernel_time_ms()
+        n_app = np.array([x["n_applies"] for x in st], dtype=np.float64)
+        finals[prec] = [d.cpu().numpy() for d in dev]
+        out[prec] = {"plan": plan, "tune_s": tune_s, "kernel_ms": kms, "wall_s": wall,
+                     "H_applies": float(n_app.sum()), "H_applies_per_s": float(n_app.sum()) / (kms * 1e-3),
+                     "element_applies_per_s": float((n_app * dims).sum()) / (kms * 1e-3),
+                     "cfet_steps_per_s": nsteps * len(insts) / (kms * 1e-3),
+                     "max_k": max(x["max_k"] for x in st)}
+        bp.close()
+        del dev
+    err = max(np.linalg.norm(a - b) for a, b in zip(finals["c64"], finals["f64"]))
+    out["c64"]["final_state_error_vs_f64_batch_max"] = float(err)
+    # single-instance FP64 propagator, instance by instance
+    nb = args.baseline_steps
+    tot_ms, tot_app = 0.0, 0.0
+    for c, h in zip(insts, host):
+        prop = P.Propagator(P.XXZChain(c.N, c.J, c.Delta, c.h), [P.XField(c.N, c.xfield)], [c.drive],
+                            m_max=cfg["m_max"], precision="f64")
+        x = torch.from_numpy(h).cuda()
+        prop.propagate(x, 0.0, dt, 1, order=order, tol=tol)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        s2 = prop.propagate(x, dt, dt, nb, order=order, tol=tol)
+        ev1.record()
+        torch.cuda.synchronize()
+        tot_ms += ev0.elapsed_time(ev1)
+        tot_app += s2["n_applies"]
+        prop.close()
+    single_ms_per_step = tot_ms / nb
+    out["single_instance_f64"] = {"ms_per_batch_step": single_ms_per_step, "steps_timed": nb,
+                                  "H_applies_per_s": tot_app / (tot_ms * 1e-3)}
+    for prec in ("f64", "c64"):
+        out[prec]["speedup_vs_single_instance_f64"] = single_ms_per_step * nsteps / out[prec]["kernel_ms"]
+    print(json.dumps({"study": "batch: %d driven XXZ chains N=%d..%d, CF6:5Opt dt=%g, %d steps, tol %g, m<=%d"
+                      % (len(insts), cfg["n_lo"], cfg["n_hi"], dt, nsteps, tol, cfg["m_max"]),
+                      "sum_dims": float(dims.sum()), **out}))
+    return 0
+
+
+def run_study_adjoint(args):
+    """Gradient of the fidelity loss for the N=18 chain (dim 2^18), 64
+    piecewise-constant amplitude segments ~ U[-1, 1] over T = 16, CF4:2,
+    dt = 0.01, drive A_k cos(2 t) sum_i X_i, tol 1e-10: the adjoint sweep
+    (forward with checkpoints every 25 steps + FP64 backward) against the
+    gradient by central differences with the plain FP64 propagator
+    (2 x 64 forward runs, timed on one and scaled)."""
+    import torch
+    import paper_1102_5071_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    N, nseg, T, dt, omega, tol = 18, 64, 16.0, 0.01, 2.0, 1e-10
+    nsteps = int(round(T / dt))
+    pr = W.spin_chain(N)
+    psi0 = torch.from_numpy(W.random_state(3, 1 << N)).cuda()
+    phi = torch.from_numpy(W.random_state(13, 1 << N)).cuda()
+    amps = W.uniform(7, nseg, -1.0, 1.0)
+    out = {}
+    for prec in ("fx", "f64"):
+        prop = P.Propagator(P.XXZChain(N, pr.J, pr.Delta, pr.h), [P.XField(N, np.ones(N))], [lambda t: 0.0],
+                            m_max=16, precision=prec)
+        prop.fidelity_grad(psi0, phi, 0.0, dt, 50, amps[:2], omega, tol=tol, checkpoint_every=25)   # warm-up
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        L, g, st = prop.fidelity_grad(psi0, phi, 0.0, dt, nsteps, amps, omega, tol=tol, checkpoint_every=25)
+        wall = time.perf_counter() - t
+        out["adjoint_forward_" + prec] = {"loss": L, "wall_s": wall, **st, "grad_norm": float(np.linalg.norm(g))}
+        prop.close()
+    # one plain FP64 forward propagation (a central-difference gradient needs 2 x 64 of them)
+    sps = nsteps // nseg
+
+    def f(t):   # the same piecewise-constant drive, segment of the step containing t
+        return amps[min(int(math.floor(t / dt)) // sps, nseg - 1)] * math.cos(omega * t)
+    prop = P.Propagator(P.XXZChain(N, pr.J, pr.Delta, pr.h), [P.XField(N, np.ones(N))], [f], m_max=16,
+                        precision="f64")
+    x = psi0.clone()
+    prop.propagate(x, 0.0, dt, 10, order=4, tol=tol)
+    x = psi0.clone()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    prop.propagate(x, 0.0, dt, nsteps, order=4, tol=tol)
+    torch.cuda.synchronize()
+    fwd_s = time.perf_counter() - t
+    prop.close()
+    out["f64_forward_s"] = fwd_s
+    out["central_difference_gradient_s"] = 2 * nseg * fwd_s
+    for prec in ("fx", "f64"):
+        out["adjoint_forward_" + prec]["speedup_vs_central_differences_f64"] = (
+            2 * nseg * fwd_s / out["adjoint_forward_" + prec]["wall_s"])
+    print(json.dumps({"study": "fidelity gradient: N=18 chain, 64 segments, T=16, CF4:2 dt=0.01, tol 1e-10",
+                      **out}))
+    return 0
+
+
+def run_study_expm(args):
+    """Krylov (Sec. 8.1, the default) against the Chebyshev technique (Sec. 8.1/8.2)
+    for the stage exponentials, both in the fixed-point format at the same
+    tolerance: the N=20 chain over T = --sweep-T with CF6:5Opt at dt in
+    {0.05, 0.02, 0.01}, each run compared with a reference (CF8:11, dt 0.0025,
+    tol 1e-13, Krylov) by ||psi - psi_ref||_2 (Chebyshev also at tolerances
+    1e-12 and 1e-14); then the grid atom (CF8:11,
+    dt 0.1, from t = 500) for --steps steps with both methods.  One JSON line
+    per run.  Chebyshev algorithmic bytes per element and term: read v_k,
+    v_{k-1} and the partial sum, write v_{k+1} and the partial sum (80 B)."""
+    import torch
+    import paper_1102_5071_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    pr, psi0 = problem()
+    T = args.sweep_T
+
+    def chain(expm, m_max=M_MAX):
+        return P.Propagator(P.XXZChain(N_SITES, pr.J, pr.Delta, pr.h), [P.XField(N_SITES, pr.xfield)],
+                            [pr.drive], m_max=m_max, max_substeps=64, expm=expm)
+
+    def timed(prop, psi, *a, **kw):
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        st = prop.propagate(psi, *a, **kw)
+        ev1.record()
+        torch.cuda.synchronize()
+        return st, ev0.elapsed_time(ev1)
+
+    ref_prop = chain("krylov", 24)
+    ref = torch.from_numpy(psi0).cuda()
+    ref_prop.propagate(ref, 0.0, 0.0025, int(round(T / 0.0025)), order=8, tol=1e-13)
+    ref_prop.close()
+    dim = 1 << N_SITES
+    # the Chebyshev tail bound is nearly attained and its stage errors add up,
+    # while the Krylov estimate is pessimistic: Chebyshev runs at three tolerances
+    for expm, tols in (("krylov", (TOL,)), ("chebyshev", (TOL, 1e-12, 1e-14))):
+        prop = chain(expm)
+        for dt, tol in [(dt, tol) for dt in (0.05, 0.02, 0.01) for tol in tols]:
+            n = int(round(T / dt))
+            psi = torch.from_numpy(psi0).cuda()
+            prop.propagate(psi, 0.0, dt, 2, order=6, tol=tol)        # warm-up (graph, tables)
+            psi = torch.from_numpy(psi0).cuda()
+            st, ms = timed(prop, psi, 0.0, dt, n, order=6, tol=tol)
+            kms = prop.kernel_time_ms()
+            row = {"study": "expm", "workload": "driven XXZ chain N=20 CF6:5Opt T=%g tol %g" % (T, tol),
+                   "expm": expm, "dt": dt, "steps": n, "H_applies": st["n_applies"],
+                   "applies_per_exponential": st["n_applies"] / st["n_exp"], "max_k": st["max_k"],
+                   "H_applies_per_s": st["n_applies"] / (ms * 1e-3), "cfet_steps_per_s": n / (ms * 1e-3),
+                   "time_s": ms * 1e-3, "final_state_error": torch.linalg.vector_norm(psi - ref).item()}
+            if expm == "chebyshev":
+                row["algorithmic_GBps"] = dim * 80.0 * st["n_applies"] / (kms * 1e-3) / 1e9
+            print(json.dumps(row))
+        prop.close()
+    a = W.ATOM
+    p = W.grid_atom(Nr=a["Nr"], L=a["L"], dr=a["dr"], E0=a["E0"], omega=a["omega"], Tp=a["Tp"])
+    psi0a, _ = W.atom_ground_state(p)
+    outs = {}
+    for expm in ("krylov", "chebyshev"):
+        prop = P.Propagator(P.DIA(p.H0_offsets, p.H0_values), [P.DIA(p.V_offsets, p.V_values)], [p.drive],
+                            m_max=a["m_max"], max_substeps=4000, expm=expm)
+        psi = torch.from_numpy(psi0a).cuda()
+        prop.apply(np.array([1.0, 0.0]), psi, torch.empty_like(psi))
+        st, ms = timed(prop, psi, 500.0, a["dt"], args.steps, order=a["order"], tol=a["tol"])
+        outs[expm] = psi
+        print(json.dumps({"study": "expm", "workload": "grid atom Nr=2000 L=100 CF8:11 dt=0.1 tol %g from t=500"
+                          % a["tol"], "expm": expm, "steps": args.steps, "H_applies": st["n_applies"],
+                          "applies_per_exponential": st["n_applies"] / st["n_exp"], "max_k": st["max_k"],
+                          "H_applies_per_s": st["n_applies"] / (ms * 1e-3), "time_s": ms * 1e-3,
+                          "ms_per_step": ms / args.steps}))
+        prop.close()
+    print(json.dumps({"study": "expm", "atom_krylov_vs_chebyshev_difference":
+                      torch.linalg.vector_norm(outs["krylov"] - outs["chebyshev"]).item()}))
+    return 0
+
+
+def run_study_timestep(args):
+    """Time-step selection (Sec. 6.6) on the N=20 chain over T = --sweep-T,
+    order 4 (CF4:2), Krylov tol 1e-12: (a) cfet_select_dt with c probed over
+    T/10 for goals 1e-6, 1e-8, 1e-10, then the run with the selected step,
+    its error against a reference (CF8:11, dt T/1600, tol 1e-13) and the cost
+    including the probe; (b) a chirped drive 0.8 cos(0.5 t + 0.15 t^2):
+    cfet_propagate_adaptive for goal 1e-8 against a uniform grid with as many
+    steps as the adaptive run took (trial steps included)."""
+    import torch
+    import paper_1102_5071_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    pr, psi0 = problem()
+    T = args.sweep_T
+
+    def chain(drive):
+        return P.Propagator(P.XXZChain(N_SITES, pr.J, pr.Delta, pr.h), [P.XField(N_SITES, pr.xfield)], [drive],
+                            m_max=M_MAX, max_substeps=64)
+
+    def reference(prop):
+        ref = torch.from_numpy(psi0).cuda()
+        prop.propagate(ref, 0.0, T / 1600, 1600, order=8, tol=1e-13)
+        return ref
+
+    prop = chain(pr.drive)
+    ref = reference(prop)
+    for target in (1e-6, 1e-8, 1e-10):
+        x = torch.from_numpy(psi0).cuda()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        dt, n, c = prop.select_dt(x, 0.0, T, target, T / 10, 8, order=4, tol=1e-12)
+        tp = time.perf_counter() - t
+        st = prop.propagate(x, 0.0, dt, n, order=4, tol=1e-12)
+        torch.cuda.synchronize()
+        tt = time.perf_counter() - t
+        print(json.dumps({"study": "timestep", "workload": "driven XXZ chain N=20 CF4:2 T=%g" % T, "goal": target,
+                          "c": c, "dt": dt, "steps": n, "final_state_error": torch.linalg.vector_norm(x - ref).item(),
+                          "probe_s": tp, "total_s": tt, "H_applies": st["n_applies"]}))
+    prop.close()
+
+    def chirp(t):
+        return 0.8 * math.cos(0.5 * t + 0.15 * t * t)
+
+    prop = chain(chirp)
+    ref = reference(prop)
+    x = torch.from_numpy(psi0).cuda()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    hs, trials, st = prop.propagate_adaptive(x, 0.0, T, 1e-8, 0.05, 1e-4, 1.0, order=4, tol=1e-12)
+    torch.cuda.synchronize()
+    ta = time.perf_counter() - t
+    err_a = torch.linalg.vector_norm(x - ref).item()
+    n_uni = 3 * trials        # every trial costs one step of h and two of h/2
+    y = torch.from_numpy(psi0).cuda()
+    prop.propagate(y, 0.0, T / n_uni, n_uni, order=4, tol=1e-12)
+    err_u = torch.linalg.vector_norm(y - ref).item()
+    print(json.dumps({"study": "timestep", "workload": "driven XXZ chain N=20, chirped drive, CF4:2 T=%g" % T,
+                      "goal": 1e-8, "accepted_steps": len(hs), "trial_steps": trials,
+                      "h_first_last": [hs[0], hs[len(hs) // 2], hs[-1]], "adaptive_error": err_a, "adaptive_s": ta,
+                      "uniform_steps_same_cost": n_uni, "uniform_error": err_u}))
+    prop.close()
+    return 0
+
+
+def run_study_pauli(args):
+    """The N=20 driven chain through the general Pauli-sum kernel (97 strings:
+    XX, YY, ZZ per bond, Z and X per site) against the FP64 chain kernel,
+    CF6:5Opt, dt 0.02, tol 1e-10, m <= 16, --steps steps: H applies/s of each
+    and the difference of their final states."""
+    import torch
+    import paper_1102_5071_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    N = N_SITES
+    pr = W.spin_chain(N)
+    terms = []
+    for i in range(N - 1):
+        terms += [(pr.J, {i: "X", i + 1: "X"}), (pr.J, {i: "Y", i + 1: "Y"}), (pr.J * pr.Delta, {i: "Z", i + 1: "Z"})]
+    terms += [(float(pr.h[i]), {i: "Z"}) for i in range(N)]
+    forms = {
+        "chain kernel (FP64)": lambda: P.Propagator(P.XXZChain(N, pr.J, pr.Delta, pr.h), [P.XField(N, pr.xfield)],
+                                                    [pr.drive], m_max=M_MAX, precision="f64"),
+        "Pauli-sum kernel (FP64)": lambda: P.Propagator(P.PauliSum(N, terms),
+                                                        [P.PauliSum(N, [(float(pr.xfield[i]), {i: "X"})
+                                                                        for i in range(N)])],
+                                                        [pr.drive], m_max=M_MAX),
+    }
+    outs = []
+    for name, make in forms.items():
+        prop = make()
+        psi = torch.from_numpy(W.random_state(PSI_SEED, 1 << N)).cuda()
+        prop.propagate(psi, 0.0, DT, 1, order=ORDER, tol=TOL)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        st = prop.propagate(psi, DT, DT, args.steps, order=ORDER, tol=TOL)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        outs.append(psi)
+        print(json.dumps({"study": "pauli", "workload": f"driven XXZ chain N={N} {SCHEME} dt={DT} tol {TOL}",
+                          "form": name, "steps": args.steps, "H_applies": st["n_applies"], "ms": ms,
+                          "H_applies_per_s": st["n_applies"] / ms * 1e3}))
+        prop.close()
+    print(json.dumps({"study": "pauli", "final_state_difference": torch.linalg.vector_norm(outs[0] - outs[1]).item()}))
+    return 0
+
+
+def run_study_reorth(args):
+    """Cost of full re-orthogonalisation: the N=20 chain in FP64 (CF6:5Opt,
+    dt 0.02, tol 1e-10, m <= 16) with the plain three-term recurrence and with
+    one classical Gram-Schmidt sweep per Lanczos vector, --steps steps: H
+    applies/s of each and the difference of their final states."""
+    import torch
+    import paper_1102_5071_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    pr = W.spin_chain(N_SITES)
+    outs = []
+    for reorth in (False, True):
+        prop = P.Propagator(P.XXZChain(N_SITES, pr.J, pr.Delta, pr.h), [P.XField(N_SITES, pr.xfield)], [pr.drive],
+                            m_max=M_MAX, precision="f64", reorth=reorth)
+        psi = torch.from_numpy(W.random_state(PSI_SEED, 1 << N_SITES)).cuda()
+        prop.propagate(psi, 0.0, DT, 1, order=ORDER, tol=TOL)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        st = prop.propagate(psi, DT, DT, args.steps, order=ORDER, tol=TOL)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        outs.append(psi)
+        print(json.dumps({"study": "reorth", "workload": f"driven XXZ chain N={N_SITES} {SCHEME} dt={DT} tol {TOL}",
+                          "reorth": reorth, "steps": args.steps, "H_applies": st["n_applies"], "ms": ms,
+                          "H_applies_per_s": st["n_applies"] / ms * 1e3}))
+        prop.close()
+    print(json.dumps({"study": "reorth", "final_state_difference": torch.linalg.vector_norm(outs[0] - outs[1]).item()}))
+    return 0
+
+
+def run_study_picture(args):
+    """Interaction against Schroedinger picture (Secs. 9.3, 9.4), FP64 Krylov,
+    N=20 chain, CF6:5Opt, tol 1e-10, m <= 16, over T = --sweep-T: the default
+    chain (|h_i| <= 1, J Delta = 0.5) and one with a strong diagonal (h_i in
+    [-8, 8], Delta = 4): Krylov applies per exponential, time, and the error of
+    each against a fine Schroedinger-picture reference (fixed point, CF8:11,
+    dt T/400, tol 1e-13)."""
+    import torch
+    import paper_1102_5071_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    T = args.sweep_T
+    psi0 = W.random_state(PSI_SEED, 1 << N_SITES)
+    for label, h_scale, Delta in (("default chain", 1.0, 0.5), ("strong diagonal", 8.0, 4.0)):
+        pr = W.spin_chain(N_SITES, Delta=Delta)
+        h = pr.h * h_scale
+
+        def make(picture, m_max=M_MAX, precision="f64"):
+            return P.Propagator(P.XXZChain(N_SITES, pr.J, Delta, h), [P.XField(N_SITES, pr.xfield)], [pr.drive],
+                                m_max=m_max, max_substeps=200, precision=precision, picture=picture)
+
+        ref_p = make("schroedinger", 30, "fx")
+        ref = torch.from_numpy(psi0).cuda()
+        ref_p.propagate(ref, 0.0, T / 400, 400, order=8, tol=1e-13)
+        ref_p.close()
+        for picture in ("schroedinger", "interaction"):
+            prop = make(picture)
+            for dt in (0.02, 0.005):
+                n = int(round(T / dt))
+                x = torch.from_numpy(psi0).cuda()
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                st = prop.propagate(x, 0.0, dt, n, order=6, tol=TOL)
+                torch.cuda.synchronize()
+                el = time.perf_counter() - t
+                print(json.dumps({"study": "picture", "workload": "N=20 chain, %s, CF6:5Opt T=%g" % (label, T),
+                                  "picture": picture, "dt": dt, "steps": n,
+                                  "applies_per_exponential": st["n_applies"] / st["n_exp"],
+                                  "substeps_per_exponential": st["n_substeps"] / st["n_exp"],
+                                  "time_s": el, "final_state_error": torch.linalg.vector_norm(x - ref).item()}))
+            prop.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--precision", default="fx", choices=["fx", "f64", "c64"])
+    ap.add_argument("--sweep", action="store_true",
+                    help="accuracy study: final-state error and throughput per (order, dt) over T")
+    ap.add_argument("--sweep-T", type=float, default=20.0)
+    ap.add_argument("--study", choices=sorted(STUDIES))
+    ap.add_argument("--grid-size", type=int, default=0, help="CTAs of the persistent kernel (0 = co-resident maximum)")
+    ap.add_argument("--apply-form", default="auto", choices=["auto", "elementwise", "tiled"],
+                    help="sizes study: XXZ-chain apply form of the fixed-point and complex64 kernels")
+    ap.add_argument("--baseline-steps", type=int, default=10,
+                    help="batch study: steps of the single-instance baseline per instance")
+    args = ap.parse_args()
+    if args.sweep:
+        return run_sweep(args)
+    if args.study is None:
+        ap.error("give --sweep or --study")
+    return STUDIES[args.study](args)
+
+
+STUDIES = {"atom": run_study_atom, "sizes": run_study_sizes, "batch": run_study_batch, "adjoint": run_study_adjoint,
+           "expm": run_study_expm, "timestep": run_study_timestep, "pauli": run_study_pauli,
+           "reorth": run_study_reorth, "picture": run_study_picture}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -30,6 +30,9 @@ pytestmark = pytest.mark.gpu
 ULP32 = 2.0 ** -24
 
 
+FORMS = {"0": "elementwise", "1": "tiled"}
+
+
 def budget(n_substeps):
     return n_substeps * 64 * ULP32
 
@@ -221,14 +224,13 @@ def test_c64_full_size_atom_without_field_keeps_the_1s_state(torch_cuda):
 
 # ---------------------------------------------------------------- window-tiled apply
 # Long chains take the window-tiled apply (shared-memory tiles of 2^12
-# elements, one pass per window of index bits; the environment variable
-# CFET_TILED forces it on or off when the context is created).  Chains of
+# elements, one pass per window of index bits; the option apply_form forces it
+# on or off).  Chains of
 # 13..19 sites have two windows, 20..26 three, 27..30 four.
 
 @pytest.mark.parametrize("N,nfields", [(13, 1), (14, 2), (16, 1), (17, 2)])
-def test_c64_tiled_matches_oracle(torch_cuda, monkeypatch, N, nfields):
-    monkeypatch.setenv("CFET_TILED", "1")
-    prop, op, drives = _spin(N, nfields=nfields, m_max=16, max_substeps=200)
+def test_c64_tiled_matches_oracle(torch_cuda, N, nfields):
+    prop, op, drives = _spin(N, nfields=nfields, m_max=16, max_substeps=200, apply_form="tiled")
     err, same, st, aerr = _run(torch_cuda, prop, op, drives, W.random_state(11, 1 << N), 0.2, 0.05, 3, "CF6:5Opt",
                                1e-9, 16)
     assert err <= budget(st["n_substeps"]), (err, st["n_substeps"])
@@ -251,7 +253,7 @@ def _one_magnon_hamiltonian(N, J, Delta, h):
 
 
 @pytest.mark.parametrize("N", [22, 23, 27])
-def test_c64_tiled_one_magnon_sector_is_exact(torch_cuda, monkeypatch, N):
+def test_c64_tiled_one_magnon_sector_is_exact(torch_cuda, N):
     # without an x field the one-magnon sector is closed: a chain of 22, 23
     # (three windows) or 27 sites (four) started with one spin down must follow the N x N
     # problem exactly and leave every other amplitude at zero; hops across all
@@ -262,11 +264,10 @@ def test_c64_tiled_one_magnon_sector_is_exact(torch_cuda, monkeypatch, N):
     H6 = O.xxz_dense(6, 0.8, 0.6, h6)
     idx6 = [1 << k for k in range(6)]
     assert np.allclose(H6[np.ix_(idx6, idx6)], _one_magnon_hamiltonian(6, 0.8, 0.6, h6), atol=1e-14)
-    monkeypatch.setenv("CFET_TILED", "1")
     J, Dl = 0.8, 0.6
     h = W.uniform(4, N, -1, 1)
     prop = P.Propagator(P.XXZChain(N, J, Dl, h), [P.XField(N, np.zeros(N))], [lambda t: 0.0], m_max=24,
-                        max_substeps=400, precision="c64")
+                        max_substeps=400, precision="c64", apply_form="tiled")
     k0, T = N // 2 - 1, 3.0
     psi0 = np.zeros(1 << N, dtype=np.complex128)
     psi0[1 << k0] = 1.0
@@ -284,13 +285,12 @@ def test_c64_tiled_one_magnon_sector_is_exact(torch_cuda, monkeypatch, N):
     assert np.linalg.norm(rest) == 0.0
 
 
-def test_c64_tiled_zero_coupling_factorises_n22(torch_cuda, monkeypatch):
+def test_c64_tiled_zero_coupling_factorises_n22(torch_cuda):
     # J = 0 with two site-dependent x fields: the chain of 22 sites (three
     # windows) factorises into driven two-level systems (flips of every bit,
     # per-site field coefficients, diagonal); sampled amplitudes against the
     # product of the oracle's single-site propagations
     import paper_1102_5071_gb300 as P
-    monkeypatch.setenv("CFET_TILED", "1")
     N = 22
     pr = W.spin_chain(N, J=0.0, Delta=0.0, A=1.3, omega=1.7)
     a1, a2 = W.uniform(21, N, 0.5, 1.5), W.uniform(22, N, -1, 1)
@@ -299,7 +299,7 @@ def test_c64_tiled_zero_coupling_factorises_n22(torch_cuda, monkeypatch):
         return 0.4 * math.sin(0.9 * t)
 
     prop = P.Propagator(P.XXZChain(N, 0.0, 0.0, pr.h), [P.XField(N, a1), P.XField(N, a2)], [pr.drive, g],
-                        m_max=16, precision="c64")
+                        m_max=16, precision="c64", apply_form="tiled")
     psi0 = W.neel_state(N)
     nsteps, dt = 30, 0.05
     x = _dev(torch_cuda, psi0)
@@ -320,7 +320,7 @@ def test_c64_tiled_zero_coupling_factorises_n22(torch_cuda, monkeypatch):
     assert abs(np.linalg.norm(out) - 1.0) <= budget(st["n_substeps"])
 
 
-def test_c64_tiled_matches_elementwise_and_fixed_point_n22(torch_cuda, monkeypatch):
+def test_c64_tiled_matches_elementwise_and_fixed_point_n22(torch_cuda):
     # the driven chain of 22 sites: tiled and element-wise complex64 applies
     # replaying the fixed-point path's decisions agree within twice the
     # rounding budget, and each within the budget of the fixed-point result
@@ -336,8 +336,7 @@ def test_c64_tiled_matches_elementwise_and_fixed_point_n22(torch_cuda, monkeypat
     _, log = fx.propagate(xf, 0.1, 0.04, 2, order=6, tol=1e-9, record=True)
     outs = {}
     for flag in ("1", "0"):
-        monkeypatch.setenv("CFET_TILED", flag)
-        prop, _, _ = _spin(N, **kw)
+        prop, _, _ = _spin(N, apply_form=FORMS[flag], **kw)
         x = _dev(torch_cuda, psi0)
         st = prop.propagate(x, 0.1, 0.04, 2, order=6, tol=1e-9, forced=log)
         outs[flag] = x.cpu().numpy()

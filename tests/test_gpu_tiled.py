@@ -1,8 +1,8 @@
 """GPU parity of the window-tiled apply of the fixed-point kernel (long XXZ
 chains; tiles of 2^11 elements, one pass per window of index bits; two
 windows for 12..18 sites, three for 19..25, four for 26..32).  The
-environment variable CFET_TILED forces the tiled or the element-wise form when
-a context is created (the default takes the tiled form from 23 sites).
+option apply_form forces the tiled or the element-wise form (the default
+takes the tiled form from 23 sites).
 
 Tolerances as in test_gpu_parity.py: ||psi_gpu - psi_oracle||_2 <= 1e-10 with
 the oracle's Krylov decisions replayed; the tiled and element-wise forms
@@ -21,6 +21,7 @@ from oracle import cfet as OC, operators as O
 pytestmark = pytest.mark.gpu
 
 PARITY = 1e-10
+FORMS = {"0": "elementwise", "1": "tiled"}
 
 
 @pytest.fixture(scope="module")
@@ -48,10 +49,9 @@ def _spin(N, nfields=1, J=1.0, Delta=0.5, **kw):
 
 
 @pytest.mark.parametrize("N,nfields", [(13, 1), (14, 2), (16, 1)])
-def test_fx_tiled_matches_oracle(torch_cuda, monkeypatch, N, nfields):
+def test_fx_tiled_matches_oracle(torch_cuda, N, nfields):
     # two windows; forced (the oracle's decisions) and adaptive runs
-    monkeypatch.setenv("CFET_TILED", "1")
-    prop, op, drives = _spin(N, nfields=nfields, m_max=16, max_substeps=200)
+    prop, op, drives = _spin(N, nfields=nfields, m_max=16, max_substeps=200, apply_form="tiled")
     psi0 = W.random_state(11, 1 << N)
     ref, log, na = OC.propagate(op, psi0, 0.2, 0.05, 2, "CF6:5Opt", drives, 1e-11, 16, return_log=True,
                                 max_substeps=200)
@@ -65,11 +65,10 @@ def test_fx_tiled_matches_oracle(torch_cuda, monkeypatch, N, nfields):
 
 
 @pytest.mark.parametrize("N,nfields", [(19, 2), (20, 1)])
-def test_fx_tiled_three_windows_match_oracle(torch_cuda, monkeypatch, N, nfields):
+def test_fx_tiled_three_windows_match_oracle(torch_cuda, N, nfields):
     # three windows (19 sites with site-dependent fields; 20 sites, the
     # benchmark chain): one CF4:2 step with a fixed Krylov dimension 10
-    monkeypatch.setenv("CFET_TILED", "1")
-    prop, op, drives = _spin(N, nfields=nfields, m_max=10)
+    prop, op, drives = _spin(N, nfields=nfields, m_max=10, apply_form="tiled")
     psi0 = W.random_state(2, 1 << N)
     ref = OC.propagate(op, psi0, 0.0, 0.05, 1, 4, drives, 0.0, 10)
     t = _dev(torch_cuda, psi0)
@@ -92,7 +91,7 @@ def _one_magnon_hamiltonian(N, J, Delta, h):
 
 
 @pytest.mark.parametrize("N", [22, 26])
-def test_fx_tiled_one_magnon_sector_is_exact(torch_cuda, monkeypatch, N):
+def test_fx_tiled_one_magnon_sector_is_exact(torch_cuda, N):
     # without an x field the one-magnon sector is closed: 22 sites (three
     # windows) and 26 sites (four) started with one spin down follow the N x N
     # problem to the Krylov tolerance, every other amplitude stays exactly zero
@@ -102,11 +101,10 @@ def test_fx_tiled_one_magnon_sector_is_exact(torch_cuda, monkeypatch, N):
     idx6 = [1 << k for k in range(6)]
     assert np.allclose(O.xxz_dense(6, 0.8, 0.6, h6)[np.ix_(idx6, idx6)], _one_magnon_hamiltonian(6, 0.8, 0.6, h6),
                        atol=1e-14)
-    monkeypatch.setenv("CFET_TILED", "1")
     J, Dl = 0.8, 0.6
     h = W.uniform(4, N, -1, 1)
     prop = P.Propagator(P.XXZChain(N, J, Dl, h), [P.XField(N, np.zeros(N))], [lambda t: 0.0], m_max=20,
-                        max_substeps=400, precision="fx")
+                        max_substeps=400, precision="fx", apply_form="tiled")
     k0, T = N // 2 - 1, 2.0
     psi0 = np.zeros(1 << N, dtype=np.complex128)
     psi0[1 << k0] = 1.0
@@ -124,12 +122,11 @@ def test_fx_tiled_one_magnon_sector_is_exact(torch_cuda, monkeypatch, N):
     assert np.linalg.norm(rest) == 0.0
 
 
-def test_fx_tiled_zero_coupling_factorises_n22(torch_cuda, monkeypatch):
+def test_fx_tiled_zero_coupling_factorises_n22(torch_cuda):
     # J = 0 with two site-dependent x fields: 22 sites (three windows)
     # factorise into driven two-level systems; sampled amplitudes against the
     # product of the oracle's single-site propagations
     import paper_1102_5071_gb300 as P
-    monkeypatch.setenv("CFET_TILED", "1")
     N = 22
     pr = W.spin_chain(N, J=0.0, Delta=0.0, A=1.3, omega=1.7)
     a1, a2 = W.uniform(21, N, 0.5, 1.5), W.uniform(22, N, -1, 1)
@@ -138,7 +135,7 @@ def test_fx_tiled_zero_coupling_factorises_n22(torch_cuda, monkeypatch):
         return 0.4 * math.sin(0.9 * t)
 
     prop = P.Propagator(P.XXZChain(N, 0.0, 0.0, pr.h), [P.XField(N, a1), P.XField(N, a2)], [pr.drive, g],
-                        m_max=16, precision="fx")
+                        m_max=16, precision="fx", apply_form="tiled")
     psi0 = W.neel_state(N)
     nsteps, dt = 30, 0.05
     x = _dev(torch_cuda, psi0)
@@ -159,7 +156,7 @@ def test_fx_tiled_zero_coupling_factorises_n22(torch_cuda, monkeypatch):
     assert abs(np.linalg.norm(out) - 1.0) <= PARITY
 
 
-def test_fx_tiled_matches_elementwise_n23(torch_cuda, monkeypatch):
+def test_fx_tiled_matches_elementwise_n23(torch_cuda):
     # the driven chain of 23 sites: the element-wise run's decisions replayed
     # by the tiled form; the two results agree far below the parity bound
     N = 23
@@ -167,8 +164,7 @@ def test_fx_tiled_matches_elementwise_n23(torch_cuda, monkeypatch):
     out = {}
     log = None
     for flag in ("0", "1"):
-        monkeypatch.setenv("CFET_TILED", flag)
-        prop, _, _ = _spin(N, m_max=16, max_substeps=200)
+        prop, _, _ = _spin(N, m_max=16, max_substeps=200, apply_form=FORMS[flag])
         x = _dev(torch_cuda, psi0)
         if log is None:
             _, log = prop.propagate(x, 0.1, 0.04, 2, order=6, tol=1e-10, record=True)
