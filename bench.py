@@ -56,6 +56,18 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 fl
 DRAM_BYTES_PER_ITERATION = {"fx": (1.207240448e9 + 1.633021184e9) / 76, "c64": (191.0784e6 + 649.152256e6) / 76,
                             "f64": None}
 
+# ncu L2 (lts__t_bytes) bytes per Lanczos iteration, same capture; None until measured
+LTS_BYTES_PER_ITERATION = {"fx": None, "c64": None, "f64": None}
+
+# final-state error: horizon, and the reference run (CF8:11 at REF_DT, REF_TOL)
+ERR_T = 1.0
+REF_DT = 0.0025
+REF_TOL = 1e-13
+
+# L2 copy probe: two buffers of this size (together far below the 129 MB L2)
+L2_PROBE_BYTES = 16 << 20
+L2_PROBE_REPS = 2000
+
 # ncu DRAM read+write bytes per term of the Chebyshev kernel (2-step capture: 66 terms)
 DRAM_BYTES_PER_TERM_CHEB = (17.067008e6 + 21.68192e6) / 66
 
@@ -158,22 +170,79 @@ class ClockSampler:
                 if any(r[3].replace(".", "").isdigit() for r in rows) else None}
 
 
-def cpu_baseline_sample():
-    """The oracle, as it stands, on a bounded sample of the same workload: one
-    stage exponential of the first CF6:5Opt step with a fixed Krylov dimension
-    of 6 (6 H applications on the 2^20 chain)."""
-    from oracle import cfet as OC, krylov as OK, operators as O, schemes as OS
+# ---------------------------------------------------------------- oracle on the host cores
+# Worker processes (started with "spawn": the parent has already touched the
+# GPU) each build the problem once and run the oracle's Lanczos exponential on
+# it; the parent adds their H applications and divides by the wall time.
+_ORACLE = {}
+
+
+def _oracle_init():
+    from oracle import cfet as OC, operators as O, schemes as OS
     pr, psi0 = problem()
-    op = O.SpinChain(N_SITES, pr.J, pr.Delta, pr.h, [pr.xfield])
-    c = OC.stage_coefficients(OS.get(SCHEME), 0.0, DT, [pr.drive])[-1]
+    _ORACLE["op"] = O.SpinChain(N_SITES, pr.J, pr.Delta, pr.h, [pr.xfield])
+    _ORACLE["psi0"] = psi0
+    _ORACLE["drive"] = pr.drive
+    _ORACLE["OC"], _ORACLE["OS"] = OC, OS
+
+
+def _oracle_task(args):
+    """One bounded sample: the first stage exponential (exp(Omega_s)) of the
+    CF6:5Opt step at t = step * DT, either adaptive (tol, m_max of the bench)
+    or with a fixed Krylov dimension k_fixed; returns the H applications."""
+    from oracle import krylov as OK
+    step, k_fixed = args
+    OC, OS, op = _ORACLE["OC"], _ORACLE["OS"], _ORACLE["op"]
+    c = OC.stage_coefficients(OS.get(SCHEME), step * DT, DT, [_ORACLE["drive"]])[-1]
+    tol, m = (0.0, k_fixed) if k_fixed else (TOL, M_MAX)
+    _, _, na = OK.expv(lambda v: op.apply(c, v), _ORACLE["psi0"], DT, tol, m)
+    return na
+
+
+class OraclePool:
+    """The oracle, as it stands, on `workers` host processes (one thread each)."""
+
+    def __init__(self, workers):
+        import multiprocessing as mp
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[k] = "1"
+        self.workers = workers
+        self.pool = mp.get_context("spawn").Pool(workers, initializer=_oracle_init)
+
+    def run(self, step, k_fixed=0):
+        t = time.perf_counter()
+        na = sum(self.pool.map(_oracle_task, [(step, k_fixed)] * self.workers, chunksize=1))
+        return na, time.perf_counter() - t
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def host_desc():
+    return f"{platform.machine()}, {os.cpu_count()} cores"
+
+
+def cpu_baseline_sample():
+    """The oracle on a bounded sample of the same workload: the first stage
+    exponential of CF6:5Opt on the N=20 chain with a fixed Krylov dimension of
+    6 (6 H applications), once on one core and once on every host core at the
+    same time (one process per core, each doing the same sample)."""
     k = 6
-    t = time.perf_counter()
-    _, log, na = OK.expv(lambda v: op.apply(c, v), psi0, DT, 0.0, k)
-    el = time.perf_counter() - t
-    return {"value": na / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle expv, first stage exponential of {SCHEME} on the N={N_SITES} chain, "
-                      f"fixed Krylov dimension {k} ({na} H applies, {el:.1f} s, numpy single thread, "
-                      f"{platform.machine()} {os.cpu_count()} cores)"}
+    one = OraclePool(1)
+    one.run(0, k)                        # warm: imports, problem set-up
+    na1, el1 = one.run(0, k)
+    one.close()
+    P = os.cpu_count() or 1
+    allc = OraclePool(P)
+    allc.run(0, 2)
+    naP, elP = allc.run(0, k)
+    allc.close()
+    return {"value": naP / elP, "unit": UNIT, "cores": P, "kind": "oracle",
+            "single_core_value": na1 / el1,
+            "sample": f"oracle expv, first stage exponential of {SCHEME} on the N={N_SITES} chain, fixed Krylov "
+                      f"dimension {k} ({k} H applies per process): {P} processes with one numpy thread each, "
+                      f"{elP:.1f} s; alone on one core {el1:.1f} s ({host_desc()})"}
 
 
 def aggregate_over_ranks(ms, units, device="cuda"):
@@ -200,34 +269,175 @@ def dist_env():
 
 
 def run_reference(args):
+    """The reference arm: the oracle on every host core.  Each step is one
+    bounded sample per core: the first stage exponential of the CF6:5Opt step
+    at t = step * dt with a fixed Krylov dimension of 2 (two H applications on
+    the full 2^20 vector; an adaptive exponential takes ~7 and would make the
+    run last many minutes)."""
     ws, rank, _ = dist_env()
     if ws > 1 and rank != 0:
         return 0
-    from oracle import cfet as OC, krylov as OK, operators as O, schemes as OS
-    pr, psi0 = problem()
-    op = O.SpinChain(N_SITES, pr.J, pr.Delta, pr.h, [pr.xfield])
-    c = OC.stage_coefficients(OS.get(SCHEME), 0.0, DT, [pr.drive])[-1]
-    k = 2   # bounded sample per step: two Lanczos iterations on the full vector
-    psi = psi0
-    for _ in range(args.warmup):
-        psi, _, _ = OK.expv(lambda v: op.apply(c, v), psi, DT, 0.0, k)
-    t = time.perf_counter()
-    na_tot = 0
-    for _ in range(args.steps):
-        psi, _, na = OK.expv(lambda v: op.apply(c, v), psi, DT, 0.0, k)
+    P = os.cpu_count() or 1
+    pool = OraclePool(P)
+    k_fixed = 2
+    for w in range(args.warmup):
+        pool.run(w, k_fixed)
+    na_tot, el = 0, 0.0
+    for k in range(args.steps):
+        na, t = pool.run(args.warmup + k, k_fixed)
         na_tot += na
-    el = time.perf_counter() - t
+        el += t
+    pool.close()
     value = na_tot / el
-    sample = (f"each step: oracle expv with fixed Krylov dimension {k} on the N={N_SITES} chain "
-              f"({k} H applies), numpy single thread, {platform.machine()} {os.cpu_count()} cores")
+    sample = (f"each step: on each of {P} processes (one numpy thread each) the oracle's Krylov exponential "
+              f"of the first stage of a {SCHEME} step of the N={N_SITES} chain with fixed dimension {k_fixed} "
+              f"({k_fixed} H applies per process); {host_desc()}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": P, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+# ---------------------------------------------------------------- device measurements
+def make_chain(P, pr, N, precision, m_max=M_MAX, **kw):
+    return P.Propagator(P.XXZChain(N, pr.J, pr.Delta, pr.h), [P.XField(N, pr.xfield)], [pr.drive], m_max=m_max,
+                        max_substeps=64, precision=precision, **kw)
+
+
+def final_state_error(P, torch, pr, psi0, N, precision, T, order, dt, tol, ref_state=None):
+    """||psi - psi_ref||_2 after time T from psi0 for (order, dt, tol) against
+    the FP64-class reference CF8:11, dt = REF_DT, tol REF_TOL, m <= 24 (computed
+    once and passed back in ref_state)."""
+    if ref_state is None:
+        ref = torch.from_numpy(psi0).cuda()
+        rp = make_chain(P, pr, N, "fx", m_max=24)
+        rp.propagate(ref, 0.0, REF_DT, int(round(T / REF_DT)), order=8, tol=REF_TOL)
+        rp.close()
+        ref_state = ref
+    x = torch.from_numpy(psi0).cuda()
+    p = make_chain(P, pr, N, precision)
+    p.propagate(x, 0.0, dt, int(round(T / dt)), order=order, tol=tol)
+    p.close()
+    return torch.linalg.vector_norm(x - ref_state).item(), ref_state
+
+
+def timed_reps(prop, psi, t0, K, barrier, min_ms, reps=None):
+    """Propagations of exactly K steps, each between barriers and CUDA events
+    on the launching stream, repeated until at least min_ms have been timed
+    (or `reps` times): [(ms, kernel_ms, stats)], t0 after them."""
+    import torch
+    stream = torch.cuda.current_stream()
+    out = []
+    total = 0.0
+    while (reps is None and (total < min_ms or len(out) < 3)) or (reps is not None and len(out) < reps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        ev0.record(stream)
+        st = prop.propagate(psi, t0, DT, K, order=ORDER, tol=TOL)
+        ev1.record(stream)
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        out.append((ms, prop.kernel_time_ms(), st))
+        total += ms
+        t0 += K * DT
+    return out, t0
+
+
+def roofline_of(precision, reps, dim, hbm_peak, per_launch_div):
+    """Roofline object of the persistent kernel from the median rep."""
+    elem = 8.0 if precision == "c64" else 16.0
+    ach_gbs, ach_tf, bytes_l, kms_l = [], [], [], []
+    for ms, kms, st in reps:
+        b, f = algorithmic_counts(st, dim, elem_bytes=elem)
+        ach_gbs.append(b / (kms * 1e-3) / 1e9)
+        ach_tf.append(f / (kms * 1e-3) / 1e12)
+        bytes_l.append(b / per_launch_div)
+        kms_l.append(kms)
+    gbs, tf = statistics.median(ach_gbs), statistics.median(ach_tf)
+    n_app_med = statistics.median([st["n_applies"] for _, _, st in reps])
+    if precision in ("fx", "c64"):
+        per_it = DRAM_BYTES_PER_ITERATION[precision]
+        return {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "traffic": per_it * n_app_med / per_launch_div if per_it is not None else None,
+                "traffic_note": "per launch: ncu DRAM read+write bytes per Lanczos iteration (2-step capture) x "
+                                "the launch's iterations (median rep); algorithmic bytes per launch: %.4g"
+                                % statistics.median(bytes_l),
+                "kernel": "k_propagate_fx (persistent Lanczos, int64 fixed-point vectors)" if precision == "fx"
+                else "k_propagate_c64 (persistent Lanczos, complex64 vectors, FP64-class reductions)",
+                "kernel_ms": statistics.median(kms_l), "launches": per_launch_div,
+                "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), burst figure",
+                "fp64_equivalent_tflops": tf}
+    return {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": tf / FP64_PEAK_TFLOPS, "traffic": None,
+            "kernel": "k_propagate (persistent Lanczos, FP64)", "kernel_ms": statistics.median(kms_l),
+            "launches": per_launch_div, "hbm_algorithmic_gbs": gbs, "hbm_peak_gbs": hbm_peak,
+            "hbm_frac": gbs / hbm_peak,
+            "peak_note": "FP64 peak from unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
+
+
+def l2_roofline(P, torch, precision, roof):
+    """L2 view of the N = 20 kernel (its vector and most of its basis are
+    L2-resident): the L2-served copy rate measured here as the peak, the
+    kernel's ncu L2 traffic (lts bytes) and its algorithmic bytes per second."""
+    nb = L2_PROBE_BYTES
+    a = torch.empty(nb // 16, dtype=torch.complex128, device="cuda")
+    b = torch.empty_like(a)
+    a.zero_()
+    peak = max(P.probe_copy_gbs(a, b, reps=L2_PROBE_REPS) for _ in range(3))
+    del a, b
+    out = {"unit": "GB/s", "peak": peak,
+           "peak_note": f"cfet_probe_copy_gbs: {L2_PROBE_REPS} alternating copies between two "
+                        f"{nb >> 20} MiB buffers in one launch (read + write bytes), best of 3, measured in this run",
+           "achieved_algorithmic": roof["achieved"] if roof["unit"] == "GB/s" else roof["hbm_algorithmic_gbs"]}
+    out["frac_algorithmic"] = out["achieved_algorithmic"] / peak
+    per_it = LTS_BYTES_PER_ITERATION.get(precision)
+    if per_it is not None and roof.get("kernel_ms"):
+        n_it = roof["_n_app"]
+        out["traffic"] = per_it * n_it
+        out["achieved"] = per_it * n_it / (roof["kernel_ms"] * 1e-3) / 1e9
+        out["frac"] = out["achieved"] / peak
+        out["traffic_note"] = "ncu lts__t_bytes per Lanczos iteration (2-step capture) x the launch's iterations"
+    else:
+        out["traffic"] = out["achieved"] = out["frac"] = None
+    return out
+
+
+def small_chain_line(P, torch):
+    """The N = 8 chain (dim 256): Neel state, CF4:2, dt 0.01, T 10 (1000 steps),
+    tol 1e-12, m <= 16; CFET steps/s of one 1000-step propagation and its
+    final-state error against CF8:11 at dt 0.0025, tol 1e-14."""
+    cfg = W.CHAIN_SMALL
+    N = cfg["N"]
+    pr = W.spin_chain(N)
+    psi0 = W.neel_state(N)
+    n = int(round(cfg["T"] / cfg["dt"]))
+    prop = make_chain(P, pr, N, "fx", m_max=cfg["m_max"])
+    x = torch.from_numpy(psi0).cuda()
+    prop.propagate(x, 0.0, cfg["dt"], 10, order=cfg["order"], tol=cfg["tol"])   # warm-up
+    x = torch.from_numpy(psi0).cuda()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    st = prop.propagate(x, 0.0, cfg["dt"], n, order=cfg["order"], tol=cfg["tol"])
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    kms = prop.kernel_time_ms()
+    prop.close()
+    ref = torch.from_numpy(psi0).cuda()
+    rp = make_chain(P, pr, N, "fx", m_max=24)
+    rp.propagate(ref, 0.0, 0.0025, int(round(cfg["T"] / 0.0025)), order=8, tol=1e-14)
+    rp.close()
+    return {"workload": f"driven XXZ chain N={N} (dim {1 << N}), Neel state, CF4:2 dt={cfg['dt']}, T={cfg['T']}, "
+                        f"tol {cfg['tol']}, m_max {cfg['m_max']}", "precision": "fx",
+            "cfet_steps_per_s": n / (ms * 1e-3), "H_applies_per_s": st["n_applies"] / (ms * 1e-3),
+            "us_per_apply": 1e3 * kms / st["n_applies"], "ms": ms, "kernel_ms": kms, "H_applies": st["n_applies"],
+            "final_state_error": torch.linalg.vector_norm(x - ref).item(),
+            "reference": "CF8:11, dt 0.0025, tol 1e-14, m_max 24 (fixed point)"}
 
 
 def run_gpu(args):
@@ -241,16 +451,19 @@ def run_gpu(args):
         torch.cuda.set_device(0)
     import paper_1102_5071_gb300 as P
     P.build()
+    # the host-core oracle runs first, before this process touches the GPU
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample()
     pr, psi0 = problem()
     dim = 1 << N_SITES
     cheb = args.expm == "chebyshev"
-    prop = P.Propagator(P.XXZChain(N_SITES, pr.J, pr.Delta, pr.h), [P.XField(N_SITES, pr.xfield)], [pr.drive],
-                        m_max=M_MAX, max_substeps=64, precision=args.precision, block_size=args.block_size,
-                        grid_size=args.grid_size, expm=args.expm)
+    prop = make_chain(P, pr, N_SITES, args.precision, block_size=args.block_size, grid_size=args.grid_size,
+                      expm=args.expm)
     psi = torch.from_numpy(psi0).cuda()
     t0 = 0.0
     # warm-up steps (untimed)
-    st = prop.propagate(psi, t0, DT, args.warmup, order=ORDER, tol=TOL)
+    prop.propagate(psi, t0, DT, args.warmup, order=ORDER, tol=TOL)
     t0 += args.warmup * DT
 
     def barrier():
@@ -259,36 +472,43 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    stream = torch.cuda.current_stream()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # the number of timed repetitions of the K-step call: enough for
+    # args.min_timed_ms on the slowest rank, the same on every rank
+    cal, t0 = timed_reps(prop, psi, t0, args.steps, barrier, 0.0, reps=1)
+    cal_ms, _ = aggregate_over_ranks(cal[0][0], 0.0)
+    nrep = max(3, int(math.ceil(args.min_timed_ms / max(cal_ms, 1e-3))))
     with ClockSampler(local) as clk:
-        barrier()
-        ev0.record(stream)
-        stats = prop.propagate(psi, t0, DT, args.steps, order=ORDER, tol=TOL)
-        ev1.record(stream)
-        barrier()
-    t0 += args.steps * DT
-    ms = ev0.elapsed_time(ev1)
-    kernel_ms = prop.kernel_time_ms()
+        reps, t0 = timed_reps(prop, psi, t0, args.steps, barrier, 0.0, reps=nrep)
     clocks = clk.summary()
-    n_app = stats["n_applies"]
-    ms_max, app_total = aggregate_over_ranks(ms, n_app)
-    value = app_total / (ms_max * 1e-3)
+    per_rep = [aggregate_over_ranks(ms, st["n_applies"]) for ms, _, st in reps]
+    values = [u / (m * 1e-3) for m, u in per_rep]
+    value = statistics.median(values)
+    ms_med = statistics.median([m for m, _ in per_rep])
+    launches = math.ceil(args.steps / 256)
 
-    # roofline of the persistent kernel (one launch per 256 steps)
-    bytes_, flops = algorithmic_counts(stats, dim, elem_bytes=8.0 if args.precision == "c64" else 16.0)
-    if cheb:
-        # per element and term: read v_k, v_{k-1}, the sum; write v_{k+1}, the sum (80 B); the first
-        # term of an exponential reads v_0 and writes v_1 and the sum (48 B), the last writes v_0 only (64 B)
-        bytes_ = dim * (80.0 * n_app - 48.0 * stats["n_exp"])
-    achieved_tflops = flops / (kernel_ms * 1e-3) / 1e12
-    achieved_gbs = bytes_ / (kernel_ms * 1e-3) / 1e9
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    if cheb:
+        kms = statistics.median([k for _, k, _ in reps])
+        n_app = statistics.median([st["n_applies"] for _, _, st in reps])
+        n_exp = reps[0][2]["n_exp"]
+        # per element and term: read v_k, v_{k-1}, the sum; write v_{k+1}, the sum (80 B); the first
+        # term of an exponential reads v_0 and writes v_1 and the sum (48 B), the last writes v_0 only (64 B)
+        bytes_ = dim * (80.0 * n_app - 48.0 * n_exp)
+        gbs = bytes_ / (kms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                    "traffic": DRAM_BYTES_PER_TERM_CHEB * n_app / launches,
+                    "traffic_note": "per launch: ncu DRAM read+write bytes per Chebyshev term (2-step capture) x "
+                                    "the launch's terms; algorithmic bytes per launch: %.4g" % (bytes_ / launches),
+                    "kernel": "k_cheb_fx (persistent Chebyshev recurrence, int64 fixed-point vectors)",
+                    "kernel_ms": kms, "launches": launches,
+                    "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), burst figure"}
+    else:
+        roofline = roofline_of(args.precision, reps, dim, hbm_peak, launches)
 
     # end-to-end through the host-buffer entry point: each step uploads psi
     # from pinned host memory, runs one CFET step, downloads psi
@@ -311,71 +531,68 @@ def run_gpu(args):
     if ws > 1 and e2e_steps:
         s_max, app_all = aggregate_over_ranks(e2e_s, e2e_app)
         e2e_val = app_all / s_max
+    prop.close()
 
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_sample()
-
-    if cheb:
-        per_t = DRAM_BYTES_PER_TERM_CHEB
-        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": achieved_gbs / hbm_peak,
-                    "traffic": per_t * n_app / math.ceil(args.steps / 256) if per_t is not None else None,
-                    "traffic_note": "per launch: ncu DRAM read+write bytes per Chebyshev term (2-step capture) x "
-                                    "the launch's terms; algorithmic bytes per launch: %.4g"
-                                    % (bytes_ / math.ceil(args.steps / 256)),
-                    "kernel": "k_cheb_fx (persistent Chebyshev recurrence, int64 fixed-point vectors)",
-                    "kernel_ms": kernel_ms, "launches": math.ceil(args.steps / 256),
-                    "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), burst figure"}
-    elif args.precision in ("fx", "c64"):
-        per_it = DRAM_BYTES_PER_ITERATION[args.precision]
-        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": achieved_gbs / hbm_peak,
-                    "traffic": per_it * n_app / math.ceil(args.steps / 256) if per_it is not None else None,
-                    "traffic_note": "per launch: ncu DRAM read+write bytes per Lanczos iteration (2-step "
-                                    "capture) x the launch's iterations; algorithmic bytes per launch: %.4g"
-                                    % (bytes_ / math.ceil(args.steps / 256)),
-                    "kernel": "k_propagate_fx (persistent Lanczos, int64 fixed-point vectors)"
-                    if args.precision == "fx" else
-                    "k_propagate_c64 (persistent Lanczos, complex64 vectors, FP64-class reductions)",
-                    "kernel_ms": kernel_ms, "launches": math.ceil(args.steps / 256),
-                    "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), burst figure",
-                    "fp64_equivalent_tflops": achieved_tflops}
-    else:
-        roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                    "kernel": "k_propagate (persistent Lanczos, FP64)", "kernel_ms": kernel_ms,
-                    "launches": math.ceil(args.steps / 256),
-                    "hbm_algorithmic_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak,
-                    "hbm_frac": achieved_gbs / hbm_peak,
-                    "peak_note": "FP64 peak from unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
     if rank == 0:
+        st_all = [st for _, _, st in reps]
+        med = sorted(range(len(reps)), key=lambda i: values[i])[len(reps) // 2]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": ms_med / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fx": "i64", "c64": "f32", "f64": "f64"}[args.precision],
             "data": "synthetic", "config": dict(workload_config(), precision=args.precision, expm=args.expm),
-            "cfet_steps_per_s": args.steps * ws / (ms_max * 1e-3),
-            "krylov": {"applies_per_step": n_app / args.steps, "substeps": stats["n_substeps"],
-                       "max_k": stats["max_k"], "max_err_est": stats["max_err_est"],
-                       # SM clock cycles per CTA (mean, max over CTAs), in millions
-                       "phase_Mcycles": {k: v * 1e-6 for k, v in zip(PHASES, stats.get("phase_ns", [0] * 8))},
+            "timed_repeats": len(reps),
+            "timing_note": f"the {args.steps}-step call timed {len(reps)} times back to back (CUDA events, "
+                           f"barrier and synchronize around each); value and ms_per_step are the medians",
+            "cfet_steps_per_s": args.steps * ws / (ms_med * 1e-3),
+            "krylov": {"applies_per_step": statistics.median([s["n_applies"] for s in st_all]) / args.steps,
+                       "substeps": st_all[med]["n_substeps"], "max_k": max(s["max_k"] for s in st_all),
+                       "max_err_est": max(s["max_err_est"] for s in st_all),
+                       # SM clock cycles per CTA of the median rep (mean, max over CTAs), in millions
+                       "phase_Mcycles": {k: v * 1e-6 for k, v in zip(PHASES, st_all[med].get("phase_ns", [0] * 8))},
                        "phase_max_Mcycles": {k: v * 1e-6 for k, v in zip(PHASES,
-                                                                           stats.get("phase_max_ns", [0] * 8))}},
+                                                                           st_all[med].get("phase_max_ns", [0] * 8))}},
             "roofline": roofline,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 16 * dim, "d2h_bytes_per_step": 16 * dim,
                     "steps": e2e_steps},
-            "gpu_launches": math.ceil(args.steps / 256),
+            "gpu_launches": launches,
             "clocks": clocks,
         }
+        if not args.quick:
+            # accuracy of the benchmarked setting, outside the timed region
+            err, ref_state = final_state_error(P, torch, pr, psi0, N_SITES, args.precision, ERR_T, ORDER, DT, TOL)
+            line["final_state_error"] = {
+                "value": err, "T": ERR_T, "steps": int(round(ERR_T / DT)),
+                "reference": f"CF8:11, dt {REF_DT}, tol {REF_TOL}, m_max 24 (fixed point), same psi0",
+                "note": "||psi - psi_ref||_2 of the benchmarked scheme, dt, tolerance and precision from t = 0"}
+            if not cheb and args.precision != "f64":
+                # the complex128 (FP64) form of the same workload, as a secondary arm
+                fp = make_chain(P, pr, N_SITES, "f64")
+                x = torch.from_numpy(psi0).cuda()
+                fp.propagate(x, 0.0, DT, args.warmup, order=ORDER, tol=TOL)
+                r64, _ = timed_reps(fp, x, args.warmup * DT, args.steps, torch.cuda.synchronize,
+                                    args.min_timed_ms / 4)
+                roof64 = roofline_of("f64", r64, dim, hbm_peak, launches)
+                fp.close()
+                e64, _ = final_state_error(P, torch, pr, psi0, N_SITES, "f64", ERR_T, ORDER, DT, TOL, ref_state)
+                line["f64_arm"] = {
+                    "value": statistics.median([st["n_applies"] / (ms * 1e-3) for ms, _, st in r64]),
+                    "unit": UNIT, "cfet_steps_per_s": args.steps / (statistics.median([m for m, _, _ in r64]) * 1e-3),
+                    "ms_per_step": statistics.median([m for m, _, _ in r64]) / args.steps, "timed_repeats": len(r64),
+                    "dtype": "f64", "roofline": roof64, "final_state_error": e64}
+            roof = dict(roofline, _n_app=statistics.median([s["n_applies"] for s in st_all]) / launches)
+            if not cheb:
+                line["l2_roofline"] = l2_roofline(P, torch, args.precision, roof)
+            line["small_chain"] = small_chain_line(P, torch)
+            del ref_state
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
+        dist.barrier()
         dist.destroy_process_group()
-    prop.close()
     return 0
 
 
@@ -393,6 +610,10 @@ def main():
                     help="stage exponentials: Krylov (default) or the Chebyshev expansion (fixed point only)")
     ap.add_argument("--grid-size", type=int, default=0,
                     help="CTAs of the persistent kernel (0 = co-resident maximum)")
+    ap.add_argument("--min-timed-ms", type=float, default=2000.0,
+                    help="the K-step call is repeated until at least this much has been timed (median reported)")
+    ap.add_argument("--quick", action="store_true",
+                    help="headline figures only (no final-state error, FP64 arm, L2 probe or N=8 line)")
     ap.add_argument("--block-size", type=int, default=0,
                     help="threads per CTA of the FP64 kernel; the fixed-point kernel uses 2x this many workers + 1 control warp")
     args = ap.parse_args()

@@ -557,6 +557,18 @@ cfet_status cfet_fidelity_grad(cfet_ctx* ctx, const void* psi0, const void* phi,
  * CFET_ETIMEOUT, CFET_ECUDA otherwise.  Synchronises the device.            */
 cfet_status cfet_selftest_wait_timeout(int32_t which, double timeout_s, int32_t* device_status);
 
+/* Copy-bandwidth probe (no counterpart in the paper; the measured
+ * denominator of the L2 roofline): one launch of `reps` grid-stride copies of
+ * `bytes` bytes, alternating a -> b and b -> a, timed with CUDA events on
+ * `stream`; *gbs = 2 bytes reps / time in GB/s (read + write).  a, b: two
+ * distinct caller-owned device buffers of at least `bytes` bytes, 16-byte
+ * aligned; their contents are overwritten.  Buffers that fit in L2 together
+ * give the L2-served copy rate, larger ones the DRAM rate.  Synchronises
+ * `stream`.  Errors: CFET_EINVAL (NULL or equal pointers, misalignment,
+ * bytes not a positive multiple of 16, reps outside [1, 100000]),
+ * CFET_ENODEV, CFET_ECUDA.                                                  */
+cfet_status cfet_probe_copy_gbs(void* a, void* b, int64_t bytes, int32_t reps, void* stream, double* gbs);
+
 /* Host-only check (no device needed) of the index arithmetic of the
  * window-tiled apply of long chains (CFET_PREC_FX uses tile_bits 11,
  * CFET_PREC_C64 12): for an nsites chain, every basis index appears in

@@ -155,6 +155,25 @@ def _stream_handle(stream):
     return C.c_void_p(stream.cuda_stream)
 
 
+def probe_copy_gbs(a, b, reps=100, stream=None):
+    """Copy rate in GB/s (read + write) of `reps` alternating copies between
+    the CUDA tensors a and b (same number of bytes, overwritten) inside one
+    launch: the L2-served rate when both fit in L2, the DRAM rate otherwise."""
+    import torch
+    if not (isinstance(a, torch.Tensor) and isinstance(b, torch.Tensor) and a.is_cuda and b.is_cuda):
+        raise TypeError("a and b must be CUDA tensors")
+    nbytes = a.numel() * a.element_size()
+    if b.numel() * b.element_size() != nbytes or not (a.is_contiguous() and b.is_contiguous()):
+        raise ValueError("a and b must be contiguous with the same number of bytes")
+    lib = _capi.load()
+    out = C.c_double(0.0)
+    st = lib.cfet_probe_copy_gbs(C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()), nbytes, int(reps),
+                                 _stream_handle(stream), C.byref(out))
+    if st != 0:
+        raise CfetError(st, lib.cfet_last_error(None).decode())
+    return out.value
+
+
 def _check_vec(t, dim, name):
     import torch
     if not isinstance(t, torch.Tensor) or t.dtype != torch.complex128 or not t.is_cuda:

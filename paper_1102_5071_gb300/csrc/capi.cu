@@ -1374,6 +1374,36 @@ cfet_status cfet_selftest_wait_timeout(int32_t which, double timeout_s, int32_t*
   return h == CFET_ETIMEOUT ? CFET_OK : fail(nullptr, CFET_ECUDA, "wait self test: the wait did not time out");
 }
 
+cfet_status cfet_probe_copy_gbs(void* a, void* b, int64_t bytes, int32_t reps, void* stream, double* gbs) {
+  if (!gbs) return fail(nullptr, CFET_EINVAL, "copy probe: gbs is NULL");
+  *gbs = 0.0;
+  if (!a || !b || a == b || bytes < 16 || (bytes % 16) != 0 || reps < 1 || reps > 100000 ||
+      (reinterpret_cast<uintptr_t>(a) % 16) != 0 || (reinterpret_cast<uintptr_t>(b) % 16) != 0)
+    return fail(nullptr, CFET_EINVAL, "copy probe: two distinct 16-byte aligned buffers, bytes a positive "
+                                      "multiple of 16, reps in [1, 100000]");
+  cfet_status s = device_available(nullptr);
+  if (s != CFET_OK) return s;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = (cudaError_t)launch_copy_probe(a, b, bytes / 16, 1, 4 * nsm, cs);  // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(e0, cs);
+  if (e == cudaSuccess) e = (cudaError_t)launch_copy_probe(a, b, bytes / 16, reps, 4 * nsm, cs);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, cs);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "copy probe");
+  *gbs = ms > 0.0f ? 2.0 * (double)bytes * reps / (ms * 1e-3) / 1e9 : 0.0;
+  return CFET_OK;
+}
+
 cfet_status cfet_fidelity_grad(cfet_ctx* ctx, const void* psi0, const void* phi, double t0, double dt,
                                int64_t nsteps, int32_t order, double krylov_tol, int32_t nseg, const double* amps,
                                double omega, double phase, int64_t checkpoint_every, void* stream, double* loss,

@@ -260,6 +260,7 @@ int launch_adjoint_spin(const AdjParams& p, const OpSpin& op, int grid, int bloc
 int launch_wait_selftest(int which, unsigned long long* rec, unsigned* bar, int* status, long long timeout_ns);
 constexpr int kDiffBlocks = 152;  // blocks (partials) of the difference norm
 int launch_diff_norm2(const double2* a, const double2* b, int n, double* part, int nblk, void* stream);
+int launch_copy_probe(void* a, void* b, long long n16, int reps, int grid, void* stream);
 int max_coresident_blocks_adjoint(int block);
 int max_coresident_blocks(int family, int block);  // per device, for the persistent kernel
 size_t propagate_smem_bytes(int block);

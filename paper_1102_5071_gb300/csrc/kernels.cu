@@ -776,4 +776,32 @@ int launch_diff_norm2(const double2* a, const double2* b, int n, double* part, i
   return (int)cudaGetLastError();
 }
 
+// Copy-bandwidth probe: `reps` grid-stride copies of n 16-byte units inside
+// one launch, alternating a -> b and b -> a (each copy reads what the
+// previous one wrote, so none can be elided), four units in flight per
+// thread.  With a and b together smaller than L2 this measures the L2-served
+// copy rate; larger buffers give the DRAM copy rate.
+__global__ void __launch_bounds__(512) k_copy_probe(int4* a, int4* b, long long n, int reps) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int r = 0; r < reps; ++r) {
+    const int4* src = (r & 1) ? b : a;
+    int4* dst = (r & 1) ? a : b;
+    long long i = t;
+    for (; i + 3 * stride < n; i += 4 * stride) {
+      const int4 v0 = src[i], v1 = src[i + stride], v2 = src[i + 2 * stride], v3 = src[i + 3 * stride];
+      dst[i] = v0;
+      dst[i + stride] = v1;
+      dst[i + 2 * stride] = v2;
+      dst[i + 3 * stride] = v3;
+    }
+    for (; i < n; i += stride) dst[i] = src[i];
+  }
+}
+
+int launch_copy_probe(void* a, void* b, long long n16, int reps, int grid, void* stream) {
+  k_copy_probe<<<grid, 512, 0, (cudaStream_t)stream>>>(static_cast<int4*>(a), static_cast<int4*>(b), n16, reps);
+  return (int)cudaGetLastError();
+}
+
 }  // namespace cfet

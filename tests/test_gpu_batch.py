@@ -208,10 +208,23 @@ def test_full_batch_workload_sampled_against_oracle(torch_cuda):
     picked = {}
     for i, c in enumerate(insts):
         picked.setdefault(c.N, i)
+    refs, flips = {}, 0
+    forced = [list(lg) for lg in logs]
     for N, i in sorted(picked.items()):
         c = insts[i]
         r, lg, _ = _oracle(c, host[i], 0.0, cfg["dt"], 2, cfg["order"], cfg["tol"], cfg["m_max"])
+        refs[i] = r
+        flips += sum(a != b for a, b in zip(lg, logs[i]))
         if lg == logs[i]:
             assert np.linalg.norm(dev[i].cpu().numpy() - r) <= PARITY, (N, i)
-        else:   # a rounding-level decision flip: the result stays within the Krylov tolerance
-            assert np.linalg.norm(dev[i].cpu().numpy() - r) <= 10 * cfg["tol"], (N, i)
+        forced[i] = lg
+    # at most one rounding-level decision flip among the sampled stage exponentials
+    assert flips <= 1, flips
+    if flips:
+        # replay the oracle's decisions where they differ: then every sampled
+        # instance must match at the parity bound
+        _, dev2 = _states(torch, insts)
+        stats2 = bp.propagate(dev2, 0.0, cfg["dt"], 2, order=cfg["order"], tol=cfg["tol"], forced=forced)
+        assert all(s["status"] == 0 for s in stats2)
+        for i, r in refs.items():
+            assert np.linalg.norm(dev2[i].cpu().numpy() - r) <= PARITY, i

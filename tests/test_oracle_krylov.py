@@ -171,3 +171,68 @@ def test_expv_tolerance_is_absolute_for_unnormalised_states(tau):
     psi = 1000.0 * W.random_state(12, 200)
     out, log, _ = K.expv(lambda v: H @ v, psi, tau, tol=1e-9, m_max=40)
     assert np.linalg.norm(out - expm(-1j * tau * H) @ psi) <= 1e-9
+
+
+# ---------------------------------------------------------------- Gershgorin width
+# The width gates when the estimate of Eq. (KryErr) is trusted (|tau| width
+# <= 2k); it must never be smaller than the true eigenvalue spread of T_k.
+# Pins: the dense eigenvalue spread (numpy eigvalsh) of random tridiagonals
+# with either sign of beta, and closed forms where Gershgorin is exact.
+
+def _width_bounds_spread(width_fn):
+    cases = []
+    for seed in range(40):
+        k = 1 + seed % 12
+        alpha = W.uniform(300 + seed, k, -3, 3)
+        beta = W.uniform(400 + seed, max(k - 1, 1), -2, 2)[:k - 1]
+        cases.append((alpha, beta))
+    cases.append((np.zeros(3), np.ones(2)))                  # spread 2 sqrt(2)
+    cases.append((np.array([5.0, -1.0, 2.0, 0.5]), np.array([0.0, 3.0, 0.0])))
+    for alpha, beta in cases:
+        lam = np.linalg.eigvalsh(K.tridiag_matrix(alpha, beta))
+        if width_fn(list(alpha), list(beta)) < (lam[-1] - lam[0]) * (1 - 1e-14) - 1e-14:
+            return False
+    return True
+
+
+def test_gershgorin_width_bounds_the_eigenvalue_spread():
+    assert _width_bounds_spread(K.gershgorin_width)
+
+
+def test_gershgorin_width_closed_forms():
+    # one row: zero width; diagonal T: the exact spread of its entries;
+    # [[a, b], [b, a]]: eigenvalues a -+ b, width 2|b| exactly; the k x k
+    # tridiagonal with zero diagonal and unit off-diagonal: rows 2..k-1 reach
+    # +-2, so the width is 4 (its spread is 4 cos(pi / (k + 1)) < 4)
+    assert K.gershgorin_width([1.7], []) == 0.0
+    assert K.gershgorin_width([3.0, -2.0, 0.5], [0.0, 0.0]) == 5.0
+    assert K.gershgorin_width([0.3, 0.3], [-1.25]) == 2.5
+    for k in (3, 7, 16):
+        assert K.gershgorin_width([0.0] * k, [1.0] * (k - 1)) == 4.0
+        lam = np.linalg.eigvalsh(K.tridiag_matrix(np.zeros(k), np.ones(k - 1)))
+        assert abs((lam[-1] - lam[0]) - 4 * math.cos(math.pi / (k + 1))) < 1e-13
+
+
+def test_planted_missing_neighbour_in_gershgorin_width_is_caught(monkeypatch):
+    # a radius that counts only the next row's coupling underestimates the
+    # spread (3 x 3 example: width 2 against 2 sqrt(2)); so does a width
+    # taken from the signed couplings
+    def one_sided(alpha, beta):
+        k = len(alpha)
+        lo, hi = np.inf, -np.inf
+        for r in range(k):
+            rad = abs(beta[r]) if r < k - 1 else 0.0
+            lo, hi = min(lo, alpha[r] - rad), max(hi, alpha[r] + rad)
+        return hi - lo
+
+    def signed(alpha, beta):
+        k = len(alpha)
+        lo, hi = np.inf, -np.inf
+        for r in range(k):
+            rad = (beta[r - 1] if r > 0 else 0.0) + (beta[r] if r < k - 1 else 0.0)
+            lo, hi = min(lo, alpha[r] - rad), max(hi, alpha[r] + rad)
+        return hi - lo
+
+    for bad in (one_sided, signed):
+        monkeypatch.setattr(K, "gershgorin_width", bad)
+        assert not _width_bounds_spread(K.gershgorin_width)
