@@ -94,7 +94,23 @@ enum {
    * are expanded into Pauli strings), the total number of strings is at most
    * 4096, and the context computes in CFET_PREC_F64 (CFET_PREC_DEFAULT
    * selects it; CFET_PREC_FX and CFET_PREC_C64 give CFET_EINVAL).           */
-  CFET_OP_PAULI = 4
+  CFET_OP_PAULI = 4,
+  /* general sparse Hermitian operator in compressed sparse row form (Sec. 8:
+   * the stage operator is a weighted sum of the operators, applied term by
+   * term with the stage scalars, so it keeps their sparsity and is never
+   * formed):
+   *   (A v)[r] = sum_{e = row_ptr[r]}^{row_ptr[r+1]-1}
+   *              (csr_re[e] + i csr_im[e]) * v[col_idx[e]]
+   * uses dim, row_ptr[dim + 1] (host, int64, row_ptr[0] = 0, non-decreasing),
+   * col_idx[nnz] (host, int32, each in [0, dim); duplicates within a row are
+   * summed), csr_re[nnz] and csr_im[nnz] (host, copied; csr_im = NULL for a
+   * real symmetric operator), nnz = row_ptr[dim].  The operator must be
+   * Hermitian: every entry's mirror holds the conjugate value to 1e-13 of
+   * the largest entry (checked at create, else CFET_EINVAL).  When H0 is CSR,
+   * every V_k must be CSR of the same dim; at most 2^31 - 2 stored entries
+   * over all operators.  Every precision and both stage-exponential methods
+   * apply.                                                                  */
+  CFET_OP_CSR = 5
 };
 
 typedef struct cfet_op {
@@ -110,6 +126,10 @@ typedef struct cfet_op {
   const uint64_t* xmask;      /* PAULI: X part of string t (host)             */
   const uint64_t* zmask;      /* PAULI: Z part of string t (host)             */
   const double* coeff;        /* PAULI: real coefficient of string t (host)   */
+  const int64_t* row_ptr;     /* CSR: row_ptr[dim + 1] (host)                 */
+  const int32_t* col_idx;     /* CSR: col_idx[row_ptr[dim]] (host)            */
+  const double* csr_re;       /* CSR: real parts of the entries (host)        */
+  const double* csr_im;       /* CSR: imaginary parts (host) or NULL (real)   */
 } cfet_op;
 
 /* Drive f_k(t), called on the host only at the Gauss-Legendre nodes

@@ -15,8 +15,8 @@ schemes    coefficient tables f_{i,n} (Tables 1-5), the symmetric expansion
            Gauss-Legendre points/weights (Table 6) and g_{i,m} (Eq. OmGLeg).
 operators  H v for the driven XXZ chain (Pauli-string definitions, Eq. 53-54
            style spin operators), the transverse field, general real sums of
-           Pauli strings applied site by site, banded (DIA) and dense
-           operators.
+           Pauli strings applied site by site, banded (DIA), compressed
+           sparse row (CSR) and dense operators.
 krylov     Lanczos / Krylov evaluation of exp(-i tau H) psi (Sec. 7.1) with
            the a-posteriori error estimate and time substepping.
 cfet       the CFET time step (Eq. Ucf with Eq. OmGLeg) and time stepping

@@ -100,6 +100,24 @@ def gershgorin_dia(offsets, values):
     return float(np.min(diag - R)), float(np.max(diag + R))
 
 
+def gershgorin_csr(row_ptr, col_idx, values):
+    """CSR operator: diagonal = real part of the sum of the entries with
+    column = row, R_r = sum of |value| of the row's other entries."""
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    col_idx = np.asarray(col_idx, dtype=np.int64)
+    values = np.asarray(values)
+    dim = len(row_ptr) - 1
+    diag = np.zeros(dim)
+    R = np.zeros(dim)
+    for r in range(dim):
+        for e in range(row_ptr[r], row_ptr[r + 1]):
+            if col_idx[e] == r:
+                diag[r] += float(np.real(values[e]))
+            else:
+                R[r] += abs(values[e])
+    return float(np.min(diag - R)), float(np.max(diag + R))
+
+
 def operator_intervals(op):
     """Gershgorin interval of H0 and of every V_k of an operator family."""
     if isinstance(op, O.SpinChain):
@@ -110,6 +128,8 @@ def operator_intervals(op):
         return [gershgorin_dia(*op.H0)] + [gershgorin_dia(o, v) for o, v in op.Vs]
     if isinstance(op, O.Dense):
         return [gershgorin_dense(op.H0)] + [gershgorin_dense(V) for V in op.Vs]
+    if isinstance(op, O.Sparse):
+        return [gershgorin_csr(*op.H0)] + [gershgorin_csr(*a) for a in op.Vs]
     raise TypeError("unknown operator family")
 
 

@@ -83,6 +83,18 @@ def dia_apply(v, offsets, values):
     return out
 
 
+def csr_apply(v, row_ptr, col_idx, values):
+    """Compressed sparse rows: (A v)[r] = sum over the stored entries e of row
+    r (e in [row_ptr[r], row_ptr[r+1])) of values[e] * v[col_idx[e]];
+    duplicate entries of a row simply add."""
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    dim = len(row_ptr) - 1
+    rows = np.repeat(np.arange(dim), np.diff(row_ptr))
+    out = np.zeros(dim, dtype=np.complex128)
+    np.add.at(out, rows, np.asarray(values) * v[np.asarray(col_idx, dtype=np.int64)])
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Operator families.  An operator family bundles H0 and the drive operators
 # V_1..V_K; apply(coeffs, v) returns (c_0 H0 + sum_k c_k V_k) v, the stage
@@ -175,6 +187,29 @@ class Banded:
         out = coeffs[0] * dia_apply(v, *self.H0)
         for k, (o, val) in enumerate(self.Vs):
             out = out + coeffs[1 + k] * dia_apply(v, o, val)
+        return out
+
+
+class Sparse:
+    """H(t) = H0 + sum_k f_k(t) V_k with every operator in CSR form, each given
+    as (row_ptr [dim + 1], col_idx [nnz], values [nnz], real or complex)."""
+
+    def __init__(self, H0, Vs):
+        def conv(a):
+            rp, ci, val = a
+            return (np.asarray(rp, dtype=np.int64), np.asarray(ci, dtype=np.int64), np.asarray(val))
+        self.H0 = conv(H0)
+        self.Vs = [conv(a) for a in Vs]
+        self.dim = len(self.H0[0]) - 1
+
+    @property
+    def nV(self):
+        return len(self.Vs)
+
+    def apply(self, coeffs, v):
+        out = coeffs[0] * csr_apply(v, *self.H0)
+        for k, a in enumerate(self.Vs):
+            out = out + coeffs[1 + k] * csr_apply(v, *a)
         return out
 
 

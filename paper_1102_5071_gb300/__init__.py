@@ -82,6 +82,26 @@ class DIA:
     values: np.ndarray
 
 
+class CSR:
+    """Hermitian sparse operator in compressed sparse row form:
+    (A v)[r] = sum_{e in [row_ptr[r], row_ptr[r+1])} values[e] v[col_idx[e]];
+    values real (a real symmetric operator) or complex.  from_scipy() takes
+    any scipy.sparse matrix."""
+
+    def __init__(self, row_ptr, col_idx, values):
+        self.row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        self.col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+        v = np.asarray(values)
+        self.re = np.ascontiguousarray(v.real, dtype=np.float64)
+        self.im = np.ascontiguousarray(v.imag, dtype=np.float64) if np.iscomplexobj(v) else None
+        self.dim = len(self.row_ptr) - 1
+
+    @classmethod
+    def from_scipy(cls, m):
+        m = m.tocsr()
+        return cls(m.indptr, m.indices, m.data)
+
+
 def _op_struct(op, keep):
     s = _capi.cfet_op()
     if isinstance(op, XXZChain):
@@ -109,6 +129,13 @@ def _op_struct(op, keep):
         s.xmask = xm.ctypes.data_as(_capi.c_uint64_p)
         s.zmask = zm.ctypes.data_as(_capi.c_uint64_p)
         s.coeff = c.ctypes.data_as(_capi.c_double_p)
+    elif isinstance(op, CSR):
+        keep += [op.row_ptr, op.col_idx, op.re] + ([op.im] if op.im is not None else [])
+        s.kind, s.dim = _capi.CFET_OP_CSR, op.dim
+        s.row_ptr = op.row_ptr.ctypes.data_as(_capi.c_int64_p)
+        s.col_idx = op.col_idx.ctypes.data_as(_capi.c_int32_p)
+        s.csr_re = op.re.ctypes.data_as(_capi.c_double_p)
+        s.csr_im = op.im.ctypes.data_as(_capi.c_double_p) if op.im is not None else None
     else:
         raise TypeError(f"unsupported operator {type(op).__name__}")
     return s
@@ -185,7 +212,7 @@ def _check_vec(t, dim, name):
 class Propagator:
     """CFET propagator for H(t) = H0 + sum_k f_k(t) V_k on the current CUDA device.
 
-    H0, V: XXZChain / XField, DIA, or PauliSum operators (see include/cfet.h);
+    H0, V: XXZChain / XField, DIA, CSR or PauliSum operators (see include/cfet.h);
     drives: one callable f_k(t) per V_k.  precision: "default" (fixed point;
     FP64 when a PauliSum is involved), "fx", "f64" or "c64"; expm: "krylov" or
     "chebyshev" (fixed point); picture: "schroedinger" or "interaction" (FP64

@@ -14,7 +14,7 @@ c_int64_p = C.POINTER(C.c_int64)
 CFET_OK, CFET_EINVAL, CFET_ENOMEM, CFET_ECUDA, CFET_EKRYLOV, CFET_ETIMEOUT, CFET_ENAN, CFET_ENODEV = range(8)
 STATUS_NAMES = ["CFET_OK", "CFET_EINVAL", "CFET_ENOMEM", "CFET_ECUDA", "CFET_EKRYLOV", "CFET_ETIMEOUT",
                 "CFET_ENAN", "CFET_ENODEV"]
-CFET_OP_XXZ_CHAIN, CFET_OP_X_FIELD, CFET_OP_DIA, CFET_OP_PAULI = 1, 2, 3, 4
+CFET_OP_XXZ_CHAIN, CFET_OP_X_FIELD, CFET_OP_DIA, CFET_OP_PAULI, CFET_OP_CSR = 1, 2, 3, 4, 5
 c_uint64_p = C.POINTER(C.c_uint64)
 
 SCHEME_IDS = {"CF2:1": 1, "CF4:2": 2, "CF4:3": 3, "CF4:3Opt": 4, "CF6:4": 5, "CF6:5": 6, "CF6:5b": 7,
@@ -25,7 +25,8 @@ class cfet_op(C.Structure):
     _fields_ = [("kind", C.c_int32), ("nsites", C.c_int32), ("dim", C.c_int64), ("J", C.c_double),
                 ("Delta", C.c_double), ("site_coeff", c_double_p), ("ndiag", C.c_int32),
                 ("offsets", c_int64_p), ("values", c_double_p), ("nterms", C.c_int32),
-                ("xmask", c_uint64_p), ("zmask", c_uint64_p), ("coeff", c_double_p)]
+                ("xmask", c_uint64_p), ("zmask", c_uint64_p), ("coeff", c_double_p),
+                ("row_ptr", c_int64_p), ("col_idx", c_int32_p), ("csr_re", c_double_p), ("csr_im", c_double_p)]
 
 
 class cfet_options(C.Structure):

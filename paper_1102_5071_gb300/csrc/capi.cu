@@ -42,6 +42,10 @@ struct cfet_ctx {
   // operators
   OpSpin spin{};
   OpDia dia{};
+  OpCsr csr{};
+  OpCsrFx csr_fx{};
+  OpCsrC csr_c{};
+  void* d_csr = nullptr;       // one allocation: rp | col | vr | vi | VR | VI | vr32 | vi32
   // interaction picture: host copies of the chain (stage weight tables)
   double ip_J = 0.0, ip_Delta = 0.0;
   std::vector<double> ip_h, ip_xf;
@@ -181,6 +185,7 @@ void free_ctx(cfet_ctx* c) {
   cudaFree(c->d_adj_seg); cudaFree(c->d_adj_acc);
   cudaFree(c->d_ts); cudaFree(c->d_ts_part);
   cudaFree(c->d_pauli);
+  cudaFree(c->d_csr);
   if (c->h_st) cudaFreeHost(c->h_st);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   delete c;
@@ -240,19 +245,23 @@ cfet_status launch_chunk(cfet_ctx* ctx, const PropParams& base, long long e0, lo
     OpSpinIP op{ctx->spin.N, p.ip_nw, p.ip_w};
     e = launch_propagate_spin_ip(p, op, ctx->grid, ctx->block, s);
   } else if (ctx->opt.expm == CFET_EXPM_CHEBYSHEV)
-    e = ctx->family == kFamilySpin ? launch_cheb_spin_fx(p, ctx->spin_fx, ctx->grid, cheb_threads(ctx->block - 32), s)
-                                   : launch_cheb_dia_fx(p, ctx->dia_fx, ctx->grid, cheb_threads(ctx->block - 32), s);
+    e = ctx->family == kFamilySpin  ? launch_cheb_spin_fx(p, ctx->spin_fx, ctx->grid, cheb_threads(ctx->block - 32), s)
+        : ctx->family == kFamilyCsr ? launch_cheb_csr_fx(p, ctx->csr_fx, ctx->grid, cheb_threads(ctx->block - 32), s)
+                                    : launch_cheb_dia_fx(p, ctx->dia_fx, ctx->grid, cheb_threads(ctx->block - 32), s);
   else if (ctx->precision == CFET_PREC_FX)
-    e = ctx->family == kFamilySpin ? launch_propagate_spin_fx(p, ctx->spin_fx, ctx->grid, ctx->block, s)
-                                   : launch_propagate_dia_fx(p, ctx->dia_fx, ctx->grid, ctx->block, s);
+    e = ctx->family == kFamilySpin  ? launch_propagate_spin_fx(p, ctx->spin_fx, ctx->grid, ctx->block, s)
+        : ctx->family == kFamilyCsr ? launch_propagate_csr_fx(p, ctx->csr_fx, ctx->grid, ctx->block, s)
+                                    : launch_propagate_dia_fx(p, ctx->dia_fx, ctx->grid, ctx->block, s);
   else if (ctx->precision == CFET_PREC_C64)
-    e = ctx->family == kFamilySpin ? launch_propagate_spin_c64(p, ctx->spin_c, ctx->grid, ctx->block, s)
-                                   : launch_propagate_dia_c64(p, ctx->dia_c, ctx->grid, ctx->block, s);
+    e = ctx->family == kFamilySpin  ? launch_propagate_spin_c64(p, ctx->spin_c, ctx->grid, ctx->block, s)
+        : ctx->family == kFamilyCsr ? launch_propagate_csr_c64(p, ctx->csr_c, ctx->grid, ctx->block, s)
+                                    : launch_propagate_dia_c64(p, ctx->dia_c, ctx->grid, ctx->block, s);
   else if (ctx->family == kFamilyPauli)
     e = launch_propagate_pauli(p, ctx->pauli, ctx->grid, ctx->block, s);
   else
-    e = ctx->family == kFamilySpin ? launch_propagate_spin(p, ctx->spin, ctx->grid, ctx->block, s)
-                                   : launch_propagate_dia(p, ctx->dia, ctx->grid, ctx->block, s);
+    e = ctx->family == kFamilySpin  ? launch_propagate_spin(p, ctx->spin, ctx->grid, ctx->block, s)
+        : ctx->family == kFamilyCsr ? launch_propagate_csr(p, ctx->csr, ctx->grid, ctx->block, s)
+                                    : launch_propagate_dia(p, ctx->dia, ctx->grid, ctx->block, s);
   if (e != cudaSuccess) return cuda_fail(ctx, (cudaError_t)e, "persistent kernel launch");
   return CFET_OK;
 }
@@ -490,6 +499,154 @@ double pwc_eval(double t, void* user) {
   return d->amps[k] * std::cos(d->omega * t + d->phase);
 }
 
+// ---------------------------------------------------------------- CSR operators
+// Structure and Hermiticity of one CSR operator (NULL when acceptable).
+// Duplicate entries of a row are summed; every stored (r, c) must have its
+// mirror (c, r) with the conjugate value, to 1e-13 of the largest entry (an
+// entry without a mirror must be that small itself); the diagonal is real.
+const char* csr_check(const cfet_op& o, int dim) {
+  if (!o.row_ptr || !o.col_idx || (!o.csr_re && o.row_ptr[dim] > 0)) return "CSR: missing arrays";
+  if (o.row_ptr[0] != 0) return "CSR: row_ptr[0] must be 0";
+  for (int r = 0; r < dim; ++r)
+    if (o.row_ptr[r + 1] < o.row_ptr[r]) return "CSR: row_ptr must be non-decreasing";
+  const int64_t nnz = o.row_ptr[dim];
+  if (nnz >= 0x7fffffffLL) return "CSR: too many stored entries";
+  struct E {
+    int r, c;
+    double re, im;
+  };
+  std::vector<E> es;
+  es.reserve((size_t)nnz);
+  double amax = 0.0;
+  for (int r = 0; r < dim; ++r)
+    for (int64_t e = o.row_ptr[r]; e < o.row_ptr[r + 1]; ++e) {
+      const int c = o.col_idx[e];
+      if (c < 0 || c >= dim) return "CSR: column index out of range";
+      const double re = o.csr_re[e], im = o.csr_im ? o.csr_im[e] : 0.0;
+      if (!is_finite_d(re) || !is_finite_d(im)) return "CSR: value not finite";
+      es.push_back({r, c, re, im});
+      amax = std::fmax(amax, std::fabs(re) + std::fabs(im));
+    }
+  auto key_less = [](const E& a, const E& b) { return a.r != b.r ? a.r < b.r : a.c < b.c; };
+  std::sort(es.begin(), es.end(), key_less);
+  std::vector<E> m;  // duplicates summed
+  m.reserve(es.size());
+  for (const E& x : es) {
+    if (!m.empty() && m.back().r == x.r && m.back().c == x.c) {
+      m.back().re += x.re;
+      m.back().im += x.im;
+    } else {
+      m.push_back(x);
+    }
+  }
+  const double tol = 1e-13 * amax;
+  for (const E& x : m) {
+    E key{x.c, x.r, 0.0, 0.0};
+    auto it = std::lower_bound(m.begin(), m.end(), key, key_less);
+    double wr = 0.0, wi = 0.0;
+    if (it != m.end() && it->r == x.c && it->c == x.r) {
+      wr = it->re;
+      wi = it->im;
+    }
+    if (std::fabs(x.re - wr) > tol || std::fabs(x.im + wi) > tol) return "CSR: operator is not Hermitian";
+  }
+  return nullptr;
+}
+
+// Device copies of the CSR operators of a context: FP64 values, fixed-point
+// values with one exponent per operator (row sums of |re| + |im| below 2^62),
+// FP32 values; one allocation.
+cfet_status csr_upload(cfet_ctx* ctx, const cfet_op* H0, int nV, const cfet_op* V) {
+  const int dim = ctx->dim;
+  const int nops = 1 + nV;
+  bool cplx = false;
+  std::vector<int> rp((size_t)nops * (dim + 1));
+  size_t nnz = 0;
+  for (int k = -1; k < nV; ++k) {
+    const cfet_op& o = k < 0 ? *H0 : V[k];
+    const int64_t n = o.row_ptr[dim];
+    for (int r = 0; r <= dim; ++r) rp[(size_t)(k + 1) * (dim + 1) + r] = (int)(nnz + o.row_ptr[r]);
+    if (o.csr_im)
+      for (int64_t e = 0; e < n; ++e) cplx = cplx || o.csr_im[e] != 0.0;
+    nnz += (size_t)n;
+  }
+  const size_t n1 = nnz > 0 ? nnz : 1;
+  std::vector<int> col(n1, 0);
+  std::vector<double> vr(n1, 0.0), vi(cplx ? n1 : 0, 0.0);
+  std::vector<long long> VR(n1, 0), VI(cplx ? n1 : 0, 0);
+  std::vector<float> vr32(n1, 0.f), vi32(cplx ? n1 : 0, 0.f);
+  OpCsrFx& fx = ctx->csr_fx;
+  size_t at = 0;
+  for (int k = -1; k < nV; ++k) {
+    const cfet_op& o = k < 0 ? *H0 : V[k];
+    const int oi = k + 1;
+    double mrow = 0.0;
+    for (int r = 0; r < dim; ++r) {
+      double rs = 0.0;
+      for (int64_t e = o.row_ptr[r]; e < o.row_ptr[r + 1]; ++e)
+        rs += std::fabs(o.csr_re[e]) + (o.csr_im ? std::fabs(o.csr_im[e]) : 0.0);
+      mrow = std::fmax(mrow, rs);
+    }
+    mrow *= 1.0 + 1e-12;
+    int E_op = 0;
+    if (mrow > 0.0) {
+      int ex = 0;
+      std::frexp(mrow, &ex);  // mrow < 2^ex
+      E_op = ex - 62;
+    }
+    fx.E_op[oi] = E_op;
+    fx.maxrow[oi] = mrow;
+    const int64_t n = o.row_ptr[dim];
+    for (int64_t e = 0; e < n; ++e, ++at) {
+      col[at] = o.col_idx[e];
+      vr[at] = o.csr_re[e];
+      VR[at] = std::llrint(std::ldexp(o.csr_re[e], -E_op));
+      vr32[at] = (float)o.csr_re[e];
+      if (cplx) {
+        const double im = o.csr_im ? o.csr_im[e] : 0.0;
+        vi[at] = im;
+        VI[at] = std::llrint(std::ldexp(im, -E_op));
+        vi32[at] = (float)im;
+      }
+    }
+    csr_interval(o.row_ptr, o.col_idx, o.csr_re, o.csr_im, dim, &ctx->op_lo[oi], &ctx->op_hi[oi]);
+  }
+  // layout: rp | col | vr | vi | VR | VI | vr32 | vi32, 16-byte aligned pieces
+  auto al = [](size_t b) { return (b + 15) & ~size_t(15); };
+  const size_t nv = cplx ? n1 : 0;
+  const size_t o_rp = 0, o_col = o_rp + al(rp.size() * sizeof(int)), o_vr = o_col + al(n1 * sizeof(int));
+  const size_t o_vi = o_vr + al(n1 * sizeof(double)), o_VR = o_vi + al(nv * sizeof(double));
+  const size_t o_VI = o_VR + al(n1 * sizeof(long long)), o_v32 = o_VI + al(nv * sizeof(long long));
+  const size_t o_i32 = o_v32 + al(n1 * sizeof(float)), bytes = o_i32 + al(nv * sizeof(float));
+  std::vector<unsigned char> blob(bytes, 0);
+  std::memcpy(blob.data() + o_rp, rp.data(), rp.size() * sizeof(int));
+  std::memcpy(blob.data() + o_col, col.data(), n1 * sizeof(int));
+  std::memcpy(blob.data() + o_vr, vr.data(), n1 * sizeof(double));
+  std::memcpy(blob.data() + o_VR, VR.data(), n1 * sizeof(long long));
+  std::memcpy(blob.data() + o_v32, vr32.data(), n1 * sizeof(float));
+  if (cplx) {
+    std::memcpy(blob.data() + o_vi, vi.data(), nv * sizeof(double));
+    std::memcpy(blob.data() + o_VI, VI.data(), nv * sizeof(long long));
+    std::memcpy(blob.data() + o_i32, vi32.data(), nv * sizeof(float));
+  }
+  cudaError_t ce = cudaMalloc(&ctx->d_csr, bytes);
+  if (ce == cudaSuccess) ce = cudaMemcpy(ctx->d_csr, blob.data(), bytes, cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) return cuda_fail(nullptr, ce, "CSR upload");
+  unsigned char* b = static_cast<unsigned char*>(ctx->d_csr);
+  const int* d_rp = reinterpret_cast<const int*>(b + o_rp);
+  const int* d_col = reinterpret_cast<const int*>(b + o_col);
+  ctx->csr = OpCsr{nops, d_rp, d_col, reinterpret_cast<const double*>(b + o_vr),
+                   cplx ? reinterpret_cast<const double*>(b + o_vi) : nullptr};
+  fx.nops = nops;
+  fx.rp = d_rp;
+  fx.col = d_col;
+  fx.VR = reinterpret_cast<const long long*>(b + o_VR);
+  fx.VI = cplx ? reinterpret_cast<const long long*>(b + o_VI) : nullptr;
+  ctx->csr_c = OpCsrC{nops, d_rp, d_col, reinterpret_cast<const float*>(b + o_v32),
+                      cplx ? reinterpret_cast<const float*>(b + o_i32) : nullptr};
+  return CFET_OK;
+}
+
 }  // namespace
 
 // ============================================================================
@@ -678,8 +835,22 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
       total += o2.ndiag;
     }
     if (total > kMaxDiag) return fail(nullptr, CFET_EINVAL, "DIA: more than 32 diagonals in total");
+  } else if (H0->kind == CFET_OP_CSR) {
+    family = kFamilyCsr;
+    if (H0->dim < 1 || H0->dim >= 0x7fffffffLL) return fail(nullptr, CFET_EINVAL, "CSR: dim must be in [1, 2^31 - 1)");
+    dim = (int)H0->dim;
+    int64_t total = 0;
+    for (int k = -1; k < nV; ++k) {
+      const cfet_op& o2 = k < 0 ? *H0 : V[k];
+      if (o2.kind != CFET_OP_CSR || o2.dim != H0->dim)
+        return fail(nullptr, CFET_EINVAL, "drive operators of a CSR operator must be CSR of the same dimension");
+      const char* why = csr_check(o2, dim);
+      if (why) return fail(nullptr, CFET_EINVAL, why);
+      total += o2.row_ptr[dim];
+    }
+    if (total >= 0x7fffffffLL) return fail(nullptr, CFET_EINVAL, "CSR: more than 2^31 - 2 stored entries in total");
   } else {
-    return fail(nullptr, CFET_EINVAL, "H0 must be an XXZ chain, a Pauli sum or a DIA operator");
+    return fail(nullptr, CFET_EINVAL, "H0 must be an XXZ chain, a Pauli sum, a DIA or a CSR operator");
   }
   {
     cfet_status s = device_available(nullptr);
@@ -925,6 +1096,13 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
       dia_interval(o2.offsets, o2.values, o2.ndiag, dim, &ctx->op_lo[k + 1], &ctx->op_hi[k + 1]);
     }
   }
+  if (family == kFamilyCsr) {
+    cfet_status cs = csr_upload(ctx, H0, nV, V);
+    if (cs != CFET_OK) {
+      free_ctx(ctx);
+      return cs;
+    }
+  }
   // long chains: the window-tiled apply of the complex64 and fixed-point
   // Krylov kernels
   if (family == kFamilySpin && (ctx->precision == CFET_PREC_C64 || ctx->precision == CFET_PREC_FX)) {
@@ -1021,6 +1199,8 @@ cfet_status cfet_apply(cfet_ctx* ctx, const double* c, const void* v_in, void* v
               ? launch_apply_spin(ctx->spin, ctx->dim, c, ctx->nV, (const double2*)v_in, (double2*)v_out, stream)
           : ctx->family == kFamilyPauli
               ? launch_apply_pauli(ctx->pauli, ctx->dim, c, ctx->nV, (const double2*)v_in, (double2*)v_out, stream)
+          : ctx->family == kFamilyCsr
+              ? launch_apply_csr(ctx->csr, ctx->dim, c, ctx->nV, (const double2*)v_in, (double2*)v_out, stream)
               : launch_apply_dia(ctx->dia, ctx->dim, c, ctx->nV, (const double2*)v_in, (double2*)v_out, stream);
   if (e != cudaSuccess) return cuda_fail(ctx, (cudaError_t)e, "apply kernel launch");
   return CFET_OK;

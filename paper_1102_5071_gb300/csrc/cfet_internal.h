@@ -96,6 +96,18 @@ struct OpDia {
   const double* val;     // [ndiag * dim]
 };
 
+// General sparse family: every operator in compressed sparse row form,
+// concatenated (Sec. 8: the stage operator sum_k c_k H_k is applied term by
+// term with the stage scalars, never formed).  Row r of operator o holds the
+// entries [rp[o * (dim + 1) + r], rp[o * (dim + 1) + r + 1]) of col / vr / vi.
+struct OpCsr {
+  int nops;              // 1 + nV
+  const int* rp;         // [nops * (dim + 1)]
+  const int* col;        // [nnz]
+  const double* vr;      // [nnz] real parts
+  const double* vi;      // [nnz] imaginary parts; NULL when every operator is real
+};
+
 // Fixed-point forms of the operator families (see kernels_fx.cu).
 struct OpSpinFx {
   int N;
@@ -121,6 +133,16 @@ struct OpDiaFx {
   int dcount[1 + kMaxDrives];     // number of diagonals of each operator
 };
 
+struct OpCsrFx {
+  int nops;               // 1 + nV
+  const int* rp;          // as OpCsr
+  const int* col;
+  const long long* VR;    // [nnz]: re * 2^-E_op[o]; per row sum |VR| + |VI| < 2^62
+  const long long* VI;    // [nnz] or NULL (real operators)
+  int E_op[1 + kMaxDrives];
+  double maxrow[1 + kMaxDrives];  // max over rows of sum (|re| + |im|), real units
+};
+
 // Mixed-precision forms (see kernels_c64.cu): FP32 operator data.
 struct OpSpinC {
   int N;
@@ -139,6 +161,14 @@ struct OpDiaC {
   const float* val;       // [ndiag * dim], zero where the column is outside [0, dim)
   int dfirst[1 + kMaxDrives];
   int dcount[1 + kMaxDrives];
+};
+
+struct OpCsrC {
+  int nops;
+  const int* rp;
+  const int* col;
+  const float* vr;
+  const float* vi;        // NULL for real operators
 };
 
 struct PropParams {
@@ -187,9 +217,12 @@ int cheb_series(double z, double tol, std::vector<double>* r, double* tail);
 void spin_h0_interval(int N, double J, double Delta, const double* h, double* lo, double* hi);
 void xfield_interval(int N, const double* a, double* lo, double* hi);
 void dia_interval(const int64_t* offsets, const double* values, int ndiag, int dim, double* lo, double* hi);
+void csr_interval(const int64_t* row_ptr, const int32_t* col, const double* re, const double* im, int dim,
+                  double* lo, double* hi);
 void stage_interval(int nops, const double* op_lo, const double* op_hi, const double* s, double* lo, double* hi);
 int launch_cheb_spin_fx(const PropParams& p, const OpSpinFx& op, int grid, int block, void* stream);
 int launch_cheb_dia_fx(const PropParams& p, const OpDiaFx& op, int grid, int block, void* stream);
+int launch_cheb_csr_fx(const PropParams& p, const OpCsrFx& op, int grid, int block, void* stream);
 int max_coresident_blocks_cheb(int family, int block);
 int cheb_threads(int workers);  // threads per CTA of the Chebyshev kernel for `workers` element threads
 
@@ -229,6 +262,7 @@ struct AdjParams {
 // (defined in kernels.cu; return a cudaError_t as int)
 int launch_propagate_spin(const PropParams& p, const OpSpin& op, int grid, int block, void* stream);
 int launch_propagate_dia(const PropParams& p, const OpDia& op, int grid, int block, void* stream);
+int launch_propagate_csr(const PropParams& p, const OpCsr& op, int grid, int block, void* stream);
 int launch_propagate_spin_ip(const PropParams& p, const OpSpinIP& op, int grid, int block, void* stream);
 int max_coresident_blocks_ip(int block, int nw);
 int launch_propagate_pauli(const PropParams& p, const OpPauli& op, int grid, int block, void* stream);
@@ -241,13 +275,17 @@ int launch_apply_spin(const OpSpin& op, int dim, const double* c, int nV, const 
                       void* stream);
 int launch_apply_dia(const OpDia& op, int dim, const double* c, int nV, const double2* vin, double2* vout,
                      void* stream);
+int launch_apply_csr(const OpCsr& op, int dim, const double* c, int nV, const double2* vin, double2* vout,
+                     void* stream);
 int launch_spin_tables(int N, int L, double J, double Delta, const double* h, double* dz_lo, double* dz_hi,
                        void* stream);
 int launch_propagate_spin_fx(const PropParams& p, const OpSpinFx& op, int grid, int block, void* stream);
 int launch_propagate_dia_fx(const PropParams& p, const OpDiaFx& op, int grid, int block, void* stream);
+int launch_propagate_csr_fx(const PropParams& p, const OpCsrFx& op, int grid, int block, void* stream);
 int max_coresident_blocks_fx(int family, int block, bool tiled);
 int launch_propagate_spin_c64(const PropParams& p, const OpSpinC& op, int grid, int block, void* stream);
 int launch_propagate_dia_c64(const PropParams& p, const OpDiaC& op, int grid, int block, void* stream);
+int launch_propagate_csr_c64(const PropParams& p, const OpCsrC& op, int grid, int block, void* stream);
 int max_coresident_blocks_c64(int family, int block, bool tiled);
 // Chains of at least this many sites take the window-tiled apply
 // (tiled_common.cuh) in the complex64 and fixed-point kernels, unless
@@ -265,6 +303,6 @@ int max_coresident_blocks_adjoint(int block);
 int max_coresident_blocks(int family, int block);  // per device, for the persistent kernel
 size_t propagate_smem_bytes(int block);
 
-enum Family { kFamilySpin = 1, kFamilyDia = 2, kFamilySpinIP = 3, kFamilyPauli = 4 };
+enum Family { kFamilySpin = 1, kFamilyDia = 2, kFamilySpinIP = 3, kFamilyPauli = 4, kFamilyCsr = 5 };
 
 }  // namespace cfet

@@ -136,6 +136,23 @@ void dia_interval(const int64_t* offsets, const double* values, int ndiag, int d
   *hi = u;
 }
 
+void csr_interval(const int64_t* row_ptr, const int32_t* col, const double* re, const double* im, int dim,
+                  double* lo, double* hi) {
+  double l = INFINITY, u = -INFINITY;
+  for (int r = 0; r < dim; ++r) {
+    double d = 0.0, R = 0.0;
+    for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+      if (col[e] == r) d += re[e];
+      else R += std::hypot(re[e], im ? im[e] : 0.0);
+    }
+    l = std::min(l, d - R);
+    u = std::max(u, d + R);
+  }
+  if (dim < 1 || !(l <= u)) l = u = 0.0;
+  *lo = l;
+  *hi = u;
+}
+
 void stage_interval(int nops, const double* op_lo, const double* op_hi, const double* s, double* lo, double* hi) {
   double l = 0.0, u = 0.0;
   for (int o = 0; o < nops; ++o) {

@@ -2,7 +2,7 @@
 // int64 (re, im) mantissas with one exponent per vector, exact integer
 // neighbour sums, products of a scalar mantissa with a stored value by the
 // high half of a 64 x 64 product, exact 128-bit reductions; and the stage
-// operator applies in that format (XXZ chain, DIA).  See kernels_fx.cu for
+// operator applies in that format (XXZ chain, DIA, CSR).  See kernels_fx.cu for
 // the number format's bounds and rounding.
 #pragma once
 
@@ -288,6 +288,53 @@ __device__ __forceinline__ longlong2 fx_apply_dia(const longlong2* q, const long
     ui += fx_mulhi(c.m_p, w.y << c.pp);
   }
   return make_longlong2(ur, ui);
+}
+
+// CSR: per operator the exact 128-bit sums of VAL * q over the row's entries
+// (complex values: re = sum VR w.x - VI w.y, im = sum VR w.y + VI w.x; the row
+// sums of |VR| + |VI| stay below 2^62 and |q| < 2^57, so no sum overflows),
+// then one rounded product with the operator's scalar mantissa as for DIA.
+__device__ __forceinline__ longlong2 fx_apply_csr(const longlong2* q, const longlong2* qm, int r, int dim,
+                                                  const OpCsrFx& op, const FxConstA& c) {
+  long long ur = 0, ui = 0;
+  for (int o = 0; o < op.nops; ++o) {
+    const int* rp = op.rp + (size_t)o * (dim + 1);
+    const int e0 = __ldg(rp + r), e1 = __ldg(rp + r + 1);
+    __int128 ar = 0, ai = 0;
+    if (op.VI) {
+      for (int e = e0; e < e1; ++e) {
+        const long long a = __ldg(op.VR + e), b = __ldg(op.VI + e);
+        const longlong2 w = q[__ldg(op.col + e)];
+        ar += (__int128)a * w.x - (__int128)b * w.y;
+        ai += (__int128)a * w.y + (__int128)b * w.x;
+      }
+    } else {
+      for (int e = e0; e < e1; ++e) {
+        const long long a = __ldg(op.VR + e);
+        const longlong2 w = q[__ldg(op.col + e)];
+        ar += (__int128)a * w.x;
+        ai += (__int128)a * w.y;
+      }
+    }
+    ur += fx_mulhi(c.m_op[o], fx_shr128(ar, c.sh_pre[o]));
+    ui += fx_mulhi(c.m_op[o], fx_shr128(ai, c.sh_pre[o]));
+  }
+  if (c.use_prev) {
+    const longlong2 w = qm[r];
+    ur += fx_mulhi(c.m_p, w.x << c.pp);
+    ui += fx_mulhi(c.m_p, w.y << c.pp);
+  }
+  return make_longlong2(ur, ui);
+}
+
+// The two stored-matrix families behind one name (DIA, CSR).
+__device__ __forceinline__ longlong2 fx_apply_sparse(const longlong2* q, const longlong2* qm, int r, int dim,
+                                                     const OpDiaFx& op, const FxConstA& c) {
+  return fx_apply_dia(q, qm, r, dim, op, c);
+}
+__device__ __forceinline__ longlong2 fx_apply_sparse(const longlong2* q, const longlong2* qm, int r, int dim,
+                                                     const OpCsrFx& op, const FxConstA& c) {
+  return fx_apply_csr(q, qm, r, dim, op, c);
 }
 
 }  // namespace cfet

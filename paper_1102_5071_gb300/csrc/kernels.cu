@@ -15,8 +15,8 @@
 // same fixed order, so all CTAs hold bit-identical alpha/beta and take the
 // same adaptive decisions without a broadcast.  Warp 0 of each CTA evaluates
 // the small exponential exp(-i tau T_k) e_1 of the tridiagonal Lanczos matrix.
-// Operator families: XXZ chain with X fields, DIA, general Pauli sums, and
-// the chain in the interaction picture; optionally every Lanczos vector is
+// Operator families: XXZ chain with X fields, DIA, CSR, general Pauli sums,
+// and the chain in the interaction picture; optionally every Lanczos vector is
 // re-orthogonalised against all earlier ones (classical Gram-Schmidt).
 #include <cuda_runtime.h>
 
@@ -47,6 +47,46 @@ __device__ __forceinline__ double2 apply_dia_at(const double2* q, int r, int dim
     }
   }
   return acc;
+}
+
+// CSR family: sum_o copf[o] sum_{e in row r of o} val[e] v[col[e]], with the
+// complex values (vr + i vi) of Hermitian operators, coef pre-scaled.
+__device__ __forceinline__ double2 apply_csr_at(const double2* q, int r, int dim, const OpCsr& op,
+                                                const double* copf) {
+  double ar = 0.0, ai = 0.0;
+  for (int o = 0; o < op.nops; ++o) {
+    const int* rp = op.rp + (size_t)o * (dim + 1);
+    const int e0 = __ldg(rp + r), e1 = __ldg(rp + r + 1);
+    double sr = 0.0, si = 0.0;
+    if (op.vi) {
+      for (int e = e0; e < e1; ++e) {
+        const double a = __ldg(op.vr + e), b = __ldg(op.vi + e);
+        const double2 w = q[__ldg(op.col + e)];
+        sr = fma(a, w.x, fma(-b, w.y, sr));
+        si = fma(a, w.y, fma(b, w.x, si));
+      }
+    } else {
+      for (int e = e0; e < e1; ++e) {
+        const double a = __ldg(op.vr + e);
+        const double2 w = q[__ldg(op.col + e)];
+        sr = fma(a, w.x, sr);
+        si = fma(a, w.y, si);
+      }
+    }
+    ar = fma(copf[o], sr, ar);
+    ai = fma(copf[o], si, ai);
+  }
+  return make_double2(ar, ai);
+}
+
+// The two stored-matrix families behind one name (DIA, CSR).
+__device__ __forceinline__ double2 apply_sparse_at(const double2* q, int r, int dim, const OpDia& op,
+                                                   const double* copf) {
+  return apply_dia_at(q, r, dim, op, copf);
+}
+__device__ __forceinline__ double2 apply_sparse_at(const double2* q, int r, int dim, const OpCsr& op,
+                                                   const double* copf) {
+  return apply_csr_at(q, r, dim, op, copf);
 }
 
 // Pauli-sum family at index y: for every group of strings with X mask xm,
@@ -287,7 +327,7 @@ __global__ void __launch_bounds__(256) k_propagate(PropParams p, Op op) {
             }
           } else {
             for (int x = x0; x < dim; x += stride) {
-              double2 hv = apply_dia_at(q, x, dim, op, S.copf);
+              double2 hv = apply_sparse_at(q, x, dim, op, S.copf);
               if (qm) {
                 const double2 w = qm[x];
                 hv.x = fma(-bm, w.x, hv.x);
@@ -544,7 +584,7 @@ __global__ void k_apply(Op op, int dim, Coefs c, int nV, const double2* __restri
     } else if constexpr (FAMILY == kFamilyPauli) {
       vout[x] = apply_pauli_at(vin, x, op, pc);
     } else {
-      vout[x] = apply_dia_at(vin, x, dim, op, copf);
+      vout[x] = apply_sparse_at(vin, x, dim, op, copf);
     }
   }
 }
@@ -602,6 +642,9 @@ int launch_propagate_spin(const PropParams& p, const OpSpin& op, int grid, int b
 int launch_propagate_dia(const PropParams& p, const OpDia& op, int grid, int block, void* stream) {
   return launch_prop<kFamilyDia>(p, op, grid, block, stream);
 }
+int launch_propagate_csr(const PropParams& p, const OpCsr& op, int grid, int block, void* stream) {
+  return launch_prop<kFamilyCsr>(p, op, grid, block, stream);
+}
 int launch_propagate_pauli(const PropParams& p, const OpPauli& op, int grid, int block, void* stream) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -656,6 +699,8 @@ int max_coresident_blocks(int family, int block) {
   cudaError_t e;
   if (family == kFamilySpin)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate<kFamilySpin, OpSpin>, block, sizeof(SmemLayout));
+  else if (family == kFamilyCsr)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate<kFamilyCsr, OpCsr>, block, sizeof(SmemLayout));
   else
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate<kFamilyDia, OpDia>, block, sizeof(SmemLayout));
   if (e != cudaSuccess) return -1;
@@ -701,6 +746,13 @@ int launch_apply_dia(const OpDia& op, int dim, const double* c, int nV, const do
   Coefs cc = {};
   for (int i = 0; i < 1 + nV; ++i) cc.c[i] = c[i];
   k_apply<kFamilyDia, OpDia><<<apply_grid(dim, 256), 256, 0, (cudaStream_t)stream>>>(op, dim, cc, nV, vin, vout);
+  return (int)cudaGetLastError();
+}
+int launch_apply_csr(const OpCsr& op, int dim, const double* c, int nV, const double2* vin, double2* vout,
+                     void* stream) {
+  Coefs cc = {};
+  for (int i = 0; i < 1 + nV; ++i) cc.c[i] = c[i];
+  k_apply<kFamilyCsr, OpCsr><<<apply_grid(dim, 256), 256, 0, (cudaStream_t)stream>>>(op, dim, cc, nV, vin, vout);
   return (int)cudaGetLastError();
 }
 int launch_apply_pauli(const OpPauli& op, int dim, const double* c, int nV, const double2* vin, double2* vout,

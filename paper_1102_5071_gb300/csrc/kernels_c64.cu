@@ -241,6 +241,50 @@ __device__ __forceinline__ float2 c_apply_dia(const float2* __restrict__ q, cons
   return make_float2(ur, ui);
 }
 
+// CSR: per operator the row's sum of val * q in FP32 (complex values of
+// Hermitian operators), then the operator's scalar.
+__device__ __forceinline__ float2 c_apply_csr(const float2* __restrict__ q, const float2* __restrict__ qm, int r,
+                                              int dim, const OpCsrC& op, const CConst& c) {
+  float ur = 0.f, ui = 0.f;
+  for (int o = 0; o < op.nops; ++o) {
+    const int* rp = op.rp + (size_t)o * (dim + 1);
+    const int e0 = __ldg(rp + r), e1 = __ldg(rp + r + 1);
+    float ar = 0.f, ai = 0.f;
+    if (op.vi) {
+      for (int e = e0; e < e1; ++e) {
+        const float a = __ldg(op.vr + e), b = __ldg(op.vi + e);
+        const float2 w = q[__ldg(op.col + e)];
+        ar = fmaf(a, w.x, fmaf(-b, w.y, ar));
+        ai = fmaf(a, w.y, fmaf(b, w.x, ai));
+      }
+    } else {
+      for (int e = e0; e < e1; ++e) {
+        const float a = __ldg(op.vr + e);
+        const float2 w = q[__ldg(op.col + e)];
+        ar = fmaf(a, w.x, ar);
+        ai = fmaf(a, w.y, ai);
+      }
+    }
+    ur = fmaf(c.co[o], ar, ur);
+    ui = fmaf(c.co[o], ai, ui);
+  }
+  if (c.use_prev) {
+    const float2 w = qm[r];
+    ur = fmaf(c.cp, w.x, ur);
+    ui = fmaf(c.cp, w.y, ui);
+  }
+  return make_float2(ur, ui);
+}
+
+__device__ __forceinline__ float2 c_apply_sparse(const float2* __restrict__ q, const float2* __restrict__ qm, int r,
+                                                 int dim, const OpDiaC& op, const CConst& c) {
+  return c_apply_dia(q, qm, r, dim, op, c);
+}
+__device__ __forceinline__ float2 c_apply_sparse(const float2* __restrict__ q, const float2* __restrict__ qm, int r,
+                                                 int dim, const OpCsrC& op, const CConst& c) {
+  return c_apply_csr(q, qm, r, dim, op, c);
+}
+
 // ------------------------------------------------------------------ control warp
 // Worker warps: compensated per-warp partial of sum j into shared memory.
 __device__ __forceinline__ void c_worker_partial(SmemC& S, float s, float c, int j = 0) {
@@ -633,7 +677,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
             for (; x < wxe; x += wstep) {
               float2 hv;
               if constexpr (FAMILY == kFamilySpin) hv = c_apply_spin(q, qm, x, op, c, S.bx);
-              else hv = c_apply_dia(q, qm, x, dim, op, c);
+              else hv = c_apply_sparse(q, qm, x, dim, op, c);
               u[x] = hv;
               const float2 v = q[x];
               ff_add_prod(s0, c0, v.x, hv.x);
@@ -943,6 +987,9 @@ int launch_propagate_spin_c64(const PropParams& p, const OpSpinC& op, int grid, 
 int launch_propagate_dia_c64(const PropParams& p, const OpDiaC& op, int grid, int block, void* stream) {
   return launch_prop_c64<kFamilyDia>(p, op, grid, block, stream);
 }
+int launch_propagate_csr_c64(const PropParams& p, const OpCsrC& op, int grid, int block, void* stream) {
+  return launch_prop_c64<kFamilyCsr>(p, op, grid, block, stream);
+}
 
 int max_coresident_blocks_c64(int family, int block, bool tiled) {
   int dev = 0, nsm = 0, per = 0;
@@ -952,6 +999,7 @@ int max_coresident_blocks_c64(int family, int block, bool tiled) {
   // asks for its tile buffers and gets the shared-memory split it needs)
   cudaFuncSetAttribute(k_propagate_c64<kFamilySpin, OpSpinC>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaFuncSetAttribute(k_propagate_c64<kFamilyDia, OpDiaC>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  cudaFuncSetAttribute(k_propagate_c64<kFamilyCsr, OpCsrC>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaFuncSetAttribute(k_propagate_c64<kFamilySpin, OpSpinC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)c64_tiled_smem_bytes());
   cudaError_t e;
@@ -959,6 +1007,9 @@ int max_coresident_blocks_c64(int family, int block, bool tiled) {
     e = tiled ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_c64<kFamilySpin, OpSpinC, true>, block,
                                                               c64_tiled_smem_bytes())
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_c64<kFamilySpin, OpSpinC>, block, sizeof(SmemC));
+  else if (family == kFamilyCsr)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_c64<kFamilyCsr, OpCsrC>, block,
+                                                      sizeof(SmemC));
   else
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_c64<kFamilyDia, OpDiaC>, block,
                                                       sizeof(SmemC));

@@ -221,7 +221,7 @@ __device__ __forceinline__ longlong2 cheb_apply1(const longlong2* cur, const lon
                                                  const Op& op, const FxConstA& c, const long long* mb, long long m_s) {
   longlong2 y;
   if constexpr (FAMILY == kFamilySpin) y = fx_apply_spin(cur, prev, x, op, c, mb);
-  else y = fx_apply_dia(cur, prev, x, dim, op, c);
+  else y = fx_apply_sparse(cur, prev, x, dim, op, c);
   if (m_s != 0) {
     const longlong2 v = cur[x];
     y.x += fx_mulhi(m_s, v.x << c.pk);
@@ -569,6 +569,9 @@ int launch_cheb_spin_fx(const PropParams& p, const OpSpinFx& op, int grid, int b
 int launch_cheb_dia_fx(const PropParams& p, const OpDiaFx& op, int grid, int block, void* stream) {
   return launch_cheb<kFamilyDia>(p, op, grid, block, stream);
 }
+int launch_cheb_csr_fx(const PropParams& p, const OpCsrFx& op, int grid, int block, void* stream) {
+  return launch_cheb<kFamilyCsr>(p, op, grid, block, stream);
+}
 
 int cheb_threads(int workers) { return workers < kChebThreads ? workers : kChebThreads; }
 
@@ -578,9 +581,13 @@ int max_coresident_blocks_cheb(int family, int block) {
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaFuncSetAttribute(k_cheb_fx<kFamilySpin, OpSpinFx>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaFuncSetAttribute(k_cheb_fx<kFamilyDia, OpDiaFx>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  cudaFuncSetAttribute(k_cheb_fx<kFamilyCsr, OpCsrFx>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaError_t e;
   if (family == kFamilySpin)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cheb_fx<kFamilySpin, OpSpinFx>, block,
+                                                      sizeof(SmemCheb));
+  else if (family == kFamilyCsr)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cheb_fx<kFamilyCsr, OpCsrFx>, block,
                                                       sizeof(SmemCheb));
   else
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cheb_fx<kFamilyDia, OpDiaFx>, block,

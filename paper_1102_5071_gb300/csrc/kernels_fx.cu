@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
             for (; x < wxe; x += wstep) {
               longlong2 hv;
               if constexpr (FAMILY == kFamilySpin) hv = fx_apply_spin(q, qm, x, op, c, S.mb);
-              else hv = fx_apply_dia(q, qm, x, dim, op, c);
+              else hv = fx_apply_sparse(q, qm, x, dim, op, c);
               u[x] = hv;
               const longlong2 v = q[x];
               a2 += (__int128)v.x * hv.x + (__int128)v.y * hv.y;
@@ -931,6 +931,9 @@ int launch_propagate_spin_fx(const PropParams& p, const OpSpinFx& op, int grid, 
 int launch_propagate_dia_fx(const PropParams& p, const OpDiaFx& op, int grid, int block, void* stream) {
   return launch_prop_fx<kFamilyDia>(p, op, grid, block, stream);
 }
+int launch_propagate_csr_fx(const PropParams& p, const OpCsrFx& op, int grid, int block, void* stream) {
+  return launch_prop_fx<kFamilyCsr>(p, op, grid, block, stream);
+}
 
 size_t fx_tiled_smem_bytes() { return ((sizeof(SmemFx) + 127) & ~size_t(127)) + 4 * kFxTileElems * sizeof(longlong2); }
 
@@ -943,6 +946,7 @@ int max_coresident_blocks_fx(int family, int block, bool tiled) {
   // (a tiled launch asks for its tile buffers and gets the split it needs)
   cudaFuncSetAttribute(k_propagate_fx<kFamilySpin, OpSpinFx>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaFuncSetAttribute(k_propagate_fx<kFamilyDia, OpDiaFx>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  cudaFuncSetAttribute(k_propagate_fx<kFamilyCsr, OpCsrFx>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
   cudaFuncSetAttribute(k_propagate_fx<kFamilySpin, OpSpinFx, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)fx_tiled_smem_bytes());
   cudaError_t e;
@@ -950,6 +954,9 @@ int max_coresident_blocks_fx(int family, int block, bool tiled) {
     e = tiled ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_fx<kFamilySpin, OpSpinFx, true>, block,
                                                               fx_tiled_smem_bytes())
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_fx<kFamilySpin, OpSpinFx>, block, sizeof(SmemFx));
+  else if (family == kFamilyCsr)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_fx<kFamilyCsr, OpCsrFx>, block,
+                                                      sizeof(SmemFx));
   else
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_fx<kFamilyDia, OpDiaFx>, block,
                                                       sizeof(SmemFx));

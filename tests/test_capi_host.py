@@ -310,3 +310,39 @@ def test_chebyshev_coefficients_validate(lib):
     buf = np.zeros(2)
     st = lib.cfet_chebyshev_coefficients(10.0, 1e-8, 2, buf.ctypes.data_as(_capi.c_double_p), C.byref(K), C.byref(tail))
     assert st == _capi.CFET_EINVAL and K.value > 1
+
+
+def test_create_validates_csr_operators(lib):
+    # CFET_OP_CSR: structure, column range, finite values and Hermiticity are
+    # checked before any device work; a valid operator then reaches the device
+    # check (CFET_ENODEV without a GPU)
+    keep = []
+    cb = _capi.DRIVE_FN(lambda t, u: 0.0)
+    rp = np.array([0, 1, 2], dtype=np.int64)
+    herm = P.CSR(rp, np.array([1, 0]), np.array([0.5 + 0.25j, 0.5 - 0.25j]))
+    cases = [
+        (P.CSR(rp, np.array([1, 0]), np.array([0.5 + 0.25j, 0.5 + 0.25j])), b"Hermitian"),
+        (P.CSR(rp, np.array([2, 0]), np.array([1.0, 1.0])), b"column"),
+        (P.CSR(np.array([0, 2, 1], dtype=np.int64), np.array([0, 1]), np.array([1.0, 1.0])), b"row_ptr"),
+        (P.CSR(np.array([1, 1, 2], dtype=np.int64), np.array([0, 1]), np.array([1.0, 1.0])), b"row_ptr"),
+        (P.CSR(np.array([0, 1], dtype=np.int64), np.array([0]), np.array([1.0 + 0.5j])), b"Hermitian"),
+        (P.CSR(rp, np.array([1, 0]), np.array([np.inf, np.inf])), b"finite"),
+    ]
+    for op, word in cases:
+        st, _ = _create(lib, P._op_struct(op, keep), [], [])
+        assert st == _capi.CFET_EINVAL and word in lib.cfet_last_error(None), (word, lib.cfet_last_error(None))
+    # drive operators of a CSR H0 must be CSR of the same dimension
+    dia = P._op_struct(P.DIA(np.array([0]), np.ones((1, 2))), keep)
+    st, _ = _create(lib, P._op_struct(herm, keep), [dia], [cb])
+    assert st == _capi.CFET_EINVAL and b"CSR" in lib.cfet_last_error(None)
+    other = P.CSR(np.array([0, 1, 2, 3], dtype=np.int64), np.array([0, 1, 2]), np.ones(3))
+    st, _ = _create(lib, P._op_struct(herm, keep), [P._op_struct(other, keep)], [cb])
+    assert st == _capi.CFET_EINVAL
+    # mirrors within the tolerance, duplicates summed, empty rows: valid
+    dup = P.CSR(np.array([0, 3, 4, 4], dtype=np.int64), np.array([1, 0, 1, 0]),
+                np.array([0.25 + 0.5j, 2.0, 0.25 + 0.5j, 0.5 - 1.0j]))
+    for op in (herm, dup):
+        st, ctx = _create(lib, P._op_struct(op, keep), [], [])
+        assert st in (_capi.CFET_OK, _capi.CFET_ENODEV), lib.cfet_last_error(None)
+        if st == _capi.CFET_OK:
+            lib.cfet_destroy(ctx)

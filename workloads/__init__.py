@@ -199,6 +199,71 @@ def chain_batch(n: int = 256, n_lo: int = 10, n_hi: int = 16, seed: int = 7, J: 
 
 
 # ---------------------------------------------------------------------------
+# Sparse Hermitian operators in compressed sparse row form
+# ---------------------------------------------------------------------------
+def _csr_from_entries(dim, rows, cols, vals):
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    row_ptr = np.zeros(dim + 1, dtype=np.int64)
+    np.add.at(row_ptr, rows + 1, 1)
+    return np.cumsum(row_ptr), cols.astype(np.int32), vals
+
+
+def random_hermitian_csr(seed: int, dim: int, per_row: int = 6, complex_values: bool = True,
+                         band: int = 0, duplicates: int = 0):
+    """(row_ptr, col_idx, values) of a seeded sparse Hermitian matrix: a real
+    diagonal U[-1, 1], and per row `per_row` upper-triangle partners (within
+    `band` columns when band > 0, anywhere otherwise) with values whose real
+    and imaginary parts are U[-1, 1] (real only without complex_values),
+    mirrored with the conjugate value; `duplicates` entries are split into two
+    stored halves (the same matrix, with repeated (row, column) pairs)."""
+    u = uniform(seed, dim * (3 * per_row + 1) + 2 * duplicates + 1)
+    pos = 0
+    rows, cols, vals = [np.arange(dim)], [np.arange(dim)], [u[pos:pos + dim] * 2.0 - 1.0]
+    pos += dim
+    r = np.repeat(np.arange(dim), per_row)
+    span = np.where(band > 0, np.minimum(band, dim - 1 - r), dim - 1 - r)
+    off = 1 + np.floor(u[pos:pos + dim * per_row] * np.maximum(span, 1)).astype(np.int64)
+    pos += dim * per_row
+    ok = span >= 1
+    c = np.minimum(r + off, dim - 1)
+    re = u[pos:pos + dim * per_row] * 2.0 - 1.0
+    pos += dim * per_row
+    im = (u[pos:pos + dim * per_row] * 2.0 - 1.0) if complex_values else np.zeros(dim * per_row)
+    pos += dim * per_row
+    r, c, v = r[ok & (c > r)], c[ok & (c > r)], (re + 1j * im)[ok & (c > r)]
+    rows += [r, c]
+    cols += [c, r]
+    vals += [v, np.conj(v)]
+    rows, cols = np.concatenate(rows), np.concatenate(cols)
+    vals = np.concatenate([np.asarray(a, dtype=np.complex128) for a in vals])
+    if duplicates:
+        pick = (u[pos:pos + duplicates] * len(rows)).astype(np.int64)
+        half = vals[pick] * 0.5
+        vals[pick] = half
+        rows, cols = np.concatenate([rows, rows[pick]]), np.concatenate([cols, cols[pick]])
+        vals = np.concatenate([vals, half])
+    rp, ci, vv = _csr_from_entries(dim, rows, cols, vals)
+    return rp, ci, (vv if complex_values else vv.real.copy())
+
+
+def dia_to_csr(offsets, values):
+    """(row_ptr, col_idx, values) of a real DIA operator (stored diagonals,
+    entries outside the matrix dropped, zeros kept)."""
+    values = np.asarray(values, dtype=np.float64)
+    dim = values.shape[1]
+    r = np.arange(dim)
+    rows, cols, vals = [], [], []
+    for d, off in enumerate(offsets):
+        c = r + int(off)
+        ok = (c >= 0) & (c < dim)
+        rows.append(r[ok])
+        cols.append(c[ok])
+        vals.append(values[d, ok])
+    return _csr_from_entries(dim, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
+# ---------------------------------------------------------------------------
 # Named workloads (sizes of the driven-chain and grid-atom experiments)
 # ---------------------------------------------------------------------------
 CHAIN_SMALL = dict(N=8, J=1.0, Delta=0.5, A=1.0, omega=2.0, h_seed=1, order=4, dt=0.01, T=10.0,
