@@ -437,7 +437,9 @@ def small_chain_line(P, torch):
             "cfet_steps_per_s": n / (ms * 1e-3), "H_applies_per_s": st["n_applies"] / (ms * 1e-3),
             "us_per_apply": 1e3 * kms / st["n_applies"], "ms": ms, "kernel_ms": kms, "H_applies": st["n_applies"],
             "final_state_error": torch.linalg.vector_norm(x - ref).item(),
-            "reference": "CF8:11, dt 0.0025, tol 1e-14, m_max 24 (fixed point)"}
+            "reference": "CF8:11, dt 0.0025, tol 1e-14, m_max 24 (fixed point)",
+            "grid": None if not st.get("phase_ns") else "see phase_Mcycles",
+            "phase_Mcycles": {k: v * 1e-6 for k, v in zip(PHASES, st.get("phase_ns", [0] * 8))}}
 
 
 def run_gpu(args):

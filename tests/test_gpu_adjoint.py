@@ -5,14 +5,15 @@
   fixed-point and FP64 formats, with and without intermediate checkpoints;
 * the full-size configuration (N = 18, 64 amplitude segments, T = 16,
   CF4:2, dt = 0.01, FP64): all 64 components against central finite
-  differences (h = 1e-6) of the GPU loss, with a fixed Krylov dimension so
-  that the loss is a smooth function of the amplitudes;
+  differences (h = 1e-6) of the GPU fidelity, relative to the largest
+  component, with a fixed Krylov dimension so that the loss is a smooth
+  function of the amplitudes;
 * the torch.autograd wrapper and argument validation.
 
 Tolerances: the forward and backward Krylov exponentials are accurate to the
 Krylov tolerance per stage, so loss and gradient differ from the exact ones by
 a few times n_stages x tol; central differences have truncation error
-O(h^2) and rounding error O(eps / h) ~ 1e-10 relative to the loss.
+O(h^2) and rounding error O(eps F / h), F the fidelity that is differenced.
 """
 
 
@@ -102,25 +103,31 @@ def test_full_size_gradient_matches_central_differences(torch_cuda):
     fwd = P.Propagator(P.XXZChain(N, pr.J, pr.Delta, pr.h), [P.XField(N, np.ones(N))], [f], m_max=m, precision="fx")
     x = torch.empty_like(psi0)
 
-    def loss(am):
+    def fidelity(am):
         cur[:] = am
         x.copy_(psi0)
         fwd.propagate(x, 0.0, dt, nsteps, order=4, tol=0.0)
-        return 1.0 - abs(torch.vdot(phi, x).item()) ** 2
+        return abs(torch.vdot(phi, x).item()) ** 2
 
-    assert abs(loss(amps) - L) <= 1e-12
+    F0 = fidelity(amps)
+    assert abs((1.0 - F0) - L) <= 1e-12
+    # A random target in dim 2^18 has |<phi|psi>|^2 ~ 2^-18, so the gradient
+    # components are ~1e-6: they are compared relative to the largest one.  The
+    # fidelity itself is differenced (not 1 - F, whose rounding at 1 would
+    # swamp differences of ~1e-12); its rounding noise is ~1e-19, i.e. ~1e-13
+    # in a central difference with h = 1e-6, far below 1e-4 of the gradient.
     h = 1e-6
-    scale = max(1.0, np.max(np.abs(g)))
     fd = np.empty(nseg)
     for k in range(nseg):
         ap, am_ = amps.copy(), amps.copy()
         ap[k] += h
         am_[k] -= h
-        fd[k] = (loss(ap) - loss(am_)) / (2 * h)
+        fd[k] = -(fidelity(ap) - fidelity(am_)) / (2 * h)
     fwd.close()
+    gmax = np.max(np.abs(g))
     worst = int(np.argmax(np.abs(fd - g)))
-    assert np.max(np.abs(fd - g)) <= 1e-6 * scale, (worst, fd[worst], g[worst])
-    assert np.max(np.abs(g)) > 1e-3        # a gradient that is not trivially zero
+    assert gmax > 10 * F0 / nsteps                   # not trivially zero: ~F0 spread over the segments
+    assert np.max(np.abs(fd - g)) <= 1e-4 * gmax, (worst, fd[worst], g[worst], gmax)
     assert st["max_drift"] <= 1e-9
 
 
