@@ -56,8 +56,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 fl
 DRAM_BYTES_PER_ITERATION = {"fx": (1.207240448e9 + 1.633021184e9) / 76, "c64": (191.0784e6 + 649.152256e6) / 76,
                             "f64": None}
 
-# ncu L2 (lts__t_bytes) bytes per Lanczos iteration, same capture; None until measured
-LTS_BYTES_PER_ITERATION = {"fx": None, "c64": None, "f64": None}
+# ncu L2 (lts__t_bytes) bytes per Lanczos iteration of the element-wise fixed-point
+# kernel (2-step capture: 76 iterations, see profiles/); None where not measured
+LTS_BYTES_PER_ITERATION = {"fx": 32462538176 / 76, "c64": None, "f64": None}
 
 # final-state error: horizon, and the reference run (CF8:11 at REF_DT, REF_TOL)
 ERR_T = 1.0
@@ -461,7 +462,7 @@ def run_gpu(args):
     dim = 1 << N_SITES
     cheb = args.expm == "chebyshev"
     prop = make_chain(P, pr, N_SITES, args.precision, block_size=args.block_size, grid_size=args.grid_size,
-                      expm=args.expm)
+                      expm=args.expm, apply_form=args.apply_form)
     psi = torch.from_numpy(psi0).cuda()
     t0 = 0.0
     # warm-up steps (untimed)
@@ -543,7 +544,8 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms_med / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fx": "i64", "c64": "f32", "f64": "f64"}[args.precision],
-            "data": "synthetic", "config": dict(workload_config(), precision=args.precision, expm=args.expm),
+            "data": "synthetic", "config": dict(workload_config(), precision=args.precision, expm=args.expm,
+                                                apply_form=args.apply_form),
             "timed_repeats": len(reps),
             "timing_note": f"the {args.steps}-step call timed {len(reps)} times back to back (CUDA events, "
                            f"barrier and synchronize around each); value and ms_per_step are the medians",
@@ -612,6 +614,8 @@ def main():
                     help="stage exponentials: Krylov (default) or the Chebyshev expansion (fixed point only)")
     ap.add_argument("--grid-size", type=int, default=0,
                     help="CTAs of the persistent kernel (0 = co-resident maximum)")
+    ap.add_argument("--apply-form", default="auto", choices=["auto", "elementwise", "tiled", "staged"],
+                    help="XXZ-chain apply form of the fixed-point and complex64 kernels")
     ap.add_argument("--min-timed-ms", type=float, default=2000.0,
                     help="the K-step call is repeated until at least this much has been timed (median reported)")
     ap.add_argument("--quick", action="store_true",

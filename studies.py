@@ -560,6 +560,203 @@ def run_study_picture(args):
     return 0
 
 
+def _timed(torch, fn):
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    out = fn()
+    ev1.record()
+    torch.cuda.synchronize()
+    return out, ev0.elapsed_time(ev1)
+
+
+# FP64 settings searched for an equal final-state error: (dt, Krylov tol)
+EE_DTS = (0.02, 0.04, 0.05, 0.1, 0.2)
+EE_TOLS = (1e-10, 1e-8, 1e-7, 1e-6, 1e-5)
+
+
+def run_study_equal_error(args):
+    """Speed-ups of the mixed-precision, batched and adjoint forms over the
+    plain FP64 GPU propagator at the same final-state error (the effort-error
+    relation of Sec. 6.1: a cheaper, less accurate setting of the baseline is
+    allowed whenever it still meets the form's error).
+
+    1. complex64 vectors, N = 20 chain, CF6:5Opt dt 0.02 tol 1e-10 over
+       T = --ee-T: error against CF8:11 dt 0.0025 tol 1e-13; the fastest FP64
+       setting (order 6, dt in EE_DTS, tol in EE_TOLS) with an error not
+       above it.
+    2. the complex64 batch (256 chains N = 10..16, CF6:5Opt dt 0.02 tol 1e-10,
+       T = --ee-batch-T): largest per-instance error against an FP64 batch at
+       CF8:11 dt 0.0025 tol 1e-13; FP64 settings screened on 14 instances
+       (two per size), the fastest adequate one timed instance by instance on
+       all 256 with the single-instance FP64 propagator.
+    3. the adjoint gradient (N = 18, 64 segments, T = 16, CF4:2 dt 0.01, FP64,
+       tol 1e-10): largest component error against the adjoint at tol 1e-13,
+       relative to the largest component; central differences of the fidelity
+       with the FP64 propagator (decisions recorded at the nominal amplitudes
+       and replayed at +-h, so the fidelity is smooth), h and tol screened on 4
+       components, the fastest adequate setting costed as 128 propagations."""
+    import torch
+    import paper_1102_5071_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    out = {"study": "equal final-state error: mixed precision, batch, adjoint against the plain FP64 propagator"}
+    # ---------------- 1. complex64 single instance
+    pr, psi0 = problem()
+    T = args.ee_T
+
+    def chain(prec, m_max=M_MAX):
+        return P.Propagator(P.XXZChain(N_SITES, pr.J, pr.Delta, pr.h), [P.XField(N_SITES, pr.xfield)], [pr.drive],
+                            m_max=m_max, max_substeps=64, precision=prec)
+
+    ref = torch.from_numpy(psi0).cuda()
+    rp = chain("fx", 24)
+    rp.propagate(ref, 0.0, 0.0025, int(round(T / 0.0025)), order=8, tol=1e-13)
+    rp.close()
+
+    def run(prec, dt, tol, order=ORDER):
+        p = chain(prec)
+        x = torch.from_numpy(psi0).cuda()
+        p.propagate(x, 0.0, dt, 2, order=order, tol=tol)     # warm-up (graph, tables)
+        x = torch.from_numpy(psi0).cuda()
+        st, ms = _timed(torch, lambda: p.propagate(x, 0.0, dt, int(round(T / dt)), order=order, tol=tol))
+        p.close()
+        return torch.linalg.vector_norm(x - ref).item(), ms, st["n_applies"]
+
+    e_form, t_form, a_form = run("c64", DT, TOL)
+    rows = []
+    for dt in EE_DTS:
+        for tol in EE_TOLS:
+            e, ms, na = run("f64", dt, tol)
+            rows.append({"dt": dt, "tol": tol, "error": e, "ms": ms, "H_applies": na})
+    ok = [r for r in rows if r["error"] <= e_form]
+    best = min(ok, key=lambda r: r["ms"]) if ok else None
+    same = next(r for r in rows if r["dt"] == DT and r["tol"] == TOL)
+    out["complex64"] = {"workload": f"N={N_SITES} chain, CF6:5Opt, T={T}", "form": {"dt": DT, "tol": TOL,
+                        "error": e_form, "ms": t_form, "H_applies": a_form},
+                        "f64_at_equal_error": best, "speedup_at_equal_error": best["ms"] / t_form if best else None,
+                        "f64_same_setting": same, "speedup_same_setting": same["ms"] / t_form, "f64_grid": rows}
+    print(json.dumps({"part": "complex64", **out["complex64"]}), flush=True)
+    del ref
+
+    # ---------------- 2. complex64 batch
+    cfg = W.BATCH
+    insts = W.chain_batch(cfg["n"], cfg["n_lo"], cfg["n_hi"])
+    chains = [P.Chain(c.N, c.J, c.Delta, c.h, c.xfield, None, c.A, c.omega, 0.0) for c in insts]
+    host = [W.random_state(c.psi_seed, 1 << c.N) for c in insts]
+    Tb = args.ee_batch_T
+    refb = P.BatchPropagator(chains, m_max=24, precision="f64")
+    rdev = [torch.from_numpy(h).cuda() for h in host]
+    refb.propagate(rdev, 0.0, 0.0025, int(round(Tb / 0.0025)), order=8, tol=1e-13)
+    refb.close()
+    bp = P.BatchPropagator(chains, m_max=cfg["m_max"], precision="c64")
+    plan = bp.tune(0.0, cfg["dt"], order=cfg["order"], tol=cfg["tol"], nsteps=1)
+    dev = [torch.from_numpy(h).cuda() for h in host]
+    bp.propagate(dev, 0.0, cfg["dt"], 1, order=cfg["order"], tol=cfg["tol"])
+    dev = [torch.from_numpy(h).cuda() for h in host]
+    _, tb = _timed(torch, lambda: bp.propagate(dev, 0.0, cfg["dt"], int(round(Tb / cfg["dt"])), order=cfg["order"],
+                                               tol=cfg["tol"]))
+    errs = [torch.linalg.vector_norm(a - b).item() for a, b in zip(dev, rdev)]
+    e_b = max(errs)
+    bp.close()
+
+    def single(i, dt, tol):
+        c = insts[i]
+        p = P.Propagator(P.XXZChain(c.N, c.J, c.Delta, c.h), [P.XField(c.N, c.xfield)], [c.drive],
+                         m_max=cfg["m_max"], max_substeps=64, precision="f64")
+        x = torch.from_numpy(host[i]).cuda()
+        p.propagate(x, 0.0, dt, 1, order=cfg["order"], tol=tol)
+        x = torch.from_numpy(host[i]).cuda()
+        _, ms = _timed(torch, lambda: p.propagate(x, 0.0, dt, int(round(Tb / dt)), order=cfg["order"], tol=tol))
+        p.close()
+        return torch.linalg.vector_norm(x - rdev[i]).item(), ms
+
+    screen = []
+    for n in range(cfg["n_lo"], cfg["n_hi"] + 1):
+        screen += [i for i, c in enumerate(insts) if c.N == n][:2]
+    cand = []
+    for dt in EE_DTS:
+        if abs(Tb / dt - round(Tb / dt)) > 1e-9:
+            continue
+        for tol in EE_TOLS:
+            res = [single(i, dt, tol) for i in screen]
+            cand.append({"dt": dt, "tol": tol, "screen_max_error": max(e for e, _ in res),
+                         "screen_ms": sum(m for _, m in res)})
+    okb = sorted([c for c in cand if c["screen_max_error"] <= e_b], key=lambda c: c["screen_ms"])
+    chosen = None
+    for c in okb:       # verify on all instances, fastest screened setting first
+        res = [single(i, c["dt"], c["tol"]) for i in range(len(insts))]
+        full = {"dt": c["dt"], "tol": c["tol"], "max_error": max(e for e, _ in res),
+                "ms": sum(m for _, m in res)}
+        if full["max_error"] <= e_b:
+            chosen = full
+            break
+    out["complex64_batch"] = {"workload": f"{len(insts)} chains N={cfg['n_lo']}..{cfg['n_hi']}, CF6:5Opt, T={Tb}",
+                              "plan": plan, "form": {"dt": cfg["dt"], "tol": cfg["tol"], "max_error": e_b, "ms": tb},
+                              "f64_single_instance_at_equal_error": chosen,
+                              "speedup_at_equal_error": chosen["ms"] / tb if chosen else None, "screen": cand}
+    print(json.dumps({"part": "complex64_batch", **out["complex64_batch"]}), flush=True)
+    del rdev, dev
+
+    # ---------------- 3. adjoint gradient
+    N, nseg, Tg, dtg, omega = 18, 64, 16.0, 0.01, 2.0
+    nsteps = int(round(Tg / dtg))
+    prg = W.spin_chain(N)
+    p0 = torch.from_numpy(W.random_state(3, 1 << N)).cuda()
+    phi = torch.from_numpy(W.random_state(13, 1 << N)).cuda()
+    amps = W.uniform(7, nseg, -1.0, 1.0)
+    gp = P.Propagator(P.XXZChain(N, prg.J, prg.Delta, prg.h), [P.XField(N, np.ones(N))], [lambda t: 0.0], m_max=16,
+                      precision="f64")
+    gp.fidelity_grad(p0, phi, 0.0, dtg, 50, amps[:2], omega, tol=1e-10, checkpoint_every=25)
+    (_, g_ref, _), _ = _timed(torch, lambda: gp.fidelity_grad(p0, phi, 0.0, dtg, nsteps, amps, omega, tol=1e-13,
+                                                               checkpoint_every=25))
+    (_, g_adj, _), t_adj = _timed(torch, lambda: gp.fidelity_grad(p0, phi, 0.0, dtg, nsteps, amps, omega, tol=1e-10,
+                                                                   checkpoint_every=25))
+    gp.close()
+    gmax = float(np.max(np.abs(g_ref)))
+    e_adj = float(np.max(np.abs(g_adj - g_ref))) / gmax
+    cur = amps.copy()
+    sps = nsteps // nseg
+
+    def f(t):   # amplitude of the segment of the step containing t (read in place), times cos(omega t)
+        return cur[min(int(math.floor(t / dtg)) // sps, nseg - 1)] * math.cos(omega * t)
+    fp = P.Propagator(P.XXZChain(N, prg.J, prg.Delta, prg.h), [P.XField(N, np.ones(N))], [f], m_max=16,
+                      precision="f64")
+    x = torch.empty_like(p0)
+
+    def fid(am, tol, log=None, record=False):
+        cur[:] = am
+        x.copy_(p0)
+        r = fp.propagate(x, 0.0, dtg, nsteps, order=4, tol=tol, forced=log, record=record)
+        return abs(torch.vdot(phi, x).item()) ** 2, (r[1] if record else None)
+
+    sample = [0, 21, 42, 63]
+    fd_rows = []
+    for tol in (1e-10, 1e-12):
+        _, log = fid(amps, tol, record=True)
+        (_, _), t_prop = _timed(torch, lambda: fid(amps, tol, log))
+        for h in (1e-4, 1e-5, 1e-6):
+            errs = []
+            for k in sample:
+                ap, am_ = amps.copy(), amps.copy()
+                ap[k] += h
+                am_[k] -= h
+                fd = -(fid(ap, tol, log)[0] - fid(am_, tol, log)[0]) / (2 * h)
+                errs.append(abs(fd - g_ref[k]) / gmax)
+            fd_rows.append({"tol": tol, "h": h, "sample_max_rel_error": max(errs), "ms_per_propagation": t_prop,
+                            "gradient_ms": 2 * nseg * t_prop})
+    fp.close()
+    okg = [r for r in fd_rows if r["sample_max_rel_error"] <= e_adj]
+    bestg = min(okg, key=lambda r: r["gradient_ms"]) if okg else min(fd_rows, key=lambda r: r["sample_max_rel_error"])
+    out["adjoint"] = {"workload": "N=18 chain, 64 segments, T=16, CF4:2 dt=0.01, FP64",
+                      "form": {"tol": 1e-10, "max_rel_error": e_adj, "ms": t_adj},
+                      "central_differences_at_equal_error" if okg else "central_differences_best_reached": bestg,
+                      "speedup_at_equal_error": bestg["gradient_ms"] / t_adj if okg else None,
+                      "speedup_lower_bound": None if okg else bestg["gradient_ms"] / t_adj, "fd_grid": fd_rows}
+    print(json.dumps({"part": "adjoint", **out["adjoint"]}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--steps", type=int, default=20)
@@ -568,6 +765,8 @@ def main():
                     help="accuracy study: final-state error and throughput per (order, dt) over T")
     ap.add_argument("--sweep-T", type=float, default=20.0)
     ap.add_argument("--study", choices=sorted(STUDIES))
+    ap.add_argument("--ee-T", type=float, default=4.0, help="equal-error study: chain horizon")
+    ap.add_argument("--ee-batch-T", type=float, default=0.4, help="equal-error study: batch horizon")
     ap.add_argument("--grid-size", type=int, default=0, help="CTAs of the persistent kernel (0 = co-resident maximum)")
     ap.add_argument("--apply-form", default="auto", choices=["auto", "elementwise", "tiled"],
                     help="sizes study: XXZ-chain apply form of the fixed-point and complex64 kernels")
@@ -583,7 +782,7 @@ def main():
 
 STUDIES = {"atom": run_study_atom, "sizes": run_study_sizes, "batch": run_study_batch, "adjoint": run_study_adjoint,
            "expm": run_study_expm, "timestep": run_study_timestep, "pauli": run_study_pauli,
-           "reorth": run_study_reorth, "picture": run_study_picture}
+           "reorth": run_study_reorth, "picture": run_study_picture, "equal_error": run_study_equal_error}
 
 
 if __name__ == "__main__":
