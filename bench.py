@@ -614,7 +614,7 @@ def main():
                     help="stage exponentials: Krylov (default) or the Chebyshev expansion (fixed point only)")
     ap.add_argument("--grid-size", type=int, default=0,
                     help="CTAs of the persistent kernel (0 = co-resident maximum)")
-    ap.add_argument("--apply-form", default="auto", choices=["auto", "elementwise", "tiled", "staged"],
+    ap.add_argument("--apply-form", default="auto", choices=["auto", "elementwise", "tiled"],
                     help="XXZ-chain apply form of the fixed-point and complex64 kernels")
     ap.add_argument("--min-timed-ms", type=float, default=2000.0,
                     help="the K-step call is repeated until at least this much has been timed (median reported)")

@@ -234,14 +234,8 @@ enum { CFET_PREC_DEFAULT = 0, CFET_PREC_F64 = 1, CFET_PREC_FX = 2, CFET_PREC_C64
  *  ELEMENTWISE : every element gathers its neighbours from global memory.
  *  TILED       : window passes over shared-memory tiles; chains of 13..30
  *                sites (other sizes, operators and precisions keep the
- *                element-wise form).
- *  STAGED      : element-wise, with each CTA's contiguous chunk of the
- *                current Krylov vector also held in shared memory (written
- *                by the pass that produces the vector), so that neighbours
- *                inside the chunk are read from there; fixed point with
- *                Krylov stage exponentials, when the chunk fits (otherwise
- *                the element-wise form).  Any other value: CFET_EINVAL.     */
-enum { CFET_APPLY_AUTO = 0, CFET_APPLY_ELEMENTWISE = 1, CFET_APPLY_TILED = 2, CFET_APPLY_STAGED = 3 };
+ *                element-wise form).  Any other value: CFET_EINVAL.         */
+enum { CFET_APPLY_AUTO = 0, CFET_APPLY_ELEMENTWISE = 1, CFET_APPLY_TILED = 2 };
 
 /* How cfet_propagate evaluates each stage exponential exp(-i dt H_j) psi.
  *  KRYLOV    : the Lanczos/Krylov loop (Sec. 8.1) with the a-posteriori error

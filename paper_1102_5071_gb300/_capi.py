@@ -43,9 +43,8 @@ CFET_EXPM_KRYLOV, CFET_EXPM_CHEBYSHEV = 0, 1
 EXPM = {"krylov": CFET_EXPM_KRYLOV, "chebyshev": CFET_EXPM_CHEBYSHEV}
 CFET_PICTURE_SCHROEDINGER, CFET_PICTURE_INTERACTION = 0, 1
 PICTURES = {"schroedinger": CFET_PICTURE_SCHROEDINGER, "interaction": CFET_PICTURE_INTERACTION}
-CFET_APPLY_AUTO, CFET_APPLY_ELEMENTWISE, CFET_APPLY_TILED, CFET_APPLY_STAGED = 0, 1, 2, 3
-APPLY_FORMS = {"auto": CFET_APPLY_AUTO, "elementwise": CFET_APPLY_ELEMENTWISE, "tiled": CFET_APPLY_TILED,
-               "staged": CFET_APPLY_STAGED}
+CFET_APPLY_AUTO, CFET_APPLY_ELEMENTWISE, CFET_APPLY_TILED = 0, 1, 2
+APPLY_FORMS = {"auto": CFET_APPLY_AUTO, "elementwise": CFET_APPLY_ELEMENTWISE, "tiled": CFET_APPLY_TILED}
 
 
 class cfet_stats(C.Structure):

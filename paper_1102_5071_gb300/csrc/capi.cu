@@ -72,7 +72,6 @@ struct cfet_ctx {
   float* d_val32 = nullptr;
   float2* d_qbasis32 = nullptr;
   bool tiled = false;          // window-tiled apply (long chains, complex64 and fixed point)
-  bool staged = false;         // fixed-point chains: shared-memory copy of each CTA's chunk
   // Pauli-sum family (FP64): strings grouped by X mask
   OpPauli pauli{};
   void* d_pauli = nullptr;     // one allocation: gx | gstart | tz | top | tc | tim
@@ -314,7 +313,6 @@ PropParams base_params(cfet_ctx* ctx, double2* psi, double tau, double tol) {
   p.qbasis = ctx->d_qbasis;
   p.qbasis32 = ctx->d_qbasis32;
   p.tiled = ctx->tiled ? 1 : 0;
-  p.staged = ctx->staged ? 1 : 0;
   p.reorth = ctx->opt.reorth;
   return p;
 }
@@ -734,10 +732,8 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
   if (o.reorth != 0 && o.reorth != 1) return fail(nullptr, CFET_EINVAL, "reorth must be 0 or 1");
   if (o.reorth && (o.precision != CFET_PREC_F64 || o.expm != CFET_EXPM_KRYLOV))
     return fail(nullptr, CFET_EINVAL, "reorth requires CFET_PREC_F64 and CFET_EXPM_KRYLOV");
-  if (o.apply_form != CFET_APPLY_AUTO && o.apply_form != CFET_APPLY_ELEMENTWISE && o.apply_form != CFET_APPLY_TILED &&
-      o.apply_form != CFET_APPLY_STAGED)
-    return fail(nullptr, CFET_EINVAL,
-                "apply_form must be CFET_APPLY_AUTO, CFET_APPLY_ELEMENTWISE, CFET_APPLY_TILED or CFET_APPLY_STAGED");
+  if (o.apply_form != CFET_APPLY_AUTO && o.apply_form != CFET_APPLY_ELEMENTWISE && o.apply_form != CFET_APPLY_TILED)
+    return fail(nullptr, CFET_EINVAL, "apply_form must be CFET_APPLY_AUTO, CFET_APPLY_ELEMENTWISE or CFET_APPLY_TILED");
   if (o.block_size == 0) o.block_size = (o.precision == CFET_PREC_F64) ? 256 : 384;
   {
     // FP64 kernel: block_size threads (<= 256); fixed-point and mixed-precision
@@ -1147,14 +1143,6 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
   ctx->grid = want < maxg ? want : maxg;
   if (ctl_warp && ctx->grid > kMaxCtlGrid) ctx->grid = kMaxCtlGrid;  // record exchange limit
   if (ctx->grid < 1) ctx->grid = 1;
-  // staged apply (fixed-point chains, element-wise form): when each CTA's
-  // chunk fits in shared memory next to the kernel's scalars
-  if (family == kFamilySpin && ctx->precision == CFET_PREC_FX && !ctx->tiled && o.expm == CFET_EXPM_KRYLOV &&
-      o.apply_form == CFET_APPLY_STAGED) {
-    const size_t smem = fx_staged_smem_bytes(dim, ctx->grid);
-    const int ms = max_coresident_blocks_fx_staged(ctx->block, smem);
-    ctx->staged = ms >= ctx->grid;
-  }
 
   if (ctx->precision == CFET_PREC_FX)  // basis q_1..q_{m_max+1}; the Chebyshev kernel's three vectors
     CKC(cudaMalloc(&ctx->d_qbasis, (size_t)std::max(o.m_max + 1, 3) * dim * sizeof(longlong2)),

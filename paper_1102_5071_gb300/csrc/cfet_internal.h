@@ -183,7 +183,7 @@ struct PropParams {
   int m_min, m_max, max_substeps;
   int tiled;             // spin chains: window-tiled apply (complex64 and fixed-point kernels)
   int reorth;            // FP64 kernel: full re-orthogonalisation of every Lanczos vector
-  int staged;            // spin chains, fixed point: shared-memory copy of each CTA's chunk for the apply
+  int pad1;
   // decisions (device arrays, nullable)
   const int* f_nsub; const int* f_k; const int* f_h;
   int* r_nsub; int* r_k; int* r_h; long long r_cap;
@@ -283,8 +283,6 @@ int launch_propagate_spin_fx(const PropParams& p, const OpSpinFx& op, int grid, 
 int launch_propagate_dia_fx(const PropParams& p, const OpDiaFx& op, int grid, int block, void* stream);
 int launch_propagate_csr_fx(const PropParams& p, const OpCsrFx& op, int grid, int block, void* stream);
 int max_coresident_blocks_fx(int family, int block, bool tiled);
-size_t fx_staged_smem_bytes(int dim, int grid);
-int max_coresident_blocks_fx_staged(int block, size_t smem);
 int launch_propagate_spin_c64(const PropParams& p, const OpSpinC& op, int grid, int block, void* stream);
 int launch_propagate_dia_c64(const PropParams& p, const OpDiaC& op, int grid, int block, void* stream);
 int launch_propagate_csr_c64(const PropParams& p, const OpCsrC& op, int grid, int block, void* stream);

@@ -103,6 +103,11 @@ static __device__ bool ctl_exchange(unsigned long long* rec, const unsigned (&mi
   constexpr bool kWordMajor = W > 8;
   const int lane = threadIdx.x & 31;
   const int G = gridDim.x;
+  if (G == 1) {  // a single CTA: its own record is the total; nothing to publish or wait for
+    acc.reset();
+    acc.add(mine);
+    return true;
+  }
   const long long c0 = sm_clock();
   if (lane == 0) {
     if (fence) __threadfence();

@@ -264,112 +264,6 @@ __device__ __forceinline__ void fx_apply_spin2(const longlong2* q, const longlon
   r2 = make_longlong2(ur2, ui2);
 }
 
-// Staged form of fx_apply_spin2: the CTA's own chunk [c0, c0 + clen) of q is
-// also held in shared memory (sq, written by the pass that produced q), so
-// neighbours inside the chunk are read from there and only the others from
-// global memory.  A flip of bit i or a hop of bond (i, i + 1) moves the index
-// by exactly 2^i, so for 2^i >= clen the neighbour is always outside: those
-// bits (i >= nb) skip the test.  Same arithmetic as fx_apply_spin2.
-__device__ __forceinline__ longlong2 fx_ld_near(const longlong2* q, const longlong2* sq, int y, int c0,
-                                                unsigned clen) {
-  const unsigned o = (unsigned)(y - c0);
-  return o < clen ? sq[o] : q[y];
-}
-
-__device__ __forceinline__ void fx_apply_spin2_staged(const longlong2* q, const longlong2* sq, const longlong2* qm,
-                                                      int x, int x2, int c0, unsigned clen, int nb,
-                                                      const OpSpinFx& op, const FxConstA& c, const long long* mb,
-                                                      longlong2& r1, longlong2& r2) {
-  const int N = op.N, L = op.lo_bits;
-  const long long dz1 = __ldg(op.DZ_lo + (x & ((1 << L) - 1))) + __ldg(op.DZ_hi + (x >> (L - 1)));
-  const long long dz2 = __ldg(op.DZ_lo + (x2 & ((1 << L) - 1))) + __ldg(op.DZ_hi + (x2 >> (L - 1)));
-  const long long Dp1 = fx_mulhi(c.m_cz, dz1 << 1) << 3;
-  const long long Dp2 = fx_mulhi(c.m_cz, dz2 << 1) << 3;
-  const longlong2 v1 = sq[x - c0], v2 = sq[x2 - c0];
-  long long ur1 = fx_mulhi(Dp1, v1.x << c.pk), ui1 = fx_mulhi(Dp1, v1.y << c.pk);
-  long long ur2 = fx_mulhi(Dp2, v2.x << c.pk), ui2 = fx_mulhi(Dp2, v2.y << c.pk);
-  long long hr1 = 0, hi1 = 0, hr2 = 0, hi2 = 0;
-  const unsigned mask = (1u << (N - 1)) - 1u;
-  const unsigned anti1 = ((unsigned)x ^ ((unsigned)x >> 1)) & mask;
-  const unsigned anti2 = ((unsigned)x2 ^ ((unsigned)x2 >> 1)) & mask;
-  const int nh = nb < N - 1 ? nb : N - 1;
-#pragma unroll 4
-  for (int i = 0; i < nh; ++i) {
-    if ((anti1 >> i) & 1u) {
-      const longlong2 w = fx_ld_near(q, sq, x ^ (3 << i), c0, clen);
-      hr1 += w.x;
-      hi1 += w.y;
-    }
-    if ((anti2 >> i) & 1u) {
-      const longlong2 w = fx_ld_near(q, sq, x2 ^ (3 << i), c0, clen);
-      hr2 += w.x;
-      hi2 += w.y;
-    }
-  }
-#pragma unroll 4
-  for (int i = nh; i < N - 1; ++i) {
-    if ((anti1 >> i) & 1u) {
-      const longlong2 w = q[x ^ (3 << i)];
-      hr1 += w.x;
-      hi1 += w.y;
-    }
-    if ((anti2 >> i) & 1u) {
-      const longlong2 w = q[x2 ^ (3 << i)];
-      hr2 += w.x;
-      hi2 += w.y;
-    }
-  }
-  ur1 += fx_mulhi(c.m_hop, hr1 << c.ph);
-  ui1 += fx_mulhi(c.m_hop, hi1 << c.ph);
-  ur2 += fx_mulhi(c.m_hop, hr2 << c.ph);
-  ui2 += fx_mulhi(c.m_hop, hi2 << c.ph);
-  const int nf = nb < N ? nb : N;
-  if (op.uniform) {
-    long long xr1 = 0, xi1 = 0, xr2 = 0, xi2 = 0;
-#pragma unroll 4
-    for (int i = 0; i < nf; ++i) {
-      const longlong2 w1 = fx_ld_near(q, sq, x ^ (1 << i), c0, clen);
-      const longlong2 w2 = fx_ld_near(q, sq, x2 ^ (1 << i), c0, clen);
-      xr1 += w1.x;
-      xi1 += w1.y;
-      xr2 += w2.x;
-      xi2 += w2.y;
-    }
-#pragma unroll 4
-    for (int i = nf; i < N; ++i) {
-      const longlong2 w1 = q[x ^ (1 << i)];
-      const longlong2 w2 = q[x2 ^ (1 << i)];
-      xr1 += w1.x;
-      xi1 += w1.y;
-      xr2 += w2.x;
-      xi2 += w2.y;
-    }
-    ur1 += fx_mulhi(c.m_x, xr1 << c.px);
-    ui1 += fx_mulhi(c.m_x, xi1 << c.px);
-    ur2 += fx_mulhi(c.m_x, xr2 << c.px);
-    ui2 += fx_mulhi(c.m_x, xi2 << c.px);
-  } else {
-#pragma unroll 4
-    for (int i = 0; i < N; ++i) {
-      const longlong2 w1 = i < nf ? fx_ld_near(q, sq, x ^ (1 << i), c0, clen) : q[x ^ (1 << i)];
-      const longlong2 w2 = i < nf ? fx_ld_near(q, sq, x2 ^ (1 << i), c0, clen) : q[x2 ^ (1 << i)];
-      ur1 += fx_mulhi(mb[i], w1.x << c.pk);
-      ui1 += fx_mulhi(mb[i], w1.y << c.pk);
-      ur2 += fx_mulhi(mb[i], w2.x << c.pk);
-      ui2 += fx_mulhi(mb[i], w2.y << c.pk);
-    }
-  }
-  if (c.use_prev) {
-    const longlong2 w1 = qm[x], w2 = qm[x2];
-    ur1 += fx_mulhi(c.m_p, w1.x << c.pp);
-    ui1 += fx_mulhi(c.m_p, w1.y << c.pp);
-    ur2 += fx_mulhi(c.m_p, w2.x << c.pp);
-    ui2 += fx_mulhi(c.m_p, w2.y << c.pp);
-  }
-  r1 = make_longlong2(ur1, ui1);
-  r2 = make_longlong2(ur2, ui2);
-}
-
 __device__ __forceinline__ longlong2 fx_apply_dia(const longlong2* q, const longlong2* qm, int r, int dim,
                                                   const OpDiaFx& op, const FxConstA& c) {
   long long ur = 0, ui = 0;

@@ -379,7 +379,7 @@ __device__ double fx_estimate(SmemFx& S, int k, double ts) {
 // ------------------------------------------------------------------ the kernel
 // TILED: the window-tiled apply of long spin chains (a separate instantiation,
 // so that the element-wise kernel carries none of its code).
-template <int FAMILY, class Op, bool TILED = false, bool STAGED = false>
+template <int FAMILY, class Op, bool TILED = false>
 __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropParams p, Op op) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmemFx& S = *reinterpret_cast<SmemFx*>(smem_raw);
@@ -413,17 +413,6 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
     nwin = tiled_windows<kFxTileBits>(op.N, win);
   }
   longlong2* tbuf = reinterpret_cast<longlong2*>(smem_raw + ((sizeof(SmemFx) + 127) & ~size_t(127)));
-  // staged apply: this CTA's chunk [c0, c0 + clen) of the vector the next
-  // apply reads, written to shared memory by the pass that produces it (the
-  // conversion of psi, the orthogonalisation, the reconstruction); flips of
-  // bits i < nb may land inside the chunk
-  longlong2* sq = tbuf;
-  const int c0 = blockIdx.x * chunk;
-  const unsigned clen = (unsigned)max(0, min(dim, c0 + chunk) - c0);
-  int nb = 0;
-  if constexpr (STAGED) {
-    while (nb < 31 && (1u << nb) < clen) ++nb;
-  }
   int wslot = 0;
   DevStatus* st = p.st;
   const bool glead = (blockIdx.x == 0) && lead;
@@ -483,7 +472,6 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
         const double2 v = p.psi[x];
         const longlong2 qv = make_longlong2(__double2ll_rn(v.x * sc), __double2ll_rn(v.y * sc));
         Q(1)[x] = qv;
-        if constexpr (STAGED) sq[x - c0] = qv;
         a2 += (__int128)qv.x * qv.x + (__int128)qv.y * qv.y;
         mx = max(mx, fx_absmax(qv.x, qv.y));
       }
@@ -594,13 +582,10 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
             if constexpr (FAMILY == kFamilySpin) {
               for (; x + wstep < wxe; x += 2 * wstep) {
                 longlong2 h1, h2;
-                if constexpr (STAGED)
-                  fx_apply_spin2_staged(q, sq, qm, x, x + wstep, c0, clen, nb, op, c, S.mb, h1, h2);
-                else
-                  fx_apply_spin2(q, qm, x, x + wstep, op, c, S.mb, h1, h2);
+                fx_apply_spin2(q, qm, x, x + wstep, op, c, S.mb, h1, h2);
                 u[x] = h1;
                 u[x + wstep] = h2;
-                const longlong2 v1 = STAGED ? sq[x - c0] : q[x], v2 = STAGED ? sq[x + wstep - c0] : q[x + wstep];
+                const longlong2 v1 = q[x], v2 = q[x + wstep];
                 a2 += (__int128)v1.x * h1.x + (__int128)v1.y * h1.y;
                 a2 += (__int128)v2.x * h2.x + (__int128)v2.y * h2.y;
                 mx = max(mx, max(fx_absmax(h1.x, h1.y), fx_absmax(h2.x, h2.y)));
@@ -698,12 +683,11 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
             long long mx = 0;
             const long long tw0 = sm_clock();
             for (int x = wx0; x < wxe; x += wstep) {
-              const longlong2 v = STAGED ? sq[x - c0] : q[x];
+              const longlong2 v = q[x];
               const longlong2 uu = u[x];
               const long long wr = fx_rshr(uu.x, sh_u) + fx_mulhi(m_a, v.x << pk);
               const long long wi = fx_rshr(uu.y, sh_u) + fx_mulhi(m_a, v.y << pk);
               u[x] = make_longlong2(wr, wi);
-              if constexpr (STAGED) sq[x - c0] = make_longlong2(wr, wi);
               b2 += (__int128)wr * wr + (__int128)wi * wi;
               mx = max(mx, fx_absmax(wr, wi));
             }
@@ -856,7 +840,6 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
               im += p3 - p1 - p2;
             }
             Q(1)[x] = make_longlong2(re, im);
-            if constexpr (STAGED) sq[x - c0] = make_longlong2(re, im);
             if (final_rec) p.psi[x] = make_double2(__ll2double_rn(re) * outscale, __ll2double_rn(im) * outscale);
             a2 += (__int128)re * re + (__int128)im * im;
             mx = max(mx, fx_absmax(re, im));
@@ -929,7 +912,7 @@ static int launch_prop_fx(const PropParams& p, const Op& op, int grid, int block
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = p.tiled ? fx_tiled_smem_bytes() : p.staged ? fx_staged_smem_bytes(p.dim, grid) : sizeof(SmemFx);
+  cfg.dynamicSmemBytes = p.tiled ? fx_tiled_smem_bytes() : sizeof(SmemFx);
   cfg.stream = (cudaStream_t)stream;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeCooperative;
@@ -938,7 +921,6 @@ static int launch_prop_fx(const PropParams& p, const Op& op, int grid, int block
   cfg.numAttrs = 1;
   if constexpr (FAMILY == kFamilySpin) {
     if (p.tiled) return (int)cudaLaunchKernelEx(&cfg, k_propagate_fx<FAMILY, Op, true>, p, op);
-    if (p.staged) return (int)cudaLaunchKernelEx(&cfg, k_propagate_fx<FAMILY, Op, false, true>, p, op);
   }
   return (int)cudaLaunchKernelEx(&cfg, k_propagate_fx<FAMILY, Op>, p, op);
 }
@@ -954,28 +936,6 @@ int launch_propagate_csr_fx(const PropParams& p, const OpCsrFx& op, int grid, in
 }
 
 size_t fx_tiled_smem_bytes() { return ((sizeof(SmemFx) + 127) & ~size_t(127)) + 4 * kFxTileElems * sizeof(longlong2); }
-
-size_t fx_staged_smem_bytes(int dim, int grid) {
-  const size_t chunk = ((size_t)dim + grid - 1) / grid;
-  return ((sizeof(SmemFx) + 127) & ~size_t(127)) + chunk * sizeof(longlong2);
-}
-
-// Co-resident CTAs of the staged spin kernel with its shared-memory chunk
-// (0 when it does not fit); sets the kernel's dynamic shared-memory limit.
-int max_coresident_blocks_fx_staged(int block, size_t smem) {
-  int dev = 0, nsm = 0, per = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (smem > (size_t)optin) return 0;
-  if (cudaFuncSetAttribute(k_propagate_fx<kFamilySpin, OpSpinFx, false, true>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return -1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_propagate_fx<kFamilySpin, OpSpinFx, false, true>, block,
-                                                    smem) != cudaSuccess)
-    return -1;
-  return per * nsm;
-}
 
 int max_coresident_blocks_fx(int family, int block, bool tiled) {
   int dev = 0, nsm = 0, per = 0;
