@@ -54,6 +54,7 @@ struct SmemAdj {
   double bsite[2][kMaxSites];
   double beta0[2];
   int k[2], active[2];
+  int nq;   // Gauss-Legendre nodes of this stage integral (0: beyond the largest rule)
   int ok;
 };
 
@@ -254,6 +255,25 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(AdjParams p, OpSpin op)
       return;
     }
     const int kp = S.k[0], kl = S.k[1];
+    // Rule of the stage integral: the integrand is a sum of e^{i om' r} with
+    // |om'| <= om = |tau| (width_psi + width_lambda); the n-node rule on [0, 1]
+    // integrates e^{i om r} to 1e-14 for om up to 1.25 (6), 10 (12), 39.5 (24)
+    // and 114 (48 nodes).  Beyond that the sweep gives up (CFET_EKRYLOV);
+    // every CTA takes the same decision (identical scalars).
+    if (tid < 32) {
+      int nq = 6;
+      if (kp > 0 && kl > 0) {
+        const double om = fabs(tau) * (gersh_width(kp, S.alpha[0] + 1, S.beta[0] + 1) +
+                                       gersh_width(kl, S.alpha[1] + 1, S.beta[1] + 1));
+        nq = om <= 1.25 ? 6 : (om <= 10.0 ? 12 : (om <= 39.5 ? 24 : (om <= 114.0 ? 48 : 0)));
+      }
+      if (lane == 0) S.nq = nq;
+    }
+    __syncthreads();
+    if (S.nq == 0) {
+      if (lead) atomicCAS(&p.st->status, 0, (int)CFET_EKRYLOV);
+      return;
+    }
     // ---- W[i][j] = <v_lambda_i | V | v_psi_j> (normalised vectors), V = sum_i a_i X_i
     for (int j = 1; j <= kp; ++j) {
       for (int i = 0; i < 2 * kl; ++i) v[i] = 0.0;
@@ -282,11 +302,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(AdjParams p, OpSpin op)
     }
     // ---- stage integral (warp 0) and gradient accumulation
     if (tid < 32 && kp > 0 && kl > 0) {
-      const double om = fabs(tau) * (gersh_width(kp, S.alpha[0] + 1, S.beta[0] + 1) +
-                                     gersh_width(kl, S.alpha[1] + 1, S.beta[1] + 1));
-      int q0 = p.nq6, nq = 6;
-      if (om > 2.0) { q0 = p.nq12; nq = 12; }
-      if (om > 8.0) { q0 = p.nq24; nq = 24; }
+      const int nq = S.nq;
+      const int q0 = nq == 6 ? p.nq6 : (nq == 12 ? p.nq12 : (nq == 24 ? p.nq24 : p.nq48));
       double Ir = 0.0, Ii = 0.0;
       for (int q = 0; q < nq; ++q) {
         const double r = p.glx[q0 + q], wq = p.glw[q0 + q];

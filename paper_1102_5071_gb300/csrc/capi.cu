@@ -1634,7 +1634,7 @@ cfet_status cfet_fidelity_grad(cfet_ctx* ctx, const void* psi0, const void* phi,
     CK(cudaMalloc(&ctx->d_adj_part, 2 * (2 * kAdjMaxK + 2) * (size_t)ctx->adj_grid * sizeof(double)),
        "cudaMalloc(adjoint partials)");
   }
-  const int nql = 6 + 12 + 24;
+  const int nql = 6 + 12 + 24 + 48;
   if ((size_t)(3 * nexp + 2 * nql) > ctx->adj_tab_n) {
     cudaFree(ctx->d_adj_tab);
     cudaFree(ctx->d_adj_seg);
@@ -1682,6 +1682,7 @@ cfet_status cfet_fidelity_grad(cfet_ctx* ctx, const void* psi0, const void* phi,
   gauss_legendre_01(6, glx, glw);
   gauss_legendre_01(12, glx + 6, glw + 6);
   gauss_legendre_01(24, glx + 18, glw + 18);
+  gauss_legendre_01(48, glx + 42, glw + 42);
   CK(cudaMemcpyAsync(ctx->d_adj_tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, st),
      "adjoint table upload");
   CK(cudaMemcpyAsync(ctx->d_adj_seg, segv.data(), segv.size() * sizeof(int), cudaMemcpyHostToDevice, st),
@@ -1751,6 +1752,7 @@ cfet_status cfet_fidelity_grad(cfet_ctx* ctx, const void* psi0, const void* phi,
     p.nq6 = 0;
     p.nq12 = 6;
     p.nq24 = 18;
+    p.nq48 = 42;
     p.glx = ctx->d_adj_tab + 3 * nexp;
     p.glw = p.glx + nql;
     p.grad = ctx->d_adj_acc;

@@ -228,7 +228,7 @@ int cheb_threads(int workers);  // threads per CTA of the Chebyshev kernel for `
 
 // Backward (adjoint) sweep of the fidelity gradient (see adjoint.cu).
 constexpr int kAdjMaxK = 16;     // Krylov dimension limit of the adjoint sweep
-constexpr int kAdjMaxNodes = 24; // Gauss-Legendre nodes of the stage integral
+constexpr int kAdjMaxNodes = 48; // Gauss-Legendre nodes of the stage integral
 
 struct AdjParams {
   int dim;
@@ -246,7 +246,7 @@ struct AdjParams {
   const double* gam;       //   d c1 / d amplitude
   const int* seg;          //   amplitude segment
   long long e_lo, e_hi;    // exponentials e_hi - 1 down to e_lo are undone
-  int nq6, nq12, nq24;     // offsets of the 6-, 12-, 24-node rules in glx / glw
+  int nq6, nq12, nq24, nq48;  // offsets of the 6-, 12-, 24-, 48-node rules in glx / glw
   int pad1;
   const double* glx;       // Gauss-Legendre nodes on [0, 1]
   const double* glw;

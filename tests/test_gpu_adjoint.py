@@ -64,6 +64,42 @@ def test_gradient_matches_oracle_small(torch_cuda, prec, order, ce):
     assert st["max_drift"] <= 1e-10 and st["n_applies_backward"] > 0
 
 
+@pytest.mark.parametrize("dt", [0.6, 2.0])
+def test_gradient_with_long_stages_matches_oracle(torch_cuda, dt):
+    # long stage exponentials make the stage integral oscillate fast:
+    # om = |tau| (width_psi + width_lambda) selects the 24-node (dt 0.6) and
+    # the 48-node rule (dt 2.0); the gradient still matches the oracle's exact
+    # one (dense exponentials and Frechet derivatives)
+    torch = torch_cuda
+    N, nseg, nsteps, omega, phase = 4, 2, 4, 2.0, 0.3
+    a = W.uniform(41, N, 0.3, 1.2)
+    prop, pr = _prop(N, "f64", a=a)
+    psi0, phi = W.random_state(1, 1 << N), W.random_state(11, 1 << N)
+    amps = W.uniform(5, nseg, -1.0, 1.0)
+    H0 = O.xxz_dense(N, pr.J, pr.Delta, pr.h)
+    V = O.xfield_dense(N, a)
+    L_ref, g_ref = OA.grad_dense(H0, V, psi0, phi, amps, omega, phase, 0.0, dt, nsteps, 4)
+    L, g, st = prop.fidelity_grad(torch.from_numpy(psi0).cuda(), torch.from_numpy(phi).cuda(), 0.0, dt, nsteps,
+                                  amps, omega, phase, order=4, tol=1e-13, checkpoint_every=1)
+    assert abs(L - L_ref) <= 1e-11, (L, L_ref)
+    assert np.max(np.abs(g - g_ref)) <= 1e-9, (g, g_ref)
+
+
+def test_gradient_beyond_the_largest_rule_reports_ekrylov(torch_cuda):
+    # fixed Krylov dimension (tol <= 0) with a very long step: the stage
+    # integral would need more than 48 nodes, the sweep gives up
+    torch = torch_cuda
+    import paper_1102_5071_gb300 as P
+    N = 4
+    prop, pr = _prop(N, "f64")
+    x = torch.from_numpy(W.random_state(1, 1 << N)).cuda()
+    y = torch.from_numpy(W.random_state(11, 1 << N)).cuda()
+    with pytest.raises(P.CfetError, match="EKRYLOV"):
+        prop.fidelity_grad(x, y, 0.0, 20.0, 2, [0.5, -0.4], 2.0, order=4, tol=0.0)
+    L, g, st = prop.fidelity_grad(x, y, 0.0, 0.1, 2, [0.5, -0.4], 2.0, order=4, tol=1e-12)   # still usable
+    assert np.all(np.isfinite(g))
+
+
 def test_checkpoint_spacing_does_not_change_the_gradient(torch_cuda):
     torch = torch_cuda
     N, nseg, nsteps, dt = 10, 5, 40, 0.02

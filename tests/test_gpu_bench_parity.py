@@ -18,9 +18,9 @@
   perturbation moves one full step by 9e-5.)
 
 Tolerances: ||psi_gpu - psi_oracle||_2 <= 1e-10 for the fixed-point and FP64
-formats; the complex64 format within its rounding budget (each of at most k
-combined vectors after at most four FP32 roundings, sum |y_i| <= sqrt(k)):
-n_substeps * 4 k * 2^-24.
+formats; the complex64 format within its rounding budget (k combined vectors,
+each after at most four FP32 roundings, weights with sum |y_i| <= sqrt(k), one
+more rounding of the result): n_substeps * (4 sqrt(k) + 1) * 2^-24.
 """
 
 import numpy as np
@@ -36,7 +36,7 @@ ULP32 = 2.0 ** -24
 
 
 def c64_budget(n_substeps, k):
-    return n_substeps * 4 * k * ULP32
+    return n_substeps * (4.0 * np.sqrt(k) + 1.0) * ULP32
 
 
 @pytest.fixture(scope="module")

@@ -4,13 +4,17 @@ oracle.
 
 Tolerance.  The method is the oracle's; only the storage and arithmetic of
 the vectors change.  Per Krylov substep the result is a combination
-beta0 sum_i y_i s_i q_i of at most 16 stored vectors, each produced by at most
-four FP32 roundings (store of psi, apply sum, recurrence, store), with
-sum_i |y_i| <= sqrt(k) <= 4, which bounds the substep's relative error by
-16 * 4 ulps of FP32 = 64 * 2^-24.  Unitary propagation does not amplify
-earlier errors, so they add at most linearly over substeps:
+beta0 sum_i y_i s_i q_i of k stored vectors (k <= m_max), each produced by at
+most four FP32 roundings of relative size 2^-24 (store of psi, apply sum,
+recurrence, store), weighted by y = exp(-i tau T_k) e_1 with ||y||_2 = 1, so
+sum_i |y_i| <= sqrt(k); the combined result is rounded once more.  This
+bounds the substep's relative error by (4 sqrt(k) + 1) 2^-24 (17 * 2^-24 for
+k <= 16).  Unitary propagation does not amplify earlier errors, so they add at
+most linearly over substeps:
 
-    ||psi_c64 - psi_oracle||_2 <= n_substeps * 64 * 2^-24 * ||psi0||.
+    ||psi_c64 - psi_oracle||_2 <= n_substeps * (4 sqrt(m_max) + 1) * 2^-24 * ||psi0||.
+
+(Measured errors are about 1.4 * 2^-24 per substep on the N = 20 chain.)
 
 The oracle's Krylov decisions are replayed (forced mode) so that only
 rounding is measured; adaptive runs must take the same decisions in at least
@@ -33,8 +37,8 @@ ULP32 = 2.0 ** -24
 FORMS = {"0": "elementwise", "1": "tiled"}
 
 
-def budget(n_substeps):
-    return n_substeps * 64 * ULP32
+def budget(n_substeps, k=16):
+    return n_substeps * (4.0 * math.sqrt(k) + 1.0) * ULP32
 
 
 @pytest.fixture(scope="module")
@@ -89,7 +93,7 @@ def test_c64_schemes(torch_cuda, scheme):
     prop, op, drives = _spin(9, nfields=2, m_max=20, max_substeps=200)
     err, same, st, _ = _run(torch_cuda, prop, op, drives, W.random_state(5, 1 << 9), 0.37, 0.05, 6, scheme,
                             1e-9, 20)
-    assert err <= budget(st["n_substeps"]), err
+    assert err <= budget(st["n_substeps"], 20), err
     assert same >= 0.95, same
 
 
@@ -97,7 +101,7 @@ def test_c64_substeps(torch_cuda):
     prop, op, drives = _spin(10, m_max=8, max_substeps=400)
     err, same, st, _ = _run(torch_cuda, prop, op, drives, W.random_state(6, 1 << 10), 0.0, 0.6, 3, 6, 1e-8, 8)
     assert st["n_substeps"] > st["n_exp"]
-    assert err <= budget(st["n_substeps"]), err
+    assert err <= budget(st["n_substeps"], 8), err
 
 
 def test_c64_fixed_krylov_dimension(torch_cuda):
@@ -107,7 +111,7 @@ def test_c64_fixed_krylov_dimension(torch_cuda):
     t = _dev(torch_cuda, psi0)
     st = prop.propagate(t, 0.0, 0.02, 15, order=6, tol=0.0)
     assert st["n_applies"] == 15 * 5 * 10
-    assert np.linalg.norm(t.cpu().numpy() - ref) <= budget(st["n_substeps"])
+    assert np.linalg.norm(t.cpu().numpy() - ref) <= budget(st["n_substeps"], 10)
 
 
 def test_c64_chain_n20_one_step(torch_cuda):
@@ -116,7 +120,7 @@ def test_c64_chain_n20_one_step(torch_cuda):
     ref = OC.propagate(op, psi0, 0.0, 0.05, 1, 4, drives, 0.0, 10)
     t = _dev(torch_cuda, psi0)
     st = prop.propagate(t, 0.0, 0.05, 1, order=4, tol=0.0)
-    assert np.linalg.norm(t.cpu().numpy() - ref) <= budget(st["n_substeps"])
+    assert np.linalg.norm(t.cpu().numpy() - ref) <= budget(st["n_substeps"], 10)
 
 
 def test_c64_chain_n20_zero_coupling_factorises(torch_cuda):
@@ -157,7 +161,7 @@ def test_c64_time_independent_matches_expm(torch_cuda):
     st = prop.propagate(t, 0.0, 0.1, 5, order=8, tol=1e-9)
     ref = expm(-1j * 0.5 * O.xxz_dense(N, pr.J, pr.Delta, pr.h)) @ psi0
     # Krylov tolerance 1e-9 per substep plus the rounding budget
-    assert np.linalg.norm(t.cpu().numpy() - ref) <= budget(st["n_substeps"]) + st["n_substeps"] * 1e-9
+    assert np.linalg.norm(t.cpu().numpy() - ref) <= budget(st["n_substeps"], 30) + st["n_substeps"] * 1e-9
 
 
 def test_c64_atom_reduced(torch_cuda):
@@ -168,7 +172,7 @@ def test_c64_atom_reduced(torch_cuda):
     op = O.Banded((p.H0_offsets, p.H0_values), [(p.V_offsets, p.V_values)])
     psi0, _ = W.atom_ground_state(p)
     err, same, st, _ = _run(torch_cuda, prop, op, [p.drive], psi0, 300.0, 0.1, 2, 8, 1e-9, 32)
-    assert err <= budget(st["n_substeps"]), (err, st["n_substeps"])
+    assert err <= budget(st["n_substeps"], 32), (err, st["n_substeps"])
 
 
 def test_c64_edge_cases(torch_cuda):
@@ -278,7 +282,7 @@ def test_c64_tiled_one_magnon_sector_is_exact(torch_cuda, N):
     e[k0] = 1.0
     ref = expm(-1j * T * _one_magnon_hamiltonian(N, J, Dl, h)) @ e
     sector = np.array([1 << k for k in range(N)])
-    bound = budget(st["n_substeps"]) + st["n_substeps"] * 1e-9
+    bound = budget(st["n_substeps"], 24) + st["n_substeps"] * 1e-9
     assert np.linalg.norm(out[sector] - ref) <= bound, (np.linalg.norm(out[sector] - ref), bound)
     rest = out.copy()
     rest[sector] = 0.0
