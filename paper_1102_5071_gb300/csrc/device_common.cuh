@@ -104,8 +104,8 @@ static __device__ bool ctl_exchange(unsigned long long* rec, const unsigned (&mi
   const int lane = threadIdx.x & 31;
   const int G = gridDim.x;
   if (G == 1) {  // a single CTA: its own record is the total; nothing to publish or wait for
-    acc.reset();
-    acc.add(mine);
+    acc.reset();  // (as below: lane 0 holds record 0, the caller combines the lanes)
+    if (lane == 0) acc.add(mine);
     return true;
   }
   const long long c0 = sm_clock();
@@ -481,6 +481,65 @@ static __device__ void small_expm_e1(int k, const double* a, const double* b, do
   if (on0) { yr[r0] = ar0 * cs + ai0 * sn; yi[r0] = ai0 * cs - ar0 * sn; }
   if (on1) { yr[r1] = ar1 * cs + ai1 * sn; yi[r1] = ai1 * cs - ar1 * sn; }
   __syncwarp();
+}
+
+__constant__ float kInvNf[kSmallTaylorTerms + 1] = {
+    0.f, 1.f, 1.f / 2, 1.f / 3, 1.f / 4, 1.f / 5, 1.f / 6, 1.f / 7, 1.f / 8, 1.f / 9, 1.f / 10,
+    1.f / 11, 1.f / 12, 1.f / 13, 1.f / 14, 1.f / 15, 1.f / 16, 1.f / 17, 1.f / 18};
+
+// FP32 screen of the Krylov error estimate err = scale |y_k|, y =
+// exp(-i ts T_k) e_1 (whole warp; k <= 16 rows on half-warps as in
+// small_expm_e1; only one Taylor step, |ts| rho <= 1).  The shifted Taylor
+// series is summed in FP32 together with the same recurrence on magnitudes,
+// m_n = |c_n| |T - sig| m_{n-1}, m_0 = e_1, which bounds every rounding error
+// of the FP32 terms (each term's component is off by at most about 4 n 2^-24
+// of m_n; 2^-15 per unit of sum_n m_n covers 18 terms with a margin of 8).
+// True only when err exceeds thr even after that bound is taken off: the FP64
+// evaluation (same series, same number of terms) would then reject k too, so
+// the FP64 small exponential can be skipped.  Warp-uniform result.
+static __device__ bool small_expm_rejects32(int k, const double* a, const double* b, double ts, double scale,
+                                            double thr) {
+  if (k < 1 || k > 16 || !(thr >= 0.0)) return false;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int r = lane & 15;
+  const bool imag = lane >= 16, on = r < k;
+  const double ad = on ? a[r] : 0.0;
+  const float bl = (on && r > 0) ? (float)b[r - 1] : 0.f, br = (on && r < k - 1) ? (float)b[r] : 0.f;
+  const float rad = fabsf(bl) + fabsf(br);
+  float lo = on ? (float)ad - rad : 3e38f, hi = on ? (float)ad + rad : -3e38f;
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {  // both halves hold the same rows
+    lo = fminf(lo, __shfl_xor_sync(full, lo, o));
+    hi = fmaxf(hi, __shfl_xor_sync(full, hi, o));
+  }
+  const float sig = 0.5f * (lo + hi), rho = 0.5f * (hi - lo);
+  const float x = fabsf((float)ts) * rho * 1.001f;  // (the FP64 path's substep count is ceil(|ts| rho))
+  if (!(x <= 1.0f)) return false;
+  const int nterms = x > 0.5f ? kSmallTaylorTerms : (x > 0.25f ? 15 : (x > 0.1f ? 12 : 10));
+  const float d = on ? (float)(ad - (double)sig) : 0.f, ad_ = fabsf(d), abl = fabsf(bl), abr = fabsf(br);
+  const float tsf = (float)ts;
+  float t = (r == 0 && !imag) ? 1.f : 0.f, acc = t, m = t, msum = 0.f;
+  for (int n = 1; n <= nterms; ++n) {
+    const float c = tsf * kInvNf[n];
+    const float tl = __shfl_up_sync(full, t, 1, 16), tn = __shfl_down_sync(full, t, 1, 16);
+    const float ml = __shfl_up_sync(full, m, 1, 16), mn = __shfl_down_sync(full, m, 1, 16);
+    const float z = fmaf(br, tn, fmaf(bl, tl, d * t));
+    const float w = fmaf(abr, mn, fmaf(abl, ml, ad_ * m));
+    const float zo = __shfl_xor_sync(full, z, 16), wo = __shfl_xor_sync(full, w, 16);
+    t = imag ? -c * zo : c * zo;
+    m = fabsf(c) * wo;
+    acc += t;
+    msum += m;
+  }
+  // row k - 1: real part on lane k - 1, imaginary part on lane k + 15
+  const float yre = __shfl_sync(full, acc, k - 1), yim = __shfl_sync(full, acc, k + 15);
+  const float bnd = __shfl_sync(full, msum, k - 1) + __shfl_sync(full, msum, k + 15);
+  const double yk = (double)hypotf(yre, yim);
+  // (1e-16: the FP64 path may truncate its series after a different number of
+  // terms; every such tail is below 1e-17 for |ts| rho <= 1)
+  const double lower = yk * (1.0 - 0x1p-20) - 0x1p-15 * (double)bnd - 1e-16;
+  return scale * lower > thr;
 }
 
 // Gershgorin width of T (max of a_r + radius minus min of a_r - radius), an

@@ -370,9 +370,13 @@ __device__ void c_const_a(SmemC& S, const Op& op, int it) {
   }
 }
 
-__device__ double c_estimate(SmemC& S, int k, double ts) {
+// Error estimate of iteration k (control warp), with the FP32 screen of
+// fx_estimate: above thr without the FP64 small exponential when it can.
+__device__ double c_estimate(SmemC& S, int k, double ts, double thr) {
+  const double scale = S.beta0 * S.beta[k];
+  if (small_expm_rejects32(k, S.alpha + 1, S.beta + 1, ts, scale, thr)) return 2.0 * thr + 1e-300;
   small_expm_e1(k, S.alpha + 1, S.beta + 1, ts, S.yr, S.yi, S.tr, S.ti);
-  return S.beta0 * S.beta[k] * hypot(S.yr[k - 1], S.yi[k - 1]);
+  return scale * hypot(S.yr[k - 1], S.yi[k - 1]);
 }
 
 // ------------------------------------------------------------------ tiled apply (large chains)
@@ -694,7 +698,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
           } else {
             if (pend) {
               const long long te0 = sm_clock();
-              const double err = c_estimate(S, it - 1, remaining);
+              const double err = c_estimate(S, it - 1, remaining, p.tol * remaining / p.tau);
               if (lane == 0) {
                 S.err_prev = err;
                 S.stop_prev = err <= p.tol * remaining / p.tau;
@@ -799,7 +803,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
               if (it < klimit) {
                 pend_next = 1;  // estimate runs during the next apply
               } else {
-                err = c_estimate(S, it, remaining);
+                err = c_estimate(S, it, remaining, p.tol * remaining / p.tau);
                 acc_flag = err <= p.tol * remaining / p.tau;
               }
             }
@@ -851,7 +855,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
             for (int h = 1; h <= 40; ++h) {
               const double ts = ldexp(remaining, -h);
               if (!(fabs(ts) * width <= 2.0 * it)) continue;
-              err = c_estimate(S, it, ts);
+              err = c_estimate(S, it, ts, p.tol * ts / p.tau);
               if (err <= p.tol * ts / p.tau) { hh = h; break; }
             }
             if (lane == 0) { S.acc_h = hh; S.err_now = err; S.y_ready = hh > 0; }

@@ -370,10 +370,14 @@ __device__ void fx_const_a(SmemFx& S, const Op& op, int it) {
 }
 
 // Error estimate of iteration k (control warp): err = beta0 beta_k |y_k| with
-// y = exp(-i ts T_k) e_1 left in S.yr/S.yi.
-__device__ double fx_estimate(SmemFx& S, int k, double ts) {
+// y = exp(-i ts T_k) e_1 left in S.yr/S.yi.  When the FP32 screen shows that
+// err exceeds the threshold thr, the FP64 evaluation is skipped and a value
+// above thr is returned (S.yr/S.yi then stay untouched).
+__device__ double fx_estimate(SmemFx& S, int k, double ts, double thr) {
+  const double scale = S.beta0 * S.beta[k];
+  if (small_expm_rejects32(k, S.alpha + 1, S.beta + 1, ts, scale, thr)) return 2.0 * thr + 1e-300;
   small_expm_e1(k, S.alpha + 1, S.beta + 1, ts, S.yr, S.yi, S.tr, S.ti);
-  return S.beta0 * S.beta[k] * hypot(S.yr[k - 1], S.yi[k - 1]);
+  return scale * hypot(S.yr[k - 1], S.yi[k - 1]);
 }
 
 // ------------------------------------------------------------------ the kernel
@@ -608,7 +612,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
           } else {
             if (pend) {
               const long long te0 = sm_clock();
-              const double err = fx_estimate(S, it - 1, remaining);
+              const double err = fx_estimate(S, it - 1, remaining, p.tol * remaining / p.tau);
               if (lane == 0) {
                 S.err_prev = err;
                 S.stop_prev = err <= p.tol * remaining / p.tau;
@@ -730,7 +734,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
                 if (it < klimit) {
                   pend_next = 1;  // estimate runs during the next apply
                 } else {
-                  err = fx_estimate(S, it, remaining);
+                  err = fx_estimate(S, it, remaining, p.tol * remaining / p.tau);
                   acc_flag = err <= p.tol * remaining / p.tau;
                 }
               }
@@ -769,7 +773,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
             for (int h = 1; h <= 40; ++h) {
               const double ts = fx_scale2(remaining, -h);
               if (!(fabs(ts) * width <= 2.0 * it)) continue;
-              err = fx_estimate(S, it, ts);
+              err = fx_estimate(S, it, ts, p.tol * ts / p.tau);
               if (err <= p.tol * ts / p.tau) { hh = h; break; }
             }
             if (lane == 0) { S.acc_h = hh; S.err_now = err; S.y_ready = hh > 0; }
