@@ -443,6 +443,36 @@ def small_chain_line(P, torch):
             "phase_Mcycles": {k: v * 1e-6 for k, v in zip(PHASES, st.get("phase_ns", [0] * 8))}}
 
 
+def grid_atom_line(P, torch):
+    """The grid atom (Nr 2000, l < 100, dim 200 000, CF8:11, dt 0.1, m <= 64,
+    tol 1e-10) for one step from t = 500 (pulse maximum), starting from the
+    discrete 1s state: H applies/s, substeps per stage exponential and the
+    projected time of the full T = 1000 pulse."""
+    a = W.ATOM
+    p = W.grid_atom(Nr=a["Nr"], L=a["L"], dr=a["dr"], E0=a["E0"], omega=a["omega"], Tp=a["Tp"])
+    psi0, _ = W.atom_ground_state(p)
+    prop = P.Propagator(P.DIA(p.H0_offsets, p.H0_values), [P.DIA(p.V_offsets, p.V_values)], [p.drive],
+                        m_max=a["m_max"], max_substeps=4000)
+    x = torch.from_numpy(psi0).cuda()
+    prop.apply(np.array([1.0, 0.0]), x, torch.empty_like(x))   # context, tables
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    st = prop.propagate(x, 500.0, a["dt"], 1, order=a["order"], tol=a["tol"])
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    kms = prop.kernel_time_ms()
+    prop.close()
+    nfull = int(round(a["Tp"] / a["dt"]))
+    return {"workload": "grid atom Nr=2000 dr=0.1 l<100 (dim 200000), E0=0.05, omega=0.057, Tp=1000, CF8:11 dt=0.1, "
+                        "m_max 64, tol 1e-10, one step from t=500, 1s state", "precision": "fx",
+            "H_applies_per_s": st["n_applies"] / (ms * 1e-3), "ms_per_step": ms, "kernel_ms": kms,
+            "H_applies": st["n_applies"], "substeps_per_exponential": st["n_substeps"] / max(1, st["n_exp"]),
+            "max_k": st["max_k"], "norm_drift": abs(torch.linalg.vector_norm(x).item() - 1.0),
+            "full_pulse_projected_h": ms * 1e-3 * nfull / 3600.0}
+
+
 def run_gpu(args):
     import torch
     ws, rank, local = dist_env()
@@ -589,6 +619,7 @@ def run_gpu(args):
             if not cheb:
                 line["l2_roofline"] = l2_roofline(P, torch, args.precision, roof)
             line["small_chain"] = small_chain_line(P, torch)
+            line["grid_atom"] = grid_atom_line(P, torch)
             del ref_state
         if cpu is not None:
             line["cpu_baseline"] = cpu
@@ -619,7 +650,7 @@ def main():
     ap.add_argument("--min-timed-ms", type=float, default=2000.0,
                     help="the K-step call is repeated until at least this much has been timed (median reported)")
     ap.add_argument("--quick", action="store_true",
-                    help="headline figures only (no final-state error, FP64 arm, L2 probe or N=8 line)")
+                    help="headline figures only (no final-state error, FP64 arm, L2 probe, N=8 or atom line)")
     ap.add_argument("--block-size", type=int, default=0,
                     help="threads per CTA of the FP64 kernel; the fixed-point kernel uses 2x this many workers + 1 control warp")
     args = ap.parse_args()

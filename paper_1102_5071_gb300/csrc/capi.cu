@@ -74,7 +74,8 @@ struct cfet_ctx {
   bool tiled = false;          // window-tiled apply (long chains, complex64 and fixed point)
   // Pauli-sum family (FP64): strings grouped by X mask
   OpPauli pauli{};
-  void* d_pauli = nullptr;     // one allocation: gx | gstart | tz | top | tc | tim
+  void* d_pauli = nullptr;     // one allocation: gx | gstart | tz | top | tc | tim | greal
+  double* d_pauli_dtab = nullptr;  // diagonal tables of the Z-only strings
   double* d_partials = nullptr;
   unsigned* d_bar = nullptr;
   DevStatus* d_st = nullptr;
@@ -185,6 +186,7 @@ void free_ctx(cfet_ctx* c) {
   cudaFree(c->d_adj_seg); cudaFree(c->d_adj_acc);
   cudaFree(c->d_ts); cudaFree(c->d_ts_part);
   cudaFree(c->d_pauli);
+  cudaFree(c->d_pauli_dtab);
   cudaFree(c->d_csr);
   if (c->h_st) cudaFreeHost(c->h_st);
   if (c->h_scal) cudaFreeHost(c->h_scal);
@@ -911,7 +913,12 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
     const size_t o_top = o_tz + 8 * ((nt * sizeof(unsigned) + 7) / 8);
     const size_t o_tc = o_top + 8 * ((nt * sizeof(int) + 7) / 8);
     const size_t o_tim = o_tc + (size_t)nt * sizeof(double);
-    const size_t bytes = o_tim + (size_t)nt + 8;
+    const size_t o_gre = o_tim + 8 * (((size_t)nt + 7) / 8);
+    const size_t bytes = o_gre + (size_t)ng + 8;
+    std::vector<unsigned char> greal(ng, 1);
+    for (int g = 0; g < ng; ++g)
+      for (int t = gstart[g]; t < gstart[g + 1]; ++t)
+        if (tim[t]) greal[g] = 0;
     std::vector<unsigned char> blob(bytes, 0);
     if (ng) std::memcpy(blob.data() + o_gx, gx.data(), ng * sizeof(unsigned));
     std::memcpy(blob.data() + o_gs, gstart.data(), (ng + 1) * sizeof(int));
@@ -921,6 +928,7 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
       std::memcpy(blob.data() + o_tc, tc.data(), nt * sizeof(double));
       std::memcpy(blob.data() + o_tim, tim.data(), nt);
     }
+    if (ng) std::memcpy(blob.data() + o_gre, greal.data(), ng);
     CKC(cudaMalloc(&ctx->d_pauli, bytes), "cudaMalloc(Pauli tables)");
     CKC(cudaMemcpy(ctx->d_pauli, blob.data(), bytes, cudaMemcpyHostToDevice), "upload Pauli tables");
     unsigned char* base = (unsigned char*)ctx->d_pauli;
@@ -933,6 +941,31 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
     ctx->pauli.top = (const int*)(base + o_top);
     ctx->pauli.tc = (const double*)(base + o_tc);
     ctx->pauli.tim = base + o_tim;
+    ctx->pauli.greal = base + o_gre;
+    ctx->pauli.g0 = 0;
+    ctx->pauli.nd = 0;
+    ctx->pauli.dtab = nullptr;
+    // Z-only strings (group 0 when its X mask is 0): per-operator tables over
+    // all indices when they take at most 2 GiB
+    if (ng > 0 && gx[0] == 0u) {
+      const int n0 = gstart[1];
+      bool has[1 + kMaxDrives] = {};
+      for (int t = 0; t < n0; ++t) has[top[t]] = true;
+      int nd = 0;
+      for (int o2 = 0; o2 <= nV; ++o2)
+        if (has[o2]) ctx->pauli.dop[nd++] = o2;
+      if (nd > 0 && (size_t)nd * ((size_t)1 << nsites) * sizeof(double) <= (size_t(2) << 30)) {
+        CKC(cudaMalloc(&ctx->d_pauli_dtab, (size_t)nd * ((size_t)1 << nsites) * sizeof(double)),
+            "cudaMalloc(Pauli diagonal tables)");
+        ctx->pauli.nd = nd;
+        const int e = launch_pauli_diag_table(ctx->pauli, n0, ctx->d_pauli_dtab, nullptr);
+        const cudaError_t es = cudaDeviceSynchronize();
+        CKC((cudaError_t)e, "Pauli diagonal table kernel");
+        CKC(es, "Pauli diagonal table kernel");
+        ctx->pauli.dtab = ctx->d_pauli_dtab;
+        ctx->pauli.g0 = 1;
+      }
+    }
   }
   if (family == kFamilySpin) {
     const int N = nsites;

@@ -86,6 +86,14 @@ struct OpPauli {
   const int* top;            // [nterms]: 0 = H0, 1 + k = V_k
   const double* tc;          // [nterms]
   const unsigned char* tim;  // [nterms]
+  const unsigned char* greal;  // [ngroups]: 1 when every string of the group has a real phase
+  // Tabulated diagonal: the Z-only strings (group 0, X mask 0) summed per
+  // operator for every index, dtab[j * 2^N + y] = sum over the strings of
+  // operator dop[j] of tc (-1)^popc(y & z); the apply then starts at group g0.
+  int g0;                    // 1 when group 0 is tabulated, else 0
+  int nd;                    // operators with a table
+  int dop[1 + kMaxDrives];
+  const double* dtab;
 };
 
 // Banded family: all operators in DIA form, concatenated.
@@ -267,6 +275,7 @@ int launch_propagate_spin_ip(const PropParams& p, const OpSpinIP& op, int grid, 
 int max_coresident_blocks_ip(int block, int nw);
 int launch_propagate_pauli(const PropParams& p, const OpPauli& op, int grid, int block, void* stream);
 int max_coresident_blocks_pauli(int block, int nterms);
+int launch_pauli_diag_table(const OpPauli& op, int n0, double* dtab, void* stream);
 int launch_apply_pauli(const OpPauli& op, int dim, const double* c, int nV, const double2* vin, double2* vout,
                        void* stream);
 // psi[x] *= exp(i sign d(x) t[which]) with d the diagonal of the XXZ chain H0

@@ -93,23 +93,53 @@ __device__ __forceinline__ double2 apply_sparse_at(const double2* q, int r, int 
 // the partner y ^ xm weighted by sum_t pc[t] (-1)^popc((y ^ xm) & z_t), with
 // the strings of odd popc(x & z) contributing an imaginary weight (the phase
 // i^popc(x & z) of the string; its sign is folded into pc).
-__device__ __forceinline__ double2 apply_pauli_at(const double2* q, int y, const OpPauli& op, const double* pc) {
+// The Z-only group may come from per-operator tables (scal: the stage
+// scalars c_o); groups whose strings all have real phases take real products.
+__device__ __forceinline__ double2 apply_pauli_at(const double2* q, int y, const OpPauli& op, const double* pc,
+                                                  const double* scal) {
   double ar = 0.0, ai = 0.0;
-  int t = __ldg(op.gstart);
-  for (int g = 0; g < op.ngroups; ++g) {
+  if (op.nd > 0) {
+    double d = 0.0;
+    for (int j = 0; j < op.nd; ++j) d = fma(scal[op.dop[j]], __ldg(op.dtab + ((size_t)j << op.N) + y), d);
+    const double2 w = q[y];
+    ar = d * w.x;
+    ai = d * w.y;
+  }
+  int t = __ldg(op.gstart + op.g0);
+  for (int g = op.g0; g < op.ngroups; ++g) {
     const unsigned b = (unsigned)y ^ __ldg(op.gx + g);
     const int t1 = __ldg(op.gstart + g + 1);
-    double cr = 0.0, ci = 0.0;
-    for (; t < t1; ++t) {
-      const double c = (__popc(b & __ldg(op.tz + t)) & 1) ? -pc[t] : pc[t];
-      if (__ldg(op.tim + t)) ci += c;
-      else cr += c;
-    }
     const double2 w = q[b];
-    ar = fma(cr, w.x, fma(-ci, w.y, ar));
-    ai = fma(cr, w.y, fma(ci, w.x, ai));
+    if (__ldg(op.greal + g)) {
+      double cr = 0.0;
+      for (; t < t1; ++t) cr += (__popc(b & __ldg(op.tz + t)) & 1) ? -pc[t] : pc[t];
+      ar = fma(cr, w.x, ar);
+      ai = fma(cr, w.y, ai);
+    } else {
+      double cr = 0.0, ci = 0.0;
+      for (; t < t1; ++t) {
+        const double c = (__popc(b & __ldg(op.tz + t)) & 1) ? -pc[t] : pc[t];
+        if (__ldg(op.tim + t)) ci += c;
+        else cr += c;
+      }
+      ar = fma(cr, w.x, fma(-ci, w.y, ar));
+      ai = fma(cr, w.y, fma(ci, w.x, ai));
+    }
   }
   return make_double2(ar, ai);
+}
+
+// Diagonal tables of a Pauli-sum context: strings [0, n0) are the Z-only group.
+__global__ void k_pauli_diag_table(OpPauli op, int n0, double* dtab) {
+  const size_t dim = (size_t)1 << op.N;
+  for (size_t y = (size_t)blockIdx.x * blockDim.x + threadIdx.x; y < dim; y += (size_t)gridDim.x * blockDim.x) {
+    for (int j = 0; j < op.nd; ++j) {
+      double s = 0.0;
+      for (int t = 0; t < n0; ++t)
+        if (op.top[t] == op.dop[j]) s += (__popc((unsigned)y & op.tz[t]) & 1) ? -op.tc[t] : op.tc[t];
+      dtab[((size_t)j << op.N) + y] = s;
+    }
+  }
 }
 
 // Interaction-picture spin apply at index x (OpSpinIP): sum over the single
@@ -298,7 +328,7 @@ __global__ void __launch_bounds__(256) k_propagate(PropParams p, Op op) {
           } else if constexpr (FAMILY == kFamilyPauli) {
             const double* pc = reinterpret_cast<const double*>(smem_raw + ip_table_offset<SmemLayout>());
             for (int x = x0; x < dim; x += stride) {
-              double2 hv = apply_pauli_at(q, x, op, pc);
+              double2 hv = apply_pauli_at(q, x, op, pc, S.scal);
               hv.x *= s_it;
               hv.y *= s_it;
               if (qm) {
@@ -582,7 +612,7 @@ __global__ void k_apply(Op op, int dim, Coefs c, int nV, const double2* __restri
       sc.cxx = c.c[0] * op.J2;
       vout[x] = apply_spin_at(vin, x, op, sc, bsite);
     } else if constexpr (FAMILY == kFamilyPauli) {
-      vout[x] = apply_pauli_at(vin, x, op, pc);
+      vout[x] = apply_pauli_at(vin, x, op, pc, c.c);
     } else {
       vout[x] = apply_sparse_at(vin, x, dim, op, copf);
     }
@@ -753,6 +783,13 @@ int launch_apply_csr(const OpCsr& op, int dim, const double* c, int nV, const do
   Coefs cc = {};
   for (int i = 0; i < 1 + nV; ++i) cc.c[i] = c[i];
   k_apply<kFamilyCsr, OpCsr><<<apply_grid(dim, 256), 256, 0, (cudaStream_t)stream>>>(op, dim, cc, nV, vin, vout);
+  return (int)cudaGetLastError();
+}
+int launch_pauli_diag_table(const OpPauli& op, int n0, double* dtab, void* stream) {
+  const size_t dim = (size_t)1 << op.N;
+  size_t g = (dim + 255) / 256;
+  if (g > 4096) g = 4096;
+  k_pauli_diag_table<<<(unsigned)g, 256, 0, (cudaStream_t)stream>>>(op, n0, dtab);
   return (int)cudaGetLastError();
 }
 int launch_apply_pauli(const OpPauli& op, int dim, const double* c, int nV, const double2* vin, double2* vout,
