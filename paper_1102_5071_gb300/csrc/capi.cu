@@ -12,6 +12,8 @@
 // upload, state reset, persistent-kernel chunks, status read-back) is
 // captured into a CUDA graph owned by the context and replayed; an unchanged
 // topology only updates the executable graph in place.
+#include <cuda.h>  // CUtensorMap and its enums (the encoder comes from the runtime's driver entry point)
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -26,6 +28,10 @@
 #include "tiled_common.cuh"
 
 using namespace cfet;
+
+// TMA maps of the window-tiled complex64 apply over the Krylov basis of ctx
+// (nvec vectors of 2^N elements), one per window, copied to device memory.
+static cfet_status build_tile_maps(cfet_ctx* ctx, int N, int nvec);
 
 struct cfet_ctx {
   int device = 0;
@@ -72,6 +78,7 @@ struct cfet_ctx {
   float* d_val32 = nullptr;
   float2* d_qbasis32 = nullptr;
   bool tiled = false;          // window-tiled apply (long chains, complex64 and fixed point)
+  unsigned char* d_tmaps = nullptr;  // complex64 tiled apply: one TMA map per window
   // Pauli-sum family (FP64): strings grouped by X mask
   OpPauli pauli{};
   void* d_pauli = nullptr;     // one allocation: gx | gstart | tz | top | tc | tim | greal
@@ -187,6 +194,7 @@ void free_ctx(cfet_ctx* c) {
   cudaFree(c->d_ts); cudaFree(c->d_ts_part);
   cudaFree(c->d_pauli);
   cudaFree(c->d_pauli_dtab);
+  cudaFree(c->d_tmaps);
   cudaFree(c->d_csr);
   if (c->h_st) cudaFreeHost(c->h_st);
   if (c->h_scal) cudaFreeHost(c->h_scal);
@@ -315,6 +323,7 @@ PropParams base_params(cfet_ctx* ctx, double2* psi, double tau, double tol) {
   p.qbasis = ctx->d_qbasis;
   p.qbasis32 = ctx->d_qbasis32;
   p.tiled = ctx->tiled ? 1 : 0;
+  p.tmaps = ctx->d_tmaps;
   p.reorth = ctx->opt.reorth;
   return p;
 }
@@ -1182,6 +1191,13 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
         "cudaMalloc(Krylov basis)");
   else if (ctx->precision == CFET_PREC_C64)
     CKC(cudaMalloc(&ctx->d_qbasis32, (size_t)(o.m_max + 1) * dim * sizeof(float2)), "cudaMalloc(Krylov basis)");
+  if (ctx->precision == CFET_PREC_C64 && ctx->tiled) {
+    const cfet_status ts = build_tile_maps(ctx, nsites, o.m_max + 1);
+    if (ts != CFET_OK) {
+      free_ctx(ctx);
+      return ts;
+    }
+  }
   else
     CKC(cudaMalloc(&ctx->d_basis, (size_t)o.m_max * dim * sizeof(double2)), "cudaMalloc(Krylov basis)");
   if (ctx->precision == CFET_PREC_FX) {
@@ -1511,6 +1527,72 @@ cfet_status cfet_sync(cfet_ctx* ctx, void* stream, cfet_stats* stats) {
 // units of complex64 tiles (element pairs) contiguous and aligned, and the
 // window count within its bound.
 extern "C++" {
+// TMA geometry of window w of the window-tiled complex64 apply (tiles of
+// 2^kC64TileBits 8-byte elements, a map over the whole Krylov basis of nvec
+// contiguous vectors, so that the vector index continues the outermost
+// dimension).  Window 0 views the basis as 256-element rows (box: 16 rows);
+// window w >= 1 splits the index into its bits [0, c) (as 256 x 2^(c-8) when
+// c > 8: a box dimension holds at most 256 elements), [c, b0), the window's
+// bits [b0, b0 + width) and the rest (box: the low bits x 1 x 2^width x 1).
+struct TileMapGeom {
+  int rank;
+  uint64_t dims[5];
+  uint64_t strides[4];  // bytes, dimensions 1 .. rank - 1
+  uint32_t box[5];
+};
+static void tile_map_geometry(int N, int w, const TileWin& W, int nvec, TileMapGeom* g) {
+  const uint64_t e = 8, dim = uint64_t(1) << N, nv = (uint64_t)nvec;
+  if (w == 0) {
+    *g = TileMapGeom{2, {256, (dim >> 8) * nv, 0, 0, 0}, {256 * e, 0, 0, 0}, {256, 16, 0, 0, 0}};
+    return;
+  }
+  const int c = W.c, b0 = W.b0, wd = W.width;
+  const uint64_t lo = uint64_t(1) << c, mid = uint64_t(1) << (b0 - c), win = uint64_t(1) << wd;
+  const uint64_t rest = (uint64_t(1) << (N - b0 - wd)) * nv;
+  const uint64_t s_mid = lo * e, s_win = (uint64_t(1) << b0) * e, s_rest = (uint64_t(1) << (b0 + wd)) * e;
+  if (c <= 8)
+    *g = TileMapGeom{4, {lo, mid, win, rest, 0}, {s_mid, s_win, s_rest, 0}, {(uint32_t)lo, 1, (uint32_t)win, 1, 0}};
+  else
+    *g = TileMapGeom{5, {256, lo >> 8, mid, win, rest}, {256 * e, s_mid, s_win, s_rest},
+                     {256, (uint32_t)(lo >> 8), 1, (uint32_t)win, 1}};
+}
+// Coordinates of tile t of vector v (as the kernel's tile_load / tile_store).
+static void tile_map_coords(int N, int w, const TileWin& W, int t, int v, int* c) {
+  if (w == 0) {
+    c[0] = 0; c[1] = (t << 4) + v * (1 << (N - 8));
+    return;
+  }
+  const int nb = W.b0 - W.c, tl = t & ((1 << nb) - 1), th = (t >> nb) + v * (1 << (N - W.b0 - W.width));
+  if (W.c <= 8) {
+    c[0] = 0; c[1] = tl; c[2] = 0; c[3] = th;
+  } else {
+    c[0] = 0; c[1] = 0; c[2] = tl; c[3] = 0; c[4] = th;
+  }
+}
+// Element (index within the basis) that box slot j of the box at coordinates c
+// holds: the box is laid out in shared memory with dimension 0 fastest.
+static int64_t tile_map_element(const TileMapGeom& g, const int* c, int j) {
+  int64_t off = 0, stride = 1;  // stride in elements of the current dimension
+  for (int d = 0; d < g.rank; ++d) {
+    const int64_t idx = (int64_t)c[d] + (j % (int)g.box[d]);
+    j /= (int)g.box[d];
+    if (idx >= (int64_t)g.dims[d]) return -1;
+    off += idx * stride;
+    if (d + 1 < g.rank) stride = (int64_t)(g.strides[d] / 8);
+  }
+  return off;
+}
+// Constraints of a tiled TMA map: rank <= 5, box dimensions in [1, 256], inner
+// box a multiple of 16 bytes, strides multiples of 16 bytes below 2^40.
+static bool tile_map_valid(const TileMapGeom& g) {
+  if (g.rank < 1 || g.rank > 5 || (g.box[0] * 8) % 16 != 0) return false;
+  for (int d = 0; d < g.rank; ++d)
+    if (g.box[d] < 1 || g.box[d] > 256 || g.dims[d] < 1 || g.dims[d] > (uint64_t(1) << 32)) return false;
+  for (int d = 0; d + 1 < g.rank; ++d)
+    if (g.strides[d] % 16 != 0 || g.strides[d] >= (uint64_t(1) << 40)) return false;
+  return true;
+}
+
 template <int TB>
 static bool check_tiling(int N, int64_t* checked) {
   TileWin W[kTiledMaxWindows] = {};
@@ -1543,12 +1625,66 @@ static bool check_tiling(int N, int64_t* checked) {
         }
         ++*checked;
       }
+    if (TB == kC64TileBits) {  // the TMA boxes of the complex64 kernel hold the same slots
+      TileMapGeom g;
+      tile_map_geometry(N, w, W[w], 3, &g);
+      if (!tile_map_valid(g)) return false;
+      int64_t boxn = 1;
+      for (int d = 0; d < g.rank; ++d) boxn *= g.box[d];
+      if (boxn != (int64_t(1) << TB)) return false;
+      for (int v = 0; v < 3; v += 2)
+        for (int t = 0; t < ntiles; ++t) {
+          int c[5];
+          tile_map_coords(N, w, W[w], t, v, c);
+          for (int d = 0; d < g.rank; ++d)
+            if (c[d] < 0 || (d == 0 && c[d] != 0)) return false;
+          for (int j = 0; j < (1 << TB); ++j) {
+            const int64_t x = w == 0 ? ((int64_t)t << TB) | j : tile_x(W[w], t, j);
+            if (tile_map_element(g, c, j) != x + (int64_t)v * dim) return false;
+          }
+        }
+    }
   }
   for (int i = 0; i < N; ++i)
     if (flips[i] != 1) return false;
   for (int i = 0; i + 1 < N; ++i)
     if (bonds[i] != 1) return false;
   return true;
+}
+}  // extern "C++"
+
+extern "C++" {
+static cfet_status build_tile_maps(cfet_ctx* ctx, int N, int nvec) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return fail(nullptr, CFET_ECUDA, "cuTensorMapEncodeTiled is not available");
+    }
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  TileWin W[kTiledMaxWindows] = {};
+  const int nwin = tiled_windows<kC64TileBits>(N, W);
+  std::vector<CUtensorMap> maps(nwin);
+  for (int w = 0; w < nwin; ++w) {
+    TileMapGeom g;
+    tile_map_geometry(N, w, W[w], nvec, &g);
+    if (!tile_map_valid(g)) return fail(nullptr, CFET_EINVAL, "tiled apply: invalid TMA geometry");
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUresult r = encode(&maps[w], CU_TENSOR_MAP_DATA_TYPE_INT64, (cuuint32_t)g.rank, ctx->d_qbasis32, g.dims,
+                              g.strides, g.box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(nullptr, CFET_ECUDA, "cuTensorMapEncodeTiled failed for the tiled apply");
+  }
+  static_assert(sizeof(CUtensorMap) == kTmaMapBytes, "tensor map size");
+  cudaError_t e = cudaMalloc(&ctx->d_tmaps, (size_t)nwin * sizeof(CUtensorMap));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(ctx->d_tmaps, maps.data(), (size_t)nwin * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "upload of the TMA maps");
+  return CFET_OK;
 }
 }  // extern "C++"
 

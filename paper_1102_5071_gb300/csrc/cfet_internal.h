@@ -214,6 +214,9 @@ struct PropParams {
   const double2* ip_w;
   const double* ip_times;
   int ip_nw;
+  // window-tiled complex64 apply: one TMA tensor map (128 bytes) per window
+  // over the Krylov basis (device memory, 64-byte aligned)
+  const unsigned char* tmaps;
 };
 
 // Chebyshev record of one stage exponential (host-computed, see chebyshev.cpp):
@@ -300,6 +303,7 @@ int max_coresident_blocks_c64(int family, int block, bool tiled);
 // (tiled_common.cuh) in the complex64 and fixed-point kernels, unless
 // cfet_options.apply_form asks for one form.
 constexpr int kC64TiledMinSites = 23;
+constexpr int kC64TileBits = 12;    // tiles of 2^12 complex64 elements (32 KB)
 constexpr int kFxTiledMinSites = 23;
 constexpr int kTiledMinSites = 13;  // tiles of up to 2^12 elements
 constexpr int kTiledMaxSites = 30;  // four windows cover 32 sites at 2^11-element tiles

@@ -97,6 +97,7 @@ struct SmemC {
   double wnorm2;                 // ||w||^2 of the current iteration (from the phase-A sums)
   double qnorm2[kMaxKrylov + 3]; // ||q_i||^2 of the stored vectors (reduced after they are written)
   int abort_flag, stop_prev, accept_now, pend, y_ready, acc_h;
+  int tma_fail;                  // tiled apply: a tile wait gave up
   double err_now, err_prev;
   double beta0;
 };
@@ -380,126 +381,184 @@ __device__ double c_estimate(SmemC& S, int k, double ts, double thr) {
 }
 
 // ------------------------------------------------------------------ tiled apply (large chains)
-// Window tiling of tiled_common.cuh.  The vector each element reads for
-// itself (q_{k-1} in window 0, the partial u after it) is staged with the
-// tile, so the loop touches global memory only to store u: two q tiles and two
-// such tiles of 2^12 complex64 elements (128 KB).  The last window also takes
-// <q, u> and ||u||^2.
-constexpr int kTileBits = 12;
+// Window tiling of tiled_common.cuh with tiles of 2^12 complex64 elements
+// moved by TMA.  Each of kTmaStages stages holds the q tile and the tile of
+// the vector each element reads for itself (q_{k-1} in window 0, the partial
+// u after it): 64 KB per stage.  One worker (the producer) keeps two tiles in
+// flight ahead of the others: it arms the stage's mbarrier with the bytes of
+// both loads and issues them, and once the workers have written a tile's
+// results (in place over its own-element buffer) it stores that buffer with a
+// bulk tensor store.  The loop touches global memory only for the diagonal
+// tables; the last window also takes <q, u> and ||u||^2.
+constexpr int kTileBits = kC64TileBits;
 constexpr int kTileElems = 1 << kTileBits;
+constexpr unsigned kTileBytes = kTileElems * sizeof(float2);
 
-// One window pass of this CTA's worker threads over its tiles.
-// buf: q tiles [2][kTileElems], then the staged own-element vector [2][kTileElems].
-template <bool FIRST, bool LAST>
-__device__ void c_tiled_pass(float2* buf, const OpSpinC& op, const CConst& c, const float* bx,
-                             const float2* __restrict__ q, const float2* __restrict__ qm, float2* __restrict__ u,
-                             const TileWin& W, int nworkers, float& s0, float& c0, float& s1, float& c1) {
-  const int tid = threadIdx.x;
-  const int G = gridDim.x;
-  const int N = op.N;
-  const int ntiles = 1 << (N - kTileBits);
-  const bool aux = !FIRST || c.use_prev;
-  const float2* asrc = FIRST ? qm : u;
-  auto xof = [&](int t, int j) { return FIRST ? (t << kTileBits) | j : tile_x(W, t, j); };
-  auto load = [&](int slot, int t) {
-    float2* qb = buf + slot * kTileElems;
-    float2* ab = buf + (2 + slot) * kTileElems;
-    for (int unit = tid; unit < kTileElems / 2; unit += nworkers) {
-      const int x = xof(t, 2 * unit);
-      cp_async16(qb + 2 * unit, q + x);
-      if (aux) cp_async16(ab + 2 * unit, asrc + x);
-    }
-    cp_async_commit();
-  };
-  int t = blockIdx.x;
-  if (t < ntiles) load(0, t);
-  for (int k = 0; t < ntiles; ++k, t += G) {
-    const float2* cur = buf + (k & 1) * kTileElems;
-    const float2* acur = buf + (2 + (k & 1)) * kTileElems;
-    cp_async_wait_all();
-    workers_sync(nworkers);
-    if (t + G < ntiles) load((k + 1) & 1, t + G);
-    for (int j = tid; j < kTileElems; j += nworkers) {
-      const int x = xof(t, j);
-      float ur, ui, hr = 0.f, hi = 0.f, fr = 0.f, fi = 0.f;
-      if (FIRST) {
-        const int L = op.lo_bits;
-        const float dz = __ldg(op.dz_lo + (x & ((1 << L) - 1))) + __ldg(op.dz_hi + (x >> (L - 1)));
-        const float d = c.cz * dz;
-        const float2 v = cur[j];
-        ur = d * v.x;
-        ui = d * v.y;
-        const unsigned anti = ((unsigned)j ^ ((unsigned)j >> 1)) & ((1u << (kTileBits - 1)) - 1u);
-#pragma unroll
-        for (int i = 0; i < kTileBits - 1; ++i)
-          if ((anti >> i) & 1u) {
-            const float2 w = cur[j ^ (3 << i)];
-            hr += w.x;
-            hi += w.y;
-          }
-        if (op.uniform) {
-#pragma unroll
-          for (int i = 0; i < kTileBits; ++i) {
-            const float2 w = cur[j ^ (1 << i)];
-            fr += w.x;
-            fi += w.y;
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < kTileBits; ++i) {
-            const float2 w = cur[j ^ (1 << i)];
-            ur = fmaf(bx[i], w.x, ur);
-            ui = fmaf(bx[i], w.y, ui);
-          }
-        }
-        if (c.use_prev) {
-          const float2 w = acur[j];
-          ur = fmaf(c.cp, w.x, ur);
-          ui = fmaf(c.cp, w.y, ui);
-        }
-      } else {
-        const float2 a = acur[j];
-        ur = a.x;
-        ui = a.y;
-        const unsigned jh = (unsigned)j >> W.c;  // bits b0 .. b0+width-1 of x
-        const unsigned anti = (jh ^ (jh >> 1)) & ((1u << (W.width - 1)) - 1u);
-        for (int i = 0; i < W.width - 1; ++i)
-          if ((anti >> i) & 1u) {
-            const float2 w = cur[j ^ (3 << (W.c + i))];
-            hr += w.x;
-            hi += w.y;
-          }
-        if (op.uniform) {
-          for (int i = 1; i < W.width; ++i) {
-            const float2 w = cur[j ^ (1 << (W.c + i))];
-            fr += w.x;
-            fi += w.y;
-          }
-        } else {
-          for (int i = 1; i < W.width; ++i) {
-            const float2 w = cur[j ^ (1 << (W.c + i))];
-            ur = fmaf(bx[W.b0 + i], w.x, ur);
-            ui = fmaf(bx[W.b0 + i], w.y, ui);
-          }
-        }
-      }
-      ur = fmaf(c.ch, hr, ur);
-      ui = fmaf(c.ch, hi, ui);
-      if (op.uniform) {
-        ur = fmaf(c.cx, fr, ur);
-        ui = fmaf(c.cx, fi, ui);
-      }
-      u[x] = make_float2(ur, ui);
-      if (LAST) {
-        const float2 v = cur[j];
-        ff_add_prod(s0, c0, v.x, ur);
-        ff_add_prod(s0, c0, v.y, ui);
-        ff_add_prod(s1, c1, ur, ur);
-        ff_add_prod(s1, c1, ui, ui);
+struct TmaPass {
+  const unsigned char* maps;  // kTmaMapBytes per window
+  unsigned long long* bar;    // [kTmaStages] in shared memory
+  float2* stage;              // [kTmaStages][2][kTileElems] in shared memory
+  int* fail;                  // shared flag: a wait gave up
+  unsigned* phase;            // parity bits of the stages (per thread, identical in all workers)
+  int* status;
+  long long timeout_ns;
+};
+
+// Bounded wait for a stage's tile; false (status CFET_ETIMEOUT) when it gave up.
+__device__ bool tile_wait(unsigned long long* bar, unsigned parity, int* status, long long timeout_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = global_timer_ns();
+  unsigned spins = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if ((++spins & 255u) == 0u) {
+      if (ld_volatile_i32(status) != 0) return false;
+      if (global_timer_ns() - t0 > timeout_ns) {
+        atomicCAS(status, 0, (int)CFET_ETIMEOUT);
+        return false;
       }
     }
   }
-  cp_async_wait_all();
+  return true;
+}
+
+// One window pass of this CTA's worker threads over its tiles (vectors are
+// basis indices: iq the applied q, ia the own-element input, iu the output).
+template <bool FIRST, bool LAST>
+__device__ void c_tiled_pass(const TmaPass& T, const OpSpinC& op, const CConst& c, const float* bx, int iq, int ia,
+                             int iu, const TileWin& W, int w, int nworkers, float& s0, float& c0, float& s1,
+                             float& c1) {
+  const int tid = threadIdx.x;
+  const int G = gridDim.x;
+  const int ntiles = 1 << (op.N - kTileBits);
+  const bool aux = !FIRST || c.use_prev;
+  const unsigned bytes = aux ? 2 * kTileBytes : kTileBytes;
+  const void* map = T.maps + (size_t)w * kTmaMapBytes;
+  const bool prod = tid == 0;
+  auto issue = [&](int k, int t) {  // producer: tile t into stage k % kTmaStages
+    const int st = k % kTmaStages;
+    float2* qb = T.stage + (size_t)st * 2 * kTileElems;
+    mbar_arrive_expect_tx(T.bar + st, bytes);
+    tile_load(qb, map, FIRST, W, op.N, t, iq, T.bar + st);
+    if (aux) tile_load(qb + kTileElems, map, FIRST, W, op.N, t, ia, T.bar + st);
+  };
+  if (prod) {
+    fence_proxy_async_all();  // vectors written by generic stores before the exchange, read by TMA now
+    for (int k = 0; k < kTmaStages - 1; ++k)
+      if (blockIdx.x + k * G < ntiles) issue(k, blockIdx.x + k * G);
+  }
+  int k = 0;
+  for (int t = blockIdx.x; t < ntiles; ++k, t += G) {
+    const int st = k % kTmaStages;
+    const float2* cur = T.stage + (size_t)st * 2 * kTileElems;
+    float2* acur = T.stage + (size_t)st * 2 * kTileElems + kTileElems;
+    const unsigned par = (*T.phase >> st) & 1u;
+    *T.phase ^= 1u << st;
+    if (!tile_wait(T.bar + st, par, T.status, T.timeout_ns)) *T.fail = 1;
+    if (!*T.fail) {
+      for (int j = tid; j < kTileElems; j += nworkers) {
+        float ur, ui, hr = 0.f, hi = 0.f, fr = 0.f, fi = 0.f;
+        if (FIRST) {
+          const int x = (t << kTileBits) | j;
+          const int L = op.lo_bits;
+          const float dz = __ldg(op.dz_lo + (x & ((1 << L) - 1))) + __ldg(op.dz_hi + (x >> (L - 1)));
+          const float d = c.cz * dz;
+          const float2 v = cur[j];
+          ur = d * v.x;
+          ui = d * v.y;
+          const unsigned anti = ((unsigned)j ^ ((unsigned)j >> 1)) & ((1u << (kTileBits - 1)) - 1u);
+#pragma unroll
+          for (int i = 0; i < kTileBits - 1; ++i)
+            if ((anti >> i) & 1u) {
+              const float2 wv = cur[j ^ (3 << i)];
+              hr += wv.x;
+              hi += wv.y;
+            }
+          if (op.uniform) {
+#pragma unroll
+            for (int i = 0; i < kTileBits; ++i) {
+              const float2 wv = cur[j ^ (1 << i)];
+              fr += wv.x;
+              fi += wv.y;
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < kTileBits; ++i) {
+              const float2 wv = cur[j ^ (1 << i)];
+              ur = fmaf(bx[i], wv.x, ur);
+              ui = fmaf(bx[i], wv.y, ui);
+            }
+          }
+          if (c.use_prev) {
+            const float2 wv = acur[j];
+            ur = fmaf(c.cp, wv.x, ur);
+            ui = fmaf(c.cp, wv.y, ui);
+          }
+        } else {
+          const float2 a = acur[j];
+          ur = a.x;
+          ui = a.y;
+          const unsigned jh = (unsigned)j >> W.c;  // bits b0 .. b0+width-1 of x
+          const unsigned anti = (jh ^ (jh >> 1)) & ((1u << (W.width - 1)) - 1u);
+          for (int i = 0; i < W.width - 1; ++i)
+            if ((anti >> i) & 1u) {
+              const float2 wv = cur[j ^ (3 << (W.c + i))];
+              hr += wv.x;
+              hi += wv.y;
+            }
+          if (op.uniform) {
+            for (int i = 1; i < W.width; ++i) {
+              const float2 wv = cur[j ^ (1 << (W.c + i))];
+              fr += wv.x;
+              fi += wv.y;
+            }
+          } else {
+            for (int i = 1; i < W.width; ++i) {
+              const float2 wv = cur[j ^ (1 << (W.c + i))];
+              ur = fmaf(bx[W.b0 + i], wv.x, ur);
+              ui = fmaf(bx[W.b0 + i], wv.y, ui);
+            }
+          }
+        }
+        ur = fmaf(c.ch, hr, ur);
+        ui = fmaf(c.ch, hi, ui);
+        if (op.uniform) {
+          ur = fmaf(c.cx, fr, ur);
+          ui = fmaf(c.cx, fi, ui);
+        }
+        acur[j] = make_float2(ur, ui);  // the own element only: read above by this thread
+        if (LAST) {
+          const float2 v = cur[j];
+          ff_add_prod(s0, c0, v.x, ur);
+          ff_add_prod(s0, c0, v.y, ui);
+          ff_add_prod(s1, c1, ur, ur);
+          ff_add_prod(s1, c1, ui, ui);
+        }
+      }
+    }
+    fence_proxy_async_smem();  // the results, written by generic stores, are read by the TMA store
+    workers_sync(nworkers);
+    if (*T.fail) break;
+    if (prod) {
+      tile_store(map, FIRST, W, op.N, t, iu, acur);
+      bulk_commit();
+      const int tn = t + (kTmaStages - 1) * G;
+      if (tn < ntiles) {
+        bulk_wait_read_1();  // the stage to refill was stored from at tile k - 1
+        issue(k + kTmaStages - 1, tn);
+      }
+    }
+  }
+  if (prod) {
+    bulk_wait_all();         // u written before the exchange that follows
+    fence_proxy_async_all();
+    if (*T.fail) {           // tiles still in flight: wait for them, again with a limit
+      for (int s2 = 0; s2 < kTmaStages; ++s2) {
+        const unsigned par = (*T.phase >> s2) & 1u;
+        tile_wait(T.bar + s2, par, T.status, T.timeout_ns);
+      }
+    }
+  }
+  workers_sync(nworkers);
 }
 
 // ------------------------------------------------------------------ the kernel
@@ -535,7 +594,18 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
   if constexpr (TILED) {
     nwin = tiled_windows<kTileBits>(op.N, win);
   }
-  float2* tbuf = reinterpret_cast<float2*>(smem_raw + ((sizeof(SmemC) + 127) & ~size_t(127)));
+  // tiled apply: the stages' mbarriers and tile buffers behind SmemC
+  unsigned char* tiles_base = smem_raw + ((sizeof(SmemC) + 127) & ~size_t(127));
+  unsigned tph = 0;  // parities of the stages' mbarriers (the same in every worker)
+  const TmaPass TP{p.tmaps, reinterpret_cast<unsigned long long*>(tiles_base),
+                   reinterpret_cast<float2*>(tiles_base + 128), &S.tma_fail, &tph, &p.st->status, p.timeout_ns};
+  if constexpr (TILED) {
+    if (tid == 0) {  // ordered before any use by the CTA barriers of the conversion pass
+      for (int s2 = 0; s2 < kTmaStages; ++s2) mbar_init(TP.bar + s2, 1);
+      S.tma_fail = 0;
+      mbar_init_fence();
+    }
+  }
   int wslot = 0;
   DevStatus* st = p.st;
   const bool glead = (blockIdx.x == 0) && lead;
@@ -643,13 +713,17 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
             if constexpr (TILED) {
               {  // window passes, grid exchanges between them (control warp)
                 for (int w = 0; w < nwin; ++w) {
+                  // basis indices: q_it is vector it - 1, q_{it-1} vector it - 2, u vector it
+                  const int iq = it - 1, ia = w == 0 ? (it > 1 ? it - 2 : 0) : it, iu = it;
                   if (w == 0) {
-                    if (nwin == 1) c_tiled_pass<true, true>(tbuf, op, c, S.bx, q, qm, u, win[0], wstep, s0, c0, s1, c1);
-                    else c_tiled_pass<true, false>(tbuf, op, c, S.bx, q, qm, u, win[0], wstep, s0, c0, s1, c1);
+                    if (nwin == 1)
+                      c_tiled_pass<true, true>(TP, op, c, S.bx, iq, ia, iu, win[0], 0, wstep, s0, c0, s1, c1);
+                    else
+                      c_tiled_pass<true, false>(TP, op, c, S.bx, iq, ia, iu, win[0], 0, wstep, s0, c0, s1, c1);
                   } else if (w == nwin - 1) {
-                    c_tiled_pass<false, true>(tbuf, op, c, S.bx, q, qm, u, win[w], wstep, s0, c0, s1, c1);
+                    c_tiled_pass<false, true>(TP, op, c, S.bx, iq, ia, iu, win[w], w, wstep, s0, c0, s1, c1);
                   } else {
-                    c_tiled_pass<false, false>(tbuf, op, c, S.bx, q, qm, u, win[w], wstep, s0, c0, s1, c1);
+                    c_tiled_pass<false, false>(TP, op, c, S.bx, iq, ia, iu, win[w], w, wstep, s0, c0, s1, c1);
                   }
                   if (w + 1 < nwin) {
                     window_written_sync();    // all threads: window w written
@@ -964,7 +1038,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
 
 // ------------------------------------------------------------------ launchers
 size_t c64_tiled_smem_bytes() {
-  return ((sizeof(SmemC) + 127) & ~size_t(127)) + 4 * kTileElems * sizeof(float2);
+  return ((sizeof(SmemC) + 127) & ~size_t(127)) + 128 + (size_t)kTmaStages * 2 * kTileBytes;
 }
 
 template <int FAMILY, class Op>

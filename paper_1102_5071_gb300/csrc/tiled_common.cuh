@@ -62,4 +62,108 @@ __device__ __forceinline__ void workers_sync(int n) { asm volatile("bar.sync 1, 
 __device__ __forceinline__ void window_written_sync() { asm volatile("bar.sync 2;" ::: "memory"); }
 __device__ __forceinline__ void window_exchanged_sync() { asm volatile("bar.sync 3;" ::: "memory"); }
 
+// ------------------------------------------------------------------ TMA tile transfers
+// Tensor maps of the tiled apply (built on the host over the whole Krylov
+// basis; its vectors are contiguous, so the vector index continues the
+// outermost dimension; every coordinate non-negative, the innermost 0):
+//   window 0: (256, 2^(N-8) nvec) 8-byte elements, box (256, 16): tile t of
+//     vector v at (0, 16 t + 2^(N-8) v) = elements [4096 t, 4096 t + 4096);
+//   window w >= 1, c <= 8: (2^c, 2^(b0-c), 2^width, 2^(N-b0-width) nvec), box
+//     (2^c, 1, 2^width, 1) at (0, tl, 0, th + 2^(N-b0-width) v), tile
+//     t = (th << (b0 - c)) | tl;  c > 8: the low bits as (256, 2^(c-8)), box
+//     (256, 2^(c-8), 1, 2^width, 1) at (0, 0, tl, 0, th + ...).
+//   Shared memory holds the box with dimension 0 fastest: slot
+//   (j & (2^c - 1)) | (window bits << c), the slot order of tile_x.
+constexpr int kTmaMapBytes = 128;    // sizeof(CUtensorMap)
+constexpr int kTmaStages = 3;        // tiles in flight per CTA
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// Make mbarrier.init visible to the other threads and to the async proxy (then a CTA barrier).
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Order this thread's generic-proxy accesses with later async-proxy (TMA) ones.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* map, int c0, int c1, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const void* map, int c0, int c1, int c2, int c3,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+      ::"r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_5d(void* dst, const void* map, int c0, int c1, int c2, int c3, int c4,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+      ::"r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_2d(const void* map, int c0, int c1, const void* src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];"
+               ::"l"(map), "r"(c0), "r"(c1), "r"(smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void tma_store_4d(const void* map, int c0, int c1, int c2, int c3, const void* src) {
+  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];"
+               ::"l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void tma_store_5d(const void* map, int c0, int c1, int c2, int c3, int c4,
+                                             const void* src) {
+  asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];"
+               ::"l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Wait until at most one committed store group still reads shared memory.
+__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+// Wait until every committed store group has completed its writes.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Tile t of window W (first: window 0) of vector v of an N-site chain: TMA
+// load into dst (bar completes with the bytes) and TMA store from src.
+__device__ __forceinline__ void tile_load(void* dst, const void* map, bool first, const TileWin& W, int N, int t,
+                                          int v, unsigned long long* bar) {
+  if (first) {
+    tma_load_2d(dst, map, 0, (t << 4) + v * (1 << (N - 8)), bar);
+    return;
+  }
+  const int nb = W.b0 - W.c, tl = t & ((1 << nb) - 1), th = (t >> nb) + v * (1 << (N - W.b0 - W.width));
+  if (W.c <= 8) tma_load_4d(dst, map, 0, tl, 0, th, bar);
+  else tma_load_5d(dst, map, 0, 0, tl, 0, th, bar);
+}
+__device__ __forceinline__ void tile_store(const void* map, bool first, const TileWin& W, int N, int t, int v,
+                                           const void* src) {
+  if (first) {
+    tma_store_2d(map, 0, (t << 4) + v * (1 << (N - 8)), src);
+    return;
+  }
+  const int nb = W.b0 - W.c, tl = t & ((1 << nb) - 1), th = (t >> nb) + v * (1 << (N - W.b0 - W.width));
+  if (W.c <= 8) tma_store_4d(map, 0, tl, 0, th, src);
+  else tma_store_5d(map, 0, 0, tl, 0, th, src);
+}
+
 }  // namespace cfet
