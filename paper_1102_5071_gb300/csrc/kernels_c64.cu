@@ -455,83 +455,138 @@ __device__ void c_tiled_pass(const TmaPass& T, const OpSpinC& op, const CConst& 
     *T.phase ^= 1u << st;
     if (!tile_wait(T.bar + st, par, T.status, T.timeout_ns)) *T.fail = 1;
     if (!*T.fail) {
-      for (int j = tid; j < kTileElems; j += nworkers) {
-        float ur, ui, hr = 0.f, hi = 0.f, fr = 0.f, fi = 0.f;
+      // Element pairs (2 jp, 2 jp + 1) of the tile: a flip or hop of any bit
+      // above bit 0 moves both elements of a pair to the two elements of
+      // another pair, so each such neighbour pair is one 16-byte load; the
+      // flip of bit 0 swaps the pair, and the hop of bond (0, 1) takes one
+      // element of pair jp ^ 1.
+      const float4* cur4 = reinterpret_cast<const float4*>(cur);
+      float4* acur4 = reinterpret_cast<float4*>(acur);
+      for (int jp = tid; jp < kTileElems / 2; jp += nworkers) {
+        const int j = 2 * jp;
+        const float4 v = cur4[jp];
+        float ur0, ui0, ur1, ui1;
+        float hr0 = 0.f, hi0 = 0.f, hr1 = 0.f, hi1 = 0.f, fr0 = 0.f, fi0 = 0.f, fr1 = 0.f, fi1 = 0.f;
         if (FIRST) {
-          const int x = (t << kTileBits) | j;
+          const int x = (t << kTileBits) | j;  // even
           const int L = op.lo_bits;
-          const float dz = __ldg(op.dz_lo + (x & ((1 << L) - 1))) + __ldg(op.dz_hi + (x >> (L - 1)));
-          const float d = c.cz * dz;
-          const float2 v = cur[j];
-          ur = d * v.x;
-          ui = d * v.y;
+          const float2 dlo = *reinterpret_cast<const float2*>(op.dz_lo + (x & ((1 << L) - 1)));
+          const float dhi = __ldg(op.dz_hi + (x >> (L - 1)));
+          const float d0 = c.cz * (dlo.x + dhi), d1 = c.cz * (dlo.y + dhi);
+          ur0 = d0 * v.x;
+          ui0 = d0 * v.y;
+          ur1 = d1 * v.z;
+          ui1 = d1 * v.w;
           const unsigned anti = ((unsigned)j ^ ((unsigned)j >> 1)) & ((1u << (kTileBits - 1)) - 1u);
+          {  // bond (0, 1): element 0 hops when bit 1 is set, element 1 when it is clear
+            const float4 w = cur4[jp ^ 1];
+            if ((j >> 1) & 1) {
+              hr0 += w.z;
+              hi0 += w.w;
+            } else {
+              hr1 += w.x;
+              hi1 += w.y;
+            }
+          }
 #pragma unroll
-          for (int i = 0; i < kTileBits - 1; ++i)
+          for (int i = 1; i < kTileBits - 1; ++i)
             if ((anti >> i) & 1u) {
-              const float2 wv = cur[j ^ (3 << i)];
-              hr += wv.x;
-              hi += wv.y;
+              const float4 w = cur4[jp ^ (3 << (i - 1))];
+              hr0 += w.x;
+              hi0 += w.y;
+              hr1 += w.z;
+              hi1 += w.w;
             }
           if (op.uniform) {
+            fr0 = v.z;  // flip of bit 0
+            fi0 = v.w;
+            fr1 = v.x;
+            fi1 = v.y;
 #pragma unroll
-            for (int i = 0; i < kTileBits; ++i) {
-              const float2 wv = cur[j ^ (1 << i)];
-              fr += wv.x;
-              fi += wv.y;
+            for (int i = 1; i < kTileBits; ++i) {
+              const float4 w = cur4[jp ^ (1 << (i - 1))];
+              fr0 += w.x;
+              fi0 += w.y;
+              fr1 += w.z;
+              fi1 += w.w;
             }
           } else {
+            ur0 = fmaf(bx[0], v.z, ur0);
+            ui0 = fmaf(bx[0], v.w, ui0);
+            ur1 = fmaf(bx[0], v.x, ur1);
+            ui1 = fmaf(bx[0], v.y, ui1);
 #pragma unroll
-            for (int i = 0; i < kTileBits; ++i) {
-              const float2 wv = cur[j ^ (1 << i)];
-              ur = fmaf(bx[i], wv.x, ur);
-              ui = fmaf(bx[i], wv.y, ui);
+            for (int i = 1; i < kTileBits; ++i) {
+              const float4 w = cur4[jp ^ (1 << (i - 1))];
+              ur0 = fmaf(bx[i], w.x, ur0);
+              ui0 = fmaf(bx[i], w.y, ui0);
+              ur1 = fmaf(bx[i], w.z, ur1);
+              ui1 = fmaf(bx[i], w.w, ui1);
             }
           }
           if (c.use_prev) {
-            const float2 wv = acur[j];
-            ur = fmaf(c.cp, wv.x, ur);
-            ui = fmaf(c.cp, wv.y, ui);
+            const float4 w = acur4[jp];
+            ur0 = fmaf(c.cp, w.x, ur0);
+            ui0 = fmaf(c.cp, w.y, ui0);
+            ur1 = fmaf(c.cp, w.z, ur1);
+            ui1 = fmaf(c.cp, w.w, ui1);
           }
         } else {
-          const float2 a = acur[j];
-          ur = a.x;
-          ui = a.y;
+          // the window's bits are slot bits c .. c + width - 1, pair bits c - 1 ..
+          const float4 a = acur4[jp];
+          ur0 = a.x;
+          ui0 = a.y;
+          ur1 = a.z;
+          ui1 = a.w;
           const unsigned jh = (unsigned)j >> W.c;  // bits b0 .. b0+width-1 of x
           const unsigned anti = (jh ^ (jh >> 1)) & ((1u << (W.width - 1)) - 1u);
           for (int i = 0; i < W.width - 1; ++i)
             if ((anti >> i) & 1u) {
-              const float2 wv = cur[j ^ (3 << (W.c + i))];
-              hr += wv.x;
-              hi += wv.y;
+              const float4 w = cur4[jp ^ (3 << (W.c - 1 + i))];
+              hr0 += w.x;
+              hi0 += w.y;
+              hr1 += w.z;
+              hi1 += w.w;
             }
           if (op.uniform) {
             for (int i = 1; i < W.width; ++i) {
-              const float2 wv = cur[j ^ (1 << (W.c + i))];
-              fr += wv.x;
-              fi += wv.y;
+              const float4 w = cur4[jp ^ (1 << (W.c - 1 + i))];
+              fr0 += w.x;
+              fi0 += w.y;
+              fr1 += w.z;
+              fi1 += w.w;
             }
           } else {
             for (int i = 1; i < W.width; ++i) {
-              const float2 wv = cur[j ^ (1 << (W.c + i))];
-              ur = fmaf(bx[W.b0 + i], wv.x, ur);
-              ui = fmaf(bx[W.b0 + i], wv.y, ui);
+              const float4 w = cur4[jp ^ (1 << (W.c - 1 + i))];
+              const float b = bx[W.b0 + i];
+              ur0 = fmaf(b, w.x, ur0);
+              ui0 = fmaf(b, w.y, ui0);
+              ur1 = fmaf(b, w.z, ur1);
+              ui1 = fmaf(b, w.w, ui1);
             }
           }
         }
-        ur = fmaf(c.ch, hr, ur);
-        ui = fmaf(c.ch, hi, ui);
+        ur0 = fmaf(c.ch, hr0, ur0);
+        ui0 = fmaf(c.ch, hi0, ui0);
+        ur1 = fmaf(c.ch, hr1, ur1);
+        ui1 = fmaf(c.ch, hi1, ui1);
         if (op.uniform) {
-          ur = fmaf(c.cx, fr, ur);
-          ui = fmaf(c.cx, fi, ui);
+          ur0 = fmaf(c.cx, fr0, ur0);
+          ui0 = fmaf(c.cx, fi0, ui0);
+          ur1 = fmaf(c.cx, fr1, ur1);
+          ui1 = fmaf(c.cx, fi1, ui1);
         }
-        acur[j] = make_float2(ur, ui);  // the own element only: read above by this thread
+        acur4[jp] = make_float4(ur0, ui0, ur1, ui1);  // the own pair only: read above by this thread
         if (LAST) {
-          const float2 v = cur[j];
-          ff_add_prod(s0, c0, v.x, ur);
-          ff_add_prod(s0, c0, v.y, ui);
-          ff_add_prod(s1, c1, ur, ur);
-          ff_add_prod(s1, c1, ui, ui);
+          ff_add_prod(s0, c0, v.x, ur0);
+          ff_add_prod(s0, c0, v.y, ui0);
+          ff_add_prod(s0, c0, v.z, ur1);
+          ff_add_prod(s0, c0, v.w, ui1);
+          ff_add_prod(s1, c1, ur0, ur0);
+          ff_add_prod(s1, c1, ui0, ui0);
+          ff_add_prod(s1, c1, ur1, ur1);
+          ff_add_prod(s1, c1, ui1, ui1);
         }
       }
     }
