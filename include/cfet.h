@@ -600,6 +600,36 @@ cfet_status cfet_probe_copy_gbs(void* a, void* b, int64_t bytes, int32_t reps, v
  * is inconsistent.                                                          */
 cfet_status cfet_selftest_tiling(int32_t nsites, int32_t tile_bits, int64_t* checked);
 
+/* Host-only checks (no device needed) of the scalar helpers that the
+ * control warps of the persistent kernels use instead of FP64 instructions
+ * (the same source compiled for the host).
+ *
+ * cfet_selftest_i128_to_double: out[i] = (hi[i] 2^64 + lo[i]) 2^shift, the
+ * two's-complement 128-bit integers rounded to the nearest double (ties to
+ * even), for i < n; shift in [-200, 200].  This is how the exact 128-bit
+ * reductions of the fixed-point kernels become FP64 values.
+ *
+ * cfet_selftest_krylov_bounds: for the k x k real symmetric tridiagonal T_k
+ * with diagonal a[0..k-1] and couplings b[0..k-2] (the Lanczos matrix of
+ * Sec. 8.1) and the step ts:
+ *   log2_bounds[0] = a certified lower bound of log2 |e_{k-1}^T exp(-i ts T_k) e_0|
+ *     (leading Taylor term |ts|^{k-1} prod b_j / (k-1)! times
+ *     2 - exp(g), g = |ts| D + (|ts| B)^2 / k, D = half the spread of the
+ *     diagonal, B = max b_j, all roundings taken off), or -1e30 when that bound
+ *     is void; log2_bounds[1] = a certified upper bound (the leading term times
+ *     exp(g)), or 1e30; the kernels reject k without evaluating the
+ *     exponential when beta0 beta_k times the lower bound exceeds the
+ *     estimate's threshold, and skip the FP32 screen when the upper bound
+ *     already meets it;
+ *   *gate = 1 when |ts| w <= 2k, 0 when |ts| w > 2k for certain (w the
+ *     Gershgorin width of T_k, the gate of the estimate), -1 when the FP32
+ *     evaluation cannot decide (the kernels then evaluate it in FP64).
+ * k in [1, 64]; CFET_EINVAL otherwise or for NULL pointers.                 */
+cfet_status cfet_selftest_i128_to_double(const uint64_t* lo, const int64_t* hi, int64_t n, int32_t shift,
+                                         double* out);
+cfet_status cfet_selftest_krylov_bounds(int32_t k, const double* a, const double* b, double ts, double* log2_bounds,
+                                        int32_t* gate);
+
 /* Dimension and drive-operator count of ctx (for bindings).                 */
 int64_t cfet_dim(const cfet_ctx* ctx);
 int32_t cfet_num_drives(const cfet_ctx* ctx);

@@ -358,7 +358,8 @@ __device__ void run_instance(const BParams& P, int ii, int part, int nparts, boo
           if (w0) {
             const double b = sqrt(bsum);
             const double prev_b = it > 1 ? S.beta[it - 1] : 0.0;
-            const bool breakdown = b <= 1e-13 * (fabs(S.alpha[it]) + prev_b + 1.0);
+            const bool breakdown =
+                sb_no_breakdown(b, S.alpha[it], prev_b) != 1 && b <= 1e-13 * (fabs(S.alpha[it]) + prev_b + 1.0);
             if (lane == 0) {
               S.beta[it] = b;
               S.scale[it + 1] = 1.0 / b;
@@ -372,10 +373,15 @@ __device__ void run_instance(const BParams& P, int ii, int part, int nparts, boo
               acc_flag = (it == P.m_max) || breakdown;
             } else if (breakdown) {
               acc_flag = 1;
-            } else if (it >= P.m_min && fabs(remaining) * gersh_width(it, S.alpha + 1, S.beta + 1) <= 2.0 * it) {
-              small_expm_e1(it, S.alpha + 1, S.beta + 1, remaining, S.yr, S.yi, S.tr, S.ti);
-              err = beta0 * b * hypot(S.yr[it - 1], S.yi[it - 1]);
-              acc_flag = err <= P.tol * remaining / P.tau;
+            } else if (it >= P.m_min && gersh_gate(it, S.alpha + 1, S.beta + 1, remaining)) {
+              const double thr = P.tol * remaining / P.tau;
+              if (krylov_lead_rejects(it, S.alpha + 1, S.beta + 1, remaining, beta0 * b, thr)) {
+                err = 2.0 * thr + 1e-300;
+              } else {
+                small_expm_e1(it, S.alpha + 1, S.beta + 1, remaining, S.yr, S.yi, S.tr, S.ti);
+                err = beta0 * b * hypot(S.yr[it - 1], S.yi[it - 1]);
+                acc_flag = err <= thr;
+              }
             }
             if (lane == 0) {
               S.accept_now = acc_flag;

@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "cfet_internal.h"
+#include "scalar_bounds.cuh"
 #include "tiled_common.cuh"
 
 using namespace cfet;
@@ -40,6 +41,11 @@ struct cfet_ctx {
   int nV = 0;
   cfet_options opt{};
   int grid = 1, block = 256;
+  // one-CTA fixed-point launches with the Krylov basis in shared memory: the
+  // CTA's size (one worker thread per element, at most block - 32, plus the
+  // control warp)
+  bool small_fx = false;
+  int small_block = 0;
   int precision = CFET_PREC_FX;
   std::string err;
   // drives
@@ -258,10 +264,12 @@ cfet_status launch_chunk(cfet_ctx* ctx, const PropParams& base, long long e0, lo
     e = ctx->family == kFamilySpin  ? launch_cheb_spin_fx(p, ctx->spin_fx, ctx->grid, cheb_threads(ctx->block - 32), s)
         : ctx->family == kFamilyCsr ? launch_cheb_csr_fx(p, ctx->csr_fx, ctx->grid, cheb_threads(ctx->block - 32), s)
                                     : launch_cheb_dia_fx(p, ctx->dia_fx, ctx->grid, cheb_threads(ctx->block - 32), s);
-  else if (ctx->precision == CFET_PREC_FX)
-    e = ctx->family == kFamilySpin  ? launch_propagate_spin_fx(p, ctx->spin_fx, ctx->grid, ctx->block, s)
-        : ctx->family == kFamilyCsr ? launch_propagate_csr_fx(p, ctx->csr_fx, ctx->grid, ctx->block, s)
-                                    : launch_propagate_dia_fx(p, ctx->dia_fx, ctx->grid, ctx->block, s);
+  else if (ctx->precision == CFET_PREC_FX) {
+    const int b = ctx->small_fx ? ctx->small_block : ctx->block;
+    e = ctx->family == kFamilySpin  ? launch_propagate_spin_fx(p, ctx->spin_fx, ctx->grid, b, s)
+        : ctx->family == kFamilyCsr ? launch_propagate_csr_fx(p, ctx->csr_fx, ctx->grid, b, s)
+                                    : launch_propagate_dia_fx(p, ctx->dia_fx, ctx->grid, b, s);
+  }
   else if (ctx->precision == CFET_PREC_C64)
     e = ctx->family == kFamilySpin  ? launch_propagate_spin_c64(p, ctx->spin_c, ctx->grid, ctx->block, s)
         : ctx->family == kFamilyCsr ? launch_propagate_csr_c64(p, ctx->csr_c, ctx->grid, ctx->block, s)
@@ -325,6 +333,7 @@ PropParams base_params(cfet_ctx* ctx, double2* psi, double tau, double tol) {
   p.tiled = ctx->tiled ? 1 : 0;
   p.tmaps = ctx->d_tmaps;
   p.reorth = ctx->opt.reorth;
+  p.small = ctx->small_fx ? 1 : 0;
   return p;
 }
 
@@ -1031,6 +1040,8 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
     ctx->spin_fx.DZ_lo = ctx->d_DZ;
     ctx->spin_fx.DZ_hi = ctx->d_DZ + nlo;
     ctx->spin_fx.maxdz = maxdz;
+    ctx->spin_fx.nbond = (double)(N - 1);
+    ctx->spin_fx.nsite = (double)N;
     ctx->spin_fx.J2 = 2.0 * H0->J;
     ctx->spin_fx.xf = ctx->d_xf;
     // FP32 diagonal tables of the mixed-precision path
@@ -1186,6 +1197,14 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
   if (ctl_warp && ctx->grid > kMaxCtlGrid) ctx->grid = kMaxCtlGrid;  // record exchange limit
   if (ctx->grid < 1) ctx->grid = 1;
 
+  if (ctx->precision == CFET_PREC_FX && o.expm == CFET_EXPM_KRYLOV && ctx->grid == 1 && !ctx->tiled) {
+    // a single CTA: the basis fits in its shared memory for small problems
+    const size_t sb = fx_small_smem_bytes(dim, o.m_max);
+    if (sb > 0 && fx_small_prepare(sb) == 0) {
+      ctx->small_fx = true;
+      ctx->small_block = 32 + std::min(ctx->block - 32, (dim + 31) / 32 * 32);
+    }
+  }
   if (ctx->precision == CFET_PREC_FX)  // basis q_1..q_{m_max+1}; the Chebyshev kernel's three vectors
     CKC(cudaMalloc(&ctx->d_qbasis, (size_t)std::max(o.m_max + 1, 3) * dim * sizeof(longlong2)),
         "cudaMalloc(Krylov basis)");
@@ -1695,6 +1714,34 @@ cfet_status cfet_selftest_tiling(int32_t nsites, int32_t tile_bits, int64_t* che
     return fail(nullptr, CFET_EINVAL, "tiling self-test: tile_bits 11 or 12, nsites in [tile_bits, 27]");
   const bool ok = tile_bits == 11 ? check_tiling<11>(nsites, checked) : check_tiling<12>(nsites, checked);
   if (!ok) return fail(nullptr, CFET_ECUDA, "tiling self-test: window tiling inconsistent");
+  return CFET_OK;
+}
+
+cfet_status cfet_selftest_i128_to_double(const uint64_t* lo, const int64_t* hi, int64_t n, int32_t shift,
+                                         double* out) {
+  if (!lo || !hi || !out || n < 0 || shift < -200 || shift > 200)
+    return fail(nullptr, CFET_EINVAL, "selftest: lo, hi, out required, n >= 0, shift in [-200, 200]");
+  for (int64_t i = 0; i < n; ++i) out[i] = sb_i128_to_double(lo[i], hi[i], shift);
+  return CFET_OK;
+}
+
+cfet_status cfet_selftest_krylov_bounds(int32_t k, const double* a, const double* b, double ts, double* log2_bounds,
+                                        int32_t* gate) {
+  if (k < 1 || k > kMaxKrylov || !a || (k > 1 && !b) || !log2_bounds || !gate)
+    return fail(nullptr, CFET_EINVAL, "selftest: k in [1, 64], a, b, log2_bounds and gate required");
+  LeadAcc s;
+  sb_lead_init(s);
+  GershAcc g;
+  sb_gersh_init(g);
+  for (int r = 0; r < k; ++r) {
+    sb_lead_row(s, r, k, a, b);
+    sb_gersh_row(g, r, k, a, b);
+  }
+  float lo, hi;
+  sb_lead_log2_bounds(s, k, ts, lo, hi);
+  log2_bounds[0] = lo;
+  log2_bounds[1] = hi;
+  *gate = sb_gersh_gate(g, k, ts);
   return CFET_OK;
 }
 

@@ -126,6 +126,7 @@ struct OpSpinFx {
   const long long* DZ_hi;
   double maxdz;           // bound of |dz(x)| in real units
   double J2;              // 2 J
+  double nbond, nsite;    // N - 1 and N as doubles (no conversion on the control path)
   const double* xf;       // [nV * N] per-field per-site X coefficients
 };
 
@@ -191,7 +192,7 @@ struct PropParams {
   int m_min, m_max, max_substeps;
   int tiled;             // spin chains: window-tiled apply (complex64 and fixed-point kernels)
   int reorth;            // FP64 kernel: full re-orthogonalisation of every Lanczos vector
-  int pad1;
+  int small;             // fixed-point kernel, one CTA: the Krylov basis lives in shared memory
   // decisions (device arrays, nullable)
   const int* f_nsub; const int* f_k; const int* f_h;
   int* r_nsub; int* r_k; int* r_h; long long r_cap;
@@ -295,6 +296,10 @@ int launch_propagate_spin_fx(const PropParams& p, const OpSpinFx& op, int grid, 
 int launch_propagate_dia_fx(const PropParams& p, const OpDiaFx& op, int grid, int block, void* stream);
 int launch_propagate_csr_fx(const PropParams& p, const OpCsrFx& op, int grid, int block, void* stream);
 int max_coresident_blocks_fx(int family, int block, bool tiled);
+// One-CTA fixed-point launches with the Krylov basis in shared memory.
+constexpr size_t kFxSmallSmemMax = 200 * 1024;
+size_t fx_small_smem_bytes(int dim, int m_max);
+int fx_small_prepare(size_t bytes);
 int launch_propagate_spin_c64(const PropParams& p, const OpSpinC& op, int grid, int block, void* stream);
 int launch_propagate_dia_c64(const PropParams& p, const OpDiaC& op, int grid, int block, void* stream);
 int launch_propagate_csr_c64(const PropParams& p, const OpCsrC& op, int grid, int block, void* stream);

@@ -8,6 +8,7 @@
 #include <cmath>
 
 #include "cfet_internal.h"
+#include "scalar_bounds.cuh"
 
 namespace cfet {
 
@@ -316,34 +317,51 @@ __constant__ double kInvN[kSmallTaylorTerms + 1] = {
 static __device__ void small_expm_e1(int k, const double* a, const double* b, double ts, double* yr, double* yi,
                                      double* tr, double* ti) {
   const int lane = threadIdx.x & 31;
-  double lo = 1e300, hi = -1e300;
+  // Spectral interval of T_k from FP32 Gershgorin bounds of the truncated
+  // entries, widened by their error: the shift and the number of terms only
+  // need bounds.  Without a shift (|ts| max |lambda| <= 1/2) the phase
+  // e^{-i ts sig} and its sincos drop out.
+  GershAcc g;
+  sb_gersh_init(g);
+  int bad = 0;
   for (int r = lane; r < k; r += 32) {
-    const double rad = (r > 0 ? fabs(b[r - 1]) : 0.0) + (r < k - 1 ? fabs(b[r]) : 0.0);
-    lo = fmin(lo, a[r] - rad);
-    hi = fmax(hi, a[r] + rad);
+    sb_gersh_row(g, r, k, a, b);
+    bad |= sb_nonfinite(a[r]) | (r < k - 1 ? sb_nonfinite(b[r]) : 0);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    GershAcc t;
+    t.lo = __shfl_xor_sync(0xffffffffu, g.lo, o);
+    t.hi = __shfl_xor_sync(0xffffffffu, g.hi, o);
+    t.amag = __shfl_xor_sync(0xffffffffu, g.amag, o);
+    t.bmag = __shfl_xor_sync(0xffffffffu, g.bmag, o);
+    sb_gersh_merge(g, t);
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
   }
-  const double sig = 0.5 * (lo + hi), rho = 0.5 * (hi - lo);
-  // number of Taylor substeps, bounded: a non-finite spread gives S = 1 (the
-  // result is then non-finite and rejected by the caller), a huge one 65536
-  const double sr = fabs(ts) * rho;
+  const float werr = 0x1p-19f * (g.amag + 2.0f * g.bmag) + 0x1p-21f * (fabsf(g.lo) + fabsf(g.hi));
+  const float lo32 = g.lo - werr, hi32 = g.hi + werr, mag = fmaxf(fabsf(lo32), fabsf(hi32));
+  const float tsa = sb_abs_up(ts) * (1.0f + 0x1p-20f);
+  const bool noshift = tsa * mag <= 0.5f;
+  // half-width about sig (sig rounded to a float: 2^-24 mag more)
+  const float rho32 = noshift ? mag : (0.5f * (hi32 - lo32) * (1.0f + 0x1p-20f) + 0x1p-23f * mag);
+  const double sig = noshift ? 0.0 : sb_f2d(0.5f * (lo32 + hi32));
+  const float sr32 = tsa * rho32 * (1.0f + 0x1p-20f);
+  // number of Taylor substeps, bounded: non-finite entries give S = 1 (the
+  // result is then non-finite and rejected by the caller), a huge spread 65536
   int S = 1;
-  if (sr == sr) S = sr < 65536.0 ? (int)ceil(sr) : 65536;
+  if (!bad) S = sr32 < 65536.0f ? (int)ceilf(sr32) : 65536;
   if (S < 1) S = 1;
-  const double hstep = ts / S;
-  const double x = sr / S;
-  const int nterms = x > 0.5 ? kSmallTaylorTerms : (x > 0.25 ? 15 : (x > 0.1 ? 12 : 10));
+  const double hstep = S == 1 ? ts : ts / S;
+  const float x = bad ? 1.0f : sr32 / (float)S;
+  const int nterms = x > 0.5f ? kSmallTaylorTerms : (x > 0.25f ? 15 : (x > 0.1f ? 12 : 10));
   // rows owned by this lane: shifted diagonal and couplings in registers
   const int r0 = lane, r1 = lane + 32;
   const bool on0 = r0 < k, on1 = r1 < k;
   const double d0 = on0 ? a[r0] - sig : 0.0, d1 = on1 ? a[r1] - sig : 0.0;
   const double bl0 = (on0 && r0 > 0) ? b[r0 - 1] : 0.0, br0 = (on0 && r0 < k - 1) ? b[r0] : 0.0;
   const double bl1 = on1 ? b[r1 - 1] : 0.0, br1 = (on1 && r1 < k - 1) ? b[r1] : 0.0;
-  if (sr > kChebyshevFrom && sr < 4096.0) {
+  if (!bad && !noshift && sr32 > (float)kChebyshevFrom && sr32 < 4096.0f) {
+    const double rho = sb_f2d(rho32), sr = fabs(ts) * rho;
     const double a_ = sr, inv_a = 1.0 / a_, inv_rho = 1.0 / rho;
     const bool neg = ts < 0.0;  // (-i s)^n with s = sign(ts)
     const double x0 = d0 * inv_rho, xl0 = bl0 * inv_rho, xr0 = br0 * inv_rho;
@@ -433,6 +451,11 @@ static __device__ void small_expm_e1(int k, const double* a, const double* b, do
         acc += t;
       }
     }
+    if (noshift) {
+      if (on) (imag ? yi : yr)[r] = acc;
+      __syncwarp();
+      return;
+    }
     double sn, cs;
     sincos(ts * sig, &sn, &cs);
     const double ao = __shfl_xor_sync(0xffffffffu, acc, 16);
@@ -475,8 +498,8 @@ static __device__ void small_expm_e1(int k, const double* a, const double* b, do
       __syncwarp();
     }
   }
-  double sn, cs;
-  sincos(ts * sig, &sn, &cs);
+  double sn = 0.0, cs = 1.0;
+  if (!noshift) sincos(ts * sig, &sn, &cs);
   // multiply by e^{-i ts sig} = cs - i sn
   if (on0) { yr[r0] = ar0 * cs + ai0 * sn; yi[r0] = ai0 * cs - ar0 * sn; }
   if (on1) { yr[r1] = ar1 * cs + ai1 * sn; yi[r1] = ai1 * cs - ar1 * sn; }
@@ -558,6 +581,79 @@ static __device__ double gersh_width(int k, const double* a, const double* b) {
     hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
   }
   return hi - lo;
+}
+
+// |ts| gersh_width(k, a, b) <= 2k (the gate of the Krylov estimate), decided
+// in FP32 (sb_gersh_gate) unless that cannot be certain; whole warp,
+// warp-uniform result.
+static __device__ bool gersh_gate(int k, const double* a, const double* b, double ts) {
+  const int lane = threadIdx.x & 31;
+  GershAcc s;
+  sb_gersh_init(s);
+  for (int r = lane; r < k; r += 32) sb_gersh_row(s, r, k, a, b);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    GershAcc t;
+    t.lo = __shfl_xor_sync(0xffffffffu, s.lo, o);
+    t.hi = __shfl_xor_sync(0xffffffffu, s.hi, o);
+    t.amag = __shfl_xor_sync(0xffffffffu, s.amag, o);
+    t.bmag = __shfl_xor_sync(0xffffffffu, s.bmag, o);
+    sb_gersh_merge(s, t);
+  }
+  const int g = sb_gersh_gate(s, k, ts);
+  if (g >= 0) return g == 1;
+  return fabs(ts) * gersh_width(k, a, b) <= 2.0 * k;
+}
+
+// Certain rejection of Krylov dimension k by the estimate
+// scale |y_{k-1}| > thr from the leading Taylor term (sb_lead_decide), rows
+// on lanes; whole warp, warp-uniform result.
+static __device__ bool krylov_lead_rejects(int k, const double* a, const double* b, double ts, double scale,
+                                           double thr) {
+  const int lane = threadIdx.x & 31;
+  LeadAcc s;
+  sb_lead_init(s);
+  for (int r = lane; r < k; r += 32) sb_lead_row(s, r, k, a, b);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    LeadAcc t;
+    t.slog = __shfl_xor_sync(0xffffffffu, s.slog, o);
+    t.sabs = __shfl_xor_sync(0xffffffffu, s.sabs, o);
+    t.bmax = __shfl_xor_sync(0xffffffffu, s.bmax, o);
+    t.amin = __shfl_xor_sync(0xffffffffu, s.amin, o);
+    t.amax = __shfl_xor_sync(0xffffffffu, s.amax, o);
+    t.amag = __shfl_xor_sync(0xffffffffu, s.amag, o);
+    t.bad = __shfl_xor_sync(0xffffffffu, s.bad, o);
+    sb_lead_merge(s, t);
+  }
+  return sb_lead_decide(s, k, ts, scale, 1.0, thr) == 0;
+}
+
+// Running FP32 bounds of T_it for the control warps that keep them in shared
+// memory (members lead, gfull, alpha[1..], beta[1..]): one lane adds row
+// it - 1 (a = alpha[it], left coupling beta[it - 1]) and completes row it - 2,
+// and returns the FP32 gate decision for the step ts (sb_gersh_gate).
+template <class Sm>
+__device__ int krylov_bounds_update(Sm& S, int it, double ts) {
+  if (it == 1) {
+    sb_lead_init(S.lead);
+    sb_gersh_init(S.gfull);
+  } else {
+    sb_lead_coupling(S.lead, it - 2, S.beta[it - 1]);
+    sb_gersh_add(S.gfull, S.alpha[it - 1], it > 2 ? S.beta[it - 2] : 0.0, S.beta[it - 1]);
+  }
+  sb_lead_diag(S.lead, S.alpha[it]);
+  GershAcc g = S.gfull;
+  sb_gersh_add(g, S.alpha[it], it > 1 ? S.beta[it - 1] : 0.0, 0.0);
+  return sb_gersh_gate(g, it, ts);
+}
+// The estimate's certain decision (sb_lead_decide) from running bounds,
+// evaluated by lane 0 and returned to the whole warp.
+__device__ __forceinline__ int krylov_lead_decide(const LeadAcc& lead, int k, double ts, double beta0, double betak,
+                                                  double thr) {
+  int d = -1;
+  if ((threadIdx.x & 31) == 0) d = sb_lead_decide(lead, k, ts, beta0, betak, thr);
+  return __shfl_sync(0xffffffffu, d, 0);
 }
 
 }  // namespace cfet

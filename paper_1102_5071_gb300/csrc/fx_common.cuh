@@ -11,6 +11,7 @@
 #include <cstdint>
 
 #include "cfet_internal.h"
+#include "scalar_bounds.cuh"
 
 namespace cfet {
 
@@ -34,14 +35,17 @@ __device__ __forceinline__ int fx_ilog2_up(double v) {
   const int e = (int)((b >> 52) & 0x7ff) - 1023;
   return ((b & 0xFFFFFFFFFFFFFLL) >= 0xFFFFFFFFFF000LL) ? e + 1 : e;
 }
-// Exponent E with bound < 2^(bits + E); a zero bound gives a very small E.
+// Exponent E with bound < 2^(bits + E); a zero, negative, tiny (< 2^-963)
+// or huge bound gives a very small E.  (Range checks on the bit pattern.)
 __device__ __forceinline__ int fx_exp_for(double bound, int bits) {
-  if (!(bound > 1e-290) || !(bound < 1e290)) return -960;
+  const long long b = __double_as_longlong(bound);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (b <= 0 || ex < 1023 - 963 || ex > 1023 + 963) return -960;
   return fx_ilog2_up(bound) - (bits - 1);
 }
 // Left shift that brings a value of magnitude <= a (a >= 1) to < 2^62.
 __device__ __forceinline__ int fx_norm_shift(double a) {
-  if (!(a >= 1.0)) return 0;
+  if (__double_as_longlong(a) < 0x3FF0000000000000LL) return 0;  // a < 1 (or negative)
   const int p = 61 - fx_ilog2_up(a);
   return p < 0 ? 0 : (p > 61 ? 61 : p);
 }
@@ -125,9 +129,9 @@ __device__ __forceinline__ void fx_warp_reduce(unsigned long long& lo, long long
     mx = mx > mx2 ? mx : mx2;
   }
 }
+// (hi 2^64 + lo) 2^kRedShift rounded to the nearest double, by integer operations.
 __device__ __forceinline__ double fx_i128_to_double(unsigned long long lo, long long hi) {
-  // (hi * 2^64 + lo) * 2^kRedShift
-  return fma(__ll2double_rn(hi), 18446744073709551616.0, __ull2double_rn(lo)) * (double)(1 << kRedShift);
+  return sb_i128_to_double(lo, hi, kRedShift);
 }
 
 

@@ -452,7 +452,8 @@ __global__ void __launch_bounds__(256) k_propagate(PropParams p, Op op) {
             const double t = sum_partials(part1);
             const double b = sqrt(t);
             const double prev_b = it > 1 ? S.beta[it - 1] : 0.0;
-            const bool breakdown = b <= 1e-13 * (fabs(S.alpha[it]) + prev_b + 1.0);
+            const bool breakdown =
+                sb_no_breakdown(b, S.alpha[it], prev_b) != 1 && b <= 1e-13 * (fabs(S.alpha[it]) + prev_b + 1.0);
             int acc_flag = 0;
             double err = 0.0;
             if (forced) {
@@ -461,14 +462,18 @@ __global__ void __launch_bounds__(256) k_propagate(PropParams p, Op op) {
               acc_flag = (it == p.m_max) || breakdown;
             } else if (breakdown) {
               acc_flag = 1;
-            } else if (it >= p.m_min &&
-                       fabs(remaining) * gersh_width(it, S.alpha + 1, S.beta + 1) <= 2.0 * it) {
+            } else if (it >= p.m_min && gersh_gate(it, S.alpha + 1, S.beta + 1, remaining)) {
               // T_it: diagonal alpha[1..it], off-diagonal beta[1..it-1]; the
               // estimate is evaluated only where Eq. (KryErr) applies
-              small_expm_e1(it, S.alpha + 1, S.beta + 1, remaining, S.yr, S.yi, S.tr, S.ti);
-              const double yk = hypot(S.yr[it - 1], S.yi[it - 1]);
-              err = beta0 * b * yk;
-              acc_flag = err <= p.tol * remaining / p.tau;
+              const double thr = p.tol * remaining / p.tau;
+              if (krylov_lead_rejects(it, S.alpha + 1, S.beta + 1, remaining, beta0 * b, thr)) {
+                err = 2.0 * thr + 1e-300;
+              } else {
+                small_expm_e1(it, S.alpha + 1, S.beta + 1, remaining, S.yr, S.yi, S.tr, S.ti);
+                const double yk = hypot(S.yr[it - 1], S.yi[it - 1]);
+                err = beta0 * b * yk;
+                acc_flag = err <= thr;
+              }
             }
             if (tid == 0) {
               S.beta[it] = b;

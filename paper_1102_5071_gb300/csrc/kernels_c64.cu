@@ -100,6 +100,8 @@ struct SmemC {
   int tma_fail;                  // tiled apply: a tile wait gave up
   double err_now, err_prev;
   double beta0;
+  LeadAcc lead;                  // running FP32 bounds of the current T_k for the estimate's screens
+  GershAcc gfull;                // rows whose couplings are all known
 };
 
 // ------------------------------------------------------------------ applies
@@ -374,10 +376,13 @@ __device__ void c_const_a(SmemC& S, const Op& op, int it) {
 // Error estimate of iteration k (control warp), with the FP32 screen of
 // fx_estimate: above thr without the FP64 small exponential when it can.
 __device__ double c_estimate(SmemC& S, int k, double ts, double thr) {
+  const int dec = krylov_lead_decide(S.lead, k, ts, S.beta0, S.beta[k], thr);
+  if (dec == 0) return 2.0 * thr + 1e-300;
   const double scale = S.beta0 * S.beta[k];
-  if (small_expm_rejects32(k, S.alpha + 1, S.beta + 1, ts, scale, thr)) return 2.0 * thr + 1e-300;
+  if (dec < 0 && small_expm_rejects32(k, S.alpha + 1, S.beta + 1, ts, scale, thr)) return 2.0 * thr + 1e-300;
   small_expm_e1(k, S.alpha + 1, S.beta + 1, ts, S.yr, S.yi, S.tr, S.ti);
-  return scale * hypot(S.yr[k - 1], S.yi[k - 1]);
+  const double yr = S.yr[k - 1], yi = S.yi[k - 1];
+  return scale * sqrt(fma(yr, yr, yi * yi));
 }
 
 // ------------------------------------------------------------------ tiled apply (large chains)
@@ -913,11 +918,15 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
             const double rb = wn > 0.0 ? rsqrt(wn) : 0.0;
             const double b = wn > 0.0 ? wn * rb : 0.0;
             const double prev_b = it > 1 ? S.beta[it - 1] : 0.0;
-            const bool breakdown = b <= 1e-13 * (fabs(S.alpha[it]) + prev_b + 1.0);
+            const bool breakdown =
+                sb_no_breakdown(b, S.alpha[it], prev_b) != 1 && b <= 1e-13 * (fabs(S.alpha[it]) + prev_b + 1.0);
+            int gate = -1;
             if (lane == 0) {
               S.beta[it] = b;
               S.scale[it + 1] = rb;
+              gate = krylov_bounds_update(S, it, remaining);
             }
+            gate = __shfl_sync(0xffffffffu, gate, 0);
             __syncwarp();
             int acc_flag = 0, pend_next = 0;
             double err = 0.0;
@@ -928,7 +937,8 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
             } else if (breakdown) {
               acc_flag = 1;
             } else if (it >= p.m_min &&
-                       fabs(remaining) * gersh_width(it, S.alpha + 1, S.beta + 1) <= 2.0 * it) {
+                       (gate >= 0 ? gate == 1
+                                  : fabs(remaining) * gersh_width(it, S.alpha + 1, S.beta + 1) <= 2.0 * it)) {
               if (it < klimit) {
                 pend_next = 1;  // estimate runs during the next apply
               } else {

@@ -83,6 +83,9 @@ struct SmemFx {
   int final_rec;
   double err_now, err_prev;
   double beta0;
+  // running FP32 bounds of the current T_k for the estimate's screens
+  LeadAcc lead;
+  GershAcc gfull;  // rows whose couplings are all known
 };
 
 // ------------------------------------------------------------------ control-warp helpers
@@ -116,6 +119,11 @@ __device__ bool fx_ctl_reduce(SmemFx& S, int NW, unsigned long long* part, unsig
   lo = __shfl_sync(0xffffffffu, lo, 0);
   hi = __shfl_sync(0xffffffffu, hi, 0);
   m = __shfl_sync(0xffffffffu, m, 0);
+  if (gridDim.x == 1) {  // nothing to exchange
+    sum = fx_i128_to_double(lo, hi);
+    mxi = m;
+    return true;
+  }
   const unsigned mine[6] = {(unsigned)lo, (unsigned)(lo >> 32), (unsigned)hi,
                             (unsigned)((unsigned long long)hi >> 32), (unsigned)m,
                             (unsigned)((unsigned long long)m >> 32)};
@@ -303,7 +311,7 @@ __device__ void fx_const_a_scalars(SmemFx& S, const Op& op, int it) {
     const double ch = cz * op.J2;
     // sum and max of |b_i s_k| from the per-stage sums of |b_i|
     const double bsum = fabs(sk) * S.bsum_raw, bmax = fabs(sk) * S.bmax_raw;
-    B += (fabs(cz) * op.maxdz + fabs(ch) * (op.N - 1) + bsum) * Akr;
+    B += (fabs(cz) * op.maxdz + fabs(ch) * op.nbond + bsum) * Akr;
     const int Eu = fx_exp_for(B, kFxBits);
     const Mant mcz = fx_mant(cz);
     const int ED = fx_exp_for(fabs(cz) * op.maxdz, 59);
@@ -312,13 +320,13 @@ __device__ void fx_const_a_scalars(SmemFx& S, const Op& op, int it) {
     c.s_diag = Eu - (ED - 3) - (Ek - c.pk) - 64;
     c.m_cz = fx_fold(mcz.m, c.s_d + c.s_diag);
     const Mant mh = fx_mant(ch);
-    c.ph = fx_norm_shift((op.N > 1 ? op.N - 1 : 1) * Ak);
+    c.ph = fx_norm_shift((op.N > 1 ? op.nbond : 1.0) * Ak);
     c.m_hop = mh.m;
     c.s_hop = Eu - mh.e - (Ek - c.ph) - 64;
     c.m_hop = fx_fold(c.m_hop, c.s_hop);
     if (op.uniform) {
       const Mant mx = fx_mant(S.bsite_raw[0] * sk);
-      c.px = fx_norm_shift(op.N * Ak);
+      c.px = fx_norm_shift(op.nsite * Ak);
       c.m_x = mx.m;
       c.s_x = Eu - mx.e - (Ek - c.px) - 64;
       c.m_x = fx_fold(c.m_x, c.s_x);
@@ -374,10 +382,13 @@ __device__ void fx_const_a(SmemFx& S, const Op& op, int it) {
 // err exceeds the threshold thr, the FP64 evaluation is skipped and a value
 // above thr is returned (S.yr/S.yi then stay untouched).
 __device__ double fx_estimate(SmemFx& S, int k, double ts, double thr) {
+  const int dec = krylov_lead_decide(S.lead, k, ts, S.beta0, S.beta[k], thr);
+  if (dec == 0) return 2.0 * thr + 1e-300;
   const double scale = S.beta0 * S.beta[k];
-  if (small_expm_rejects32(k, S.alpha + 1, S.beta + 1, ts, scale, thr)) return 2.0 * thr + 1e-300;
+  if (dec < 0 && small_expm_rejects32(k, S.alpha + 1, S.beta + 1, ts, scale, thr)) return 2.0 * thr + 1e-300;
   small_expm_e1(k, S.alpha + 1, S.beta + 1, ts, S.yr, S.yi, S.tr, S.ti);
-  return scale * hypot(S.yr[k - 1], S.yi[k - 1]);
+  const double yr = S.yr[k - 1], yi = S.yi[k - 1];
+  return scale * sqrt(fma(yr, yr, yi * yi));
 }
 
 // ------------------------------------------------------------------ the kernel
@@ -433,7 +444,9 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
   int max_k = 0;
   double max_err = 0.0;
 
-  auto Q = [&](int i) -> longlong2* { return p.qbasis + (size_t)(i - 1) * dim; };
+  // one-CTA launches of small problems keep the basis in shared memory
+  longlong2* const qb = p.small ? tbuf : p.qbasis;
+  auto Q = [&](int i) -> longlong2* { return qb + (size_t)(i - 1) * dim; };
 
   // ---------------- psi (complex128) -> q_1
   // pass 1: max |component| (as ordered bit patterns of |v|) and NaN/Inf detection
@@ -652,7 +665,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
               S.alpha[it] = alpha;
               // phase-B constants: w = u - alpha s_it q_it
               const double am = alpha * s_it;
-              const double Bw = fx_scale2(__ll2double_ru(mxi), S.Eu) + fabs(am) * fx_scale2(S.A[it], S.E[it]);
+              const double Bw = fx_scale2(sb_ll_to_double_up(mxi), S.Eu) + fabs(am) * fx_scale2(S.A[it], S.E[it]);
               const int Ew = fx_exp_for(Bw, kFxBits);
               const Mant ma = fx_mant(-am);
               const int pk = fx_norm_shift(S.A[it]);
@@ -662,7 +675,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
               S.pk_b = pk;
               S.s_a = Ew - ma.e - (S.E[it] - pk) - 64;
               S.m_a = fx_fold(ma.m, S.s_a);
-              if (__ll2double_ru(mxi) >= 1.152921504606846976e18) {  // 2^60: fixed-point range exceeded (not expected)
+              if (mxi >= (1LL << 60)) {  // fixed-point range exceeded (not expected)
                 atomicCAS(&st->status, 0, (int)CFET_ENAN);
                 S.abort_flag = 1;
               }
@@ -710,16 +723,20 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
               if (lane == 0) S.abort_flag = 1;
             } else {
               // beta and 1/beta from one reciprocal square root
-              const double rb = sum > 0.0 ? rsqrt(sum) : 0.0;
+              const double rb = __double_as_longlong(sum) > 0 ? rsqrt(sum) : 0.0;
               const double b = fx_scale2(sum * rb, S.Ew);
               const double prev_b = it > 1 ? S.beta[it - 1] : 0.0;
-              const bool breakdown = b <= 1e-13 * (fabs(S.alpha[it]) + prev_b + 1.0);
+              const bool breakdown =
+                  sb_no_breakdown(b, S.alpha[it], prev_b) != 1 && b <= 1e-13 * (fabs(S.alpha[it]) + prev_b + 1.0);
+              int gate = -1;
               if (lane == 0) {
                 S.beta[it] = b;
                 S.scale[it + 1] = fx_scale2(rb, -S.Ew);
                 S.E[it + 1] = S.Ew;
-                S.A[it + 1] = __ll2double_ru(mxi);
+                S.A[it + 1] = sb_ll_to_double_up(mxi);
+                gate = krylov_bounds_update(S, it, remaining);
               }
+              gate = __shfl_sync(0xffffffffu, gate, 0);
               __syncwarp();
               int acc_flag = 0, pend_next = 0;
               double err = 0.0;
@@ -730,7 +747,8 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
               } else if (breakdown) {
                 acc_flag = 1;
               } else if (it >= p.m_min &&
-                         fabs(remaining) * gersh_width(it, S.alpha + 1, S.beta + 1) <= 2.0 * it) {
+                         (gate >= 0 ? gate == 1
+                                    : fabs(remaining) * gersh_width(it, S.alpha + 1, S.beta + 1) <= 2.0 * it)) {
                 if (it < klimit) {
                   pend_next = 1;  // estimate runs during the next apply
                 } else {
@@ -916,7 +934,7 @@ static int launch_prop_fx(const PropParams& p, const Op& op, int grid, int block
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = p.tiled ? fx_tiled_smem_bytes() : sizeof(SmemFx);
+  cfg.dynamicSmemBytes = p.tiled ? fx_tiled_smem_bytes() : p.small ? fx_small_smem_bytes(p.dim, p.m_max) : sizeof(SmemFx);
   cfg.stream = (cudaStream_t)stream;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeCooperative;
@@ -940,6 +958,25 @@ int launch_propagate_csr_fx(const PropParams& p, const OpCsrFx& op, int grid, in
 }
 
 size_t fx_tiled_smem_bytes() { return ((sizeof(SmemFx) + 127) & ~size_t(127)) + 4 * kFxTileElems * sizeof(longlong2); }
+
+// Shared memory of a one-CTA launch that holds q_1 .. q_{m_max+1} (0 when it
+// does not fit in an SM's shared memory).
+size_t fx_small_smem_bytes(int dim, int m_max) {
+  const size_t b = ((sizeof(SmemFx) + 127) & ~size_t(127)) + (size_t)(m_max + 1) * dim * sizeof(longlong2);
+  return b <= kFxSmallSmemMax ? b : 0;
+}
+
+int fx_small_prepare(size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(k_propagate_fx<kFamilySpin, OpSpinFx>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_propagate_fx<kFamilyDia, OpDiaFx>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_propagate_fx<kFamilyCsr, OpCsrFx>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes);
+  return (int)e;
+}
 
 int max_coresident_blocks_fx(int family, int block, bool tiled) {
   int dev = 0, nsm = 0, per = 0;

@@ -29,7 +29,7 @@ def lib():
 def _declared_symbols():
     text = open(os.path.join(ROOT, "include", "cfet.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(cfet_[a-z_]+)\s*\(", text)) - {"cfet_drive_fn"})
+    return sorted(set(re.findall(r"\b(cfet_[a-z0-9_]+)\s*\(", text)) - {"cfet_drive_fn"})
 
 
 def test_library_exports_every_declared_symbol(lib):

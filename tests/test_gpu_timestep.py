@@ -2,8 +2,11 @@
 cfet_error_constant, cfet_select_dt and cfet_propagate_adaptive against the
 oracle's procedures (oracle/timestep.py) run with the oracle's CFET stepping.
 
-The constants come from differences of two propagations (~1e-6 here) whose
-GPU and oracle values agree to ~1e-12, so c and dt agree to ~1e-5 relative;
+The constants come from differences of two propagations (~1e-6 at order 4,
+~2e-10 at order 6 here).  With the oracle's Krylov decisions the GPU and
+oracle states differ only by rounding, at most 1e-14 over the few thousand
+applies of the two runs, so c agrees to 1e-5 relative or to 1e-14 over the
+difference, whichever is larger;
 adaptive runs are compared by replaying the GPU's accepted steps in the oracle
 (states within the usual 1e-10 parity) and by the step sequences themselves.
 """
@@ -54,7 +57,7 @@ def test_error_constant_matches_oracle(torch_cuda, order):
     c, diff, dt2 = prop.error_constant(x, 0.0, 2.0, 20, order=order, tol=1e-13)
     c_o, diff_o, dt2_o = TS.error_constant(_oracle_step(op, drives, order), psi0, 0.0, 2.0, 20, order)
     assert dt2 == dt2_o
-    assert abs(c / c_o - 1.0) <= 1e-5, (c, c_o)
+    assert abs(c / c_o - 1.0) <= max(1e-5, 1e-14 / diff_o), (c, c_o, diff_o)
     assert np.array_equal(x.cpu().numpy(), psi0)   # psi0 unchanged
 
 
