@@ -86,6 +86,7 @@ struct SmemFx {
   // running FP32 bounds of the current T_k for the estimate's screens
   LeadAcc lead;
   GershAcc gfull;  // rows whose couplings are all known
+  int gate_it;     // FP32 gate of the current iteration (1, 0, -1: FP64 needed)
 };
 
 // ------------------------------------------------------------------ control-warp helpers
@@ -119,11 +120,6 @@ __device__ bool fx_ctl_reduce(SmemFx& S, int NW, unsigned long long* part, unsig
   lo = __shfl_sync(0xffffffffu, lo, 0);
   hi = __shfl_sync(0xffffffffu, hi, 0);
   m = __shfl_sync(0xffffffffu, m, 0);
-  if (gridDim.x == 1) {  // nothing to exchange
-    sum = fx_i128_to_double(lo, hi);
-    mxi = m;
-    return true;
-  }
   const unsigned mine[6] = {(unsigned)lo, (unsigned)(lo >> 32), (unsigned)hi,
                             (unsigned)((unsigned long long)hi >> 32), (unsigned)m,
                             (unsigned)((unsigned long long)m >> 32)};
@@ -393,8 +389,10 @@ __device__ double fx_estimate(SmemFx& S, int k, double ts, double thr) {
 
 // ------------------------------------------------------------------ the kernel
 // TILED: the window-tiled apply of long spin chains (a separate instantiation,
-// so that the element-wise kernel carries none of its code).
-template <int FAMILY, class Op, bool TILED = false>
+// so that the element-wise kernel carries none of its code).  SMALL: one CTA
+// with the Krylov basis in shared memory (separate too, so that the other
+// instantiations keep global-memory loads for the vectors).
+template <int FAMILY, class Op, bool TILED = false, bool SMALL = false>
 __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropParams p, Op op) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmemFx& S = *reinterpret_cast<SmemFx*>(smem_raw);
@@ -444,8 +442,9 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
   int max_k = 0;
   double max_err = 0.0;
 
-  // one-CTA launches of small problems keep the basis in shared memory
-  longlong2* const qb = p.small ? tbuf : p.qbasis;
+  // one-CTA launches of small problems keep the basis in shared memory (a
+  // separate instantiation: the others keep global-memory loads)
+  longlong2* const qb = SMALL ? tbuf : p.qbasis;
   auto Q = [&](int i) -> longlong2* { return qb + (size_t)(i - 1) * dim; };
 
   // ---------------- psi (complex128) -> q_1
@@ -713,6 +712,10 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
               twe = sm_clock();
               tacc[2] += twe - tw0;
             }
+          } else if (lane == 0) {
+            // meanwhile: running bounds of T_it (alpha_it and beta_{it-1} are
+            // known) and the FP32 gate of its estimate
+            S.gate_it = krylov_bounds_update(S, it, remaining);
           }
           __syncthreads();
           if (ctl) {
@@ -728,15 +731,13 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
               const double prev_b = it > 1 ? S.beta[it - 1] : 0.0;
               const bool breakdown =
                   sb_no_breakdown(b, S.alpha[it], prev_b) != 1 && b <= 1e-13 * (fabs(S.alpha[it]) + prev_b + 1.0);
-              int gate = -1;
+              const int gate = S.gate_it;
               if (lane == 0) {
                 S.beta[it] = b;
                 S.scale[it + 1] = fx_scale2(rb, -S.Ew);
                 S.E[it + 1] = S.Ew;
                 S.A[it + 1] = sb_ll_to_double_up(mxi);
-                gate = krylov_bounds_update(S, it, remaining);
               }
-              gate = __shfl_sync(0xffffffffu, gate, 0);
               __syncwarp();
               int acc_flag = 0, pend_next = 0;
               double err = 0.0;
@@ -944,6 +945,7 @@ static int launch_prop_fx(const PropParams& p, const Op& op, int grid, int block
   if constexpr (FAMILY == kFamilySpin) {
     if (p.tiled) return (int)cudaLaunchKernelEx(&cfg, k_propagate_fx<FAMILY, Op, true>, p, op);
   }
+  if (p.small) return (int)cudaLaunchKernelEx(&cfg, k_propagate_fx<FAMILY, Op, false, true>, p, op);
   return (int)cudaLaunchKernelEx(&cfg, k_propagate_fx<FAMILY, Op>, p, op);
 }
 
@@ -967,14 +969,14 @@ size_t fx_small_smem_bytes(int dim, int m_max) {
 }
 
 int fx_small_prepare(size_t bytes) {
-  cudaError_t e = cudaFuncSetAttribute(k_propagate_fx<kFamilySpin, OpSpinFx>,
+  cudaError_t e = cudaFuncSetAttribute(k_propagate_fx<kFamilySpin, OpSpinFx, false, true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_propagate_fx<kFamilyDia, OpDiaFx>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)bytes);
+    e = cudaFuncSetAttribute(k_propagate_fx<kFamilyDia, OpDiaFx, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_propagate_fx<kFamilyCsr, OpCsrFx>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)bytes);
+    e = cudaFuncSetAttribute(k_propagate_fx<kFamilyCsr, OpCsrFx, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   return (int)e;
 }
 
