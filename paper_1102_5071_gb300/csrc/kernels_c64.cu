@@ -897,7 +897,25 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
             float2* u = Q(it + 1);
             float s0 = 0.f, c0 = 0.f;  // ||w||^2 of the stored w, for the next iteration
             const long long tw0 = sm_clock();
-            for (int x = wx0; x < wxe; x += wstep) {
+            int x = wx0;
+            // four elements per step with every load issued first (more bytes
+            // in flight per thread); the sums keep the order of the plain loop
+            for (; x + 3 * wstep < wxe; x += 4 * wstep) {
+              float2 v[4], uu[4];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                v[j] = q[x + j * wstep];
+                uu[j] = u[x + j * wstep];
+              }
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const float2 w = make_float2(fmaf(am, v[j].x, uu[j].x), fmaf(am, v[j].y, uu[j].y));
+                u[x + j * wstep] = w;
+                ff_add_prod(s0, c0, w.x, w.x);
+                ff_add_prod(s0, c0, w.y, w.y);
+              }
+            }
+            for (; x < wxe; x += wstep) {
               const float2 v = q[x];
               const float2 uu = u[x];
               const float2 w = make_float2(fmaf(am, v.x, uu.x), fmaf(am, v.y, uu.y));

@@ -698,7 +698,23 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
             __int128 b2 = 0;
             long long mx = 0;
             const long long tw0 = sm_clock();
-            for (int x = wx0; x < wxe; x += wstep) {
+            int x = wx0;
+            // two elements per step with every load issued first (exact sums:
+            // the order does not matter)
+            for (; x + wstep < wxe; x += 2 * wstep) {
+              const longlong2 v0 = q[x], v1 = q[x + wstep];
+              const longlong2 u0 = u[x], u1 = u[x + wstep];
+              const long long wr0 = fx_rshr(u0.x, sh_u) + fx_mulhi(m_a, v0.x << pk);
+              const long long wi0 = fx_rshr(u0.y, sh_u) + fx_mulhi(m_a, v0.y << pk);
+              const long long wr1 = fx_rshr(u1.x, sh_u) + fx_mulhi(m_a, v1.x << pk);
+              const long long wi1 = fx_rshr(u1.y, sh_u) + fx_mulhi(m_a, v1.y << pk);
+              u[x] = make_longlong2(wr0, wi0);
+              u[x + wstep] = make_longlong2(wr1, wi1);
+              b2 += (__int128)wr0 * wr0 + (__int128)wi0 * wi0;
+              b2 += (__int128)wr1 * wr1 + (__int128)wi1 * wi1;
+              mx = max(mx, max(fx_absmax(wr0, wi0), fx_absmax(wr1, wi1)));
+            }
+            for (; x < wxe; x += wstep) {
               const longlong2 v = q[x];
               const longlong2 uu = u[x];
               const long long wr = fx_rshr(uu.x, sh_u) + fx_mulhi(m_a, v.x << pk);
