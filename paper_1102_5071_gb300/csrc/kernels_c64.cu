@@ -38,12 +38,6 @@
 #include "device_common.cuh"
 #include "tiled_common.cuh"
 
-// Spin apply on two elements per thread and loop iteration (twice the
-// independent neighbour loads per warp; 1 = on).
-#ifndef CFET_C64_PAIRS
-#define CFET_C64_PAIRS 1
-#endif
-
 namespace cfet {
 
 // ------------------------------------------------------------------ compensated sums
@@ -82,7 +76,7 @@ struct CConst {
 };
 
 struct SmemC {
-  float ws[2][32], wc[2][32];    // per-warp compensated partials of the workers (up to 2 sums)
+  float ws[3][32], wc[3][32];    // per-warp compensated partials of the workers (up to 3 sums)
   double alpha[kMaxKrylov + 2];
   double beta[kMaxKrylov + 2];
   double scale[kMaxKrylov + 3];  // 1 / ||q_i||
@@ -428,10 +422,15 @@ __device__ bool tile_wait(unsigned long long* bar, unsigned parity, int* status,
 
 // One window pass of this CTA's worker threads over its tiles (vectors are
 // basis indices: iq the applied q, ia the own-element input, iu the output).
-template <bool FIRST, bool LAST>
+// ORTH (window 0 from the second iteration on): the q tile holds u_{k-1} and
+// the aux tile q_{k-1}; the pass first forms q_k = w_{k-1} = u_{k-1} + am q_{k-1}
+// in place (the orthogonalisation step of iteration k-1, with ||w||^2 into
+// s2/c2), applies H to it and stores both w (over u_{k-1}) and the result.
+template <bool FIRST, bool LAST, bool ORTH = false>
 __device__ void c_tiled_pass(const TmaPass& T, const OpSpinC& op, const CConst& c, const float* bx, int iq, int ia,
                              int iu, const TileWin& W, int w, int nworkers, float& s0, float& c0, float& s1,
-                             float& c1) {
+                             float& c1, float am = 0.f, float* s2 = nullptr, float* c2 = nullptr) {
+  static_assert(!ORTH || FIRST, "the orthogonalisation step runs in window 0");
   const int tid = threadIdx.x;
   const int G = gridDim.x;
   const int ntiles = 1 << (op.N - kTileBits);
@@ -454,11 +453,28 @@ __device__ void c_tiled_pass(const TmaPass& T, const OpSpinC& op, const CConst& 
   int k = 0;
   for (int t = blockIdx.x; t < ntiles; ++k, t += G) {
     const int st = k % kTmaStages;
-    const float2* cur = T.stage + (size_t)st * 2 * kTileElems;
+    float2* cur = T.stage + (size_t)st * 2 * kTileElems;
     float2* acur = T.stage + (size_t)st * 2 * kTileElems + kTileElems;
     const unsigned par = (*T.phase >> st) & 1u;
     *T.phase ^= 1u << st;
     if (!tile_wait(T.bar + st, par, T.status, T.timeout_ns)) *T.fail = 1;
+    if constexpr (ORTH) {
+      if (!*T.fail) {
+        float4* w4 = reinterpret_cast<float4*>(cur);
+        const float4* p4 = reinterpret_cast<const float4*>(acur);
+        for (int jp = tid; jp < kTileElems / 2; jp += nworkers) {
+          const float4 uu = w4[jp], qq = p4[jp];
+          const float4 wv = make_float4(fmaf(am, qq.x, uu.x), fmaf(am, qq.y, uu.y), fmaf(am, qq.z, uu.z),
+                                        fmaf(am, qq.w, uu.w));
+          w4[jp] = wv;
+          ff_add_prod(*s2, *c2, wv.x, wv.x);
+          ff_add_prod(*s2, *c2, wv.y, wv.y);
+          ff_add_prod(*s2, *c2, wv.z, wv.z);
+          ff_add_prod(*s2, *c2, wv.w, wv.w);
+        }
+      }
+      workers_sync(nworkers);  // every w of the tile written before its neighbours are read
+    }
     if (!*T.fail) {
       // Element pairs (2 jp, 2 jp + 1) of the tile: a flip or hop of any bit
       // above bit 0 moves both elements of a pair to the two elements of
@@ -600,6 +616,7 @@ __device__ void c_tiled_pass(const TmaPass& T, const OpSpinC& op, const CConst& 
     if (*T.fail) break;
     if (prod) {
       tile_store(map, FIRST, W, op.N, t, iu, acur);
+      if constexpr (ORTH) tile_store(map, FIRST, W, op.N, t, iq, cur);
       bulk_commit();
       const int tn = t + (kTmaStages - 1) * G;
       if (tn < ntiles) {
@@ -767,19 +784,31 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
             // <q,u> and ||u||^2: with ||q||^2 (reduced when q was written) they
             // give alpha and ||u - alpha s q||^2, so the decisions need not wait
             // for the orthogonalisation pass
-            float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+            float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
             const long long tw0 = sm_clock();
             int x = wx0;
             if constexpr (TILED) {
               {  // window passes, grid exchanges between them (control warp)
                 for (int w = 0; w < nwin; ++w) {
                   // basis indices: q_it is vector it - 1, q_{it-1} vector it - 2, u vector it
+                  // (from it = 2 on, window 0 first turns u_{it-1} in vector
+                  // it - 1 into q_it = u_{it-1} - alpha s q_{it-1}: ORTH)
                   const int iq = it - 1, ia = w == 0 ? (it > 1 ? it - 2 : 0) : it, iu = it;
                   if (w == 0) {
-                    if (nwin == 1)
-                      c_tiled_pass<true, true>(TP, op, c, S.bx, iq, ia, iu, win[0], 0, wstep, s0, c0, s1, c1);
-                    else
-                      c_tiled_pass<true, false>(TP, op, c, S.bx, iq, ia, iu, win[0], 0, wstep, s0, c0, s1, c1);
+                    const float am = S.am;
+                    if (nwin == 1) {
+                      if (it > 1)
+                        c_tiled_pass<true, true, true>(TP, op, c, S.bx, iq, ia, iu, win[0], 0, wstep, s0, c0, s1, c1,
+                                                       am, &s2, &c2);
+                      else
+                        c_tiled_pass<true, true>(TP, op, c, S.bx, iq, ia, iu, win[0], 0, wstep, s0, c0, s1, c1);
+                    } else {
+                      if (it > 1)
+                        c_tiled_pass<true, false, true>(TP, op, c, S.bx, iq, ia, iu, win[0], 0, wstep, s0, c0, s1, c1,
+                                                        am, &s2, &c2);
+                      else
+                        c_tiled_pass<true, false>(TP, op, c, S.bx, iq, ia, iu, win[0], 0, wstep, s0, c0, s1, c1);
+                    }
                   } else if (w == nwin - 1) {
                     c_tiled_pass<false, true>(TP, op, c, S.bx, iq, ia, iu, win[w], w, wstep, s0, c0, s1, c1);
                   } else {
@@ -793,7 +822,8 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
                 x = wxe;  // nothing left for the element loops
               }
             }
-#if CFET_C64_PAIRS
+            // spin apply on two elements per thread and loop iteration (twice the
+            // independent neighbour loads per warp)
             if constexpr (FAMILY == kFamilySpin) {
               for (; x + wstep < wxe; x += 2 * wstep) {
                 float2 h1, h2;
@@ -811,7 +841,6 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
                 ff_add_prod(s1, c1, h2.y, h2.y);
               }
             }
-#endif
             for (; x < wxe; x += wstep) {
               float2 hv;
               if constexpr (FAMILY == kFamilySpin) hv = c_apply_spin(q, qm, x, op, c, S.bx);
@@ -825,6 +854,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
             }
             c_worker_partial(S, s0, c0, 0);
             c_worker_partial(S, s1, c1, 1);
+            if constexpr (TILED) c_worker_partial(S, s2, c2, 2);  // ||q_it||^2 of the w stored in window 0
             if (tid == 0) {
               twe = sm_clock();
               tacc[0] += twe - tw0;
@@ -859,14 +889,16 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
           __syncthreads();
           if (ctl) {
             const long long tc0 = sm_clock(), sp0 = tacc[5];
-            double sum[2];
-            // (the tiled apply leaves u written by other CTAs: fence)
+            double sum[3];
+            // (the tiled apply leaves u written by other CTAs: fence; it also
+            // carries ||q_it||^2 of the w that its window 0 stored)
             constexpr bool kMayTile = TILED;
             if ((kMayTile && S.abort_flag) ||
-                !c_ctl_reduce<2>(S, NW, partA, tag0 + (++gen), kMayTile, &st->status, p.timeout_ns,
-                                 sum, tacc[5])) {
+                !c_ctl_reduce<TILED ? 3 : 2>(S, NW, partA, tag0 + (++gen), kMayTile, &st->status, p.timeout_ns,
+                                             sum, tacc[5])) {
               if (lane == 0) S.abort_flag = 1;
             } else if (lane == 0 && !S.stop_prev) {
+              if (TILED && it > 1) S.qnorm2[it] = sum[2];
               // q_it holds the Lanczos vector v_it times 1/scale[it]:
               // alpha = <v, u>,  ||w||^2 = ||u - alpha v||^2
               //       = ||u||^2 - alpha^2 (2 - s^2 ||q||^2)
@@ -888,45 +920,48 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
             acc_err = S.err_prev;
             break;
           }
-          // -------- phase B(it): w = u - alpha s_it q_it on the workers; beta
-          // (known from the phase-A sums), the decisions and the next
-          // iteration's constants on the control warp at the same time
+          // -------- phase B(it): w = u - alpha s_it q_it on the workers (the
+          // tiled form does it in the next iteration's window 0); beta (known
+          // from the phase-A sums), the decisions and the next iteration's
+          // constants on the control warp at the same time
           if (!ctl) {
-            const float am = S.am;
-            const float2* q = Q(it);
-            float2* u = Q(it + 1);
-            float s0 = 0.f, c0 = 0.f;  // ||w||^2 of the stored w, for the next iteration
-            const long long tw0 = sm_clock();
-            int x = wx0;
-            // four elements per step with every load issued first (more bytes
-            // in flight per thread); the sums keep the order of the plain loop
-            for (; x + 3 * wstep < wxe; x += 4 * wstep) {
-              float2 v[4], uu[4];
-#pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                v[j] = q[x + j * wstep];
-                uu[j] = u[x + j * wstep];
+            if constexpr (!TILED) {
+              const float am = S.am;
+              const float2* q = Q(it);
+              float2* u = Q(it + 1);
+              float s0 = 0.f, c0 = 0.f;  // ||w||^2 of the stored w, for the next iteration
+              const long long tw0 = sm_clock();
+              int x = wx0;
+              // four elements per step with every load issued first (more bytes
+              // in flight per thread); the sums keep the order of the plain loop
+              for (; x + 3 * wstep < wxe; x += 4 * wstep) {
+                float2 v[4], uu[4];
+  #pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  v[j] = q[x + j * wstep];
+                  uu[j] = u[x + j * wstep];
+                }
+  #pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  const float2 w = make_float2(fmaf(am, v[j].x, uu[j].x), fmaf(am, v[j].y, uu[j].y));
+                  u[x + j * wstep] = w;
+                  ff_add_prod(s0, c0, w.x, w.x);
+                  ff_add_prod(s0, c0, w.y, w.y);
+                }
               }
-#pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                const float2 w = make_float2(fmaf(am, v[j].x, uu[j].x), fmaf(am, v[j].y, uu[j].y));
-                u[x + j * wstep] = w;
+              for (; x < wxe; x += wstep) {
+                const float2 v = q[x];
+                const float2 uu = u[x];
+                const float2 w = make_float2(fmaf(am, v.x, uu.x), fmaf(am, v.y, uu.y));
+                u[x] = w;
                 ff_add_prod(s0, c0, w.x, w.x);
                 ff_add_prod(s0, c0, w.y, w.y);
               }
-            }
-            for (; x < wxe; x += wstep) {
-              const float2 v = q[x];
-              const float2 uu = u[x];
-              const float2 w = make_float2(fmaf(am, v.x, uu.x), fmaf(am, v.y, uu.y));
-              u[x] = w;
-              ff_add_prod(s0, c0, w.x, w.x);
-              ff_add_prod(s0, c0, w.y, w.y);
-            }
-            c_worker_partial(S, s0, c0, 0);
-            if (tid == 0) {
-              twe = sm_clock();
-              tacc[2] += twe - tw0;
+              c_worker_partial(S, s0, c0, 0);
+              if (tid == 0) {
+                twe = sm_clock();
+                tacc[2] += twe - tw0;
+              }
             }
           } else {
             const long long tc0 = sm_clock();
@@ -976,7 +1011,7 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
           }
           __syncthreads();
           const bool last_it = S.accept_now || it >= klimit;
-          if (!last_it) {
+          if (!TILED && !last_it) {
             // every CTA's w must be visible before the next apply reads it; the
             // exchange also carries ||w||^2 of the stored w
             if (ctl) {
