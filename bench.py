@@ -204,9 +204,13 @@ class OraclePool:
     """The oracle, as it stands, on `workers` host processes (one thread each)."""
 
     def __init__(self, workers):
+        import importlib
         import multiprocessing as mp
         for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
             os.environ[k] = "1"
+        # fail here, not in the workers: a pool whose initializer raises keeps
+        # replacing its workers and never returns
+        importlib.import_module("oracle.cfet")
         self.workers = workers
         self.pool = mp.get_context("spawn").Pool(workers, initializer=_oracle_init)
 
