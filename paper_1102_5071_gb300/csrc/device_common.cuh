@@ -75,18 +75,20 @@ static __device__ bool warp_grid_barrier(unsigned* bar, unsigned& gen, int* stat
 // (aligned 64-bit stores are single-copy atomic); readers wait until the words
 // of every CTA carry `tag`.  No atomics and no last-arriver step: one store and
 // one round of loads per exchange.  Records of up to 8 words are stored
-// contiguously (word w of CTA i at rec[i W + w]); wider ones word-major
-// (rec[w G + i]), so that a warp's load of one word of 32 consecutive CTAs
-// touches two 128-byte lines: a 16-word exchange of 152 CTAs took 11.1 us
-// contiguous and 4.0 us word-major, while the 4- and 6-word records of the
-// Krylov kernels were 3-10 % faster contiguous (measured both ways).
+// contiguously (word w of CTA i at rec[i S + w], S = W rounded up to 8 for
+// 5..8 words, so that no record straddles two 64-byte halves of a line);
+// wider ones word-major (rec[w G + i]), so that a warp's load of one word of
+// 32 consecutive CTAs touches two 128-byte lines: a 16-word exchange of 152
+// CTAs took 11.1 us contiguous and 4.0 us word-major, while the 4- and 6-word
+// records of the Krylov kernels were 3-10 % faster contiguous (measured both
+// ways); a 6-word exchange took 6.2 us at stride 6 and 4.5 us at stride 8.
 // Lane l reads the records of CTAs l, l + 32, ..., l + 32 (kExchMaxPerLane - 1)
 // in that order and passes each to acc.add(); acc.reset() starts every polling
 // round.  `fence` orders the CTA's earlier global stores before its record
 // (writer) and the records before the CTA's later loads (reader); it is needed
 // when other CTAs will read vectors written before the exchange.  Returns false
 // in every lane when the wait limit expired (CFET_ETIMEOUT recorded) or another
-// CTA reported an error.  A slot of W words per CTA needs W G words.
+// CTA reported an error.  A slot of W words per CTA needs S G words.
 constexpr int kExchMaxPerLane = 8;  // grids of at most 256 CTAs
 
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
@@ -102,6 +104,7 @@ template <int W, class Acc>
 static __device__ bool ctl_exchange(unsigned long long* rec, const unsigned (&mine)[W], unsigned tag, bool fence,
                                     int* status, long long timeout_ns, long long& spin, Acc& acc) {
   constexpr bool kWordMajor = W > 8;
+  constexpr int kStride = (W > 4 && W <= 8) ? 8 : W;  // contiguous records: words per CTA
   const int lane = threadIdx.x & 31;
   const int G = gridDim.x;
   if (G == 1) {  // a single CTA: its own record is the total; nothing to publish or wait for
@@ -114,7 +117,7 @@ static __device__ bool ctl_exchange(unsigned long long* rec, const unsigned (&mi
     if (fence) __threadfence();
 #pragma unroll
     for (int w = 0; w < W; ++w)
-      st_relaxed_u64(kWordMajor ? rec + (size_t)w * G + blockIdx.x : rec + (size_t)blockIdx.x * W + w,
+      st_relaxed_u64(kWordMajor ? rec + (size_t)w * G + blockIdx.x : rec + (size_t)blockIdx.x * kStride + w,
                      ((unsigned long long)tag << 32) | mine[w]);
   }
   __syncwarp();
@@ -132,7 +135,7 @@ static __device__ bool ctl_exchange(unsigned long long* rec, const unsigned (&mi
 #pragma unroll
         for (int w = 0; w < W; ++w) {
           const unsigned long long x =
-              ld_relaxed_u64(kWordMajor ? rec + (size_t)w * G + i : rec + (size_t)i * W + w);
+              ld_relaxed_u64(kWordMajor ? rec + (size_t)w * G + i : rec + (size_t)i * kStride + w);
           v[w] = (unsigned)x;
           ready &= (unsigned)(x >> 32) == tag;
         }

@@ -661,10 +661,10 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
   // float-float pair (two tagged words) per CTA; tags continue across launches
   const unsigned tag0 = (unsigned)ld_volatile_i32((const int*)&p.st->tag_base);
   unsigned gen = 0;
-  unsigned long long* partA = reinterpret_cast<unsigned long long*>(p.partials);  // 3 sums: 6 words
-  unsigned long long* partB = partA + 6 * G;                                        // 1 sum: 2 words
-  unsigned long long* partR = partA + 12 * G;                                       // 1 sum: 2 words
-  unsigned long long* partW = partA + 18 * G;  // window barriers of the tiled apply: two 1-word slots
+  unsigned long long* partA = reinterpret_cast<unsigned long long*>(p.partials);  // 3 sums: 6 words (stride 8)
+  unsigned long long* partB = partA + 8 * G;                                        // 1 sum: 2 words
+  unsigned long long* partR = partA + 16 * G;                                       // 1 sum: 2 words
+  unsigned long long* partW = partA + 24 * G;  // window barriers of the tiled apply: two 1-word slots
   // tiled apply: windows and the tile buffers behind SmemC
   TileWin win[kTiledMaxWindows] = {};
   int nwin = 1;
