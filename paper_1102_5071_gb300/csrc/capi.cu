@@ -32,7 +32,7 @@ using namespace cfet;
 
 // TMA maps of the window-tiled complex64 apply over the Krylov basis of ctx
 // (nvec vectors of 2^N elements), one per window, copied to device memory.
-static cfet_status build_tile_maps(cfet_ctx* ctx, int N, int nvec);
+static cfet_status build_tile_maps(cfet_ctx* ctx, int N, int nvec, bool fx);
 
 struct cfet_ctx {
   int device = 0;
@@ -1210,8 +1210,8 @@ cfet_status cfet_create(cfet_ctx** out, const cfet_op* H0, int32_t nV, const cfe
         "cudaMalloc(Krylov basis)");
   else if (ctx->precision == CFET_PREC_C64)
     CKC(cudaMalloc(&ctx->d_qbasis32, (size_t)(o.m_max + 1) * dim * sizeof(float2)), "cudaMalloc(Krylov basis)");
-  if (ctx->precision == CFET_PREC_C64 && ctx->tiled) {
-    const cfet_status ts = build_tile_maps(ctx, nsites, o.m_max + 1);
+  if ((ctx->precision == CFET_PREC_C64 || ctx->precision == CFET_PREC_FX) && ctx->tiled) {
+    const cfet_status ts = build_tile_maps(ctx, nsites, o.m_max + 1, ctx->precision == CFET_PREC_FX);
     if (ts != CFET_OK) {
       free_ctx(ctx);
       return ts;
@@ -1546,12 +1546,13 @@ cfet_status cfet_sync(cfet_ctx* ctx, void* stream, cfet_stats* stats) {
 // units of complex64 tiles (element pairs) contiguous and aligned, and the
 // window count within its bound.
 extern "C++" {
-// TMA geometry of window w of the window-tiled complex64 apply (tiles of
-// 2^kC64TileBits 8-byte elements, a map over the whole Krylov basis of nvec
-// contiguous vectors, so that the vector index continues the outermost
-// dimension).  Window 0 views the basis as 256-element rows (box: 16 rows);
-// window w >= 1 splits the index into its bits [0, c) (as 256 x 2^(c-8) when
-// c > 8: a box dimension holds at most 256 elements), [c, b0), the window's
+// TMA geometry of window w of a window-tiled apply: tiles of 2^TB elements
+// of wpe 8-byte words (complex64: TB 12, one word; fixed point: TB 11, an int64
+// pair), a map over the whole Krylov basis of nvec contiguous vectors, so that
+// the vector index continues the outermost dimension, all in words.  Window 0
+// views the basis as rows of 256 words (box: one tile's rows); window w >= 1
+// splits the index into its bits [0, c) (2^c wpe words, as 256 x 2^c wpe / 256
+// beyond 256 words: a box dimension holds at most 256), [c, b0), the window's
 // bits [b0, b0 + width) and the rest (box: the low bits x 1 x 2^width x 1).
 struct TileMapGeom {
   int rank;
@@ -1559,37 +1560,41 @@ struct TileMapGeom {
   uint64_t strides[4];  // bytes, dimensions 1 .. rank - 1
   uint32_t box[5];
 };
-static void tile_map_geometry(int N, int w, const TileWin& W, int nvec, TileMapGeom* g) {
-  const uint64_t e = 8, dim = uint64_t(1) << N, nv = (uint64_t)nvec;
+static void tile_map_geometry(int N, int TB, int wpe, int w, const TileWin& W, int nvec, TileMapGeom* g) {
+  const uint64_t e = 8 * (uint64_t)wpe, dim = uint64_t(1) << N, nv = (uint64_t)nvec;
+  const int rs = wpe == 2 ? 7 : 8;  // log2 of the elements per 256-word row
   if (w == 0) {
-    *g = TileMapGeom{2, {256, (dim >> 8) * nv, 0, 0, 0}, {256 * e, 0, 0, 0}, {256, 16, 0, 0, 0}};
+    *g = TileMapGeom{2, {256, (dim >> rs) * nv, 0, 0, 0}, {256 * 8, 0, 0, 0},
+                     {256, (uint32_t)(1u << (TB - rs)), 0, 0, 0}};
     return;
   }
   const int c = W.c, b0 = W.b0, wd = W.width;
-  const uint64_t lo = uint64_t(1) << c, mid = uint64_t(1) << (b0 - c), win = uint64_t(1) << wd;
+  const uint64_t lo = (uint64_t(1) << c) * (uint64_t)wpe, mid = uint64_t(1) << (b0 - c), win = uint64_t(1) << wd;
   const uint64_t rest = (uint64_t(1) << (N - b0 - wd)) * nv;
-  const uint64_t s_mid = lo * e, s_win = (uint64_t(1) << b0) * e, s_rest = (uint64_t(1) << (b0 + wd)) * e;
-  if (c <= 8)
+  const uint64_t s_mid = (uint64_t(1) << c) * e, s_win = (uint64_t(1) << b0) * e, s_rest = (uint64_t(1) << (b0 + wd)) * e;
+  if (lo <= 256)
     *g = TileMapGeom{4, {lo, mid, win, rest, 0}, {s_mid, s_win, s_rest, 0}, {(uint32_t)lo, 1, (uint32_t)win, 1, 0}};
   else
-    *g = TileMapGeom{5, {256, lo >> 8, mid, win, rest}, {256 * e, s_mid, s_win, s_rest},
+    *g = TileMapGeom{5, {256, lo >> 8, mid, win, rest}, {256 * 8, s_mid, s_win, s_rest},
                      {256, (uint32_t)(lo >> 8), 1, (uint32_t)win, 1}};
 }
-// Coordinates of tile t of vector v (as the kernel's tile_load / tile_store).
-static void tile_map_coords(int N, int w, const TileWin& W, int t, int v, int* c) {
+// Coordinates of tile t of vector v (as the kernels' tile_load_t / tile_store_t).
+static void tile_map_coords(int N, int TB, int wpe, int w, const TileWin& W, int t, int v, int* c) {
+  const int rs = wpe == 2 ? 7 : 8;
   if (w == 0) {
-    c[0] = 0; c[1] = (t << 4) + v * (1 << (N - 8));
+    c[0] = 0; c[1] = (t << (TB - rs)) + v * (1 << (N - rs));
     return;
   }
   const int nb = W.b0 - W.c, tl = t & ((1 << nb) - 1), th = (t >> nb) + v * (1 << (N - W.b0 - W.width));
-  if (W.c <= 8) {
+  if (W.c <= rs) {
     c[0] = 0; c[1] = tl; c[2] = 0; c[3] = th;
   } else {
     c[0] = 0; c[1] = 0; c[2] = tl; c[3] = 0; c[4] = th;
   }
 }
-// Element (index within the basis) that box slot j of the box at coordinates c
-// holds: the box is laid out in shared memory with dimension 0 fastest.
+// Word (index within the basis, in 8-byte words) that box word j of the box at
+// coordinates c holds: the box is laid out in shared memory with dimension 0
+// fastest.
 static int64_t tile_map_element(const TileMapGeom& g, const int* c, int j) {
   int64_t off = 0, stride = 1;  // stride in elements of the current dimension
   for (int d = 0; d < g.rank; ++d) {
@@ -1644,22 +1649,24 @@ static bool check_tiling(int N, int64_t* checked) {
         }
         ++*checked;
       }
-    if (TB == kC64TileBits) {  // the TMA boxes of the complex64 kernel hold the same slots
+    {  // the TMA boxes hold the same slots (complex64: TB 12, one word per element; fixed point: TB 11, two)
+      const int wpe = TB == kC64TileBits ? 1 : 2;
       TileMapGeom g;
-      tile_map_geometry(N, w, W[w], 3, &g);
+      tile_map_geometry(N, TB, wpe, w, W[w], 3, &g);
       if (!tile_map_valid(g)) return false;
       int64_t boxn = 1;
       for (int d = 0; d < g.rank; ++d) boxn *= g.box[d];
-      if (boxn != (int64_t(1) << TB)) return false;
+      if (boxn != (int64_t(1) << TB) * wpe) return false;
       for (int v = 0; v < 3; v += 2)
         for (int t = 0; t < ntiles; ++t) {
           int c[5];
-          tile_map_coords(N, w, W[w], t, v, c);
+          tile_map_coords(N, TB, wpe, w, W[w], t, v, c);
           for (int d = 0; d < g.rank; ++d)
             if (c[d] < 0 || (d == 0 && c[d] != 0)) return false;
-          for (int j = 0; j < (1 << TB); ++j) {
+          for (int jw = 0; jw < (1 << TB) * wpe; ++jw) {
+            const int j = jw / wpe;
             const int64_t x = w == 0 ? ((int64_t)t << TB) | j : tile_x(W[w], t, j);
-            if (tile_map_element(g, c, j) != x + (int64_t)v * dim) return false;
+            if (tile_map_element(g, c, jw) != (x + (int64_t)v * dim) * wpe + jw % wpe) return false;
           }
         }
     }
@@ -1673,7 +1680,7 @@ static bool check_tiling(int N, int64_t* checked) {
 }  // extern "C++"
 
 extern "C++" {
-static cfet_status build_tile_maps(cfet_ctx* ctx, int N, int nvec) {
+static cfet_status build_tile_maps(cfet_ctx* ctx, int N, int nvec, bool fx) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -1686,14 +1693,16 @@ static cfet_status build_tile_maps(cfet_ctx* ctx, int N, int nvec) {
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
   TileWin W[kTiledMaxWindows] = {};
-  const int nwin = tiled_windows<kC64TileBits>(N, W);
+  const int TB = fx ? kFxTileBits : kC64TileBits, wpe = fx ? 2 : 1;
+  const int nwin = fx ? tiled_windows<kFxTileBits>(N, W) : tiled_windows<kC64TileBits>(N, W);
+  void* base = fx ? (void*)ctx->d_qbasis : (void*)ctx->d_qbasis32;
   std::vector<CUtensorMap> maps(nwin);
   for (int w = 0; w < nwin; ++w) {
     TileMapGeom g;
-    tile_map_geometry(N, w, W[w], nvec, &g);
+    tile_map_geometry(N, TB, wpe, w, W[w], nvec, &g);
     if (!tile_map_valid(g)) return fail(nullptr, CFET_EINVAL, "tiled apply: invalid TMA geometry");
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    const CUresult r = encode(&maps[w], CU_TENSOR_MAP_DATA_TYPE_INT64, (cuuint32_t)g.rank, ctx->d_qbasis32, g.dims,
+    const CUresult r = encode(&maps[w], CU_TENSOR_MAP_DATA_TYPE_INT64, (cuuint32_t)g.rank, base, g.dims,
                               g.strides, g.box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(nullptr, CFET_ECUDA, "cuTensorMapEncodeTiled failed for the tiled apply");

@@ -309,6 +309,7 @@ int max_coresident_blocks_c64(int family, int block, bool tiled);
 // cfet_options.apply_form asks for one form.
 constexpr int kC64TiledMinSites = 23;
 constexpr int kC64TileBits = 12;    // tiles of 2^12 complex64 elements (32 KB)
+constexpr int kFxTileBits = 11;    // fixed-point tiled apply: tiles of 2^11 int64 pairs
 constexpr int kFxTiledMinSites = 23;
 constexpr int kTiledMinSites = 13;  // tiles of up to 2^12 elements
 constexpr int kTiledMaxSites = 30;  // four windows cover 32 sites at 2^11-element tiles

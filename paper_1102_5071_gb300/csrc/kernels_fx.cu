@@ -87,6 +87,7 @@ struct SmemFx {
   LeadAcc lead;
   GershAcc gfull;  // rows whose couplings are all known
   int gate_it;     // FP32 gate of the current iteration (1, 0, -1: FP64 needed)
+  int tma_fail;    // tiled apply: a tile wait gave up
 };
 
 // ------------------------------------------------------------------ control-warp helpers
@@ -165,129 +166,185 @@ __device__ bool fx_ctl_barrier(unsigned long long* part, unsigned tag, int* stat
 
 // ------------------------------------------------------------------ tiled apply (long chains)
 // Window tiling of tiled_common.cuh with tiles of 2^11 elements (32 KB of
-// int64 pairs): two q tiles and two tiles of the vector each element reads
-// for itself (q_{k-1} in window 0, the partial u after it), 128 KB, staged by
-// cp.async and double-buffered.  Every window adds its terms in the format of
-// the apply above (exact integer neighbour sums, one rounded product per sum
-// and window), so the result differs from the element-wise apply by the
-// rounding of the extra products (units of the last place of u).  The last
-// window takes <q, u> exactly and max |u|.
-constexpr int kFxTileBits = 11;
+// int64 pairs), moved by TMA: one tensor map per window over the whole Krylov
+// basis (two 8-byte words per element), three pipeline stages of a q tile and
+// a tile of the vector each element reads for itself (q_{k-1} in window 0, the
+// partial u after it), 192 KB, one mbarrier per stage.  Worker thread 0 issues
+// the loads two tiles ahead; once the workers have written a tile's results
+// (in place over its own-element tile) it stores that tile with a bulk tensor
+// store.  Every window adds its terms in the format of the apply above (exact
+// integer neighbour sums, one rounded product per sum and window), so the
+// result differs from the element-wise apply by the rounding of the extra
+// products (units of the last place of u).  The last window takes <q, u>
+// exactly and max |u|.
 constexpr int kFxTileElems = 1 << kFxTileBits;
+constexpr unsigned kFxTileBytes = kFxTileElems * sizeof(longlong2);
 
 size_t fx_tiled_smem_bytes();
 
+struct FxTma {
+  const unsigned char* maps;  // kTmaMapBytes per window
+  unsigned long long* bar;    // [kTmaStages] in shared memory
+  longlong2* stage;           // [kTmaStages][2][kFxTileElems] in shared memory
+  int* fail;                  // shared flag: a wait gave up
+  unsigned* phase;            // parity bits of the stages (per thread, identical in all workers)
+  int* status;
+  long long timeout_ns;
+};
+
+// Bounded wait for a stage's tile; false (status CFET_ETIMEOUT) when it gave up.
+__device__ bool fx_tile_wait(unsigned long long* bar, unsigned parity, int* status, long long timeout_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = global_timer_ns();
+  unsigned spins = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if ((++spins & 255u) == 0u) {
+      if (ld_volatile_i32(status) != 0) return false;
+      if (global_timer_ns() - t0 > timeout_ns) {
+        atomicCAS(status, 0, (int)CFET_ETIMEOUT);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+// One window pass of this CTA's worker threads over its tiles (basis indices:
+// iq the applied q, ia the own-element input, iu the output).
 template <bool FIRST, bool LAST>
-__device__ void fx_tiled_pass(longlong2* buf, const OpSpinFx& op, const FxConstA& c, const long long* mb,
-                              const longlong2* __restrict__ q, const longlong2* __restrict__ qm,
-                              longlong2* __restrict__ u, const TileWin& W, int nworkers, __int128& a2,
-                              long long& mx) {
+__device__ void fx_tiled_pass(const FxTma& T, const OpSpinFx& op, const FxConstA& c, const long long* mb, int iq,
+                              int ia, int iu, const TileWin& W, int w, int nworkers, __int128& a2, long long& mx) {
   const int tid = threadIdx.x;
   const int G = gridDim.x;
   const int ntiles = 1 << (op.N - kFxTileBits);
   const bool aux = !FIRST || c.use_prev;
-  const longlong2* asrc = FIRST ? qm : u;
-  auto xof = [&](int t, int j) { return FIRST ? (t << kFxTileBits) | j : tile_x(W, t, j); };
-  auto load = [&](int slot, int t) {
-    longlong2* qb = buf + slot * kFxTileElems;
-    longlong2* ab = buf + (2 + slot) * kFxTileElems;
-    for (int j = tid; j < kFxTileElems; j += nworkers) {
-      const int x = xof(t, j);
-      cp_async16(qb + j, q + x);
-      if (aux) cp_async16(ab + j, asrc + x);
-    }
-    cp_async_commit();
+  const unsigned bytes = aux ? 2 * kFxTileBytes : kFxTileBytes;
+  const void* map = T.maps + (size_t)w * kTmaMapBytes;
+  const bool prod = tid == 0;
+  auto issue = [&](int k, int t) {  // producer: tile t into stage k % kTmaStages
+    const int st = k % kTmaStages;
+    longlong2* qb = T.stage + (size_t)st * 2 * kFxTileElems;
+    mbar_arrive_expect_tx(T.bar + st, bytes);
+    tile_load_t<kFxTileBits, 2>(qb, map, FIRST, W, op.N, t, iq, T.bar + st);
+    if (aux) tile_load_t<kFxTileBits, 2>(qb + kFxTileElems, map, FIRST, W, op.N, t, ia, T.bar + st);
   };
-  int t = blockIdx.x;
-  if (t < ntiles) load(0, t);
-  for (int k = 0; t < ntiles; ++k, t += G) {
-    const longlong2* cur = buf + (k & 1) * kFxTileElems;
-    const longlong2* acur = buf + (2 + (k & 1)) * kFxTileElems;
-    cp_async_wait_all();
-    workers_sync(nworkers);
-    if (t + G < ntiles) load((k + 1) & 1, t + G);
-    for (int j = tid; j < kFxTileElems; j += nworkers) {
-      const int x = xof(t, j);
-      long long ur, ui, hr = 0, hi = 0;
-      if (FIRST) {
-        const int L = op.lo_bits;
-        const long long dz = __ldg(op.DZ_lo + (x & ((1 << L) - 1))) + __ldg(op.DZ_hi + (x >> (L - 1)));
-        const long long Dp = fx_mulhi(c.m_cz, dz << 1) << 3;
+  if (prod) {
+    fence_proxy_async_all();  // vectors written by generic stores before the exchange, read by TMA now
+    for (int k = 0; k < kTmaStages - 1; ++k)
+      if (blockIdx.x + k * G < ntiles) issue(k, blockIdx.x + k * G);
+  }
+  int k = 0;
+  for (int t = blockIdx.x; t < ntiles; ++k, t += G) {
+    const int st = k % kTmaStages;
+    const longlong2* cur = T.stage + (size_t)st * 2 * kFxTileElems;
+    longlong2* acur = T.stage + (size_t)st * 2 * kFxTileElems + kFxTileElems;
+    const unsigned par = (*T.phase >> st) & 1u;
+    *T.phase ^= 1u << st;
+    if (!fx_tile_wait(T.bar + st, par, T.status, T.timeout_ns)) *T.fail = 1;
+    if (!*T.fail) {
+      for (int j = tid; j < kFxTileElems; j += nworkers) {
+        long long ur, ui, hr = 0, hi = 0;
         const longlong2 v = cur[j];
-        ur = fx_mulhi(Dp, v.x << c.pk);
-        ui = fx_mulhi(Dp, v.y << c.pk);
-        const unsigned anti = ((unsigned)j ^ ((unsigned)j >> 1)) & ((1u << (kFxTileBits - 1)) - 1u);
+        if (FIRST) {
+          const int x = (t << kFxTileBits) | j;
+          const int L = op.lo_bits;
+          const long long dz = __ldg(op.DZ_lo + (x & ((1 << L) - 1))) + __ldg(op.DZ_hi + (x >> (L - 1)));
+          const long long Dp = fx_mulhi(c.m_cz, dz << 1) << 3;
+          ur = fx_mulhi(Dp, v.x << c.pk);
+          ui = fx_mulhi(Dp, v.y << c.pk);
+          const unsigned anti = ((unsigned)j ^ ((unsigned)j >> 1)) & ((1u << (kFxTileBits - 1)) - 1u);
 #pragma unroll
-        for (int i = 0; i < kFxTileBits - 1; ++i)
-          if ((anti >> i) & 1u) {
-            const longlong2 w = cur[j ^ (3 << i)];
-            hr += w.x;
-            hi += w.y;
-          }
-        if (op.uniform) {
-          long long xr = 0, xi = 0;
+          for (int i = 0; i < kFxTileBits - 1; ++i)
+            if ((anti >> i) & 1u) {
+              const longlong2 wv = cur[j ^ (3 << i)];
+              hr += wv.x;
+              hi += wv.y;
+            }
+          if (op.uniform) {
+            long long xr = 0, xi = 0;
 #pragma unroll
-          for (int i = 0; i < kFxTileBits; ++i) {
-            const longlong2 w = cur[j ^ (1 << i)];
-            xr += w.x;
-            xi += w.y;
+            for (int i = 0; i < kFxTileBits; ++i) {
+              const longlong2 wv = cur[j ^ (1 << i)];
+              xr += wv.x;
+              xi += wv.y;
+            }
+            ur += fx_mulhi(c.m_x, xr << c.px);
+            ui += fx_mulhi(c.m_x, xi << c.px);
+          } else {
+#pragma unroll
+            for (int i = 0; i < kFxTileBits; ++i) {
+              const longlong2 wv = cur[j ^ (1 << i)];
+              ur += fx_mulhi(mb[i], wv.x << c.pk);
+              ui += fx_mulhi(mb[i], wv.y << c.pk);
+            }
           }
-          ur += fx_mulhi(c.m_x, xr << c.px);
-          ui += fx_mulhi(c.m_x, xi << c.px);
+          if (c.use_prev) {
+            const longlong2 wv = acur[j];
+            ur += fx_mulhi(c.m_p, wv.x << c.pp);
+            ui += fx_mulhi(c.m_p, wv.y << c.pp);
+          }
         } else {
-#pragma unroll
-          for (int i = 0; i < kFxTileBits; ++i) {
-            const longlong2 w = cur[j ^ (1 << i)];
-            ur += fx_mulhi(mb[i], w.x << c.pk);
-            ui += fx_mulhi(mb[i], w.y << c.pk);
+          const longlong2 a = acur[j];
+          ur = a.x;
+          ui = a.y;
+          const unsigned jh = (unsigned)j >> W.c;  // bits b0 .. b0+width-1 of x
+          const unsigned anti = (jh ^ (jh >> 1)) & ((1u << (W.width - 1)) - 1u);
+          for (int i = 0; i < W.width - 1; ++i)
+            if ((anti >> i) & 1u) {
+              const longlong2 wv = cur[j ^ (3 << (W.c + i))];
+              hr += wv.x;
+              hi += wv.y;
+            }
+          if (op.uniform) {
+            long long xr = 0, xi = 0;
+            for (int i = 1; i < W.width; ++i) {
+              const longlong2 wv = cur[j ^ (1 << (W.c + i))];
+              xr += wv.x;
+              xi += wv.y;
+            }
+            ur += fx_mulhi(c.m_x, xr << c.px);
+            ui += fx_mulhi(c.m_x, xi << c.px);
+          } else {
+            for (int i = 1; i < W.width; ++i) {
+              const longlong2 wv = cur[j ^ (1 << (W.c + i))];
+              ur += fx_mulhi(mb[W.b0 + i], wv.x << c.pk);
+              ui += fx_mulhi(mb[W.b0 + i], wv.y << c.pk);
+            }
           }
         }
-        if (c.use_prev) {
-          const longlong2 w = acur[j];
-          ur += fx_mulhi(c.m_p, w.x << c.pp);
-          ui += fx_mulhi(c.m_p, w.y << c.pp);
-        }
-      } else {
-        const longlong2 a = acur[j];
-        ur = a.x;
-        ui = a.y;
-        const unsigned jh = (unsigned)j >> W.c;  // bits b0 .. b0+width-1 of x
-        const unsigned anti = (jh ^ (jh >> 1)) & ((1u << (W.width - 1)) - 1u);
-        for (int i = 0; i < W.width - 1; ++i)
-          if ((anti >> i) & 1u) {
-            const longlong2 w = cur[j ^ (3 << (W.c + i))];
-            hr += w.x;
-            hi += w.y;
-          }
-        if (op.uniform) {
-          long long xr = 0, xi = 0;
-          for (int i = 1; i < W.width; ++i) {
-            const longlong2 w = cur[j ^ (1 << (W.c + i))];
-            xr += w.x;
-            xi += w.y;
-          }
-          ur += fx_mulhi(c.m_x, xr << c.px);
-          ui += fx_mulhi(c.m_x, xi << c.px);
-        } else {
-          for (int i = 1; i < W.width; ++i) {
-            const longlong2 w = cur[j ^ (1 << (W.c + i))];
-            ur += fx_mulhi(mb[W.b0 + i], w.x << c.pk);
-            ui += fx_mulhi(mb[W.b0 + i], w.y << c.pk);
-          }
+        ur += fx_mulhi(c.m_hop, hr << c.ph);
+        ui += fx_mulhi(c.m_hop, hi << c.ph);
+        acur[j] = make_longlong2(ur, ui);  // the own element only: read above by this thread
+        if (LAST) {
+          a2 += (__int128)v.x * ur + (__int128)v.y * ui;
+          mx = max(mx, fx_absmax(ur, ui));
         }
       }
-      ur += fx_mulhi(c.m_hop, hr << c.ph);
-      ui += fx_mulhi(c.m_hop, hi << c.ph);
-      const longlong2 hv = make_longlong2(ur, ui);
-      u[x] = hv;
-      if (LAST) {
-        const longlong2 v = cur[j];
-        a2 += (__int128)v.x * hv.x + (__int128)v.y * hv.y;
-        mx = max(mx, fx_absmax(hv.x, hv.y));
+    }
+    fence_proxy_async_smem();  // the results, written by generic stores, are read by the TMA store
+    workers_sync(nworkers);
+    if (*T.fail) break;
+    if (prod) {
+      tile_store_t<kFxTileBits, 2>(map, FIRST, W, op.N, t, iu, acur);
+      bulk_commit();
+      const int tn = t + (kTmaStages - 1) * G;
+      if (tn < ntiles) {
+        bulk_wait_read_1();  // the stage to refill was stored from at tile k - 1
+        issue(k + kTmaStages - 1, tn);
       }
     }
   }
-  cp_async_wait_all();
+  if (prod) {
+    bulk_wait_all();         // u written before the exchange that follows
+    fence_proxy_async_all();
+    if (*T.fail) {           // tiles still in flight: wait for them, again with a limit
+      for (int s2 = 0; s2 < kTmaStages; ++s2) {
+        const unsigned par = (*T.phase >> s2) & 1u;
+        fx_tile_wait(T.bar + s2, par, T.status, T.timeout_ns);
+      }
+    }
+  }
+  workers_sync(nworkers);
 }
 
 // Scalar part of the phase-A constants (one lane).
@@ -425,7 +482,20 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
   if constexpr (TILED) {
     nwin = tiled_windows<kFxTileBits>(op.N, win);
   }
-  longlong2* tbuf = reinterpret_cast<longlong2*>(smem_raw + ((sizeof(SmemFx) + 127) & ~size_t(127)));
+  // behind SmemFx: the shared-memory basis of one-CTA launches, or the tiled
+  // apply's stage mbarriers (128 bytes) and tile buffers
+  unsigned char* const tiles_base = smem_raw + ((sizeof(SmemFx) + 127) & ~size_t(127));
+  longlong2* tbuf = reinterpret_cast<longlong2*>(tiles_base);
+  unsigned tph = 0;  // parities of the stages' mbarriers (the same in every worker)
+  const FxTma TP{p.tmaps, reinterpret_cast<unsigned long long*>(tiles_base),
+                 reinterpret_cast<longlong2*>(tiles_base + 128), &S.tma_fail, &tph, &p.st->status, p.timeout_ns};
+  if constexpr (TILED) {
+    if (tid == 0) {  // ordered before any use by the CTA barriers of the conversion pass
+      for (int s2 = 0; s2 < kTmaStages; ++s2) mbar_init(TP.bar + s2, 1);
+      S.tma_fail = 0;
+      mbar_init_fence();
+    }
+  }
   int wslot = 0;
   DevStatus* st = p.st;
   const bool glead = (blockIdx.x == 0) && lead;
@@ -579,13 +649,17 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
             if constexpr (TILED) {
               {  // window passes, grid exchanges between them (control warp)
                 for (int w = 0; w < nwin; ++w) {
+                  // basis indices: q_it is vector it - 1, q_{it-1} vector it - 2, u vector it
+                  const int iq = it - 1, ia = w == 0 ? (it > 1 ? it - 2 : 0) : it, iu = it;
                   if (w == 0) {
-                    if (nwin == 1) fx_tiled_pass<true, true>(tbuf, op, c, S.mb, q, qm, u, win[0], wstep, a2, mx);
-                    else fx_tiled_pass<true, false>(tbuf, op, c, S.mb, q, qm, u, win[0], wstep, a2, mx);
+                    if (nwin == 1)
+                      fx_tiled_pass<true, true>(TP, op, c, S.mb, iq, ia, iu, win[0], 0, wstep, a2, mx);
+                    else
+                      fx_tiled_pass<true, false>(TP, op, c, S.mb, iq, ia, iu, win[0], 0, wstep, a2, mx);
                   } else if (w == nwin - 1) {
-                    fx_tiled_pass<false, true>(tbuf, op, c, S.mb, q, qm, u, win[w], wstep, a2, mx);
+                    fx_tiled_pass<false, true>(TP, op, c, S.mb, iq, ia, iu, win[w], w, wstep, a2, mx);
                   } else {
-                    fx_tiled_pass<false, false>(tbuf, op, c, S.mb, q, qm, u, win[w], wstep, a2, mx);
+                    fx_tiled_pass<false, false>(TP, op, c, S.mb, iq, ia, iu, win[w], w, wstep, a2, mx);
                   }
                   if (w + 1 < nwin) {
                     window_written_sync();    // all threads: window w written
@@ -975,7 +1049,9 @@ int launch_propagate_csr_fx(const PropParams& p, const OpCsrFx& op, int grid, in
   return launch_prop_fx<kFamilyCsr>(p, op, grid, block, stream);
 }
 
-size_t fx_tiled_smem_bytes() { return ((sizeof(SmemFx) + 127) & ~size_t(127)) + 4 * kFxTileElems * sizeof(longlong2); }
+size_t fx_tiled_smem_bytes() {
+  return ((sizeof(SmemFx) + 127) & ~size_t(127)) + 128 + (size_t)kTmaStages * 2 * kFxTileBytes;
+}
 
 // Shared memory of a one-CTA launch that holds q_1 .. q_{m_max+1} (0 when it
 // does not fit in an SM's shared memory).

@@ -65,13 +65,16 @@ __device__ __forceinline__ void window_exchanged_sync() { asm volatile("bar.sync
 // ------------------------------------------------------------------ TMA tile transfers
 // Tensor maps of the tiled apply (built on the host over the whole Krylov
 // basis; its vectors are contiguous, so the vector index continues the
-// outermost dimension; every coordinate non-negative, the innermost 0):
-//   window 0: (256, 2^(N-8) nvec) 8-byte elements, box (256, 16): tile t of
-//     vector v at (0, 16 t + 2^(N-8) v) = elements [4096 t, 4096 t + 4096);
+// outermost dimension; every coordinate non-negative, the innermost 0).  For
+// complex64 (one 8-byte word per element, tiles of 2^12):
+//   window 0: (256, 2^(N-8) nvec) words, box (256, 16): tile t of vector v at
+//     (0, 16 t + 2^(N-8) v) = elements [4096 t, 4096 t + 4096);
 //   window w >= 1, c <= 8: (2^c, 2^(b0-c), 2^width, 2^(N-b0-width) nvec), box
 //     (2^c, 1, 2^width, 1) at (0, tl, 0, th + 2^(N-b0-width) v), tile
 //     t = (th << (b0 - c)) | tl;  c > 8: the low bits as (256, 2^(c-8)), box
 //     (256, 2^(c-8), 1, 2^width, 1) at (0, 0, tl, 0, th + ...).
+// The fixed-point maps count two words per element (tiles of 2^11): rows of
+// 128 elements in window 0, the low dimension 2^(c+1) words (split at c > 7).
 //   Shared memory holds the box with dimension 0 fastest: slot
 //   (j & (2^c - 1)) | (window bits << c), the slot order of tile_x.
 constexpr int kTmaMapBytes = 128;    // sizeof(CUtensorMap)
@@ -143,27 +146,45 @@ __device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk
 // Wait until every committed store group has completed its writes.
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
-// Tile t of window W (first: window 0) of vector v of an N-site chain: TMA
-// load into dst (bar completes with the bytes) and TMA store from src.
-__device__ __forceinline__ void tile_load(void* dst, const void* map, bool first, const TileWin& W, int N, int t,
-                                          int v, unsigned long long* bar) {
+// Tile t of window W (first: window 0) of vector v of an N-site chain, tiles of
+// 2^TB elements of WPE 8-byte words (1: complex64, 2: an int64 pair): TMA load
+// into dst (bar completes with the bytes) and TMA store from src.  The maps view
+// the basis in 8-byte words: window 0 as rows of 256 words (2^RS elements,
+// RS = 8 - log2 WPE), a tile being 2^(TB - RS) rows; window w >= 1 as the
+// tile's 2^c low elements (one box dimension while 2^c WPE <= 256 words, else
+// 256 x 2^c WPE / 256), bits [c, b0), the window's bits and the rest.
+template <int TB, int WPE>
+__device__ __forceinline__ void tile_load_t(void* dst, const void* map, bool first, const TileWin& W, int N, int t,
+                                            int v, unsigned long long* bar) {
+  constexpr int RS = WPE == 2 ? 7 : 8;
   if (first) {
-    tma_load_2d(dst, map, 0, (t << 4) + v * (1 << (N - 8)), bar);
+    tma_load_2d(dst, map, 0, (t << (TB - RS)) + v * (1 << (N - RS)), bar);
     return;
   }
   const int nb = W.b0 - W.c, tl = t & ((1 << nb) - 1), th = (t >> nb) + v * (1 << (N - W.b0 - W.width));
-  if (W.c <= 8) tma_load_4d(dst, map, 0, tl, 0, th, bar);
+  if (W.c <= RS) tma_load_4d(dst, map, 0, tl, 0, th, bar);
   else tma_load_5d(dst, map, 0, 0, tl, 0, th, bar);
+}
+template <int TB, int WPE>
+__device__ __forceinline__ void tile_store_t(const void* map, bool first, const TileWin& W, int N, int t, int v,
+                                             const void* src) {
+  constexpr int RS = WPE == 2 ? 7 : 8;
+  if (first) {
+    tma_store_2d(map, 0, (t << (TB - RS)) + v * (1 << (N - RS)), src);
+    return;
+  }
+  const int nb = W.b0 - W.c, tl = t & ((1 << nb) - 1), th = (t >> nb) + v * (1 << (N - W.b0 - W.width));
+  if (W.c <= RS) tma_store_4d(map, 0, tl, 0, th, src);
+  else tma_store_5d(map, 0, 0, tl, 0, th, src);
+}
+// The complex64 kernel's tiles: 2^12 elements of one word.
+__device__ __forceinline__ void tile_load(void* dst, const void* map, bool first, const TileWin& W, int N, int t,
+                                          int v, unsigned long long* bar) {
+  tile_load_t<12, 1>(dst, map, first, W, N, t, v, bar);
 }
 __device__ __forceinline__ void tile_store(const void* map, bool first, const TileWin& W, int N, int t, int v,
                                            const void* src) {
-  if (first) {
-    tma_store_2d(map, 0, (t << 4) + v * (1 << (N - 8)), src);
-    return;
-  }
-  const int nb = W.b0 - W.c, tl = t & ((1 << nb) - 1), th = (t >> nb) + v * (1 << (N - W.b0 - W.width));
-  if (W.c <= 8) tma_store_4d(map, 0, tl, 0, th, src);
-  else tma_store_5d(map, 0, 0, tl, 0, th, src);
+  tile_store_t<12, 1>(map, first, W, N, t, v, src);
 }
 
 }  // namespace cfet
