@@ -938,20 +938,28 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_fx(PropPa
           __int128 a2 = 0;
           long long mx = 0;
           const long long tw0 = sm_clock();
+          // (cr + i ci)(vr + i vi) with three products; the sums (< 2^63) are
+          // halved to stay in fx_mulhi's operand range
+          auto term = [&](int i, const longlong2 v, long long& re, long long& im) {
+            const int pi = S.cp[i];
+            const long long cr = S.crm[i], ci = S.cim[i];
+            const long long vr = v.x << pi, vi = v.y << pi;
+            const long long p1 = fx_mulhi(cr, vr), p2 = fx_mulhi(ci, vi);
+            const long long p3 = fx_mulhi((cr + ci) >> 1, (vr + vi) >> 1) << 2;
+            re += p1 - p2;
+            im += p3 - p1 - p2;
+          };
           for (int x = wx0; x < wxe; x += wstep) {
             long long re = 0, im = 0;
-            for (int i = 0; i < acc_k; ++i) {
-              const longlong2 v = Q(i + 1)[x];
-              const int pi = S.cp[i];
-              const long long cr = S.crm[i], ci = S.cim[i];
-              const long long vr = v.x << pi, vi = v.y << pi;
-              // (cr + i ci)(vr + i vi) with three products; the sums (< 2^63)
-              // are halved to stay in fx_mulhi's operand range
-              const long long p1 = fx_mulhi(cr, vr), p2 = fx_mulhi(ci, vi);
-              const long long p3 = fx_mulhi((cr + ci) >> 1, (vr + vi) >> 1) << 2;
-              re += p1 - p2;
-              im += p3 - p1 - p2;
+            int i = 0;
+            for (; i + 3 < acc_k; i += 4) {  // four basis loads in flight before their use
+              longlong2 v[4];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) v[j] = Q(i + j + 1)[x];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) term(i + j, v[j], re, im);
             }
+            for (; i < acc_k; ++i) term(i, Q(i + 1)[x], re, im);
             Q(1)[x] = make_longlong2(re, im);
             if (final_rec) p.psi[x] = make_double2(__ll2double_rn(re) * outscale, __ll2double_rn(im) * outscale);
             a2 += (__int128)re * re + (__int128)im * im;
