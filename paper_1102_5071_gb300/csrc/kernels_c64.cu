@@ -1083,7 +1083,19 @@ __global__ void __launch_bounds__(CFET_CTL_MAX_THREADS, 1) k_propagate_c64(PropP
           const long long tw0 = sm_clock();
           for (int x = wx0; x < wxe; x += wstep) {
             float re = 0.f, im = 0.f;
-            for (int i = 0; i < acc_k; ++i) {
+            int i = 0;
+            for (; i + 3 < acc_k; i += 4) {  // four basis loads in flight before their use (same order)
+              float2 v[4];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) v[j] = Q(i + j + 1)[x];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const float cr = S.cr[i + j], ci = S.ci[i + j];
+                re = fmaf(cr, v[j].x, fmaf(-ci, v[j].y, re));
+                im = fmaf(cr, v[j].y, fmaf(ci, v[j].x, im));
+              }
+            }
+            for (; i < acc_k; ++i) {
               const float2 v = Q(i + 1)[x];
               const float cr = S.cr[i], ci = S.ci[i];
               re = fmaf(cr, v.x, fmaf(-ci, v.y, re));
