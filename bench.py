@@ -53,11 +53,11 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 fl
 # from one ncu capture of the same kernel build on the 2-step case (76
 # iterations): see profiles/.  Must be reset to None whenever the kernel
 # changes and re-measured.
-DRAM_BYTES_PER_ITERATION = {"fx": (1.195001856e9 + 1.631781376e9) / 76, "c64": None, "f64": None}
+DRAM_BYTES_PER_ITERATION = {"fx": (1.192853248e9 + 1.631790848e9) / 76, "c64": None, "f64": None}
 
 # ncu L2 (lts__t_bytes) bytes per Lanczos iteration of the element-wise fixed-point
 # kernel (2-step capture: 76 iterations, see profiles/); None where not measured
-LTS_BYTES_PER_ITERATION = {"fx": 31852570016 / 76, "c64": None, "f64": None}
+LTS_BYTES_PER_ITERATION = {"fx": 31846678688 / 76, "c64": None, "f64": None}
 
 # final-state error: horizon, and the reference run (CF8:11 at REF_DT, REF_TOL)
 ERR_T = 1.0
