@@ -17,7 +17,9 @@
 //     combined as float-float pairs over the warp and in FP64 over the CTA
 //     and the grid, in one fixed order (every CTA holds bit-identical sums);
 //   * the stage and Lanczos scalars, the tridiagonal exponential, the error
-//     estimate and all decisions are FP64 on the control warp;
+//     estimate and all decisions are FP64-class on the control warp (taken in
+//     FP32 or integers only where scalar_bounds.cuh shows the FP64 decision
+//     for certain);
 //   * psi enters and leaves as complex128; in between it is held as q_1.
 // The result differs from the FP64 method by FP32 rounding of the vectors
 // (relative 2^-24 per element and operation), not by the Krylov decisions.
@@ -28,7 +30,9 @@
 // already apply H for iteration k+1, as in the fixed-point kernel).
 //
 // Long chains: the TILED instantiation applies H in window passes over
-// shared-memory tiles (tiled_common.cuh) instead of element by element.
+// shared-memory tiles moved by TMA (tiled_common.cuh) instead of element by
+// element; its window 0 also does the previous iteration's orthogonalisation
+// step, so it has one grid exchange per iteration less.
 #include <cuda_runtime.h>
 
 #include <cmath>

@@ -23,16 +23,20 @@
 //     rounded to FP64 once.
 //
 // Work split.  Each CTA has NW worker warps doing only integer element work
-// and one control warp doing all FP64 scalar work: the global reductions,
-// the grid barrier, the per-pass constants, and the small tridiagonal
-// exponential of the error estimate.  The error estimate of iteration k runs
+// and one control warp doing all scalar work: the global reductions, the grid
+// barrier, the per-pass constants, and the small tridiagonal exponential of
+// the error estimate (FP64 where the result must be exact; bounds and certain
+// decisions in integer and FP32 arithmetic, scalar_bounds.cuh, because one
+// FP64 warp instruction costs 64 cycles here).  The error estimate of iteration k runs
 // on the control warp while the workers already compute the apply of
 // iteration k+1; if it accepts k, that apply is discarded.  The accepted
 // estimate's y = exp(-i tau T_k) e_1 is reused for the reconstruction.
 //
 // Long chains.  The TILED instantiation replaces the element-wise spin apply
-// by window passes over shared-memory tiles (tiled_common.cuh) separated by
-// grid exchanges, for chains whose vectors leave L2.
+// by window passes over shared-memory tiles moved by TMA (tiled_common.cuh)
+// separated by grid exchanges, for chains whose vectors leave L2.  Small
+// problems.  The SMALL instantiation runs one CTA with the whole Krylov basis
+// in shared memory.
 #include <cuda_runtime.h>
 
 #include <cmath>
