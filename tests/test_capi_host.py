@@ -190,6 +190,18 @@ def test_window_tiling_of_long_chains(lib, tile_bits, nsites, windows):
     assert n.value == windows << nsites
 
 
+@pytest.mark.parametrize("tile_bits", [11, 12])
+def test_window_tiling_every_chain_length(lib, tile_bits):
+    # every chain length the tiled kernels can take up to 24 sites: the window
+    # cover and, for both kernels, every TMA box slot of every tile of three
+    # basis vectors against the tiling (the maps are built the same way at
+    # run time, so a geometry that fails here never reaches the GPU)
+    for nsites in range(max(tile_bits, 13), 25):
+        n = C.c_int64()
+        assert lib.cfet_selftest_tiling(nsites, tile_bits, C.byref(n)) == _capi.CFET_OK, (nsites, lib.cfet_last_error(None))
+        assert n.value >= 2 << nsites
+
+
 def test_window_tiling_selftest_validates(lib):
     n = C.c_int64()
     assert lib.cfet_selftest_tiling(20, 10, C.byref(n)) == _capi.CFET_EINVAL
