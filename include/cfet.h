@@ -627,6 +627,11 @@ cfet_status cfet_selftest_tiling(int32_t nsites, int32_t tile_bits, int64_t* che
  * k in [1, 64]; CFET_EINVAL otherwise or for NULL pointers.                 */
 cfet_status cfet_selftest_i128_to_double(const uint64_t* lo, const int64_t* hi, int64_t n, int32_t shift,
                                          double* out);
+/* cfet_selftest_ll_to_double_up: out[i] = the smallest double not below v[i]
+ * (v[i] >= 0; 0 for v[i] <= 0), for i < n: the conversion of the fixed-point
+ * kernels' int64 maxima, which enter the exponent bounds and must not round
+ * down.  CFET_EINVAL for NULL pointers or n < 0.                            */
+cfet_status cfet_selftest_ll_to_double_up(const int64_t* v, int64_t n, double* out);
 cfet_status cfet_selftest_krylov_bounds(int32_t k, const double* a, const double* b, double ts, double* log2_bounds,
                                         int32_t* gate);
 

@@ -141,6 +141,7 @@ def load() -> C.CDLL:
         "cfet_selftest_wait_timeout": (C.c_int, [C.c_int32, C.c_double, c_int32_p]),
         "cfet_selftest_tiling": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_int64)]),
         "cfet_selftest_i128_to_double": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]),
+        "cfet_selftest_ll_to_double_up": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
         "cfet_selftest_krylov_bounds": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_double,
                                                   C.c_void_p, C.POINTER(C.c_int32)]),
         "cfet_probe_copy_gbs": (C.c_int, [vp, vp, C.c_int64, C.c_int32, vp, c_double_p]),
@@ -170,6 +171,6 @@ EXPORTED = ["cfet_options_default", "cfet_scheme_info", "cfet_chebyshev_coeffici
             "cfet_batch_create", "cfet_batch_destroy", "cfet_batch_last_error", "cfet_batch_size",
             "cfet_batch_propagate", "cfet_batch_tune", "cfet_batch_get_plan", "cfet_batch_set_plan",
             "cfet_batch_kernel_time_ms", "cfet_fidelity_grad", "cfet_selftest_wait_timeout", "cfet_selftest_tiling",
-            "cfet_selftest_i128_to_double", "cfet_selftest_krylov_bounds",
+            "cfet_selftest_i128_to_double", "cfet_selftest_ll_to_double_up", "cfet_selftest_krylov_bounds",
             "cfet_probe_copy_gbs", "cfet_error_constant", "cfet_select_dt", "cfet_propagate_adaptive",
             "cfet_dim", "cfet_num_drives"]

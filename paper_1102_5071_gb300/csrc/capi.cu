@@ -1734,6 +1734,12 @@ cfet_status cfet_selftest_i128_to_double(const uint64_t* lo, const int64_t* hi, 
   return CFET_OK;
 }
 
+cfet_status cfet_selftest_ll_to_double_up(const int64_t* v, int64_t n, double* out) {
+  if (!v || !out || n < 0) return fail(nullptr, CFET_EINVAL, "selftest: v, out required, n >= 0");
+  for (int64_t i = 0; i < n; ++i) out[i] = sb_ll_to_double_up(v[i]);
+  return CFET_OK;
+}
+
 cfet_status cfet_selftest_krylov_bounds(int32_t k, const double* a, const double* b, double ts, double* log2_bounds,
                                         int32_t* gate) {
   if (k < 1 || k > kMaxKrylov || !a || (k > 1 && !b) || !log2_bounds || !gate)

@@ -8,8 +8,8 @@
 // arithmetic with explicit error margins: a helper either returns the FP64
 // decision for certain or says that it cannot, and the caller then evaluates
 // the FP64 form.  Everything here also compiles for the host, where
-// cfet_selftest_i128_to_double and cfet_selftest_krylov_bounds expose it to
-// tests against exact arithmetic.
+// cfet_selftest_i128_to_double, cfet_selftest_ll_to_double_up and
+// cfet_selftest_krylov_bounds expose it to tests against exact arithmetic.
 #pragma once
 
 #include <cuda_runtime.h>

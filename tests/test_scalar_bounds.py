@@ -1,9 +1,10 @@
 """Host checks of the control warp's FP64-free scalar helpers (scalar_bounds.cuh
-compiled for the host behind cfet_selftest_i128_to_double and
-cfet_selftest_krylov_bounds; no GPU).
+compiled for the host behind cfet_selftest_i128_to_double,
+cfet_selftest_ll_to_double_up and cfet_selftest_krylov_bounds; no GPU).
 
 * The exact 128-bit reductions of the fixed-point kernels become doubles by
-  integer operations: compared with Python's correctly rounded int -> float.
+  integer operations: compared with Python's correctly rounded int -> float;
+  the int64 maxima are converted rounding up (checked with exact fractions).
 * The certain decisions on a Krylov dimension (Sec. 8.1's estimate
   beta0 beta_k |y_k|, y = exp(-i ts T_k) e_1) rest on lower and upper bounds
   of |y_k| from the leading Taylor term: checked against y computed in
@@ -54,6 +55,25 @@ def test_i128_to_double_is_correctly_rounded(lib):
         for v, o in zip(vals, out):
             ref = math.ldexp(float(v), shift)  # float(int) rounds to nearest, ties to even
             assert o == ref, (v, shift, o, ref)
+
+
+def test_ll_to_double_up_is_the_smallest_double_not_below(lib):
+    # the int64 maxima of the fixed-point vectors enter the exponent bounds
+    # rounded up: never below the integer, and the next double down is below it
+    from fractions import Fraction
+    rng = random.Random(6)
+    vals = [0, 1, 2, 3, (1 << 53) - 1, 1 << 53, (1 << 53) + 1, (1 << 54) + 1, (1 << 62) - 1, (1 << 63) - 1,
+            (1 << 60) + (1 << 7), -5]
+    vals += [rng.getrandbits(b) for b in (10, 40, 53, 54, 58, 62, 63) for _ in range(30)]
+    v = np.array(vals, dtype=np.int64)
+    out = np.zeros(len(vals))
+    assert lib.cfet_selftest_ll_to_double_up(v.ctypes.data, len(vals), out.ctypes.data) == _capi.CFET_OK
+    for x, o in zip(vals, out):
+        if x <= 0:
+            assert o == 0.0
+            continue
+        assert Fraction(o) >= x, (x, o)
+        assert Fraction(np.nextafter(o, 0.0)) < x, (x, o)
 
 
 def _exact_y(a, b, ts, digits=60):
